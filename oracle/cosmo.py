@@ -1,0 +1,160 @@
+"""Oracle (test infrastructure): cosmology and time-integration coefficients in float64.
+
+Units (the paper fixes none): lengths in Mpc/h, wavenumbers in h/Mpc, time in 1/H0 so
+that H0 = 1, flat LCDM without radiation, H(a)/H0 = sqrt(Om a^-3 + 1 - Om).  The
+parameter vector is theta = (A_s, n_s, Omega_m, Omega_b, h) (Sec. 2.1).  Every function
+accepts complex theta so that derivatives can be taken by the complex step
+df/dx = Im f(x + i eps) / eps, which is exact to rounding for analytic functions.
+"""
+import numpy as np
+
+C_OVER_H0 = 2997.92458     # c / (100 km/s/Mpc) in Mpc/h
+T_CMB = 2.7255             # K
+K_PIVOT = 0.05             # 1/Mpc (not h/Mpc); the paper leaves it unstated
+A_IC = 1e-4                # start of the growth integration (App. A leaves it unstated)
+LNA_STEP = 1.0 / 512.0     # largest RK4 step in ln a
+
+THETA_NAMES = ("A_s", "n_s", "Omega_m", "Omega_b", "h")
+
+
+def hubble(a, Om):
+    """E(a) = H(a)/H0 for flat LCDM (reading of the units; Sec. 2.1 and App. A)."""
+    return np.sqrt(Om * a ** -3 + (1.0 - Om))
+
+
+def omega_m_of_a(a, Om):
+    """Omega_m(a) = Omega_m H0^2 / (a^3 H^2)  (App. A, Eq. 53)."""
+    return Om * a ** -3 / hubble(a, Om) ** 2
+
+
+def _growth_rhs(lna, y, Om):
+    """Right-hand side of the first-order suppression-factor ODE (App. A, Eq. 56).
+
+    y = (G1, G1') with ' = d/d ln a.  With H'/H = -3/2 Omega_m(a) for flat LCDM,
+    G1'' = -(4 + H'/H) G1' - (3 + H'/H - 3/2 Omega_m(a)) G1.
+    """
+    a = np.exp(lna)
+    om = omega_m_of_a(a, Om)
+    dlnh = -1.5 * om
+    g, dg = y
+    ddg = -(4.0 + dlnh) * dg - (3.0 + dlnh - 1.5 * om) * g
+    return np.array([dg, ddg])
+
+
+def growth_g1(a_targets, Om):
+    """G1 = D1/a and G1' = dG1/dln a at each a in ``a_targets`` (App. A, Eqs. 55-57).
+
+    Classical RK4 in ln a from a_ic = 1e-4 with G1 = 1, G1' = 0 (Eq. 57), stepping to
+    each target exactly (no interpolation) with steps no larger than 1/512 in ln a.
+    Pinned: Omega_m = 1 gives G1 = 1 exactly; for LCDM D1 matches the integral form
+    D1 ~ H(a) int da / (a H)^3 (tests/test_oracle_cosmo.py).
+    """
+    a_targets = np.asarray(a_targets, dtype=np.float64)
+    order = np.argsort(a_targets)
+    out_g = np.zeros(a_targets.shape, dtype=np.result_type(Om, np.float64))
+    out_dg = np.zeros_like(out_g)
+    y = np.array([1.0 + 0.0 * Om, 0.0 * Om])
+    lna = np.log(A_IC)
+    for idx in order:
+        target = np.log(a_targets[idx])
+        span = target - lna
+        nsub = int(np.ceil(span / LNA_STEP)) if span > 0 else 0
+        if nsub > 0:
+            h = span / nsub
+            for _ in range(nsub):
+                k1 = _growth_rhs(lna, y, Om)
+                k2 = _growth_rhs(lna + 0.5 * h, y + 0.5 * h * k1, Om)
+                k3 = _growth_rhs(lna + 0.5 * h, y + 0.5 * h * k2, Om)
+                k4 = _growth_rhs(lna + h, y + h * k3, Om)
+                y = y + (h / 6.0) * (k1 + 2 * k2 + 2 * k3 + k4)
+                lna = lna + h
+            lna = target
+        out_g[idx] = y[0]
+        out_dg[idx] = y[1]
+    return out_g, out_dg
+
+
+def growth_factors(a, Om):
+    """D1, D1' (= dD1/dln a), G_D and G_K at scale factors ``a``.
+
+    D1 = a G1 and D1' = a (G1 + G1') (App. A, Eq. 59 with m = 1);
+    G_D = a^2 H D1' (App. A, Eq. 58);
+    G_K = a^3 H^2 [D1'' + (2 + H'/H) D1'], which by the D1 growth equation (App. A,
+    Eq. 52) equals (3/2) Omega_m H0^2 D1 -- the closed form used here.  The test suite
+    checks it against the Eq. 58 form evaluated with D1'' from the ODE.
+    """
+    a = np.asarray(a, dtype=np.float64)
+    g, dg = growth_g1(a, Om)
+    d1 = a * g
+    dd1 = a * (g + dg)
+    gd = a ** 2 * hubble(a, Om) * dd1
+    gk = 1.5 * Om * d1
+    return d1, dd1, gd, gk
+
+
+def time_grid(a0, a1, n_steps):
+    """Scale factors a_0..a_n linear in a (Sec. 4, 'time steps linearly spaced in a')."""
+    return a0 + (a1 - a0) * np.arange(n_steps + 1, dtype=np.float64) / n_steps
+
+
+def kdk_factors(a_grid, Om):
+    """FastPM kick/drift factors for each step i = 1..n (Sec. 2.3, Eqs. 15-16).
+
+    With a_{i-1/2} the arithmetic mean of a_{i-1} and a_i (the paper does not fix it):
+      K1_i = K(t_{i-1}, t_{i-1}, t_{i-1/2}) = [G_D(a_{i-1/2}) - G_D(a_{i-1})] / G_K(a_{i-1})
+      D_i  = D(t_{i-1/2}, t_{i-1}, t_i)    = [D1(a_i) - D1(a_{i-1})] / G_D(a_{i-1/2})
+      K2_i = K(t_i, t_{i-1/2}, t_i)        = [G_D(a_i) - G_D(a_{i-1/2})] / G_K(a_i)
+    Returns arrays (K1, D, K2), each of length n.  Pinned by the Zel'dovich exactness of
+    the leapfrog with the linear-theory force (tests/test_oracle_pm.py).
+    """
+    a_grid = np.asarray(a_grid, dtype=np.float64)
+    a_half = 0.5 * (a_grid[:-1] + a_grid[1:])
+    d1, _, gd, gk = growth_factors(a_grid, Om)
+    d1h, _, gdh, _ = growth_factors(a_half, Om)
+    k1 = (gdh - gd[:-1]) / gk[:-1]
+    dd = (d1[1:] - d1[:-1]) / gdh
+    k2 = (gd[1:] - gdh) / gk[1:]
+    return k1, dd, k2
+
+
+def transfer_eh_nowiggle(k, Om, Ob, h, tcmb=T_CMB):
+    """Eisenstein & Hu (1998) no-wiggle transfer function, k in h/Mpc (Sec. 2.1).
+
+    The paper names the fitting formula but does not print it.  Transcribed from
+    Eisenstein & Hu 1998, ApJ 496, 605: sound horizon fit (their Eq. 26), alpha_Gamma
+    (Eq. 31), Gamma_eff (Eq. 30), q (Eq. 28), T0(q) = L0 / (L0 + C0 q^2) (Eq. 29).
+    Parity unpinned beyond the limits T -> 1 as k -> 0, monotone decrease in k and the
+    zero-baryon case (alpha_Gamma = 1).
+    """
+    omh2 = Om * h * h
+    obh2 = Ob * h * h
+    fb = Ob / Om
+    theta27 = tcmb / 2.7
+    s = 44.5 * np.log(9.83 / omh2) / np.sqrt(1.0 + 10.0 * obh2 ** 0.75)
+    alpha = 1.0 - 0.328 * np.log(431.0 * omh2) * fb + 0.38 * np.log(22.3 * omh2) * fb * fb
+    k_mpc = k * h
+    gamma_eff = Om * h * (alpha + (1.0 - alpha) / (1.0 + (0.43 * k_mpc * s) ** 4))
+    q = k * theta27 ** 2 / gamma_eff
+    l0 = np.log(2.0 * np.e + 1.8 * q)
+    c0 = 14.2 + 731.0 / (1.0 + 62.5 * q)
+    return l0 / (l0 + c0 * q * q)
+
+
+def plin(k, theta):
+    """Linear matter power spectrum P_lin(k) in (Mpc/h)^3 at D1 = a normalisation.
+
+    Sec. 2.1, Eq. 7:  k^3 P / (2 pi^2) = 4/25 A_s (k/k_pivot)^(n_s-1) T^2(k) c^4 k^4 /
+    (Omega_m^2 H0^4), with k in h/Mpc, k_pivot = 0.05/Mpc = 0.05/h h/Mpc and c/H0 in
+    Mpc/h.  k must be > 0.
+    """
+    As, ns, Om, Ob, h = theta
+    t = transfer_eh_nowiggle(k, Om, Ob, h)
+    return (2.0 * np.pi ** 2 / k ** 3 * 0.16 * As * (k * h / K_PIVOT) ** (ns - 1.0)
+            * t * t * (C_OVER_H0 * k) ** 4 / Om ** 2)
+
+
+def complex_step(fn, theta, j, eps=1e-30):
+    """d fn(theta) / d theta_j by the complex step (exact to rounding for analytic fn)."""
+    th = np.array(theta, dtype=np.complex128)
+    th[j] += 1j * eps
+    return np.imag(fn(th)) / eps

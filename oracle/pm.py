@@ -1,0 +1,359 @@
+"""Oracle (test infrastructure): particle-mesh forward model and discrete adjoint, float64.
+
+Conventions (the paper leaves them open; the same readings bind the CUDA library):
+
+* Periodic box of side L, mesh of n_mesh^3 nodes at g * l (l = L / n_mesh), particle
+  lattice of n_ptcl^3 points q = j * l_p + l/2 (l_p = L / n_ptcl), arrays in C order with the
+  last axis fastest; vector fields are (3, N) with component c along array axis c.
+* DFT with e^{-i k.x} and no normalisation forward, 1/N^3 on the inverse; k = 2 pi n / L
+  with n in [-N/2, N/2); the k = 0 mode of every Green's function is 0; a derivative
+  -i k_c (or +i k_c) is zeroed on the Nyquist plane of axis c.
+* CIC weights by the floor convention: u = x / l, i = floor(u), t = u - i, weight 1 - t to
+  node i and t to node i + 1 per axis; the weight gradient is -1/l and +1/l (the right
+  derivative at the kink).
+* Particle mass m = n_mesh^3 / n_ptcl^3 so that the mean density is 1 and
+  delta = rho - 1.
+"""
+from dataclasses import dataclass
+import itertools
+
+import numpy as np
+
+from . import cosmo
+
+
+@dataclass(frozen=True)
+class PMConfig:
+    box: float          # L in Mpc/h
+    n_mesh: int         # mesh nodes per side
+    n_ptcl: int         # particles per side
+    a0: float = 1.0 / 64
+    a1: float = 1.0
+    n_steps: int = 10
+    deconv: bool = False
+
+    @property
+    def cell(self):
+        return self.box / self.n_mesh
+
+    @property
+    def mass(self):
+        return float(self.n_mesh) ** 3 / float(self.n_ptcl) ** 3
+
+
+# ----------------------------------------------------------------------------- lattice
+
+def lattice(cfg):
+    """Lagrangian lattice positions q = j l_p + l/2, shape (3, N) (Sec. 2.1, Eq. 1).
+
+    The half-cell offset (a reading: the paper only says "a Cartesian grid") puts
+    unperturbed particles at mesh-cell centres, where the CIC weight of Eq. 10 is
+    differentiable, instead of on the nodes, where its kink makes the linear response
+    of the density depend on the sign of the displacement."""
+    n = cfg.n_ptcl
+    idx = np.indices((n, n, n)).reshape(3, -1).astype(np.float64)
+    return idx * (cfg.box / n) + 0.5 * cfg.cell
+
+
+def _kgrid(n, box):
+    """Wavevector components on the rfftn layout (last axis halved) and n^2 = |n|^2."""
+    f = np.fft.fftfreq(n, d=1.0 / n)                # integers in [-n/2, n/2)
+    n0 = f.reshape(n, 1, 1)
+    n1 = f.reshape(1, n, 1)
+    n2 = np.arange(n // 2 + 1, dtype=np.float64).reshape(1, 1, n // 2 + 1)
+    kf = 2.0 * np.pi / box
+    return (kf * n0, kf * n1, kf * n2), (n0, n1, n2)
+
+
+def _derivative_multipliers(n, box):
+    """i k_c with the Nyquist plane of axis c zeroed, and k^2 (k = 0 set to 1)."""
+    (k0, k1, k2), (n0, n1, n2) = _kgrid(n, box)
+    ks = []
+    for kc, nc in ((k0, n0), (k1, n1), (k2, n2)):
+        ks.append(np.where(np.abs(nc) == n // 2, 0.0, kc))
+    k2sum = k0 ** 2 + k1 ** 2 + k2 ** 2
+    return ks, k2sum
+
+
+# ------------------------------------------------------------------ initial conditions
+
+def za_unit_displacement(omega, theta, cfg, dlnp=None):
+    """First-order displacement s^(1) on the lattice for unit growth (Sec. 2.1).
+
+    delta1(k) = sqrt(P_lin(k) / l_p^3) * DFT[omega](k)   (Eq. 6 with the lattice
+    normalisation <|DFT omega|^2> = N and delta_cont(k) = l_p^3 DFT[delta]);
+    s1 = -grad phi_s with laplacian phi_s = delta1 (Eqs. 3-4), i.e.
+    s1_c = IDFT[ i k_c / k^2 * delta1(k) ].
+    If ``dlnp`` (a callable k -> d ln P / d theta_j) is given, returns
+    d s1 / d theta_j = IDFT[ i k_c / k^2 * (1/2 dlnp) * delta1 ] instead.
+    Pinned by the ensemble power spectrum of delta1 and by the Zel'dovich growth tests.
+    """
+    n, box = cfg.n_ptcl, cfg.box
+    lp = box / n
+    ks, k2 = _derivative_multipliers(n, box)
+    k = np.sqrt(k2)
+    k_safe = np.where(k2 > 0, k, 1.0)
+    amp = np.sqrt(cosmo.plin(k_safe, theta) / lp ** 3)
+    if dlnp is not None:
+        amp = amp * 0.5 * dlnp(k_safe)
+    amp = np.where(k2 > 0, amp, 0.0)
+    wk = np.fft.rfftn(np.asarray(omega, dtype=np.float64).reshape(n, n, n))
+    dk = amp * wk
+    out = np.empty((3, n ** 3))
+    for c in range(3):
+        out[c] = np.fft.irfftn(1j * ks[c] / np.where(k2 > 0, k2, 1.0) * dk, s=(n, n, n), axes=(0, 1, 2)).ravel()
+    return out
+
+
+def za_initial_state(omega, theta, cfg):
+    """Zel'dovich initial conditions at a0: s0 = D1 s1, p0 = G_D s1 (Sec. 2.1, Eq. 2 at
+    first order, with p = a^2 H D1' s1 = G_D s1 by Eq. 14/58)."""
+    s1 = za_unit_displacement(omega, theta, cfg)
+    d1, _, gd, _ = cosmo.growth_factors(np.array([cfg.a0]), theta[2])
+    return d1[0] * s1, gd[0] * s1, s1
+
+
+# ------------------------------------------------------------------------------- CIC
+
+def _cic_corners(x, cfg):
+    """Yield (flat node index, weight, weight gradient (3, N)) for the 8 CIC corners of
+    every particle (Sec. 2.2, Eq. 10, floor convention)."""
+    n, l = cfg.n_mesh, cfg.cell
+    u = x / l
+    i = np.floor(u)
+    t = u - i
+    i = i.astype(np.int64)
+    for d in itertools.product((0, 1), repeat=3):
+        w1 = [t[c] if d[c] else 1.0 - t[c] for c in range(3)]
+        dw1 = [(1.0 / l if d[c] else -1.0 / l) * np.ones_like(t[c]) for c in range(3)]
+        w = w1[0] * w1[1] * w1[2]
+        grad = np.stack([dw1[0] * w1[1] * w1[2], w1[0] * dw1[1] * w1[2], w1[0] * w1[1] * dw1[2]])
+        idx = (((i[0] + d[0]) % n) * n + (i[1] + d[1]) % n) * n + (i[2] + d[2]) % n
+        yield idx, w, grad
+
+
+def cic_scatter(x, values, cfg):
+    """Mesh field sum_j values_j W(x_g, x_j) (Sec. 2.2, Eq. 10)."""
+    m = cfg.n_mesh ** 3
+    out = np.zeros(m)
+    for idx, w, _ in _cic_corners(x, cfg):
+        out += np.bincount(idx, weights=values * w, minlength=m)
+    return out.reshape((cfg.n_mesh,) * 3)
+
+
+def cic_gather(mesh, x, cfg):
+    """Particle values sum_g W(x_g, x_j) mesh(g) (Sec. 2.2, the gather with Eq. 10)."""
+    flat = mesh.ravel()
+    out = np.zeros(x.shape[1])
+    for idx, w, _ in _cic_corners(x, cfg):
+        out += w * flat[idx]
+    return out
+
+
+def cic_gather_grad(mesh, x, cfg):
+    """sum_g grad_{x_j} W(x_g, x_j) mesh(g), shape (3, N): derivative of the gather with
+    respect to the particle position (the weight-gradient term of the force VJP)."""
+    flat = mesh.ravel()
+    out = np.zeros((3, x.shape[1]))
+    for idx, _, grad in _cic_corners(x, cfg):
+        out += grad * flat[idx]
+    return out
+
+
+def density(x, cfg):
+    """Overdensity delta = rho - 1 with rho = m sum_j W (Sec. 2.1 definition of delta)."""
+    return cic_scatter(x, np.full(x.shape[1], cfg.mass), cfg) - 1.0
+
+
+# ----------------------------------------------------------------------------- force
+
+def _green(cfg, Om):
+    """Fourier multipliers H_c(k) = -i k_c G(k), G(k) = -3/2 Omega_m / k^2, G(0) = 0
+    (Sec. 2.2, Eq. 11 and the -i k gradient), optionally divided by the CIC window
+    prod_c sinc^4(k_c l / 2) (deconvolution for scatter and gather)."""
+    n = cfg.n_mesh
+    ks, k2 = _derivative_multipliers(n, cfg.box)
+    g = np.where(k2 > 0, -1.5 * Om / np.where(k2 > 0, k2, 1.0), 0.0)
+    if cfg.deconv:
+        (k0, k1, k2c), _ = _kgrid(n, cfg.box)
+        win = 1.0
+        for kc in (k0, k1, k2c):
+            win = win * np.sinc(kc * cfg.cell / (2.0 * np.pi)) ** 4
+        g = g / win
+    return [-1j * kc * g for kc in ks]
+
+
+def force_meshes(delta, Om, cfg):
+    """Force field f_c = -d_c varphi on the mesh from delta (Sec. 2.2): one forward DFT,
+    the multiplier -i k_c G(k), three inverse DFTs."""
+    n = cfg.n_mesh
+    dk = np.fft.rfftn(delta)
+    return np.stack([np.fft.irfftn(h * dk, s=(n, n, n), axes=(0, 1, 2)) for h in _green(cfg, Om)])
+
+
+def pm_force(x, Om, cfg):
+    """Particle accelerations a = -grad varphi(x) (Sec. 2.2; operator F of Eq. 16)."""
+    f = force_meshes(density(x, cfg), Om, cfg)
+    return np.stack([cic_gather(f[c], x, cfg) for c in range(3)]), f
+
+
+def force_vjp(x, pi, f, Om, cfg):
+    """alpha = pi . d a / d x (Sec. 3.6, Eq. 49 second line of F), written out:
+
+    alpha_j = sum_g grad_{x_j} W(x_g, x_j) [ pi_j . f(g) + m psi(g) ],
+    psi = sum_c L_c^T scatter(pi_c), L_c^T = IDFT conj(H_c) DFT (the transpose of the
+    real operator delta -> f_c).  The first term is the gather-weight derivative, the
+    second the dependence of the density on the positions.
+    """
+    n = cfg.n_mesh
+    alpha = np.zeros_like(pi)
+    for c in range(3):
+        alpha += pi[c] * cic_gather_grad(f[c], x, cfg)
+    hs = _green(cfg, Om)
+    psi_k = 0.0
+    for c in range(3):
+        psi_k = psi_k + np.conj(hs[c]) * np.fft.rfftn(cic_scatter(x, pi[c], cfg))
+    psi = np.fft.irfftn(psi_k, s=(n, n, n), axes=(0, 1, 2))
+    alpha += cfg.mass * cic_gather_grad(psi, x, cfg)
+    return alpha
+
+
+# ------------------------------------------------------------------------- integrate
+
+def forward(omega, theta, cfg, store_every=0, force_fn=None):
+    """Zel'dovich ICs then the FastPM kick-drift-kick leapfrog (Sec. 2.3, Eq. 16).
+
+    a_0 = F_0 first; then for i = 1..n: p += a K1_i; s += p D_i; a = F_i; p += a K2_i.
+    Returns a dict with the final displacement s, momentum p, acceleration a, the
+    density delta_n at a_n, and (store_every > 0) the states (s_j, p_j) at steps
+    j = 0, k, 2k, ... for the checkpointed adjoint.  ``force_fn(x, s)`` replaces the PM
+    force (used by the Zel'dovich-exactness pin with the linear-theory force).
+    """
+    q = lattice(cfg)
+    Om = theta[2]
+    if force_fn is None:
+        def force_fn(x, _s):
+            return pm_force(x, Om, cfg)[0]
+    s, p, _ = za_initial_state(omega, theta, cfg)
+    k1, dd, k2 = cosmo.kdk_factors(cosmo.time_grid(cfg.a0, cfg.a1, cfg.n_steps), Om)
+    store = {}
+    if store_every:
+        store[0] = (s.copy(), p.copy())
+    a = force_fn(q + s, s)
+    for i in range(1, cfg.n_steps + 1):
+        p = p + a * k1[i - 1]
+        s = s + p * dd[i - 1]
+        a = force_fn(q + s, s)
+        p = p + a * k2[i - 1]
+        if store_every and i % store_every == 0:
+            store[i] = (s.copy(), p.copy())
+    return dict(s=s, p=p, a=a, delta=density(q + s, cfg), store=store)
+
+
+def mse_loss(delta, target):
+    """Objective J = mean_g (delta(g) - target(g))^2 on the final density mesh (Sec. 2.4,
+    Eq. 17 as a field-level MSE) and its derivative dJ/d delta."""
+    diff = delta - target
+    return float(np.mean(diff * diff)), 2.0 * diff / diff.size
+
+
+def _dlnp_funcs(theta):
+    """d ln P_lin / d theta_j (j = 0..4) by the complex step, as callables of k."""
+    def make(j):
+        return lambda k: cosmo.complex_step(lambda th: np.log(cosmo.plin(k, th)), theta, j)
+    return [make(j) for j in range(5)]
+
+
+def adjoint(omega, theta, cfg, fwd, dj_ddelta=None, dj_ds=None, dj_dp=None, ckpt=None):
+    """Discrete adjoint with reverse time integration (Sec. 3.6, Eqs. 49-51).
+
+    Starts from the final state in ``fwd`` and integrates the leapfrog backward jointly
+    with (xi, pi).  Initial conditions (Eq. 50): xi_n = dJ/dx_n, pi_n = dJ/dp_n, and
+    a_n, alpha_n, zeta_n from F_n.  For i = n..1:
+      K_i^{i-1/2}:  p -= a K2_i;  xi += alpha K2_i;  g += (pi.a) dK2_i + zeta K2_i
+      D_i^{i-1}:    g += (xi.p) dD_i;  s -= p D_i;  pi += xi D_i
+      F_{i-1}:      a, alpha = pi . da/dx, zeta = pi . da/dtheta = (pi.a)/Omega_m e_Om
+      K_{i-1/2}^{i-1}: p -= a K1_i;  xi += alpha K1_i;  g += (pi.a) dK1_i + zeta K1_i
+    (D(t_c,t_b,t_a) = -D(t_c,t_a,t_b) turns the printed signs into these.)  Finally
+    (Eq. 51) dJ/domega = (D1 xi_0 + G_D pi_0) . ds1/domega and the theta terms of the
+    initial conditions.  ``ckpt`` maps step j to a stored (s_j, p_j) that replaces the
+    reverse-integrated state when step j is reached (piecewise resumption, Sec. 3.5).
+    Returns dict(grad_omega (n_ptcl^3,), grad_theta (5,), s0, p0 (reverse-integrated)).
+    """
+    q = lattice(cfg)
+    Om = theta[2]
+    n = cfg.n_steps
+    agrid = cosmo.time_grid(cfg.a0, cfg.a1, n)
+    k1, dd, k2 = cosmo.kdk_factors(agrid, Om)
+    dk1, ddd, dk2 = (cosmo.complex_step(lambda th: cosmo.kdk_factors(agrid, th[2])[j], theta, 2)
+                     for j in range(3))
+    ckpt = ckpt or {}
+    s = fwd["s"].copy()
+    p = fwd["p"].copy()
+    g_om = 0.0
+    x = q + s
+    xi = np.zeros_like(s)
+    if dj_ddelta is not None:
+        xi += cfg.mass * cic_gather_grad(np.asarray(dj_ddelta).reshape((cfg.n_mesh,) * 3), x, cfg)
+    if dj_ds is not None:
+        xi += dj_ds
+    pi = np.zeros_like(s) if dj_dp is None else np.array(dj_dp, dtype=np.float64)
+    a, f = pm_force(x, Om, cfg)
+    alpha = force_vjp(x, pi, f, Om, cfg)
+    for i in range(n, 0, -1):
+        pa = float(np.sum(pi * a))
+        p = p - a * k2[i - 1]
+        xi = xi + alpha * k2[i - 1]
+        g_om += pa * dk2[i - 1] + (pa / Om) * k2[i - 1]
+        g_om += float(np.sum(xi * p)) * ddd[i - 1]
+        s = s - p * dd[i - 1]
+        pi = pi + xi * dd[i - 1]
+        if (i - 1) in ckpt:
+            s = ckpt[i - 1][0].copy()
+        x = q + s
+        a, f = pm_force(x, Om, cfg)
+        alpha = force_vjp(x, pi, f, Om, cfg)
+        pa = float(np.sum(pi * a))
+        p = p - a * k1[i - 1]
+        xi = xi + alpha * k1[i - 1]
+        g_om += pa * dk1[i - 1] + (pa / Om) * k1[i - 1]
+        if (i - 1) in ckpt:
+            p = ckpt[i - 1][1].copy()
+    # initial conditions (Eq. 51): x0 = q + D1(a0) s1, p0 = G_D(a0) s1
+    d1, _, gd, _ = cosmo.growth_factors(np.array([cfg.a0]), Om)
+    dd1 = cosmo.complex_step(lambda th: cosmo.growth_factors(np.array([cfg.a0]), th[2])[0], theta, 2)[0]
+    dgd = cosmo.complex_step(lambda th: cosmo.growth_factors(np.array([cfg.a0]), th[2])[2], theta, 2)[0]
+    s1 = za_unit_displacement(omega, theta, cfg)
+    sbar = d1[0] * xi + gd[0] * pi
+    grad_theta = np.zeros(5)
+    for j, dlnp in enumerate(_dlnp_funcs(theta)):
+        grad_theta[j] = float(np.sum(sbar * za_unit_displacement(omega, theta, cfg, dlnp=dlnp)))
+    grad_theta[2] += g_om + float(np.sum(xi * s1)) * dd1 + float(np.sum(pi * s1)) * dgd
+    grad_omega = za_transpose(sbar, theta, cfg)
+    return dict(grad_omega=grad_omega, grad_theta=grad_theta, s0=s, p0=p, xi0=xi, pi0=pi)
+
+
+def za_transpose(sbar, theta, cfg):
+    """Transpose of the linear map omega -> s1 applied to sbar (3, N):
+    sum_c IDFT[ conj(i k_c sqrt(P/l_p^3) / k^2) DFT[sbar_c] ] (adjoint of Sec. 2.1's
+    Eq. 6 chain).  Pinned by the dot-product test <v, s1(w)> = <ZA^T(v), w>."""
+    n, box = cfg.n_ptcl, cfg.box
+    lp = box / n
+    ks, k2 = _derivative_multipliers(n, box)
+    k_safe = np.where(k2 > 0, np.sqrt(k2), 1.0)
+    amp = np.where(k2 > 0, np.sqrt(cosmo.plin(k_safe, theta) / lp ** 3), 0.0)
+    acc = 0.0
+    for c in range(3):
+        b = 1j * ks[c] / np.where(k2 > 0, k2, 1.0) * amp
+        acc = acc + np.conj(b) * np.fft.rfftn(sbar[c].reshape(n, n, n))
+    return np.fft.irfftn(acc, s=(n, n, n), axes=(0, 1, 2)).ravel()
+
+
+def loss_and_gradient(omega, theta, target, cfg, ckpt_every=0):
+    """J(omega, theta) = MSE(delta_n, target) and (dJ/domega, dJ/dtheta) by the adjoint.
+    ``ckpt_every`` > 0 resumes the reverse pass from states stored every k steps."""
+    fwd = forward(omega, theta, cfg, store_every=ckpt_every)
+    loss, dj = mse_loss(fwd["delta"], target)
+    ckpt = fwd["store"] if ckpt_every else None
+    adj = adjoint(omega, theta, cfg, fwd, dj_ddelta=dj, ckpt=ckpt)
+    return loss, adj, fwd

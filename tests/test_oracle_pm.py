@@ -1,0 +1,302 @@
+"""Pins for the oracle's particle-mesh forward model and adjoint (CPU only).
+
+Each test checks the oracle against something other than itself: exact invariants of
+CIC and of the antisymmetric force operator, a brute-force DFT, Newton's law, the
+Zel'dovich solution, linear growth, reversibility and central finite differences.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import cosmo, pm
+from paper_2211_09815_gb300 import inputs
+
+THETA = inputs.THETA_FIDUCIAL
+
+
+def _rand_positions(rng, n, box):
+    return rng.uniform(0, box, size=(3, n))
+
+
+# ------------------------------------------------------------------------------ CIC
+
+def test_cic_mass_conservation_and_lattice_node():
+    cfg = pm.PMConfig(box=10.0, n_mesh=8, n_ptcl=4)
+    rng = np.random.default_rng(0)
+    x = _rand_positions(rng, 64, cfg.box)
+    rho = pm.cic_scatter(x, np.full(64, cfg.mass), cfg)
+    assert abs(rho.sum() - 64 * cfg.mass) < 1e-12 * 64 * cfg.mass
+    # a particle on a node puts all its mass into that node
+    xn = np.array([[3 * cfg.cell], [5 * cfg.cell], [7 * cfg.cell]])
+    rho1 = pm.cic_scatter(xn, np.array([1.0]), cfg)
+    assert rho1[3, 5, 7] == pytest.approx(1.0, abs=1e-15)
+    assert abs(rho1.sum() - 1.0) < 1e-15
+    # gather of a constant field is that constant (weights sum to 1)
+    assert np.allclose(pm.cic_gather(np.full((8, 8, 8), 2.5), x, cfg), 2.5, atol=1e-14)
+
+
+def test_cic_periodic_wrap():
+    cfg = pm.PMConfig(box=10.0, n_mesh=8, n_ptcl=4)
+    x = np.array([[cfg.box - 0.25 * cfg.cell], [0.0], [0.0]])
+    rho = pm.cic_scatter(x, np.array([1.0]), cfg)
+    assert rho[7, 0, 0] == pytest.approx(0.25)
+    assert rho[0, 0, 0] == pytest.approx(0.75)
+
+
+def test_scatter_is_transpose_of_gather():
+    cfg = pm.PMConfig(box=10.0, n_mesh=8, n_ptcl=4)
+    rng = np.random.default_rng(1)
+    x = _rand_positions(rng, 50, cfg.box)
+    v = rng.normal(size=50)
+    mesh = rng.normal(size=(8, 8, 8))
+    lhs = np.dot(pm.cic_gather(mesh, x, cfg), v)
+    rhs = np.sum(mesh * pm.cic_scatter(x, v, cfg))
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_gather_gradient_matches_finite_difference():
+    cfg = pm.PMConfig(box=10.0, n_mesh=8, n_ptcl=4)
+    rng = np.random.default_rng(2)
+    x = _rand_positions(rng, 20, cfg.box)
+    mesh = rng.normal(size=(8, 8, 8))
+    g = pm.cic_gather_grad(mesh, x, cfg)
+    h = 1e-7
+    for c in range(3):
+        xp, xm = x.copy(), x.copy()
+        xp[c] += h
+        xm[c] -= h
+        fd = (pm.cic_gather(mesh, xp, cfg) - pm.cic_gather(mesh, xm, cfg)) / (2 * h)
+        assert np.allclose(fd, g[c], rtol=1e-6, atol=1e-7)
+
+
+# -------------------------------------------------------------------------- Fourier
+
+def _naive_force(delta, Om, box):
+    """Brute-force O(N^6) evaluation of f_c(x) = 1/N^3 sum_k H_c(k) sum_y delta(y)
+    e^{-ik(y-x)} over the full k grid, H_c = -i k_c (-3/2 Om / k^2), Nyquist of axis c
+    zeroed, k = 0 dropped (Sec. 2.2, Eq. 11 and the -ik gradient)."""
+    n = delta.shape[0]
+    idx = np.array(list(itertools.product(range(n), repeat=3)))          # (N, 3)
+    freq = np.where(idx >= n // 2, idx - n, idx).astype(float)            # n in [-N/2, N/2)
+    k = 2 * np.pi / box * freq
+    k2 = np.sum(k * k, axis=1)
+    phase = np.exp(-2j * np.pi * (freq @ idx.T) / n)                      # (k, y)
+    dk = phase @ delta.ravel()
+    out = []
+    for c in range(3):
+        kc = np.where(np.abs(freq[:, c]) == n // 2, 0.0, k[:, c])
+        h = np.where(k2 > 0, -1j * kc * (-1.5 * Om) / np.where(k2 > 0, k2, 1), 0)
+        out.append(np.real(np.conj(phase).T @ (h * dk)) / n ** 3)
+    return np.stack(out)
+
+
+def test_force_mesh_matches_naive_dft_8cubed():
+    cfg = pm.PMConfig(box=50.0, n_mesh=8, n_ptcl=4)
+    rng = np.random.default_rng(3)
+    delta = rng.normal(size=(8, 8, 8))
+    f = pm.force_meshes(delta, 0.31, cfg)
+    ref = _naive_force(delta, 0.31, cfg.box)
+    assert np.allclose(f.reshape(3, -1), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_force_operator_is_antisymmetric():
+    """<u, L_c v> = -<L_c u, v>: the -ik_c G kernel is odd, so the net force vanishes."""
+    cfg = pm.PMConfig(box=50.0, n_mesh=16, n_ptcl=8)
+    rng = np.random.default_rng(4)
+    u = rng.normal(size=(16, 16, 16))
+    v = rng.normal(size=(16, 16, 16))
+    fu = pm.force_meshes(u, 0.31, cfg)
+    fv = pm.force_meshes(v, 0.31, cfg)
+    for c in range(3):
+        a = np.sum(u * fv[c])
+        b = np.sum(fu[c] * v)
+        assert abs(a + b) < 1e-12 * (abs(a) + 1e-30)
+
+
+def test_zero_net_force_and_zero_self_force():
+    cfg = pm.PMConfig(box=50.0, n_mesh=16, n_ptcl=8)
+    rng = np.random.default_rng(5)
+    x = _rand_positions(rng, 300, cfg.box)
+    a, _ = pm.pm_force(x, 0.31, cfg)
+    scale = np.abs(a).sum(axis=1)
+    assert np.all(np.abs(a.sum(axis=1)) < 1e-12 * scale)
+    a1, _ = pm.pm_force(np.array([[13.3], [7.1], [40.2]]), 0.31, cfg)
+    assert np.all(np.abs(a1) < 1e-14)
+
+
+@pytest.mark.parametrize("r_cells", [4.0, 6.0, 12.0])
+def test_pair_force_matches_newton(r_cells):
+    """Two particles at separation r, l < r << L: averaged over random positions and
+    orientations, the PM acceleration equals the Newtonian 3/2 Om m l^3 / (4 pi r^2)
+    (Poisson Eq. 9 for a point mass) times the periodic-box background correction
+    1 - 4 pi/3 (r/L)^3, within 5%.  Single axis-aligned pairs ring (the exact -ik
+    gradient keeps the mesh's high-k modes), hence the average."""
+    cfg = pm.PMConfig(box=64.0, n_mesh=64, n_ptcl=2)
+    l = cfg.cell
+    rng = np.random.default_rng(9)
+    newton = 1.5 * 0.31 * cfg.mass * l ** 3 / (4 * np.pi * (r_cells * l) ** 2)
+    newton *= 1 - 4 * np.pi / 3 * (r_cells * l / cfg.box) ** 3
+    ratios = []
+    for _ in range(48):
+        x0 = rng.uniform(0, cfg.box, 3)
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        x = np.stack([x0, x0 + r_cells * l * d], axis=1)
+        a, _ = pm.pm_force(x, 0.31, cfg)
+        assert np.allclose(a[:, 0], -a[:, 1], rtol=1e-10, atol=1e-10 * newton)
+        ratios.append(-(a[:, 1] @ d) / newton)
+    assert abs(np.mean(ratios) - 1) < 0.05
+
+
+# ------------------------------------------------------------------ time integration
+
+def test_leapfrog_reproduces_zeldovich_exactly():
+    """Sec. 2.3: with the linear-theory force a = 3/2 Om s, FastPM KDK reproduces ZA,
+    s_i = D1(a_i) s1 and p_i = G_D(a_i) s1, for any step count (pins Eqs. 14-16)."""
+    cfg = pm.PMConfig(box=64.0, n_mesh=16, n_ptcl=8, n_steps=7)
+    om = inputs.white_noise(8, 11).astype(np.float64)
+    Om = THETA[2]
+    out = pm.forward(om, THETA, cfg, force_fn=lambda x, s: 1.5 * Om * s)
+    s1 = pm.za_unit_displacement(om, THETA, cfg)
+    d1, _, gd, _ = cosmo.growth_factors(np.array([cfg.a1]), Om)
+    assert np.allclose(out["s"], d1[0] * s1, rtol=1e-12, atol=1e-13 * np.abs(s1).max())
+    assert np.allclose(out["p"], gd[0] * s1, rtol=1e-12, atol=1e-13 * np.abs(s1).max())
+
+
+def test_linear_growth_with_pm_force():
+    """Small-amplitude ZA ICs under the real PM force: the lowest axis-aligned displacement
+    modes grow as D1(a)/D1(a0) within 1e-3 (pins the force sign, normalisation and FFT
+    scaling).
+
+    Run with one mesh cell per particle and the CIC deconvolution on: there the PM
+    response of a displaced lattice at low k is linear theory up to O((k l)^2).  With
+    two cells per particle the exact -ik gradient keeps the lattice alias at the mesh
+    Nyquist, which strengthens the low-k force by a constant few per cent (a property
+    of the discretisation, not a pin)."""
+    cfg = pm.PMConfig(box=256.0, n_mesh=32, n_ptcl=32, a0=1 / 64, a1=1.0, n_steps=10,
+                      deconv=True)
+    th = (THETA[0] * 1e-8,) + tuple(THETA[1:])
+    om = inputs.white_noise(32, 12).astype(np.float64)
+    out = pm.forward(om, th, cfg)
+    s1 = pm.za_unit_displacement(om, th, cfg)
+    d1 = cosmo.growth_factors(np.array([cfg.a1]), th[2])[0][0]
+    n = cfg.n_ptcl
+    (k0, k1, k2), _ = pm._kgrid(n, cfg.box)
+    kk2 = k0 ** 2 + k1 ** 2 + k2 ** 2
+    # axis-aligned modes |n| <= 2 (diagonal modes carry an O(1e-2) anisotropic alias)
+    axis = ((k0 != 0).astype(int) + (k1 != 0).astype(int) + (k2 != 0).astype(int)) == 1
+    low = axis & (kk2 <= (2 * np.pi / cfg.box) ** 2 * 4.01)
+    for c in range(3):
+        got = np.fft.rfftn(out["s"][c].reshape(n, n, n))[low]
+        want = d1 * np.fft.rfftn(s1[c].reshape(n, n, n))[low]
+        assert np.max(np.abs(got - want)) < 1e-3 * np.max(np.abs(want))
+
+
+def test_reversibility_fp64():
+    """Forward 10 steps then reverse 10 steps recovers the ICs to 1e-10 relative
+    (the paper's FP64 reversibility is 7e-13 to 1.3e-10)."""
+    cfg = pm.PMConfig(box=64.0, n_mesh=16, n_ptcl=8, n_steps=10)
+    om = inputs.white_noise(8, 13).astype(np.float64)
+    fwd = pm.forward(om, THETA, cfg)
+    adj = pm.adjoint(om, THETA, cfg, fwd)
+    s0, p0, _ = pm.za_initial_state(om, THETA, cfg)
+    assert np.sqrt(np.mean((adj["s0"] - s0) ** 2)) < 1e-10 * np.std(s0)
+    assert np.sqrt(np.mean((adj["p0"] - p0) ** 2)) < 1e-10 * np.std(p0)
+
+
+# ------------------------------------------------------------------------ gradients
+
+def test_za_map_transpose_dot_product():
+    cfg = pm.PMConfig(box=64.0, n_mesh=16, n_ptcl=8)
+    rng = np.random.default_rng(6)
+    w = rng.normal(size=(8, 8, 8))
+    v = rng.normal(size=(3, 512))
+    lhs = np.sum(v * pm.za_unit_displacement(w, THETA, cfg))
+    rhs = np.sum(pm.za_transpose(v, THETA, cfg) * w.ravel())
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_force_vjp_matches_finite_difference():
+    cfg = pm.PMConfig(box=40.0, n_mesh=16, n_ptcl=8)
+    rng = np.random.default_rng(7)
+    x = _rand_positions(rng, 40, cfg.box)
+    pi = rng.normal(size=(3, 40))
+    dx = rng.normal(size=(3, 40))
+    a, f = pm.pm_force(x, 0.31, cfg)
+    alpha = pm.force_vjp(x, pi, f, 0.31, cfg)
+    h = 1e-7
+    ap, _ = pm.pm_force(x + h * dx, 0.31, cfg)
+    am, _ = pm.pm_force(x - h * dx, 0.31, cfg)
+    fd = np.sum(pi * (ap - am)) / (2 * h)
+    assert abs(fd - np.sum(alpha * dx)) < 1e-6 * abs(fd)
+
+
+FD_CFG = pm.PMConfig(box=24.0, n_mesh=16, n_ptcl=8, n_steps=4)
+
+
+def _loss(om, th, target):
+    fwd = pm.forward(om, th, FD_CFG)
+    return pm.mse_loss(fwd["delta"], target)[0]
+
+
+@pytest.fixture(scope="module")
+def fd_case():
+    om = inputs.white_noise(8, 1).astype(np.float64)
+    target = pm.forward(inputs.white_noise(8, 2).astype(np.float64), THETA, FD_CFG)["delta"]
+    loss, adj, _ = pm.loss_and_gradient(om, THETA, target, FD_CFG)
+    return om, target, loss, adj
+
+
+def test_adjoint_gradient_omega_vs_central_fd(fd_case):
+    """Sec. 3.6: dJ/domega by the adjoint equals central FD along random directions."""
+    om, target, _, adj = fd_case
+    rng = np.random.default_rng(8)
+    for _ in range(2):
+        v = rng.normal(size=om.shape)
+        h = 1e-6
+        fd = (_loss(om + h * v, THETA, target) - _loss(om - h * v, THETA, target)) / (2 * h)
+        ad = np.sum(adj["grad_omega"] * v.ravel())
+        assert abs(fd - ad) <= 1e-6 * abs(fd)
+
+
+@pytest.mark.parametrize("j", range(5))
+def test_adjoint_gradient_theta_vs_central_fd(fd_case, j):
+    """Sec. 3.6, Eq. 51: dJ/dtheta_j by the adjoint equals central FD in theta_j."""
+    om, target, _, adj = fd_case
+    h = 1e-6 * abs(THETA[j])
+    tp = list(THETA)
+    tm = list(THETA)
+    tp[j] += h
+    tm[j] -= h
+    fd = (_loss(om, tp, target) - _loss(om, tm, target)) / (2 * h)
+    assert abs(fd - adj["grad_theta"][j]) <= 1e-6 * abs(fd) + 1e-12
+
+
+def test_reverse_time_adjoint_equals_stored_trajectory(fd_case):
+    """Reverse time integration (Sec. 3.5) gives the stored-trajectory gradient to ~1e-10
+    in FP64; resuming from checkpoints every step is the stored trajectory."""
+    om, target, _, adj = fd_case
+    _, adj_st, _ = pm.loss_and_gradient(om, THETA, target, FD_CFG, ckpt_every=1)
+    g, gs = adj["grad_omega"], adj_st["grad_omega"]
+    assert np.linalg.norm(g - gs) < 1e-9 * np.linalg.norm(gs)
+    assert np.allclose(adj["grad_theta"], adj_st["grad_theta"], rtol=1e-9)
+
+
+def test_white_noise_power_recovers_plin():
+    """Eq. 5-6: <|delta1(k)|^2> l_p^6 / V = P_lin(k), averaged over seeds and shells."""
+    cfg = pm.PMConfig(box=200.0, n_mesh=32, n_ptcl=16)
+    n = cfg.n_ptcl
+    lp = cfg.box / n
+    (k0, k1, k2), _ = pm._kgrid(n, cfg.box)
+    kk = np.sqrt(k0 ** 2 + k1 ** 2 + k2 ** 2)
+    shell = (kk > 0.06) & (kk < 0.16)     # below the lattice Nyquist 0.25 h/Mpc
+    pk = []
+    for seed in range(24):
+        om = inputs.white_noise(n, 100 + seed).astype(np.float64)
+        s1 = pm.za_unit_displacement(om, THETA, cfg)
+        # delta1 = -div s1  in Fourier: -i k . s1(k)
+        dk = sum(-1j * kc * np.fft.rfftn(s1[c].reshape(n, n, n)) for c, kc in enumerate((k0, k1, k2)))
+        pk.append(np.abs(dk[shell]) ** 2 * lp ** 6 / cfg.box ** 3 / cosmo.plin(kk[shell], THETA))
+    ratio = np.mean(pk)
+    assert abs(ratio - 1) < 0.05
