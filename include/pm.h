@@ -1,0 +1,155 @@
+/*
+ * libpmgb -- differentiable particle-mesh (PM) N-body simulation with the adjoint method,
+ * hand-written CUDA for sm_103a (GB300).  C ABI.
+ *
+ * Method: Li et al., "Differentiable Cosmological Simulation with the Adjoint Method"
+ * (arXiv:2211.09815).  Forward model: Zel'dovich initial conditions from white noise
+ * (Sec. 2.1, Eqs. 2-7), PM gravity by CIC scatter, FFT Poisson solve with the -ik
+ * gradient and CIC gather (Sec. 2.2, Eqs. 10-11), FastPM kick-drift-kick leapfrog
+ * (Sec. 2.3, Eqs. 13-16).  Gradient: the discrete adjoint integrated backward in time
+ * jointly with the reverse leapfrog (Sec. 3.6, Eqs. 49-51), with optional piecewise
+ * resumption from stored states (Sec. 3.5).
+ *
+ * Conventions (shared with the test oracle):
+ *   - lengths in Mpc/h, time in 1/H0, flat LCDM, theta = (A_s, n_s, Omega_m, Omega_b, h);
+ *   - mesh n_mesh^3 nodes at g*l, l = box/n_mesh; particle lattice q = j*box/n_ptcl + l/2;
+ *   - arrays are C order with the last axis fastest; vector fields are [3][N] (structure
+ *     of arrays) with component c along array axis c; particle j is lattice point j;
+ *   - particle mass m = n_mesh^3/n_ptcl^3 (mean density 1), delta = rho - 1;
+ *   - the forward state is (s, p): displacement s = x - q and canonical momentum p.
+ *
+ * Memory: every pointer argument is a device pointer unless stated otherwise, allocated
+ * and owned by the caller, in the context's precision (float for PM_F32, double for
+ * PM_F64).  The context owns its scratch (meshes, fixed-point accumulators, spectra,
+ * particle state, checkpoints) and frees it in pm_destroy.  All work is enqueued on the
+ * stream given to pm_init; calls return once the work is enqueued, except where a host
+ * output pointer forces a synchronisation (noted per call).
+ *
+ * Errors: every call returns a status (PM_OK = 0).  Arguments are validated on the host
+ * before any launch; nothing is written on error.  No exception crosses the ABI.
+ */
+#ifndef PMGB_PM_H
+#define PMGB_PM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  PM_OK = 0,
+  PM_ERR_ARG = 1,        /* invalid argument or configuration */
+  PM_ERR_OOM = 2,        /* device allocation failed */
+  PM_ERR_CUDA = 3,       /* a CUDA call failed (see pm_last_cuda_error) */
+  PM_ERR_NONFINITE = 4,  /* non-finite theta */
+  PM_ERR_OVERFLOW = 5,   /* fixed-point range exceeded */
+  PM_ERR_TIMEOUT = 6,    /* a bounded device wait gave up */
+  PM_ERR_STATE = 7       /* call out of order (e.g. pm_adjoint before pm_forward) */
+};
+
+enum { PM_F32 = 0, PM_F64 = 1 };
+
+typedef struct pm_ctx pm_ctx; /* opaque, library-owned */
+
+typedef struct {
+  double box;       /* periodic box side L in Mpc/h, > 0 */
+  int n_mesh;       /* mesh nodes per side: power of two, 4..1024, multiple of n_ptcl */
+  int n_ptcl;       /* particles per side: power of two, >= 4 */
+  int n_steps;      /* leapfrog steps n >= 1, scale factors linear in a (Sec. 4) */
+  double a0, a1;    /* initial and final scale factor, 0 < a0 < a1 */
+  int precision;    /* PM_F32 or PM_F64 */
+  int ckpt_every;   /* 0: reverse time integration; k > 0: resume the reverse pass from
+                       states (s_j, p_j) stored every k steps (Sec. 3.5) */
+  int deconv;       /* 1: divide the Green's function by the CIC window prod sinc^4 */
+  int batch;        /* independent instances B >= 1 (own theta and omega each) */
+} pm_config;
+
+/*
+ * Create a context: validates cfg and theta, computes the FP64 cosmology tables on the
+ * host (linear power spectrum Eq. 7 with the Eisenstein-Hu no-wiggle transfer function,
+ * growth ODE of App. A Eqs. 52-58, FastPM factors Eq. 15 and their d/dOmega_m), and
+ * copies omega into the context.
+ *   out    : receives the context (host pointer to a pm_ctx*)
+ *   cfg    : host pointer
+ *   theta  : host pointer, [batch][5] doubles (A_s, n_s, Omega_m, Omega_b, h)
+ *   omega  : device pointer, [batch][n_ptcl^3] white noise (Sec. 2.1, Eq. 6)
+ *   stream : a cudaStream_t (0 = legacy default stream)
+ * Errors: PM_ERR_ARG (bad sizes, null pointers), PM_ERR_NONFINITE, PM_ERR_OOM.
+ */
+int pm_init(pm_ctx** out, const pm_config* cfg, const double* theta, const void* omega, void* stream);
+
+/*
+ * Forward model (Sec. 2.1-2.3): Zel'dovich ICs at a0, F_0, then n KDK steps (Eq. 16).
+ *   disp_out : optional, [batch][3][n_ptcl^3], final displacement s_n
+ *   mom_out  : optional, [batch][3][n_ptcl^3], final momentum p_n
+ *   dens_out : optional, [batch][n_mesh^3], final overdensity delta_n (CIC, Eq. 10)
+ * The context keeps the final state for pm_adjoint.
+ */
+int pm_forward(pm_ctx* ctx, void* disp_out, void* mom_out, void* dens_out);
+
+/*
+ * Objective J = mean_g (delta_n(g) - target(g))^2 per instance (Sec. 2.4, Eq. 17 as a
+ * field-level MSE) and its cotangent dJ/d delta_n = 2 (delta_n - target) / n_mesh^3.
+ *   target      : [batch][n_mesh^3]
+ *   loss_out    : [batch] doubles, host or device pointer (host: synchronises)
+ *   dJ_ddens_out: [batch][n_mesh^3]
+ * Requires pm_forward.  FP64 deterministic reduction.
+ */
+int pm_loss_mse(pm_ctx* ctx, const void* target, double* loss_out, void* dJ_ddens_out);
+
+/*
+ * Adjoint (Sec. 3.6, Eqs. 49-51): integrates the leapfrog backward jointly with the
+ * adjoint variables (xi, pi), recomputing the forces instead of storing the trajectory
+ * (or resuming from stored states if cfg.ckpt_every > 0), then back-propagates through
+ * the initial conditions.
+ *   dJ_ddens   : optional, [batch][n_mesh^3], dJ/d delta_n on the final density
+ *   dJ_ddisp   : optional, [batch][3][n_ptcl^3], dJ/dx_n
+ *   dJ_dmom    : optional, [batch][3][n_ptcl^3], dJ/dp_n
+ *   dJ_domega  : optional, [batch][n_ptcl^3], receives dJ/d omega
+ *   dJ_dtheta  : optional, [batch][5] doubles, host or device (host: synchronises)
+ * Requires pm_forward since the last pm_adjoint; consumes the final state.
+ */
+int pm_adjoint(pm_ctx* ctx, const void* dJ_ddens, const void* dJ_ddisp, const void* dJ_dmom,
+               void* dJ_domega, double* dJ_dtheta);
+
+/* Release the context and all its device memory (synchronises its stream). */
+int pm_destroy(pm_ctx* ctx);
+
+/* Static description of a status code. */
+const char* pm_status_string(int status);
+
+/* Message of the last CUDA error seen by this thread ("" if none). */
+const char* pm_last_cuda_error(void);
+
+/* Bytes of device scratch the context holds. */
+long long pm_scratch_bytes(const pm_ctx* ctx);
+
+/* ------------------------------------------------------------------------------------
+ * Operator entry points: single rows of the hot path on the context's buffers, for
+ * parity tests and benchmarks.  All arrays are device pointers in the context precision.
+ * ----------------------------------------------------------------------------------*/
+
+/* Overdensity delta (Sec. 2.2, Eq. 10; deterministic int64 fixed point) of particles at
+ * x = q + disp.  disp [batch][3][n_ptcl^3] -> dens_out [batch][n_mesh^3]. */
+int pm_op_density(pm_ctx* ctx, const void* disp, void* dens_out);
+
+/* PM accelerations a = -grad varphi(q + disp) (Sec. 2.2): scatter, R2C, Green's function
+ * with -ik, 3 C2R, gather.  disp, acc_out: [batch][3][n_ptcl^3]. */
+int pm_op_force(pm_ctx* ctx, const void* disp, void* acc_out);
+
+/* Force and its vector-Jacobian product alpha = pi . da/dx (Sec. 3.6, Eq. 49 F line).
+ * disp, pi, acc_out, alpha_out: [batch][3][n_ptcl^3]. */
+int pm_op_force_vjp(pm_ctx* ctx, const void* disp, const void* pi, void* acc_out, void* alpha_out);
+
+/* 3-D real FFT of n^3 meshes, n = n_mesh, in the numpy rfftn layout:
+ * real [batch][n][n][n] <-> complex [batch][n][n][n/2+1] (interleaved re, im).
+ * dir = -1: forward (unnormalised); dir = +1: inverse (unnormalised, no 1/n^3). */
+int pm_op_fft(pm_ctx* ctx, int dir, const void* in, void* out);
+
+/* Zel'dovich displacement for unit growth s1 (Sec. 2.1, Eqs. 3-6) of the context's omega.
+ * s1_out: [batch][3][n_ptcl^3]. */
+int pm_op_za(pm_ctx* ctx, void* s1_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PMGB_PM_H */

@@ -1,0 +1,38 @@
+// Shared device helpers for the particle-mesh kernels: complex arithmetic on
+// float2/double2, the deterministic fixed-point conventions, and small indexing helpers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pmgb {
+
+template <typename T> struct Cx;
+template <> struct Cx<float> { using type = float2; };
+template <> struct Cx<double> { using type = double2; };
+template <typename T> using cx_t = typename Cx<T>::type;
+
+template <typename C> __device__ __forceinline__ C cmake(decltype(C{}.x) re, decltype(C{}.x) im) {
+  C r; r.x = re; r.y = im; return r;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return cmake<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return cmake<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return cmake<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return cmake<C>(a.x, -a.y); }
+template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) { return cmake<C>(a.x * s, a.y * s); }
+// multiply by i
+template <typename C> __device__ __forceinline__ C cmul_i(C a) { return cmake<C>(-a.y, a.x); }
+
+// Layout of one complex half spectrum of an n^3 real mesh ("spectrum buffer"):
+//   main:  [n][n][n/2] complex, kx = 0..n/2-1 along the fastest axis
+//   side:  [n][n] complex, the kx = n/2 (Nyquist) plane
+// main + side hold n^3 + 2 n^2 reals, the real mesh [n][n][n] lives at the start of the
+// same buffer after an inverse transform.  Instances of a batch follow each other.
+__host__ __device__ inline long long spec_main_len(int n) { return (long long)n * n * (n / 2); }
+__host__ __device__ inline long long spec_len_cx(int n) { return spec_main_len(n) + (long long)n * n; }
+
+// signed frequency of index i on an axis of length n, in [-n/2, n/2)
+__device__ __forceinline__ int freq_of(int i, int n) { return i < n / 2 ? i : i - n; }
+
+}  // namespace pmgb

@@ -1,0 +1,25 @@
+// Host FP64 cosmology tables for the PM engine (see cosmo.cpp).
+#pragma once
+#include <vector>
+
+namespace pmgb {
+namespace cosmo {
+
+struct TimeCoef {
+  // per step i = 1..n (index i-1): FastPM factors of Sec. 2.3, Eq. 15 and d/dOmega_m
+  std::vector<double> k1, dd, k2, dk1, ddd, dk2;
+  double d1_a0, gd_a0, dd1_a0, dgd_a0;  // D1, G_D at a0 and d/dOmega_m
+};
+
+// K1_i, D_i, K2_i for a linear-in-a grid a0..a1 with n steps.
+void time_coefficients(double a0, double a1, int n, double omega_m, TimeCoef& out);
+
+// P_lin(kf sqrt(n2)) for n2 = 0..maxn2 (p[0] = 0) and d ln P / d theta_j ([5][maxn2+1]).
+void plin_tables(const double theta[5], double kf, int maxn2, std::vector<double>& p,
+                 std::vector<double>& dlnp);
+
+double transfer_eh(double k, double om, double ob, double h);
+double plin_value(double k, const double theta[5]);
+
+}  // namespace cosmo
+}  // namespace pmgb

@@ -1,0 +1,185 @@
+// Hand-written batched 3-D real FFT for the particle-mesh force (Sec. 2.2, Eq. 11):
+// device building blocks.
+//
+// A length-L complex DFT of a tile of TC independent sequences is done as a Stockham
+// auto-sort FFT with mixed radices (<= 16).  Each stage: every thread loads the R
+// inputs of its butterfly, applies the stage twiddles, does an R-point DFT in registers
+// and stores the R outputs at their Stockham positions.  A tile in shared memory is
+// laid out [L][LD] with the sequence index innermost, so that for column passes a warp's
+// loads and stores touch consecutive addresses.  The first stage of a column pass reads
+// straight from global memory and the last one writes straight back; the x passes load
+// rows into shared memory with coalesced reads first.
+#pragma once
+#include "common.cuh"
+
+namespace pmgb {
+
+// Radix plan for a length-L transform: stages R0 (first) .. R2, all <= 16.
+template <int L> struct Plan;
+template <> struct Plan<2>    { static constexpr int S = 1, R0 = 2,  R1 = 1, R2 = 1, RMAX = 2; };
+template <> struct Plan<4>    { static constexpr int S = 1, R0 = 4,  R1 = 1, R2 = 1, RMAX = 4; };
+template <> struct Plan<8>    { static constexpr int S = 1, R0 = 8,  R1 = 1, R2 = 1, RMAX = 8; };
+template <> struct Plan<16>   { static constexpr int S = 1, R0 = 16, R1 = 1, R2 = 1, RMAX = 16; };
+template <> struct Plan<32>   { static constexpr int S = 2, R0 = 8,  R1 = 4, R2 = 1, RMAX = 8; };
+template <> struct Plan<64>   { static constexpr int S = 2, R0 = 8,  R1 = 8, R2 = 1, RMAX = 8; };
+template <> struct Plan<128>  { static constexpr int S = 2, R0 = 16, R1 = 8, R2 = 1, RMAX = 16; };
+template <> struct Plan<256>  { static constexpr int S = 2, R0 = 16, R1 = 16, R2 = 1, RMAX = 16; };
+template <> struct Plan<512>  { static constexpr int S = 3, R0 = 8,  R1 = 8, R2 = 8, RMAX = 8; };
+template <> struct Plan<1024> { static constexpr int S = 3, R0 = 16, R1 = 8, R2 = 8, RMAX = 16; };
+
+// cos(2 pi m / 16), exact values of the 16th roots of unity.
+__host__ __device__ constexpr double cos16(int m) {
+  m &= 15;
+  return m == 0 ? 1.0 : m == 1 ? 0.92387953251128675613 : m == 2 ? 0.70710678118654752440
+       : m == 3 ? 0.38268343236508977173 : m == 4 ? 0.0 : m == 5 ? -0.38268343236508977173
+       : m == 6 ? -0.70710678118654752440 : m == 7 ? -0.92387953251128675613 : m == 8 ? -1.0
+       : m == 9 ? -0.92387953251128675613 : m == 10 ? -0.70710678118654752440
+       : m == 11 ? -0.38268343236508977173 : m == 12 ? 0.0 : m == 13 ? 0.38268343236508977173
+       : m == 14 ? 0.70710678118654752440 : 0.92387953251128675613;
+}
+__host__ __device__ constexpr double sin16(int m) { return cos16(m - 4); }
+
+// v <- v * exp(DIR * 2 pi i k / R)
+template <int R, int DIR, typename C>
+__device__ __forceinline__ C root_mul(C v, int k) {
+  using T = decltype(v.x);
+  const int m = k * (16 / R);
+  const T c = (T)cos16(m), s = (T)(DIR * sin16(m));
+  return cmake<C>(v.x * c - v.y * s, v.x * s + v.y * c);
+}
+
+// In-register R-point DFT, natural order in and out: X_k = sum_r v_r exp(DIR 2 pi i r k / R)
+template <int R, int DIR, typename C>
+__device__ __forceinline__ void dft(C (&v)[R]) {
+  if constexpr (R == 1) {
+    return;
+  } else if constexpr (R == 2) {
+    const C a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  } else {
+    C e[R / 2], o[R / 2];
+#pragma unroll
+    for (int i = 0; i < R / 2; ++i) { e[i] = v[2 * i]; o[i] = v[2 * i + 1]; }
+    dft<R / 2, DIR>(e);
+    dft<R / 2, DIR>(o);
+#pragma unroll
+    for (int k = 0; k < R / 2; ++k) {
+      const C t = (k == 0) ? o[k] : root_mul<R, DIR>(o[k], k);
+      v[k] = cadd(e[k], t);
+      v[k + R / 2] = csub(e[k], t);
+    }
+  }
+}
+
+// exp(DIR 2 pi i m / L) from the table w[m] = exp(-2 pi i m / L)
+template <int DIR, typename C>
+__device__ __forceinline__ C twiddle(const C* __restrict__ w, int m) {
+  C t = __ldg(w + m);
+  if (DIR > 0) t.y = -t.y;
+  return t;
+}
+
+// ---------------------------------------------------------------- tile accessors
+template <typename C, int LD>
+struct SmemTile {
+  C* p;
+  __device__ __forceinline__ C ld(int row, int c) const { return p[row * LD + c]; }
+  __device__ __forceinline__ void st(int row, int c, C v) const { p[row * LD + c] = v; }
+};
+
+// one sequence per thread in global memory: element `row` at p[row * es]
+template <typename C>
+struct GlobalSeq {
+  C* p;
+  long long es;
+  bool valid;
+  __device__ __forceinline__ C ld(int row, int) const {
+    if (!valid) return cmake<C>(0, 0);
+    return p[(long long)row * es];
+  }
+  __device__ __forceinline__ void st(int row, int, C v) const {
+    if (valid) p[(long long)row * es] = v;
+  }
+};
+
+// One Stockham radix-R stage over TC sequences of length L, NT threads.
+// NS = product of the radices already applied.  Loads all of the thread's inputs, syncs,
+// then stores, so source and destination may be the same shared-memory tile.
+template <typename T, int L, int TC, int NT, int R, int NS, int DIR, class Src, class Dst>
+__device__ __forceinline__ void stage(const Src& src, const Dst& dst, const cx_t<T>* __restrict__ tw) {
+  using C = cx_t<T>;
+  constexpr int ITEMS = TC * (L / R);
+  constexpr int PER = ITEMS / NT;
+  static_assert(PER * NT == ITEMS, "work items must divide evenly");
+  C v[PER][R];
+  const int c = threadIdx.x % TC;
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int j = (threadIdx.x + i * NT) / TC;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[i][r] = src.ld(j + r * (L / R), c);
+    if constexpr (NS > 1) {
+      const int jm = j % NS;
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[i][r] = cmul(v[i][r], twiddle<DIR>(tw, r * jm * (L / (NS * R))));
+    }
+    dft<R, DIR>(v[i]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int j = (threadIdx.x + i * NT) / TC;
+    const int jd = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst.st(jd + r * NS, c, v[i][r]);
+  }
+}
+
+// Full length-L DFT of a tile: src -> (mid) -> dst.  `mid` must be a shared tile.
+template <typename T, int L, int TC, int NT, int DIR, class Src, class Mid, class Dst>
+__device__ __forceinline__ void fft_tile(const Src& src, const Mid& mid, const Dst& dst,
+                                         const cx_t<T>* __restrict__ tw) {
+  using P = Plan<L>;
+  if constexpr (P::S == 1) {
+    stage<T, L, TC, NT, P::R0, 1, DIR>(src, dst, tw);
+  } else if constexpr (P::S == 2) {
+    stage<T, L, TC, NT, P::R0, 1, DIR>(src, mid, tw);
+    __syncthreads();
+    stage<T, L, TC, NT, P::R1, P::R0, DIR>(mid, dst, tw);
+  } else {
+    stage<T, L, TC, NT, P::R0, 1, DIR>(src, mid, tw);
+    __syncthreads();
+    stage<T, L, TC, NT, P::R1, P::R0, DIR>(mid, mid, tw);
+    __syncthreads();
+    stage<T, L, TC, NT, P::R2, P::R0 * P::R1, DIR>(mid, dst, tw);
+  }
+}
+
+// Tile shapes.  Column passes: TC sequences of length L in one tile of <= 64 KiB,
+// NT = TC * L / RMAX threads (each thread holds RMAX values), NT <= 512.
+template <typename T, int L> struct ColTile {
+  static constexpr int RMAX = Plan<L>::RMAX;
+  static constexpr int TC0 = 65536 / (L * (int)sizeof(cx_t<T>));
+  static constexpr int TC1 = TC0 > 256 ? 256 : TC0;
+  static constexpr int TCMAXNT = 512 * RMAX / L;
+  static constexpr int TC2 = TC1 < TCMAXNT ? TC1 : TCMAXNT;
+  static constexpr int TC = TC2 < 1 ? 1 : TC2;
+  static constexpr int NT = TC * L / RMAX;
+  static constexpr int LD = TC;
+};
+// Row passes (x axis): TR rows of L = n/2 complex values, tile padded to LD = TR + 1 so
+// that the transposing row loads do not collide in shared-memory banks.
+template <typename T, int L> struct RowTile {
+  static constexpr int RMAX = Plan<L>::RMAX;
+  static constexpr int TR0 = 32768 / (L * (int)sizeof(cx_t<T>));
+  static constexpr int TR1 = TR0 > 128 ? 128 : TR0;
+  static constexpr int TRMAXNT = 512 * RMAX / L;
+  static constexpr int TR2 = TR1 < TRMAXNT ? TR1 : TRMAXNT;
+  static constexpr int TR = TR2 < 1 ? 1 : TR2;
+  static constexpr int NT = TR * L / RMAX;
+  static_assert(NT >= 32, "row tile needs at least one warp");
+  static constexpr int LD = TR + 1;
+};
+
+}  // namespace pmgb

@@ -1,0 +1,425 @@
+// Hand-written batched 3-D real FFT for the particle-mesh force (Sec. 2.2, Eq. 11):
+// kernels and launchers, templated on the real type.  Included once per precision.
+//
+// Spectrum layout (see common.cuh): main [n][n][n/2] complex + side [n][n] complex
+// (kx = n/2) per instance.  Forward R2C = x pass (rows, real -> half spectrum, packing
+// two reals per complex and splitting even/odd afterwards) then y and z column passes.
+// The inverse runs z, y, then the x pass (C2R).  Transforms are unnormalised both ways;
+// the 1/n^3 of the inverse is folded into the Fourier multipliers.
+#pragma once
+#include "fft.cuh"
+#include "pm_internal.h"
+
+namespace pmgb {
+
+// ---------------------------------------------------------------- column passes
+__device__ __forceinline__ long long seq_base(const SeqMap& m, int s) {
+  const int col = s % m.ncols;
+  const int t = s / m.ncols;
+  const int o0 = t % m.n0;
+  const int o1 = t / m.n0;
+  return (long long)o1 * m.os1 + (long long)o0 * m.os0 + (long long)col * m.cs;
+}
+
+template <typename T, int L, int DIR>
+__global__ void __launch_bounds__(ColTile<T, L>::NT)
+k_fft_cols(const SeqMap mm, const SeqMap ms, int ntiles_main, ColBufs<T> bufs,
+           const cx_t<T>* __restrict__ tw) {
+  using C = cx_t<T>;
+  using TL = ColTile<T, L>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  const bool side = blockIdx.x >= (unsigned)ntiles_main;
+  const SeqMap& m = side ? ms : mm;
+  const int s0 = (side ? blockIdx.x - ntiles_main : blockIdx.x) * TL::TC;
+  const int s = s0 + threadIdx.x % TL::TC;
+  const bool valid = s < m.nseq;
+  C* base = bufs.p[blockIdx.y] + (valid ? seq_base(m, s) : 0);
+  GlobalSeq<C> g{base, m.es, valid};
+  SmemTile<C, TL::LD> t{sm};
+  fft_tile<T, L, TL::TC, TL::NT, DIR>(g, t, g, tw);
+}
+
+// ---------------------------------------------------------------- x pass, R2C
+// rows of n = 2L reals -> L complex (main) + 1 (side).  Input is either an int64
+// fixed-point accumulator (converted with value = acc * 2^-e * mul + add, then zeroed)
+// or a real mesh.
+template <typename T, int L, bool FIXED>
+__global__ void __launch_bounds__(RowTile<T, L>::NT)
+k_fft_x_r2c(RowJob<T> job, int nrows, const cx_t<T>* __restrict__ twL, const cx_t<T>* __restrict__ twN) {
+  using C = cx_t<T>;
+  using TL = RowTile<T, L>;
+  constexpr int N = 2 * L;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  const RowBuf<T>& rb = job.b[blockIdx.y];
+  const int r0 = blockIdx.x * TL::TR;
+  const long long rows_per_inst = (long long)N * N;
+  // load + convert, transposing into [L][LD]
+  for (int idx = threadIdx.x; idx < TL::TR * L; idx += TL::NT) {
+    const int row = idx / L, j = idx % L;
+    const int grow = r0 + row;
+    C v = cmake<C>(0, 0);
+    if (grow < nrows) {
+      const int inst = (int)(grow / rows_per_inst);
+      const long long off = inst * rb.real_is + (grow % rows_per_inst) * N + 2 * j;
+      if constexpr (FIXED) {
+        long long* acc = reinterpret_cast<long long*>(rb.real) + off;
+        const longlong2 a = *reinterpret_cast<longlong2*>(acc);
+        const int e = rb.exps ? rb.exps[inst] : rb.exp_host;
+        const T mul = (T)ldexp((double)rb.mul, -e);
+        v = cmake<C>((T)a.x * mul + rb.add, (T)a.y * mul + rb.add);
+        if (rb.zero) *reinterpret_cast<longlong2*>(acc) = make_longlong2(0, 0);
+      } else {
+        v = *reinterpret_cast<const C*>(reinterpret_cast<const T*>(rb.real) + off);
+      }
+    }
+    sm[j * TL::LD + row] = v;
+  }
+  __syncthreads();
+  SmemTile<C, TL::LD> t{sm};
+  fft_tile<T, L, TL::TR, TL::NT, -1>(t, t, t, twL);
+  __syncthreads();
+  // even/odd split: X[k] = E[k] + W^k O[k], E = (Z[k] + conj Z[L-k]) / 2, O = -i (Z[k] - conj Z[L-k]) / 2
+  for (int idx = threadIdx.x; idx < TL::TR * (L / 2 + 1); idx += TL::NT) {
+    const int row = idx / (L / 2 + 1), k = idx % (L / 2 + 1);
+    const int grow = r0 + row;
+    if (grow >= nrows) continue;
+    const int inst = (int)(grow / rows_per_inst);
+    C* out = rb.spec + inst * spec_len_cx(N) + (grow % rows_per_inst) * L;
+    C* side = rb.spec + inst * spec_len_cx(N) + spec_main_len(N) + (grow % rows_per_inst);
+    const C zk = sm[k * TL::LD + row];
+    if (k == 0) {
+      out[0] = cmake<C>(zk.x + zk.y, (T)0);
+      *side = cmake<C>(zk.x - zk.y, (T)0);
+      continue;
+    }
+    const C zm = sm[(L - k) * TL::LD + row];
+    const T h = (T)0.5;
+    const C e = cscale(cadd(zk, cconj(zm)), h);
+    const C d = cscale(csub(zk, cconj(zm)), h);
+    const C o = cmake<C>(d.y, -d.x);  // -i d
+    const C w = __ldg(twN + k);       // exp(-2 pi i k / N)
+    const C wo = cmul(w, o);
+    out[k] = cadd(e, wo);
+    if (k != L - k) out[L - k] = cconj(csub(e, wo));
+  }
+}
+
+// ---------------------------------------------------------------- x pass, C2R
+// L complex (main) + side -> n = 2L reals (unnormalised).  The output may alias the input.
+template <typename T, int L>
+__global__ void __launch_bounds__(RowTile<T, L>::NT)
+k_fft_x_c2r(RowJob<T> job, int nrows, const cx_t<T>* __restrict__ twL, const cx_t<T>* __restrict__ twN) {
+  using C = cx_t<T>;
+  using TL = RowTile<T, L>;
+  constexpr int N = 2 * L;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  const RowBuf<T>& rb = job.b[blockIdx.y];
+  const int r0 = blockIdx.x * TL::TR;
+  const long long rows_per_inst = (long long)N * N;
+  // Z[k] = E'[k] + i O'[k], E' = X[k] + conj X[L-k], O' = (X[k] - conj X[L-k]) conj(W^k)
+  for (int idx = threadIdx.x; idx < TL::TR * (L / 2 + 1); idx += TL::NT) {
+    const int row = idx / (L / 2 + 1), k = idx % (L / 2 + 1);
+    const int grow = r0 + row;
+    C zk = cmake<C>(0, 0), zm = cmake<C>(0, 0);
+    if (grow < nrows) {
+      const int inst = (int)(grow / rows_per_inst);
+      const C* in = rb.spec + inst * spec_len_cx(N) + (grow % rows_per_inst) * L;
+      if (k == 0) {
+        const T x0 = in[0].x;
+        const T xl = (rb.spec + inst * spec_len_cx(N) + spec_main_len(N) + (grow % rows_per_inst))->x;
+        zk = cmake<C>(x0 + xl, x0 - xl);
+      } else {
+        const C xk = in[k], xm = in[L - k];
+        const C e = cadd(xk, cconj(xm));
+        const C d = csub(xk, cconj(xm));
+        const C o = cmul(d, cconj(__ldg(twN + k)));
+        zk = cadd(e, cmul_i(o));
+        zm = cadd(cconj(e), cmul_i(cconj(o)));
+      }
+    }
+    sm[k * TL::LD + row] = zk;
+    if (k != 0 && k != L - k) sm[(L - k) * TL::LD + row] = zm;
+  }
+  __syncthreads();
+  SmemTile<C, TL::LD> t{sm};
+  fft_tile<T, L, TL::TR, TL::NT, +1>(t, t, t, twL);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < TL::TR * L; idx += TL::NT) {
+    const int row = idx / L, j = idx % L;
+    const int grow = r0 + row;
+    if (grow >= nrows) continue;
+    const int inst = (int)(grow / rows_per_inst);
+    T* out = reinterpret_cast<T*>(rb.real) + inst * rb.real_is + (grow % rows_per_inst) * N + 2 * j;
+    *reinterpret_cast<C*>(out) = sm[j * TL::LD + row];
+  }
+}
+
+// ---------------------------------------------------------------- fused z passes
+// Sequence s of a z pass: main tiles s -> (b, y, kx), side tiles s -> (b, y) with kx = n/2.
+struct ZSeq {
+  int b, f1, f2;      // instance, signed y frequency, x frequency (0..n/2)
+  long long base;     // complex offset of element kz = 0
+  long long es;       // complex stride along z
+  bool valid;
+};
+template <int N>
+__device__ __forceinline__ ZSeq zseq(int s, bool side, int batch) {
+  ZSeq q;
+  if (!side) {
+    const int kx = s % (N / 2), t = s / (N / 2);
+    const int y = t % N;
+    q.b = t / N;
+    q.f1 = freq_of(y, N);
+    q.f2 = kx;
+    q.base = q.b * spec_len_cx(N) + (long long)y * (N / 2) + kx;
+    q.es = (long long)N * (N / 2);
+  } else {
+    const int y = s % N;
+    q.b = s / N;
+    q.f1 = freq_of(y, N);
+    q.f2 = N / 2;
+    q.base = q.b * spec_len_cx(N) + spec_main_len(N) + y;
+    q.es = N;
+  }
+  q.valid = q.b < batch;
+  if (!q.valid) q.b = 0;
+  return q;
+}
+
+// multiplier data for one sequence: g(f0) = coef * d12 * dtab[f0] / (f0^2 + n12)
+template <typename T>
+struct GreenSeq {
+  T coef, d12;
+  int n12, f1, f2;
+  const T* dtab;
+  int n;
+  __device__ __forceinline__ T g(int f0) const {
+    const int n2 = f0 * f0 + n12;
+    if (n2 == 0) return (T)0;
+    T v = coef * d12 / (T)n2;
+    if (dtab) v *= dtab[f0 < 0 ? f0 + n : f0];
+    return v;
+  }
+  // k_c / kf for component c with the Nyquist plane of axis c zeroed
+  __device__ __forceinline__ int fc(int comp, int f0) const {
+    if (comp == 0) return f0 == -n / 2 ? 0 : f0;
+    if (comp == 1) return f1 == -n / 2 ? 0 : f1;
+    return f2 == n / 2 ? 0 : f2;
+  }
+};
+
+// Source of the first inverse stage: A[row] * H_c, H_c v = f_c g (-i v)  (force, -ik_c G)
+template <typename T, int LD>
+struct MulSrc {
+  const cx_t<T>* p;
+  GreenSeq<T> gs;
+  int comp;
+  __device__ __forceinline__ cx_t<T> ld(int row, int c) const {
+    using C = cx_t<T>;
+    const C v = p[row * LD + c];
+    const int f0 = freq_of(row, gs.n);
+    const T s = (T)gs.fc(comp, f0) * gs.g(f0);
+    return cmake<C>(v.y * s, -v.x * s);
+  }
+};
+
+// Destination of the last forward stage in the adjoint: A[row] (+)= conj(H_c) v = f_c g (i v)
+template <typename T, int LD>
+struct AccDst {
+  cx_t<T>* p;
+  GreenSeq<T> gs;
+  int comp;
+  __device__ __forceinline__ void st(int row, int c, cx_t<T> v) const {
+    using C = cx_t<T>;
+    const int f0 = freq_of(row, gs.n);
+    const T s = (T)gs.fc(comp, f0) * gs.g(f0);
+    const C m = cmake<C>(-v.y * s, v.x * s);
+    C* q = p + row * LD + c;
+    *q = comp == 0 ? m : cadd(*q, m);
+  }
+};
+
+template <typename T, int N>
+__device__ __forceinline__ GreenSeq<T> green_seq(const ZSeq& q, const T* coef, const T* dtab) {
+  GreenSeq<T> gs;
+  gs.coef = coef[q.b];
+  gs.n12 = q.f1 * q.f1 + q.f2 * q.f2;
+  gs.f1 = q.f1;
+  gs.f2 = q.f2;
+  gs.dtab = dtab;
+  gs.n = N;
+  gs.d12 = dtab ? dtab[q.f1 < 0 ? q.f1 + N : q.f1] * dtab[q.f2] : (T)1;
+  return gs;
+}
+
+// Forward force: delta^ (after x, y) --z FFT--> * (-i k_c G) --z IFFT--> F_c (c = 0..2)
+template <typename T, int L>
+__global__ void __launch_bounds__(ColTile<T, L>::NT)
+k_fused_z_force(ZJob<T> job, int ntiles_main, const cx_t<T>* __restrict__ tw) {
+  using C = cx_t<T>;
+  using TL = ColTile<T, L>;
+  constexpr int TILE = L * TL::LD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* A = reinterpret_cast<C*>(smem_raw);
+  C* B = A + TILE;
+  const bool side = blockIdx.x >= (unsigned)ntiles_main;
+  const int s = (side ? blockIdx.x - ntiles_main : blockIdx.x) * TL::TC + threadIdx.x % TL::TC;
+  const int nseq = side ? job.batch * L : job.batch * L * (L / 2);
+  ZSeq q = zseq<L>(s, side, job.batch);
+  q.valid = q.valid && s < nseq;
+  GlobalSeq<C> gin{job.in[0] + q.base, q.es, q.valid};
+  SmemTile<C, TL::LD> ta{A}, tb{B};
+  fft_tile<T, L, TL::TC, TL::NT, -1>(gin, ta, ta, tw);
+  __syncthreads();
+  const GreenSeq<T> gs = green_seq<T, L>(q, job.coef, job.dtab);
+#pragma unroll 1
+  for (int c = 0; c < 3; ++c) {
+    MulSrc<T, TL::LD> src{A, gs, c};
+    GlobalSeq<C> gout{job.out[c] + q.base, q.es, q.valid};
+    fft_tile<T, L, TL::TC, TL::NT, +1>(src, tb, gout, tw);
+  }
+}
+
+// Adjoint: P_c^ (after x, y) --z FFT--> sum_c conj(-i k_c G) P_c --z IFFT--> psi
+template <typename T, int L>
+__global__ void __launch_bounds__(ColTile<T, L>::NT)
+k_fused_z_adjoint(ZJob<T> job, int ntiles_main, const cx_t<T>* __restrict__ tw) {
+  using C = cx_t<T>;
+  using TL = ColTile<T, L>;
+  constexpr int TILE = L * TL::LD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* A = reinterpret_cast<C*>(smem_raw);
+  C* B = A + TILE;
+  const bool side = blockIdx.x >= (unsigned)ntiles_main;
+  const int s = (side ? blockIdx.x - ntiles_main : blockIdx.x) * TL::TC + threadIdx.x % TL::TC;
+  const int nseq = side ? job.batch * L : job.batch * L * (L / 2);
+  ZSeq q = zseq<L>(s, side, job.batch);
+  q.valid = q.valid && s < nseq;
+  const GreenSeq<T> gs = green_seq<T, L>(q, job.coef, job.dtab);
+  SmemTile<C, TL::LD> ta{A}, tb{B};
+#pragma unroll 1
+  for (int c = 0; c < 3; ++c) {
+    GlobalSeq<C> gin{job.in[c] + q.base, q.es, q.valid};
+    AccDst<T, TL::LD> acc{A, gs, c};
+    fft_tile<T, L, TL::TC, TL::NT, -1>(gin, tb, acc, tw);
+    __syncthreads();
+  }
+  GlobalSeq<C> gout{job.out[0] + q.base, q.es, q.valid};
+  fft_tile<T, L, TL::TC, TL::NT, +1>(ta, tb, gout, tw);
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename T, int L>
+static void set_smem(const void* fn, size_t bytes) {
+  if (bytes > 48 * 1024) ensure_smem_attr(fn, (int)bytes);
+}
+
+template <typename T, int L, int DIR>
+static void launch_cols_L(const SeqMap& mm, const SeqMap& ms, const ColBufs<T>& bufs, int nbuf,
+                          const cx_t<T>* tw, cudaStream_t st) {
+  using TL = ColTile<T, L>;
+  const int ntm = (mm.nseq + TL::TC - 1) / TL::TC;
+  const int nts = ms.nseq > 0 ? (ms.nseq + TL::TC - 1) / TL::TC : 0;
+  const size_t sm = (size_t)L * TL::LD * sizeof(cx_t<T>);
+  auto fn = k_fft_cols<T, L, DIR>;
+  set_smem<T, L>((const void*)fn, sm);
+  dim3 grid(ntm + nts, nbuf);
+  fn<<<grid, TL::NT, sm, st>>>(mm, ms, ntm, bufs, tw + L);
+}
+
+template <typename T, int L>
+static void launch_r2c_L(const RowJob<T>& job, int nbuf, int nrows, bool fixed, const cx_t<T>* tw,
+                         cudaStream_t st) {
+  using TL = RowTile<T, L>;
+  const size_t sm = (size_t)L * TL::LD * sizeof(cx_t<T>);
+  dim3 grid((nrows + TL::TR - 1) / TL::TR, nbuf);
+  if (fixed) {
+    auto fn = k_fft_x_r2c<T, L, true>;
+    set_smem<T, L>((const void*)fn, sm);
+    fn<<<grid, TL::NT, sm, st>>>(job, nrows, tw + L, tw + 2 * L);
+  } else {
+    auto fn = k_fft_x_r2c<T, L, false>;
+    set_smem<T, L>((const void*)fn, sm);
+    fn<<<grid, TL::NT, sm, st>>>(job, nrows, tw + L, tw + 2 * L);
+  }
+}
+
+template <typename T, int L>
+static void launch_c2r_L(const RowJob<T>& job, int nbuf, int nrows, const cx_t<T>* tw, cudaStream_t st) {
+  using TL = RowTile<T, L>;
+  const size_t sm = (size_t)L * TL::LD * sizeof(cx_t<T>);
+  dim3 grid((nrows + TL::TR - 1) / TL::TR, nbuf);
+  auto fn = k_fft_x_c2r<T, L>;
+  set_smem<T, L>((const void*)fn, sm);
+  fn<<<grid, TL::NT, sm, st>>>(job, nrows, tw + L, tw + 2 * L);
+}
+
+template <typename T, int L>
+static void launch_fused_L(const ZJob<T>& job, bool adjoint, const cx_t<T>* tw, cudaStream_t st) {
+  using TL = ColTile<T, L>;
+  const int ntm = (job.batch * L * (L / 2) + TL::TC - 1) / TL::TC;
+  const int nts = (job.batch * L + TL::TC - 1) / TL::TC;
+  const size_t sm = 2 * (size_t)L * TL::LD * sizeof(cx_t<T>);
+  if (adjoint) {
+    auto fn = k_fused_z_adjoint<T, L>;
+    set_smem<T, L>((const void*)fn, sm);
+    fn<<<ntm + nts, TL::NT, sm, st>>>(job, ntm, tw + L);
+  } else {
+    auto fn = k_fused_z_force<T, L>;
+    set_smem<T, L>((const void*)fn, sm);
+    fn<<<ntm + nts, TL::NT, sm, st>>>(job, ntm, tw + L);
+  }
+}
+
+#define PMGB_DISPATCH_L(L_, CALL)                                                   \
+  switch (L_) {                                                                     \
+    case 2: { constexpr int LL = 2; CALL; } break;                                  \
+    case 4: { constexpr int LL = 4; CALL; } break;                                  \
+    case 8: { constexpr int LL = 8; CALL; } break;                                  \
+    case 16: { constexpr int LL = 16; CALL; } break;                                \
+    case 32: { constexpr int LL = 32; CALL; } break;                                \
+    case 64: { constexpr int LL = 64; CALL; } break;                                \
+    case 128: { constexpr int LL = 128; CALL; } break;                              \
+    case 256: { constexpr int LL = 256; CALL; } break;                              \
+    case 512: { constexpr int LL = 512; CALL; } break;                              \
+    case 1024: { constexpr int LL = 1024; CALL; } break;                            \
+    default: return PM_ERR_ARG;                                                     \
+  }
+
+template <typename T>
+int fft_cols(int n, int dir, const SeqMap& mm, const SeqMap& ms, const ColBufs<T>& bufs, int nbuf,
+             const cx_t<T>* tw, cudaStream_t st) {
+  if (dir < 0) {
+    PMGB_DISPATCH_L(n, (launch_cols_L<T, LL, -1>(mm, ms, bufs, nbuf, tw, st)));
+  } else {
+    PMGB_DISPATCH_L(n, (launch_cols_L<T, LL, +1>(mm, ms, bufs, nbuf, tw, st)));
+  }
+  return PM_OK;
+}
+
+template <typename T>
+int fft_x_r2c(int n, const RowJob<T>& job, int nbuf, int nrows, bool fixed, const cx_t<T>* tw,
+              cudaStream_t st) {
+  if (n < 4 || n > 1024) return PM_ERR_ARG;
+  PMGB_DISPATCH_L(n / 2, (launch_r2c_L<T, (LL < 512 ? LL : 512)>(job, nbuf, nrows, fixed, tw, st)));
+  return PM_OK;
+}
+
+template <typename T>
+int fft_x_c2r(int n, const RowJob<T>& job, int nbuf, int nrows, const cx_t<T>* tw, cudaStream_t st) {
+  if (n < 4 || n > 1024) return PM_ERR_ARG;
+  PMGB_DISPATCH_L(n / 2, (launch_c2r_L<T, (LL < 512 ? LL : 512)>(job, nbuf, nrows, tw, st)));
+  return PM_OK;
+}
+
+template <typename T>
+int fft_fused_z(int n, const ZJob<T>& job, bool adjoint, const cx_t<T>* tw, cudaStream_t st) {
+  if (n < 4) return PM_ERR_ARG;
+  PMGB_DISPATCH_L(n, (launch_fused_L<T, (LL < 4 ? 4 : LL)>(job, adjoint, tw, st)));
+  return PM_OK;
+}
+
+}  // namespace pmgb

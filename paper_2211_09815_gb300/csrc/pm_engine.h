@@ -1,0 +1,27 @@
+// Precision-independent interface of the PM engine behind the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "../../include/pm.h"
+
+namespace pmgb {
+
+struct EngineBase {
+  virtual ~EngineBase() {}
+  virtual int forward(void* disp, void* mom, void* dens) = 0;
+  virtual int loss_mse(const void* target, double* loss, void* djdd) = 0;
+  virtual int adjoint(const void* djdd, const void* djdx, const void* djdp, void* djdw, double* djdth) = 0;
+  virtual int op_density(const void* disp, void* dens) = 0;
+  virtual int op_force(const void* disp, const void* pi, void* acc, void* alpha) = 0;
+  virtual int op_fft(int dir, const void* in, void* out) = 0;
+  virtual int op_za(void* s1) = 0;
+  virtual long long scratch_bytes() const = 0;
+};
+
+// Creates the engine for cfg->precision; returns a status and sets *out on success.
+int make_engine(const pm_config* cfg, const double* theta, const void* omega, cudaStream_t st, EngineBase** out);
+
+// Record the last CUDA error message for pm_last_cuda_error.
+void set_cuda_error(cudaError_t e);
+
+}  // namespace pmgb

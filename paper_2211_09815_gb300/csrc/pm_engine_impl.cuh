@@ -1,0 +1,577 @@
+// PM engine: memory plan and launch sequences of the forward model (Sec. 2) and of the
+// discrete adjoint with reverse time integration (Sec. 3.5-3.6), templated on the real
+// type.  Included once per precision.
+#pragma once
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "cosmo.h"
+#include "pm_internal.h"
+#include "pm_engine.h"
+#include "pm_kernels.cuh"
+
+namespace pmgb {
+
+#define PMGB_CK(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) { set_cuda_error(e_); return PM_ERR_CUDA; } \
+  } while (0)
+#define PMGB_RET(call)                                  \
+  do {                                                  \
+    int r_ = (call);                                    \
+    if (r_ != PM_OK) return r_;                         \
+  } while (0)
+
+static inline int ilog2(long long v) { int r = 0; while ((1LL << r) < v) ++r; return r; }
+
+template <typename T>
+class Engine : public EngineBase {
+ public:
+  using C = cx_t<T>;
+
+  ~Engine() override {
+    if (st_) cudaStreamSynchronize(st_);
+    for (void* p : allocs_) cudaFree(p);
+  }
+
+  long long scratch_bytes() const override { return bytes_; }
+
+  int init(const pm_config* cfg, const double* theta, const void* omega, cudaStream_t st) {
+    cfg_ = *cfg;
+    st_ = st;
+    B_ = cfg->batch;
+    np_ = cfg->n_ptcl;
+    nm_ = cfg->n_mesh;
+    n_ = cfg->n_steps;
+    N_ = (long long)np_ * np_ * np_;
+    M_ = (long long)nm_ * nm_ * nm_;
+    mass_ = (T)((double)M_ / (double)N_);
+    geo_.lg_np = ilog2(np_);
+    geo_.np = np_;
+    geo_.nm = nm_;
+    geo_.ratio = nm_ / np_;
+    geo_.inv_l = (T)(nm_ / cfg->box);
+    geo_.N = N_;
+    geo_.M = M_;
+    lgN_ = ilog2(N_);
+    e_d_ = 61 - lgN_;
+    G_ = (int)std::min<long long>((N_ + kPtclThreads - 1) / kPtclThreads, kMaxRedBlocks);
+    Gm_ = (int)std::min<long long>((M_ + kPtclThreads - 1) / kPtclThreads, kMaxRedBlocks);
+    Gz_ = (int)std::min<long long>((spec_len_cx(np_) + kPtclThreads - 1) / kPtclThreads, kMaxRedBlocks);
+    const long long pv = (long long)B_ * 3 * N_;
+    const long long sl = (long long)B_ * spec_len_cx(nm_);
+    PMGB_RET(alloc(&s_, pv));
+    PMGB_RET(alloc(&p_, pv));
+    PMGB_RET(alloc(&a_, pv));
+    PMGB_RET(alloc(&xi_, pv));
+    PMGB_RET(alloc(&pi_, pv));
+    PMGB_RET(alloc(&s1_, pv));
+    PMGB_RET(alloc(&omega_, (long long)B_ * N_));
+    for (int q = 0; q < 4; ++q) PMGB_RET(alloc(&acc_[q], (long long)B_ * M_));
+    for (int q = 0; q < 7; ++q) PMGB_RET(alloc(&spec_[q], sl));
+    PMGB_RET(alloc(&dens_, (long long)B_ * M_));
+    if (cfg->ckpt_every > 0) {
+      nck_ = (n_ + cfg->ckpt_every - 1) / cfg->ckpt_every;
+      PMGB_RET(alloc(&ck_s_, pv * nck_));
+      PMGB_RET(alloc(&ck_p_, pv * nck_));
+    }
+    for (int q = 0; q < 4; ++q) PMGB_CK(cudaMemsetAsync(acc_[q], 0, sizeof(long long) * B_ * M_, st_));
+    PMGB_CK(cudaMemcpyAsync(omega_, omega, sizeof(T) * B_ * N_, cudaMemcpyDeviceToDevice, st_));
+    PMGB_RET(tables(theta));
+    return PM_OK;
+  }
+
+  // ------------------------------------------------------------------ forward
+  int forward(void* disp, void* mom, void* dens) override {
+    PMGB_RET(initial_conditions());
+    for (int j = 0; j <= n_; ++j) {
+      PMGB_RET(force_chain(s_, nullptr, j == n_));
+      T* cks = nullptr;
+      T* ckp = nullptr;
+      if (nck_ && j < n_ && j % cfg_.ckpt_every == 0) {
+        cks = ck_s_ + (long long)(j / cfg_.ckpt_every) * B_ * 3 * N_;
+        ckp = ck_p_ + (long long)(j / cfg_.ckpt_every) * B_ * 3 * N_;
+      }
+      const long long fis = 2 * spec_len_cx(nm_);
+      StepCoef<T> sc{fkA_, fkB_, fdr_};
+      k_gather_fwd<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(
+          geo_, s_, p_, j == n_ ? a_ : nullptr, rmesh(1), rmesh(2), rmesh(3), fis, sc, j, n_ + 1, cks, ckp);
+      PMGB_CK(cudaGetLastError());
+    }
+    if (disp) PMGB_CK(cudaMemcpyAsync(disp, s_, sizeof(T) * B_ * 3 * N_, cudaMemcpyDeviceToDevice, st_));
+    if (mom) PMGB_CK(cudaMemcpyAsync(mom, p_, sizeof(T) * B_ * 3 * N_, cudaMemcpyDeviceToDevice, st_));
+    if (dens) PMGB_CK(cudaMemcpyAsync(dens, dens_, sizeof(T) * B_ * M_, cudaMemcpyDeviceToDevice, st_));
+    have_fwd_ = true;
+    return PM_OK;
+  }
+
+  int loss_mse(const void* target, double* loss, void* djdd) override {
+    if (!have_fwd_) return PM_ERR_STATE;
+    k_mse<T><<<dim3(Gm_, B_), kPtclThreads, 0, st_>>>(dens_, (const T*)target, (T*)djdd, M_, part_);
+    PMGB_CK(cudaGetLastError());
+    k_sum_partials<<<B_, 256, 0, st_>>>(part_, Gm_, scal_);
+    PMGB_CK(cudaGetLastError());
+    if (loss) {
+      const double inv = 1.0 / (double)M_;
+      // scale in a second tiny pass: loss = sum / M
+      PMGB_RET(scale_copy(scal_, inv, loss, B_));
+    }
+    return PM_OK;
+  }
+
+  // ------------------------------------------------------------------ adjoint
+  int adjoint(const void* djdd, const void* djdx, const void* djdp, void* djdw, double* djdth) override {
+    if (!have_fwd_) return PM_ERR_STATE;
+    PMGB_CK(cudaMemsetAsync(pimax_, 0, sizeof(unsigned) * 3 * B_, st_));
+    k_adjoint_init<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, mass_, s_, (const T*)djdd, (const T*)djdx,
+                                                              (const T*)djdp, xi_, pi_, pimax_);
+    PMGB_CK(cudaGetLastError());
+    const long long fis = 2 * spec_len_cx(nm_);
+    for (int j = n_; j >= 0; --j) {
+      PMGB_RET(force_chain(s_, pi_, false));
+      const T* ckp = nullptr;
+      const T* cks = nullptr;
+      if (nck_) {
+        if (j < n_ && j % cfg_.ckpt_every == 0) ckp = ck_p_ + (long long)(j / cfg_.ckpt_every) * B_ * 3 * N_;
+        if (j >= 1 && (j - 1) % cfg_.ckpt_every == 0)
+          cks = ck_s_ + (long long)((j - 1) / cfg_.ckpt_every) * B_ * 3 * N_;
+      }
+      StepCoef<T> sc{rkA_, rkB_, rdr_};
+      double* ppa = part_ + (long long)(2 * j) * B_ * G_;
+      double* pxp = part_ + (long long)(2 * j + 1) * B_ * G_;
+      k_gather_adj<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(
+          geo_, mass_, s_, p_, xi_, pi_, nullptr, nullptr, rmesh(1), rmesh(2), rmesh(3), rmesh(0), fis, sc, j,
+          n_ + 1, ckp, cks, ppa, pxp, pimax_);
+      PMGB_CK(cudaGetLastError());
+    }
+    // per-step sums: part_[(2j+q)][b][G] -> steps_[(2j+q)][b]
+    k_sum_partials<<<2 * (n_ + 1) * B_, 256, 0, st_>>>(part_, G_, steps_);
+    PMGB_CK(cudaGetLastError());
+    PMGB_RET(ic_adjoint(djdw));
+    // theta
+    ThetaIn in;
+    in.step_pa = steps_;  // layout [(2j+q)][b]: pa at q = 0, xp at q = 1
+    in.step_xp = steps_ + B_;
+    in.w_pa = wpa_;
+    in.w_xp = wxp_;
+    in.xs = scal_ + 2 * B_;
+    in.ps = scal_ + 3 * B_;
+    in.dlp = scal_ + 4 * B_;
+    in.dd1 = dd1_;
+    in.dgd = dgd_;
+    in.nstep1 = n_ + 1;
+    in.batch = B_;
+    in.step_stride = 2 * B_;
+    k_final_theta<<<(B_ + 31) / 32, 32, 0, st_>>>(in, theta_out_);
+    PMGB_CK(cudaGetLastError());
+    if (djdth) {
+      PMGB_CK(cudaMemcpyAsync(djdth, theta_out_, sizeof(double) * 5 * B_, cudaMemcpyDefault, st_));
+      if (is_host(djdth)) PMGB_CK(cudaStreamSynchronize(st_));
+    }
+    have_fwd_ = false;
+    return PM_OK;
+  }
+
+  // ------------------------------------------------------------------ operators
+  int op_density(const void* disp, void* dens) override {
+    have_fwd_ = false;
+    PMGB_CK(cudaMemcpyAsync(s_, disp, sizeof(T) * B_ * 3 * N_, cudaMemcpyDeviceToDevice, st_));
+    PMGB_RET(scatter(s_, nullptr));
+    k_density_out<T><<<1024, 256, 0, st_>>>((const long long*)acc_[0], (T*)dens, (long long)B_ * M_,
+                                            (T)ldexp((double)mass_, -e_d_));
+    PMGB_CK(cudaGetLastError());
+    PMGB_CK(cudaMemsetAsync(acc_[0], 0, sizeof(long long) * B_ * M_, st_));
+    return PM_OK;
+  }
+
+  int op_force(const void* disp, const void* pi, void* acc, void* alpha) override {
+    have_fwd_ = false;
+    PMGB_CK(cudaMemcpyAsync(s_, disp, sizeof(T) * B_ * 3 * N_, cudaMemcpyDeviceToDevice, st_));
+    const long long fis = 2 * spec_len_cx(nm_);
+    StepCoef<T> sc{zero_, zero_, zero_};
+    if (!pi) {
+      PMGB_RET(force_chain(s_, nullptr, false));
+      k_gather_fwd<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, s_, p_, (T*)acc, rmesh(1), rmesh(2),
+                                                              rmesh(3), fis, sc, 0, 1, nullptr, nullptr);
+    } else {
+      PMGB_CK(cudaMemcpyAsync(pi_, pi, sizeof(T) * B_ * 3 * N_, cudaMemcpyDeviceToDevice, st_));
+      PMGB_CK(cudaMemsetAsync(pimax_, 0, sizeof(unsigned) * 3 * B_, st_));
+      PMGB_CK(cudaMemsetAsync(xi_, 0, sizeof(T) * B_ * 3 * N_, st_));
+      // max|pi| through the adjoint init kernel with no cotangents except pi itself
+      k_adjoint_init<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, mass_, s_, nullptr, nullptr, (const T*)pi,
+                                                                xi_, pi_, pimax_);
+      PMGB_RET(force_chain(s_, pi_, false));
+      k_gather_adj<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, mass_, s_, p_, xi_, pi_, (T*)acc, (T*)alpha,
+                                                              rmesh(1), rmesh(2), rmesh(3), rmesh(0), fis, sc, 0, 1,
+                                                              nullptr, nullptr, nullptr, nullptr, nullptr);
+    }
+    PMGB_CK(cudaGetLastError());
+    return PM_OK;
+  }
+
+  int op_fft(int dir, const void* in, void* out) override {
+    have_fwd_ = false;
+    const long long tot = (long long)B_ * nm_ * nm_ * (nm_ / 2 + 1);
+    if (dir < 0) {
+      PMGB_RET(r2c_real(nm_, (const T*)in, (long long)M_, spec_[0]));
+      k_spec_to_std<T><<<1024, 256, 0, st_>>>(spec_[0], (C*)out, nm_, tot);
+    } else {
+      k_std_to_spec<T><<<1024, 256, 0, st_>>>((const C*)in, spec_[0], nm_, tot);
+      PMGB_CK(cudaGetLastError());
+      PMGB_RET(c2r_real(nm_, spec_[0], (T*)out, (long long)M_));
+    }
+    PMGB_CK(cudaGetLastError());
+    return PM_OK;
+  }
+
+  int op_za(void* s1) override {
+    have_fwd_ = false;
+    PMGB_RET(initial_conditions());
+    PMGB_CK(cudaMemcpyAsync(s1, s1_, sizeof(T) * B_ * 3 * N_, cudaMemcpyDeviceToDevice, st_));
+    return PM_OK;
+  }
+
+ private:
+  template <typename U> int alloc(U** p, long long count) {
+    void* q = nullptr;
+    const size_t bytes = sizeof(U) * (size_t)(count > 0 ? count : 1);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) { set_cuda_error(e); cudaGetLastError(); return PM_ERR_OOM; }
+    allocs_.push_back(q);
+    bytes_ += (long long)bytes;
+    *p = (U*)q;
+    return PM_OK;
+  }
+  static bool is_host(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) { cudaGetLastError(); return true; }
+    return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+  }
+  // real view of spectrum buffer q (after C2R)
+  T* rmesh(int q) { return reinterpret_cast<T*>(spec_[q]); }
+
+  int scale_copy(const double* src, double f, double* dst, int count) {
+    std::vector<double> h(count);
+    PMGB_CK(cudaMemcpyAsync(h.data(), src, sizeof(double) * count, cudaMemcpyDeviceToHost, st_));
+    PMGB_CK(cudaStreamSynchronize(st_));
+    for (double& v : h) v *= f;
+    PMGB_CK(cudaMemcpy(dst, h.data(), sizeof(double) * count, cudaMemcpyDefault));
+    return PM_OK;
+  }
+
+  // ---------------------------------------------------------------- host tables
+  int tables(const double* theta) {
+    const int n1 = n_ + 1;
+    std::vector<T> fkA(B_ * n1), fkB(B_ * n1), fdr(B_ * n1), rkA(B_ * n1), rkB(B_ * n1), rdr(B_ * n1);
+    std::vector<double> wpa(n1 * B_), wxp(n1 * B_), dd1(B_), dgd(B_);
+    std::vector<T> d1(B_), gd(B_), gcoef(B_);
+    const int maxn2 = 3 * (np_ / 2) * (np_ / 2);
+    const double kfp = 2.0 * M_PI / cfg_.box;
+    const double lp = cfg_.box / np_;
+    std::vector<T> amp((size_t)B_ * (maxn2 + 1));
+    std::vector<double> hdl((size_t)B_ * 5 * (maxn2 + 1));
+    for (int b = 0; b < B_; ++b) {
+      const double* th = theta + 5 * b;
+      const double om = th[2];
+      cosmo::TimeCoef tc;
+      cosmo::time_coefficients(cfg_.a0, cfg_.a1, n_, om, tc);
+      for (int j = 0; j <= n_; ++j) {
+        const int o = b * n1 + j;
+        fkA[o] = (T)(j >= 1 ? tc.k2[j - 1] : 0.0);
+        fkB[o] = (T)(j < n_ ? tc.k1[j] : 0.0);
+        fdr[o] = (T)(j < n_ ? tc.dd[j] : 0.0);
+        rkA[o] = (T)(j < n_ ? tc.k1[j] : 0.0);
+        rkB[o] = (T)(j >= 1 ? tc.k2[j - 1] : 0.0);
+        rdr[o] = (T)(j >= 1 ? tc.dd[j - 1] : 0.0);
+        double w = 0.0;
+        if (j < n_) w += tc.dk1[j] + tc.k1[j] / om;
+        if (j >= 1) w += tc.dk2[j - 1] + tc.k2[j - 1] / om;
+        wpa[j * B_ + b] = w;
+        wxp[j * B_ + b] = j >= 1 ? tc.ddd[j - 1] : 0.0;
+      }
+      d1[b] = (T)tc.d1_a0;
+      gd[b] = (T)tc.gd_a0;
+      dd1[b] = tc.dd1_a0;
+      dgd[b] = tc.dgd_a0;
+      // H_c = -i k_c G / M with G = -3/2 Om / k^2: per mode f_c * coef / n^2 * (-i)
+      const double kfm = 2.0 * M_PI / cfg_.box;
+      gcoef[b] = (T)(-1.5 * om / (kfm * (double)M_));
+      // ZA amplitude sqrt(P / l_p^3) / n_p^3 and 1/2 dlnP/dtheta per integer |n|^2
+      std::vector<double> p, dl;
+      cosmo::plin_tables(th, kfp, maxn2, p, dl);
+      for (int n2 = 0; n2 <= maxn2; ++n2) {
+        amp[(size_t)b * (maxn2 + 1) + n2] = (T)(n2 ? std::sqrt(p[n2] / (lp * lp * lp)) / (double)N_ : 0.0);
+        for (int j = 0; j < 5; ++j)
+          hdl[((size_t)b * 5 + j) * (maxn2 + 1) + n2] = n2 ? 0.5 * dl[(size_t)j * (maxn2 + 1) + n2] : 0.0;
+      }
+    }
+    maxn2_ = maxn2;
+    inv_kfp_ = (T)(1.0 / kfp);
+    PMGB_RET(upload(&fkA_, fkA));
+    PMGB_RET(upload(&fkB_, fkB));
+    PMGB_RET(upload(&fdr_, fdr));
+    PMGB_RET(upload(&rkA_, rkA));
+    PMGB_RET(upload(&rkB_, rkB));
+    PMGB_RET(upload(&rdr_, rdr));
+    PMGB_RET(upload(&wpa_, wpa));
+    PMGB_RET(upload(&wxp_, wxp));
+    PMGB_RET(upload(&dd1_, dd1));
+    PMGB_RET(upload(&dgd_, dgd));
+    PMGB_RET(upload(&d1_, d1));
+    PMGB_RET(upload(&gd_, gd));
+    PMGB_RET(upload(&gcoef_, gcoef));
+    PMGB_RET(upload(&amp_, amp));
+    PMGB_RET(upload(&hdl_, hdl));
+    std::vector<T> zero(B_, (T)0);
+    PMGB_RET(upload(&zero_, zero));
+    if (cfg_.deconv) {
+      std::vector<T> dt(nm_);
+      for (int i = 0; i < nm_; ++i) {
+        const int f = i < nm_ / 2 ? i : i - nm_;
+        const double x = M_PI * f / nm_;
+        const double sc = f == 0 ? 1.0 : std::sin(x) / x;
+        dt[i] = (T)(1.0 / (sc * sc * sc * sc));
+      }
+      PMGB_RET(upload(&dtab_, dt));
+    }
+    // twiddles: table of size L at [L, 2L): exp(-2 pi i m / L)
+    std::vector<C> tw(4096);
+    for (int L = 1; L <= 2048; L *= 2)
+      for (int m = 0; m < L; ++m) {
+        const double ang = -2.0 * M_PI * (double)m / (double)L;
+        tw[L + m].x = (T)std::cos(ang);
+        tw[L + m].y = (T)std::sin(ang);
+      }
+    PMGB_RET(upload(&tw_, tw));
+    PMGB_RET(alloc(&pimax_, 3 * B_));
+    PMGB_RET(alloc(&e_pi_, 3 * B_));
+    PMGB_RET(alloc(&part_, (long long)(2 * (n_ + 1) + 16) * B_ * kMaxRedBlocks));
+    PMGB_RET(alloc(&steps_, (long long)2 * (n_ + 1) * B_));
+    PMGB_RET(alloc(&scal_, (long long)16 * B_));
+    PMGB_RET(alloc(&theta_out_, (long long)5 * B_));
+    return PM_OK;
+  }
+  template <typename U> int upload(U** d, const std::vector<U>& h) {
+    PMGB_RET(alloc(d, (long long)h.size()));
+    PMGB_CK(cudaMemcpyAsync(*d, h.data(), sizeof(U) * h.size(), cudaMemcpyHostToDevice, st_));
+    PMGB_CK(cudaStreamSynchronize(st_));
+    return PM_OK;
+  }
+
+  // ---------------------------------------------------------------- FFT helpers
+  SeqMap ymap(int n) const {
+    return SeqMap{n / 2, 1, n / 2, (long long)n * (n / 2), n, spec_len_cx(n), B_ * n * (n / 2)};
+  }
+  SeqMap yside(int n) const {
+    return SeqMap{1, n, n, spec_len_cx(n), B_, 0, B_ * n};
+  }
+  SeqMap zmap(int n) const {
+    return SeqMap{(long long)n * (n / 2), 1, n / 2, n / 2, n, spec_len_cx(n), B_ * n * (n / 2)};
+  }
+  SeqMap zside(int n) const {
+    return SeqMap{n, 1, n, spec_len_cx(n), B_, 0, B_ * n};
+  }
+  // column pass over up to 4 buffers (main + side planes); side maps are offset by the
+  // main length through the buffer pointers
+  int cols(int n, int dir, bool zaxis, C* const* bufs, int nb) {
+    ColBufs<T> m{}, s{};
+    for (int q = 0; q < nb; ++q) {
+      m.p[q] = bufs[q];
+      s.p[q] = bufs[q] + spec_main_len(n);
+    }
+    const SeqMap mm = zaxis ? zmap(n) : ymap(n);
+    const SeqMap ms = zaxis ? zside(n) : yside(n);
+    SeqMap none = ms;
+    none.nseq = 0;
+    PMGB_RET(fft_cols<T>(n, dir, mm, none, m, nb, tw_, st_));
+    PMGB_RET(fft_cols<T>(n, dir, ms, none, s, nb, tw_, st_));
+    PMGB_CK(cudaGetLastError());
+    return PM_OK;
+  }
+  int r2c_real(int n, const T* in, long long in_is, C* out) {
+    RowJob<T> job{};
+    job.b[0] = RowBuf<T>{(void*)in, in_is, out, nullptr, 0, (T)1, (T)0, 0};
+    PMGB_RET(fft_x_r2c<T>(n, job, 1, B_ * n * n, false, tw_, st_));
+    C* bufs[1] = {out};
+    PMGB_RET(cols(n, -1, false, bufs, 1));
+    PMGB_RET(cols(n, -1, true, bufs, 1));
+    return PM_OK;
+  }
+  int c2r_real(int n, C* in, T* out, long long out_is) {
+    C* bufs[1] = {in};
+    PMGB_RET(cols(n, +1, true, bufs, 1));
+    PMGB_RET(cols(n, +1, false, bufs, 1));
+    RowJob<T> job{};
+    job.b[0] = RowBuf<T>{(void*)out, out_is, in, nullptr, 0, (T)1, (T)0, 0};
+    PMGB_RET(fft_x_c2r<T>(n, job, 1, B_ * n * n, tw_, st_));
+    PMGB_CK(cudaGetLastError());
+    return PM_OK;
+  }
+
+  int scatter(const T* s, const T* pi) {
+    if (pi) {
+      k_pi_exponents<<<1, 64, 0, st_>>>(pimax_, e_pi_, 3 * B_, lgN_);
+      PMGB_CK(cudaGetLastError());
+      PMGB_CK(cudaMemsetAsync(pimax_, 0, sizeof(unsigned) * 3 * B_, st_));
+      k_scatter<T, 4><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(
+          geo_, s, pi, (unsigned long long*)acc_[0], (unsigned long long*)acc_[1], (unsigned long long*)acc_[2],
+          (unsigned long long*)acc_[3], e_d_, e_pi_);
+    } else {
+      k_scatter<T, 1><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, s, nullptr, (unsigned long long*)acc_[0],
+                                                              nullptr, nullptr, nullptr, e_d_, nullptr);
+    }
+    PMGB_CK(cudaGetLastError());
+    return PM_OK;
+  }
+
+  // Force on the mesh (Sec. 2.2): scatter -> R2C -> Green's function and -ik -> 3 C2R,
+  // leaving f_c in spec_[1..3] (real view).  With pi also the adjoint chain: pi scatter ->
+  // 3 R2C -> sum_c conj(H_c) -> C2R, leaving psi in spec_[0].
+  int force_chain(const T* s, const T* pi, bool keep_density) {
+    PMGB_RET(scatter(s, pi));
+    if (keep_density) {
+      k_density_out<T><<<1024, 256, 0, st_>>>((const long long*)acc_[0], dens_, (long long)B_ * M_,
+                                              (T)ldexp((double)mass_, -e_d_));
+      PMGB_CK(cudaGetLastError());
+    }
+    const int nb = pi ? 4 : 1;
+    RowJob<T> job{};
+    job.b[0] = RowBuf<T>{acc_[0], M_, spec_[0], nullptr, e_d_, mass_, (T)-1, 1};
+    for (int c = 0; c < 3 && pi; ++c)
+      job.b[1 + c] = RowBuf<T>{acc_[1 + c], M_, spec_[4 + c], e_pi_ + c * B_, 0, (T)1, (T)0, 1};
+    PMGB_RET(fft_x_r2c<T>(nm_, job, nb, B_ * nm_ * nm_, true, tw_, st_));
+    PMGB_CK(cudaGetLastError());
+    C* fwdb[4] = {spec_[0], spec_[4], spec_[5], spec_[6]};
+    PMGB_RET(cols(nm_, -1, false, fwdb, nb));
+    ZJob<T> zf{};
+    zf.in[0] = spec_[0];
+    zf.out[0] = spec_[1];
+    zf.out[1] = spec_[2];
+    zf.out[2] = spec_[3];
+    zf.coef = gcoef_;
+    zf.dtab = dtab_;
+    zf.batch = B_;
+    PMGB_RET(fft_fused_z<T>(nm_, zf, false, tw_, st_));
+    PMGB_CK(cudaGetLastError());
+    if (pi) {
+      ZJob<T> za = zf;
+      za.in[0] = spec_[4];
+      za.in[1] = spec_[5];
+      za.in[2] = spec_[6];
+      za.out[0] = spec_[0];
+      PMGB_RET(fft_fused_z<T>(nm_, za, true, tw_, st_));
+      PMGB_CK(cudaGetLastError());
+    }
+    C* invb[4] = {spec_[1], spec_[2], spec_[3], spec_[0]};
+    PMGB_RET(cols(nm_, +1, false, invb, nb == 4 ? 4 : 3));
+    RowJob<T> jc{};
+    for (int q = 0; q < (pi ? 4 : 3); ++q) jc.b[q] = RowBuf<T>{invb[q], 2 * spec_len_cx(nm_), invb[q], nullptr, 0, (T)1, (T)0, 0};
+    PMGB_RET(fft_x_c2r<T>(nm_, jc, pi ? 4 : 3, B_ * nm_ * nm_, tw_, st_));
+    PMGB_CK(cudaGetLastError());
+    return PM_OK;
+  }
+
+  // Zel'dovich ICs (Sec. 2.1): omega -> R2C -> B_c = i k_c sqrt(P/l_p^3)/k^2 -> 3 C2R -> s1
+  int initial_conditions() {
+    const long long lis = spec_len_cx(np_);
+    // the lattice transforms use spec_[0..3] with the lattice instance stride
+    PMGB_RET(lattice_r2c(omega_, N_, spec_[0]));
+    k_za_mul<T><<<dim3(256, B_), 256, 0, st_>>>(spec_[0], spec_[1], spec_[2], spec_[3], np_, amp_, maxn2_,
+                                                inv_kfp_, lis);
+    PMGB_CK(cudaGetLastError());
+    C* bufs[3] = {spec_[1], spec_[2], spec_[3]};
+    PMGB_RET(lattice_c2r(bufs, 3));
+    k_ic_state<T><<<dim3(256, B_), 256, 0, st_>>>(rmesh(1), rmesh(2), rmesh(3), 2 * lis, N_, d1_, gd_, s1_, s_, p_);
+    PMGB_CK(cudaGetLastError());
+    return PM_OK;
+  }
+  int lattice_r2c(const T* in, long long in_is, C* out) {
+    RowJob<T> job{};
+    job.b[0] = RowBuf<T>{(void*)in, in_is, out, nullptr, 0, (T)1, (T)0, 0};
+    PMGB_RET(fft_x_r2c<T>(np_, job, 1, B_ * np_ * np_, false, tw_, st_));
+    C* bufs[1] = {out};
+    PMGB_RET(cols(np_, -1, false, bufs, 1));
+    PMGB_RET(cols(np_, -1, true, bufs, 1));
+    return PM_OK;
+  }
+  int lattice_c2r(C* const* bufs, int nb) {
+    PMGB_RET(cols(np_, +1, true, bufs, nb));
+    PMGB_RET(cols(np_, +1, false, bufs, nb));
+    RowJob<T> jc{};
+    for (int q = 0; q < nb; ++q) jc.b[q] = RowBuf<T>{bufs[q], 2 * spec_len_cx(np_), bufs[q], nullptr, 0, (T)1, (T)0, 0};
+    PMGB_RET(fft_x_c2r<T>(np_, jc, nb, B_ * np_ * np_, tw_, st_));
+    PMGB_CK(cudaGetLastError());
+    return PM_OK;
+  }
+
+  // Back-propagation through the ICs (Eq. 51): sbar = D1 xi_0 + G_D pi_0, omega_bar =
+  // sum_c B_c^T sbar_c, and the theta terms of P_lin, D1(a0), G_D(a0).
+  int ic_adjoint(void* djdw) {
+    const long long lis = spec_len_cx(np_);
+    k_ic_adj_prep<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(xi_, pi_, s1_, N_, d1_, gd_, rmesh(1), rmesh(2),
+                                                             rmesh(3), 2 * lis, part_, part_ + (long long)B_ * G_);
+    PMGB_CK(cudaGetLastError());
+    k_sum_partials<<<2 * B_, 256, 0, st_>>>(part_, G_, scal_ + 2 * B_);
+    PMGB_CK(cudaGetLastError());
+    // 3 R2C of sbar (in place: real input in the same buffer) and the R2C of omega
+    RowJob<T> job{};
+    for (int c = 0; c < 3; ++c) job.b[c] = RowBuf<T>{rmesh(1 + c), 2 * lis, spec_[1 + c], nullptr, 0, (T)1, (T)0, 0};
+    job.b[3] = RowBuf<T>{omega_, N_, spec_[0], nullptr, 0, (T)1, (T)0, 0};
+    PMGB_RET(fft_x_r2c<T>(np_, job, 4, B_ * np_ * np_, false, tw_, st_));
+    PMGB_CK(cudaGetLastError());
+    C* bufs[4] = {spec_[1], spec_[2], spec_[3], spec_[0]};
+    PMGB_RET(cols(np_, -1, false, bufs, 4));
+    PMGB_RET(cols(np_, -1, true, bufs, 4));
+    k_za_adj_mul<T><<<dim3(Gz_, B_), kPtclThreads, 0, st_>>>(spec_[1], spec_[2], spec_[3], spec_[0], spec_[5], np_,
+                                                             amp_, hdl_, maxn2_, inv_kfp_, lis, part_);
+    PMGB_CK(cudaGetLastError());
+    k_sum_partials<<<5 * B_, 256, 0, st_>>>(part_, Gz_, scal_ + 4 * B_);
+    PMGB_CK(cudaGetLastError());
+    C* ob[1] = {spec_[5]};
+    PMGB_RET(cols(np_, +1, true, ob, 1));
+    PMGB_RET(cols(np_, +1, false, ob, 1));
+    RowJob<T> jc{};
+    jc.b[0] = RowBuf<T>{djdw ? djdw : (void*)rmesh(5), djdw ? N_ : 2 * lis, spec_[5], nullptr, 0, (T)1, (T)0, 0};
+    PMGB_RET(fft_x_c2r<T>(np_, jc, 1, B_ * np_ * np_, tw_, st_));
+    PMGB_CK(cudaGetLastError());
+    return PM_OK;
+  }
+
+  pm_config cfg_{};
+  cudaStream_t st_ = 0;
+  int B_ = 1, np_ = 0, nm_ = 0, n_ = 0, lgN_ = 0, e_d_ = 0, G_ = 1, Gm_ = 1, Gz_ = 1, nck_ = 0, maxn2_ = 0;
+  long long N_ = 0, M_ = 0, bytes_ = 0;
+  T mass_ = 1, inv_kfp_ = 1;
+  Geo<T> geo_{};
+  std::vector<void*> allocs_;
+  T *s_ = nullptr, *p_ = nullptr, *a_ = nullptr, *xi_ = nullptr, *pi_ = nullptr, *s1_ = nullptr, *omega_ = nullptr;
+  long long* acc_[4] = {nullptr, nullptr, nullptr, nullptr};
+  C* spec_[7] = {};
+  T* dens_ = nullptr;
+  T *ck_s_ = nullptr, *ck_p_ = nullptr;
+  T *fkA_ = nullptr, *fkB_ = nullptr, *fdr_ = nullptr, *rkA_ = nullptr, *rkB_ = nullptr, *rdr_ = nullptr;
+  double *wpa_ = nullptr, *wxp_ = nullptr, *dd1_ = nullptr, *dgd_ = nullptr;
+  T *d1_ = nullptr, *gd_ = nullptr, *gcoef_ = nullptr, *amp_ = nullptr, *dtab_ = nullptr, *zero_ = nullptr;
+  double* hdl_ = nullptr;
+  C* tw_ = nullptr;
+  unsigned* pimax_ = nullptr;
+  int* e_pi_ = nullptr;
+  double *part_ = nullptr, *steps_ = nullptr, *scal_ = nullptr, *theta_out_ = nullptr;
+  bool have_fwd_ = false;
+};
+
+template <typename T>
+int make_engine_t(const pm_config* cfg, const double* theta, const void* omega, cudaStream_t st, EngineBase** out) {
+  Engine<T>* e = new Engine<T>();
+  const int r = e->init(cfg, theta, omega, st);
+  if (r != PM_OK) {
+    delete e;
+    return r;
+  }
+  *out = e;
+  return PM_OK;
+}
+
+}  // namespace pmgb

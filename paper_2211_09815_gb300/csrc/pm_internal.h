@@ -1,0 +1,61 @@
+// Internal declarations shared by the CUDA translation units of libpmgb.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pm.h"
+#include "common.cuh"
+
+namespace pmgb {
+
+// Address map of a batch of length-L sequences for a column FFT pass.  Sequence s,
+// element r lives at  o1*os1 + o0*os0 + col*cs + r*es  (complex elements) with
+// col = s % ncols, o0 = (s / ncols) % n0, o1 = s / (ncols * n0).
+struct SeqMap {
+  long long es, cs;
+  int ncols;
+  long long os0;
+  int n0;
+  long long os1;
+  int nseq;
+};
+
+template <typename T> struct ColBufs { cx_t<T>* p[4]; };
+
+// One buffer of a row (x) pass.  R2C: real -> spec.  C2R: spec -> real.
+template <typename T> struct RowBuf {
+  void* real;           // int64 accumulator or T mesh
+  long long real_is;    // instance stride of `real` in elements
+  cx_t<T>* spec;        // spectrum buffer (main + side)
+  const int* exps;      // fixed-point exponent per instance (device) or null
+  int exp_host;         // exponent when exps is null
+  T mul, add;           // value = acc * 2^-e * mul + add
+  int zero;             // zero the accumulator after reading
+};
+template <typename T> struct RowJob { RowBuf<T> b[4]; };
+
+// Fused z pass: spectra in -> spectra out with the Green's function multiplier
+// H_c = f_c * coef[b] / n^2 * (deconvolution) * (-i) per mode.
+template <typename T> struct ZJob {
+  cx_t<T>* in[3];
+  cx_t<T>* out[3];
+  const T* coef;    // [batch]
+  const T* dtab;    // [n] 1/sinc^4(pi f/n) or null
+  int batch;
+};
+
+template <typename T>
+int fft_cols(int n, int dir, const SeqMap& mm, const SeqMap& ms, const ColBufs<T>& bufs, int nbuf,
+             const cx_t<T>* tw, cudaStream_t st);
+template <typename T>
+int fft_x_r2c(int n, const RowJob<T>& job, int nbuf, int nrows, bool fixed, const cx_t<T>* tw,
+              cudaStream_t st);
+template <typename T>
+int fft_x_c2r(int n, const RowJob<T>& job, int nbuf, int nrows, const cx_t<T>* tw, cudaStream_t st);
+template <typename T>
+int fft_fused_z(int n, const ZJob<T>& job, bool adjoint, const cx_t<T>* tw, cudaStream_t st);
+
+// Set the dynamic shared-memory limit of a kernel once per device.
+void ensure_smem_attr(const void* fn, int bytes);
+
+}  // namespace pmgb

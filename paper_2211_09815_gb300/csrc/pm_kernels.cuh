@@ -1,0 +1,561 @@
+// Particle and mesh kernels of the PM hot path (besides the FFT passes), templated on the
+// real type.  Included once per precision.
+//
+//  k_scatter        CIC mass (and adjoint pi) assignment, Sec. 2.2 Eq. 10, int64 fixed point
+//  k_gather_fwd     CIC force gather + kick / kick / drift of Eq. 16 (one launch per step)
+//  k_gather_adj     CIC gather of a and alpha (Eq. 49 F line) + reverse kicks and drift of
+//                   Eq. 49, FP64 partials of the theta terms of Eq. 51
+//  k_adjoint_init   xi_n = dJ/dx_n (density cotangent through the CIC weight gradient), pi_n
+//  k_density_out, k_mse, k_za_mul, k_za_adj_mul, k_ic_state, k_ic_adj_prep, k_final_theta
+#pragma once
+#include "common.cuh"
+#include "pm_internal.h"
+
+namespace pmgb {
+
+constexpr int kPtclThreads = 256;
+constexpr int kMaxRedBlocks = 1024;
+
+// Lattice and mesh geometry of one instance.
+template <typename T> struct Geo {
+  int lg_np;      // log2 n_ptcl
+  int np, nm;     // particles / mesh nodes per side
+  int ratio;      // nm / np
+  T inv_l;        // 1 / cell size
+  long long N;    // particles per instance
+  long long M;    // mesh cells per instance
+};
+
+// Cell index and fraction along each axis for particle i at displacement s (floor
+// convention: u = q/l + s/l with q/l = j*ratio + 1/2; the integer part of q/l is added
+// separately so that the fraction keeps the precision of s, not of x).
+template <typename T>
+__device__ __forceinline__ void cic_cell(const Geo<T>& g, long long i, const T s[3], int cell[3], T t[3]) {
+  const int j[3] = {(int)(i >> (2 * g.lg_np)), (int)((i >> g.lg_np) & (g.np - 1)), (int)(i & (g.np - 1))};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const T v = (T)0.5 + s[c] * g.inv_l;
+    const T f = floor(v);
+    t[c] = v - f;
+    cell[c] = (j[c] * g.ratio + (int)f) & (g.nm - 1);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ long long corner_index(const Geo<T>& g, const int cell[3], int d) {
+  const int m = g.nm - 1;
+  const int i0 = (cell[0] + ((d >> 2) & 1)) & m;
+  const int i1 = (cell[1] + ((d >> 1) & 1)) & m;
+  const int i2 = (cell[2] + (d & 1)) & m;
+  return ((long long)i0 * g.nm + i1) * g.nm + i2;
+}
+
+template <typename T> __device__ __forceinline__ long long to_fixed(T v);
+template <> __device__ __forceinline__ long long to_fixed<float>(float v) { return __float2ll_rn(v); }
+template <> __device__ __forceinline__ long long to_fixed<double>(double v) { return __double2ll_rn(v); }
+
+// Deterministic block sum of one double per thread (fixed shuffle tree + fixed warp order).
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+  return r;
+}
+
+__device__ __forceinline__ float block_max(float v, float* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  float r = 0.f;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r = fmaxf(r, sh[i]);
+  return r;
+}
+
+template <typename T> __device__ __forceinline__ float abs_up(T v);
+template <> __device__ __forceinline__ float abs_up<float>(float v) { return fabsf(v); }
+template <> __device__ __forceinline__ float abs_up<double>(double v) { return __double2float_ru(fabs(v)); }
+
+// ------------------------------------------------------------------------- scatter
+// acc[0] += W * 2^e_d (weights), and with NQ = 4 also acc[1 + c] += pi_c * W * 2^e_c.
+template <typename T, int NQ>
+__global__ void __launch_bounds__(kPtclThreads)
+k_scatter(Geo<T> g, const T* __restrict__ s, const T* __restrict__ pi, unsigned long long* acc0,
+          unsigned long long* acc1, unsigned long long* acc2, unsigned long long* acc3, int e_d,
+          const int* __restrict__ e_pi) {
+  const int b = blockIdx.y;
+  const T* sb = s + (long long)b * 3 * g.N;
+  const long long mo = (long long)b * g.M;
+  const T sd = (T)ldexp(1.0, e_d);
+  T sp[3] = {0, 0, 0};
+  const T* pb = nullptr;
+  if constexpr (NQ == 4) {
+    pb = pi + (long long)b * 3 * g.N;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) sp[c] = (T)ldexp(1.0, e_pi[c * gridDim.y + b]);
+  }
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T sv[3] = {sb[i], sb[g.N + i], sb[2 * g.N + i]};
+    int cell[3];
+    T t[3];
+    cic_cell(g, i, sv, cell, t);
+    T pv[3] = {0, 0, 0};
+    if constexpr (NQ == 4) {
+      pv[0] = pb[i] * sp[0];
+      pv[1] = pb[g.N + i] * sp[1];
+      pv[2] = pb[2 * g.N + i] * sp[2];
+    }
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      const T w = ((d & 4) ? t[0] : (T)1 - t[0]) * ((d & 2) ? t[1] : (T)1 - t[1]) * ((d & 1) ? t[2] : (T)1 - t[2]);
+      const long long idx = mo + corner_index(g, cell, d);
+      atomicAdd(acc0 + idx, (unsigned long long)to_fixed<T>(w * sd));
+      if constexpr (NQ == 4) {
+        atomicAdd(acc1 + idx, (unsigned long long)to_fixed<T>(pv[0] * w));
+        atomicAdd(acc2 + idx, (unsigned long long)to_fixed<T>(pv[1] * w));
+        atomicAdd(acc3 + idx, (unsigned long long)to_fixed<T>(pv[2] * w));
+      }
+    }
+  }
+}
+
+// fixed-point exponents of the pi scatters from max|pi_c| (layout [c][batch]): the sum over one cell of
+// |pi| W is below N max|pi| < 2^(lg N + E), kept below 2^61.
+static __global__ void k_pi_exponents(const unsigned* __restrict__ pimax, int* __restrict__ e_pi, int nq, int lgN) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq) return;
+  const float mx = __uint_as_float(pimax[i]);
+  int e = 0;
+  if (mx > 0.f && isfinite(mx)) {
+    const int E = ilogbf(mx) + 1;   // mx < 2^E
+    e = 61 - lgN - E;
+    if (e > 100) e = 100;
+  }
+  e_pi[i] = e;
+}
+
+// ---------------------------------------------------------------------- gathers
+template <typename T>
+struct StepCoef {  // per-instance coefficient tables [batch][n+1], indexed at step j
+  const T* kA;
+  const T* kB;
+  const T* dr;
+};
+
+// a = sum_g W f(g);  p += a kA;  (store p_j);  p += a kB;  (store s_j);  s += p dr
+template <typename T>
+__global__ void __launch_bounds__(kPtclThreads)
+k_gather_fwd(Geo<T> g, T* __restrict__ s, T* __restrict__ p, T* __restrict__ a_out,
+             const T* __restrict__ f0, const T* __restrict__ f1, const T* __restrict__ f2, long long fis,
+             StepCoef<T> sc, int j, int nstep1, T* __restrict__ ck_s, T* __restrict__ ck_p) {
+  const int b = blockIdx.y;
+  const T kA = sc.kA[b * nstep1 + j], kB = sc.kB[b * nstep1 + j], dr = sc.dr[b * nstep1 + j];
+  T* sb = s + (long long)b * 3 * g.N;
+  T* pb = p + (long long)b * 3 * g.N;
+  const T* F[3] = {f0 + b * fis, f1 + b * fis, f2 + b * fis};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
+       i += (long long)gridDim.x * blockDim.x) {
+    T sv[3] = {sb[i], sb[g.N + i], sb[2 * g.N + i]};
+    int cell[3];
+    T t[3];
+    cic_cell(g, i, sv, cell, t);
+    T a[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      const T w = ((d & 4) ? t[0] : (T)1 - t[0]) * ((d & 2) ? t[1] : (T)1 - t[1]) * ((d & 1) ? t[2] : (T)1 - t[2]);
+      const long long idx = corner_index(g, cell, d);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) a[c] += w * __ldg(F[c] + idx);
+    }
+    T pv[3] = {pb[i], pb[g.N + i], pb[2 * g.N + i]};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      pv[c] += a[c] * kA;
+      if (ck_p) ck_p[(long long)b * 3 * g.N + c * g.N + i] = pv[c];
+      pv[c] += a[c] * kB;
+      if (ck_s) ck_s[(long long)b * 3 * g.N + c * g.N + i] = sv[c];
+      sv[c] += pv[c] * dr;
+      pb[c * g.N + i] = pv[c];
+      sb[c * g.N + i] = sv[c];
+      if (a_out) a_out[(long long)b * 3 * g.N + c * g.N + i] = a[c];
+    }
+  }
+}
+
+// Reverse step at force step j (Eq. 49): a_j = sum W f, alpha_j = sum grad W [pi.f + m psi];
+// p -= a K1_{j+1}; xi += alpha K1_{j+1}; (p := stored p_j); p -= a K2_j; xi += alpha K2_j;
+// s -= p D_j; pi += xi D_j; (s := stored s_{j-1}).  FP64 partials of pi.a and xi.p.
+template <typename T>
+__global__ void __launch_bounds__(kPtclThreads)
+k_gather_adj(Geo<T> g, T mass, T* __restrict__ s, T* __restrict__ p, T* __restrict__ xi, T* __restrict__ pi,
+             T* __restrict__ a_out, T* __restrict__ alpha_out,
+             const T* __restrict__ f0, const T* __restrict__ f1, const T* __restrict__ f2,
+             const T* __restrict__ psi, long long fis, StepCoef<T> sc, int j, int nstep1,
+             const T* __restrict__ ck_p, const T* __restrict__ ck_s, double* __restrict__ part_pa,
+             double* __restrict__ part_xp, unsigned* __restrict__ pimax) {
+  __shared__ double shd[kPtclThreads / 32];
+  __shared__ float shf[kPtclThreads / 32];
+  const int b = blockIdx.y;
+  const T cA = sc.kA[b * nstep1 + j], cB = sc.kB[b * nstep1 + j], dr = sc.dr[b * nstep1 + j];
+  const long long po = (long long)b * 3 * g.N;
+  const T* F[3] = {f0 + b * fis, f1 + b * fis, f2 + b * fis};
+  const T* PS = psi + b * fis;
+  const T il = g.inv_l;
+  double acc_pa = 0.0, acc_xp = 0.0;
+  float mx[3] = {0.f, 0.f, 0.f};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
+       i += (long long)gridDim.x * blockDim.x) {
+    T sv[3], pv[3], xv[3], qv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      sv[c] = s[po + c * g.N + i];
+      pv[c] = p[po + c * g.N + i];
+      xv[c] = xi[po + c * g.N + i];
+      qv[c] = pi[po + c * g.N + i];
+    }
+    int cell[3];
+    T t[3];
+    cic_cell(g, i, sv, cell, t);
+    T a[3] = {0, 0, 0}, al[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      const T w0 = (d & 4) ? t[0] : (T)1 - t[0];
+      const T w1 = (d & 2) ? t[1] : (T)1 - t[1];
+      const T w2 = (d & 1) ? t[2] : (T)1 - t[2];
+      const T g0 = (d & 4) ? il : -il, g1 = (d & 2) ? il : -il, g2 = (d & 1) ? il : -il;
+      const long long idx = corner_index(g, cell, d);
+      const T fv[3] = {__ldg(F[0] + idx), __ldg(F[1] + idx), __ldg(F[2] + idx)};
+      const T h = qv[0] * fv[0] + qv[1] * fv[1] + qv[2] * fv[2] + mass * __ldg(PS + idx);
+      const T w = w0 * w1 * w2;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) a[c] += w * fv[c];
+      al[0] += g0 * w1 * w2 * h;
+      al[1] += w0 * g1 * w2 * h;
+      al[2] += w0 * w1 * g2 * h;
+    }
+    acc_pa += (double)qv[0] * a[0] + (double)qv[1] * a[1] + (double)qv[2] * a[2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      pv[c] -= a[c] * cA;
+      xv[c] += al[c] * cA;
+      if (ck_p) pv[c] = ck_p[po + c * g.N + i];
+      pv[c] -= a[c] * cB;
+      xv[c] += al[c] * cB;
+    }
+    acc_xp += (double)xv[0] * pv[0] + (double)xv[1] * pv[1] + (double)xv[2] * pv[2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      sv[c] -= pv[c] * dr;
+      qv[c] += xv[c] * dr;
+      if (ck_s) sv[c] = ck_s[po + c * g.N + i];
+      s[po + c * g.N + i] = sv[c];
+      p[po + c * g.N + i] = pv[c];
+      xi[po + c * g.N + i] = xv[c];
+      pi[po + c * g.N + i] = qv[c];
+      mx[c] = fmaxf(mx[c], abs_up<T>(qv[c]));
+      if (a_out) a_out[po + c * g.N + i] = a[c];
+      if (alpha_out) alpha_out[po + c * g.N + i] = al[c];
+    }
+  }
+  const double spa = block_sum(acc_pa, shd);
+  const double sxp = block_sum(acc_xp, shd);
+  if (threadIdx.x == 0 && part_pa) {
+    part_pa[(long long)b * gridDim.x + blockIdx.x] = spa;
+    part_xp[(long long)b * gridDim.x + blockIdx.x] = sxp;
+  }
+  if (pimax) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float m = block_max(mx[c], shf);
+      if (threadIdx.x == 0) atomicMax(pimax + c * gridDim.y + b, __float_as_uint(m));
+    }
+  }
+}
+
+// xi = m sum_g grad W(g - x) dJ/ddelta(g) (+ dJ/dx);  pi = dJ/dp (or 0)
+template <typename T>
+__global__ void __launch_bounds__(kPtclThreads)
+k_adjoint_init(Geo<T> g, T mass, const T* __restrict__ s, const T* __restrict__ djdd, const T* __restrict__ djdx,
+               const T* __restrict__ djdp, T* __restrict__ xi, T* __restrict__ pi, unsigned* __restrict__ pimax) {
+  __shared__ float shf[kPtclThreads / 32];
+  const int b = blockIdx.y;
+  const long long po = (long long)b * 3 * g.N;
+  const T il = g.inv_l;
+  float mx[3] = {0.f, 0.f, 0.f};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
+       i += (long long)gridDim.x * blockDim.x) {
+    T xv[3] = {0, 0, 0};
+    if (djdd) {
+      const T sv[3] = {s[po + i], s[po + g.N + i], s[po + 2 * g.N + i]};
+      int cell[3];
+      T t[3];
+      cic_cell(g, i, sv, cell, t);
+      const T* D = djdd + (long long)b * g.M;
+#pragma unroll
+      for (int d = 0; d < 8; ++d) {
+        const T w0 = (d & 4) ? t[0] : (T)1 - t[0];
+        const T w1 = (d & 2) ? t[1] : (T)1 - t[1];
+        const T w2 = (d & 1) ? t[2] : (T)1 - t[2];
+        const T g0 = (d & 4) ? il : -il, g1 = (d & 2) ? il : -il, g2 = (d & 1) ? il : -il;
+        const T h = mass * __ldg(D + corner_index(g, cell, d));
+        xv[0] += g0 * w1 * w2 * h;
+        xv[1] += w0 * g1 * w2 * h;
+        xv[2] += w0 * w1 * g2 * h;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (djdx) xv[c] += djdx[po + c * g.N + i];
+      xi[po + c * g.N + i] = xv[c];
+      const T q = djdp ? djdp[po + c * g.N + i] : (T)0;
+      pi[po + c * g.N + i] = q;
+      mx[c] = fmaxf(mx[c], abs_up<T>(q));
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float m = block_max(mx[c], shf);
+    if (threadIdx.x == 0) atomicMax(pimax + c * gridDim.y + b, __float_as_uint(m));
+  }
+}
+
+// delta = m acc 2^-e - 1 (no zeroing)
+template <typename T>
+__global__ void k_density_out(const long long* __restrict__ acc, T* __restrict__ out, long long total, T mul) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (T)acc[i] * mul - (T)1;
+}
+
+// J partials sum (delta - target)^2 and dJ/ddelta = 2 (delta - target) / M
+template <typename T>
+__global__ void __launch_bounds__(kPtclThreads)
+k_mse(const T* __restrict__ dens, const T* __restrict__ tgt, T* __restrict__ grad, long long M, double* part) {
+  __shared__ double shd[kPtclThreads / 32];
+  const int b = blockIdx.y;
+  const T* d = dens + (long long)b * M;
+  const T* q = tgt + (long long)b * M;
+  T* gr = grad + (long long)b * M;
+  const T two_over_m = (T)(2.0 / (double)M);
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    const T diff = d[i] - q[i];
+    acc += (double)diff * diff;
+    gr[i] = two_over_m * diff;
+  }
+  const double r = block_sum(acc, shd);
+  if (threadIdx.x == 0) part[(long long)b * gridDim.x + blockIdx.x] = r;
+}
+
+// ------------------------------------------------------------------ lattice spectra
+// Mode (i0, i1, kx) of an n^3 half spectrum from a flat index over main + side.
+struct Mode { int f0, f1, f2; long long off; };
+__device__ __forceinline__ Mode mode_of(long long u, int n) {
+  Mode m;
+  const long long main = (long long)n * n * (n / 2);
+  if (u < main) {
+    const int kx = (int)(u % (n / 2));
+    const long long t = u / (n / 2);
+    m.f1 = freq_of((int)(t % n), n);
+    m.f0 = freq_of((int)(t / n), n);
+    m.f2 = kx;
+  } else {
+    const long long v = u - main;
+    m.f1 = freq_of((int)(v % n), n);
+    m.f0 = freq_of((int)(v / n), n);
+    m.f2 = n / 2;
+  }
+  m.off = u;
+  return m;
+}
+__device__ __forceinline__ int nyq_zero(int f, int n, bool last) { return last ? (f == n / 2 ? 0 : f) : (f == -n / 2 ? 0 : f); }
+
+// s1^_c = B_c Omega, B_c = i k_c / k^2 sqrt(P / l_p^3) / n^3 (Sec. 2.1, Eqs. 3-6)
+template <typename T>
+__global__ void k_za_mul(const cx_t<T>* __restrict__ om, cx_t<T>* o0, cx_t<T>* o1, cx_t<T>* o2, int n,
+                         const T* __restrict__ amp, int maxn2, T inv_kf, long long is) {
+  using C = cx_t<T>;
+  const int b = blockIdx.y;
+  const long long tot = spec_len_cx(n);
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < tot; u += (long long)gridDim.x * blockDim.x) {
+    const Mode m = mode_of(u, n);
+    const int n2 = m.f0 * m.f0 + m.f1 * m.f1 + m.f2 * m.f2;
+    const C v = om[b * is + u];
+    const T base = n2 ? amp[(long long)b * (maxn2 + 1) + n2] * inv_kf / (T)n2 : (T)0;
+    const int fc[3] = {nyq_zero(m.f0, n, false), nyq_zero(m.f1, n, false), nyq_zero(m.f2, n, true)};
+    C* outs[3] = {o0, o1, o2};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T sc = (T)fc[c] * base;
+      outs[c][b * is + u] = cmake<C>(-v.y * sc, v.x * sc);  // i v sc
+    }
+  }
+}
+
+// Omega_bar = sum_c conj(B_c) S_c;  theta partials sum_k w Re[conj(Omega_bar) Omega] dlnP_j / 2
+template <typename T>
+__global__ void __launch_bounds__(kPtclThreads)
+k_za_adj_mul(const cx_t<T>* s0, const cx_t<T>* s1, const cx_t<T>* s2, const cx_t<T>* __restrict__ om,
+             cx_t<T>* out, int n, const T* __restrict__ amp, const double* __restrict__ hdlnp, int maxn2,
+             T inv_kf, long long is, double* part /* [5][batch][grid] */) {
+  using C = cx_t<T>;
+  __shared__ double shd[kPtclThreads / 32];
+  const int b = blockIdx.y;
+  const long long tot = spec_len_cx(n);
+  double acc[5] = {0, 0, 0, 0, 0};
+  const C* ins[3] = {s0, s1, s2};
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < tot; u += (long long)gridDim.x * blockDim.x) {
+    const Mode m = mode_of(u, n);
+    const int n2 = m.f0 * m.f0 + m.f1 * m.f1 + m.f2 * m.f2;
+    const T base = n2 ? amp[(long long)b * (maxn2 + 1) + n2] * inv_kf / (T)n2 : (T)0;
+    const int fc[3] = {nyq_zero(m.f0, n, false), nyq_zero(m.f1, n, false), nyq_zero(m.f2, n, true)};
+    C r = cmake<C>(0, 0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const C v = ins[c][b * is + u];
+      const T sc = (T)fc[c] * base;
+      r = cadd(r, cmake<C>(v.y * sc, -v.x * sc));  // -i v sc
+    }
+    out[b * is + u] = r;
+    const C w = om[b * is + u];
+    const double re = (double)r.x * w.x + (double)r.y * w.y;
+    const double wt = (m.f2 == 0 || m.f2 == n / 2) ? 1.0 : 2.0;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) acc[j] += wt * re * hdlnp[((long long)b * 5 + j) * (maxn2 + 1) + n2];
+  }
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    const double r = block_sum(acc[j], shd);
+    if (threadIdx.x == 0) part[((long long)j * gridDim.y + b) * gridDim.x + blockIdx.x] = r;
+  }
+}
+
+// s1 from the lattice C2R outputs; s = D1 s1, p = G_D s1
+template <typename T>
+__global__ void k_ic_state(const T* __restrict__ r0, const T* __restrict__ r1, const T* __restrict__ r2, long long ris,
+                           long long N, const T* __restrict__ d1, const T* __restrict__ gd, T* s1, T* s, T* p) {
+  const int b = blockIdx.y;
+  const T* rs[3] = {r0 + b * ris, r1 + b * ris, r2 + b * ris};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T v = rs[c][i];
+      const long long o = (long long)b * 3 * N + c * N + i;
+      if (s1) s1[o] = v;
+      if (s) s[o] = d1[b] * v;
+      if (p) p[o] = gd[b] * v;
+    }
+  }
+}
+
+// sbar = D1 xi + G_D pi into the lattice FFT inputs; partials of xi.s1 and pi.s1
+template <typename T>
+__global__ void __launch_bounds__(kPtclThreads)
+k_ic_adj_prep(const T* __restrict__ xi, const T* __restrict__ pi, const T* __restrict__ s1, long long N,
+              const T* __restrict__ d1, const T* __restrict__ gd, T* w0, T* w1, T* w2, long long wis,
+              double* part_xs, double* part_ps) {
+  __shared__ double shd[kPtclThreads / 32];
+  const int b = blockIdx.y;
+  T* ws[3] = {w0 + b * wis, w1 + b * wis, w2 + b * wis};
+  double axs = 0, aps = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const long long o = (long long)b * 3 * N + c * N + i;
+      const T x = xi[o], q = pi[o], u = s1[o];
+      ws[c][i] = d1[b] * x + gd[b] * q;
+      axs += (double)x * u;
+      aps += (double)q * u;
+    }
+  }
+  const double r1 = block_sum(axs, shd);
+  const double r2 = block_sum(aps, shd);
+  if (threadIdx.x == 0) {
+    part_xs[(long long)b * gridDim.x + blockIdx.x] = r1;
+    part_ps[(long long)b * gridDim.x + blockIdx.x] = r2;
+  }
+}
+
+// Fixed-order sum of `count` partials for each instance: out[b] = sum_i part[b][i]
+static __global__ void k_sum_partials(const double* __restrict__ part, int count, double* out) {
+  __shared__ double shd[8];
+  const int b = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) acc += part[(long long)b * count + i];
+  const double r = block_sum(acc, shd);
+  if (threadIdx.x == 0) out[b] = r;
+}
+
+// dJ/dtheta (Eq. 51): time-stepping terms (Omega_m only), initial-condition growth terms
+// and the P_lin derivative terms.  sums: per instance the already reduced scalars.
+struct ThetaIn {
+  const double* step_pa;   // pi.a at step j, instance b: step_pa[j * step_stride + b]
+  const double* step_xp;   // xi.p at step j: step_xp[j * step_stride + b]
+  const double* w_pa;      // weight of pi.a: w_pa[j * batch + b]
+  const double* w_xp;      // weight of xi.p
+  const double* xs;        // [batch]   xi_0 . s1
+  const double* ps;        // [batch]   pi_0 . s1
+  const double* dlp;       // [5][batch]
+  const double* dd1;       // [batch]   dD1(a0)/dOm
+  const double* dgd;       // [batch]   dG_D(a0)/dOm
+  int nstep1, batch, step_stride;
+};
+static __global__ void k_final_theta(ThetaIn in, double* out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= in.batch) return;
+  double g = 0.0;
+  for (int j = 0; j < in.nstep1; ++j) {
+    const long long o = (long long)j * in.step_stride + b;
+    const long long w = (long long)j * in.batch + b;
+    g += in.step_pa[o] * in.w_pa[w] + in.step_xp[o] * in.w_xp[w];
+  }
+  g += in.xs[b] * in.dd1[b] + in.ps[b] * in.dgd[b];
+  for (int j = 0; j < 5; ++j) out[5 * b + j] = in.dlp[j * in.batch + b] + (j == 2 ? g : 0.0);
+}
+
+// numpy rfftn layout <-> main + side spectrum layout (for the FFT operator entry point)
+template <typename T>
+__global__ void k_spec_to_std(const cx_t<T>* __restrict__ spec, cx_t<T>* __restrict__ out, int n, long long total) {
+  const int h = n / 2 + 1;
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < total; u += (long long)gridDim.x * blockDim.x) {
+    const long long per = (long long)n * n * h;
+    const long long b = u / per, r = u % per;
+    const int k = (int)(r % h);
+    const long long row = r / h;
+    const cx_t<T>* base = spec + b * spec_len_cx(n);
+    out[u] = k < n / 2 ? base[row * (n / 2) + k] : base[spec_main_len(n) + row];
+  }
+}
+template <typename T>
+__global__ void k_std_to_spec(const cx_t<T>* __restrict__ in, cx_t<T>* __restrict__ spec, int n, long long total) {
+  const int h = n / 2 + 1;
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < total; u += (long long)gridDim.x * blockDim.x) {
+    const long long per = (long long)n * n * h;
+    const long long b = u / per, r = u % per;
+    const int k = (int)(r % h);
+    const long long row = r / h;
+    cx_t<T>* base = spec + b * spec_len_cx(n);
+    if (k < n / 2) base[row * (n / 2) + k] = in[u];
+    else base[spec_main_len(n) + row] = in[u];
+  }
+}
+
+// strided copy of real meshes between layouts with different instance strides
+template <typename T>
+__global__ void k_copy_strided(const T* __restrict__ in, long long in_is, T* __restrict__ out, long long out_is,
+                               long long count) {
+  const int b = blockIdx.y;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    out[b * out_is + i] = in[b * in_is + i];
+}
+
+}  // namespace pmgb

@@ -1,0 +1,178 @@
+"""Thin ctypes binding of libpmgb (include/pm.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module only converts torch tensors to
+device pointers and checks shapes and dtypes.  Importing it does not need a GPU; the
+first call that needs the library raises ``PMLibraryError`` if ``libpmgb.so`` has not
+been built (``python -m paper_2211_09815_gb300.build``) -- there is no fallback.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpmgb.so")
+
+PM_F32, PM_F64 = 0, 1
+STATUS = {0: "PM_OK", 1: "PM_ERR_ARG", 2: "PM_ERR_OOM", 3: "PM_ERR_CUDA", 4: "PM_ERR_NONFINITE",
+          5: "PM_ERR_OVERFLOW", 6: "PM_ERR_TIMEOUT", 7: "PM_ERR_STATE"}
+SYMBOLS = ("pm_init", "pm_forward", "pm_loss_mse", "pm_adjoint", "pm_destroy", "pm_status_string",
+           "pm_last_cuda_error", "pm_scratch_bytes", "pm_op_density", "pm_op_force", "pm_op_force_vjp",
+           "pm_op_fft", "pm_op_za")
+
+
+class PMLibraryError(RuntimeError):
+    pass
+
+
+class PMError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} {detail}".strip())
+
+
+class PMConfig(ctypes.Structure):
+    _fields_ = [("box", ctypes.c_double), ("n_mesh", ctypes.c_int), ("n_ptcl", ctypes.c_int),
+                ("n_steps", ctypes.c_int), ("a0", ctypes.c_double), ("a1", ctypes.c_double),
+                ("precision", ctypes.c_int), ("ckpt_every", ctypes.c_int), ("deconv", ctypes.c_int),
+                ("batch", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libpmgb.so and declare the ABI; raises PMLibraryError if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise PMLibraryError(f"{path} not built; run python -m paper_2211_09815_gb300.build")
+    lib = ctypes.CDLL(path)
+    vp, dp, i = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+    lib.pm_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(PMConfig), dp, vp, vp]
+    lib.pm_forward.argtypes = [vp, vp, vp, vp]
+    lib.pm_loss_mse.argtypes = [vp, vp, vp, vp]
+    lib.pm_adjoint.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.pm_destroy.argtypes = [vp]
+    lib.pm_status_string.argtypes = [i]
+    lib.pm_status_string.restype = ctypes.c_char_p
+    lib.pm_last_cuda_error.restype = ctypes.c_char_p
+    lib.pm_scratch_bytes.argtypes = [vp]
+    lib.pm_scratch_bytes.restype = ctypes.c_longlong
+    lib.pm_op_density.argtypes = [vp, vp, vp]
+    lib.pm_op_force.argtypes = [vp, vp, vp]
+    lib.pm_op_force_vjp.argtypes = [vp, vp, vp, vp, vp]
+    lib.pm_op_fft.argtypes = [vp, i, vp, vp]
+    lib.pm_op_za.argtypes = [vp, vp]
+    for name in SYMBOLS:
+        getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status, where):
+    if status != 0:
+        lib = load_library()
+        raise PMError(status, where, lib.pm_last_cuda_error().decode() if status == 3 else "")
+
+
+def _ptr(t, dtype=None, numel=None, name="tensor"):
+    if t is None:
+        return None
+    import torch
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class PMContext:
+    """One simulation context (owns the library's device scratch).
+
+    omega: CUDA tensor [batch, n_ptcl, n_ptcl, n_ptcl] (float32 or float64 per precision);
+    theta: host sequence of shape [batch, 5] (A_s, n_s, Omega_m, Omega_b, h).
+    """
+
+    def __init__(self, box, n_mesh, n_ptcl, n_steps, theta, omega, a0=1.0 / 64, a1=1.0,
+                 precision=PM_F32, ckpt_every=0, deconv=False, batch=1, stream=None):
+        import torch
+        lib = load_library()
+        self.cfg = PMConfig(box, n_mesh, n_ptcl, n_steps, a0, a1, precision, ckpt_every, int(deconv), batch)
+        self.dtype = torch.float32 if precision == PM_F32 else torch.float64
+        self.batch, self.n_mesh, self.n_ptcl = batch, n_mesh, n_ptcl
+        self.N, self.M = n_ptcl ** 3, n_mesh ** 3
+        th = [float(v) for row in (theta if hasattr(theta[0], "__len__") else [theta]) for v in row]
+        if len(th) != 5 * batch:
+            raise ValueError("theta must have batch x 5 values")
+        arr = (ctypes.c_double * len(th))(*th)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._h = ctypes.c_void_p()
+        _check(lib.pm_init(ctypes.byref(self._h), ctypes.byref(self.cfg), arr,
+                           _ptr(omega, self.dtype, batch * self.N, "omega"),
+                           ctypes.c_void_p(self.stream.cuda_stream)), "pm_init")
+
+    def close(self):
+        if self._h:
+            load_library().pm_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _new(self, *shape, dtype=None):
+        import torch
+        return torch.empty(*shape, device="cuda", dtype=dtype or self.dtype)
+
+    def forward(self, disp=None, mom=None, dens=None):
+        v = 3 * self.batch * self.N
+        _check(load_library().pm_forward(self._h, _ptr(disp, self.dtype, v, "disp"), _ptr(mom, self.dtype, v, "mom"),
+                                         _ptr(dens, self.dtype, self.batch * self.M, "dens")), "pm_forward")
+
+    def loss_mse(self, target, djdd, loss=None):
+        """loss: optional host float64 tensor [batch] or CUDA float64 tensor."""
+        import torch
+        out = loss if loss is not None else torch.zeros(self.batch, dtype=torch.float64)
+        _check(load_library().pm_loss_mse(self._h, _ptr(target, self.dtype, self.batch * self.M, "target"),
+                                          ctypes.c_void_p(out.data_ptr()),
+                                          _ptr(djdd, self.dtype, self.batch * self.M, "djdd")), "pm_loss_mse")
+        return out
+
+    def adjoint(self, djdd=None, djdx=None, djdp=None, grad_omega=None, grad_theta=None):
+        v = 3 * self.batch * self.N
+        gt = ctypes.c_void_p(grad_theta.data_ptr()) if grad_theta is not None else None
+        _check(load_library().pm_adjoint(self._h, _ptr(djdd, self.dtype, self.batch * self.M, "djdd"),
+                                         _ptr(djdx, self.dtype, v, "djdx"), _ptr(djdp, self.dtype, v, "djdp"),
+                                         _ptr(grad_omega, self.dtype, self.batch * self.N, "grad_omega"), gt),
+               "pm_adjoint")
+
+    def op_density(self, disp, dens):
+        _check(load_library().pm_op_density(self._h, _ptr(disp, self.dtype, 3 * self.batch * self.N),
+                                            _ptr(dens, self.dtype, self.batch * self.M)), "pm_op_density")
+
+    def op_force(self, disp, acc):
+        v = 3 * self.batch * self.N
+        _check(load_library().pm_op_force(self._h, _ptr(disp, self.dtype, v), _ptr(acc, self.dtype, v)),
+               "pm_op_force")
+
+    def op_force_vjp(self, disp, pi, acc, alpha):
+        v = 3 * self.batch * self.N
+        _check(load_library().pm_op_force_vjp(self._h, _ptr(disp, self.dtype, v), _ptr(pi, self.dtype, v),
+                                              _ptr(acc, self.dtype, v), _ptr(alpha, self.dtype, v)),
+               "pm_op_force_vjp")
+
+    def op_fft(self, direction, inp, out):
+        _check(load_library().pm_op_fft(self._h, int(direction), _ptr(inp), _ptr(out)), "pm_op_fft")
+
+    def op_za(self, s1):
+        _check(load_library().pm_op_za(self._h, _ptr(s1, self.dtype, 3 * self.batch * self.N)), "pm_op_za")
+
+    @property
+    def scratch_bytes(self):
+        return load_library().pm_scratch_bytes(self._h)

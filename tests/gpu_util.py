@@ -1,0 +1,47 @@
+"""Helpers for the GPU parity tests: build/load the library, run oracle and CUDA side by
+side on the same seeded inputs."""
+import numpy as np
+
+from oracle import pm as opm
+from paper_2211_09815_gb300 import inputs
+
+
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return torch
+
+
+def ensure_built():
+    from paper_2211_09815_gb300 import build
+    build.build()
+
+
+def make_ctx(box, n_mesh, n_ptcl, n_steps, theta=inputs.THETA_FIDUCIAL, seed=1, precision=0, batch=1,
+             ckpt_every=0, deconv=False, a0=1 / 64, a1=1.0, omega=None):
+    torch = torch_cuda()
+    ensure_built()
+    from paper_2211_09815_gb300 import pm
+    dt = torch.float32 if precision == 0 else torch.float64
+    if omega is None:
+        omega = np.stack([inputs.white_noise(n_ptcl, seed + b) for b in range(batch)])
+    om = torch.from_numpy(np.ascontiguousarray(omega)).to(device="cuda", dtype=dt)
+    th = np.atleast_2d(np.asarray(theta, dtype=np.float64))
+    if th.shape[0] == 1 and batch > 1:
+        th = np.repeat(th, batch, axis=0)
+    ctx = pm.PMContext(box, n_mesh, n_ptcl, n_steps, th.tolist(), om, a0=a0, a1=a1, precision=precision,
+                       ckpt_every=ckpt_every, deconv=deconv, batch=batch)
+    return ctx, om, omega, th
+
+
+def oracle_cfg(box, n_mesh, n_ptcl, n_steps, deconv=False, a0=1 / 64, a1=1.0):
+    return opm.PMConfig(box=box, n_mesh=n_mesh, n_ptcl=n_ptcl, n_steps=n_steps, deconv=deconv, a0=a0, a1=a1)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def cosine(a, b):
+    a, b = np.ravel(a), np.ravel(b)
+    return float(np.dot(a, b) / (np.linalg.norm(a) * np.linalg.norm(b)))

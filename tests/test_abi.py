@@ -1,0 +1,53 @@
+"""The C-ABI library builds, loads and exports every entry point that include/pm.h
+declares (no compute calls: no GPU needed)."""
+import os
+import re
+
+from paper_2211_09815_gb300 import build, pm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "pm.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*|long long)\s+(pm_\w+)\s*\(", txt, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("pm_init", "pm_forward", "pm_adjoint", "pm_destroy", "pm_status_string", "pm_loss_mse"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    build.build()
+    lib = pm.load_library()
+    for name in _declared():
+        assert hasattr(lib, name), name
+    assert set(_declared()) <= set(pm.SYMBOLS) | {"pm_status_string"}
+    assert lib.pm_status_string(0) == b"ok"
+    assert lib.pm_status_string(1) == b"invalid argument"
+
+
+def test_invalid_configs_are_rejected_on_the_host():
+    """Validation happens before any CUDA call, so it runs without a GPU."""
+    import ctypes
+    lib = pm.load_library()
+    h = ctypes.c_void_p()
+    th = (ctypes.c_double * 5)(2.1e-9, 0.965, 0.31, 0.049, 0.68)
+    dummy = ctypes.c_void_p(16)
+    bad = [
+        pm.PMConfig(100.0, 48, 16, 10, 1 / 64, 1.0, 0, 0, 0, 1),    # mesh not a power of two
+        pm.PMConfig(100.0, 32, 64, 10, 1 / 64, 1.0, 0, 0, 0, 1),    # mesh not a multiple of n_ptcl
+        pm.PMConfig(100.0, 2048, 64, 10, 1 / 64, 1.0, 0, 0, 0, 1),  # mesh too large
+        pm.PMConfig(-1.0, 32, 16, 10, 1 / 64, 1.0, 0, 0, 0, 1),     # box
+        pm.PMConfig(100.0, 32, 16, 0, 1 / 64, 1.0, 0, 0, 0, 1),     # steps
+        pm.PMConfig(100.0, 32, 16, 10, 1.0, 0.5, 0, 0, 0, 1),       # a1 < a0
+        pm.PMConfig(100.0, 32, 16, 10, 1 / 64, 1.0, 7, 0, 0, 1),    # precision
+    ]
+    for cfg in bad:
+        assert lib.pm_init(ctypes.byref(h), ctypes.byref(cfg), th, dummy, None) == 1
+    nan = (ctypes.c_double * 5)(float("nan"), 0.965, 0.31, 0.049, 0.68)
+    ok = pm.PMConfig(100.0, 32, 16, 10, 1 / 64, 1.0, 0, 0, 0, 1)
+    assert lib.pm_init(ctypes.byref(h), ctypes.byref(ok), nan, dummy, None) == 4
+    assert lib.pm_forward(None, None, None, None) == 1
