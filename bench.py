@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark of the adjoint-gradient particle-mesh step on GB300.
+
+One bench step is one full gradient evaluation of the large single-instance workload:
+512^3 particles, 1024^3 FP32 mesh, 1000 Mpc/h box, Zel'dovich ICs at a = 1/64, 100 KDK
+steps to a = 1, density MSE objective against a target from a second seed, then the
+adjoint with reverse time integration back to dJ/domega and dJ/dtheta.  The metric is
+PM gradient steps per second: 100 / (time of one evaluation); each counted step
+includes its forward KDK step and its reverse adjoint step (ICs, loss and the IC adjoint
+are amortised into it).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own independent instance (replicas; the
+path has no data-parallel exchange): weak scaling, value = all ranks' steps / max time.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "adjoint-gradient PM steps/s at 512^3 particles; achieved HBM BW fraction"
+WORKLOADS = {
+    # name: (box, n_mesh, n_ptcl, n_steps)
+    "large": (1000.0, 1024, 512, 100),
+    "medium": (400.0, 512, 256, 63),
+    "small": (200.0, 256, 128, 63),
+}
+THETA = (2.1e-9, 0.965, 0.31, 0.049, 0.68)
+SAMPLE_SCALE = 512.0  # the oracle sample covers 1/512 of the large workload's particles and cells
+SAMPLE_TEXT = ("FP64 oracle (numpy, 1 thread): one forward + one adjoint PM step at 64^3 particles / 128^3 mesh / "
+               "125 Mpc/h, scaled x512 in volume to the 512^3 / 1024^3 workload (FFT log factor ignored, "
+               "which flatters the oracle)")
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ algorithmic bytes
+def algorithmic_bytes(n_steps, N, M, batch=1):
+    """Compulsory FP32 traffic per gradient evaluation and per kernel category: one read
+    and one write of every mesh a pass touches, particle arrays read and written once.
+    Forward: n+1 force evaluations; adjoint: n+1 forward + adjoint force evaluations."""
+    f = n_steps + 1
+    b = {
+        "scatter": f * (4 * M + 12 * N) + f * (16 * M + 24 * N),
+        "fft_x_r2c": f * 8 * M + f * 32 * M,
+        "fft_cols": f * (8 * M + 24 * M) + f * (32 * M + 32 * M),
+        "fused_z_force": 2 * f * 16 * M,
+        "fused_z_adjoint": f * 16 * M,
+        "fft_x_c2r": f * 24 * M + f * 32 * M,
+        "gather_fwd": f * (12 * M + 48 * N),
+        "gather_adj": f * (16 * M + 96 * N),
+    }
+    return {k: v * batch for k, v in b.items()}
+
+
+# ----------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (read-only queries)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------- oracle sample
+def oracle_sample_seconds(repeats=1):
+    """FP64 oracle, one forward PM step plus one adjoint PM step (force, force VJP and
+    the kicks/drift) at 64^3 particles on a 128^3 mesh in a 125 Mpc/h box -- the large
+    workload's cell size and particle/mesh ratio at 1/512 of its volume."""
+    from oracle import cosmo
+    from oracle import pm as opm
+    from paper_2211_09815_gb300 import inputs
+    cfg = opm.PMConfig(box=125.0, n_mesh=128, n_ptcl=64, n_steps=100)
+    om = inputs.white_noise(64, 1).astype(np.float64)
+    s, p, _ = opm.za_initial_state(om, THETA, cfg)
+    q = opm.lattice(cfg)
+    k1, dd, k2 = cosmo.kdk_factors(cosmo.time_grid(cfg.a0, cfg.a1, cfg.n_steps), THETA[2])
+    pi = np.zeros_like(s)
+    xi = np.ones_like(s) * 1e-3
+    times = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        # forward step i = 1: kick, drift, force, kick
+        a, _ = opm.pm_force(q + s, THETA[2], cfg)
+        p1 = p + a * k1[0]
+        s1 = s + p1 * dd[0]
+        a, _ = opm.pm_force(q + s1, THETA[2], cfg)
+        p1 = p1 + a * k2[0]
+        # adjoint step: reverse kick, reverse drift, force + VJP, reverse kick
+        p2 = p1 - a * k2[0]
+        xi2 = xi + a * k2[0]
+        s2 = s1 - p2 * dd[0]
+        pi2 = pi + xi2 * dd[0]
+        a2, f = opm.pm_force(q + s2, THETA[2], cfg)
+        al = opm.force_vjp(q + s2, pi2 + 1e-3, f, THETA[2], cfg)
+        _ = (p2 - a2 * k1[0], xi2 + al * k1[0])
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample_seconds(1)
+    times = oracle_sample_seconds(args.steps)
+    scale = SAMPLE_SCALE
+    t_scaled = float(np.mean(times)) * scale
+    value = 1.0 / t_scaled
+    sample = SAMPLE_TEXT
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_scaled * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "512^3 particles, 1024^3 mesh, 1000 Mpc/h, 100 KDK steps (sampled)"},
+           "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ------------------------------------------------------------------------ ours
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2211_09815_gb300 import build, inputs, pm
+
+    torch.cuda.set_device(local_rank)
+    build.build()
+    box, nm, npc, n = WORKLOADS[args.workload]
+    N, M = npc ** 3, nm ** 3
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    seed = 1 + 10 * rank
+    om_host = torch.from_numpy(inputs.white_noise(npc, seed)).pin_memory()
+    om = om_host.to("cuda")
+    # target density from a second seed, made by the same forward model
+    om2 = torch.from_numpy(inputs.white_noise(npc, seed + 1)).to("cuda")
+    ctx_t = pm.PMContext(box, nm, npc, n, [THETA], om2)
+    target = torch.empty(M, device="cuda")
+    ctx_t.forward(dens=target)
+    torch.cuda.synchronize()
+    ctx_t.close()
+    del om2
+    ctx = pm.PMContext(box, nm, npc, n, [THETA], om)
+    djdd = torch.empty(M, device="cuda")
+    gw = torch.empty(N, device="cuda")
+    gt = torch.zeros(5, dtype=torch.float64, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+    def evaluation():
+        ctx.forward()
+        ctx.loss_mse(target, djdd, loss)
+        ctx.adjoint(djdd=djdd, grad_omega=gw, grad_theta=gt)
+
+    for _ in range(args.warmup):
+        evaluation()
+    torch.cuda.synchronize()
+    ctx.profile_read()
+    ctx.profile(True)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        evaluation()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    loss_val = float(loss.item())
+    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    ms_per_eval = ms_max / args.steps
+    value = world * n * args.steps / (ms_max / 1e3)
+
+    # end to end through the C ABI with host buffers: omega and target in, loss and
+    # gradients out, copies inside the timed region
+    tgt_host = target.cpu().pin_memory()
+    gw_host = torch.empty(N, dtype=torch.float32).pin_memory()
+    gt_host = torch.zeros(5, dtype=torch.float64)
+    loss_host = torch.zeros(1, dtype=torch.float64)
+    ctx.gradient(tgt_host, omega=om_host, loss=loss_host, grad_omega=gw_host, grad_theta=gt_host)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.gradient(tgt_host, omega=om_host, loss=loss_host, grad_omega=gw_host, grad_theta=gt_host)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    e2e_ms = max(e0.elapsed_time(e1), wall * 1e3)
+    t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = world * n * args.steps / (float(t.item()) / 1e3)
+    ctx.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel category
+    alg = algorithmic_bytes(n, N, M)
+    cats = {k: v for k, v in prof.items() if k in alg}
+    dom = max(cats, key=lambda k: cats[k][0])
+    dom_ms, dom_launches = cats[dom]
+    dom_bytes = alg[dom] * args.steps
+    peak, peak_kind = _peaks()
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    traffic = _ncu_traffic(dom)
+    launches_total = int(sum(v[1] for v in prof.values()))
+    step_bytes = sum(alg.values()) / n
+    out = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_eval, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{npc}^3 particles, {nm}^3 mesh, {box:g} Mpc/h, {n} KDK steps a=1/64->1, "
+                               "ZA ICs, density MSE, reverse-time adjoint; one bench step = one gradient "
+                               "evaluation", "batch": 1, "ckpt_every": 0,
+                   "l2": "inputs larger than L2 (every mesh pass streams 4.3-8.6 GB)",
+                   "parallelism": f"replicas x{world}", "ms_per_pm_step": ms_per_eval / n},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
+                     "traffic": traffic, "launches": dom_launches},
+        "step_roofline": {"algorithmic_GB_per_pm_step": step_bytes / 1e9,
+                          "achieved_GBs": step_bytes / (ms_per_eval / n / 1e3) / 1e9,
+                          "frac": step_bytes / (ms_per_eval / n / 1e3) / 1e9 / peak},
+        "kernels_ms_per_eval": {k: v[0] / args.steps for k, v in prof.items()},
+        "gpu_launches": launches_total,
+        "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": 4 * (N + M),
+                "d2h_bytes_per_step": 4 * N + 8 * 5 + 8},
+        "clocks": clk,
+        "loss": loss_val,
+    }
+    if not args.no_cpu_baseline:
+        times = oracle_sample_seconds(3)
+        t = float(np.mean(times))
+        out["cpu_baseline"] = {"value": 1.0 / (t * SAMPLE_SCALE), "unit": "steps/s", "cores": 1, "kind": "oracle",
+                               "sample": SAMPLE_TEXT + "; mean of 3 samples, %.2f s each" % t}
+    print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def _ncu_traffic(kernel):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if it
+    covers the current kernel build (profiles/ncu_traffic.json), else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d.get(kernel)
+    except (OSError, ValueError):
+        return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

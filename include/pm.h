@@ -111,6 +111,47 @@ int pm_loss_mse(pm_ctx* ctx, const void* target, double* loss_out, void* dJ_dden
 int pm_adjoint(pm_ctx* ctx, const void* dJ_ddens, const void* dJ_ddisp, const void* dJ_dmom,
                void* dJ_domega, double* dJ_dtheta);
 
+/*
+ * Replace the inputs of a context without reallocating: theta (host, [batch][5], optional:
+ * the host tables are recomputed) and/or omega (host or device, [batch][n_ptcl^3],
+ * optional, copied on the context stream).  Invalidates the forward state.
+ */
+int pm_set_inputs(pm_ctx* ctx, const double* theta, const void* omega);
+
+/*
+ * One gradient evaluation of the density MSE objective with host or device buffers:
+ * omega (optional, new white noise) and target ([batch][n_mesh^3]) are copied in,
+ * then pm_forward, pm_loss_mse and pm_adjoint run on the context stream, and
+ *   loss       : optional [batch] doubles (host or device)
+ *   grad_omega : optional [batch][n_ptcl^3] (host or device)
+ *   grad_theta : optional [batch][5] doubles (host or device)
+ * are copied out.  Synchronises when any output is in host memory.  The first call
+ * allocates the context's target, cotangent and gradient buffers.
+ */
+int pm_gradient(pm_ctx* ctx, const void* omega, const void* target, double* loss, void* grad_omega,
+                double* grad_theta);
+
+/* Per-category timing of the context's kernel launches with CUDA events on its stream. */
+enum {
+  PM_PROF_SCATTER = 0,   /* CIC scatter (density, and pi in the adjoint)        */
+  PM_PROF_X_R2C = 1,     /* x pass of the R2C FFT (fixed-point -> spectrum)      */
+  PM_PROF_COLS = 2,      /* y column passes (forward and inverse)                */
+  PM_PROF_Z_FORCE = 3,   /* fused z FFT + Green's function -ik G + inverse z     */
+  PM_PROF_Z_ADJ = 4,     /* fused z FFT + adjoint Green's function + inverse z   */
+  PM_PROF_X_C2R = 5,     /* x pass of the C2R FFT                                */
+  PM_PROF_GATHER_FWD = 6,/* CIC force gather + kick + drift                      */
+  PM_PROF_GATHER_ADJ = 7,/* CIC gather of a and alpha + reverse kicks and drift   */
+  PM_PROF_OTHER = 8,     /* initial conditions, loss, reductions, IC adjoint       */
+  PM_PROF_NCAT = 9
+};
+/* enable != 0 starts event timing (and clears the accumulators); 0 stops it.  Kernel
+ * launch counts are kept either way. */
+int pm_profile(pm_ctx* ctx, int enable);
+/* Synchronises the stream; writes the milliseconds (events on) and kernel launch counts
+ * per category accumulated since the last read into ms[PM_PROF_NCAT] and
+ * launches[PM_PROF_NCAT] (either may be null), then clears them. */
+int pm_profile_read(pm_ctx* ctx, double* ms, long long* launches);
+
 /* Release the context and all its device memory (synchronises its stream). */
 int pm_destroy(pm_ctx* ctx);
 

@@ -56,6 +56,7 @@ using namespace pmgb;
 
 struct pm_ctx {
   EngineBase* eng;
+  pm_config cfg;
 };
 
 extern "C" {
@@ -73,7 +74,7 @@ int pm_init(pm_ctx** out, const pm_config* cfg, const double* theta, const void*
     return PM_ERR_OOM;
   }
   if (r != PM_OK) return r;
-  *out = new pm_ctx{e};
+  *out = new pm_ctx{e, *cfg};
   return PM_OK;
 }
 
@@ -91,6 +92,32 @@ int pm_adjoint(pm_ctx* ctx, const void* dJ_ddens, const void* dJ_ddisp, const vo
                double* dJ_dtheta) {
   if (!ctx) return PM_ERR_ARG;
   return ctx->eng->adjoint(dJ_ddens, dJ_ddisp, dJ_dmom, dJ_domega, dJ_dtheta);
+}
+
+int pm_set_inputs(pm_ctx* ctx, const double* theta, const void* omega) {
+  if (!ctx) return PM_ERR_ARG;
+  if (theta) {
+    pm_config c = ctx->cfg;
+    const int v = validate(&c, theta);
+    if (v != PM_OK) return v;
+  }
+  return ctx->eng->set_inputs(theta, omega);
+}
+
+int pm_gradient(pm_ctx* ctx, const void* omega, const void* target, double* loss, void* grad_omega,
+                double* grad_theta) {
+  if (!ctx || !target) return PM_ERR_ARG;
+  return ctx->eng->gradient(omega, target, loss, grad_omega, grad_theta);
+}
+
+int pm_profile(pm_ctx* ctx, int enable) {
+  if (!ctx) return PM_ERR_ARG;
+  return ctx->eng->profile(enable);
+}
+
+int pm_profile_read(pm_ctx* ctx, double* ms, long long* launches) {
+  if (!ctx) return PM_ERR_ARG;
+  return ctx->eng->profile_read(ms, launches);
 }
 
 int pm_destroy(pm_ctx* ctx) {

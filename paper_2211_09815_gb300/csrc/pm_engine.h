@@ -16,6 +16,10 @@ struct EngineBase {
   virtual int op_fft(int dir, const void* in, void* out) = 0;
   virtual int op_za(void* s1) = 0;
   virtual long long scratch_bytes() const = 0;
+  virtual int profile(int enable) = 0;
+  virtual int profile_read(double* ms, long long* launches) = 0;
+  virtual int set_inputs(const double* theta, const void* omega) = 0;
+  virtual int gradient(const void* omega, const void* target, double* loss, void* grad_omega, double* grad_theta) = 0;
 };
 
 // Creates the engine for cfg->precision; returns a status and sets *out on success.

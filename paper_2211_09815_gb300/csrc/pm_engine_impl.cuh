@@ -26,6 +26,62 @@ namespace pmgb {
 
 static inline int ilog2(long long v) { int r = 0; while ((1LL << r) < v) ++r; return r; }
 
+// Optional per-category CUDA-event timing of the engine's launches on its stream, and a
+// count of the kernels it launched.
+enum ProfCat { P_SCATTER = 0, P_X_R2C, P_COLS, P_Z_FORCE, P_Z_ADJ, P_X_C2R, P_GATHER_FWD, P_GATHER_ADJ, P_OTHER, P_NCAT };
+
+struct Prof {
+  bool on = false;
+  struct Rec { int cat; cudaEvent_t a, b; };
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<Rec> recs;
+  double ms[P_NCAT] = {};
+  long long launches[P_NCAT] = {};
+  cudaEvent_t cur = nullptr;
+  cudaEvent_t get() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  void begin(cudaStream_t st, int cat, int nk) {
+    launches[cat] += nk;
+    if (!on) return;
+    cur = get();
+    cudaEventRecord(cur, st);
+  }
+  void end(cudaStream_t st, int cat) {
+    if (!on) return;
+    cudaEvent_t b = get();
+    cudaEventRecord(b, st);
+    recs.push_back(Rec{cat, cur, b});
+  }
+  int read(cudaStream_t st, double* ms_out, long long* n_out) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return PM_ERR_CUDA;
+    for (const Rec& r : recs) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, r.a, r.b);
+      ms[r.cat] += t;
+    }
+    recs.clear();
+    used = 0;
+    for (int c = 0; c < P_NCAT; ++c) {
+      if (ms_out) ms_out[c] = ms[c];
+      if (n_out) n_out[c] = launches[c];
+      ms[c] = 0.0;
+      launches[c] = 0;
+    }
+    return PM_OK;
+  }
+  ~Prof() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
 template <typename T>
 class Engine : public EngineBase {
  public:
@@ -37,6 +93,13 @@ class Engine : public EngineBase {
   }
 
   long long scratch_bytes() const override { return bytes_; }
+
+  int profile(int enable) override {
+    PMGB_RET(prof_.read(st_, nullptr, nullptr));
+    prof_.on = enable != 0;
+    return PM_OK;
+  }
+  int profile_read(double* ms, long long* launches) override { return prof_.read(st_, ms, launches); }
 
   int init(const pm_config* cfg, const double* theta, const void* omega, cudaStream_t st) {
     cfg_ = *cfg;
@@ -85,7 +148,9 @@ class Engine : public EngineBase {
 
   // ------------------------------------------------------------------ forward
   int forward(void* disp, void* mom, void* dens) override {
+    prof_.begin(st_, P_OTHER, 12);
     PMGB_RET(initial_conditions());
+    prof_.end(st_, P_OTHER);
     for (int j = 0; j <= n_; ++j) {
       PMGB_RET(force_chain(s_, nullptr, j == n_));
       T* cks = nullptr;
@@ -96,8 +161,10 @@ class Engine : public EngineBase {
       }
       const long long fis = 2 * spec_len_cx(nm_);
       StepCoef<T> sc{fkA_, fkB_, fdr_};
+      prof_.begin(st_, P_GATHER_FWD, 1);
       k_gather_fwd<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(
           geo_, s_, p_, j == n_ ? a_ : nullptr, rmesh(1), rmesh(2), rmesh(3), fis, sc, j, n_ + 1, cks, ckp);
+      prof_.end(st_, P_GATHER_FWD);
       PMGB_CK(cudaGetLastError());
     }
     if (disp) PMGB_CK(cudaMemcpyAsync(disp, s_, sizeof(T) * B_ * 3 * N_, cudaMemcpyDeviceToDevice, st_));
@@ -107,16 +174,22 @@ class Engine : public EngineBase {
     return PM_OK;
   }
 
-  int loss_mse(const void* target, double* loss, void* djdd) override {
+  int loss_mse_dev(const void* target, void* djdd) {
     if (!have_fwd_) return PM_ERR_STATE;
+    prof_.begin(st_, P_OTHER, 2);
     k_mse<T><<<dim3(Gm_, B_), kPtclThreads, 0, st_>>>(dens_, (const T*)target, (T*)djdd, M_, part_);
     PMGB_CK(cudaGetLastError());
-    k_sum_partials<<<B_, 256, 0, st_>>>(part_, Gm_, scal_);
+    k_sum_partials<<<B_, 256, 0, st_>>>(part_, Gm_, scal_, 1.0 / (double)M_);
+    prof_.end(st_, P_OTHER);
     PMGB_CK(cudaGetLastError());
+    return PM_OK;
+  }
+
+  int loss_mse(const void* target, double* loss, void* djdd) override {
+    PMGB_RET(loss_mse_dev(target, djdd));
     if (loss) {
-      const double inv = 1.0 / (double)M_;
-      // scale in a second tiny pass: loss = sum / M
-      PMGB_RET(scale_copy(scal_, inv, loss, B_));
+      PMGB_CK(cudaMemcpyAsync(loss, scal_, sizeof(double) * B_, cudaMemcpyDefault, st_));
+      if (is_host(loss)) PMGB_CK(cudaStreamSynchronize(st_));
     }
     return PM_OK;
   }
@@ -125,8 +198,10 @@ class Engine : public EngineBase {
   int adjoint(const void* djdd, const void* djdx, const void* djdp, void* djdw, double* djdth) override {
     if (!have_fwd_) return PM_ERR_STATE;
     PMGB_CK(cudaMemsetAsync(pimax_, 0, sizeof(unsigned) * 3 * B_, st_));
+    prof_.begin(st_, P_OTHER, 1);
     k_adjoint_init<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, mass_, s_, (const T*)djdd, (const T*)djdx,
                                                               (const T*)djdp, xi_, pi_, pimax_);
+    prof_.end(st_, P_OTHER);
     PMGB_CK(cudaGetLastError());
     const long long fis = 2 * spec_len_cx(nm_);
     for (int j = n_; j >= 0; --j) {
@@ -141,13 +216,16 @@ class Engine : public EngineBase {
       StepCoef<T> sc{rkA_, rkB_, rdr_};
       double* ppa = part_ + (long long)(2 * j) * B_ * G_;
       double* pxp = part_ + (long long)(2 * j + 1) * B_ * G_;
+      prof_.begin(st_, P_GATHER_ADJ, 1);
       k_gather_adj<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(
           geo_, mass_, s_, p_, xi_, pi_, nullptr, nullptr, rmesh(1), rmesh(2), rmesh(3), rmesh(0), fis, sc, j,
           n_ + 1, ckp, cks, ppa, pxp, pimax_);
+      prof_.end(st_, P_GATHER_ADJ);
       PMGB_CK(cudaGetLastError());
     }
     // per-step sums: part_[(2j+q)][b][G] -> steps_[(2j+q)][b]
-    k_sum_partials<<<2 * (n_ + 1) * B_, 256, 0, st_>>>(part_, G_, steps_);
+    prof_.begin(st_, P_OTHER, 15);
+    k_sum_partials<<<2 * (n_ + 1) * B_, 256, 0, st_>>>(part_, G_, steps_, 1.0);
     PMGB_CK(cudaGetLastError());
     PMGB_RET(ic_adjoint(djdw));
     // theta
@@ -165,6 +243,7 @@ class Engine : public EngineBase {
     in.batch = B_;
     in.step_stride = 2 * B_;
     k_final_theta<<<(B_ + 31) / 32, 32, 0, st_>>>(in, theta_out_);
+    prof_.end(st_, P_OTHER);
     PMGB_CK(cudaGetLastError());
     if (djdth) {
       PMGB_CK(cudaMemcpyAsync(djdth, theta_out_, sizeof(double) * 5 * B_, cudaMemcpyDefault, st_));
@@ -226,6 +305,38 @@ class Engine : public EngineBase {
     return PM_OK;
   }
 
+  // New theta (host, [batch][5]) and/or omega (host or device): tables are recomputed on
+  // the host and copied into the existing device buffers.
+  int set_inputs(const double* theta, const void* omega) override {
+    if (theta) PMGB_RET(tables(theta));
+    if (omega) PMGB_CK(cudaMemcpyAsync(omega_, omega, sizeof(T) * B_ * N_, cudaMemcpyDefault, st_));
+    have_fwd_ = false;
+    return PM_OK;
+  }
+
+  // One gradient evaluation with host or device buffers: omega in, target in, forward,
+  // MSE loss, adjoint, loss / grad_omega / grad_theta out.  Host outputs synchronise.
+  int gradient(const void* omega, const void* target, double* loss, void* grad_omega, double* grad_theta) override {
+    if (!tgt_) {
+      PMGB_RET(alloc(&tgt_, (long long)B_ * M_));
+      PMGB_RET(alloc(&djdd_, (long long)B_ * M_));
+      PMGB_RET(alloc(&gw_, (long long)B_ * N_));
+    }
+    if (omega) PMGB_CK(cudaMemcpyAsync(omega_, omega, sizeof(T) * B_ * N_, cudaMemcpyDefault, st_));
+    PMGB_CK(cudaMemcpyAsync(tgt_, target, sizeof(T) * B_ * M_, cudaMemcpyDefault, st_));
+    PMGB_RET(forward(nullptr, nullptr, nullptr));
+    PMGB_RET(loss_mse_dev(tgt_, djdd_));
+    PMGB_RET(adjoint(djdd_, nullptr, nullptr, gw_, nullptr));
+    if (loss) {
+      PMGB_CK(cudaMemcpyAsync(loss, scal_, sizeof(double) * B_, cudaMemcpyDefault, st_));
+    }
+    if (grad_omega) PMGB_CK(cudaMemcpyAsync(grad_omega, gw_, sizeof(T) * B_ * N_, cudaMemcpyDefault, st_));
+    if (grad_theta) PMGB_CK(cudaMemcpyAsync(grad_theta, theta_out_, sizeof(double) * 5 * B_, cudaMemcpyDefault, st_));
+    if ((loss && is_host(loss)) || (grad_omega && is_host(grad_omega)) || (grad_theta && is_host(grad_theta)))
+      PMGB_CK(cudaStreamSynchronize(st_));
+    return PM_OK;
+  }
+
   int op_za(void* s1) override {
     have_fwd_ = false;
     PMGB_RET(initial_conditions());
@@ -251,15 +362,6 @@ class Engine : public EngineBase {
   }
   // real view of spectrum buffer q (after C2R)
   T* rmesh(int q) { return reinterpret_cast<T*>(spec_[q]); }
-
-  int scale_copy(const double* src, double f, double* dst, int count) {
-    std::vector<double> h(count);
-    PMGB_CK(cudaMemcpyAsync(h.data(), src, sizeof(double) * count, cudaMemcpyDeviceToHost, st_));
-    PMGB_CK(cudaStreamSynchronize(st_));
-    for (double& v : h) v *= f;
-    PMGB_CK(cudaMemcpy(dst, h.data(), sizeof(double) * count, cudaMemcpyDefault));
-    return PM_OK;
-  }
 
   // ---------------------------------------------------------------- host tables
   int tables(const double* theta) {
@@ -345,6 +447,7 @@ class Engine : public EngineBase {
         tw[L + m].y = (T)std::sin(ang);
       }
     PMGB_RET(upload(&tw_, tw));
+    if (pimax_) return PM_OK;
     PMGB_RET(alloc(&pimax_, 3 * B_));
     PMGB_RET(alloc(&e_pi_, 3 * B_));
     PMGB_RET(alloc(&part_, (long long)(2 * (n_ + 1) + 16) * B_ * kMaxRedBlocks));
@@ -354,7 +457,7 @@ class Engine : public EngineBase {
     return PM_OK;
   }
   template <typename U> int upload(U** d, const std::vector<U>& h) {
-    PMGB_RET(alloc(d, (long long)h.size()));
+    if (!*d) PMGB_RET(alloc(d, (long long)h.size()));
     PMGB_CK(cudaMemcpyAsync(*d, h.data(), sizeof(U) * h.size(), cudaMemcpyHostToDevice, st_));
     PMGB_CK(cudaStreamSynchronize(st_));
     return PM_OK;
@@ -412,15 +515,21 @@ class Engine : public EngineBase {
 
   int scatter(const T* s, const T* pi) {
     if (pi) {
+      prof_.begin(st_, P_OTHER, 1);
       k_pi_exponents<<<1, 64, 0, st_>>>(pimax_, e_pi_, 3 * B_, lgN_);
+      prof_.end(st_, P_OTHER);
       PMGB_CK(cudaGetLastError());
       PMGB_CK(cudaMemsetAsync(pimax_, 0, sizeof(unsigned) * 3 * B_, st_));
+      prof_.begin(st_, P_SCATTER, 1);
       k_scatter<T, 4><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(
           geo_, s, pi, (unsigned long long*)acc_[0], (unsigned long long*)acc_[1], (unsigned long long*)acc_[2],
           (unsigned long long*)acc_[3], e_d_, e_pi_);
+      prof_.end(st_, P_SCATTER);
     } else {
+      prof_.begin(st_, P_SCATTER, 1);
       k_scatter<T, 1><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, s, nullptr, (unsigned long long*)acc_[0],
                                                               nullptr, nullptr, nullptr, e_d_, nullptr);
+      prof_.end(st_, P_SCATTER);
     }
     PMGB_CK(cudaGetLastError());
     return PM_OK;
@@ -432,8 +541,10 @@ class Engine : public EngineBase {
   int force_chain(const T* s, const T* pi, bool keep_density) {
     PMGB_RET(scatter(s, pi));
     if (keep_density) {
+      prof_.begin(st_, P_OTHER, 1);
       k_density_out<T><<<1024, 256, 0, st_>>>((const long long*)acc_[0], dens_, (long long)B_ * M_,
                                               (T)ldexp((double)mass_, -e_d_));
+      prof_.end(st_, P_OTHER);
       PMGB_CK(cudaGetLastError());
     }
     const int nb = pi ? 4 : 1;
@@ -441,10 +552,14 @@ class Engine : public EngineBase {
     job.b[0] = RowBuf<T>{acc_[0], M_, spec_[0], nullptr, e_d_, mass_, (T)-1, 1};
     for (int c = 0; c < 3 && pi; ++c)
       job.b[1 + c] = RowBuf<T>{acc_[1 + c], M_, spec_[4 + c], e_pi_ + c * B_, 0, (T)1, (T)0, 1};
+    prof_.begin(st_, P_X_R2C, 1);
     PMGB_RET(fft_x_r2c<T>(nm_, job, nb, B_ * nm_ * nm_, true, tw_, st_));
+    prof_.end(st_, P_X_R2C);
     PMGB_CK(cudaGetLastError());
     C* fwdb[4] = {spec_[0], spec_[4], spec_[5], spec_[6]};
+    prof_.begin(st_, P_COLS, 2);
     PMGB_RET(cols(nm_, -1, false, fwdb, nb));
+    prof_.end(st_, P_COLS);
     ZJob<T> zf{};
     zf.in[0] = spec_[0];
     zf.out[0] = spec_[1];
@@ -453,7 +568,9 @@ class Engine : public EngineBase {
     zf.coef = gcoef_;
     zf.dtab = dtab_;
     zf.batch = B_;
+    prof_.begin(st_, P_Z_FORCE, 1);
     PMGB_RET(fft_fused_z<T>(nm_, zf, false, tw_, st_));
+    prof_.end(st_, P_Z_FORCE);
     PMGB_CK(cudaGetLastError());
     if (pi) {
       ZJob<T> za = zf;
@@ -461,14 +578,20 @@ class Engine : public EngineBase {
       za.in[1] = spec_[5];
       za.in[2] = spec_[6];
       za.out[0] = spec_[0];
+      prof_.begin(st_, P_Z_ADJ, 1);
       PMGB_RET(fft_fused_z<T>(nm_, za, true, tw_, st_));
+      prof_.end(st_, P_Z_ADJ);
       PMGB_CK(cudaGetLastError());
     }
     C* invb[4] = {spec_[1], spec_[2], spec_[3], spec_[0]};
+    prof_.begin(st_, P_COLS, 2);
     PMGB_RET(cols(nm_, +1, false, invb, nb == 4 ? 4 : 3));
+    prof_.end(st_, P_COLS);
     RowJob<T> jc{};
     for (int q = 0; q < (pi ? 4 : 3); ++q) jc.b[q] = RowBuf<T>{invb[q], 2 * spec_len_cx(nm_), invb[q], nullptr, 0, (T)1, (T)0, 0};
+    prof_.begin(st_, P_X_C2R, 1);
     PMGB_RET(fft_x_c2r<T>(nm_, jc, pi ? 4 : 3, B_ * nm_ * nm_, tw_, st_));
+    prof_.end(st_, P_X_C2R);
     PMGB_CK(cudaGetLastError());
     return PM_OK;
   }
@@ -513,7 +636,7 @@ class Engine : public EngineBase {
     k_ic_adj_prep<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(xi_, pi_, s1_, N_, d1_, gd_, rmesh(1), rmesh(2),
                                                              rmesh(3), 2 * lis, part_, part_ + (long long)B_ * G_);
     PMGB_CK(cudaGetLastError());
-    k_sum_partials<<<2 * B_, 256, 0, st_>>>(part_, G_, scal_ + 2 * B_);
+    k_sum_partials<<<2 * B_, 256, 0, st_>>>(part_, G_, scal_ + 2 * B_, 1.0);
     PMGB_CK(cudaGetLastError());
     // 3 R2C of sbar (in place: real input in the same buffer) and the R2C of omega
     RowJob<T> job{};
@@ -527,7 +650,7 @@ class Engine : public EngineBase {
     k_za_adj_mul<T><<<dim3(Gz_, B_), kPtclThreads, 0, st_>>>(spec_[1], spec_[2], spec_[3], spec_[0], spec_[5], np_,
                                                              amp_, hdl_, maxn2_, inv_kfp_, lis, part_);
     PMGB_CK(cudaGetLastError());
-    k_sum_partials<<<5 * B_, 256, 0, st_>>>(part_, Gz_, scal_ + 4 * B_);
+    k_sum_partials<<<5 * B_, 256, 0, st_>>>(part_, Gz_, scal_ + 4 * B_, 1.0);
     PMGB_CK(cudaGetLastError());
     C* ob[1] = {spec_[5]};
     PMGB_RET(cols(np_, +1, true, ob, 1));
@@ -546,6 +669,7 @@ class Engine : public EngineBase {
   T mass_ = 1, inv_kfp_ = 1;
   Geo<T> geo_{};
   std::vector<void*> allocs_;
+  T *tgt_ = nullptr, *djdd_ = nullptr, *gw_ = nullptr;
   T *s_ = nullptr, *p_ = nullptr, *a_ = nullptr, *xi_ = nullptr, *pi_ = nullptr, *s1_ = nullptr, *omega_ = nullptr;
   long long* acc_[4] = {nullptr, nullptr, nullptr, nullptr};
   C* spec_[7] = {};
@@ -560,6 +684,7 @@ class Engine : public EngineBase {
   int* e_pi_ = nullptr;
   double *part_ = nullptr, *steps_ = nullptr, *scal_ = nullptr, *theta_out_ = nullptr;
   bool have_fwd_ = false;
+  Prof prof_;
 };
 
 template <typename T>

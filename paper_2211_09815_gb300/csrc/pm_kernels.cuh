@@ -486,13 +486,13 @@ k_ic_adj_prep(const T* __restrict__ xi, const T* __restrict__ pi, const T* __res
 }
 
 // Fixed-order sum of `count` partials for each instance: out[b] = sum_i part[b][i]
-static __global__ void k_sum_partials(const double* __restrict__ part, int count, double* out) {
+static __global__ void k_sum_partials(const double* __restrict__ part, int count, double* out, double scale) {
   __shared__ double shd[8];
   const int b = blockIdx.x;
   double acc = 0.0;
   for (int i = threadIdx.x; i < count; i += blockDim.x) acc += part[(long long)b * count + i];
   const double r = block_sum(acc, shd);
-  if (threadIdx.x == 0) out[b] = r;
+  if (threadIdx.x == 0) out[b] = r * scale;
 }
 
 // dJ/dtheta (Eq. 51): time-stepping terms (Omega_m only), initial-condition growth terms

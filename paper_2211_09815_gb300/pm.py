@@ -16,7 +16,9 @@ STATUS = {0: "PM_OK", 1: "PM_ERR_ARG", 2: "PM_ERR_OOM", 3: "PM_ERR_CUDA", 4: "PM
           5: "PM_ERR_OVERFLOW", 6: "PM_ERR_TIMEOUT", 7: "PM_ERR_STATE"}
 SYMBOLS = ("pm_init", "pm_forward", "pm_loss_mse", "pm_adjoint", "pm_destroy", "pm_status_string",
            "pm_last_cuda_error", "pm_scratch_bytes", "pm_op_density", "pm_op_force", "pm_op_force_vjp",
-           "pm_op_fft", "pm_op_za")
+           "pm_op_fft", "pm_op_za", "pm_set_inputs", "pm_gradient", "pm_profile", "pm_profile_read")
+PROF_NAMES = ("scatter", "fft_x_r2c", "fft_cols", "fused_z_force", "fused_z_adjoint", "fft_x_c2r",
+              "gather_fwd", "gather_adj", "other")
 
 
 class PMLibraryError(RuntimeError):
@@ -63,6 +65,10 @@ def load_library(path=LIB_PATH):
     lib.pm_op_force_vjp.argtypes = [vp, vp, vp, vp, vp]
     lib.pm_op_fft.argtypes = [vp, i, vp, vp]
     lib.pm_op_za.argtypes = [vp, vp]
+    lib.pm_set_inputs.argtypes = [vp, dp, vp]
+    lib.pm_gradient.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.pm_profile.argtypes = [vp, i]
+    lib.pm_profile_read.argtypes = [vp, vp, vp]
     for name in SYMBOLS:
         getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
     _lib = lib
@@ -172,6 +178,33 @@ class PMContext:
 
     def op_za(self, s1):
         _check(load_library().pm_op_za(self._h, _ptr(s1, self.dtype, 3 * self.batch * self.N)), "pm_op_za")
+
+    def set_inputs(self, theta=None, omega=None):
+        """theta: host [batch][5] or None; omega: host (pinned) or CUDA tensor or None."""
+        lib = load_library()
+        arr = None
+        if theta is not None:
+            th = [float(v) for row in (theta if hasattr(theta[0], "__len__") else [theta]) for v in row]
+            arr = (ctypes.c_double * len(th))(*th)
+        om = ctypes.c_void_p(omega.data_ptr()) if omega is not None else None
+        _check(lib.pm_set_inputs(self._h, arr, om), "pm_set_inputs")
+
+    def gradient(self, target, omega=None, loss=None, grad_omega=None, grad_theta=None):
+        """All arguments are torch tensors on the host (pinned) or the device."""
+        def p(t):
+            return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        _check(load_library().pm_gradient(self._h, p(omega), p(target), p(loss), p(grad_omega), p(grad_theta)),
+               "pm_gradient")
+
+    def profile(self, enable=True):
+        _check(load_library().pm_profile(self._h, int(enable)), "pm_profile")
+
+    def profile_read(self):
+        """{category: (milliseconds, kernel launches)} accumulated since the last read."""
+        ms = (ctypes.c_double * len(PROF_NAMES))()
+        n = (ctypes.c_longlong * len(PROF_NAMES))()
+        _check(load_library().pm_profile_read(self._h, ms, n), "pm_profile_read")
+        return {name: (ms[i], n[i]) for i, name in enumerate(PROF_NAMES)}
 
     @property
     def scratch_bytes(self):
