@@ -321,6 +321,30 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_op_case(args):
+    """One pm_op_force and one pm_op_force_vjp call on the chosen workload: every kernel of
+    the forward and adjoint force chains launched once or twice, for ncu captures."""
+    import torch
+    from paper_2211_09815_gb300 import build, inputs, pm
+    build.build()
+    box, nm, npc, n = WORKLOADS[args.workload]
+    N = npc ** 3
+    om = torch.from_numpy(inputs.white_noise(npc, 1)).to("cuda")
+    ctx = pm.PMContext(box, nm, npc, n, [THETA], om)
+    s1 = torch.empty(3 * N, device="cuda")
+    ctx.op_za(s1)
+    disp = s1 * 40.0     # a clustered, late-time-like displacement field
+    pi = torch.ones(3 * N, device="cuda") * 1e-3
+    acc = torch.empty(3 * N, device="cuda")
+    alpha = torch.empty(3 * N, device="cuda")
+    ctx.op_force(disp, acc)
+    ctx.op_force_vjp(disp, pi, acc, alpha)
+    torch.cuda.synchronize()
+    ctx.close()
+    print(json.dumps({"op_case": args.workload, "acc_rms": float(acc.pow(2).mean().sqrt()),
+                      "alpha_rms": float(alpha.pow(2).mean().sqrt())}))
+
+
 def _ncu_traffic(kernel):
     """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if it
     covers the current kernel build (profiles/ncu_traffic.json), else None."""
@@ -343,11 +367,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--op-case", action="store_true",
+                    help="run one force and one force-VJP operator call (no timing), for profilers")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
-    if args.impl == "reference":
+    if args.op_case:
+        run_op_case(args)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_ours(args, rank, world, local_rank)
