@@ -190,6 +190,37 @@ int pm_op_fft(pm_ctx* ctx, int dir, const void* in, void* out);
  * s1_out: [batch][3][n_ptcl^3]. */
 int pm_op_za(pm_ctx* ctx, void* s1_out);
 
+/* ------------------------------------------------------------------------------------
+ * Allocation-free entry point.  The paper has no counterpart: this is a service for
+ * callers that cannot call cudaMalloc -- code whose device memory belongs entirely to its
+ * own pool allocator (a framework's caching allocator, a server with a fixed memory
+ * budget), where a foreign allocation fails or fragments the pool, and loops that must
+ * not pay for cudaMalloc/cudaFree, which can synchronise the device.
+ * ----------------------------------------------------------------------------------*/
+
+/* Largest mesh (cells) pm_density_noalloc accepts: 128^3.  Its int64 accumulator is a
+ * fixed 16 MiB array in the library's device memory, held by every GPU that loads the
+ * library until the process exits. */
+#define PM_NOALLOC_MAX_CELLS (128LL * 128 * 128)
+
+/*
+ * CIC overdensity delta = rho - 1 of particles at x = q + disp (the same deterministic
+ * int64 fixed-point deposit as pm_op_density, FP32 only, one instance), using no device
+ * allocation and no context.
+ *   box      : periodic box side in Mpc/h
+ *   n_mesh   : mesh nodes per side, power of two, n_mesh^3 <= PM_NOALLOC_MAX_CELLS
+ *   n_ptcl   : particles per side, power of two >= 4, dividing n_mesh
+ *   disp     : device, float [3][n_ptcl^3] displacements (caller-owned)
+ *   dens_out : device, float [n_mesh^3] (caller-owned)
+ *   stream   : a cudaStream_t (0 = legacy default stream)
+ * Returns PM_ERR_ARG for bad sizes, including n_mesh^3 > PM_NOALLOC_MAX_CELLS (use
+ * pm_op_density with a context for larger meshes).  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress, with that device current); make that
+ * first call before any stream capture.  Every call clears and reuses the same array, so
+ * calls that overlap on one GPU race with each other: serialise them (one stream).
+ */
+int pm_density_noalloc(double box, int n_mesh, int n_ptcl, const float* disp, float* dens_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

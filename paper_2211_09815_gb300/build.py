@@ -16,7 +16,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libpmgb.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["pm_api.cu", "engine_f32.cu", "engine_f64.cu", "fft_f32.cu", "fft_f64.cu"]
+CU_SOURCES = ["pm_api.cu", "engine_f32.cu", "engine_f64.cu", "fft_f32.cu", "fft_f64.cu", "noalloc.cu"]
 CPP_SOURCES = ["cosmo.cpp"]
 
 

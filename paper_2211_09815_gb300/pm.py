@@ -16,7 +16,9 @@ STATUS = {0: "PM_OK", 1: "PM_ERR_ARG", 2: "PM_ERR_OOM", 3: "PM_ERR_CUDA", 4: "PM
           5: "PM_ERR_OVERFLOW", 6: "PM_ERR_TIMEOUT", 7: "PM_ERR_STATE"}
 SYMBOLS = ("pm_init", "pm_forward", "pm_loss_mse", "pm_adjoint", "pm_destroy", "pm_status_string",
            "pm_last_cuda_error", "pm_scratch_bytes", "pm_op_density", "pm_op_force", "pm_op_force_vjp",
-           "pm_op_fft", "pm_op_za", "pm_set_inputs", "pm_gradient", "pm_profile", "pm_profile_read")
+           "pm_op_fft", "pm_op_za", "pm_set_inputs", "pm_gradient", "pm_profile", "pm_profile_read",
+           "pm_density_noalloc")
+NOALLOC_MAX_CELLS = 128 ** 3
 PROF_NAMES = ("scatter", "fft_x_r2c", "fft_cols", "fused_z_force", "fused_z_adjoint", "fft_x_c2r",
               "gather_fwd", "gather_adj", "other")
 
@@ -69,6 +71,7 @@ def load_library(path=LIB_PATH):
     lib.pm_gradient.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.pm_profile.argtypes = [vp, i]
     lib.pm_profile_read.argtypes = [vp, vp, vp]
+    lib.pm_density_noalloc.argtypes = [ctypes.c_double, i, i, vp, vp, vp]
     for name in SYMBOLS:
         getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
     _lib = lib
@@ -94,6 +97,21 @@ def _ptr(t, dtype=None, numel=None, name="tensor"):
     if numel is not None and t.numel() != numel:
         raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def density_noalloc(box, n_mesh, n_ptcl, disp, dens_out, stream=None):
+    """CIC overdensity with no device allocation (pm_density_noalloc), for callers that
+    cannot call cudaMalloc; float32 only, n_mesh**3 <= NOALLOC_MAX_CELLS.  The library
+    reuses one fixed device array for every call: do not run two calls concurrently on
+    one GPU."""
+    import torch
+    if n_mesh ** 3 > NOALLOC_MAX_CELLS:
+        raise ValueError(f"n_mesh**3 = {n_mesh ** 3} exceeds the allocation-free limit {NOALLOC_MAX_CELLS}")
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(load_library().pm_density_noalloc(float(box), int(n_mesh), int(n_ptcl),
+                                             _ptr(disp, torch.float32, 3 * n_ptcl ** 3, "disp"),
+                                             _ptr(dens_out, torch.float32, n_mesh ** 3, "dens_out"),
+                                             ctypes.c_void_p(st.cuda_stream)), "pm_density_noalloc")
 
 
 class PMContext:
