@@ -81,11 +81,17 @@ __device__ __forceinline__ C twiddle(const C* __restrict__ w, int m) {
 }
 
 // ---------------------------------------------------------------- tile accessors
+// Shared-memory row of tile element (row, c): one padding row is inserted after every 16
+// rows, so that the rows 16 apart that the first radix-16 stage stores in one warp
+// instruction fall into different halves of the 32 banks.
+__host__ __device__ constexpr int skew_rows(int rows) { return rows + (rows >> 4); }
+__device__ __forceinline__ int srow(int row) { return row + (row >> 4); }
+
 template <typename C, int LD>
 struct SmemTile {
   C* p;
-  __device__ __forceinline__ C ld(int row, int c) const { return p[row * LD + c]; }
-  __device__ __forceinline__ void st(int row, int c, C v) const { p[row * LD + c] = v; }
+  __device__ __forceinline__ C ld(int row, int c) const { return p[srow(row) * LD + c]; }
+  __device__ __forceinline__ void st(int row, int c, C v) const { p[srow(row) * LD + c] = v; }
 };
 
 // one sequence per thread in global memory: element `row` at p[row * es]
@@ -156,18 +162,21 @@ __device__ __forceinline__ void fft_tile(const Src& src, const Mid& mid, const D
   }
 }
 
-// Tile shapes.  Column passes: TC sequences of length L in one tile of <= 64 KiB,
+// Tile shapes.  Column passes: TC sequences of length L in one tile of <= BYTES,
 // NT = TC * L / RMAX threads (each thread holds RMAX values), NT <= 512.
-template <typename T, int L> struct ColTile {
+template <typename T, int L, int BYTES = 65536> struct ColTile {
   static constexpr int RMAX = Plan<L>::RMAX;
-  static constexpr int TC0 = 65536 / (L * (int)sizeof(cx_t<T>));
+  static constexpr int TC0 = BYTES / (L * (int)sizeof(cx_t<T>));
   static constexpr int TC1 = TC0 > 256 ? 256 : TC0;
   static constexpr int TCMAXNT = 512 * RMAX / L;
   static constexpr int TC2 = TC1 < TCMAXNT ? TC1 : TCMAXNT;
   static constexpr int TC = TC2 < 1 ? 1 : TC2;
   static constexpr int NT = TC * L / RMAX;
   static constexpr int LD = TC;
+  static constexpr int SMEM = skew_rows(L) * LD * (int)sizeof(cx_t<T>);
 };
+// Fused z passes keep two tiles; half-size tiles leave room for several blocks per SM.
+template <typename T, int L> using FusedTile = ColTile<T, L, 32768>;
 // Row passes (x axis): TR rows of L = n/2 complex values, tile padded to LD = TR + 1 so
 // that the transposing row loads do not collide in shared-memory banks.
 template <typename T, int L> struct RowTile {
@@ -180,6 +189,7 @@ template <typename T, int L> struct RowTile {
   static constexpr int NT = TR * L / RMAX;
   static_assert(NT >= 32, "row tile needs at least one warp");
   static constexpr int LD = TR + 1;
+  static constexpr int SMEM = skew_rows(L) * LD * (int)sizeof(cx_t<T>);
 };
 
 }  // namespace pmgb

@@ -22,7 +22,7 @@ __device__ __forceinline__ long long seq_base(const SeqMap& m, int s) {
 }
 
 template <typename T, int L, int DIR>
-__global__ void __launch_bounds__(ColTile<T, L>::NT)
+__global__ void __launch_bounds__(ColTile<T, L>::NT, 2)
 k_fft_cols(const SeqMap mm, const SeqMap ms, int ntiles_main, ColBufs<T> bufs,
            const cx_t<T>* __restrict__ tw) {
   using C = cx_t<T>;
@@ -46,35 +46,53 @@ k_fft_cols(const SeqMap mm, const SeqMap ms, int ntiles_main, ColBufs<T> bufs,
 // or a real mesh.
 template <typename T, int L, bool FIXED>
 __global__ void __launch_bounds__(RowTile<T, L>::NT)
-k_fft_x_r2c(RowJob<T> job, int nrows, const cx_t<T>* __restrict__ twL, const cx_t<T>* __restrict__ twN) {
+k_fft_x_r2c(RowJob<T> job, int nrows, int nbuf, const cx_t<T>* __restrict__ twL,
+            const cx_t<T>* __restrict__ twN) {
   using C = cx_t<T>;
   using TL = RowTile<T, L>;
   constexpr int N = 2 * L;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
-  const RowBuf<T>& rb = job.b[blockIdx.y];
-  const int r0 = blockIdx.x * TL::TR;
+  // the buffers of one row tile are neighbouring blocks, so that interleaved fixed-point
+  // accumulators (several quantities per 32-byte sector) are read while still in L2
+  const RowBuf<T>& rb = job.b[blockIdx.x % nbuf];
+  const int r0 = (blockIdx.x / nbuf) * TL::TR;
   const long long rows_per_inst = (long long)N * N;
+  // all rows of a tile belong to one instance (TR divides N^2)
+  const int inst0 = (int)(min((long long)r0, (long long)nrows - 1) / rows_per_inst);
+  T mul = (T)1, add = (T)0;
+  if constexpr (FIXED) {
+    const int e = rb.exps ? rb.exps[inst0] : rb.exp_host;
+    mul = (T)ldexp((double)rb.mul, -e);
+    add = rb.add;
+  }
   // load + convert, transposing into [L][LD]
   for (int idx = threadIdx.x; idx < TL::TR * L; idx += TL::NT) {
     const int row = idx / L, j = idx % L;
     const int grow = r0 + row;
     C v = cmake<C>(0, 0);
     if (grow < nrows) {
-      const int inst = (int)(grow / rows_per_inst);
-      const long long off = inst * rb.real_is + (grow % rows_per_inst) * N + 2 * j;
+      const long long off = inst0 * rb.real_is + (grow % rows_per_inst) * N + 2 * j;
       if constexpr (FIXED) {
-        long long* acc = reinterpret_cast<long long*>(rb.real) + off;
-        const longlong2 a = *reinterpret_cast<longlong2*>(acc);
-        const int e = rb.exps ? rb.exps[inst] : rb.exp_host;
-        const T mul = (T)ldexp((double)rb.mul, -e);
-        v = cmake<C>((T)a.x * mul + rb.add, (T)a.y * mul + rb.add);
-        if (rb.zero) *reinterpret_cast<longlong2*>(acc) = make_longlong2(0, 0);
+        if (rb.qstride == 1) {
+          long long* acc = reinterpret_cast<long long*>(rb.real) + off;
+          const longlong2 a = *reinterpret_cast<longlong2*>(acc);
+          v = cmake<C>((T)a.x * mul + add, (T)a.y * mul + add);
+          if (rb.zero) *reinterpret_cast<longlong2*>(acc) = make_longlong2(0, 0);
+        } else {
+          long long* acc = reinterpret_cast<long long*>(rb.real) + off * rb.qstride;
+          const long long a0 = acc[0], a1 = acc[rb.qstride];
+          v = cmake<C>((T)a0 * mul + add, (T)a1 * mul + add);
+          if (rb.zero) {
+            acc[0] = 0;
+            acc[rb.qstride] = 0;
+          }
+        }
       } else {
         v = *reinterpret_cast<const C*>(reinterpret_cast<const T*>(rb.real) + off);
       }
     }
-    sm[j * TL::LD + row] = v;
+    sm[srow(j) * TL::LD + row] = v;
   }
   __syncthreads();
   SmemTile<C, TL::LD> t{sm};
@@ -88,13 +106,13 @@ k_fft_x_r2c(RowJob<T> job, int nrows, const cx_t<T>* __restrict__ twL, const cx_
     const int inst = (int)(grow / rows_per_inst);
     C* out = rb.spec + inst * spec_len_cx(N) + (grow % rows_per_inst) * L;
     C* side = rb.spec + inst * spec_len_cx(N) + spec_main_len(N) + (grow % rows_per_inst);
-    const C zk = sm[k * TL::LD + row];
+    const C zk = sm[srow(k) * TL::LD + row];
     if (k == 0) {
       out[0] = cmake<C>(zk.x + zk.y, (T)0);
       *side = cmake<C>(zk.x - zk.y, (T)0);
       continue;
     }
-    const C zm = sm[(L - k) * TL::LD + row];
+    const C zm = sm[srow(L - k) * TL::LD + row];
     const T h = (T)0.5;
     const C e = cscale(cadd(zk, cconj(zm)), h);
     const C d = cscale(csub(zk, cconj(zm)), h);
@@ -140,8 +158,8 @@ k_fft_x_c2r(RowJob<T> job, int nrows, const cx_t<T>* __restrict__ twL, const cx_
         zm = cadd(cconj(e), cmul_i(cconj(o)));
       }
     }
-    sm[k * TL::LD + row] = zk;
-    if (k != 0 && k != L - k) sm[(L - k) * TL::LD + row] = zm;
+    sm[srow(k) * TL::LD + row] = zk;
+    if (k != 0 && k != L - k) sm[srow(L - k) * TL::LD + row] = zm;
   }
   __syncthreads();
   SmemTile<C, TL::LD> t{sm};
@@ -153,7 +171,7 @@ k_fft_x_c2r(RowJob<T> job, int nrows, const cx_t<T>* __restrict__ twL, const cx_
     if (grow >= nrows) continue;
     const int inst = (int)(grow / rows_per_inst);
     T* out = reinterpret_cast<T*>(rb.real) + inst * rb.real_is + (grow % rows_per_inst) * N + 2 * j;
-    *reinterpret_cast<C*>(out) = sm[j * TL::LD + row];
+    *reinterpret_cast<C*>(out) = sm[srow(j) * TL::LD + row];
   }
 }
 
@@ -219,7 +237,7 @@ struct MulSrc {
   int comp;
   __device__ __forceinline__ cx_t<T> ld(int row, int c) const {
     using C = cx_t<T>;
-    const C v = p[row * LD + c];
+    const C v = p[srow(row) * LD + c];
     const int f0 = freq_of(row, gs.n);
     const T s = (T)gs.fc(comp, f0) * gs.g(f0);
     return cmake<C>(v.y * s, -v.x * s);
@@ -237,7 +255,7 @@ struct AccDst {
     const int f0 = freq_of(row, gs.n);
     const T s = (T)gs.fc(comp, f0) * gs.g(f0);
     const C m = cmake<C>(-v.y * s, v.x * s);
-    C* q = p + row * LD + c;
+    C* q = p + srow(row) * LD + c;
     *q = comp == 0 ? m : cadd(*q, m);
   }
 };
@@ -257,11 +275,11 @@ __device__ __forceinline__ GreenSeq<T> green_seq(const ZSeq& q, const T* coef, c
 
 // Forward force: delta^ (after x, y) --z FFT--> * (-i k_c G) --z IFFT--> F_c (c = 0..2)
 template <typename T, int L>
-__global__ void __launch_bounds__(ColTile<T, L>::NT)
+__global__ void __launch_bounds__(FusedTile<T, L>::NT, 2)
 k_fused_z_force(ZJob<T> job, int ntiles_main, const cx_t<T>* __restrict__ tw) {
   using C = cx_t<T>;
-  using TL = ColTile<T, L>;
-  constexpr int TILE = L * TL::LD;
+  using TL = FusedTile<T, L>;
+  constexpr int TILE = skew_rows(L) * TL::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* A = reinterpret_cast<C*>(smem_raw);
   C* B = A + TILE;
@@ -285,11 +303,11 @@ k_fused_z_force(ZJob<T> job, int ntiles_main, const cx_t<T>* __restrict__ tw) {
 
 // Adjoint: P_c^ (after x, y) --z FFT--> sum_c conj(-i k_c G) P_c --z IFFT--> psi
 template <typename T, int L>
-__global__ void __launch_bounds__(ColTile<T, L>::NT)
+__global__ void __launch_bounds__(FusedTile<T, L>::NT, 2)
 k_fused_z_adjoint(ZJob<T> job, int ntiles_main, const cx_t<T>* __restrict__ tw) {
   using C = cx_t<T>;
-  using TL = ColTile<T, L>;
-  constexpr int TILE = L * TL::LD;
+  using TL = FusedTile<T, L>;
+  constexpr int TILE = skew_rows(L) * TL::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* A = reinterpret_cast<C*>(smem_raw);
   C* B = A + TILE;
@@ -323,7 +341,7 @@ static void launch_cols_L(const SeqMap& mm, const SeqMap& ms, const ColBufs<T>& 
   using TL = ColTile<T, L>;
   const int ntm = (mm.nseq + TL::TC - 1) / TL::TC;
   const int nts = ms.nseq > 0 ? (ms.nseq + TL::TC - 1) / TL::TC : 0;
-  const size_t sm = (size_t)L * TL::LD * sizeof(cx_t<T>);
+  const size_t sm = TL::SMEM;
   auto fn = k_fft_cols<T, L, DIR>;
   set_smem<T, L>((const void*)fn, sm);
   dim3 grid(ntm + nts, nbuf);
@@ -334,23 +352,23 @@ template <typename T, int L>
 static void launch_r2c_L(const RowJob<T>& job, int nbuf, int nrows, bool fixed, const cx_t<T>* tw,
                          cudaStream_t st) {
   using TL = RowTile<T, L>;
-  const size_t sm = (size_t)L * TL::LD * sizeof(cx_t<T>);
-  dim3 grid((nrows + TL::TR - 1) / TL::TR, nbuf);
+  const size_t sm = TL::SMEM;
+  dim3 grid(((nrows + TL::TR - 1) / TL::TR) * nbuf, 1);
   if (fixed) {
     auto fn = k_fft_x_r2c<T, L, true>;
     set_smem<T, L>((const void*)fn, sm);
-    fn<<<grid, TL::NT, sm, st>>>(job, nrows, tw + L, tw + 2 * L);
+    fn<<<grid, TL::NT, sm, st>>>(job, nrows, nbuf, tw + L, tw + 2 * L);
   } else {
     auto fn = k_fft_x_r2c<T, L, false>;
     set_smem<T, L>((const void*)fn, sm);
-    fn<<<grid, TL::NT, sm, st>>>(job, nrows, tw + L, tw + 2 * L);
+    fn<<<grid, TL::NT, sm, st>>>(job, nrows, nbuf, tw + L, tw + 2 * L);
   }
 }
 
 template <typename T, int L>
 static void launch_c2r_L(const RowJob<T>& job, int nbuf, int nrows, const cx_t<T>* tw, cudaStream_t st) {
   using TL = RowTile<T, L>;
-  const size_t sm = (size_t)L * TL::LD * sizeof(cx_t<T>);
+  const size_t sm = TL::SMEM;
   dim3 grid((nrows + TL::TR - 1) / TL::TR, nbuf);
   auto fn = k_fft_x_c2r<T, L>;
   set_smem<T, L>((const void*)fn, sm);
@@ -359,10 +377,10 @@ static void launch_c2r_L(const RowJob<T>& job, int nbuf, int nrows, const cx_t<T
 
 template <typename T, int L>
 static void launch_fused_L(const ZJob<T>& job, bool adjoint, const cx_t<T>* tw, cudaStream_t st) {
-  using TL = ColTile<T, L>;
+  using TL = FusedTile<T, L>;
   const int ntm = (job.batch * L * (L / 2) + TL::TC - 1) / TL::TC;
   const int nts = (job.batch * L + TL::TC - 1) / TL::TC;
-  const size_t sm = 2 * (size_t)L * TL::LD * sizeof(cx_t<T>);
+  const size_t sm = 2 * (size_t)TL::SMEM;
   if (adjoint) {
     auto fn = k_fused_z_adjoint<T, L>;
     set_smem<T, L>((const void*)fn, sm);

@@ -79,8 +79,7 @@ extern "C" int pm_density_noalloc(double box, int n_mesh, int n_ptcl, const floa
   cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * M, st);
   if (e != cudaSuccess) { set_cuda_error(e); return PM_ERR_CUDA; }
   const int grid = (int)std::min<long long>((N + kPtclThreads - 1) / kPtclThreads, kMaxRedBlocks);
-  k_scatter<float, 1><<<dim3(grid, 1), kPtclThreads, 0, st>>>(g, disp, nullptr, acc, nullptr, nullptr, nullptr, e_d,
-                                                              nullptr);
+  k_scatter<float, 1><<<dim3(grid, 1), kPtclThreads, 0, st>>>(g, disp, nullptr, acc, e_d, nullptr);
   k_density_out<float><<<1024, 256, 0, st>>>((const long long*)acc, dens_out, M,
                                               (float)ldexp((double)M / (double)N, -e_d));
   e = cudaGetLastError();

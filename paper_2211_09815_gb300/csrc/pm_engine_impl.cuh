@@ -132,7 +132,10 @@ class Engine : public EngineBase {
     PMGB_RET(alloc(&pi_, pv));
     PMGB_RET(alloc(&s1_, pv));
     PMGB_RET(alloc(&omega_, (long long)B_ * N_));
-    for (int q = 0; q < 4; ++q) PMGB_RET(alloc(&acc_[q], (long long)B_ * M_));
+    // one int64 array of [B][M][4] (density, pi_x, pi_y, pi_z interleaved per cell) for the
+    // adjoint scatter; the forward density scatter uses its first B*M elements as [B][M]
+    PMGB_RET(alloc(&accq_, (long long)4 * B_ * M_));
+    acc_[0] = accq_;
     for (int q = 0; q < 7; ++q) PMGB_RET(alloc(&spec_[q], sl));
     PMGB_RET(alloc(&dens_, (long long)B_ * M_));
     if (cfg->ckpt_every > 0) {
@@ -140,7 +143,7 @@ class Engine : public EngineBase {
       PMGB_RET(alloc(&ck_s_, pv * nck_));
       PMGB_RET(alloc(&ck_p_, pv * nck_));
     }
-    for (int q = 0; q < 4; ++q) PMGB_CK(cudaMemsetAsync(acc_[q], 0, sizeof(long long) * B_ * M_, st_));
+    PMGB_CK(cudaMemsetAsync(accq_, 0, sizeof(long long) * 4 * B_ * M_, st_));
     PMGB_CK(cudaMemcpyAsync(omega_, omega, sizeof(T) * B_ * N_, cudaMemcpyDeviceToDevice, st_));
     PMGB_RET(tables(theta));
     return PM_OK;
@@ -495,7 +498,7 @@ class Engine : public EngineBase {
   }
   int r2c_real(int n, const T* in, long long in_is, C* out) {
     RowJob<T> job{};
-    job.b[0] = RowBuf<T>{(void*)in, in_is, out, nullptr, 0, (T)1, (T)0, 0};
+    job.b[0] = RowBuf<T>{(void*)in, in_is, out, nullptr, 0, (T)1, (T)0, 0, 1};
     PMGB_RET(fft_x_r2c<T>(n, job, 1, B_ * n * n, false, tw_, st_));
     C* bufs[1] = {out};
     PMGB_RET(cols(n, -1, false, bufs, 1));
@@ -507,7 +510,7 @@ class Engine : public EngineBase {
     PMGB_RET(cols(n, +1, true, bufs, 1));
     PMGB_RET(cols(n, +1, false, bufs, 1));
     RowJob<T> job{};
-    job.b[0] = RowBuf<T>{(void*)out, out_is, in, nullptr, 0, (T)1, (T)0, 0};
+    job.b[0] = RowBuf<T>{(void*)out, out_is, in, nullptr, 0, (T)1, (T)0, 0, 1};
     PMGB_RET(fft_x_c2r<T>(n, job, 1, B_ * n * n, tw_, st_));
     PMGB_CK(cudaGetLastError());
     return PM_OK;
@@ -521,14 +524,13 @@ class Engine : public EngineBase {
       PMGB_CK(cudaGetLastError());
       PMGB_CK(cudaMemsetAsync(pimax_, 0, sizeof(unsigned) * 3 * B_, st_));
       prof_.begin(st_, P_SCATTER, 1);
-      k_scatter<T, 4><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(
-          geo_, s, pi, (unsigned long long*)acc_[0], (unsigned long long*)acc_[1], (unsigned long long*)acc_[2],
-          (unsigned long long*)acc_[3], e_d_, e_pi_);
+      k_scatter<T, 4><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, s, pi, (unsigned long long*)accq_, e_d_,
+                                                              e_pi_);
       prof_.end(st_, P_SCATTER);
     } else {
       prof_.begin(st_, P_SCATTER, 1);
       k_scatter<T, 1><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, s, nullptr, (unsigned long long*)acc_[0],
-                                                              nullptr, nullptr, nullptr, e_d_, nullptr);
+                                                              e_d_, nullptr);
       prof_.end(st_, P_SCATTER);
     }
     PMGB_CK(cudaGetLastError());
@@ -549,9 +551,13 @@ class Engine : public EngineBase {
     }
     const int nb = pi ? 4 : 1;
     RowJob<T> job{};
-    job.b[0] = RowBuf<T>{acc_[0], M_, spec_[0], nullptr, e_d_, mass_, (T)-1, 1};
-    for (int c = 0; c < 3 && pi; ++c)
-      job.b[1 + c] = RowBuf<T>{acc_[1 + c], M_, spec_[4 + c], e_pi_ + c * B_, 0, (T)1, (T)0, 1};
+    if (!pi) {
+      job.b[0] = RowBuf<T>{acc_[0], M_, spec_[0], nullptr, e_d_, mass_, (T)-1, 1, 1};
+    } else {
+      job.b[0] = RowBuf<T>{accq_, M_, spec_[0], nullptr, e_d_, mass_, (T)-1, 1, 4};
+      for (int c = 0; c < 3; ++c)
+        job.b[1 + c] = RowBuf<T>{accq_ + 1 + c, M_, spec_[4 + c], e_pi_ + c * B_, 0, (T)1, (T)0, 1, 4};
+    }
     prof_.begin(st_, P_X_R2C, 1);
     PMGB_RET(fft_x_r2c<T>(nm_, job, nb, B_ * nm_ * nm_, true, tw_, st_));
     prof_.end(st_, P_X_R2C);
@@ -588,7 +594,7 @@ class Engine : public EngineBase {
     PMGB_RET(cols(nm_, +1, false, invb, nb == 4 ? 4 : 3));
     prof_.end(st_, P_COLS);
     RowJob<T> jc{};
-    for (int q = 0; q < (pi ? 4 : 3); ++q) jc.b[q] = RowBuf<T>{invb[q], 2 * spec_len_cx(nm_), invb[q], nullptr, 0, (T)1, (T)0, 0};
+    for (int q = 0; q < (pi ? 4 : 3); ++q) jc.b[q] = RowBuf<T>{invb[q], 2 * spec_len_cx(nm_), invb[q], nullptr, 0, (T)1, (T)0, 0, 1};
     prof_.begin(st_, P_X_C2R, 1);
     PMGB_RET(fft_x_c2r<T>(nm_, jc, pi ? 4 : 3, B_ * nm_ * nm_, tw_, st_));
     prof_.end(st_, P_X_C2R);
@@ -612,7 +618,7 @@ class Engine : public EngineBase {
   }
   int lattice_r2c(const T* in, long long in_is, C* out) {
     RowJob<T> job{};
-    job.b[0] = RowBuf<T>{(void*)in, in_is, out, nullptr, 0, (T)1, (T)0, 0};
+    job.b[0] = RowBuf<T>{(void*)in, in_is, out, nullptr, 0, (T)1, (T)0, 0, 1};
     PMGB_RET(fft_x_r2c<T>(np_, job, 1, B_ * np_ * np_, false, tw_, st_));
     C* bufs[1] = {out};
     PMGB_RET(cols(np_, -1, false, bufs, 1));
@@ -623,7 +629,7 @@ class Engine : public EngineBase {
     PMGB_RET(cols(np_, +1, true, bufs, nb));
     PMGB_RET(cols(np_, +1, false, bufs, nb));
     RowJob<T> jc{};
-    for (int q = 0; q < nb; ++q) jc.b[q] = RowBuf<T>{bufs[q], 2 * spec_len_cx(np_), bufs[q], nullptr, 0, (T)1, (T)0, 0};
+    for (int q = 0; q < nb; ++q) jc.b[q] = RowBuf<T>{bufs[q], 2 * spec_len_cx(np_), bufs[q], nullptr, 0, (T)1, (T)0, 0, 1};
     PMGB_RET(fft_x_c2r<T>(np_, jc, nb, B_ * np_ * np_, tw_, st_));
     PMGB_CK(cudaGetLastError());
     return PM_OK;
@@ -640,8 +646,8 @@ class Engine : public EngineBase {
     PMGB_CK(cudaGetLastError());
     // 3 R2C of sbar (in place: real input in the same buffer) and the R2C of omega
     RowJob<T> job{};
-    for (int c = 0; c < 3; ++c) job.b[c] = RowBuf<T>{rmesh(1 + c), 2 * lis, spec_[1 + c], nullptr, 0, (T)1, (T)0, 0};
-    job.b[3] = RowBuf<T>{omega_, N_, spec_[0], nullptr, 0, (T)1, (T)0, 0};
+    for (int c = 0; c < 3; ++c) job.b[c] = RowBuf<T>{rmesh(1 + c), 2 * lis, spec_[1 + c], nullptr, 0, (T)1, (T)0, 0, 1};
+    job.b[3] = RowBuf<T>{omega_, N_, spec_[0], nullptr, 0, (T)1, (T)0, 0, 1};
     PMGB_RET(fft_x_r2c<T>(np_, job, 4, B_ * np_ * np_, false, tw_, st_));
     PMGB_CK(cudaGetLastError());
     C* bufs[4] = {spec_[1], spec_[2], spec_[3], spec_[0]};
@@ -656,7 +662,7 @@ class Engine : public EngineBase {
     PMGB_RET(cols(np_, +1, true, ob, 1));
     PMGB_RET(cols(np_, +1, false, ob, 1));
     RowJob<T> jc{};
-    jc.b[0] = RowBuf<T>{djdw ? djdw : (void*)rmesh(5), djdw ? N_ : 2 * lis, spec_[5], nullptr, 0, (T)1, (T)0, 0};
+    jc.b[0] = RowBuf<T>{djdw ? djdw : (void*)rmesh(5), djdw ? N_ : 2 * lis, spec_[5], nullptr, 0, (T)1, (T)0, 0, 1};
     PMGB_RET(fft_x_c2r<T>(np_, jc, 1, B_ * np_ * np_, tw_, st_));
     PMGB_CK(cudaGetLastError());
     return PM_OK;
@@ -671,7 +677,8 @@ class Engine : public EngineBase {
   std::vector<void*> allocs_;
   T *tgt_ = nullptr, *djdd_ = nullptr, *gw_ = nullptr;
   T *s_ = nullptr, *p_ = nullptr, *a_ = nullptr, *xi_ = nullptr, *pi_ = nullptr, *s1_ = nullptr, *omega_ = nullptr;
-  long long* acc_[4] = {nullptr, nullptr, nullptr, nullptr};
+  long long* acc_[1] = {nullptr};
+  long long* accq_ = nullptr;
   C* spec_[7] = {};
   T* dens_ = nullptr;
   T *ck_s_ = nullptr, *ck_p_ = nullptr;

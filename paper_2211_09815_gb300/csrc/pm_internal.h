@@ -31,6 +31,7 @@ template <typename T> struct RowBuf {
   int exp_host;         // exponent when exps is null
   T mul, add;           // value = acc * 2^-e * mul + add
   int zero;             // zero the accumulator after reading
+  int qstride;          // fixed point: int64 elements between consecutive cells (1 or 4)
 };
 template <typename T> struct RowJob { RowBuf<T> b[4]; };
 

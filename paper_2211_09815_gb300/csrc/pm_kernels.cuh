@@ -86,11 +86,11 @@ template <> __device__ __forceinline__ float abs_up<float>(float v) { return fab
 template <> __device__ __forceinline__ float abs_up<double>(double v) { return __double2float_ru(fabs(v)); }
 
 // ------------------------------------------------------------------------- scatter
-// acc[0] += W * 2^e_d (weights), and with NQ = 4 also acc[1 + c] += pi_c * W * 2^e_c.
+// NQ = 1: acc[cell] += W * 2^e_d (weights).  NQ = 4: acc is [cell][4] and receives the
+// weight and pi_c * W * 2^e_c (c = 0..2) in one 32-byte sector per cell.
 template <typename T, int NQ>
 __global__ void __launch_bounds__(kPtclThreads)
-k_scatter(Geo<T> g, const T* __restrict__ s, const T* __restrict__ pi, unsigned long long* acc0,
-          unsigned long long* acc1, unsigned long long* acc2, unsigned long long* acc3, int e_d,
+k_scatter(Geo<T> g, const T* __restrict__ s, const T* __restrict__ pi, unsigned long long* acc, int e_d,
           const int* __restrict__ e_pi) {
   const int b = blockIdx.y;
   const T* sb = s + (long long)b * 3 * g.N;
@@ -119,11 +119,14 @@ k_scatter(Geo<T> g, const T* __restrict__ s, const T* __restrict__ pi, unsigned 
     for (int d = 0; d < 8; ++d) {
       const T w = ((d & 4) ? t[0] : (T)1 - t[0]) * ((d & 2) ? t[1] : (T)1 - t[1]) * ((d & 1) ? t[2] : (T)1 - t[2]);
       const long long idx = mo + corner_index(g, cell, d);
-      atomicAdd(acc0 + idx, (unsigned long long)to_fixed<T>(w * sd));
-      if constexpr (NQ == 4) {
-        atomicAdd(acc1 + idx, (unsigned long long)to_fixed<T>(pv[0] * w));
-        atomicAdd(acc2 + idx, (unsigned long long)to_fixed<T>(pv[1] * w));
-        atomicAdd(acc3 + idx, (unsigned long long)to_fixed<T>(pv[2] * w));
+      if constexpr (NQ == 1) {
+        atomicAdd(acc + idx, (unsigned long long)to_fixed<T>(w * sd));
+      } else {
+        unsigned long long* q = acc + 4 * idx;
+        atomicAdd(q, (unsigned long long)to_fixed<T>(w * sd));
+        atomicAdd(q + 1, (unsigned long long)to_fixed<T>(pv[0] * w));
+        atomicAdd(q + 2, (unsigned long long)to_fixed<T>(pv[1] * w));
+        atomicAdd(q + 3, (unsigned long long)to_fixed<T>(pv[2] * w));
       }
     }
   }
