@@ -175,8 +175,8 @@ template <typename T, int L, int BYTES = 65536> struct ColTile {
   static constexpr int LD = TC;
   static constexpr int SMEM = skew_rows(L) * LD * (int)sizeof(cx_t<T>);
 };
-// Fused z passes keep two tiles; half-size tiles leave room for several blocks per SM.
-template <typename T, int L> using FusedTile = ColTile<T, L, 32768>;
+// Fused z passes keep two tiles of the column-pass shape.
+template <typename T, int L> using FusedTile = ColTile<T, L, 65536>;
 // Row passes (x axis): TR rows of L = n/2 complex values, tile padded to LD = TR + 1 so
 // that the transposing row loads do not collide in shared-memory banks.
 template <typename T, int L> struct RowTile {

@@ -41,58 +41,80 @@ k_fft_cols(const SeqMap mm, const SeqMap ms, int ntiles_main, ColBufs<T> bufs,
 }
 
 // ---------------------------------------------------------------- x pass, R2C
-// rows of n = 2L reals -> L complex (main) + 1 (side).  Input is either an int64
-// fixed-point accumulator (converted with value = acc * 2^-e * mul + add, then zeroed)
-// or a real mesh.
-template <typename T, int L, bool FIXED>
+// int64 fixed point -> real without the FP64 pipe (slow on this part): split into the
+// signed high and unsigned low 32-bit words and recombine with one FP32 fma.
+template <typename T> __device__ __forceinline__ T fix2real(long long a);
+template <> __device__ __forceinline__ float fix2real<float>(long long a) {
+  return __fmaf_rn((float)(int)(a >> 32), 4294967296.0f, (float)(unsigned)a);
+}
+template <> __device__ __forceinline__ double fix2real<double>(long long a) { return (double)a; }
+
+// rows of n = 2L reals -> L complex (main) + 1 (side).  The input is an int64 fixed-point
+// accumulator (value = acc * 2^-e * mul + add, zeroed after reading) or a real mesh.
+// Q = 1: one quantity per block; the tile holds TR rows.  Q = 4: the accumulator is
+// [cell][4] (four quantities per 32-byte sector) and one block converts all four for
+// TR/4 rows, so every sector is read and zeroed whole; tile sequence c = q * (TR/4) + row.
+template <typename T, int L, bool FIXED, int Q>
 __global__ void __launch_bounds__(RowTile<T, L>::NT)
 k_fft_x_r2c(RowJob<T> job, int nrows, int nbuf, const cx_t<T>* __restrict__ twL,
             const cx_t<T>* __restrict__ twN) {
   using C = cx_t<T>;
   using TL = RowTile<T, L>;
   constexpr int N = 2 * L;
+  constexpr int RT = TL::TR / Q;   // rows per tile
+  static_assert(RT * Q == TL::TR && RT >= 1, "row tile must split into Q quantities");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
-  // the buffers of one row tile are neighbouring blocks, so that interleaved fixed-point
-  // accumulators (several quantities per 32-byte sector) are read while still in L2
-  const RowBuf<T>& rb = job.b[blockIdx.x % nbuf];
-  const int r0 = (blockIdx.x / nbuf) * TL::TR;
+  // Q = 1: the buffers of one row tile are neighbouring blocks
+  const int qb = Q == 1 ? blockIdx.x % nbuf : 0;
+  const int r0 = (Q == 1 ? blockIdx.x / nbuf : blockIdx.x) * RT;
   const long long rows_per_inst = (long long)N * N;
-  // all rows of a tile belong to one instance (TR divides N^2)
+  // all rows of a tile belong to one instance (RT divides N^2)
   const int inst0 = (int)(min((long long)r0, (long long)nrows - 1) / rows_per_inst);
-  T mul = (T)1, add = (T)0;
-  if constexpr (FIXED) {
-    const int e = rb.exps ? rb.exps[inst0] : rb.exp_host;
-    mul = (T)ldexp((double)rb.mul, -e);
-    add = rb.add;
+  T mul[Q], add[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const RowBuf<T>& rb = job.b[Q == 1 ? qb : q];
+    mul[q] = (T)1;
+    add[q] = (T)0;
+    if constexpr (FIXED) {
+      const int e = rb.exps ? rb.exps[inst0] : rb.exp_host;
+      mul[q] = (T)ldexp((double)rb.mul, -e);
+      add[q] = rb.add;
+    }
   }
+  const RowBuf<T>& rb0 = job.b[qb];
   // load + convert, transposing into [L][LD]
-  for (int idx = threadIdx.x; idx < TL::TR * L; idx += TL::NT) {
+  for (int idx = threadIdx.x; idx < RT * L; idx += TL::NT) {
     const int row = idx / L, j = idx % L;
     const int grow = r0 + row;
-    C v = cmake<C>(0, 0);
+    C v[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) v[q] = cmake<C>(0, 0);
     if (grow < nrows) {
-      const long long off = inst0 * rb.real_is + (grow % rows_per_inst) * N + 2 * j;
-      if constexpr (FIXED) {
-        if (rb.qstride == 1) {
-          long long* acc = reinterpret_cast<long long*>(rb.real) + off;
-          const longlong2 a = *reinterpret_cast<longlong2*>(acc);
-          v = cmake<C>((T)a.x * mul + add, (T)a.y * mul + add);
-          if (rb.zero) *reinterpret_cast<longlong2*>(acc) = make_longlong2(0, 0);
-        } else {
-          long long* acc = reinterpret_cast<long long*>(rb.real) + off * rb.qstride;
-          const long long a0 = acc[0], a1 = acc[rb.qstride];
-          v = cmake<C>((T)a0 * mul + add, (T)a1 * mul + add);
-          if (rb.zero) {
-            acc[0] = 0;
-            acc[rb.qstride] = 0;
-          }
+      const long long off = inst0 * rb0.real_is + (grow % rows_per_inst) * N + 2 * j;
+      if constexpr (FIXED && Q == 1) {
+        long long* acc = reinterpret_cast<long long*>(rb0.real) + off;
+        const longlong2 a = *reinterpret_cast<longlong2*>(acc);
+        v[0] = cmake<C>(fix2real<T>(a.x) * mul[0] + add[0], fix2real<T>(a.y) * mul[0] + add[0]);
+        if (rb0.zero) *reinterpret_cast<longlong2*>(acc) = make_longlong2(0, 0);
+      } else if constexpr (FIXED) {
+        longlong2* acc = reinterpret_cast<longlong2*>(reinterpret_cast<long long*>(rb0.real) + 4 * off);
+        const longlong2 e0 = acc[0], e1 = acc[1], o0 = acc[2], o1 = acc[3];   // cells 2j and 2j+1
+        const long long ev[4] = {e0.x, e0.y, e1.x, e1.y}, od[4] = {o0.x, o0.y, o1.x, o1.y};
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+          v[q] = cmake<C>(fix2real<T>(ev[q]) * mul[q] + add[q], fix2real<T>(od[q]) * mul[q] + add[q]);
+        if (rb0.zero) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc[u] = make_longlong2(0, 0);
         }
       } else {
-        v = *reinterpret_cast<const C*>(reinterpret_cast<const T*>(rb.real) + off);
+        v[0] = *reinterpret_cast<const C*>(reinterpret_cast<const T*>(rb0.real) + off);
       }
     }
-    sm[srow(j) * TL::LD + row] = v;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) sm[srow(j) * TL::LD + q * RT + row] = v[q];
   }
   __syncthreads();
   SmemTile<C, TL::LD> t{sm};
@@ -100,19 +122,20 @@ k_fft_x_r2c(RowJob<T> job, int nrows, int nbuf, const cx_t<T>* __restrict__ twL,
   __syncthreads();
   // even/odd split: X[k] = E[k] + W^k O[k], E = (Z[k] + conj Z[L-k]) / 2, O = -i (Z[k] - conj Z[L-k]) / 2
   for (int idx = threadIdx.x; idx < TL::TR * (L / 2 + 1); idx += TL::NT) {
-    const int row = idx / (L / 2 + 1), k = idx % (L / 2 + 1);
+    const int c = idx / (L / 2 + 1), k = idx % (L / 2 + 1);
+    const int q = c / RT, row = c % RT;
     const int grow = r0 + row;
     if (grow >= nrows) continue;
-    const int inst = (int)(grow / rows_per_inst);
-    C* out = rb.spec + inst * spec_len_cx(N) + (grow % rows_per_inst) * L;
-    C* side = rb.spec + inst * spec_len_cx(N) + spec_main_len(N) + (grow % rows_per_inst);
-    const C zk = sm[srow(k) * TL::LD + row];
+    C* spec = job.b[Q == 1 ? qb : q].spec;
+    C* out = spec + inst0 * spec_len_cx(N) + (grow % rows_per_inst) * L;
+    C* side = spec + inst0 * spec_len_cx(N) + spec_main_len(N) + (grow % rows_per_inst);
+    const C zk = sm[srow(k) * TL::LD + c];
     if (k == 0) {
       out[0] = cmake<C>(zk.x + zk.y, (T)0);
       *side = cmake<C>(zk.x - zk.y, (T)0);
       continue;
     }
-    const C zm = sm[srow(L - k) * TL::LD + row];
+    const C zm = sm[srow(L - k) * TL::LD + c];
     const T h = (T)0.5;
     const C e = cscale(cadd(zk, cconj(zm)), h);
     const C d = cscale(csub(zk, cconj(zm)), h);
@@ -275,7 +298,7 @@ __device__ __forceinline__ GreenSeq<T> green_seq(const ZSeq& q, const T* coef, c
 
 // Forward force: delta^ (after x, y) --z FFT--> * (-i k_c G) --z IFFT--> F_c (c = 0..2)
 template <typename T, int L>
-__global__ void __launch_bounds__(FusedTile<T, L>::NT, 2)
+__global__ void __launch_bounds__(FusedTile<T, L>::NT)
 k_fused_z_force(ZJob<T> job, int ntiles_main, const cx_t<T>* __restrict__ tw) {
   using C = cx_t<T>;
   using TL = FusedTile<T, L>;
@@ -303,7 +326,7 @@ k_fused_z_force(ZJob<T> job, int ntiles_main, const cx_t<T>* __restrict__ tw) {
 
 // Adjoint: P_c^ (after x, y) --z FFT--> sum_c conj(-i k_c G) P_c --z IFFT--> psi
 template <typename T, int L>
-__global__ void __launch_bounds__(FusedTile<T, L>::NT, 2)
+__global__ void __launch_bounds__(FusedTile<T, L>::NT)
 k_fused_z_adjoint(ZJob<T> job, int ntiles_main, const cx_t<T>* __restrict__ tw) {
   using C = cx_t<T>;
   using TL = FusedTile<T, L>;
@@ -353,13 +376,20 @@ static void launch_r2c_L(const RowJob<T>& job, int nbuf, int nrows, bool fixed, 
                          cudaStream_t st) {
   using TL = RowTile<T, L>;
   const size_t sm = TL::SMEM;
+  if (fixed && job.b[0].qstride == 4 && nbuf == 4 && TL::TR % 4 == 0) {
+    auto fn = k_fft_x_r2c<T, L, true, 4>;
+    set_smem<T, L>((const void*)fn, sm);
+    dim3 grid((nrows + TL::TR / 4 - 1) / (TL::TR / 4), 1);
+    fn<<<grid, TL::NT, sm, st>>>(job, nrows, nbuf, tw + L, tw + 2 * L);
+    return;
+  }
   dim3 grid(((nrows + TL::TR - 1) / TL::TR) * nbuf, 1);
   if (fixed) {
-    auto fn = k_fft_x_r2c<T, L, true>;
+    auto fn = k_fft_x_r2c<T, L, true, 1>;
     set_smem<T, L>((const void*)fn, sm);
     fn<<<grid, TL::NT, sm, st>>>(job, nrows, nbuf, tw + L, tw + 2 * L);
   } else {
-    auto fn = k_fft_x_r2c<T, L, false>;
+    auto fn = k_fft_x_r2c<T, L, false, 1>;
     set_smem<T, L>((const void*)fn, sm);
     fn<<<grid, TL::NT, sm, st>>>(job, nrows, nbuf, tw + L, tw + 2 * L);
   }
