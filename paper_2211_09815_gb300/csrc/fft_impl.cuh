@@ -7,6 +7,8 @@
 // The inverse runs z, y, then the x pass (C2R).  Transforms are unnormalised both ways;
 // the 1/n^3 of the inverse is folded into the Fourier multipliers.
 #pragma once
+#include <type_traits>
+
 #include "fft.cuh"
 #include "pm_internal.h"
 
@@ -84,37 +86,68 @@ k_fft_x_r2c(RowJob<T> job, int nrows, int nbuf, const cx_t<T>* __restrict__ twL,
     }
   }
   const RowBuf<T>& rb0 = job.b[qb];
-  // load + convert, transposing into [L][LD]
-  for (int idx = threadIdx.x; idx < RT * L; idx += TL::NT) {
+  // load + convert, transposing into [L][LD]; every load of the thread is issued before
+  // the first conversion so that ITER loads per thread are in flight at once
+  constexpr int ITER = RT * L / TL::NT;
+  static_assert(ITER * TL::NT == RT * L, "row loads must divide evenly");
+  constexpr int W = FIXED ? (Q == 1 ? 2 : 8) : 1;   // int64 words (or one complex) per load unit
+  using Raw = typename std::conditional<FIXED, long long, C>::type;
+  Raw raw[ITER][W];
+  bool ok[ITER];
+#pragma unroll
+  for (int it = 0; it < ITER; ++it) {
+    const int idx = threadIdx.x + it * TL::NT;
     const int row = idx / L, j = idx % L;
     const int grow = r0 + row;
-    C v[Q];
+    ok[it] = grow < nrows;
+    const long long off = inst0 * rb0.real_is + (long long)(ok[it] ? grow % rows_per_inst : 0) * N + 2 * j;
+    if constexpr (FIXED && Q == 1) {
+      const longlong2 a = ok[it] ? *reinterpret_cast<const longlong2*>(reinterpret_cast<long long*>(rb0.real) + off)
+                                 : make_longlong2(0, 0);
+      raw[it][0] = a.x;
+      raw[it][1] = a.y;
+    } else if constexpr (FIXED) {
+      const longlong2* acc = reinterpret_cast<const longlong2*>(reinterpret_cast<long long*>(rb0.real) + 4 * off);
 #pragma unroll
-    for (int q = 0; q < Q; ++q) v[q] = cmake<C>(0, 0);
-    if (grow < nrows) {
-      const long long off = inst0 * rb0.real_is + (grow % rows_per_inst) * N + 2 * j;
-      if constexpr (FIXED && Q == 1) {
-        long long* acc = reinterpret_cast<long long*>(rb0.real) + off;
-        const longlong2 a = *reinterpret_cast<longlong2*>(acc);
-        v[0] = cmake<C>(fix2real<T>(a.x) * mul[0] + add[0], fix2real<T>(a.y) * mul[0] + add[0]);
-        if (rb0.zero) *reinterpret_cast<longlong2*>(acc) = make_longlong2(0, 0);
-      } else if constexpr (FIXED) {
-        longlong2* acc = reinterpret_cast<longlong2*>(reinterpret_cast<long long*>(rb0.real) + 4 * off);
-        const longlong2 e0 = acc[0], e1 = acc[1], o0 = acc[2], o1 = acc[3];   // cells 2j and 2j+1
-        const long long ev[4] = {e0.x, e0.y, e1.x, e1.y}, od[4] = {o0.x, o0.y, o1.x, o1.y};
-#pragma unroll
-        for (int q = 0; q < Q; ++q)
-          v[q] = cmake<C>(fix2real<T>(ev[q]) * mul[q] + add[q], fix2real<T>(od[q]) * mul[q] + add[q]);
-        if (rb0.zero) {
-#pragma unroll
-          for (int u = 0; u < 4; ++u) acc[u] = make_longlong2(0, 0);
-        }
-      } else {
-        v[0] = *reinterpret_cast<const C*>(reinterpret_cast<const T*>(rb0.real) + off);
+      for (int u = 0; u < 4; ++u) {
+        const longlong2 a = ok[it] ? acc[u] : make_longlong2(0, 0);
+        raw[it][2 * u] = a.x;
+        raw[it][2 * u + 1] = a.y;
       }
+    } else {
+      raw[it][0] = ok[it] ? *reinterpret_cast<const C*>(reinterpret_cast<const T*>(rb0.real) + off) : cmake<C>(0, 0);
     }
+  }
+  if (FIXED && rb0.zero) {
 #pragma unroll
-    for (int q = 0; q < Q; ++q) sm[srow(j) * TL::LD + q * RT + row] = v[q];
+    for (int it = 0; it < ITER; ++it) {
+      if (!ok[it]) continue;
+      const int idx = threadIdx.x + it * TL::NT;
+      const int row = idx / L, j = idx % L;
+      const long long off = inst0 * rb0.real_is + ((r0 + row) % rows_per_inst) * N + 2 * j;
+      longlong2* acc = reinterpret_cast<longlong2*>(reinterpret_cast<long long*>(rb0.real) + (Q == 1 ? 1 : 4) * off);
+#pragma unroll
+      for (int u = 0; u < (Q == 1 ? 1 : 4); ++u) acc[u] = make_longlong2(0, 0);
+    }
+  }
+#pragma unroll
+  for (int it = 0; it < ITER; ++it) {
+    const int idx = threadIdx.x + it * TL::NT;
+    const int row = idx / L, j = idx % L;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      C v;
+      if constexpr (FIXED && Q == 1) {
+        v = cmake<C>(fix2real<T>(raw[it][0]) * mul[0] + add[0], fix2real<T>(raw[it][1]) * mul[0] + add[0]);
+      } else if constexpr (FIXED) {
+        // raw holds cell 2j's four quantities, then cell 2j+1's
+        v = cmake<C>(fix2real<T>(raw[it][q]) * mul[q] + add[q], fix2real<T>(raw[it][4 + q]) * mul[q] + add[q]);
+      } else {
+        v = raw[it][0];
+      }
+      if (!ok[it]) v = cmake<C>(0, 0);
+      sm[srow(j) * TL::LD + q * RT + row] = v;
+    }
   }
   __syncthreads();
   SmemTile<C, TL::LD> t{sm};
@@ -160,26 +193,41 @@ k_fft_x_c2r(RowJob<T> job, int nrows, const cx_t<T>* __restrict__ twL, const cx_
   const RowBuf<T>& rb = job.b[blockIdx.y];
   const int r0 = blockIdx.x * TL::TR;
   const long long rows_per_inst = (long long)N * N;
-  // Z[k] = E'[k] + i O'[k], E' = X[k] + conj X[L-k], O' = (X[k] - conj X[L-k]) conj(W^k)
-  for (int idx = threadIdx.x; idx < TL::TR * (L / 2 + 1); idx += TL::NT) {
+  // Z[k] = E'[k] + i O'[k], E' = X[k] + conj X[L-k], O' = (X[k] - conj X[L-k]) conj(W^k);
+  // all loads of the thread are issued before the first use
+  constexpr int PAIRS = TL::TR * (L / 2 + 1);
+  constexpr int ITER = (PAIRS + TL::NT - 1) / TL::NT;
+  C xk[ITER], xm[ITER];
+#pragma unroll
+  for (int it = 0; it < ITER; ++it) {
+    const int idx = threadIdx.x + it * TL::NT;
     const int row = idx / (L / 2 + 1), k = idx % (L / 2 + 1);
     const int grow = r0 + row;
-    C zk = cmake<C>(0, 0), zm = cmake<C>(0, 0);
-    if (grow < nrows) {
+    xk[it] = cmake<C>(0, 0);
+    xm[it] = cmake<C>(0, 0);
+    if (idx < PAIRS && grow < nrows) {
       const int inst = (int)(grow / rows_per_inst);
-      const C* in = rb.spec + inst * spec_len_cx(N) + (grow % rows_per_inst) * L;
-      if (k == 0) {
-        const T x0 = in[0].x;
-        const T xl = (rb.spec + inst * spec_len_cx(N) + spec_main_len(N) + (grow % rows_per_inst))->x;
-        zk = cmake<C>(x0 + xl, x0 - xl);
-      } else {
-        const C xk = in[k], xm = in[L - k];
-        const C e = cadd(xk, cconj(xm));
-        const C d = csub(xk, cconj(xm));
-        const C o = cmul(d, cconj(__ldg(twN + k)));
-        zk = cadd(e, cmul_i(o));
-        zm = cadd(cconj(e), cmul_i(cconj(o)));
-      }
+      const C* base = rb.spec + inst * spec_len_cx(N);
+      const C* in = base + (grow % rows_per_inst) * L;
+      xk[it] = in[k];
+      xm[it] = k == 0 ? base[spec_main_len(N) + (grow % rows_per_inst)] : in[L - k];
+    }
+  }
+#pragma unroll
+  for (int it = 0; it < ITER; ++it) {
+    const int idx = threadIdx.x + it * TL::NT;
+    if (idx >= PAIRS) continue;
+    const int row = idx / (L / 2 + 1), k = idx % (L / 2 + 1);
+    C zk, zm = cmake<C>(0, 0);
+    if (k == 0) {
+      const T x0 = xk[it].x, xl = xm[it].x;
+      zk = cmake<C>(x0 + xl, x0 - xl);
+    } else {
+      const C e = cadd(xk[it], cconj(xm[it]));
+      const C d = csub(xk[it], cconj(xm[it]));
+      const C o = cmul(d, cconj(__ldg(twN + k)));
+      zk = cadd(e, cmul_i(o));
+      zm = cadd(cconj(e), cmul_i(cconj(o)));
     }
     sm[srow(k) * TL::LD + row] = zk;
     if (k != 0 && k != L - k) sm[srow(L - k) * TL::LD + row] = zm;
@@ -376,12 +424,14 @@ static void launch_r2c_L(const RowJob<T>& job, int nbuf, int nrows, bool fixed, 
                          cudaStream_t st) {
   using TL = RowTile<T, L>;
   const size_t sm = TL::SMEM;
-  if (fixed && job.b[0].qstride == 4 && nbuf == 4 && TL::TR % 4 == 0) {
-    auto fn = k_fft_x_r2c<T, L, true, 4>;
-    set_smem<T, L>((const void*)fn, sm);
-    dim3 grid((nrows + TL::TR / 4 - 1) / (TL::TR / 4), 1);
-    fn<<<grid, TL::NT, sm, st>>>(job, nrows, nbuf, tw + L, tw + 2 * L);
-    return;
+  if constexpr (TL::TR % 4 == 0 && ((TL::TR / 4) * L) % TL::NT == 0) {
+    if (fixed && job.b[0].qstride == 4 && nbuf == 4) {
+      auto fn = k_fft_x_r2c<T, L, true, 4>;
+      set_smem<T, L>((const void*)fn, sm);
+      dim3 grid((nrows + TL::TR / 4 - 1) / (TL::TR / 4), 1);
+      fn<<<grid, TL::NT, sm, st>>>(job, nrows, nbuf, tw + L, tw + 2 * L);
+      return;
+    }
   }
   dim3 grid(((nrows + TL::TR - 1) / TL::TR) * nbuf, 1);
   if (fixed) {
