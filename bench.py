@@ -289,6 +289,9 @@ def run_ours(args, rank, world, local_rank):
     traffic = _ncu_traffic(dom)
     launches_total = int(sum(v[1] for v in prof.values()))
     step_bytes = sum(alg.values()) / n
+    # compulsory traffic of one forward + one adjoint step (one read and one write per 3-D
+    # FFT, fused Fourier multipliers): forward 48M + 60N, adjoint 104M + 120N bytes
+    comp_bytes = 152 * M + 180 * N
     out = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_eval, "higher_is_better": True, "scaling": "weak",
@@ -301,9 +304,10 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
                      "traffic": traffic, "launches": dom_launches},
-        "step_roofline": {"algorithmic_GB_per_pm_step": step_bytes / 1e9,
-                          "achieved_GBs": step_bytes / (ms_per_eval / n / 1e3) / 1e9,
-                          "frac": step_bytes / (ms_per_eval / n / 1e3) / 1e9 / peak},
+        "step_roofline": {"compulsory_GB_per_pm_step": comp_bytes / 1e9,
+                          "compulsory_frac": comp_bytes / (ms_per_eval / n / 1e3) / 1e9 / peak,
+                          "pass_GB_per_pm_step": step_bytes / 1e9,
+                          "pass_frac": step_bytes / (ms_per_eval / n / 1e3) / 1e9 / peak},
         "kernels_ms_per_eval": {k: v[0] / args.steps for k, v in prof.items()},
         "gpu_launches": launches_total,
         "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": 4 * (N + M),

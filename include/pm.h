@@ -131,6 +131,20 @@ int pm_set_inputs(pm_ctx* ctx, const double* theta, const void* omega);
 int pm_gradient(pm_ctx* ctx, const void* omega, const void* target, double* loss, void* grad_omega,
                 double* grad_theta);
 
+/*
+ * Shell-averaged power spectrum of an overdensity mesh (a summary statistic of the
+ * observable, Sec. 2.4): P(k_b) = V / M^2 <|DFT delta(k)|^2> over the modes with
+ * b <= |n| < b + 1 (n the integer wavevector), b = 0 .. n_mesh/2 - 1, the mean taken over
+ * the full k-space shell.  The sums are deterministic (int64 fixed point with a per-bin
+ * scale), accumulated in FP64 precision.
+ *   dens   : device [batch][n_mesh^3], or null for the context's last forward density
+ *   pk     : [batch][n_mesh/2] doubles, host or device
+ *   kmean  : optional [n_mesh/2] doubles, mean |k| per bin in h/Mpc
+ *   nmodes : optional [n_mesh/2] doubles, number of modes per bin
+ * Synchronises the stream.  Errors: PM_ERR_STATE when dens is null before any forward.
+ */
+int pm_power_spectrum(pm_ctx* ctx, const void* dens, double* pk, double* kmean, double* nmodes);
+
 /* Per-category timing of the context's kernel launches with CUDA events on its stream. */
 enum {
   PM_PROF_SCATTER = 0,   /* CIC scatter (density, and pi in the adjoint)        */

@@ -357,3 +357,27 @@ def loss_and_gradient(omega, theta, target, cfg, ckpt_every=0):
     ckpt = fwd["store"] if ckpt_every else None
     adj = adjoint(omega, theta, cfg, fwd, dj_ddelta=dj, ckpt=ckpt)
     return loss, adj, fwd
+
+
+def power_spectrum(delta, box):
+    """Shell-averaged power spectrum of a real mesh field (the summary statistic of
+    Sec. 2.4): P(k_b) = V / M^2 <|DFT delta(k)|^2> over modes with b <= |n| < b + 1,
+    b = 0 .. n/2 - 1, averaged over the full k-space sphere (each half-spectrum mode
+    off the kx = 0 and kx = n/2 planes stands for itself and its conjugate).
+    Returns (mean |k| per bin in h/Mpc, P per bin, number of modes per bin)."""
+    n = delta.shape[0]
+    dk = np.fft.rfftn(delta)
+    (k0, k1, k2), (n0, n1, n2) = _kgrid(n, box)
+    nn = np.sqrt(n0 ** 2 + n1 ** 2 + n2 ** 2)
+    w = np.where((n2 == 0) | (n2 == n // 2), 1.0, 2.0) * np.ones_like(nn)
+    b = np.floor(nn).astype(np.int64)
+    keep = b < n // 2
+    nb = n // 2
+    cnt = np.bincount(b[keep], weights=w[keep], minlength=nb)
+    pw = np.bincount(b[keep], weights=(w * np.abs(dk) ** 2)[keep], minlength=nb)
+    ks = np.bincount(b[keep], weights=(w * nn)[keep], minlength=nb)
+    m = float(n) ** 3
+    with np.errstate(invalid="ignore", divide="ignore"):
+        pk = box ** 3 / m ** 2 * pw / cnt
+        kmean = 2 * np.pi / box * ks / cnt
+    return kmean, pk, cnt

@@ -174,6 +174,7 @@ class Engine : public EngineBase {
     if (mom) PMGB_CK(cudaMemcpyAsync(mom, p_, sizeof(T) * B_ * 3 * N_, cudaMemcpyDeviceToDevice, st_));
     if (dens) PMGB_CK(cudaMemcpyAsync(dens, dens_, sizeof(T) * B_ * M_, cudaMemcpyDeviceToDevice, st_));
     have_fwd_ = true;
+    have_dens_ = true;
     return PM_OK;
   }
 
@@ -337,6 +338,38 @@ class Engine : public EngineBase {
     if (grad_theta) PMGB_CK(cudaMemcpyAsync(grad_theta, theta_out_, sizeof(double) * 5 * B_, cudaMemcpyDefault, st_));
     if ((loss && is_host(loss)) || (grad_omega && is_host(grad_omega)) || (grad_theta && is_host(grad_theta)))
       PMGB_CK(cudaStreamSynchronize(st_));
+    return PM_OK;
+  }
+
+  // Shell-averaged P(k) of dens ([B][M]; null: the last forward density), n_mesh/2 bins
+  int power_spectrum(const void* dens, double* pk, double* kmean, double* nmodes) override {
+    const int nb = nm_ / 2;
+    if (!pw_acc_) {
+      PMGB_RET(alloc(&pw_acc_, (long long)(B_ + 2) * nb));
+      PMGB_RET(alloc(&pw_max_, (long long)B_ * nb));
+      PMGB_RET(alloc(&pw_e_, (long long)B_ * nb));
+      PMGB_RET(alloc(&pw_out_, (long long)(B_ + 2) * nb));
+    }
+    if (!dens && !have_dens_) return PM_ERR_STATE;
+    const T* d = dens ? (const T*)dens : dens_;
+    PMGB_RET(r2c_real(nm_, d, M_, spec_[6]));
+    PMGB_CK(cudaMemsetAsync(pw_acc_, 0, sizeof(unsigned long long) * (B_ + 2) * nb, st_));
+    PMGB_CK(cudaMemsetAsync(pw_max_, 0, sizeof(unsigned) * B_ * nb, st_));
+    const long long is = spec_len_cx(nm_);
+    k_power_max<T><<<dim3(512, B_), 256, 0, st_>>>(spec_[6], nm_, is, nb, pw_max_);
+    k_power_exponents<<<(B_ * nb + 255) / 256, 256, 0, st_>>>(pw_max_, pw_e_, B_ * nb, ilog2(M_));
+    k_power_acc<T><<<dim3(512, B_), 256, 0, st_>>>(spec_[6], nm_, is, nb, pw_e_, pw_acc_, pw_acc_ + B_ * nb,
+                                                  pw_acc_ + (B_ + 1) * nb);
+    const double vol = cfg_.box * cfg_.box * cfg_.box;
+    k_power_final<<<(B_ * nb + 255) / 256, 256, 0, st_>>>(pw_acc_, pw_acc_ + B_ * nb, pw_acc_ + (B_ + 1) * nb, pw_e_,
+                                                        nb, B_, vol / ((double)M_ * (double)M_),
+                                                        2.0 * M_PI / cfg_.box, pw_out_, pw_out_ + B_ * nb,
+                                                        pw_out_ + (B_ + 1) * nb);
+    PMGB_CK(cudaGetLastError());
+    if (pk) PMGB_CK(cudaMemcpyAsync(pk, pw_out_, sizeof(double) * B_ * nb, cudaMemcpyDefault, st_));
+    if (kmean) PMGB_CK(cudaMemcpyAsync(kmean, pw_out_ + B_ * nb, sizeof(double) * nb, cudaMemcpyDefault, st_));
+    if (nmodes) PMGB_CK(cudaMemcpyAsync(nmodes, pw_out_ + (B_ + 1) * nb, sizeof(double) * nb, cudaMemcpyDefault, st_));
+    PMGB_CK(cudaStreamSynchronize(st_));
     return PM_OK;
   }
 
@@ -676,6 +709,11 @@ class Engine : public EngineBase {
   Geo<T> geo_{};
   std::vector<void*> allocs_;
   T *tgt_ = nullptr, *djdd_ = nullptr, *gw_ = nullptr;
+  unsigned long long* pw_acc_ = nullptr;
+  unsigned* pw_max_ = nullptr;
+  int* pw_e_ = nullptr;
+  double* pw_out_ = nullptr;
+  bool have_dens_ = false;
   T *s_ = nullptr, *p_ = nullptr, *a_ = nullptr, *xi_ = nullptr, *pi_ = nullptr, *s1_ = nullptr, *omega_ = nullptr;
   long long* acc_[1] = {nullptr};
   long long* accq_ = nullptr;

@@ -525,6 +525,76 @@ static __global__ void k_final_theta(ThetaIn in, double* out) {
   for (int j = 0; j < 5; ++j) out[5 * b + j] = in.dlp[j * in.batch + b] + (j == 2 ? g : 0.0);
 }
 
+// ------------------------------------------------------------- power spectrum
+// Shell-averaged power of a half spectrum (summary statistic of Sec. 2.4): bin b holds the
+// modes with b <= |n| < b + 1; off-plane modes count twice (for their conjugates).  The
+// sums are exact int64 fixed point with a per-bin scale from a first max pass, so the
+// result does not depend on the order of the additions.
+__device__ __forceinline__ int isqrt_floor(int v) {
+  int r = (int)sqrtf((float)v);
+  while (r * r > v) --r;
+  while ((r + 1) * (r + 1) <= v) ++r;
+  return r;
+}
+
+template <typename T>
+__global__ void k_power_max(const cx_t<T>* __restrict__ spec, int n, long long is, int nb, unsigned* pmax) {
+  const int b = blockIdx.y;
+  const long long tot = spec_len_cx(n);
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < tot; u += (long long)gridDim.x * blockDim.x) {
+    const Mode m = mode_of(u, n);
+    const int bin = isqrt_floor(m.f0 * m.f0 + m.f1 * m.f1 + m.f2 * m.f2);
+    if (bin >= nb) continue;
+    const cx_t<T> v = spec[b * is + u];
+    const double w = (m.f2 == 0 || m.f2 == n / 2) ? 1.0 : 2.0;
+    const double p = w * ((double)v.x * v.x + (double)v.y * v.y);
+    atomicMax(pmax + b * nb + bin, __float_as_uint(__double2float_ru(p)));
+  }
+}
+
+template <typename T>
+__global__ void k_power_acc(const cx_t<T>* __restrict__ spec, int n, long long is, int nb, const int* __restrict__ e,
+                            unsigned long long* acc, unsigned long long* cnt, unsigned long long* ksum) {
+  const int b = blockIdx.y;
+  const long long tot = spec_len_cx(n);
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < tot; u += (long long)gridDim.x * blockDim.x) {
+    const Mode m = mode_of(u, n);
+    const int n2 = m.f0 * m.f0 + m.f1 * m.f1 + m.f2 * m.f2;
+    const int bin = isqrt_floor(n2);
+    if (bin >= nb) continue;
+    const cx_t<T> v = spec[b * is + u];
+    const int w = (m.f2 == 0 || m.f2 == n / 2) ? 1 : 2;
+    const double p = w * ((double)v.x * v.x + (double)v.y * v.y);
+    atomicAdd(acc + b * nb + bin, (unsigned long long)__double2ll_rn(ldexp(p, e[b * nb + bin])));
+    if (b == 0) {
+      atomicAdd(cnt + bin, (unsigned long long)w);
+      atomicAdd(ksum + bin, (unsigned long long)__double2ll_rn(w * sqrt((double)n2) * 1048576.0));
+    }
+  }
+}
+
+// per-bin exponent: sum over <= 2^lgM modes of values < 2^E stays below 2^62
+static __global__ void k_power_exponents(const unsigned* __restrict__ pmax, int* e, int count, int lgM) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const float mx = __uint_as_float(pmax[i]);
+  e[i] = (mx > 0.f && isfinite(mx)) ? min(62 - lgM - (ilogbf(mx) + 1), 1000) : 0;
+}
+
+static __global__ void k_power_final(const unsigned long long* acc, const unsigned long long* cnt,
+                                     const unsigned long long* ksum, const int* e, int nb, int batch, double vol_m2,
+                                     double kf, double* pk, double* kmean, double* nmodes) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb * batch) return;
+  const int bin = i % nb;
+  const double c = (double)cnt[bin];
+  pk[i] = c > 0 ? vol_m2 * ldexp((double)(long long)acc[i], -e[i]) / c : 0.0;
+  if (i < nb) {
+    if (kmean) kmean[bin] = c > 0 ? kf * ldexp((double)(long long)ksum[bin], -20) / c : 0.0;
+    if (nmodes) nmodes[bin] = c;
+  }
+}
+
 // numpy rfftn layout <-> main + side spectrum layout (for the FFT operator entry point)
 template <typename T>
 __global__ void k_spec_to_std(const cx_t<T>* __restrict__ spec, cx_t<T>* __restrict__ out, int n, long long total) {

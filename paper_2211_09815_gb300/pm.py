@@ -17,7 +17,7 @@ STATUS = {0: "PM_OK", 1: "PM_ERR_ARG", 2: "PM_ERR_OOM", 3: "PM_ERR_CUDA", 4: "PM
 SYMBOLS = ("pm_init", "pm_forward", "pm_loss_mse", "pm_adjoint", "pm_destroy", "pm_status_string",
            "pm_last_cuda_error", "pm_scratch_bytes", "pm_op_density", "pm_op_force", "pm_op_force_vjp",
            "pm_op_fft", "pm_op_za", "pm_set_inputs", "pm_gradient", "pm_profile", "pm_profile_read",
-           "pm_density_noalloc")
+           "pm_density_noalloc", "pm_power_spectrum")
 NOALLOC_MAX_CELLS = 128 ** 3
 PROF_NAMES = ("scatter", "fft_x_r2c", "fft_cols", "fused_z_force", "fused_z_adjoint", "fft_x_c2r",
               "gather_fwd", "gather_adj", "other")
@@ -72,6 +72,7 @@ def load_library(path=LIB_PATH):
     lib.pm_profile.argtypes = [vp, i]
     lib.pm_profile_read.argtypes = [vp, vp, vp]
     lib.pm_density_noalloc.argtypes = [ctypes.c_double, i, i, vp, vp, vp]
+    lib.pm_power_spectrum.argtypes = [vp, vp, vp, vp, vp]
     for name in SYMBOLS:
         getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
     _lib = lib
@@ -213,6 +214,19 @@ class PMContext:
             return ctypes.c_void_p(t.data_ptr()) if t is not None else None
         _check(load_library().pm_gradient(self._h, p(omega), p(target), p(loss), p(grad_omega), p(grad_theta)),
                "pm_gradient")
+
+    def power_spectrum(self, dens=None):
+        """(kmean [n/2], P [batch, n/2], nmodes [n/2]) as float64 numpy arrays."""
+        import numpy as np
+        nb = self.n_mesh // 2
+        pk = np.zeros((self.batch, nb))
+        km = np.zeros(nb)
+        nm = np.zeros(nb)
+        f = ctypes.POINTER(ctypes.c_double)
+        _check(load_library().pm_power_spectrum(self._h, _ptr(dens, self.dtype, self.batch * self.M, "dens"),
+                                                pk.ctypes.data_as(f), km.ctypes.data_as(f), nm.ctypes.data_as(f)),
+               "pm_power_spectrum")
+        return km, pk, nm
 
     def profile(self, enable=True):
         _check(load_library().pm_profile(self._h, int(enable)), "pm_profile")

@@ -300,3 +300,23 @@ def test_white_noise_power_recovers_plin():
         pk.append(np.abs(dk[shell]) ** 2 * lp ** 6 / cfg.box ** 3 / cosmo.plin(kk[shell], THETA))
     ratio = np.mean(pk)
     assert abs(ratio - 1) < 0.05
+
+
+def test_power_spectrum_of_a_plane_wave():
+    """A single cosine mode of amplitude A at |n| = 3 along x puts V A^2 / 4 (per of the
+    two +-k modes) into bin 3 and nothing elsewhere; bin 3 holds 6 * ... modes, so the
+    shell average is (2 modes with power (A M / 2)^2 V / M^2) / (modes in the shell)."""
+    n, box = 16, 50.0
+    x = np.arange(n) * box / n
+    A = 0.7
+    delta = A * np.cos(2 * np.pi * 3 * x / box)[:, None, None] * np.ones((n, n, n))
+    kmean, pk, cnt = pm.power_spectrum(delta, box)
+    total = pk * cnt
+    expect = 2 * (A * n ** 3 / 2) ** 2 * box ** 3 / n ** 6
+    assert abs(total[3] / expect - 1) < 1e-12
+    assert np.all(np.abs(np.delete(total, 3)) < 1e-20 * expect + 1e-25)
+    # mode counts cover the half-open shells exactly
+    (k0, k1, k2), (n0, n1, n2) = pm._kgrid(n, box)
+    nn = np.sqrt(n0 ** 2 + n1 ** 2 + n2 ** 2)
+    full = np.sum(np.floor(np.sqrt(np.add.outer(np.add.outer(np.fft.fftfreq(n, 1 / n) ** 2, np.fft.fftfreq(n, 1 / n) ** 2), np.fft.fftfreq(n, 1 / n) ** 2))) == 3)
+    assert cnt[3] == full
