@@ -349,6 +349,109 @@ def run_op_case(args):
                       "alpha_rms": float(alpha.pow(2).mean().sqrt())}))
 
 
+def run_batched(args):
+    """Batched ensemble: 16 instances of 128^3 particles on 256^3 meshes (200 Mpc/h), own
+    seed and theta each, 32 steps, forward + adjoint.  The batched context runs every
+    kernel once for all instances and replays a captured CUDA graph; it is compared with 16
+    sequential single-instance FP32 contexts (eager launches) on the same inputs."""
+    import torch
+    from paper_2211_09815_gb300 import build, inputs, pm
+    build.build()
+    B, box, nm, npc, n = 16, 200.0, 256, 128, 32
+    N, M = npc ** 3, nm ** 3
+    theta = inputs.ensemble_theta(B)
+    stream = torch.cuda.Stream()
+    out = {"mode": "batched", "batch": B, "workload": "16 x 128^3 particles, 256^3 mesh, 200 Mpc/h, 32 steps"}
+    with torch.cuda.stream(stream):
+        om = torch.from_numpy(np.stack([inputs.white_noise(npc, 1 + b) for b in range(B)])).cuda()
+        om_t = torch.from_numpy(np.stack([inputs.white_noise(npc, 101 + b) for b in range(B)])).cuda()
+        ctx = pm.PMContext(box, nm, npc, n, theta.tolist(), om_t, batch=B, stream=stream)
+        tgt = torch.empty(B * M, device="cuda")
+        ctx.forward(dens=tgt)
+        ctx.set_inputs(omega=om)
+        loss = torch.zeros(B, dtype=torch.float64, device="cuda")
+        gw = torch.empty(B * N, device="cuda")
+        gt = torch.zeros(5 * B, dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup):
+            ctx.gradient_graph(tgt, loss=loss, grad_omega=gw, grad_theta=gt)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.gradient_graph(tgt, loss=loss, grad_omega=gw, grad_theta=gt)
+        e1.record(stream)
+        stream.synchronize()
+        t_batched = e0.elapsed_time(e1) / args.steps
+        gw_b = gw.cpu().numpy().reshape(B, N)
+        ctx.close()
+        # 16 sequential single-instance contexts, eager launches
+        t_single = 0.0
+        max_diff = 0.0
+        for b in range(B):
+            c1 = pm.PMContext(box, nm, npc, n, [theta[b].tolist()], om[b].contiguous(), stream=stream)
+            djdd = torch.empty(M, device="cuda")
+            g1 = torch.empty(N, device="cuda")
+            t1 = tgt[b * M:(b + 1) * M]
+            c1.forward(); c1.loss_mse(t1, djdd); c1.adjoint(djdd=djdd, grad_omega=g1)
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            c1.forward(); c1.loss_mse(t1, djdd); c1.adjoint(djdd=djdd, grad_omega=g1)
+            f1.record(stream)
+            stream.synchronize()
+            t_single += f0.elapsed_time(f1)
+            max_diff = max(max_diff, float(np.max(np.abs(g1.cpu().numpy() - gw_b[b]))))
+            c1.close()
+    out.update({"ms_per_batched_eval": t_batched, "ms_16_sequential_evals": t_single,
+                "speedup": t_single / t_batched,
+                "batched_instance_steps_per_s": B * n / (t_batched / 1e3),
+                "sequential_instance_steps_per_s": B * n / (t_single / 1e3),
+                "max_abs_grad_diff_batched_vs_single": max_diff})
+    print(json.dumps(out))
+
+
+def run_ckpt_compare(args):
+    """Reverse-time recomputation vs checkpoints every 8 steps vs every step (the stored
+    trajectory) at 256^3 particles / 512^3 mesh / 400 Mpc/h / 63 steps: device memory,
+    time per gradient evaluation and the gradient differences."""
+    import torch
+    from paper_2211_09815_gb300 import build, inputs, pm
+    build.build()
+    box, nm, npc, n = 400.0, 512, 256, 63
+    N, M = npc ** 3, nm ** 3
+    om = torch.from_numpy(inputs.white_noise(npc, 1)).cuda()
+    om2 = torch.from_numpy(inputs.white_noise(npc, 2)).cuda()
+    c0 = pm.PMContext(box, nm, npc, n, [THETA], om2)
+    tgt = torch.empty(M, device="cuda")
+    c0.forward(dens=tgt)
+    c0.close()
+    res, grads = {}, {}
+    for k in (0, 8, 1):
+        torch.cuda.synchronize()
+        ctx = pm.PMContext(box, nm, npc, n, [THETA], om, ckpt_every=k)
+        djdd = torch.empty(M, device="cuda")
+        gw = torch.empty(N, device="cuda")
+        gt = torch.zeros(5, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            ctx.forward(); ctx.loss_mse(tgt, djdd); ctx.adjoint(djdd=djdd, grad_omega=gw, grad_theta=gt)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.forward(); ctx.loss_mse(tgt, djdd); ctx.adjoint(djdd=djdd, grad_omega=gw, grad_theta=gt)
+        e1.record()
+        torch.cuda.synchronize()
+        res[f"ckpt_every_{k}"] = {"ms_per_eval": e0.elapsed_time(e1), "scratch_GB": ctx.scratch_bytes / 1e9}
+        grads[k] = (gw.cpu().numpy().astype(np.float64), gt.cpu().numpy())
+        ctx.close()
+    g0, g8, g1 = grads[0][0], grads[8][0], grads[1][0]
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    def cos(a, b):
+        return float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
+    res["grad_omega_reverse_vs_stored"] = {"rel_l2": rel(g0, g1), "cosine": cos(g0, g1)}
+    res["grad_omega_ckpt8_vs_stored"] = {"rel_l2": rel(g8, g1), "cosine": cos(g8, g1)}
+    res["grad_theta"] = {str(k): grads[k][1].tolist() for k in grads}
+    print(json.dumps({"mode": "ckpt_compare", "workload": "256^3 particles, 512^3 mesh, 400 Mpc/h, 63 steps",
+                      **res}))
+
+
 def _ncu_traffic(kernel):
     """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if it
     covers the current kernel build (profiles/ncu_traffic.json), else None."""
@@ -371,13 +474,19 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched", action="store_true", help="16-instance batched graph vs sequential runs")
+    ap.add_argument("--compare-ckpt", action="store_true", help="reverse time vs checkpoints: memory/time")
     ap.add_argument("--op-case", action="store_true",
                     help="run one force and one force-VJP operator call (no timing), for profilers")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
-    if args.op_case:
+    if args.batched:
+        run_batched(args)
+    elif args.compare_ckpt:
+        run_ckpt_compare(args)
+    elif args.op_case:
         run_op_case(args)
     elif args.impl == "reference":
         run_reference(args, rank, world)

@@ -132,6 +132,18 @@ int pm_gradient(pm_ctx* ctx, const void* omega, const void* target, double* loss
                 double* grad_theta);
 
 /*
+ * One gradient evaluation (pm_forward, pm_loss_mse, pm_adjoint) on device buffers, replayed
+ * from a CUDA graph: the first call (and any call whose pointers differ from the previous
+ * one) runs the evaluation once normally, then captures it on the context stream and
+ * instantiates the graph; every call launches the graph.  New theta/omega between calls go
+ * through pm_set_inputs (they land in the buffers the graph reads).  All of target
+ * ([batch][n_mesh^3]), loss ([batch]), grad_omega ([batch][n_ptcl^3]) and grad_theta
+ * ([batch][5]) must be device pointers (optional except target), and the context must
+ * have been created on a stream other than the legacy default stream (PM_ERR_ARG).
+ */
+int pm_gradient_graph(pm_ctx* ctx, const void* target, double* loss, void* grad_omega, double* grad_theta);
+
+/*
  * Shell-averaged power spectrum of an overdensity mesh (a summary statistic of the
  * observable, Sec. 2.4): P(k_b) = V / M^2 <|DFT delta(k)|^2> over the modes with
  * b <= |n| < b + 1 (n the integer wavevector), b = 0 .. n_mesh/2 - 1, the mean taken over

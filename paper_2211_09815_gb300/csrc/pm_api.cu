@@ -110,6 +110,11 @@ int pm_gradient(pm_ctx* ctx, const void* omega, const void* target, double* loss
   return ctx->eng->gradient(omega, target, loss, grad_omega, grad_theta);
 }
 
+int pm_gradient_graph(pm_ctx* ctx, const void* target, double* loss, void* grad_omega, double* grad_theta) {
+  if (!ctx || !target) return PM_ERR_ARG;
+  return ctx->eng->gradient_graph(target, loss, grad_omega, grad_theta);
+}
+
 int pm_power_spectrum(pm_ctx* ctx, const void* dens, double* pk, double* kmean, double* nmodes) {
   if (!ctx || !pk) return PM_ERR_ARG;
   return ctx->eng->power_spectrum(dens, pk, kmean, nmodes);

@@ -19,6 +19,7 @@ struct EngineBase {
   virtual int profile(int enable) = 0;
   virtual int profile_read(double* ms, long long* launches) = 0;
   virtual int set_inputs(const double* theta, const void* omega) = 0;
+  virtual int gradient_graph(const void* target, double* loss, void* gw, double* gt) = 0;
   virtual int power_spectrum(const void* dens, double* pk, double* kmean, double* nmodes) = 0;
   virtual int gradient(const void* omega, const void* target, double* loss, void* grad_omega, double* grad_theta) = 0;
 };

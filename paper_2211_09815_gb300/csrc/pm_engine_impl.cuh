@@ -89,6 +89,7 @@ class Engine : public EngineBase {
 
   ~Engine() override {
     if (st_) cudaStreamSynchronize(st_);
+    if (graph_exec_) cudaGraphExecDestroy(graph_exec_);
     for (void* p : allocs_) cudaFree(p);
   }
 
@@ -175,6 +176,14 @@ class Engine : public EngineBase {
     if (dens) PMGB_CK(cudaMemcpyAsync(dens, dens_, sizeof(T) * B_ * M_, cudaMemcpyDeviceToDevice, st_));
     have_fwd_ = true;
     have_dens_ = true;
+    return PM_OK;
+  }
+
+  int eval_device(const void* target, double* loss, void* gw, double* gt) {
+    PMGB_RET(forward(nullptr, nullptr, nullptr));
+    PMGB_RET(loss_mse_dev(target, djdd_));
+    if (loss) PMGB_CK(cudaMemcpyAsync(loss, scal_, sizeof(double) * B_, cudaMemcpyDeviceToDevice, st_));
+    PMGB_RET(adjoint(djdd_, nullptr, nullptr, gw, gt));
     return PM_OK;
   }
 
@@ -370,6 +379,40 @@ class Engine : public EngineBase {
     if (kmean) PMGB_CK(cudaMemcpyAsync(kmean, pw_out_ + B_ * nb, sizeof(double) * nb, cudaMemcpyDefault, st_));
     if (nmodes) PMGB_CK(cudaMemcpyAsync(nmodes, pw_out_ + (B_ + 1) * nb, sizeof(double) * nb, cudaMemcpyDefault, st_));
     PMGB_CK(cudaStreamSynchronize(st_));
+    return PM_OK;
+  }
+
+  // One gradient evaluation on device buffers, captured once into a CUDA graph on the
+  // context stream and replayed afterwards (re-captured when the pointers change).
+  int gradient_graph(const void* target, double* loss, void* gw, double* gt) override {
+    if (st_ == 0) return PM_ERR_ARG;  // the legacy default stream cannot be captured
+    if ((loss && is_host(loss)) || (gw && is_host(gw)) || (gt && is_host(gt)) || is_host(target)) return PM_ERR_ARG;
+    if (!djdd_) PMGB_RET(alloc(&djdd_, (long long)B_ * M_));
+    const void* args[4] = {target, loss, gw, gt};
+    bool same = graph_exec_ != nullptr;
+    for (int i = 0; i < 4 && same; ++i) same = args[i] == graph_args_[i];
+    if (!same) {
+      if (graph_exec_) {
+        cudaGraphExecDestroy(graph_exec_);
+        graph_exec_ = nullptr;
+      }
+      PMGB_RET(eval_device(target, loss, gw, gt));  // warm-up outside the capture
+      PMGB_CK(cudaStreamSynchronize(st_));
+      cudaGraph_t g = nullptr;
+      PMGB_CK(cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal));
+      const int r = eval_device(target, loss, gw, gt);
+      const cudaError_t e = cudaStreamEndCapture(st_, &g);
+      if (r != PM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+      }
+      PMGB_CK(e);
+      const cudaError_t ei = cudaGraphInstantiate(&graph_exec_, g, 0);
+      cudaGraphDestroy(g);
+      PMGB_CK(ei);
+      for (int i = 0; i < 4; ++i) graph_args_[i] = args[i];
+    }
+    PMGB_CK(cudaGraphLaunch(graph_exec_, st_));
     return PM_OK;
   }
 
@@ -714,6 +757,8 @@ class Engine : public EngineBase {
   int* pw_e_ = nullptr;
   double* pw_out_ = nullptr;
   bool have_dens_ = false;
+  cudaGraphExec_t graph_exec_ = nullptr;
+  const void* graph_args_[4] = {nullptr, nullptr, nullptr, nullptr};
   T *s_ = nullptr, *p_ = nullptr, *a_ = nullptr, *xi_ = nullptr, *pi_ = nullptr, *s1_ = nullptr, *omega_ = nullptr;
   long long* acc_[1] = {nullptr};
   long long* accq_ = nullptr;

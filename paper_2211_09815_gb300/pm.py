@@ -17,7 +17,7 @@ STATUS = {0: "PM_OK", 1: "PM_ERR_ARG", 2: "PM_ERR_OOM", 3: "PM_ERR_CUDA", 4: "PM
 SYMBOLS = ("pm_init", "pm_forward", "pm_loss_mse", "pm_adjoint", "pm_destroy", "pm_status_string",
            "pm_last_cuda_error", "pm_scratch_bytes", "pm_op_density", "pm_op_force", "pm_op_force_vjp",
            "pm_op_fft", "pm_op_za", "pm_set_inputs", "pm_gradient", "pm_profile", "pm_profile_read",
-           "pm_density_noalloc", "pm_power_spectrum")
+           "pm_density_noalloc", "pm_power_spectrum", "pm_gradient_graph")
 NOALLOC_MAX_CELLS = 128 ** 3
 PROF_NAMES = ("scatter", "fft_x_r2c", "fft_cols", "fused_z_force", "fused_z_adjoint", "fft_x_c2r",
               "gather_fwd", "gather_adj", "other")
@@ -73,6 +73,7 @@ def load_library(path=LIB_PATH):
     lib.pm_profile_read.argtypes = [vp, vp, vp]
     lib.pm_density_noalloc.argtypes = [ctypes.c_double, i, i, vp, vp, vp]
     lib.pm_power_spectrum.argtypes = [vp, vp, vp, vp, vp]
+    lib.pm_gradient_graph.argtypes = [vp, vp, vp, vp, vp]
     for name in SYMBOLS:
         getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
     _lib = lib
@@ -214,6 +215,13 @@ class PMContext:
             return ctypes.c_void_p(t.data_ptr()) if t is not None else None
         _check(load_library().pm_gradient(self._h, p(omega), p(target), p(loss), p(grad_omega), p(grad_theta)),
                "pm_gradient")
+
+    def gradient_graph(self, target, loss=None, grad_omega=None, grad_theta=None):
+        """pm_gradient_graph: device tensors only; needs a non-default stream."""
+        def p(t):
+            return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        _check(load_library().pm_gradient_graph(self._h, p(target), p(loss), p(grad_omega), p(grad_theta)),
+               "pm_gradient_graph")
 
     def power_spectrum(self, dens=None):
         """(kmean [n/2], P [batch, n/2], nmodes [n/2]) as float64 numpy arrays."""

@@ -122,3 +122,43 @@ def test_batched_instances_equal_single_runs():
         assert np.array_equal(one["s"][0], both["s"][b])
         assert np.array_equal(one["grad_omega"][0], both["grad_omega"][b])
         assert np.array_equal(one["grad_theta"][0], both["grad_theta"][b])
+
+
+def test_graph_replay_equals_eager_batched():
+    """pm_gradient_graph (captured once, replayed with new omega) gives the eager result
+    bit for bit, for a batch of two instances with different cosmologies."""
+    torch = torch_cuda()
+    from paper_2211_09815_gb300 import pm
+    cfg = dict(C0)
+    N, M = cfg["n_ptcl"] ** 3, cfg["n_mesh"] ** 3
+    theta2 = [THETA, (2.3e-9, 0.95, 0.28, 0.049, 0.68)]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        om = torch.from_numpy(np.stack([inputs.white_noise(cfg["n_ptcl"], s) for s in (1, 2)])).cuda()
+        ctx = pm.PMContext(cfg["box"], cfg["n_mesh"], cfg["n_ptcl"], cfg["n_steps"], theta2, om, batch=2,
+                           stream=stream)
+        tgt = torch.zeros(2 * M, device="cuda")
+        loss = torch.zeros(2, dtype=torch.float64, device="cuda")
+        gw = torch.empty(2 * N, device="cuda")
+        gt = torch.zeros(10, dtype=torch.float64, device="cuda")
+        results = []
+        for seeds in ((1, 2), (3, 4), (1, 2)):
+            om2 = torch.from_numpy(np.stack([inputs.white_noise(cfg["n_ptcl"], s) for s in seeds])).cuda()
+            ctx.set_inputs(omega=om2)
+            ctx.gradient_graph(tgt, loss=loss, grad_omega=gw, grad_theta=gt)
+            stream.synchronize()
+            g_graph = (gw.cpu().numpy().copy(), gt.cpu().numpy().copy(), loss.cpu().numpy().copy())
+            ctx.set_inputs(omega=om2)
+            ctx.forward()
+            djdd = torch.empty(2 * M, device="cuda")
+            ctx.loss_mse(tgt, djdd)
+            gw2 = torch.empty(2 * N, device="cuda")
+            gt2 = torch.zeros(10, dtype=torch.float64, device="cuda")
+            ctx.adjoint(djdd=djdd, grad_omega=gw2, grad_theta=gt2)
+            stream.synchronize()
+            assert np.array_equal(g_graph[0], gw2.cpu().numpy())
+            assert np.array_equal(g_graph[1], gt2.cpu().numpy())
+            results.append(g_graph)
+        assert not np.array_equal(results[0][0], results[1][0])
+        assert np.array_equal(results[0][0], results[2][0])
+        ctx.close()
