@@ -452,6 +452,66 @@ def run_ckpt_compare(args):
                       **res}))
 
 
+def run_precision_study(args):
+    """FP32 against an FP64 GPU run of the same workload, per output: final displacement
+    RMS (in cells), momentum relative L2, per-shell P(k) relative error, dJ/domega cosine
+    and relative L2, dJ/dtheta relative error."""
+    import torch
+    from paper_2211_09815_gb300 import build, inputs, pm
+    build.build()
+    box, nm, npc, n = WORKLOADS[args.workload]
+    N, M = npc ** 3, nm ** 3
+    out = {}
+    tgt_np = None
+    for prec in (0, 1):
+        dt = torch.float32 if prec == 0 else torch.float64
+        if tgt_np is None:
+            om2 = torch.from_numpy(inputs.white_noise(npc, 2)).cuda()
+            c0 = pm.PMContext(box, nm, npc, n, [THETA], om2)
+            t = torch.empty(M, device="cuda")
+            c0.forward(dens=t)
+            tgt_np = t.cpu().numpy()
+            c0.close()
+            del om2, t
+        om = torch.from_numpy(inputs.white_noise(npc, 1)).to("cuda", dt)
+        ctx = pm.PMContext(box, nm, npc, n, [THETA], om, precision=prec)
+        disp = torch.empty(3 * N, device="cuda", dtype=dt)
+        mom = torch.empty_like(disp)
+        ctx.forward(disp=disp, mom=mom)
+        km, pk, nmodes = ctx.power_spectrum()
+        tgt = torch.from_numpy(tgt_np).to("cuda", dt)
+        djdd = torch.empty(M, device="cuda", dtype=dt)
+        ctx.loss_mse(tgt, djdd)
+        gw = torch.empty(N, device="cuda", dtype=dt)
+        gt = torch.zeros(5, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.adjoint(djdd=djdd, grad_omega=gw, grad_theta=gt)
+        torch.cuda.synchronize()
+        out[prec] = dict(s=disp.cpu().numpy().astype(np.float64), p=mom.cpu().numpy().astype(np.float64),
+                         pk=pk[0], nmodes=nmodes, gw=gw.cpu().numpy().astype(np.float64), gt=gt.cpu().numpy(),
+                         adj_s=time.perf_counter() - t0)
+        ctx.close()
+        del om, disp, mom, tgt, djdd, gw, gt
+        torch.cuda.empty_cache()
+    a, b = out[0], out[1]
+    cell = box / nm
+    ok = b["nmodes"] > 0
+    ok[0] = False
+    res = {
+        "mode": "precision_study", "workload": f"{npc}^3 particles, {nm}^3 mesh, {box:g} Mpc/h, {n} steps",
+        "disp_rms_cells": float(np.sqrt(np.mean((a["s"] - b["s"]) ** 2)) / cell),
+        "mom_rel_l2": float(np.linalg.norm(a["p"] - b["p"]) / np.linalg.norm(b["p"])),
+        "pk_max_rel": float(np.max(np.abs(a["pk"][ok] / b["pk"][ok] - 1))),
+        "grad_omega_cosine": float(a["gw"] @ b["gw"] / (np.linalg.norm(a["gw"]) * np.linalg.norm(b["gw"]))),
+        "grad_omega_rel_l2": float(np.linalg.norm(a["gw"] - b["gw"]) / np.linalg.norm(b["gw"])),
+        "grad_theta_rel": (np.abs(a["gt"] / b["gt"] - 1)).tolist(),
+        "grad_theta_fp64": b["gt"].tolist(),
+        "adjoint_seconds": {"f32": a["adj_s"], "f64": b["adj_s"]},
+    }
+    print(json.dumps(res))
+
+
 def _ncu_traffic(kernel):
     """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if it
     covers the current kernel build (profiles/ncu_traffic.json), else None."""
@@ -476,6 +536,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", action="store_true", help="16-instance batched graph vs sequential runs")
     ap.add_argument("--compare-ckpt", action="store_true", help="reverse time vs checkpoints: memory/time")
+    ap.add_argument("--precision-study", action="store_true", help="FP32 vs FP64 GPU run, errors per output")
     ap.add_argument("--op-case", action="store_true",
                     help="run one force and one force-VJP operator call (no timing), for profilers")
     args = ap.parse_args()
@@ -486,6 +547,8 @@ def main():
         run_batched(args)
     elif args.compare_ckpt:
         run_ckpt_compare(args)
+    elif args.precision_study:
+        run_precision_study(args)
     elif args.op_case:
         run_op_case(args)
     elif args.impl == "reference":

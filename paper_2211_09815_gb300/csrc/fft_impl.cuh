@@ -10,6 +10,7 @@
 #include <type_traits>
 
 #include "fft.cuh"
+#include "fft_tma.cuh"
 #include "pm_internal.h"
 
 namespace pmgb {
@@ -472,6 +473,106 @@ static void launch_fused_L(const ZJob<T>& job, bool adjoint, const cx_t<T>* tw, 
   }
 }
 
+template <typename T, int L> static int tiles_of() { return L * ((L / 2) / TmaTile<T, L>::TC); }
+
+template <typename T, int L, int DIR, int KIND>
+static void launch_tma_L(const CUtensorMap* maps, const TmaJob<T>& job, int tiles, const cx_t<T>* tw, int nsm,
+                         cudaStream_t st) {
+  using TT = TmaTile<T, L>;
+  TmaMaps m{};
+  for (int i = 0; i < (KIND == 0 ? job.nbuf : (KIND == 1 ? 1 : 3)); ++i) m.m[i] = maps[i];
+  const size_t sm = (size_t)(KIND == 0 ? 2 : 3) * TT::BYTES + 1024;
+  auto fn = k_cols_tma<T, L, DIR, KIND>;
+  ensure_smem_attr((const void*)fn, (int)sm);
+  const int items = KIND == 0 ? job.nbuf * tiles : tiles;
+  const int grid = items < nsm ? items : nsm;
+  fn<<<grid, TT::NT, sm, st>>>(m, job, tiles, tw + L);
+}
+
+#define PMGB_DISPATCH_TMA(L_, CALL)                                                 \
+  switch (L_) {                                                                     \
+    case 128: { constexpr int LL = 128; CALL; } break;                              \
+    case 256: { constexpr int LL = 256; CALL; } break;                              \
+    case 512: { constexpr int LL = 512; CALL; } break;                              \
+    case 1024: { constexpr int LL = 1024; CALL; } break;                            \
+    default: return PM_ERR_ARG;                                                     \
+  }
+
+template <typename T>
+int fft_cols_tma(int n, int batch, int dir, int zaxis, const CUtensorMap* maps, cx_t<T>* const* bufs, int nb,
+                 const cx_t<T>* tw, int* err, int nsm, cudaStream_t st) {
+  TmaJob<T> job{};
+  job.batch = batch;
+  for (int i = 0; i < nb; ++i) job.out[i] = bufs[i];
+  job.nbuf = nb;
+  job.zaxis = zaxis;
+  job.err = err;
+  if (dir < 0) {
+    PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, -1, 0>(maps, job, batch * tiles_of<T, LL>(), tw, nsm, st)));
+  } else {
+    PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, +1, 0>(maps, job, batch * tiles_of<T, LL>(), tw, nsm, st)));
+  }
+  return PM_OK;
+}
+
+template <typename T>
+int fft_fused_tma(int n, bool adjoint, const CUtensorMap* maps, const ZJob<T>& zj, const cx_t<T>* tw, int* err,
+                  int nsm, cudaStream_t st) {
+  TmaJob<T> job{};
+  for (int i = 0; i < 3; ++i) job.out[i] = zj.out[i];
+  job.nbuf = 1;
+  job.zaxis = 1;
+  job.batch = zj.batch;
+  job.coef = zj.coef;
+  job.dtab = zj.dtab;
+  job.err = err;
+  if (adjoint) {
+    PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, +1, 2>(maps, job, zj.batch * tiles_of<T, LL>(), tw, nsm, st)));
+  } else {
+    PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, +1, 1>(maps, job, zj.batch * tiles_of<T, LL>(), tw, nsm, st)));
+  }
+  return PM_OK;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).  The
+// spectrum main array is viewed as a 4-D tensor of int64 words: (kx words, y, z, batch).
+template <typename T, int L>
+static int make_maps_L(int batch, cx_t<T>* buf, CUtensorMap* ymap, CUtensorMap* zmap) {
+  using Fn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
+                          const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                          CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Fn encode = nullptr;
+  if (!encode) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !f)
+      return PM_ERR_CUDA;
+    encode = (Fn)f;
+  }
+  using TT = TmaTile<T, L>;
+  constexpr int eb = (int)sizeof(cx_t<T>);
+  const cuuint64_t dims[4] = {(cuuint64_t)(L / 2) * TT::W, (cuuint64_t)L, (cuuint64_t)L, (cuuint64_t)batch};
+  const cuuint64_t strides[3] = {(cuuint64_t)(L / 2) * eb, (cuuint64_t)L * (L / 2) * eb,
+                                 (cuuint64_t)spec_len_cx(L) * eb};
+  const cuuint32_t ybox[4] = {(cuuint32_t)(TT::TC * TT::W), (cuuint32_t)TT::RB, 1, 1};
+  const cuuint32_t zbox[4] = {(cuuint32_t)(TT::TC * TT::W), 1, (cuuint32_t)TT::RB, 1};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  const CUresult r1 = encode(ymap, CU_TENSOR_MAP_DATA_TYPE_INT64, 4, (void*)buf, dims, strides, ybox, es,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const CUresult r2 = encode(zmap, CU_TENSOR_MAP_DATA_TYPE_INT64, 4, (void*)buf, dims, strides, zbox, es,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return (r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS) ? PM_OK : PM_ERR_CUDA;
+}
+
+template <typename T>
+int make_spec_tensor_maps(int n, int batch, cx_t<T>* buf, CUtensorMap* ymap, CUtensorMap* zmap) {
+  PMGB_DISPATCH_TMA(n, return (make_maps_L<T, LL>(batch, buf, ymap, zmap)));
+  return PM_ERR_ARG;
+}
+
 #define PMGB_DISPATCH_L(L_, CALL)                                                   \
   switch (L_) {                                                                     \
     case 2: { constexpr int LL = 2; CALL; } break;                                  \
@@ -510,6 +611,29 @@ template <typename T>
 int fft_x_c2r(int n, const RowJob<T>& job, int nbuf, int nrows, const cx_t<T>* tw, cudaStream_t st) {
   if (n < 4 || n > 1024) return PM_ERR_ARG;
   PMGB_DISPATCH_L(n / 2, (launch_c2r_L<T, (LL < 512 ? LL : 512)>(job, nbuf, nrows, tw, st)));
+  return PM_OK;
+}
+
+template <typename T, int L>
+static void launch_fused_side_L(const ZJob<T>& job, bool adjoint, const cx_t<T>* tw, cudaStream_t st) {
+  using TL = FusedTile<T, L>;
+  const int nts = (job.batch * L + TL::TC - 1) / TL::TC;
+  const size_t sm = 2 * (size_t)TL::SMEM;
+  if (adjoint) {
+    auto fn = k_fused_z_adjoint<T, L>;
+    set_smem<T, L>((const void*)fn, sm);
+    fn<<<nts, TL::NT, sm, st>>>(job, 0, tw + L);
+  } else {
+    auto fn = k_fused_z_force<T, L>;
+    set_smem<T, L>((const void*)fn, sm);
+    fn<<<nts, TL::NT, sm, st>>>(job, 0, tw + L);
+  }
+}
+
+template <typename T>
+int fft_fused_side(int n, const ZJob<T>& job, bool adjoint, const cx_t<T>* tw, cudaStream_t st) {
+  if (n < 4) return PM_ERR_ARG;
+  PMGB_DISPATCH_L(n, (launch_fused_side_L<T, (LL < 4 ? 4 : LL)>(job, adjoint, tw, st)));
   return PM_OK;
 }
 

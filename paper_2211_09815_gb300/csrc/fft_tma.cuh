@@ -1,0 +1,230 @@
+// TMA-staged, double-buffered persistent column passes of the 3-D FFT (y and z axes of
+// the main half spectrum), templated on the real type.
+//
+// One CTA per SM loops over column tiles (TC sequences x L elements).  A single thread
+// issues the tensor-memory-accelerator loads of the next tile into the other half of a
+// two-slot shared-memory ring (cp.async.bulk.tensor, completion on an mbarrier) before the
+// CTA works on the current tile, so HBM reads of tile t+1 overlap the radix stages of
+// tile t.  Results leave through the last radix stage's direct global stores.
+//   KIND 0: in-place column FFT of up to four buffers (direction DIR)
+//   KIND 1: z FFT of delta^, times -ik_c G / M per component, 3 inverse z FFTs (force)
+//   KIND 2: z FFTs of pi_c^ accumulated with conj(-ik_c G) / M, 1 inverse z FFT (adjoint)
+// Every mbarrier wait is bounded: on timeout the CTA records an error flag, waits (again
+// bounded) for its own copies in flight, and returns.
+#pragma once
+#include <cuda.h>
+
+#include "fft.cuh"
+
+namespace pmgb {
+
+struct TmaMaps { CUtensorMap m[4]; };
+
+template <typename T> struct TmaJob {
+  cx_t<T>* out[4];     // KIND 0: the buffers themselves; KIND 1: F_0..2; KIND 2: psi
+  int nbuf;            // KIND 0: buffers in the launch
+  int zaxis;           // 0: y pass, 1: z pass
+  int batch;
+  const T* coef;       // Green's function coefficient per instance (KIND 1, 2)
+  const T* dtab;       // deconvolution table or null
+  int* err;            // device error flag (mbarrier timeout)
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: false (and the error flag set) if the phase never completes
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int* err) {
+  for (long long i = 0; i < (1LL << 24); ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  if (err) atomicExch(err, 1);
+  return false;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, unsigned long long* bar, int c0, int c1,
+                                            int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+        "r"(smem_u32(bar))
+      : "memory");
+}
+
+// dense [L][TC] tile (TMA writes rows back to back)
+template <typename C, int LD>
+struct DenseTile {
+  C* p;
+  __device__ __forceinline__ C ld(int row, int c) const { return p[row * LD + c]; }
+  __device__ __forceinline__ void st(int row, int c, C v) const { p[row * LD + c] = v; }
+};
+
+template <typename T, int L> struct TmaTile {
+  using CT = ColTile<T, L>;
+  static constexpr int TC = CT::TC, NT = CT::NT, LD = TC;
+  static constexpr int RB = L < 256 ? L : 256;                  // rows per TMA box
+  static constexpr int TILE = L * TC;                            // complex elements per tile
+  static constexpr int BYTES = TILE * (int)sizeof(cx_t<T>);
+  static constexpr int W = (int)sizeof(cx_t<T>) / 8;              // int64 words per complex
+};
+
+// Green's function data for a z-pass column (kx, y), as in the unstaged fused kernels.
+template <typename T, int N>
+struct ZCol {
+  T coef, d12;
+  int n12, f1, f2;
+  const T* dtab;
+  __device__ __forceinline__ T g(int f0) const {
+    const int n2 = f0 * f0 + n12;
+    if (n2 == 0) return (T)0;
+    T v = coef * d12 / (T)n2;
+    if (dtab) v *= dtab[f0 < 0 ? f0 + N : f0];
+    return v;
+  }
+  __device__ __forceinline__ int fc(int comp, int f0) const {
+    if (comp == 0) return f0 == -N / 2 ? 0 : f0;
+    if (comp == 1) return f1 == -N / 2 ? 0 : f1;
+    return f2;   // main array: kx < N/2, never the Nyquist plane
+  }
+};
+
+template <typename T, int N, int LD>
+struct DenseMulSrc {
+  const cx_t<T>* p;
+  ZCol<T, N> z;
+  int comp;
+  __device__ __forceinline__ cx_t<T> ld(int row, int c) const {
+    const cx_t<T> v = p[row * LD + c];
+    const int f0 = freq_of(row, N);
+    const T s = (T)z.fc(comp, f0) * z.g(f0);
+    return cmake<cx_t<T>>(v.y * s, -v.x * s);
+  }
+};
+template <typename T, int N, int LD>
+struct DenseAccDst {
+  cx_t<T>* p;
+  ZCol<T, N> z;
+  int comp;
+  __device__ __forceinline__ void st(int row, int c, cx_t<T> v) const {
+    const int f0 = freq_of(row, N);
+    const T s = (T)z.fc(comp, f0) * z.g(f0);
+    const cx_t<T> m = cmake<cx_t<T>>(-v.y * s, v.x * s);
+    cx_t<T>* q = p + row * LD + c;
+    *q = comp == 0 ? m : cadd(*q, m);
+  }
+};
+
+template <typename T, int L, int DIR, int KIND>
+__global__ void __launch_bounds__(TmaTile<T, L>::NT, 1)
+k_cols_tma(const __grid_constant__ TmaMaps maps, TmaJob<T> job, int tiles_per_buf, const cx_t<T>* __restrict__ tw) {
+  using C = cx_t<T>;
+  using TT = TmaTile<T, L>;
+  constexpr int N = L;
+  constexpr int NCG = (N / 2) / TT::TC;            // column groups per row of the main array
+  constexpr int NL = KIND == 2 ? 3 : 1;            // loads per work item
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // TMA destinations must be 128-byte aligned: round the dynamic base up (1 KiB slack)
+  C* ring0 = reinterpret_cast<C*>((reinterpret_cast<unsigned long long>(smem_raw) + 1023ull) & ~1023ull);
+  C* ring1 = ring0 + TT::TILE;
+  C* work = ring0 + 2 * TT::TILE;
+  __shared__ unsigned long long bars[2];
+  const int items = KIND == 0 ? job.nbuf * tiles_per_buf : tiles_per_buf;
+  const int my_items = blockIdx.x < (unsigned)items ? (items - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int nq = my_items * NL;
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  // load q of this CTA -> (work item, component)
+  auto decode = [&](int q, int& item, int& comp) {
+    item = blockIdx.x + (q / NL) * gridDim.x;
+    comp = q % NL;
+  };
+  auto issue = [&](int q) {
+    int item, comp;
+    decode(q, item, comp);
+    const int buf = KIND == 0 ? item / tiles_per_buf : comp;
+    const int u = KIND == 0 ? item % tiles_per_buf : item;
+    const int kxg = u % NCG, o = (u / NCG) % N, b = u / (NCG * N);
+    C* dst = (q & 1) ? ring1 : ring0;
+    unsigned long long* bar = &bars[q & 1];
+    fence_proxy_async();
+    mbar_expect_tx(bar, TT::BYTES);
+#pragma unroll
+    for (int r = 0; r < L / TT::RB; ++r) {
+      if (job.zaxis)
+        tma_load_4d(dst + r * TT::RB * TT::LD, &maps.m[buf], bar, kxg * TT::TC * TT::W, o, r * TT::RB, b);
+      else
+        tma_load_4d(dst + r * TT::RB * TT::LD, &maps.m[buf], bar, kxg * TT::TC * TT::W, r * TT::RB, o, b);
+    }
+  };
+  if (threadIdx.x == 0 && nq > 0) issue(0);
+  const int c = threadIdx.x % TT::TC;
+  for (int q = 0; q < nq; ++q) {
+    if (threadIdx.x == 0 && q + 1 < nq) issue(q + 1);
+    if (!mbar_wait(&bars[q & 1], (q >> 1) & 1, job.err)) {
+      // give the copies in flight a bounded chance to land before the CTA exits
+      if (threadIdx.x == 0 && q + 1 < nq) mbar_wait(&bars[(q + 1) & 1], ((q + 1) >> 1) & 1, nullptr);
+      return;
+    }
+    int item, comp;
+    decode(q, item, comp);
+    const int u = KIND == 0 ? item % tiles_per_buf : item;
+    const int kxg = u % NCG, o = (u / NCG) % N, b = u / (NCG * N);
+    const long long es = job.zaxis ? (long long)N * (N / 2) : (N / 2);
+    const long long base = (long long)b * spec_len_cx(N) + (job.zaxis ? (long long)o * (N / 2) : (long long)o * N * (N / 2)) +
+                           kxg * TT::TC + c;
+    C* cur = (q & 1) ? ring1 : ring0;
+    DenseTile<C, TT::LD> t{cur};
+    if constexpr (KIND == 0) {
+      GlobalSeq<C> g{job.out[item / tiles_per_buf] + base, es, true};
+      fft_tile<T, L, TT::TC, TT::NT, DIR>(t, t, g, tw);
+    } else {
+      ZCol<T, N> zc;
+      zc.f1 = freq_of(o, N);
+      zc.f2 = kxg * TT::TC + c;
+      zc.n12 = zc.f1 * zc.f1 + zc.f2 * zc.f2;
+      zc.coef = job.coef[b];
+      zc.dtab = job.dtab;
+      zc.d12 = job.dtab ? job.dtab[zc.f1 < 0 ? zc.f1 + N : zc.f1] * job.dtab[zc.f2] : (T)1;
+      DenseTile<C, TT::LD> wt{work};
+      if constexpr (KIND == 1) {
+        fft_tile<T, L, TT::TC, TT::NT, -1>(t, t, t, tw);
+        __syncthreads();
+#pragma unroll 1
+        for (int cc = 0; cc < 3; ++cc) {
+          DenseMulSrc<T, N, TT::LD> src{cur, zc, cc};
+          GlobalSeq<C> g{job.out[cc] + base, es, true};
+          fft_tile<T, L, TT::TC, TT::NT, +1>(src, wt, g, tw);
+        }
+      } else {
+        DenseAccDst<T, N, TT::LD> acc{work, zc, comp};
+        fft_tile<T, L, TT::TC, TT::NT, -1>(t, t, acc, tw);
+        if (comp == 2) {
+          __syncthreads();
+          GlobalSeq<C> g{job.out[0] + base, es, true};
+          fft_tile<T, L, TT::TC, TT::NT, +1>(wt, wt, g, tw);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace pmgb

@@ -181,3 +181,9 @@ int pm_op_za(pm_ctx* ctx, void* s1_out) {
 }
 
 }  // extern "C"
+
+namespace pmgb {
+
+bool tma_supported(int n) { return n == 128 || n == 256 || n == 512 || n == 1024; }
+
+}  // namespace pmgb

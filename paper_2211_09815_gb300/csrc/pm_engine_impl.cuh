@@ -3,6 +3,7 @@
 // type.  Included once per precision.
 #pragma once
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -100,7 +101,21 @@ class Engine : public EngineBase {
     prof_.on = enable != 0;
     return PM_OK;
   }
-  int profile_read(double* ms, long long* launches) override { return prof_.read(st_, ms, launches); }
+  int profile_read(double* ms, long long* launches) override {
+    PMGB_RET(prof_.read(st_, ms, launches));
+    return device_error();
+  }
+  // PM_ERR_TIMEOUT if a bounded device wait gave up since the last check (clears the flag)
+  int device_error() {
+    int e = 0;
+    PMGB_CK(cudaMemcpyAsync(&e, dev_err_, sizeof(int), cudaMemcpyDeviceToHost, st_));
+    PMGB_CK(cudaStreamSynchronize(st_));
+    if (e) {
+      PMGB_CK(cudaMemsetAsync(dev_err_, 0, sizeof(int), st_));
+      return PM_ERR_TIMEOUT;
+    }
+    return PM_OK;
+  }
 
   int init(const pm_config* cfg, const double* theta, const void* omega, cudaStream_t st) {
     cfg_ = *cfg;
@@ -145,6 +160,16 @@ class Engine : public EngineBase {
       PMGB_RET(alloc(&ck_p_, pv * nck_));
     }
     PMGB_CK(cudaMemsetAsync(accq_, 0, sizeof(long long) * 4 * B_ * M_, st_));
+    // TMA-staged column passes for the mesh-size spectra
+    int dev = 0;
+    PMGB_CK(cudaGetDevice(&dev));
+    PMGB_CK(cudaDeviceGetAttribute(&nsm_, cudaDevAttrMultiProcessorCount, dev));
+    const char* env = getenv("PMGB_TMA");
+    use_tma_ = tma_supported(nm_) && !(env && env[0] == '0');
+    PMGB_RET(alloc(&dev_err_, 1));
+    PMGB_CK(cudaMemsetAsync(dev_err_, 0, sizeof(int), st_));
+    if (use_tma_)
+      for (int q = 0; q < 7; ++q) PMGB_RET(make_spec_tensor_maps<T>(nm_, B_, spec_[q], &tmy_[q], &tmz_[q]));
     PMGB_CK(cudaMemcpyAsync(omega_, omega, sizeof(T) * B_ * N_, cudaMemcpyDeviceToDevice, st_));
     PMGB_RET(tables(theta));
     return PM_OK;
@@ -557,7 +582,30 @@ class Engine : public EngineBase {
   }
   // column pass over up to 4 buffers (main + side planes); side maps are offset by the
   // main length through the buffer pointers
+  int spec_index(const C* p) const {
+    for (int q = 0; q < 7; ++q)
+      if (spec_[q] == p) return q;
+    return -1;
+  }
   int cols(int n, int dir, bool zaxis, C* const* bufs, int nb) {
+    if (use_tma_ && n == nm_) {
+      CUtensorMap maps[4];
+      for (int q = 0; q < nb; ++q) {
+        const int i = spec_index(bufs[q]);
+        if (i < 0) return PM_ERR_STATE;
+        maps[q] = zaxis ? tmz_[i] : tmy_[i];
+      }
+      PMGB_RET(fft_cols_tma<T>(n, B_, dir, zaxis ? 1 : 0, maps, bufs, nb, tw_, dev_err_, nsm_, st_));
+      PMGB_CK(cudaGetLastError());
+      ColBufs<T> sb{};
+      for (int q = 0; q < nb; ++q) sb.p[q] = bufs[q] + spec_main_len(n);
+      const SeqMap ms = zaxis ? zside(n) : yside(n);
+      SeqMap none = ms;
+      none.nseq = 0;
+      PMGB_RET(fft_cols<T>(n, dir, ms, none, sb, nb, tw_, st_));
+      PMGB_CK(cudaGetLastError());
+      return PM_OK;
+    }
     ColBufs<T> m{}, s{};
     for (int q = 0; q < nb; ++q) {
       m.p[q] = bufs[q];
@@ -650,8 +698,13 @@ class Engine : public EngineBase {
     zf.coef = gcoef_;
     zf.dtab = dtab_;
     zf.batch = B_;
-    prof_.begin(st_, P_Z_FORCE, 1);
-    PMGB_RET(fft_fused_z<T>(nm_, zf, false, tw_, st_));
+    prof_.begin(st_, P_Z_FORCE, use_tma_ ? 2 : 1);
+    if (use_tma_) {
+      PMGB_RET(fft_fused_tma<T>(nm_, false, &tmz_[0], zf, tw_, dev_err_, nsm_, st_));
+      PMGB_RET(fft_fused_side<T>(nm_, zf, false, tw_, st_));
+    } else {
+      PMGB_RET(fft_fused_z<T>(nm_, zf, false, tw_, st_));
+    }
     prof_.end(st_, P_Z_FORCE);
     PMGB_CK(cudaGetLastError());
     if (pi) {
@@ -660,8 +713,14 @@ class Engine : public EngineBase {
       za.in[1] = spec_[5];
       za.in[2] = spec_[6];
       za.out[0] = spec_[0];
-      prof_.begin(st_, P_Z_ADJ, 1);
-      PMGB_RET(fft_fused_z<T>(nm_, za, true, tw_, st_));
+      prof_.begin(st_, P_Z_ADJ, use_tma_ ? 2 : 1);
+      if (use_tma_) {
+        const CUtensorMap pm3[3] = {tmz_[4], tmz_[5], tmz_[6]};
+        PMGB_RET(fft_fused_tma<T>(nm_, true, pm3, za, tw_, dev_err_, nsm_, st_));
+        PMGB_RET(fft_fused_side<T>(nm_, za, true, tw_, st_));
+      } else {
+        PMGB_RET(fft_fused_z<T>(nm_, za, true, tw_, st_));
+      }
       prof_.end(st_, P_Z_ADJ);
       PMGB_CK(cudaGetLastError());
     }
@@ -775,6 +834,10 @@ class Engine : public EngineBase {
   double *part_ = nullptr, *steps_ = nullptr, *scal_ = nullptr, *theta_out_ = nullptr;
   bool have_fwd_ = false;
   Prof prof_;
+  bool use_tma_ = false;
+  int nsm_ = 1;
+  int* dev_err_ = nullptr;
+  CUtensorMap tmy_[7], tmz_[7];
 };
 
 template <typename T>

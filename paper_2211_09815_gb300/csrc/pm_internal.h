@@ -1,5 +1,6 @@
 // Internal declarations shared by the CUDA translation units of libpmgb.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -55,6 +56,21 @@ template <typename T>
 int fft_x_c2r(int n, const RowJob<T>& job, int nbuf, int nrows, const cx_t<T>* tw, cudaStream_t st);
 template <typename T>
 int fft_fused_z(int n, const ZJob<T>& job, bool adjoint, const cx_t<T>* tw, cudaStream_t st);
+
+// TMA-staged persistent column passes over the main half spectrum (mesh sizes 128..1024).
+bool tma_supported(int n);
+template <typename T>
+int fft_cols_tma(int n, int batch, int dir, int zaxis, const CUtensorMap* maps, cx_t<T>* const* bufs, int nb,
+                 const cx_t<T>* tw, int* err, int nsm, cudaStream_t st);
+template <typename T>
+int fft_fused_tma(int n, bool adjoint, const CUtensorMap* maps, const ZJob<T>& job, const cx_t<T>* tw, int* err,
+                  int nsm, cudaStream_t st);
+// the side-plane (kx = n/2) tiles of the fused z passes only
+template <typename T>
+int fft_fused_side(int n, const ZJob<T>& job, bool adjoint, const cx_t<T>* tw, cudaStream_t st);
+// tensor maps of one spectrum buffer for the y pass (box along y) and the z pass (box along z)
+template <typename T>
+int make_spec_tensor_maps(int n, int batch, cx_t<T>* buf, CUtensorMap* ymap, CUtensorMap* zmap);
 
 // Set the dynamic shared-memory limit of a kernel once per device.
 void ensure_smem_attr(const void* fn, int bytes);

@@ -16,7 +16,8 @@ pytestmark = pytest.mark.gpu
 THETA = inputs.THETA_FIDUCIAL
 
 
-@pytest.mark.parametrize("precision,n,batch", [(1, 8, 1), (1, 16, 2), (0, 32, 1), (0, 64, 2), (1, 128, 1)])
+@pytest.mark.parametrize("precision,n,batch", [(1, 8, 1), (1, 16, 2), (0, 32, 1), (0, 64, 2), (1, 128, 1),
+                                               (0, 128, 2), (0, 256, 1)])
 def test_fft_roundtrip_matches_numpy(precision, n, batch):
     torch = torch_cuda()
     ctx, *_ = make_ctx(100.0, n, min(n, 8), 1, precision=precision, batch=batch)
@@ -72,8 +73,9 @@ def test_density_matches_oracle(precision, nm, npc):
     ctx.close()
 
 
-@pytest.mark.parametrize("precision,nm,npc", [(1, 16, 8), (0, 32, 16)])
+@pytest.mark.parametrize("precision,nm,npc", [(1, 16, 8), (0, 32, 16), (0, 128, 64), (1, 128, 32), (0, 256, 64)])
 def test_force_and_vjp_match_oracle(precision, nm, npc):
+    """Meshes of 128^3 and more take the TMA-staged persistent column and fused passes."""
     torch = torch_cuda()
     box = 40.0
     ctx, *_ = make_ctx(box, nm, npc, 1, precision=precision)
