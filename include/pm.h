@@ -52,7 +52,7 @@ typedef struct pm_ctx pm_ctx; /* opaque, library-owned */
 
 typedef struct {
   double box;       /* periodic box side L in Mpc/h, > 0 */
-  int n_mesh;       /* mesh nodes per side: power of two, 4..1024, multiple of n_ptcl */
+  int n_mesh;       /* mesh nodes per side: power of two, 8..1024, multiple of n_ptcl */
   int n_ptcl;       /* particles per side: power of two, >= 4 */
   int n_steps;      /* leapfrog steps n >= 1, scale factors linear in a (Sec. 4) */
   double a0, a1;    /* initial and final scale factor, 0 < a0 < a1 */

@@ -24,6 +24,9 @@ template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) 
 // multiply by i
 template <typename C> __device__ __forceinline__ C cmul_i(C a) { return cmake<C>(-a.y, a.x); }
 
+// four reals of one mesh cell (force components and the adjoint potential), one load
+template <typename T> struct alignas(4 * sizeof(T)) V4 { T x, y, z, w; };
+
 // Layout of one complex half spectrum of an n^3 real mesh ("spectrum buffer"):
 //   main:  [n][n][n/2] complex, kx = 0..n/2-1 along the fastest axis
 //   side:  [n][n] complex, the kx = n/2 (Nyquist) plane

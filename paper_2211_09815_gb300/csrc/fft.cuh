@@ -185,9 +185,11 @@ template <typename T, int L> struct RowTile {
   static constexpr int TR1 = TR0 > 128 ? 128 : TR0;
   static constexpr int TRMAXNT = 512 * RMAX / L;
   static constexpr int TR2 = TR1 < TRMAXNT ? TR1 : TRMAXNT;
-  static constexpr int TR = TR2 < 1 ? 1 : TR2;
+  // a tile never spans two instances: TR divides the n^2 = 4 L^2 rows of one mesh
+  static constexpr int TR3 = TR2 < 4 * L * L ? TR2 : 4 * L * L;
+  static constexpr int TR = TR3 < 1 ? 1 : TR3;
   static constexpr int NT = TR * L / RMAX;
-  static_assert(NT >= 32, "row tile needs at least one warp");
+  static_assert(NT >= 1 && TR * L % RMAX == 0, "row tile needs whole work items");
   static constexpr int LD = TR + 1;
   static constexpr int SMEM = skew_rows(L) * LD * (int)sizeof(cx_t<T>);
 };

@@ -13,4 +13,5 @@ template int fft_fused_tma<float>(int, bool, const CUtensorMap*, const ZJob<floa
                                  cudaStream_t);
 template int fft_fused_side<float>(int, const ZJob<float>&, bool, const cx_t<float>*, cudaStream_t);
 template int make_spec_tensor_maps<float>(int, int, cx_t<float>*, CUtensorMap*, CUtensorMap*);
+template int fft_x_c2r4<float>(int, const RowJob<float>&, int, V4<float>*, const cx_t<float>*, cudaStream_t);
 }  // namespace pmgb

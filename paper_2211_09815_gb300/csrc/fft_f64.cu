@@ -13,4 +13,5 @@ template int fft_fused_tma<double>(int, bool, const CUtensorMap*, const ZJob<dou
                                  cudaStream_t);
 template int fft_fused_side<double>(int, const ZJob<double>&, bool, const cx_t<double>*, cudaStream_t);
 template int make_spec_tensor_maps<double>(int, int, cx_t<double>*, CUtensorMap*, CUtensorMap*);
+template int fft_x_c2r4<double>(int, const RowJob<double>&, int, V4<double>*, const cx_t<double>*, cudaStream_t);
 }  // namespace pmgb

@@ -247,6 +247,83 @@ k_fft_x_c2r(RowJob<T> job, int nrows, const cx_t<T>* __restrict__ twL, const cx_
   }
 }
 
+// C2R x pass of four components at once, writing one V4 per cell ([cell](c0, c1, c2, c3),
+// instances back to back) so that a gather reads all components of a corner with one
+// load.  The block holds TR/4 rows of each component; a null spectrum pointer reads as 0.
+template <typename T, int L, int Q> struct C2R4Tile {
+  static constexpr int RT = RowTile<T, L>::TR / 4;       // rows per block
+  static constexpr int TR = Q * RT;                      // sequences per block
+  static constexpr int NT = TR * L / Plan<L>::RMAX;
+  static constexpr int LD = TR + 1;
+  static constexpr int SMEM = skew_rows(L) * LD * (int)sizeof(cx_t<T>);
+};
+
+template <typename T, int L, int Q>
+__global__ void __launch_bounds__(C2R4Tile<T, L, Q>::NT)
+k_fft_x_c2r4(RowJob<T> job, int nrows, V4<T>* __restrict__ out4, const cx_t<T>* __restrict__ twL,
+             const cx_t<T>* __restrict__ twN) {
+  using C = cx_t<T>;
+  using TL = C2R4Tile<T, L, Q>;
+  constexpr int N = 2 * L;
+  constexpr int RT = TL::RT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  const int r0 = blockIdx.x * RT;
+  const long long rows_per_inst = (long long)N * N;
+  constexpr int PAIRS = TL::TR * (L / 2 + 1);
+  constexpr int ITER = (PAIRS + TL::NT - 1) / TL::NT;
+  C xk[ITER], xm[ITER];
+#pragma unroll
+  for (int it = 0; it < ITER; ++it) {
+    const int idx = threadIdx.x + it * TL::NT;
+    const int c = idx / (L / 2 + 1), k = idx % (L / 2 + 1);
+    const int q = c / RT, row = c % RT;
+    const int grow = r0 + row;
+    xk[it] = cmake<C>(0, 0);
+    xm[it] = cmake<C>(0, 0);
+    if (idx < PAIRS && grow < nrows) {
+      const C* base = job.b[q].spec + (grow / rows_per_inst) * spec_len_cx(N);
+      const C* in = base + (grow % rows_per_inst) * L;
+      xk[it] = in[k];
+      xm[it] = k == 0 ? base[spec_main_len(N) + (grow % rows_per_inst)] : in[L - k];
+    }
+  }
+#pragma unroll
+  for (int it = 0; it < ITER; ++it) {
+    const int idx = threadIdx.x + it * TL::NT;
+    if (idx >= PAIRS) continue;
+    const int c = idx / (L / 2 + 1), k = idx % (L / 2 + 1);
+    C zk, zm = cmake<C>(0, 0);
+    if (k == 0) {
+      const T x0 = xk[it].x, xl = xm[it].x;
+      zk = cmake<C>(x0 + xl, x0 - xl);
+    } else {
+      const C e = cadd(xk[it], cconj(xm[it]));
+      const C d = csub(xk[it], cconj(xm[it]));
+      const C o = cmul(d, cconj(__ldg(twN + k)));
+      zk = cadd(e, cmul_i(o));
+      zm = cadd(cconj(e), cmul_i(cconj(o)));
+    }
+    sm[srow(k) * TL::LD + c] = zk;
+    if (k != 0 && k != L - k) sm[srow(L - k) * TL::LD + c] = zm;
+  }
+  __syncthreads();
+  SmemTile<C, TL::LD> t{sm};
+  fft_tile<T, L, TL::TR, TL::NT, +1>(t, t, t, twL);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < RT * L; idx += TL::NT) {
+    const int row = idx / L, j = idx % L;
+    const int grow = r0 + row;
+    if (grow >= nrows) continue;
+    const C v0 = sm[srow(j) * TL::LD + row], v1 = sm[srow(j) * TL::LD + RT + row];
+    const C v2 = sm[srow(j) * TL::LD + 2 * RT + row];
+    const C v3 = Q == 4 ? sm[srow(j) * TL::LD + (Q - 1) * RT + row] : cmake<C>(0, 0);
+    V4<T>* o = out4 + (long long)grow * N + 2 * j;
+    o[0] = V4<T>{v0.x, v1.x, v2.x, v3.x};
+    o[1] = V4<T>{v0.y, v1.y, v2.y, v3.y};
+  }
+}
+
 // ---------------------------------------------------------------- fused z passes
 // Sequence s of a z pass: main tiles s -> (b, y, kx), side tiles s -> (b, y) with kx = n/2.
 struct ZSeq {
@@ -604,6 +681,29 @@ int fft_x_r2c(int n, const RowJob<T>& job, int nbuf, int nrows, bool fixed, cons
               cudaStream_t st) {
   if (n < 4 || n > 1024) return PM_ERR_ARG;
   PMGB_DISPATCH_L(n / 2, (launch_r2c_L<T, (LL < 512 ? LL : 512)>(job, nbuf, nrows, fixed, tw, st)));
+  return PM_OK;
+}
+
+template <typename T, int L, int Q>
+static void launch_c2r4_LQ(const RowJob<T>& job, int nrows, V4<T>* out4, const cx_t<T>* tw, cudaStream_t st) {
+  using TL = C2R4Tile<T, L, Q>;
+  if constexpr (RowTile<T, L>::TR % 4 == 0 && (TL::TR * L) % Plan<L>::RMAX == 0) {
+    const size_t sm = TL::SMEM;
+    auto fn = k_fft_x_c2r4<T, L, Q>;
+    set_smem<T, L>((const void*)fn, sm);
+    fn<<<(nrows + TL::RT - 1) / TL::RT, TL::NT, sm, st>>>(job, nrows, out4, tw + L, tw + 2 * L);
+  }
+}
+template <typename T, int L>
+static void launch_c2r4_L(const RowJob<T>& job, int nrows, V4<T>* out4, const cx_t<T>* tw, cudaStream_t st) {
+  if (job.b[3].spec) launch_c2r4_LQ<T, L, 4>(job, nrows, out4, tw, st);
+  else launch_c2r4_LQ<T, L, 3>(job, nrows, out4, tw, st);
+}
+
+template <typename T>
+int fft_x_c2r4(int n, const RowJob<T>& job, int nrows, V4<T>* out4, const cx_t<T>* tw, cudaStream_t st) {
+  if (n < 8 || n > 1024) return PM_ERR_ARG;
+  PMGB_DISPATCH_L(n / 2, (launch_c2r4_L<T, (LL < 512 ? LL : 512)>(job, nrows, out4, tw, st)));
   return PM_OK;
 }
 

@@ -34,7 +34,7 @@ static bool pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
 static int validate(const pm_config* c, const double* theta) {
   if (!c || !theta) return PM_ERR_ARG;
   if (!(c->box > 0) || !std::isfinite(c->box)) return PM_ERR_ARG;
-  if (!pow2(c->n_mesh) || !pow2(c->n_ptcl) || c->n_ptcl < 4 || c->n_mesh < 4 || c->n_mesh > 1024) return PM_ERR_ARG;
+  if (!pow2(c->n_mesh) || !pow2(c->n_ptcl) || c->n_ptcl < 4 || c->n_mesh < 8 || c->n_mesh > 1024) return PM_ERR_ARG;
   if (c->n_mesh % c->n_ptcl != 0) return PM_ERR_ARG;
   if (c->n_steps < 1 || c->batch < 1 || c->ckpt_every < 0) return PM_ERR_ARG;
   if (!(c->a0 > 0) || !(c->a1 > c->a0) || !std::isfinite(c->a1)) return PM_ERR_ARG;

@@ -154,6 +154,7 @@ class Engine : public EngineBase {
     acc_[0] = accq_;
     for (int q = 0; q < 7; ++q) PMGB_RET(alloc(&spec_[q], sl));
     PMGB_RET(alloc(&dens_, (long long)B_ * M_));
+    PMGB_RET(alloc(&fvec_, (long long)B_ * M_));
     if (cfg->ckpt_every > 0) {
       nck_ = (n_ + cfg->ckpt_every - 1) / cfg->ckpt_every;
       PMGB_RET(alloc(&ck_s_, pv * nck_));
@@ -191,8 +192,8 @@ class Engine : public EngineBase {
       const long long fis = 2 * spec_len_cx(nm_);
       StepCoef<T> sc{fkA_, fkB_, fdr_};
       prof_.begin(st_, P_GATHER_FWD, 1);
-      k_gather_fwd<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(
-          geo_, s_, p_, j == n_ ? a_ : nullptr, rmesh(1), rmesh(2), rmesh(3), fis, sc, j, n_ + 1, cks, ckp);
+      k_gather_fwd<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, s_, p_, j == n_ ? a_ : nullptr, fvec_, sc, j,
+                                                              n_ + 1, cks, ckp);
       prof_.end(st_, P_GATHER_FWD);
       PMGB_CK(cudaGetLastError());
     }
@@ -255,9 +256,8 @@ class Engine : public EngineBase {
       double* ppa = part_ + (long long)(2 * j) * B_ * G_;
       double* pxp = part_ + (long long)(2 * j + 1) * B_ * G_;
       prof_.begin(st_, P_GATHER_ADJ, 1);
-      k_gather_adj<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(
-          geo_, mass_, s_, p_, xi_, pi_, nullptr, nullptr, rmesh(1), rmesh(2), rmesh(3), rmesh(0), fis, sc, j,
-          n_ + 1, ckp, cks, ppa, pxp, pimax_);
+      k_gather_adj<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, mass_, s_, p_, xi_, pi_, nullptr, nullptr, fvec_,
+                                                              sc, j, n_ + 1, ckp, cks, ppa, pxp, pimax_);
       prof_.end(st_, P_GATHER_ADJ);
       PMGB_CK(cudaGetLastError());
     }
@@ -310,8 +310,8 @@ class Engine : public EngineBase {
     StepCoef<T> sc{zero_, zero_, zero_};
     if (!pi) {
       PMGB_RET(force_chain(s_, nullptr, false));
-      k_gather_fwd<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, s_, p_, (T*)acc, rmesh(1), rmesh(2),
-                                                              rmesh(3), fis, sc, 0, 1, nullptr, nullptr);
+      k_gather_fwd<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, s_, p_, (T*)acc, fvec_, sc, 0, 1, nullptr,
+                                                              nullptr);
     } else {
       PMGB_CK(cudaMemcpyAsync(pi_, pi, sizeof(T) * B_ * 3 * N_, cudaMemcpyDeviceToDevice, st_));
       PMGB_CK(cudaMemsetAsync(pimax_, 0, sizeof(unsigned) * 3 * B_, st_));
@@ -321,8 +321,8 @@ class Engine : public EngineBase {
                                                                 xi_, pi_, pimax_);
       PMGB_RET(force_chain(s_, pi_, false));
       k_gather_adj<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, mass_, s_, p_, xi_, pi_, (T*)acc, (T*)alpha,
-                                                              rmesh(1), rmesh(2), rmesh(3), rmesh(0), fis, sc, 0, 1,
-                                                              nullptr, nullptr, nullptr, nullptr, nullptr);
+                                                              fvec_, sc, 0, 1, nullptr, nullptr, nullptr, nullptr,
+                                                              nullptr);
     }
     PMGB_CK(cudaGetLastError());
     return PM_OK;
@@ -728,10 +728,11 @@ class Engine : public EngineBase {
     prof_.begin(st_, P_COLS, 2);
     PMGB_RET(cols(nm_, +1, false, invb, nb == 4 ? 4 : 3));
     prof_.end(st_, P_COLS);
+    // C2R of f_0..2 (and psi) into one interleaved [cell][4] mesh for the gathers
     RowJob<T> jc{};
-    for (int q = 0; q < (pi ? 4 : 3); ++q) jc.b[q] = RowBuf<T>{invb[q], 2 * spec_len_cx(nm_), invb[q], nullptr, 0, (T)1, (T)0, 0, 1};
+    for (int q = 0; q < 4; ++q) jc.b[q] = RowBuf<T>{nullptr, 0, (q < 3 || pi) ? invb[q] : nullptr, nullptr, 0, (T)1, (T)0, 0, 1};
     prof_.begin(st_, P_X_C2R, 1);
-    PMGB_RET(fft_x_c2r<T>(nm_, jc, pi ? 4 : 3, B_ * nm_ * nm_, tw_, st_));
+    PMGB_RET(fft_x_c2r4<T>(nm_, jc, B_ * nm_ * nm_, reinterpret_cast<V4<T>*>(fvec_), tw_, st_));
     prof_.end(st_, P_X_C2R);
     PMGB_CK(cudaGetLastError());
     return PM_OK;
@@ -823,6 +824,7 @@ class Engine : public EngineBase {
   long long* accq_ = nullptr;
   C* spec_[7] = {};
   T* dens_ = nullptr;
+  V4<T>* fvec_ = nullptr;
   T *ck_s_ = nullptr, *ck_p_ = nullptr;
   T *fkA_ = nullptr, *fkB_ = nullptr, *fdr_ = nullptr, *rkA_ = nullptr, *rkB_ = nullptr, *rdr_ = nullptr;
   double *wpa_ = nullptr, *wxp_ = nullptr, *dd1_ = nullptr, *dgd_ = nullptr;

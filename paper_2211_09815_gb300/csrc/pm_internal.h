@@ -54,6 +54,9 @@ int fft_x_r2c(int n, const RowJob<T>& job, int nbuf, int nrows, bool fixed, cons
               cudaStream_t st);
 template <typename T>
 int fft_x_c2r(int n, const RowJob<T>& job, int nbuf, int nrows, const cx_t<T>* tw, cudaStream_t st);
+// C2R of up to four components into one interleaved [cell][4] real mesh
+template <typename T>
+int fft_x_c2r4(int n, const RowJob<T>& job, int nrows, V4<T>* out4, const cx_t<T>* tw, cudaStream_t st);
 template <typename T>
 int fft_fused_z(int n, const ZJob<T>& job, bool adjoint, const cx_t<T>* tw, cudaStream_t st);
 

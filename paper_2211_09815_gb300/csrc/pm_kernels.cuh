@@ -81,6 +81,19 @@ __device__ __forceinline__ float block_max(float v, float* sh) {
   return r;
 }
 
+// Per-thread partial sums of the theta terms: compensated (Kahan) summation in the working
+// precision, handed to the FP64 block reduction; FP64 arithmetic is slow on this part.
+template <typename T> struct KahanAcc {
+  T s = 0, c = 0;
+  __device__ __forceinline__ void add(T v) {
+    const T y = v - c;
+    const T t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 template <typename T> __device__ __forceinline__ float abs_up(T v);
 template <> __device__ __forceinline__ float abs_up<float>(float v) { return fabsf(v); }
 template <> __device__ __forceinline__ float abs_up<double>(double v) { return __double2float_ru(fabs(v)); }
@@ -159,26 +172,29 @@ struct StepCoef {  // per-instance coefficient tables [batch][n+1], indexed at s
 template <typename T>
 __global__ void __launch_bounds__(kPtclThreads)
 k_gather_fwd(Geo<T> g, T* __restrict__ s, T* __restrict__ p, T* __restrict__ a_out,
-             const T* __restrict__ f0, const T* __restrict__ f1, const T* __restrict__ f2, long long fis,
-             StepCoef<T> sc, int j, int nstep1, T* __restrict__ ck_s, T* __restrict__ ck_p) {
+             const V4<T>* __restrict__ fvec, StepCoef<T> sc, int j, int nstep1, T* __restrict__ ck_s,
+             T* __restrict__ ck_p) {
   const int b = blockIdx.y;
   const T kA = sc.kA[b * nstep1 + j], kB = sc.kB[b * nstep1 + j], dr = sc.dr[b * nstep1 + j];
   T* sb = s + (long long)b * 3 * g.N;
   T* pb = p + (long long)b * 3 * g.N;
-  const T* F[3] = {f0 + b * fis, f1 + b * fis, f2 + b * fis};
+  const V4<T>* F = fvec + (long long)b * g.M;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
        i += (long long)gridDim.x * blockDim.x) {
     T sv[3] = {sb[i], sb[g.N + i], sb[2 * g.N + i]};
     int cell[3];
     T t[3];
     cic_cell(g, i, sv, cell, t);
+    V4<T> fv[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) fv[d] = F[corner_index(g, cell, d)];
     T a[3] = {0, 0, 0};
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
       const T w = ((d & 4) ? t[0] : (T)1 - t[0]) * ((d & 2) ? t[1] : (T)1 - t[1]) * ((d & 1) ? t[2] : (T)1 - t[2]);
-      const long long idx = corner_index(g, cell, d);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) a[c] += w * __ldg(F[c] + idx);
+      a[0] += w * fv[d].x;
+      a[1] += w * fv[d].y;
+      a[2] += w * fv[d].z;
     }
     T pv[3] = {pb[i], pb[g.N + i], pb[2 * g.N + i]};
 #pragma unroll
@@ -201,9 +217,8 @@ k_gather_fwd(Geo<T> g, T* __restrict__ s, T* __restrict__ p, T* __restrict__ a_o
 template <typename T>
 __global__ void __launch_bounds__(kPtclThreads)
 k_gather_adj(Geo<T> g, T mass, T* __restrict__ s, T* __restrict__ p, T* __restrict__ xi, T* __restrict__ pi,
-             T* __restrict__ a_out, T* __restrict__ alpha_out,
-             const T* __restrict__ f0, const T* __restrict__ f1, const T* __restrict__ f2,
-             const T* __restrict__ psi, long long fis, StepCoef<T> sc, int j, int nstep1,
+             T* __restrict__ a_out, T* __restrict__ alpha_out, const V4<T>* __restrict__ fvec,
+             StepCoef<T> sc, int j, int nstep1,
              const T* __restrict__ ck_p, const T* __restrict__ ck_s, double* __restrict__ part_pa,
              double* __restrict__ part_xp, unsigned* __restrict__ pimax) {
   __shared__ double shd[kPtclThreads / 32];
@@ -211,10 +226,9 @@ k_gather_adj(Geo<T> g, T mass, T* __restrict__ s, T* __restrict__ p, T* __restri
   const int b = blockIdx.y;
   const T cA = sc.kA[b * nstep1 + j], cB = sc.kB[b * nstep1 + j], dr = sc.dr[b * nstep1 + j];
   const long long po = (long long)b * 3 * g.N;
-  const T* F[3] = {f0 + b * fis, f1 + b * fis, f2 + b * fis};
-  const T* PS = psi + b * fis;
+  const V4<T>* F = fvec + (long long)b * g.M;
   const T il = g.inv_l;
-  double acc_pa = 0.0, acc_xp = 0.0;
+  KahanAcc<T> acc_pa, acc_xp;
   float mx[3] = {0.f, 0.f, 0.f};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
        i += (long long)gridDim.x * blockDim.x) {
@@ -229,6 +243,9 @@ k_gather_adj(Geo<T> g, T mass, T* __restrict__ s, T* __restrict__ p, T* __restri
     int cell[3];
     T t[3];
     cic_cell(g, i, sv, cell, t);
+    V4<T> fv[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) fv[d] = F[corner_index(g, cell, d)];
     T a[3] = {0, 0, 0}, al[3] = {0, 0, 0};
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
@@ -236,17 +253,16 @@ k_gather_adj(Geo<T> g, T mass, T* __restrict__ s, T* __restrict__ p, T* __restri
       const T w1 = (d & 2) ? t[1] : (T)1 - t[1];
       const T w2 = (d & 1) ? t[2] : (T)1 - t[2];
       const T g0 = (d & 4) ? il : -il, g1 = (d & 2) ? il : -il, g2 = (d & 1) ? il : -il;
-      const long long idx = corner_index(g, cell, d);
-      const T fv[3] = {__ldg(F[0] + idx), __ldg(F[1] + idx), __ldg(F[2] + idx)};
-      const T h = qv[0] * fv[0] + qv[1] * fv[1] + qv[2] * fv[2] + mass * __ldg(PS + idx);
+      const T h = qv[0] * fv[d].x + qv[1] * fv[d].y + qv[2] * fv[d].z + mass * fv[d].w;
       const T w = w0 * w1 * w2;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) a[c] += w * fv[c];
+      a[0] += w * fv[d].x;
+      a[1] += w * fv[d].y;
+      a[2] += w * fv[d].z;
       al[0] += g0 * w1 * w2 * h;
       al[1] += w0 * g1 * w2 * h;
       al[2] += w0 * w1 * g2 * h;
     }
-    acc_pa += (double)qv[0] * a[0] + (double)qv[1] * a[1] + (double)qv[2] * a[2];
+    acc_pa.add(qv[0] * a[0] + qv[1] * a[1] + qv[2] * a[2]);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       pv[c] -= a[c] * cA;
@@ -255,7 +271,7 @@ k_gather_adj(Geo<T> g, T mass, T* __restrict__ s, T* __restrict__ p, T* __restri
       pv[c] -= a[c] * cB;
       xv[c] += al[c] * cB;
     }
-    acc_xp += (double)xv[0] * pv[0] + (double)xv[1] * pv[1] + (double)xv[2] * pv[2];
+    acc_xp.add(xv[0] * pv[0] + xv[1] * pv[1] + xv[2] * pv[2]);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       sv[c] -= pv[c] * dr;
@@ -270,8 +286,8 @@ k_gather_adj(Geo<T> g, T mass, T* __restrict__ s, T* __restrict__ p, T* __restri
       if (alpha_out) alpha_out[po + c * g.N + i] = al[c];
     }
   }
-  const double spa = block_sum(acc_pa, shd);
-  const double sxp = block_sum(acc_xp, shd);
+  const double spa = block_sum(acc_pa.value(), shd);
+  const double sxp = block_sum(acc_xp.value(), shd);
   if (threadIdx.x == 0 && part_pa) {
     part_pa[(long long)b * gridDim.x + blockIdx.x] = spa;
     part_xp[(long long)b * gridDim.x + blockIdx.x] = sxp;
