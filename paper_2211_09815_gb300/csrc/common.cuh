@@ -24,6 +24,43 @@ template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) 
 // multiply by i
 template <typename C> __device__ __forceinline__ C cmul_i(C a) { return cmake<C>(-a.y, a.x); }
 
+// Integer <-> float conversions of the fixed-point accumulators on the integer ALU
+// (correctly rounded, nearest-even): the hardware conversions involving 64-bit integers go
+// through the FP64 pipe, which is slow on this part.
+__device__ __forceinline__ float ll2f_rn(long long a) {
+  if (a == 0) return 0.0f;
+  const unsigned long long ua = a < 0 ? 0ull - (unsigned long long)a : (unsigned long long)a;
+  const int lz = __clzll(ua);
+  const unsigned long long m = ua << lz;                 // leading one at bit 63
+  unsigned mant = (unsigned)(m >> 40);                   // 24 significant bits
+  const unsigned long long rest = m & 0xFFFFFFFFFFull;    // the 40 bits shifted out
+  if (rest > 0x8000000000ull || (rest == 0x8000000000ull && (mant & 1u))) ++mant;
+  int e = 63 - lz + 127;
+  if (mant == (1u << 24)) {
+    mant >>= 1;
+    ++e;
+  }
+  return __uint_as_float(((unsigned)e << 23) | (mant & 0x7FFFFFu) | (a < 0 ? 0x80000000u : 0u));
+}
+// |v| < 2^62
+__device__ __forceinline__ long long f2ll_rn(float v) {
+  const unsigned b = __float_as_uint(v);
+  const int e = (int)((b >> 23) & 0xFFu);
+  if (e < 126) return 0;                                 // |v| < 0.5
+  const unsigned long long mant = (b & 0x7FFFFFu) | 0x800000u;
+  const int sh = e - 150;                                // v = mant * 2^sh
+  unsigned long long r;
+  if (sh >= 0) {
+    r = mant << sh;
+  } else {
+    const int rs = -sh;                                  // 1..24
+    r = mant >> rs;
+    const unsigned long long rem = mant & ((1ull << rs) - 1), half = 1ull << (rs - 1);
+    if (rem > half || (rem == half && (r & 1ull))) ++r;
+  }
+  return (b >> 31) ? -(long long)r : (long long)r;
+}
+
 // four reals of one mesh cell (force components and the adjoint potential), one load
 template <typename T> struct alignas(4 * sizeof(T)) V4 { T x, y, z, w; };
 

@@ -41,6 +41,31 @@ __device__ __forceinline__ void cic_cell(const Geo<T>& g, long long i, const T s
   }
 }
 
+// Work index -> lattice particle index: 8^3 Lagrangian blocks (x fastest inside a block,
+// so a warp reads 8 x 4 particles in full 32-byte segments) visited in Morton order of the
+// block coordinates, so that the particles in flight at any moment -- and the mesh cells
+// they scatter to or gather from -- form a compact region that stays in L2.
+__device__ __forceinline__ unsigned long long morton_compact3(unsigned long long x) {
+  x &= 0x1249249249249249ull;
+  x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+  x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+  x = (x ^ (x >> 8)) & 0x1f0000ff0000ffull;
+  x = (x ^ (x >> 16)) & 0x1f00000000ffffull;
+  x = (x ^ (x >> 32)) & 0x1fffffull;
+  return x;
+}
+template <typename T>
+__device__ __forceinline__ long long particle_of(const Geo<T>& g, long long w) {
+  const int tb = g.lg_np < 3 ? g.lg_np : 3;                 // block side 2^tb
+  const long long inner = w & ((1LL << (3 * tb)) - 1);
+  const unsigned long long blk = (unsigned long long)(w >> (3 * tb));
+  const int mask = (1 << tb) - 1;
+  const long long x = ((long long)morton_compact3(blk) << tb) | (inner & mask);
+  const long long y = ((long long)morton_compact3(blk >> 1) << tb) | ((inner >> tb) & mask);
+  const long long z = ((long long)morton_compact3(blk >> 2) << tb) | (inner >> (2 * tb));
+  return (z << (2 * g.lg_np)) | (y << g.lg_np) | x;
+}
+
 template <typename T>
 __device__ __forceinline__ long long corner_index(const Geo<T>& g, const int cell[3], int d) {
   const int m = g.nm - 1;
@@ -51,7 +76,7 @@ __device__ __forceinline__ long long corner_index(const Geo<T>& g, const int cel
 }
 
 template <typename T> __device__ __forceinline__ long long to_fixed(T v);
-template <> __device__ __forceinline__ long long to_fixed<float>(float v) { return __float2ll_rn(v); }
+template <> __device__ __forceinline__ long long to_fixed<float>(float v) { return f2ll_rn(v); }
 template <> __device__ __forceinline__ long long to_fixed<double>(double v) { return __double2ll_rn(v); }
 
 // Deterministic block sum of one double per thread (fixed shuffle tree + fixed warp order).
@@ -116,8 +141,9 @@ k_scatter(Geo<T> g, const T* __restrict__ s, const T* __restrict__ pi, unsigned 
 #pragma unroll
     for (int c = 0; c < 3; ++c) sp[c] = (T)ldexp(1.0, e_pi[c * gridDim.y + b]);
   }
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
-       i += (long long)gridDim.x * blockDim.x) {
+  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < g.N;
+       w += (long long)gridDim.x * blockDim.x) {
+    const long long i = particle_of(g, w);
     const T sv[3] = {sb[i], sb[g.N + i], sb[2 * g.N + i]};
     int cell[3];
     T t[3];
@@ -179,8 +205,9 @@ k_gather_fwd(Geo<T> g, T* __restrict__ s, T* __restrict__ p, T* __restrict__ a_o
   T* sb = s + (long long)b * 3 * g.N;
   T* pb = p + (long long)b * 3 * g.N;
   const V4<T>* F = fvec + (long long)b * g.M;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
-       i += (long long)gridDim.x * blockDim.x) {
+  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < g.N;
+       w += (long long)gridDim.x * blockDim.x) {
+    const long long i = particle_of(g, w);
     T sv[3] = {sb[i], sb[g.N + i], sb[2 * g.N + i]};
     int cell[3];
     T t[3];
@@ -230,8 +257,9 @@ k_gather_adj(Geo<T> g, T mass, T* __restrict__ s, T* __restrict__ p, T* __restri
   const T il = g.inv_l;
   KahanAcc<T> acc_pa, acc_xp;
   float mx[3] = {0.f, 0.f, 0.f};
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
-       i += (long long)gridDim.x * blockDim.x) {
+  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < g.N;
+       w += (long long)gridDim.x * blockDim.x) {
+    const long long i = particle_of(g, w);
     T sv[3], pv[3], xv[3], qv[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
