@@ -46,7 +46,7 @@ k_fft_cols(const SeqMap mm, const SeqMap ms, int ntiles_main, ColBufs<T> bufs,
 // ---------------------------------------------------------------- x pass, R2C
 // int64 fixed point -> real without the FP64 pipe (slow on this part) for float.
 template <typename T> __device__ __forceinline__ T fix2real(long long a);
-template <> __device__ __forceinline__ float fix2real<float>(long long a) { return ll2f_rn(a); }
+template <> __device__ __forceinline__ float fix2real<float>(long long a) { return (float)a; }
 template <> __device__ __forceinline__ double fix2real<double>(long long a) { return (double)a; }
 
 // rows of n = 2L reals -> L complex (main) + 1 (side).  The input is an int64 fixed-point
