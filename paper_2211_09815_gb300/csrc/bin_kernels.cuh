@@ -1,0 +1,336 @@
+// Deterministic CIC assignment without global atomics on the mesh ("owner computes").
+//
+// Every step the particles are binned by the mesh tile that holds their cell (tiles of
+// tx x ty x tz cells, x = array axis 2 fastest).  A bin is a tile and a class of three
+// bits telling whether the cell lies on the tile's last layer along x, y, z: only those
+// particles' CIC clouds reach into the next tile.  One CTA per tile then pulls the
+// particles of its own bins and the reaching classes of its seven lower neighbours, and
+// sums the weights (and in the adjoint pi_c times the weights) of the corners that land
+// in its tile in 64-bit fixed point in shared memory.  Every contribution is rounded to
+// fixed point on its own, exactly as in a global fixed-point deposit, so the sums are
+// exact and independent of the order of the particles.  The CTA then writes the real
+// meshes (delta and pi_c) once, in the working precision.
+//
+// Binning: a count (warp-aggregated integer atomics on an L2-resident array), an
+// exclusive scan, and a fill.
+#pragma once
+#include "pm_kernels.cuh"
+
+namespace pmgb {
+
+struct BinGeo {
+  int lx, ly, lz;       // log2 of the tile extent along axes 2, 1, 0
+  int ntx, nty, ntz;    // tiles per axis
+  int ntiles;           // per instance
+  long long nkeys;      // bins per instance = 8 ntiles
+};
+
+inline BinGeo make_bin_geo(int lg_nm, int lx, int ly, int lz) {
+  BinGeo b;
+  b.lx = lx < lg_nm ? lx : lg_nm;
+  b.ly = ly < lg_nm ? ly : lg_nm;
+  b.lz = lz < lg_nm ? lz : lg_nm;
+  b.ntx = 1 << (lg_nm - b.lx);
+  b.nty = 1 << (lg_nm - b.ly);
+  b.ntz = 1 << (lg_nm - b.lz);
+  b.ntiles = b.ntx * b.nty * b.ntz;
+  b.nkeys = 8LL * b.ntiles;
+  return b;
+}
+
+// class bits of a cell: on the last layer of its tile along x (bit 0), y (bit 1), z (bit 2)
+__device__ __forceinline__ unsigned bin_class(const BinGeo& bg, const int c[3]) {
+  const unsigned mx = (1u << bg.lx) - 1, my = (1u << bg.ly) - 1, mz = (1u << bg.lz) - 1;
+  return (unsigned)(((unsigned)c[2] & mx) == mx) | ((unsigned)(((unsigned)c[1] & my) == my) << 1) |
+         ((unsigned)(((unsigned)c[0] & mz) == mz) << 2);
+}
+__device__ __forceinline__ unsigned bin_key(const BinGeo& bg, const int c[3]) {
+  const unsigned tile = (((unsigned)c[0] >> bg.lz) * bg.nty + ((unsigned)c[1] >> bg.ly)) * bg.ntx + ((unsigned)c[2] >> bg.lx);
+  return tile * 8u + bin_class(bg, c);
+}
+
+// Warp-uniform loop over the work indices of this block's warps: every lane of a warp
+// takes the same number of iterations, so that the warp-wide match below sees all lanes.
+template <typename T>
+__global__ void __launch_bounds__(kPtclThreads)
+k_bin_count(Geo<T> g, BinGeo bg, const T* __restrict__ s, unsigned* __restrict__ count, unsigned* __restrict__ keys) {
+  const int b = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const T* sb = s + (long long)b * 3 * g.N;
+  unsigned* cb = count + (long long)b * bg.nkeys;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long w0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); w0 < g.N; w0 += stride) {
+    const long long w = w0 + lane;
+    const bool valid = w < g.N;
+    unsigned key = 0xFFFFFFFFu;
+    if (valid) {
+      const long long i = particle_of(g, w);
+      const T sv[3] = {sb[i], sb[g.N + i], sb[2 * g.N + i]};
+      int cell[3];
+      T t[3];
+      cic_cell(g, i, sv, cell, t);
+      key = bin_key(bg, cell);
+      keys[(long long)b * g.N + i] = key;
+    }
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+    if (valid && lane == __ffs(peers) - 1) atomicAdd(cb + key, (unsigned)__popc(peers));
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPtclThreads)
+k_bin_fill(Geo<T> g, BinGeo bg, const unsigned* __restrict__ keys, unsigned* __restrict__ cursor,
+           unsigned* __restrict__ list) {
+  const int b = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  unsigned* cb = cursor + (long long)b * bg.nkeys;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long w0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); w0 < g.N; w0 += stride) {
+    const long long w = w0 + lane;
+    const bool valid = w < g.N;
+    unsigned key = 0xFFFFFFFFu;
+    long long i = 0;
+    if (valid) {
+      i = particle_of(g, w);
+      key = keys[(long long)b * g.N + i];
+    }
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+    const int leader = __ffs(peers) - 1;
+    unsigned pos = 0;
+    if (valid && lane == leader) pos = atomicAdd(cb + key, (unsigned)__popc(peers));
+    pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
+    if (valid) list[pos + __popc(peers & ((1u << lane) - 1u))] = (unsigned)i;
+  }
+}
+
+// Exclusive scan of n counts in three launches: blocks of 2048 elements, the block totals
+// (one block), the add-back.  The scan also clears the counts for the next binning and
+// initialises the fill cursors.
+constexpr int kScanBlock = 2048;
+__device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* sh, unsigned* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;   // 256 threads
+  unsigned x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    unsigned t = lane < 8 ? sh[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xFFFFFFFFu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < 8) sh[lane] = t;
+  }
+  __syncthreads();
+  const unsigned base = w > 0 ? sh[w - 1] : 0u;
+  *total = sh[7];
+  __syncthreads();
+  return base + x - v;
+}
+
+static __global__ void __launch_bounds__(256) k_scan_blocks(unsigned* __restrict__ count, unsigned* __restrict__ start,
+                                                            unsigned* __restrict__ sums, long long n) {
+  __shared__ unsigned sh[8];
+  const long long base = (long long)blockIdx.x * kScanBlock + threadIdx.x * 8;
+  unsigned v[8], tsum = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    v[k] = base + k < n ? count[base + k] : 0u;
+    tsum += v[k];
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (base + k < n) count[base + k] = 0u;
+  unsigned total;
+  unsigned run = block_excl_scan(tsum, sh, &total);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (base + k < n) start[base + k] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+static __global__ void __launch_bounds__(256) k_scan_sums(unsigned* __restrict__ sums, int nblocks) {
+  __shared__ unsigned sh[8];
+  unsigned carry = 0;
+  for (int first = 0; first < nblocks; first += kScanBlock) {
+    const int base = first + threadIdx.x * 8;
+    unsigned v[8], tsum = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      v[k] = base + k < nblocks ? sums[base + k] : 0u;
+      tsum += v[k];
+    }
+    unsigned total;
+    unsigned run = carry + block_excl_scan(tsum, sh, &total);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (base + k < nblocks) sums[base + k] = run;
+      run += v[k];
+    }
+    carry += total;
+  }
+}
+
+static __global__ void k_scan_add(unsigned* __restrict__ start, unsigned* __restrict__ cursor,
+                                  const unsigned* __restrict__ sums, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const unsigned v = start[i] + sums[i / kScanBlock];
+    start[i] = v;
+    cursor[i] = v;
+  }
+}
+
+// The 20 particle ranges a tile pulls: (offset d of the source tile below, first class).
+// d = 0: the tile's own 8 bins as one range; d != 0: each class containing the bits of d,
+// one bin each.  Packed 3 bits per range.
+constexpr unsigned long long pack3(const int (&v)[20]) {
+  unsigned long long r = 0;
+  for (int k = 0; k < 20; ++k) r |= (unsigned long long)v[k] << (3 * k);
+  return r;
+}
+constexpr int kRangeDv[20] = {0, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 4, 4, 4, 4, 5, 5, 6, 6, 7};
+constexpr int kRangeCv[20] = {0, 1, 3, 5, 7, 2, 3, 6, 7, 3, 7, 4, 5, 6, 7, 5, 7, 6, 7, 7};
+constexpr unsigned long long kRangeD = pack3(kRangeDv);
+constexpr unsigned long long kRangeC = pack3(kRangeCv);
+
+// Exact 64-bit addition into a shared accumulator kept as two 32-bit words: the low word
+// takes a native 32-bit atomic add whose returned old value gives the carry, the high word
+// the high part plus that carry.  Each addition is exact mod 2^64, so the final pair holds
+// the exact sum in any order (64-bit shared atomics are several times slower).
+__device__ __forceinline__ void smem_add64(unsigned* lo, unsigned* hi, unsigned vl, unsigned vh) {
+  const unsigned old = atomicAdd(lo, vl);
+  const unsigned h = vh + (old + vl < old ? 1u : 0u);
+  if (h) atomicAdd(hi, h);
+}
+// the exact sum (two words) in the working precision, correctly rounded; sums that fit in
+// 32 bits take one hardware conversion
+template <typename T> __device__ __forceinline__ T words_to_real(unsigned lo, unsigned hi);
+template <> __device__ __forceinline__ float words_to_real<float>(unsigned lo, unsigned hi) {
+  if (hi == 0u) return __uint2float_rn(lo);
+  if (hi == 0xFFFFFFFFu && (lo >> 31)) return __int2float_rn((int)lo);
+  return ll2f_rn((long long)(((unsigned long long)hi << 32) | lo));
+}
+template <> __device__ __forceinline__ double words_to_real<double>(unsigned lo, unsigned hi) {
+  return (double)(long long)(((unsigned long long)hi << 32) | lo);
+}
+
+// One CTA per tile (grid: tiles x instances).  NQ = 1: delta; NQ = 4: delta and the three
+// pi sums.  Outputs: delta = m acc 2^-e_d - 1 into dout (instance stride dis), pi_c =
+// acc 2^-e_c into p0..p2 (instance stride pis).  Dynamic shared memory: NQ * cells * 8 B
+// (low words [NQ][cells], then high words [NQ][cells]).
+template <typename T, int NQ, int NT>
+__global__ void __launch_bounds__(NT, NT >= 512 ? 3 : 1)
+k_pull_scatter(Geo<T> g, BinGeo bg, const T* __restrict__ s, const T* __restrict__ pi,
+               const unsigned* __restrict__ start, const unsigned* __restrict__ list, int e_d,
+               const int* __restrict__ e_pi, T mass, T* __restrict__ dout, long long dis, T* __restrict__ p0,
+               T* __restrict__ p1, T* __restrict__ p2, long long pis) {
+  extern __shared__ __align__(16) unsigned acc[];   // [2][NQ][cells]
+  __shared__ unsigned rbeg[20], rpre[21];
+  const int b = blockIdx.y;
+  const int tile = blockIdx.x;
+  const int T2 = tile & (bg.ntx - 1), T1 = (tile / bg.ntx) & (bg.nty - 1), T0 = tile / (bg.ntx * bg.nty);
+  const int cells = 1 << (bg.lx + bg.ly + bg.lz);
+  for (int k = threadIdx.x; k < NQ * cells / 2; k += blockDim.x) reinterpret_cast<uint4*>(acc)[k] = make_uint4(0, 0, 0, 0);
+  unsigned* hacc = acc + NQ * cells;
+  if (threadIdx.x < 32) {
+    const int r = threadIdx.x;   // one lane per range
+    unsigned len = 0;
+    if (r < 20) {
+      const int d = (int)((kRangeD >> (3 * r)) & 7u), c0 = (int)((kRangeC >> (3 * r)) & 7u);
+      const int S2 = (T2 - (d & 1)) & (bg.ntx - 1);
+      const int S1 = (T1 - ((d >> 1) & 1)) & (bg.nty - 1);
+      const int S0 = (T0 - ((d >> 2) & 1)) & (bg.ntz - 1);
+      const long long key0 = (long long)b * bg.nkeys + ((long long)(S0 * bg.nty + S1) * bg.ntx + S2) * 8 + c0;
+      const unsigned a = start[key0], e = start[key0 + (d == 0 ? 8 : 1)];
+      rbeg[r] = a;
+      len = e - a;
+    }
+    unsigned x = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (r >= o) x += y;
+    }
+    if (r < 21) rpre[r] = x - len;   // exclusive prefix; rpre[20] = total
+  }
+  __syncthreads();
+  const T* sb = s + (long long)b * 3 * g.N;
+  const T* pb = nullptr;
+  const T sd = pow2i<T>(e_d);
+  T sp[3] = {0, 0, 0};
+  if constexpr (NQ == 4) {
+    pb = pi + (long long)b * 3 * g.N;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) sp[c] = pow2i<T>(e_pi[c * gridDim.y + b]);
+  }
+  const unsigned total = rpre[20];
+  const unsigned mx = (1u << bg.lx) - 1, my = (1u << bg.ly) - 1, mz = (1u << bg.lz) - 1;
+  for (unsigned f = threadIdx.x; f < total; f += blockDim.x) {
+    int r = 0;
+    while (f >= rpre[r + 1]) ++r;
+    const unsigned d = (unsigned)((kRangeD >> (3 * r)) & 7u);
+    const long long i = list[rbeg[r] + (f - rpre[r])];
+    const T sv[3] = {sb[i], sb[g.N + i], sb[2 * g.N + i]};
+    int cell[3];
+    T t[3];
+    cic_cell(g, i, sv, cell, t);
+    const unsigned cls = bin_class(bg, cell);
+    T pv[3] = {0, 0, 0};
+    if constexpr (NQ == 4) {
+      pv[0] = pb[i] * sp[0];
+      pv[1] = pb[g.N + i] * sp[1];
+      pv[2] = pb[2 * g.N + i] * sp[2];
+    }
+    const int l0 = (int)((unsigned)cell[0] & mz), l1 = (int)((unsigned)cell[1] & my), l2 = (int)((unsigned)cell[2] & mx);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      // corner e (bit 2: axis 0, bit 1: axis 1, bit 0: axis 2) crosses into the next tile
+      // along an axis iff the cell is on the tile's last layer there and the corner is the
+      // upper one; it lands in this CTA's tile iff those crossings equal d
+      const unsigned carry = cls & (unsigned)e;
+      if (carry != d) continue;
+      const int a0 = (d & 4u) ? 0 : l0 + ((e >> 2) & 1);
+      const int a1 = (d & 2u) ? 0 : l1 + ((e >> 1) & 1);
+      const int a2 = (d & 1u) ? 0 : l2 + (e & 1);
+      const int loc = (((a0 << bg.ly) + a1) << bg.lx) + a2;
+      const T w = ((e & 4) ? t[0] : (T)1 - t[0]) * ((e & 2) ? t[1] : (T)1 - t[1]) * ((e & 1) ? t[2] : (T)1 - t[2]);
+      unsigned vl, vh;
+      fixed_words<T>(w * sd, vl, vh);
+      smem_add64(acc + loc, hacc + loc, vl, vh);
+      if constexpr (NQ == 4) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          fixed_words<T>(pv[c] * w, vl, vh);
+          smem_add64(acc + (1 + c) * cells + loc, hacc + (1 + c) * cells + loc, vl, vh);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const T md = mass * pow2i<T>(-e_d);
+  T mp[3] = {0, 0, 0};
+  if constexpr (NQ == 4) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) mp[c] = pow2i<T>(-e_pi[c * gridDim.y + b]);
+  }
+  for (int k = threadIdx.x; k < cells; k += blockDim.x) {
+    const int a2 = k & (int)mx, a1 = (k >> bg.lx) & (int)my, a0 = k >> (bg.lx + bg.ly);
+    const long long cell =
+        ((long long)((T0 << bg.lz) + a0) * g.nm + ((T1 << bg.ly) + a1)) * g.nm + ((T2 << bg.lx) + a2);
+    dout[b * dis + cell] = words_to_real<T>(acc[k], hacc[k]) * md - (T)1;
+    if constexpr (NQ == 4) {
+      p0[b * pis + cell] = words_to_real<T>(acc[cells + k], hacc[cells + k]) * mp[0];
+      p1[b * pis + cell] = words_to_real<T>(acc[2 * cells + k], hacc[2 * cells + k]) * mp[1];
+      p2[b * pis + cell] = words_to_real<T>(acc[3 * cells + k], hacc[3 * cells + k]) * mp[2];
+    }
+  }
+}
+
+}  // namespace pmgb

@@ -61,6 +61,14 @@ __device__ __forceinline__ long long f2ll_rn(float v) {
   return (b >> 31) ? -(long long)r : (long long)r;
 }
 
+// 2^e built from its bit pattern, for e in the normal range of T (the FP64 pipe that
+// ldexp goes through is slow on this part)
+template <typename T> __device__ __forceinline__ T pow2i(int e);
+template <> __device__ __forceinline__ float pow2i<float>(int e) { return __int_as_float((e + 127) << 23); }
+template <> __device__ __forceinline__ double pow2i<double>(int e) {
+  return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
 // four reals of one mesh cell (force components and the adjoint potential), one load
 template <typename T> struct alignas(4 * sizeof(T)) V4 { T x, y, z, w; };
 

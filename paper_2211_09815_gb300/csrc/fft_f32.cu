@@ -4,7 +4,7 @@
 namespace pmgb {
 template int fft_cols<float>(int, int, const SeqMap&, const SeqMap&, const ColBufs<float>&, int, const cx_t<float>*,
                              cudaStream_t);
-template int fft_x_r2c<float>(int, const RowJob<float>&, int, int, bool, const cx_t<float>*, cudaStream_t);
+template int fft_x_r2c<float>(int, const RowJob<float>&, int, int, const cx_t<float>*, cudaStream_t);
 template int fft_x_c2r<float>(int, const RowJob<float>&, int, int, const cx_t<float>*, cudaStream_t);
 template int fft_fused_z<float>(int, const ZJob<float>&, bool, const cx_t<float>*, cudaStream_t);
 template int fft_cols_tma<float>(int, int, int, int, const CUtensorMap*, cx_t<float>* const*, int, const cx_t<float>*,

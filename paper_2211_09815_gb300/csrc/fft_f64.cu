@@ -4,7 +4,7 @@
 namespace pmgb {
 template int fft_cols<double>(int, int, const SeqMap&, const SeqMap&, const ColBufs<double>&, int, const cx_t<double>*,
                              cudaStream_t);
-template int fft_x_r2c<double>(int, const RowJob<double>&, int, int, bool, const cx_t<double>*, cudaStream_t);
+template int fft_x_r2c<double>(int, const RowJob<double>&, int, int, const cx_t<double>*, cudaStream_t);
 template int fft_x_c2r<double>(int, const RowJob<double>&, int, int, const cx_t<double>*, cudaStream_t);
 template int fft_fused_z<double>(int, const ZJob<double>&, bool, const cx_t<double>*, cudaStream_t);
 template int fft_cols_tma<double>(int, int, int, int, const CUtensorMap*, cx_t<double>* const*, int, const cx_t<double>*,

@@ -44,53 +44,30 @@ k_fft_cols(const SeqMap mm, const SeqMap ms, int ntiles_main, ColBufs<T> bufs,
 }
 
 // ---------------------------------------------------------------- x pass, R2C
-// int64 fixed point -> real without the FP64 pipe (slow on this part) for float.
-template <typename T> __device__ __forceinline__ T fix2real(long long a);
-template <> __device__ __forceinline__ float fix2real<float>(long long a) { return (float)a; }
-template <> __device__ __forceinline__ double fix2real<double>(long long a) { return (double)a; }
-
-// rows of n = 2L reals -> L complex (main) + 1 (side).  The input is an int64 fixed-point
-// accumulator (value = acc * 2^-e * mul + add, zeroed after reading) or a real mesh.
-// Q = 1: one quantity per block; the tile holds TR rows.  Q = 4: the accumulator is
-// [cell][4] (four quantities per 32-byte sector) and one block converts all four for
-// TR/4 rows, so every sector is read and zeroed whole; tile sequence c = q * (TR/4) + row.
-template <typename T, int L, bool FIXED, int Q>
+// rows of n = 2L reals -> L complex (main) + 1 (side).  The row pairs (2j, 2j+1) are read
+// as one complex number and transformed as L-point sequences; the even/odd split below
+// recovers the real transform.  The buffers of one row tile are neighbouring blocks.
+template <typename T, int L>
 __global__ void __launch_bounds__(RowTile<T, L>::NT)
 k_fft_x_r2c(RowJob<T> job, int nrows, int nbuf, const cx_t<T>* __restrict__ twL,
             const cx_t<T>* __restrict__ twN) {
   using C = cx_t<T>;
   using TL = RowTile<T, L>;
   constexpr int N = 2 * L;
-  constexpr int RT = TL::TR / Q;   // rows per tile
-  static_assert(RT * Q == TL::TR && RT >= 1, "row tile must split into Q quantities");
+  constexpr int RT = TL::TR;   // rows per tile
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
-  // Q = 1: the buffers of one row tile are neighbouring blocks
-  const int qb = Q == 1 ? blockIdx.x % nbuf : 0;
-  const int r0 = (Q == 1 ? blockIdx.x / nbuf : blockIdx.x) * RT;
+  const int qb = blockIdx.x % nbuf;
+  const int r0 = (blockIdx.x / nbuf) * RT;
   const long long rows_per_inst = (long long)N * N;
   // all rows of a tile belong to one instance (RT divides N^2)
   const int inst0 = (int)(min((long long)r0, (long long)nrows - 1) / rows_per_inst);
-  T mul[Q], add[Q];
-#pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    const RowBuf<T>& rb = job.b[Q == 1 ? qb : q];
-    mul[q] = (T)1;
-    add[q] = (T)0;
-    if constexpr (FIXED) {
-      const int e = rb.exps ? rb.exps[inst0] : rb.exp_host;
-      mul[q] = (T)ldexp((double)rb.mul, -e);
-      add[q] = rb.add;
-    }
-  }
   const RowBuf<T>& rb0 = job.b[qb];
-  // load + convert, transposing into [L][LD]; every load of the thread is issued before
-  // the first conversion so that ITER loads per thread are in flight at once
+  // load, transposing into [L][LD]; every load of the thread is issued before the first
+  // shared-memory store so that ITER loads per thread are in flight at once
   constexpr int ITER = RT * L / TL::NT;
   static_assert(ITER * TL::NT == RT * L, "row loads must divide evenly");
-  constexpr int W = FIXED ? (Q == 1 ? 2 : 8) : 1;   // int64 words (or one complex) per load unit
-  using Raw = typename std::conditional<FIXED, long long, C>::type;
-  Raw raw[ITER][W];
+  C raw[ITER];
   bool ok[ITER];
 #pragma unroll
   for (int it = 0; it < ITER; ++it) {
@@ -99,53 +76,13 @@ k_fft_x_r2c(RowJob<T> job, int nrows, int nbuf, const cx_t<T>* __restrict__ twL,
     const int grow = r0 + row;
     ok[it] = grow < nrows;
     const long long off = inst0 * rb0.real_is + (long long)(ok[it] ? grow % rows_per_inst : 0) * N + 2 * j;
-    if constexpr (FIXED && Q == 1) {
-      const longlong2 a = ok[it] ? *reinterpret_cast<const longlong2*>(reinterpret_cast<long long*>(rb0.real) + off)
-                                 : make_longlong2(0, 0);
-      raw[it][0] = a.x;
-      raw[it][1] = a.y;
-    } else if constexpr (FIXED) {
-      const longlong2* acc = reinterpret_cast<const longlong2*>(reinterpret_cast<long long*>(rb0.real) + 4 * off);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const longlong2 a = ok[it] ? acc[u] : make_longlong2(0, 0);
-        raw[it][2 * u] = a.x;
-        raw[it][2 * u + 1] = a.y;
-      }
-    } else {
-      raw[it][0] = ok[it] ? *reinterpret_cast<const C*>(reinterpret_cast<const T*>(rb0.real) + off) : cmake<C>(0, 0);
-    }
-  }
-  if (FIXED && rb0.zero) {
-#pragma unroll
-    for (int it = 0; it < ITER; ++it) {
-      if (!ok[it]) continue;
-      const int idx = threadIdx.x + it * TL::NT;
-      const int row = idx / L, j = idx % L;
-      const long long off = inst0 * rb0.real_is + ((r0 + row) % rows_per_inst) * N + 2 * j;
-      longlong2* acc = reinterpret_cast<longlong2*>(reinterpret_cast<long long*>(rb0.real) + (Q == 1 ? 1 : 4) * off);
-#pragma unroll
-      for (int u = 0; u < (Q == 1 ? 1 : 4); ++u) acc[u] = make_longlong2(0, 0);
-    }
+    raw[it] = ok[it] ? *reinterpret_cast<const C*>(reinterpret_cast<const T*>(rb0.real) + off) : cmake<C>(0, 0);
   }
 #pragma unroll
   for (int it = 0; it < ITER; ++it) {
     const int idx = threadIdx.x + it * TL::NT;
     const int row = idx / L, j = idx % L;
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      C v;
-      if constexpr (FIXED && Q == 1) {
-        v = cmake<C>(fix2real<T>(raw[it][0]) * mul[0] + add[0], fix2real<T>(raw[it][1]) * mul[0] + add[0]);
-      } else if constexpr (FIXED) {
-        // raw holds cell 2j's four quantities, then cell 2j+1's
-        v = cmake<C>(fix2real<T>(raw[it][q]) * mul[q] + add[q], fix2real<T>(raw[it][4 + q]) * mul[q] + add[q]);
-      } else {
-        v = raw[it][0];
-      }
-      if (!ok[it]) v = cmake<C>(0, 0);
-      sm[srow(j) * TL::LD + q * RT + row] = v;
-    }
+    sm[srow(j) * TL::LD + row] = raw[it];
   }
   __syncthreads();
   SmemTile<C, TL::LD> t{sm};
@@ -154,10 +91,10 @@ k_fft_x_r2c(RowJob<T> job, int nrows, int nbuf, const cx_t<T>* __restrict__ twL,
   // even/odd split: X[k] = E[k] + W^k O[k], E = (Z[k] + conj Z[L-k]) / 2, O = -i (Z[k] - conj Z[L-k]) / 2
   for (int idx = threadIdx.x; idx < TL::TR * (L / 2 + 1); idx += TL::NT) {
     const int c = idx / (L / 2 + 1), k = idx % (L / 2 + 1);
-    const int q = c / RT, row = c % RT;
+    const int row = c;
     const int grow = r0 + row;
     if (grow >= nrows) continue;
-    C* spec = job.b[Q == 1 ? qb : q].spec;
+    C* spec = job.b[qb].spec;
     C* out = spec + inst0 * spec_len_cx(N) + (grow % rows_per_inst) * L;
     C* side = spec + inst0 * spec_len_cx(N) + spec_main_len(N) + (grow % rows_per_inst);
     const C zk = sm[srow(k) * TL::LD + c];
@@ -495,29 +432,13 @@ static void launch_cols_L(const SeqMap& mm, const SeqMap& ms, const ColBufs<T>& 
 }
 
 template <typename T, int L>
-static void launch_r2c_L(const RowJob<T>& job, int nbuf, int nrows, bool fixed, const cx_t<T>* tw,
-                         cudaStream_t st) {
+static void launch_r2c_L(const RowJob<T>& job, int nbuf, int nrows, const cx_t<T>* tw, cudaStream_t st) {
   using TL = RowTile<T, L>;
   const size_t sm = TL::SMEM;
-  if constexpr (TL::TR % 4 == 0 && ((TL::TR / 4) * L) % TL::NT == 0) {
-    if (fixed && job.b[0].qstride == 4 && nbuf == 4) {
-      auto fn = k_fft_x_r2c<T, L, true, 4>;
-      set_smem<T, L>((const void*)fn, sm);
-      dim3 grid((nrows + TL::TR / 4 - 1) / (TL::TR / 4), 1);
-      fn<<<grid, TL::NT, sm, st>>>(job, nrows, nbuf, tw + L, tw + 2 * L);
-      return;
-    }
-  }
   dim3 grid(((nrows + TL::TR - 1) / TL::TR) * nbuf, 1);
-  if (fixed) {
-    auto fn = k_fft_x_r2c<T, L, true, 1>;
-    set_smem<T, L>((const void*)fn, sm);
-    fn<<<grid, TL::NT, sm, st>>>(job, nrows, nbuf, tw + L, tw + 2 * L);
-  } else {
-    auto fn = k_fft_x_r2c<T, L, false, 1>;
-    set_smem<T, L>((const void*)fn, sm);
-    fn<<<grid, TL::NT, sm, st>>>(job, nrows, nbuf, tw + L, tw + 2 * L);
-  }
+  auto fn = k_fft_x_r2c<T, L>;
+  set_smem<T, L>((const void*)fn, sm);
+  fn<<<grid, TL::NT, sm, st>>>(job, nrows, nbuf, tw + L, tw + 2 * L);
 }
 
 template <typename T, int L>
@@ -674,10 +595,10 @@ int fft_cols(int n, int dir, const SeqMap& mm, const SeqMap& ms, const ColBufs<T
 }
 
 template <typename T>
-int fft_x_r2c(int n, const RowJob<T>& job, int nbuf, int nrows, bool fixed, const cx_t<T>* tw,
+int fft_x_r2c(int n, const RowJob<T>& job, int nbuf, int nrows, const cx_t<T>* tw,
               cudaStream_t st) {
   if (n < 4 || n > 1024) return PM_ERR_ARG;
-  PMGB_DISPATCH_L(n / 2, (launch_r2c_L<T, (LL < 512 ? LL : 512)>(job, nbuf, nrows, fixed, tw, st)));
+  PMGB_DISPATCH_L(n / 2, (launch_r2c_L<T, (LL < 512 ? LL : 512)>(job, nbuf, nrows, tw, st)));
   return PM_OK;
 }
 

@@ -3,6 +3,7 @@
 // type.  Included once per precision.
 #pragma once
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
@@ -11,6 +12,7 @@
 #include "pm_internal.h"
 #include "pm_engine.h"
 #include "pm_kernels.cuh"
+#include "bin_kernels.cuh"
 
 namespace pmgb {
 
@@ -135,7 +137,7 @@ class Engine : public EngineBase {
     geo_.N = N_;
     geo_.M = M_;
     lgN_ = ilog2(N_);
-    e_d_ = 61 - lgN_;
+    e_d_ = fixed_top<T>(lgN_);
     G_ = (int)std::min<long long>((N_ + kPtclThreads - 1) / kPtclThreads, kMaxRedBlocks);
     Gm_ = (int)std::min<long long>((M_ + kPtclThreads - 1) / kPtclThreads, kMaxRedBlocks);
     Gz_ = (int)std::min<long long>((spec_len_cx(np_) + kPtclThreads - 1) / kPtclThreads, kMaxRedBlocks);
@@ -148,10 +150,8 @@ class Engine : public EngineBase {
     PMGB_RET(alloc(&pi_, pv));
     PMGB_RET(alloc(&s1_, pv));
     PMGB_RET(alloc(&omega_, (long long)B_ * N_));
-    // one int64 array of [B][M][4] (density, pi_x, pi_y, pi_z interleaved per cell) for the
-    // adjoint scatter; the forward density scatter uses its first B*M elements as [B][M]
-    PMGB_RET(alloc(&accq_, (long long)4 * B_ * M_));
-    acc_[0] = accq_;
+    // particle bins of the mesh-tile assignment (bin_kernels.cuh)
+    PMGB_RET(bin_setup());
     for (int q = 0; q < 7; ++q) PMGB_RET(alloc(&spec_[q], sl));
     PMGB_RET(alloc(&dens_, (long long)B_ * M_));
     PMGB_RET(alloc(&fvec_, (long long)B_ * M_));
@@ -160,7 +160,6 @@ class Engine : public EngineBase {
       PMGB_RET(alloc(&ck_s_, pv * nck_));
       PMGB_RET(alloc(&ck_p_, pv * nck_));
     }
-    PMGB_CK(cudaMemsetAsync(accq_, 0, sizeof(long long) * 4 * B_ * M_, st_));
     // TMA-staged column passes for the mesh-size spectra
     int dev = 0;
     PMGB_CK(cudaGetDevice(&dev));
@@ -295,11 +294,7 @@ class Engine : public EngineBase {
   int op_density(const void* disp, void* dens) override {
     have_fwd_ = false;
     PMGB_CK(cudaMemcpyAsync(s_, disp, sizeof(T) * B_ * 3 * N_, cudaMemcpyDeviceToDevice, st_));
-    PMGB_RET(scatter(s_, nullptr));
-    k_density_out<T><<<1024, 256, 0, st_>>>((const long long*)acc_[0], (T*)dens, (long long)B_ * M_,
-                                            (T)ldexp((double)mass_, -e_d_));
-    PMGB_CK(cudaGetLastError());
-    PMGB_CK(cudaMemsetAsync(acc_[0], 0, sizeof(long long) * B_ * M_, st_));
+    PMGB_RET(scatter(s_, nullptr, (T*)dens, M_));
     return PM_OK;
   }
 
@@ -622,8 +617,8 @@ class Engine : public EngineBase {
   }
   int r2c_real(int n, const T* in, long long in_is, C* out) {
     RowJob<T> job{};
-    job.b[0] = RowBuf<T>{(void*)in, in_is, out, nullptr, 0, (T)1, (T)0, 0, 1};
-    PMGB_RET(fft_x_r2c<T>(n, job, 1, B_ * n * n, false, tw_, st_));
+    job.b[0] = RowBuf<T>{(void*)in, in_is, out};
+    PMGB_RET(fft_x_r2c<T>(n, job, 1, B_ * n * n, tw_, st_));
     C* bufs[1] = {out};
     PMGB_RET(cols(n, -1, false, bufs, 1));
     PMGB_RET(cols(n, -1, true, bufs, 1));
@@ -634,29 +629,86 @@ class Engine : public EngineBase {
     PMGB_RET(cols(n, +1, true, bufs, 1));
     PMGB_RET(cols(n, +1, false, bufs, 1));
     RowJob<T> job{};
-    job.b[0] = RowBuf<T>{(void*)out, out_is, in, nullptr, 0, (T)1, (T)0, 0, 1};
+    job.b[0] = RowBuf<T>{(void*)out, out_is, in};
     PMGB_RET(fft_x_c2r<T>(n, job, 1, B_ * n * n, tw_, st_));
     PMGB_CK(cudaGetLastError());
     return PM_OK;
   }
 
-  int scatter(const T* s, const T* pi) {
+  // Tile shape of the assignment: 16 x 16 x 8 cells (x, y, z), or PMGB_TILE="lx,ly,lz"
+  // (log2 extents, at most 2^11 cells per tile); threads per tile 256 for the density alone
+  // and 512 with the pi sums, or PMGB_PULL_NT="n1,n4" (256 or 512 each).
+  int bin_setup() {
+    int lx = 4, ly = 4, lz = 3;
+    if (const char* env = getenv("PMGB_TILE")) {
+      int a, b, c;
+      if (sscanf(env, "%d,%d,%d", &a, &b, &c) == 3 && a >= 0 && b >= 0 && c >= 0 && a + b + c <= 11) {
+        lx = a;
+        ly = b;
+        lz = c;
+      }
+    }
+    bg_ = make_bin_geo(ilog2(nm_), lx, ly, lz);
+    nbin_ = (long long)B_ * bg_.nkeys + 1;
+    nscan_ = (int)((nbin_ + kScanBlock - 1) / kScanBlock);
+    PMGB_RET(alloc(&bkeys_, (long long)B_ * N_));
+    PMGB_RET(alloc(&blist_, (long long)B_ * N_));
+    PMGB_RET(alloc(&bcount_, nbin_));
+    PMGB_RET(alloc(&bstart_, nbin_));
+    PMGB_RET(alloc(&bcursor_, nbin_));
+    PMGB_RET(alloc(&bsums_, (long long)nscan_));
+    PMGB_CK(cudaMemsetAsync(bcount_, 0, sizeof(unsigned) * nbin_, st_));
+    if (const char* env = getenv("PMGB_PULL_NT")) {
+      int a = 0, b = 0;
+      if (sscanf(env, "%d,%d", &a, &b) == 2) {
+        pull_nt1_ = a == 512 ? 512 : 256;
+        pull_nt4_ = b == 512 ? 512 : 256;
+      }
+    }
+    ensure_smem_attr((const void*)k_pull_scatter<T, 4, 256>, 4 * 8 * 2048);
+    ensure_smem_attr((const void*)k_pull_scatter<T, 4, 512>, 4 * 8 * 2048);
+    return PM_OK;
+  }
+
+  // CIC assignment (Sec. 2.2, Eq. 10) of the density contrast -- and with pi of the three
+  // adjoint sums pi_c W -- by binning the particles over mesh tiles and one CTA per tile
+  // (bin_kernels.cuh).  delta goes to dout (instance stride dis); the pi sums go to the real
+  // views of spec_[4..6].
+  int scatter(const T* s, const T* pi, T* dout, long long dis) {
     if (pi) {
       prof_.begin(st_, P_OTHER, 1);
-      k_pi_exponents<<<1, 64, 0, st_>>>(pimax_, e_pi_, 3 * B_, lgN_);
+      k_pi_exponents<<<1, 64, 0, st_>>>(pimax_, e_pi_, 3 * B_, fixed_top<T>(lgN_));
       prof_.end(st_, P_OTHER);
       PMGB_CK(cudaGetLastError());
       PMGB_CK(cudaMemsetAsync(pimax_, 0, sizeof(unsigned) * 3 * B_, st_));
-      prof_.begin(st_, P_SCATTER, 1);
-      k_scatter<T, 4><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, s, pi, (unsigned long long*)accq_, e_d_,
-                                                              e_pi_);
-      prof_.end(st_, P_SCATTER);
-    } else {
-      prof_.begin(st_, P_SCATTER, 1);
-      k_scatter<T, 1><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, s, nullptr, (unsigned long long*)acc_[0],
-                                                              e_d_, nullptr);
-      prof_.end(st_, P_SCATTER);
     }
+    prof_.begin(st_, P_SCATTER, 6);
+    k_bin_count<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, bg_, s, bcount_, bkeys_);
+    k_scan_blocks<<<nscan_, 256, 0, st_>>>(bcount_, bstart_, bsums_, nbin_);
+    k_scan_sums<<<1, 256, 0, st_>>>(bsums_, nscan_);
+    k_scan_add<<<(int)std::min<long long>((nbin_ + 255) / 256, 4096), 256, 0, st_>>>(bstart_, bcursor_, bsums_, nbin_);
+    k_bin_fill<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, bg_, bkeys_, bcursor_, blist_);
+    const int cells = 1 << (bg_.lx + bg_.ly + bg_.lz);
+    const long long pis = 2 * spec_len_cx(nm_);
+    const dim3 grid(bg_.ntiles, B_);
+    if (pi) {
+      if (pull_nt4_ == 512)
+        k_pull_scatter<T, 4, 512><<<grid, 512, 4 * 8 * cells, st_>>>(
+            geo_, bg_, s, pi, bstart_, blist_, e_d_, e_pi_, mass_, dout, dis, rmesh(4), rmesh(5), rmesh(6), pis);
+      else
+        k_pull_scatter<T, 4, 256><<<grid, 256, 4 * 8 * cells, st_>>>(
+            geo_, bg_, s, pi, bstart_, blist_, e_d_, e_pi_, mass_, dout, dis, rmesh(4), rmesh(5), rmesh(6), pis);
+    } else {
+      if (pull_nt1_ == 512)
+        k_pull_scatter<T, 1, 512><<<grid, 512, 8 * cells, st_>>>(geo_, bg_, s, nullptr, bstart_, blist_, e_d_,
+                                                                  nullptr, mass_, dout, dis, nullptr, nullptr,
+                                                                  nullptr, 0);
+      else
+        k_pull_scatter<T, 1, 256><<<grid, 256, 8 * cells, st_>>>(geo_, bg_, s, nullptr, bstart_, blist_, e_d_,
+                                                                  nullptr, mass_, dout, dis, nullptr, nullptr,
+                                                                  nullptr, 0);
+    }
+    prof_.end(st_, P_SCATTER);
     PMGB_CK(cudaGetLastError());
     return PM_OK;
   }
@@ -665,25 +717,19 @@ class Engine : public EngineBase {
   // leaving f_c in spec_[1..3] (real view).  With pi also the adjoint chain: pi scatter ->
   // 3 R2C -> sum_c conj(H_c) -> C2R, leaving psi in spec_[0].
   int force_chain(const T* s, const T* pi, bool keep_density) {
-    PMGB_RET(scatter(s, pi));
-    if (keep_density) {
-      prof_.begin(st_, P_OTHER, 1);
-      k_density_out<T><<<1024, 256, 0, st_>>>((const long long*)acc_[0], dens_, (long long)B_ * M_,
-                                              (T)ldexp((double)mass_, -e_d_));
-      prof_.end(st_, P_OTHER);
-      PMGB_CK(cudaGetLastError());
-    }
+    // delta goes to the real view of spec_[0] (transformed in place) or, when the final
+    // density is kept for the objective, to dens_
+    const long long sis = 2 * spec_len_cx(nm_);
+    T* dmesh = keep_density ? dens_ : rmesh(0);
+    const long long dis = keep_density ? M_ : sis;
+    PMGB_RET(scatter(s, pi, dmesh, dis));
     const int nb = pi ? 4 : 1;
     RowJob<T> job{};
-    if (!pi) {
-      job.b[0] = RowBuf<T>{acc_[0], M_, spec_[0], nullptr, e_d_, mass_, (T)-1, 1, 1};
-    } else {
-      job.b[0] = RowBuf<T>{accq_, M_, spec_[0], nullptr, e_d_, mass_, (T)-1, 1, 4};
-      for (int c = 0; c < 3; ++c)
-        job.b[1 + c] = RowBuf<T>{accq_ + 1 + c, M_, spec_[4 + c], e_pi_ + c * B_, 0, (T)1, (T)0, 1, 4};
-    }
+    job.b[0] = RowBuf<T>{dmesh, dis, spec_[0]};
+    if (pi)
+      for (int c = 0; c < 3; ++c) job.b[1 + c] = RowBuf<T>{rmesh(4 + c), sis, spec_[4 + c]};
     prof_.begin(st_, P_X_R2C, 1);
-    PMGB_RET(fft_x_r2c<T>(nm_, job, nb, B_ * nm_ * nm_, true, tw_, st_));
+    PMGB_RET(fft_x_r2c<T>(nm_, job, nb, B_ * nm_ * nm_, tw_, st_));
     prof_.end(st_, P_X_R2C);
     PMGB_CK(cudaGetLastError());
     C* fwdb[4] = {spec_[0], spec_[4], spec_[5], spec_[6]};
@@ -730,7 +776,7 @@ class Engine : public EngineBase {
     prof_.end(st_, P_COLS);
     // C2R of f_0..2 (and psi) into one interleaved [cell][4] mesh for the gathers
     RowJob<T> jc{};
-    for (int q = 0; q < 4; ++q) jc.b[q] = RowBuf<T>{nullptr, 0, (q < 3 || pi) ? invb[q] : nullptr, nullptr, 0, (T)1, (T)0, 0, 1};
+    for (int q = 0; q < 4; ++q) jc.b[q] = RowBuf<T>{nullptr, 0, (q < 3 || pi) ? invb[q] : nullptr};
     prof_.begin(st_, P_X_C2R, 1);
     PMGB_RET(fft_x_c2r4<T>(nm_, jc, B_ * nm_ * nm_, reinterpret_cast<V4<T>*>(fvec_), tw_, st_));
     prof_.end(st_, P_X_C2R);
@@ -754,8 +800,8 @@ class Engine : public EngineBase {
   }
   int lattice_r2c(const T* in, long long in_is, C* out) {
     RowJob<T> job{};
-    job.b[0] = RowBuf<T>{(void*)in, in_is, out, nullptr, 0, (T)1, (T)0, 0, 1};
-    PMGB_RET(fft_x_r2c<T>(np_, job, 1, B_ * np_ * np_, false, tw_, st_));
+    job.b[0] = RowBuf<T>{(void*)in, in_is, out};
+    PMGB_RET(fft_x_r2c<T>(np_, job, 1, B_ * np_ * np_, tw_, st_));
     C* bufs[1] = {out};
     PMGB_RET(cols(np_, -1, false, bufs, 1));
     PMGB_RET(cols(np_, -1, true, bufs, 1));
@@ -765,7 +811,7 @@ class Engine : public EngineBase {
     PMGB_RET(cols(np_, +1, true, bufs, nb));
     PMGB_RET(cols(np_, +1, false, bufs, nb));
     RowJob<T> jc{};
-    for (int q = 0; q < nb; ++q) jc.b[q] = RowBuf<T>{bufs[q], 2 * spec_len_cx(np_), bufs[q], nullptr, 0, (T)1, (T)0, 0, 1};
+    for (int q = 0; q < nb; ++q) jc.b[q] = RowBuf<T>{bufs[q], 2 * spec_len_cx(np_), bufs[q]};
     PMGB_RET(fft_x_c2r<T>(np_, jc, nb, B_ * np_ * np_, tw_, st_));
     PMGB_CK(cudaGetLastError());
     return PM_OK;
@@ -782,9 +828,9 @@ class Engine : public EngineBase {
     PMGB_CK(cudaGetLastError());
     // 3 R2C of sbar (in place: real input in the same buffer) and the R2C of omega
     RowJob<T> job{};
-    for (int c = 0; c < 3; ++c) job.b[c] = RowBuf<T>{rmesh(1 + c), 2 * lis, spec_[1 + c], nullptr, 0, (T)1, (T)0, 0, 1};
-    job.b[3] = RowBuf<T>{omega_, N_, spec_[0], nullptr, 0, (T)1, (T)0, 0, 1};
-    PMGB_RET(fft_x_r2c<T>(np_, job, 4, B_ * np_ * np_, false, tw_, st_));
+    for (int c = 0; c < 3; ++c) job.b[c] = RowBuf<T>{rmesh(1 + c), 2 * lis, spec_[1 + c]};
+    job.b[3] = RowBuf<T>{omega_, N_, spec_[0]};
+    PMGB_RET(fft_x_r2c<T>(np_, job, 4, B_ * np_ * np_, tw_, st_));
     PMGB_CK(cudaGetLastError());
     C* bufs[4] = {spec_[1], spec_[2], spec_[3], spec_[0]};
     PMGB_RET(cols(np_, -1, false, bufs, 4));
@@ -798,7 +844,7 @@ class Engine : public EngineBase {
     PMGB_RET(cols(np_, +1, true, ob, 1));
     PMGB_RET(cols(np_, +1, false, ob, 1));
     RowJob<T> jc{};
-    jc.b[0] = RowBuf<T>{djdw ? djdw : (void*)rmesh(5), djdw ? N_ : 2 * lis, spec_[5], nullptr, 0, (T)1, (T)0, 0, 1};
+    jc.b[0] = RowBuf<T>{djdw ? djdw : (void*)rmesh(5), djdw ? N_ : 2 * lis, spec_[5]};
     PMGB_RET(fft_x_c2r<T>(np_, jc, 1, B_ * np_ * np_, tw_, st_));
     PMGB_CK(cudaGetLastError());
     return PM_OK;
@@ -820,8 +866,11 @@ class Engine : public EngineBase {
   cudaGraphExec_t graph_exec_ = nullptr;
   const void* graph_args_[4] = {nullptr, nullptr, nullptr, nullptr};
   T *s_ = nullptr, *p_ = nullptr, *a_ = nullptr, *xi_ = nullptr, *pi_ = nullptr, *s1_ = nullptr, *omega_ = nullptr;
-  long long* acc_[1] = {nullptr};
-  long long* accq_ = nullptr;
+  BinGeo bg_{};
+  long long nbin_ = 0;
+  int nscan_ = 1, pull_nt1_ = 256, pull_nt4_ = 512;
+  unsigned *bkeys_ = nullptr, *blist_ = nullptr, *bcount_ = nullptr, *bstart_ = nullptr, *bcursor_ = nullptr,
+           *bsums_ = nullptr;
   C* spec_[7] = {};
   T* dens_ = nullptr;
   V4<T>* fvec_ = nullptr;

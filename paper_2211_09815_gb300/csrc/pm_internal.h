@@ -25,14 +25,9 @@ template <typename T> struct ColBufs { cx_t<T>* p[4]; };
 
 // One buffer of a row (x) pass.  R2C: real -> spec.  C2R: spec -> real.
 template <typename T> struct RowBuf {
-  void* real;           // int64 accumulator or T mesh
+  void* real;           // real mesh (T)
   long long real_is;    // instance stride of `real` in elements
   cx_t<T>* spec;        // spectrum buffer (main + side)
-  const int* exps;      // fixed-point exponent per instance (device) or null
-  int exp_host;         // exponent when exps is null
-  T mul, add;           // value = acc * 2^-e * mul + add
-  int zero;             // zero the accumulator after reading
-  int qstride;          // fixed point: int64 elements between consecutive cells (1 or 4)
 };
 template <typename T> struct RowJob { RowBuf<T> b[4]; };
 
@@ -50,7 +45,7 @@ template <typename T>
 int fft_cols(int n, int dir, const SeqMap& mm, const SeqMap& ms, const ColBufs<T>& bufs, int nbuf,
              const cx_t<T>* tw, cudaStream_t st);
 template <typename T>
-int fft_x_r2c(int n, const RowJob<T>& job, int nbuf, int nrows, bool fixed, const cx_t<T>* tw,
+int fft_x_r2c(int n, const RowJob<T>& job, int nbuf, int nrows, const cx_t<T>* tw,
               cudaStream_t st);
 template <typename T>
 int fft_x_c2r(int n, const RowJob<T>& job, int nbuf, int nrows, const cx_t<T>* tw, cudaStream_t st);

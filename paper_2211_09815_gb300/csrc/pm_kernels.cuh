@@ -2,6 +2,8 @@
 // real type.  Included once per precision.
 //
 //  k_scatter        CIC mass (and adjoint pi) assignment, Sec. 2.2 Eq. 10, int64 fixed point
+//                   with global atomics (the allocation-free density entry point; the
+//                   engine assigns by mesh tiles, bin_kernels.cuh)
 //  k_gather_fwd     CIC force gather + kick / kick / drift of Eq. 16 (one launch per step)
 //  k_gather_adj     CIC gather of a and alpha (Eq. 49 F line) + reverse kicks and drift of
 //                   Eq. 49, FP64 partials of the theta terms of Eq. 51
@@ -171,19 +173,50 @@ k_scatter(Geo<T> g, const T* __restrict__ s, const T* __restrict__ pi, unsigned 
   }
 }
 
-// fixed-point exponents of the pi scatters from max|pi_c| (layout [c][batch]): the sum over one cell of
-// |pi| W is below N max|pi| < 2^(lg N + E), kept below 2^61.
-static __global__ void k_pi_exponents(const unsigned* __restrict__ pimax, int* __restrict__ e_pi, int nq, int lgN) {
+// fixed-point exponents of the pi scatters from max|pi_c| (layout [c][batch]): one
+// contribution |pi| W 2^e is below 2^(E + e) and the sum over one cell below N 2^(E + e),
+// with max|pi| < 2^E; e = top - E keeps them below 2^top and 2^(lg N + top) (top: see
+// fixed_top).
+static __global__ void k_pi_exponents(const unsigned* __restrict__ pimax, int* __restrict__ e_pi, int nq, int top) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nq) return;
   const float mx = __uint_as_float(pimax[i]);
   int e = 0;
   if (mx > 0.f && isfinite(mx)) {
     const int E = ilogbf(mx) + 1;   // mx < 2^E
-    e = 61 - lgN - E;
+    e = top - E;
     if (e > 100) e = 100;
   }
   e_pi[i] = e;
+}
+
+// Bits of one fixed-point contribution of the assignment.  FP32: 2^30, so that a
+// contribution is an int32 (its 24-bit significand loses nothing there) and the sum over a
+// cell of N contributions stays below 2^61 for N <= 2^31; FP64: 61 - lg N, the widest
+// quantum the int64 cell sums allow.
+template <typename T> inline int fixed_top(int lgN);
+template <> inline int fixed_top<float>(int lgN) { return 61 - lgN < 30 ? 61 - lgN : 30; }
+template <> inline int fixed_top<double>(int lgN) { return 61 - lgN; }
+
+// A fixed-point contribution as the two 32-bit words of an int64, correctly rounded
+// (nearest-even).  FP32 (|v| <= 2^30): below 2^23 the rounding is that of one FP32
+// addition of 2^23 (whose result's ulp is 1), above it v is an integer and its significand
+// is shifted into place.
+template <typename T> __device__ __forceinline__ void fixed_words(T v, unsigned& lo, unsigned& hi);
+template <> __device__ __forceinline__ void fixed_words<float>(float v, unsigned& lo, unsigned& hi) {
+  const float a = fabsf(v);
+  const unsigned ua = __float_as_uint(a);
+  const unsigned small = __float_as_uint(__fadd_rn(a, 8388608.0f)) - 0x4B000000u;
+  const unsigned big = ((ua & 0x7FFFFFu) | 0x800000u) << (((ua >> 23) - 150u) & 31u);
+  const unsigned r = a < 8388608.0f ? small : big;
+  const bool neg = v < 0.0f;
+  lo = neg ? 0u - r : r;
+  hi = (neg && r != 0u) ? 0xFFFFFFFFu : 0u;
+}
+template <> __device__ __forceinline__ void fixed_words<double>(double v, unsigned& lo, unsigned& hi) {
+  const unsigned long long r = (unsigned long long)__double2ll_rn(v);
+  lo = (unsigned)r;
+  hi = (unsigned)(r >> 32);
 }
 
 // ---------------------------------------------------------------------- gathers
