@@ -80,6 +80,17 @@ template <typename T> struct alignas(4 * sizeof(T)) V4 { T x, y, z, w; };
 __host__ __device__ inline long long spec_main_len(int n) { return (long long)n * n * (n / 2); }
 __host__ __device__ inline long long spec_len_cx(int n) { return spec_main_len(n) + (long long)n * n; }
 
+// Element q of a small array held in kernel parameters, chosen with selects: a dynamic
+// index into the parameter block would copy it to local memory in every thread.
+template <typename X, int K>
+__device__ __forceinline__ X pick(const X (&a)[K], int q) {
+  X r = a[0];
+#pragma unroll
+  for (int i = 1; i < K; ++i)
+    if (q == i) r = a[i];
+  return r;
+}
+
 // signed frequency of index i on an axis of length n, in [-n/2, n/2)
 __device__ __forceinline__ int freq_of(int i, int n) { return i < n / 2 ? i : i - n; }
 

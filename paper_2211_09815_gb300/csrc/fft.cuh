@@ -72,10 +72,18 @@ __device__ __forceinline__ void dft(C (&v)[R]) {
   }
 }
 
-// exp(DIR 2 pi i m / L) from the table w[m] = exp(-2 pi i m / L)
+// exp(DIR 2 pi i m / L) from the table w[m] = exp(-2 pi i m / L), read through the
+// read-only data cache, or from a copy in shared memory (SmemTw)
 template <int DIR, typename C>
 __device__ __forceinline__ C twiddle(const C* __restrict__ w, int m) {
   C t = __ldg(w + m);
+  if (DIR > 0) t.y = -t.y;
+  return t;
+}
+template <typename C> struct SmemTw { const C* p; };
+template <int DIR, typename C>
+__device__ __forceinline__ C twiddle(const SmemTw<C>& w, int m) {
+  C t = w.p[m];
   if (DIR > 0) t.y = -t.y;
   return t;
 }
@@ -112,8 +120,8 @@ struct GlobalSeq {
 // One Stockham radix-R stage over TC sequences of length L, NT threads.
 // NS = product of the radices already applied.  Loads all of the thread's inputs, syncs,
 // then stores, so source and destination may be the same shared-memory tile.
-template <typename T, int L, int TC, int NT, int R, int NS, int DIR, class Src, class Dst>
-__device__ __forceinline__ void stage(const Src& src, const Dst& dst, const cx_t<T>* __restrict__ tw) {
+template <typename T, int L, int TC, int NT, int R, int NS, int DIR, class Src, class Dst, class TW>
+__device__ __forceinline__ void stage(const Src& src, const Dst& dst, const TW& tw) {
   using C = cx_t<T>;
   constexpr int ITEMS = TC * (L / R);
   constexpr int PER = ITEMS / NT;
@@ -143,9 +151,8 @@ __device__ __forceinline__ void stage(const Src& src, const Dst& dst, const cx_t
 }
 
 // Full length-L DFT of a tile: src -> (mid) -> dst.  `mid` must be a shared tile.
-template <typename T, int L, int TC, int NT, int DIR, class Src, class Mid, class Dst>
-__device__ __forceinline__ void fft_tile(const Src& src, const Mid& mid, const Dst& dst,
-                                         const cx_t<T>* __restrict__ tw) {
+template <typename T, int L, int TC, int NT, int DIR, class Src, class Mid, class Dst, class TW>
+__device__ __forceinline__ void fft_tile(const Src& src, const Mid& mid, const Dst& dst, const TW& tw) {
   using P = Plan<L>;
   if constexpr (P::S == 1) {
     stage<T, L, TC, NT, P::R0, 1, DIR>(src, dst, tw);

@@ -37,7 +37,7 @@ k_fft_cols(const SeqMap mm, const SeqMap ms, int ntiles_main, ColBufs<T> bufs,
   const int s0 = (side ? blockIdx.x - ntiles_main : blockIdx.x) * TL::TC;
   const int s = s0 + threadIdx.x % TL::TC;
   const bool valid = s < m.nseq;
-  C* base = bufs.p[blockIdx.y] + (valid ? seq_base(m, s) : 0);
+  C* base = pick(bufs.p, blockIdx.y) + (valid ? seq_base(m, s) : 0);
   GlobalSeq<C> g{base, m.es, valid};
   SmemTile<C, TL::LD> t{sm};
   fft_tile<T, L, TL::TC, TL::NT, DIR>(g, t, g, tw);
@@ -62,7 +62,7 @@ k_fft_x_r2c(RowJob<T> job, int nrows, int nbuf, const cx_t<T>* __restrict__ twL,
   const long long rows_per_inst = (long long)N * N;
   // all rows of a tile belong to one instance (RT divides N^2)
   const int inst0 = (int)(min((long long)r0, (long long)nrows - 1) / rows_per_inst);
-  const RowBuf<T>& rb0 = job.b[qb];
+  const RowBuf<T> rb0 = pick(job.b, qb);
   // load, transposing into [L][LD]; every load of the thread is issued before the first
   // shared-memory store so that ITER loads per thread are in flight at once
   constexpr int ITER = RT * L / TL::NT;
@@ -94,7 +94,7 @@ k_fft_x_r2c(RowJob<T> job, int nrows, int nbuf, const cx_t<T>* __restrict__ twL,
     const int row = c;
     const int grow = r0 + row;
     if (grow >= nrows) continue;
-    C* spec = job.b[qb].spec;
+    C* spec = rb0.spec;
     C* out = spec + inst0 * spec_len_cx(N) + (grow % rows_per_inst) * L;
     C* side = spec + inst0 * spec_len_cx(N) + spec_main_len(N) + (grow % rows_per_inst);
     const C zk = sm[srow(k) * TL::LD + c];
@@ -125,7 +125,7 @@ k_fft_x_c2r(RowJob<T> job, int nrows, const cx_t<T>* __restrict__ twL, const cx_
   constexpr int N = 2 * L;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
-  const RowBuf<T>& rb = job.b[blockIdx.y];
+  const RowBuf<T> rb = pick(job.b, blockIdx.y);
   const int r0 = blockIdx.x * TL::TR;
   const long long rows_per_inst = (long long)N * N;
   // Z[k] = E'[k] + i O'[k], E' = X[k] + conj X[L-k], O' = (X[k] - conj X[L-k]) conj(W^k);
@@ -216,7 +216,7 @@ k_fft_x_c2r4(RowJob<T> job, int nrows, V4<T>* __restrict__ out4, const cx_t<T>* 
     xk[it] = cmake<C>(0, 0);
     xm[it] = cmake<C>(0, 0);
     if (idx < PAIRS && grow < nrows) {
-      const C* base = job.b[q].spec + (grow / rows_per_inst) * spec_len_cx(N);
+      const C* base = pick(job.b, q).spec + (grow / rows_per_inst) * spec_len_cx(N);
       const C* in = base + (grow % rows_per_inst) * L;
       xk[it] = in[k];
       xm[it] = k == 0 ? base[spec_main_len(N) + (grow % rows_per_inst)] : in[L - k];
@@ -379,7 +379,7 @@ k_fused_z_force(ZJob<T> job, int ntiles_main, const cx_t<T>* __restrict__ tw) {
 #pragma unroll 1
   for (int c = 0; c < 3; ++c) {
     MulSrc<T, TL::LD> src{A, gs, c};
-    GlobalSeq<C> gout{job.out[c] + q.base, q.es, q.valid};
+    GlobalSeq<C> gout{pick(job.out, c) + q.base, q.es, q.valid};
     fft_tile<T, L, TL::TC, TL::NT, +1>(src, tb, gout, tw);
   }
 }
@@ -403,7 +403,7 @@ k_fused_z_adjoint(ZJob<T> job, int ntiles_main, const cx_t<T>* __restrict__ tw) 
   SmemTile<C, TL::LD> ta{A}, tb{B};
 #pragma unroll 1
   for (int c = 0; c < 3; ++c) {
-    GlobalSeq<C> gin{job.in[c] + q.base, q.es, q.valid};
+    GlobalSeq<C> gin{pick(job.in, c) + q.base, q.es, q.valid};
     AccDst<T, TL::LD> acc{A, gs, c};
     fft_tile<T, L, TL::TC, TL::NT, -1>(gin, tb, acc, tw);
     __syncthreads();
@@ -476,7 +476,7 @@ static void launch_tma_L(const CUtensorMap* maps, const TmaJob<T>& job, int tile
   using TT = TmaTile<T, L>;
   TmaMaps m{};
   for (int i = 0; i < (KIND == 0 ? job.nbuf : (KIND == 1 ? 1 : 3)); ++i) m.m[i] = maps[i];
-  const size_t sm = (size_t)(KIND == 0 ? 2 : 3) * TT::BYTES + 1024;
+  const size_t sm = KIND == 0 ? 2 * (size_t)TT::BYTES + 1024 : 3 * (size_t)TT::BYTES + (size_t)L * sizeof(cx_t<T>) + 1024;
   auto fn = k_cols_tma<T, L, DIR, KIND>;
   ensure_smem_attr((const void*)fn, (int)sm);
   const int items = KIND == 0 ? job.nbuf * tiles : tiles;

@@ -129,7 +129,8 @@ struct DenseAccDst {
 
 template <typename T, int L, int DIR, int KIND>
 __global__ void __launch_bounds__(TmaTile<T, L>::NT, 1)
-k_cols_tma(const __grid_constant__ TmaMaps maps, TmaJob<T> job, int tiles_per_buf, const cx_t<T>* __restrict__ tw) {
+k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaJob<T> job, int tiles_per_buf,
+           const cx_t<T>* __restrict__ tw) {
   using C = cx_t<T>;
   using TT = TmaTile<T, L>;
   constexpr int N = L;
@@ -140,6 +141,12 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, TmaJob<T> job, int tiles_per_bu
   C* ring0 = reinterpret_cast<C*>((reinterpret_cast<unsigned long long>(smem_raw) + 1023ull) & ~1023ull);
   C* ring1 = ring0 + TT::TILE;
   C* work = ring0 + 2 * TT::TILE;
+  // twiddle table of the length-L transform: the fused passes copy it into shared memory
+  // once per CTA (measured faster there; the plain column passes read it through L1)
+  C* tws = ring0 + 3 * TT::TILE;
+  if constexpr (KIND != 0)
+    for (int m = threadIdx.x; m < L; m += blockDim.x) tws[m] = __ldg(tw + m);
+  const SmemTw<C> stw{tws};
   __shared__ unsigned long long bars[2];
   const int items = KIND == 0 ? job.nbuf * tiles_per_buf : tiles_per_buf;
   const int my_items = blockIdx.x < (unsigned)items ? (items - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -205,21 +212,21 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, TmaJob<T> job, int tiles_per_bu
       zc.d12 = job.dtab ? job.dtab[zc.f1 < 0 ? zc.f1 + N : zc.f1] * job.dtab[zc.f2] : (T)1;
       DenseTile<C, TT::LD> wt{work};
       if constexpr (KIND == 1) {
-        fft_tile<T, L, TT::TC, TT::NT, -1>(t, t, t, tw);
+        fft_tile<T, L, TT::TC, TT::NT, -1>(t, t, t, stw);
         __syncthreads();
 #pragma unroll 1
         for (int cc = 0; cc < 3; ++cc) {
           DenseMulSrc<T, N, TT::LD> src{cur, zc, cc};
           GlobalSeq<C> g{job.out[cc] + base, es, true};
-          fft_tile<T, L, TT::TC, TT::NT, +1>(src, wt, g, tw);
+          fft_tile<T, L, TT::TC, TT::NT, +1>(src, wt, g, stw);
         }
       } else {
         DenseAccDst<T, N, TT::LD> acc{work, zc, comp};
-        fft_tile<T, L, TT::TC, TT::NT, -1>(t, t, acc, tw);
+        fft_tile<T, L, TT::TC, TT::NT, -1>(t, t, acc, stw);
         if (comp == 2) {
           __syncthreads();
           GlobalSeq<C> g{job.out[0] + base, es, true};
-          fft_tile<T, L, TT::TC, TT::NT, +1>(wt, wt, g, tw);
+          fft_tile<T, L, TT::TC, TT::NT, +1>(wt, wt, g, stw);
         }
       }
     }
