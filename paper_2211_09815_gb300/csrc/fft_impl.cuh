@@ -43,6 +43,80 @@ k_fft_cols(const SeqMap mm, const SeqMap ms, int ntiles_main, ColBufs<T> bufs,
   fft_tile<T, L, TL::TC, TL::NT, DIR>(g, t, g, tw);
 }
 
+// y passes of the separable force components (sequences of mm/ms as in k_fft_cols; the
+// side plane kx = n/2 has k_2 = 0 by the Nyquist rule, main columns have k_2 = kx = col).
+// Split (inverse): U -> out1 = IFFT(U), U <- IFFT(-i k_1 U).
+// Merge (forward): P_1 <- i (k_1 FFT(P_1) + k_2 FFT(P_2)).
+template <typename T, int N>
+struct GSeqNegIK {   // -i k_row v read from a global sequence
+  const cx_t<T>* p;
+  long long es;
+  bool valid;
+  __device__ __forceinline__ cx_t<T> ld(int row, int) const {
+    if (!valid) return cmake<cx_t<T>>(0, 0);
+    const cx_t<T> v = p[(long long)row * es];
+    const T s = (T)fc_row<N>(row);
+    return cmake<cx_t<T>>(v.y * s, -v.x * s);
+  }
+};
+template <typename T, int N, int LD>
+struct SAccIK {      // A = i k_row v into a shared tile
+  cx_t<T>* p;
+  __device__ __forceinline__ void st(int row, int c, cx_t<T> v) const {
+    const T s = (T)fc_row<N>(row);
+    p[srow(row) * LD + c] = cmake<cx_t<T>>(-v.y * s, v.x * s);
+  }
+};
+template <typename T, int LD>
+struct GMergeIK {    // out = A + i k2 v
+  const cx_t<T>* acc;
+  cx_t<T>* out;
+  long long es;
+  bool valid;
+  T k2;
+  __device__ __forceinline__ void st(int row, int c, cx_t<T> v) const {
+    if (!valid) return;
+    const cx_t<T> a = acc[srow(row) * LD + c];
+    out[(long long)row * es] = cmake<cx_t<T>>(a.x - v.y * k2, a.y + v.x * k2);
+  }
+};
+
+template <typename T, int L, int MODE>   // MODE 1: split, 2: merge
+__global__ void __launch_bounds__(ColTile<T, L>::NT, 1)
+k_fft_cols_yx(const SeqMap mm, const SeqMap ms, int ntiles_main, ColBufs<T> bufs,
+              const cx_t<T>* __restrict__ tw) {
+  using C = cx_t<T>;
+  using TL = ColTile<T, L>;
+  constexpr int TILE = skew_rows(L) * TL::LD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* A = reinterpret_cast<C*>(smem_raw);
+  C* B = A + TILE;
+  const bool side = blockIdx.x >= (unsigned)ntiles_main;
+  const SeqMap& m = side ? ms : mm;
+  const int s0 = (side ? blockIdx.x - ntiles_main : blockIdx.x) * TL::TC;
+  const int s = s0 + threadIdx.x % TL::TC;
+  const bool valid = s < m.nseq;
+  const long long off = valid ? seq_base(m, s) : 0;
+  SmemTile<C, TL::LD> ta{A};
+  if constexpr (MODE == 1) {
+    GlobalSeq<C> gu{bufs.p[0] + off, m.es, valid};
+    GlobalSeq<C> g1{bufs.p[1] + off, m.es, valid};
+    fft_tile<T, L, TL::TC, TL::NT, +1>(gu, ta, g1, tw);
+    __syncthreads();
+    GSeqNegIK<T, L> src{bufs.p[0] + off, m.es, valid};
+    fft_tile<T, L, TL::TC, TL::NT, +1>(src, ta, gu, tw);
+  } else {
+    GlobalSeq<C> g1{bufs.p[0] + off, m.es, valid};
+    GlobalSeq<C> g2{bufs.p[1] + off, m.es, valid};
+    SAccIK<T, L, TL::LD> acc{B};
+    fft_tile<T, L, TL::TC, TL::NT, -1>(g1, ta, acc, tw);
+    __syncthreads();
+    const T k2 = side ? (T)0 : (T)(s % m.ncols);
+    GMergeIK<T, TL::LD> dst{B, bufs.p[0] + off, m.es, valid, k2};
+    fft_tile<T, L, TL::TC, TL::NT, -1>(g2, ta, dst, tw);
+  }
+}
+
 // ---------------------------------------------------------------- x pass, R2C
 // rows of n = 2L reals -> L complex (main) + 1 (side).  The row pairs (2j, 2j+1) are read
 // as one complex number and transformed as L-point sequences; the even/odd split below
@@ -184,6 +258,7 @@ k_fft_x_c2r(RowJob<T> job, int nrows, const cx_t<T>* __restrict__ twL, const cx_
 // C2R x pass of four components at once, writing one V4 per cell ([cell](c0, c1, c2, c3),
 // instances back to back) so that a gather reads all components of a corner with one
 // load.  The block holds TR/4 rows of each component; a null spectrum pointer reads as 0.
+// Component dq (or none if dq < 0) is multiplied by -i k_x on the way in.
 template <typename T, int L, int Q> struct C2R4Tile {
   static constexpr int RT = RowTile<T, L>::TR / 4;       // rows per block
   static constexpr int TR = Q * RT;                      // sequences per block
@@ -194,7 +269,7 @@ template <typename T, int L, int Q> struct C2R4Tile {
 
 template <typename T, int L, int Q>
 __global__ void __launch_bounds__(C2R4Tile<T, L, Q>::NT)
-k_fft_x_c2r4(RowJob<T> job, int nrows, V4<T>* __restrict__ out4, const cx_t<T>* __restrict__ twL,
+k_fft_x_c2r4(RowJob<T> job, int nrows, int dq, V4<T>* __restrict__ out4, const cx_t<T>* __restrict__ twL,
              const cx_t<T>* __restrict__ twN) {
   using C = cx_t<T>;
   using TL = C2R4Tile<T, L, Q>;
@@ -220,6 +295,12 @@ k_fft_x_c2r4(RowJob<T> job, int nrows, V4<T>* __restrict__ out4, const cx_t<T>* 
       const C* in = base + (grow % rows_per_inst) * L;
       xk[it] = in[k];
       xm[it] = k == 0 ? base[spec_main_len(N) + (grow % rows_per_inst)] : in[L - k];
+      if (q == dq) {
+        // component dq is the x derivative -i k_x of its spectrum (Nyquist kx = L: 0)
+        const T sk = (T)k, sl = k == 0 ? (T)0 : (T)(L - k);
+        xk[it] = cmake<C>(xk[it].y * sk, -xk[it].x * sk);
+        xm[it] = cmake<C>(xm[it].y * sl, -xm[it].x * sl);
+      }
     }
   }
 #pragma unroll
@@ -312,34 +393,43 @@ struct GreenSeq {
   }
 };
 
-// Source of the first inverse stage: A[row] * H_c, H_c v = f_c g (-i v)  (force, -ik_c G)
+// Source of an inverse z stage in the force pass, output `mode`: 0: -i k_0 G v (z force),
+// 1: G v (shared by the y and x force components, whose -i k_1, -i k_2 are constant along
+// a z column and are applied in the y and x passes)
 template <typename T, int LD>
 struct MulSrc {
   const cx_t<T>* p;
   GreenSeq<T> gs;
-  int comp;
+  int mode;
   __device__ __forceinline__ cx_t<T> ld(int row, int c) const {
     using C = cx_t<T>;
     const C v = p[srow(row) * LD + c];
     const int f0 = freq_of(row, gs.n);
-    const T s = (T)gs.fc(comp, f0) * gs.g(f0);
+    const T g = gs.g(f0);
+    if (mode == 1) return cmake<C>(v.x * g, v.y * g);
+    const T s = (T)gs.fc(0, f0) * g;
     return cmake<C>(v.y * s, -v.x * s);
   }
 };
 
-// Destination of the last forward stage in the adjoint: A[row] (+)= conj(H_c) v = f_c g (i v)
+// Destination of a forward z stage in the adjoint pass, input `mode`:
+// 0: A = conj(-i k_0 G) v = i k_0 G v;  1: A += G v (the input is i (k_1 P_1 + k_2 P_2))
 template <typename T, int LD>
 struct AccDst {
   cx_t<T>* p;
   GreenSeq<T> gs;
-  int comp;
+  int mode;
   __device__ __forceinline__ void st(int row, int c, cx_t<T> v) const {
     using C = cx_t<T>;
     const int f0 = freq_of(row, gs.n);
-    const T s = (T)gs.fc(comp, f0) * gs.g(f0);
-    const C m = cmake<C>(-v.y * s, v.x * s);
+    const T g = gs.g(f0);
     C* q = p + srow(row) * LD + c;
-    *q = comp == 0 ? m : cadd(*q, m);
+    if (mode == 1) {
+      *q = cadd(*q, cmake<C>(v.x * g, v.y * g));
+    } else {
+      const T s = (T)gs.fc(0, f0) * g;
+      *q = cmake<C>(-v.y * s, v.x * s);
+    }
   }
 };
 
@@ -356,7 +446,7 @@ __device__ __forceinline__ GreenSeq<T> green_seq(const ZSeq& q, const T* coef, c
   return gs;
 }
 
-// Forward force: delta^ (after x, y) --z FFT--> * (-i k_c G) --z IFFT--> F_c (c = 0..2)
+// Forward force: delta^ (after x, y) --z FFT--> * (-i k_0 G), * G --z IFFT--> z force, U
 template <typename T, int L>
 __global__ void __launch_bounds__(FusedTile<T, L>::NT)
 k_fused_z_force(ZJob<T> job, int ntiles_main, const cx_t<T>* __restrict__ tw) {
@@ -377,14 +467,15 @@ k_fused_z_force(ZJob<T> job, int ntiles_main, const cx_t<T>* __restrict__ tw) {
   __syncthreads();
   const GreenSeq<T> gs = green_seq<T, L>(q, job.coef, job.dtab);
 #pragma unroll 1
-  for (int c = 0; c < 3; ++c) {
+  for (int c = 0; c < 2; ++c) {
     MulSrc<T, TL::LD> src{A, gs, c};
     GlobalSeq<C> gout{pick(job.out, c) + q.base, q.es, q.valid};
     fft_tile<T, L, TL::TC, TL::NT, +1>(src, tb, gout, tw);
   }
 }
 
-// Adjoint: P_c^ (after x, y) --z FFT--> sum_c conj(-i k_c G) P_c --z IFFT--> psi
+// Adjoint: P_0, V = i (k_1 P_1 + k_2 P_2) (after x, y) --z FFT--> G (i k_0 P_0 + V)
+// --z IFFT--> psi
 template <typename T, int L>
 __global__ void __launch_bounds__(FusedTile<T, L>::NT)
 k_fused_z_adjoint(ZJob<T> job, int ntiles_main, const cx_t<T>* __restrict__ tw) {
@@ -402,7 +493,7 @@ k_fused_z_adjoint(ZJob<T> job, int ntiles_main, const cx_t<T>* __restrict__ tw) 
   const GreenSeq<T> gs = green_seq<T, L>(q, job.coef, job.dtab);
   SmemTile<C, TL::LD> ta{A}, tb{B};
 #pragma unroll 1
-  for (int c = 0; c < 3; ++c) {
+  for (int c = 0; c < 2; ++c) {
     GlobalSeq<C> gin{pick(job.in, c) + q.base, q.es, q.valid};
     AccDst<T, TL::LD> acc{A, gs, c};
     fft_tile<T, L, TL::TC, TL::NT, -1>(gin, tb, acc, tw);
@@ -429,6 +520,18 @@ static void launch_cols_L(const SeqMap& mm, const SeqMap& ms, const ColBufs<T>& 
   set_smem<T, L>((const void*)fn, sm);
   dim3 grid(ntm + nts, nbuf);
   fn<<<grid, TL::NT, sm, st>>>(mm, ms, ntm, bufs, tw + L);
+}
+
+template <typename T, int L, int MODE>
+static void launch_cols_yx_L(const SeqMap& mm, const SeqMap& ms, const ColBufs<T>& bufs, const cx_t<T>* tw,
+                             cudaStream_t st) {
+  using TL = ColTile<T, L>;
+  const int ntm = (mm.nseq + TL::TC - 1) / TL::TC;
+  const int nts = ms.nseq > 0 ? (ms.nseq + TL::TC - 1) / TL::TC : 0;
+  const size_t sm = 2 * (size_t)TL::SMEM;
+  auto fn = k_fft_cols_yx<T, L, MODE>;
+  set_smem<T, L>((const void*)fn, sm);
+  fn<<<ntm + nts, TL::NT, sm, st>>>(mm, ms, ntm, bufs, tw + L);
 }
 
 template <typename T, int L>
@@ -475,7 +578,8 @@ static void launch_tma_L(const CUtensorMap* maps, const TmaJob<T>& job, int tile
                          cudaStream_t st) {
   using TT = TmaTile<T, L>;
   TmaMaps m{};
-  for (int i = 0; i < (KIND == 0 ? job.nbuf : (KIND == 1 ? 1 : 3)); ++i) m.m[i] = maps[i];
+  const int nmaps = KIND == 0 ? job.nbuf : ((KIND == 2 || KIND == 4) ? 2 : 1);
+  for (int i = 0; i < nmaps; ++i) m.m[i] = maps[i];
   const size_t sm = KIND == 0 ? 2 * (size_t)TT::BYTES + 1024 : 3 * (size_t)TT::BYTES + (size_t)L * sizeof(cx_t<T>) + 1024;
   auto fn = k_cols_tma<T, L, DIR, KIND>;
   ensure_smem_attr((const void*)fn, (int)sm);
@@ -507,6 +611,33 @@ int fft_cols_tma(int n, int batch, int dir, int zaxis, const CUtensorMap* maps, 
   } else {
     PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, +1, 0>(maps, job, batch * tiles_of<T, LL>(), tw, nsm, st)));
   }
+  return PM_OK;
+}
+
+template <typename T>
+int fft_ysplit_tma(int n, int batch, const CUtensorMap* umap, cx_t<T>* u, cx_t<T>* out1, const cx_t<T>* tw,
+                   int* err, int nsm, cudaStream_t st) {
+  TmaJob<T> job{};
+  job.out[0] = u;
+  job.out[1] = out1;
+  job.nbuf = 1;
+  job.zaxis = 0;
+  job.batch = batch;
+  job.err = err;
+  PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, +1, 3>(umap, job, batch * tiles_of<T, LL>(), tw, nsm, st)));
+  return PM_OK;
+}
+
+template <typename T>
+int fft_ymerge_tma(int n, int batch, const CUtensorMap* pmaps, cx_t<T>* p1, const cx_t<T>* tw, int* err, int nsm,
+                   cudaStream_t st) {
+  TmaJob<T> job{};
+  job.out[0] = p1;
+  job.nbuf = 1;
+  job.zaxis = 0;
+  job.batch = batch;
+  job.err = err;
+  PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, -1, 4>(pmaps, job, batch * tiles_of<T, LL>(), tw, nsm, st)));
   return PM_OK;
 }
 
@@ -595,6 +726,26 @@ int fft_cols(int n, int dir, const SeqMap& mm, const SeqMap& ms, const ColBufs<T
 }
 
 template <typename T>
+int fft_cols_split(int n, const SeqMap& mm, const SeqMap& ms, cx_t<T>* u, cx_t<T>* out1, const cx_t<T>* tw,
+                   cudaStream_t st) {
+  ColBufs<T> b{};
+  b.p[0] = u;
+  b.p[1] = out1;
+  PMGB_DISPATCH_L(n, (launch_cols_yx_L<T, LL, 1>(mm, ms, b, tw, st)));
+  return PM_OK;
+}
+
+template <typename T>
+int fft_cols_merge(int n, const SeqMap& mm, const SeqMap& ms, cx_t<T>* p1, cx_t<T>* p2, const cx_t<T>* tw,
+                   cudaStream_t st) {
+  ColBufs<T> b{};
+  b.p[0] = p1;
+  b.p[1] = p2;
+  PMGB_DISPATCH_L(n, (launch_cols_yx_L<T, LL, 2>(mm, ms, b, tw, st)));
+  return PM_OK;
+}
+
+template <typename T>
 int fft_x_r2c(int n, const RowJob<T>& job, int nbuf, int nrows, const cx_t<T>* tw,
               cudaStream_t st) {
   if (n < 4 || n > 1024) return PM_ERR_ARG;
@@ -603,25 +754,27 @@ int fft_x_r2c(int n, const RowJob<T>& job, int nbuf, int nrows, const cx_t<T>* t
 }
 
 template <typename T, int L, int Q>
-static void launch_c2r4_LQ(const RowJob<T>& job, int nrows, V4<T>* out4, const cx_t<T>* tw, cudaStream_t st) {
+static void launch_c2r4_LQ(const RowJob<T>& job, int nrows, int dq, V4<T>* out4, const cx_t<T>* tw,
+                           cudaStream_t st) {
   using TL = C2R4Tile<T, L, Q>;
   if constexpr (RowTile<T, L>::TR % 4 == 0 && (TL::TR * L) % Plan<L>::RMAX == 0) {
     const size_t sm = TL::SMEM;
     auto fn = k_fft_x_c2r4<T, L, Q>;
     set_smem<T, L>((const void*)fn, sm);
-    fn<<<(nrows + TL::RT - 1) / TL::RT, TL::NT, sm, st>>>(job, nrows, out4, tw + L, tw + 2 * L);
+    fn<<<(nrows + TL::RT - 1) / TL::RT, TL::NT, sm, st>>>(job, nrows, dq, out4, tw + L, tw + 2 * L);
   }
 }
 template <typename T, int L>
-static void launch_c2r4_L(const RowJob<T>& job, int nrows, V4<T>* out4, const cx_t<T>* tw, cudaStream_t st) {
-  if (job.b[3].spec) launch_c2r4_LQ<T, L, 4>(job, nrows, out4, tw, st);
-  else launch_c2r4_LQ<T, L, 3>(job, nrows, out4, tw, st);
+static void launch_c2r4_L(const RowJob<T>& job, int nrows, int dq, V4<T>* out4, const cx_t<T>* tw,
+                          cudaStream_t st) {
+  if (job.b[3].spec) launch_c2r4_LQ<T, L, 4>(job, nrows, dq, out4, tw, st);
+  else launch_c2r4_LQ<T, L, 3>(job, nrows, dq, out4, tw, st);
 }
 
 template <typename T>
-int fft_x_c2r4(int n, const RowJob<T>& job, int nrows, V4<T>* out4, const cx_t<T>* tw, cudaStream_t st) {
+int fft_x_c2r4(int n, const RowJob<T>& job, int nrows, int dq, V4<T>* out4, const cx_t<T>* tw, cudaStream_t st) {
   if (n < 8 || n > 1024) return PM_ERR_ARG;
-  PMGB_DISPATCH_L(n / 2, (launch_c2r4_L<T, (LL < 512 ? LL : 512)>(job, nrows, out4, tw, st)));
+  PMGB_DISPATCH_L(n / 2, (launch_c2r4_L<T, (LL < 512 ? LL : 512)>(job, nrows, dq, out4, tw, st)));
   return PM_OK;
 }
 

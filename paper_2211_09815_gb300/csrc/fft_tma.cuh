@@ -7,8 +7,13 @@
 // CTA works on the current tile, so HBM reads of tile t+1 overlap the radix stages of
 // tile t.  Results leave through the last radix stage's direct global stores.
 //   KIND 0: in-place column FFT of up to four buffers (direction DIR)
-//   KIND 1: z FFT of delta^, times -ik_c G / M per component, 3 inverse z FFTs (force)
-//   KIND 2: z FFTs of pi_c^ accumulated with conj(-ik_c G) / M, 1 inverse z FFT (adjoint)
+//   KIND 1: z FFT of delta^, 2 inverse z FFTs: of -i k_0 G delta^ (z force) and of
+//           G delta^ (shared by the y and x force components; -i k_1 and -i k_2 are
+//           constant along a z column)
+//   KIND 2: z FFTs of P_0 and of V = i (k_1 P_1 + k_2 P_2), accumulated as
+//           G (i k_0 P_0 + V), 1 inverse z FFT (adjoint psi)
+//   KIND 3: inverse y of U: IFFT(U) and IFFT(-i k_1 U)
+//   KIND 4: forward y of P_1 and P_2 into V = i (k_1 Y(P_1) + k_2 Y(P_2))
 // Every mbarrier wait is bounded: on timeout the CTA records an error flag, waits (again
 // bounded) for its own copies in flight, and returns.
 #pragma once
@@ -21,7 +26,8 @@ namespace pmgb {
 struct TmaMaps { CUtensorMap m[4]; };
 
 template <typename T> struct TmaJob {
-  cx_t<T>* out[4];     // KIND 0: the buffers themselves; KIND 1: F_0..2; KIND 2: psi
+  cx_t<T>* out[4];     // KIND 0: the buffers; 1: z force, U; 2: psi; 3: y force (U's buffer),
+                       // x force before -i k_2; 4: V (P_1's buffer)
   int nbuf;            // KIND 0: buffers in the launch
   int zaxis;           // 0: y pass, 1: z pass
   int batch;
@@ -101,29 +107,76 @@ struct ZCol {
   }
 };
 
+// z pass, force: multiplier of the inverse transform of output `mode`:
+//   0: -i k_0 G (the z component), 1: G (shared by the y and x components, whose -i k_1
+//   and -i k_2 are constant along a z column and are applied in the y and x passes)
 template <typename T, int N, int LD>
 struct DenseMulSrc {
   const cx_t<T>* p;
   ZCol<T, N> z;
-  int comp;
+  int mode;
   __device__ __forceinline__ cx_t<T> ld(int row, int c) const {
     const cx_t<T> v = p[row * LD + c];
     const int f0 = freq_of(row, N);
-    const T s = (T)z.fc(comp, f0) * z.g(f0);
+    const T g = z.g(f0);
+    if (mode == 1) return cmake<cx_t<T>>(v.x * g, v.y * g);
+    const T s = (T)z.fc(0, f0) * g;
     return cmake<cx_t<T>>(v.y * s, -v.x * s);
   }
 };
+// z pass, adjoint: the last forward stage of input `mode` into the accumulator:
+//   0: A = conj(-i k_0 G) v = i k_0 G v;  1: A += G v (the input already carries
+//   i (k_1 P_1 + k_2 P_2), formed in the y pass)
 template <typename T, int N, int LD>
 struct DenseAccDst {
   cx_t<T>* p;
   ZCol<T, N> z;
-  int comp;
+  int mode;
   __device__ __forceinline__ void st(int row, int c, cx_t<T> v) const {
     const int f0 = freq_of(row, N);
-    const T s = (T)z.fc(comp, f0) * z.g(f0);
-    const cx_t<T> m = cmake<cx_t<T>>(-v.y * s, v.x * s);
+    const T g = z.g(f0);
     cx_t<T>* q = p + row * LD + c;
-    *q = comp == 0 ? m : cadd(*q, m);
+    if (mode == 1) {
+      *q = cadd(*q, cmake<cx_t<T>>(v.x * g, v.y * g));
+    } else {
+      const T s = (T)z.fc(0, f0) * g;
+      *q = cmake<cx_t<T>>(-v.y * s, v.x * s);
+    }
+  }
+};
+// signed frequency along a column with the Nyquist row zeroed (derivative rule)
+template <int N> __device__ __forceinline__ int fc_row(int row) {
+  const int f = freq_of(row, N);
+  return f == -N / 2 ? 0 : f;
+}
+// y pass, inverse split: source -i k_1 v of the y component
+template <typename T, int N, int LD>
+struct YMulSrc {
+  const cx_t<T>* p;
+  __device__ __forceinline__ cx_t<T> ld(int row, int c) const {
+    const cx_t<T> v = p[row * LD + c];
+    const T s = (T)fc_row<N>(row);
+    return cmake<cx_t<T>>(v.y * s, -v.x * s);
+  }
+};
+// y pass, forward merge: A = i k_1 Y(P_1), then out = A + i k_2 Y(P_2) written to HBM
+template <typename T, int N, int LD>
+struct YAccDst {
+  cx_t<T>* p;
+  __device__ __forceinline__ void st(int row, int c, cx_t<T> v) const {
+    const T s = (T)fc_row<N>(row);
+    p[row * LD + c] = cmake<cx_t<T>>(-v.y * s, v.x * s);
+  }
+};
+template <typename T, int LD>
+struct YMergeDst {
+  const cx_t<T>* acc;
+  cx_t<T>* out;     // this thread's column in HBM
+  long long es;
+  T k2;             // x frequency of the column
+  __device__ __forceinline__ void st(int row, int c, cx_t<T> v) const {
+    const cx_t<T> a = acc[row * LD + c];
+    out[(long long)row * es] = cmake<cx_t<T>>(a.x - v.y * k2, a.y + v.x * k2);
   }
 };
 
@@ -135,7 +188,7 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaJob<
   using TT = TmaTile<T, L>;
   constexpr int N = L;
   constexpr int NCG = (N / 2) / TT::TC;            // column groups per row of the main array
-  constexpr int NL = KIND == 2 ? 3 : 1;            // loads per work item
+  constexpr int NL = (KIND == 2 || KIND == 4) ? 2 : 1;   // loads per work item
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // TMA destinations must be 128-byte aligned: round the dynamic base up (1 KiB slack)
   C* ring0 = reinterpret_cast<C*>((reinterpret_cast<unsigned long long>(smem_raw) + 1023ull) & ~1023ull);
@@ -202,7 +255,7 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaJob<
     if constexpr (KIND == 0) {
       GlobalSeq<C> g{job.out[item / tiles_per_buf] + base, es, true};
       fft_tile<T, L, TT::TC, TT::NT, DIR>(t, t, g, tw);
-    } else {
+    } else if constexpr (KIND == 1 || KIND == 2) {
       ZCol<T, N> zc;
       zc.f1 = freq_of(o, N);
       zc.f2 = kxg * TT::TC + c;
@@ -215,7 +268,7 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaJob<
         fft_tile<T, L, TT::TC, TT::NT, -1>(t, t, t, stw);
         __syncthreads();
 #pragma unroll 1
-        for (int cc = 0; cc < 3; ++cc) {
+        for (int cc = 0; cc < 2; ++cc) {
           DenseMulSrc<T, N, TT::LD> src{cur, zc, cc};
           GlobalSeq<C> g{job.out[cc] + base, es, true};
           fft_tile<T, L, TT::TC, TT::NT, +1>(src, wt, g, stw);
@@ -223,11 +276,30 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaJob<
       } else {
         DenseAccDst<T, N, TT::LD> acc{work, zc, comp};
         fft_tile<T, L, TT::TC, TT::NT, -1>(t, t, acc, stw);
-        if (comp == 2) {
+        if (comp == 1) {
           __syncthreads();
           GlobalSeq<C> g{job.out[0] + base, es, true};
           fft_tile<T, L, TT::TC, TT::NT, +1>(wt, wt, g, stw);
         }
+      }
+    } else if constexpr (KIND == 3) {
+      // inverse y of the shared x/y force transform U: IFFT(U) -> out[1] (the x component
+      // before its -i k_2), IFFT(-i k_1 U) -> out[0] (the y component, in place)
+      DenseTile<C, TT::LD> wt{work};
+      GlobalSeq<C> g1{job.out[1] + base, es, true};
+      fft_tile<T, L, TT::TC, TT::NT, +1>(t, wt, g1, stw);
+      __syncthreads();
+      YMulSrc<T, N, TT::LD> src{cur};
+      GlobalSeq<C> g0{job.out[0] + base, es, true};
+      fft_tile<T, L, TT::TC, TT::NT, +1>(src, t, g0, stw);
+    } else {
+      // forward y of the adjoint's x and y sums: out[0] = i (k_1 Y(P_1) + k_2 Y(P_2))
+      if (comp == 0) {
+        YAccDst<T, N, TT::LD> acc{work};
+        fft_tile<T, L, TT::TC, TT::NT, -1>(t, t, acc, stw);
+      } else {
+        YMergeDst<T, TT::LD> dst{work, job.out[0] + base, es, (T)(kxg * TT::TC + c)};
+        fft_tile<T, L, TT::TC, TT::NT, -1>(t, t, dst, stw);
       }
     }
     __syncthreads();

@@ -713,9 +713,12 @@ class Engine : public EngineBase {
     return PM_OK;
   }
 
-  // Force on the mesh (Sec. 2.2): scatter -> R2C -> Green's function and -ik -> 3 C2R,
-  // leaving f_c in spec_[1..3] (real view).  With pi also the adjoint chain: pi scatter ->
-  // 3 R2C -> sum_c conj(H_c) -> C2R, leaving psi in spec_[0].
+  // Force on the mesh (Sec. 2.2): scatter -> R2C -> Green's function and -ik -> 3 C2R into
+  // the [cell][4] mesh fvec_.  With pi also the adjoint chain: pi scatter -> 3 R2C ->
+  // sum_c conj(H_c) -> C2R (psi, the fourth component).  The x and y components share
+  // the inverse z transform of G delta^ (-i k_1, -i k_2 are constant along a z column and
+  // are applied in the y and x passes); the adjoint's x and y terms are combined in the
+  // forward y pass, so the z passes transform 3 columns each instead of 4.
   int force_chain(const T* s, const T* pi, bool keep_density) {
     // delta goes to the real view of spec_[0] (transformed in place) or, when the final
     // density is kept for the objective, to dens_
@@ -732,15 +735,18 @@ class Engine : public EngineBase {
     PMGB_RET(fft_x_r2c<T>(nm_, job, nb, B_ * nm_ * nm_, tw_, st_));
     prof_.end(st_, P_X_R2C);
     PMGB_CK(cudaGetLastError());
-    C* fwdb[4] = {spec_[0], spec_[4], spec_[5], spec_[6]};
-    prof_.begin(st_, P_COLS, 2);
-    PMGB_RET(cols(nm_, -1, false, fwdb, nb));
+    // y forward: delta (and P_0) in place; the adjoint's P_1 and P_2 merge into
+    // V = i (k_1 P_1 + k_2 P_2) in spec_[5]
+    C* fwdb[2] = {spec_[0], spec_[4]};
+    prof_.begin(st_, P_COLS, pi ? 4 : 2);
+    PMGB_RET(cols(nm_, -1, false, fwdb, pi ? 2 : 1));
+    if (pi) PMGB_RET(cols_yx(false, spec_[5], spec_[6]));
     prof_.end(st_, P_COLS);
+    // z: delta^ -> z force (spec_[1]) and U = IFFT_z(G delta^) (spec_[2])
     ZJob<T> zf{};
     zf.in[0] = spec_[0];
     zf.out[0] = spec_[1];
     zf.out[1] = spec_[2];
-    zf.out[2] = spec_[3];
     zf.coef = gcoef_;
     zf.dtab = dtab_;
     zf.batch = B_;
@@ -754,15 +760,16 @@ class Engine : public EngineBase {
     prof_.end(st_, P_Z_FORCE);
     PMGB_CK(cudaGetLastError());
     if (pi) {
+      // z: G (i k_0 P_0 + V) -> psi (spec_[0])
       ZJob<T> za = zf;
       za.in[0] = spec_[4];
       za.in[1] = spec_[5];
-      za.in[2] = spec_[6];
       za.out[0] = spec_[0];
+      za.out[1] = nullptr;
       prof_.begin(st_, P_Z_ADJ, use_tma_ ? 2 : 1);
       if (use_tma_) {
-        const CUtensorMap pm3[3] = {tmz_[4], tmz_[5], tmz_[6]};
-        PMGB_RET(fft_fused_tma<T>(nm_, true, pm3, za, tw_, dev_err_, nsm_, st_));
+        const CUtensorMap pm2[2] = {tmz_[4], tmz_[5]};
+        PMGB_RET(fft_fused_tma<T>(nm_, true, pm2, za, tw_, dev_err_, nsm_, st_));
         PMGB_RET(fft_fused_side<T>(nm_, za, true, tw_, st_));
       } else {
         PMGB_RET(fft_fused_z<T>(nm_, za, true, tw_, st_));
@@ -770,16 +777,54 @@ class Engine : public EngineBase {
       prof_.end(st_, P_Z_ADJ);
       PMGB_CK(cudaGetLastError());
     }
-    C* invb[4] = {spec_[1], spec_[2], spec_[3], spec_[0]};
-    prof_.begin(st_, P_COLS, 2);
-    PMGB_RET(cols(nm_, +1, false, invb, nb == 4 ? 4 : 3));
+    // y inverse: z force (and psi) in place; U splits into the y force (spec_[2]) and the
+    // x force before its -i k_x (spec_[3])
+    C* invb[2] = {spec_[1], spec_[0]};
+    prof_.begin(st_, P_COLS, 4);
+    PMGB_RET(cols(nm_, +1, false, invb, pi ? 2 : 1));
+    PMGB_RET(cols_yx(true, spec_[2], spec_[3]));
     prof_.end(st_, P_COLS);
-    // C2R of f_0..2 (and psi) into one interleaved [cell][4] mesh for the gathers
+    // C2R of f_0..2 (and psi) into one interleaved [cell][4] mesh for the gathers; the x
+    // force takes its -i k_x here
+    C* c2rb[4] = {spec_[1], spec_[2], spec_[3], spec_[0]};
     RowJob<T> jc{};
-    for (int q = 0; q < 4; ++q) jc.b[q] = RowBuf<T>{nullptr, 0, (q < 3 || pi) ? invb[q] : nullptr};
+    for (int q = 0; q < 4; ++q) jc.b[q] = RowBuf<T>{nullptr, 0, (q < 3 || pi) ? c2rb[q] : nullptr};
     prof_.begin(st_, P_X_C2R, 1);
-    PMGB_RET(fft_x_c2r4<T>(nm_, jc, B_ * nm_ * nm_, reinterpret_cast<V4<T>*>(fvec_), tw_, st_));
+    PMGB_RET(fft_x_c2r4<T>(nm_, jc, B_ * nm_ * nm_, 2, reinterpret_cast<V4<T>*>(fvec_), tw_, st_));
     prof_.end(st_, P_X_C2R);
+    PMGB_CK(cudaGetLastError());
+    return PM_OK;
+  }
+
+  // y pass of the separable force components on the mesh spectra: split (inverse) u ->
+  // u = IFFT(-i k_1 u), b = IFFT(u); merge (forward) u = i (k_1 FFT(u) + k_2 FFT(b))
+  int cols_yx(bool split, C* u, C* b) {
+    const int n = nm_;
+    SeqMap none = yside(n);
+    none.nseq = 0;
+    if (use_tma_) {
+      const int iu = spec_index(u), ib = spec_index(b);
+      if (iu < 0 || ib < 0) return PM_ERR_STATE;
+      if (split) {
+        PMGB_RET(fft_ysplit_tma<T>(n, B_, &tmy_[iu], u, b, tw_, dev_err_, nsm_, st_));
+      } else {
+        const CUtensorMap pm2[2] = {tmy_[iu], tmy_[ib]};
+        PMGB_RET(fft_ymerge_tma<T>(n, B_, pm2, u, tw_, dev_err_, nsm_, st_));
+      }
+    } else if (split) {
+      PMGB_RET(fft_cols_split<T>(n, ymap(n), none, u, b, tw_, st_));
+    } else {
+      PMGB_RET(fft_cols_merge<T>(n, ymap(n), none, u, b, tw_, st_));
+    }
+    PMGB_CK(cudaGetLastError());
+    // side planes (kx = n/2): launched as side sequences, so that k_2 = 0 there
+    C* us = u + spec_main_len(n);
+    C* bs = b + spec_main_len(n);
+    if (split) {
+      PMGB_RET(fft_cols_split<T>(n, none, yside(n), us, bs, tw_, st_));
+    } else {
+      PMGB_RET(fft_cols_merge<T>(n, none, yside(n), us, bs, tw_, st_));
+    }
     PMGB_CK(cudaGetLastError());
     return PM_OK;
   }

@@ -44,14 +44,24 @@ template <typename T> struct ZJob {
 template <typename T>
 int fft_cols(int n, int dir, const SeqMap& mm, const SeqMap& ms, const ColBufs<T>& bufs, int nbuf,
              const cx_t<T>* tw, cudaStream_t st);
+// y passes of the separable force components (main columns of mm and side columns of ms):
+// split (inverse): out1 = IFFT(u), u = IFFT(-i k_1 u); merge (forward):
+// p1 = i (k_1 FFT(p1) + k_2 FFT(p2))
+template <typename T>
+int fft_cols_split(int n, const SeqMap& mm, const SeqMap& ms, cx_t<T>* u, cx_t<T>* out1, const cx_t<T>* tw,
+                   cudaStream_t st);
+template <typename T>
+int fft_cols_merge(int n, const SeqMap& mm, const SeqMap& ms, cx_t<T>* p1, cx_t<T>* p2, const cx_t<T>* tw,
+                   cudaStream_t st);
 template <typename T>
 int fft_x_r2c(int n, const RowJob<T>& job, int nbuf, int nrows, const cx_t<T>* tw,
               cudaStream_t st);
 template <typename T>
 int fft_x_c2r(int n, const RowJob<T>& job, int nbuf, int nrows, const cx_t<T>* tw, cudaStream_t st);
-// C2R of up to four components into one interleaved [cell][4] real mesh
+// C2R of up to four components into one interleaved [cell][4] real mesh; component dq
+// (none if dq < 0) is multiplied by -i k_x first
 template <typename T>
-int fft_x_c2r4(int n, const RowJob<T>& job, int nrows, V4<T>* out4, const cx_t<T>* tw, cudaStream_t st);
+int fft_x_c2r4(int n, const RowJob<T>& job, int nrows, int dq, V4<T>* out4, const cx_t<T>* tw, cudaStream_t st);
 template <typename T>
 int fft_fused_z(int n, const ZJob<T>& job, bool adjoint, const cx_t<T>* tw, cudaStream_t st);
 
@@ -63,6 +73,13 @@ int fft_cols_tma(int n, int batch, int dir, int zaxis, const CUtensorMap* maps, 
 template <typename T>
 int fft_fused_tma(int n, bool adjoint, const CUtensorMap* maps, const ZJob<T>& job, const cx_t<T>* tw, int* err,
                   int nsm, cudaStream_t st);
+// the same split and merge over the main spectrum with TMA-staged tiles
+template <typename T>
+int fft_ysplit_tma(int n, int batch, const CUtensorMap* umap, cx_t<T>* u, cx_t<T>* out1, const cx_t<T>* tw,
+                   int* err, int nsm, cudaStream_t st);
+template <typename T>
+int fft_ymerge_tma(int n, int batch, const CUtensorMap* pmaps, cx_t<T>* p1, const cx_t<T>* tw, int* err, int nsm,
+                   cudaStream_t st);
 // the side-plane (kx = n/2) tiles of the fused z passes only
 template <typename T>
 int fft_fused_side(int n, const ZJob<T>& job, bool adjoint, const cx_t<T>* tw, cudaStream_t st);
