@@ -60,9 +60,13 @@ def algorithmic_bytes(n_steps, N, M, batch=1):
     b = {
         "scatter": f * (4 * M + 12 * N) + f * (16 * M + 24 * N),
         "fft_x_r2c": f * 8 * M + f * 32 * M,
-        "fft_cols": f * (8 * M + 24 * M) + f * (32 * M + 32 * M),
-        "fused_z_force": 2 * f * 16 * M,
-        "fused_z_adjoint": f * 16 * M,
+        # y passes: forward chain delta (8M) + z force (8M) + the x/y split (4M in, 8M out);
+        # adjoint chain delta, P_0 (16M) + the x/y merge (8M in, 4M out) + z force, psi
+        # (16M) + split (12M)
+        "fft_cols": f * (8 * M + 8 * M + 12 * M) + f * (16 * M + 12 * M + 16 * M + 12 * M),
+        # z passes: 1 spectrum in, 2 out (force); 2 in, 1 out (adjoint)
+        "fused_z_force": 2 * f * 12 * M,
+        "fused_z_adjoint": f * 12 * M,
         "fft_x_c2r": f * 24 * M + f * 32 * M,
         "gather_fwd": f * (12 * M + 48 * N),
         "gather_adj": f * (16 * M + 96 * N),
@@ -213,6 +217,11 @@ def run_ours(args, rank, world, local_rank):
     gw = torch.empty(N, device="cuda")
     gt = torch.zeros(5, dtype=torch.float64, device="cuda")
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    tuning = None
+    if not args.no_autotune:
+        # launch shapes from the autotuner, timed on the final (clustered) forward state
+        ctx.forward()
+        tuning, _ = ctx.autotune()
 
     def evaluation():
         ctx.forward()
@@ -300,7 +309,9 @@ def run_ours(args, rank, world, local_rank):
                                "ZA ICs, density MSE, reverse-time adjoint; one bench step = one gradient "
                                "evaluation", "batch": 1, "ckpt_every": 0,
                    "l2": "inputs larger than L2 (every mesh pass streams 4.3-8.6 GB)",
-                   "parallelism": f"replicas x{world}", "ms_per_pm_step": ms_per_eval / n},
+                   "parallelism": f"replicas x{world}", "ms_per_pm_step": ms_per_eval / n,
+                   "tuning": tuning if tuning is not None else "defaults"},
+        "particle_updates_per_s": 2 * N * value,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
                      "traffic": traffic, "alg_bytes": alg[dom] / (n + 1),
@@ -358,6 +369,55 @@ def run_op_case(args):
                       "alpha_rms": float(alpha.pow(2).mean().sqrt())}))
 
 
+def run_fft_compare(args):
+    """The hand-written 3-D R2C and C2R of a 1024^3 FP32 mesh (pm_op_fft: x, y and z passes
+    plus the conversion to the standard [n][n][n/2+1] layout) timed beside cuFFT through
+    torch.fft (a reference point, not part of the path), same input, CUDA events."""
+    import torch
+    from paper_2211_09815_gb300 import build, inputs, pm
+    build.build()
+    nm = 1024 if args.workload == "large" else WORKLOADS[args.workload][1]
+    npc = 64
+    om = torch.from_numpy(inputs.white_noise(npc, 1)).to("cuda")
+    ctx = pm.PMContext(1000.0, nm, npc, 1, [THETA], om)
+    x = torch.randn(nm, nm, nm, device="cuda", generator=torch.Generator(device="cuda").manual_seed(1))
+    spec = torch.empty(nm, nm, nm // 2 + 1, 2, device="cuda")
+    back = torch.empty(nm, nm, nm, device="cuda")
+
+    def timed(fn, reps=5):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        t = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            t.append(a.elapsed_time(b))
+        return sorted(t)[len(t) // 2]
+
+    ours_r2c = timed(lambda: ctx.op_fft(-1, x, spec))
+    ours_c2r = timed(lambda: ctx.op_fft(+1, spec, back))
+    ref = torch.fft.rfftn(x)
+    got = torch.view_as_complex(spec)
+    err = float((got - ref).abs().max() / ref.abs().max())
+    del ref, got
+    ctx.close()
+    torch.cuda.empty_cache()
+    cufft_r2c = timed(lambda: torch.fft.rfftn(x))
+    X = torch.fft.rfftn(x)
+    cufft_c2r = timed(lambda: torch.fft.irfftn(X, s=(nm, nm, nm)))
+    gb = (4 * nm ** 3 + 8 * nm * nm * (nm // 2 + 1)) / 1e9
+    print(json.dumps({"mode": "fft_compare", "mesh": nm, "dtype": "f32",
+                      "ours_ms": {"r2c": ours_r2c, "c2r": ours_c2r},
+                      "cufft_ms": {"r2c": cufft_r2c, "c2r": cufft_c2r},
+                      "io_GB_per_transform": gb,
+                      "ours_note": "x, y, z passes + layout conversion to [n][n][n/2+1]",
+                      "max_rel_diff_vs_cufft": err}))
+
+
 def run_batched(args):
     """Batched ensemble: 16 instances of 128^3 particles on 256^3 meshes (200 Mpc/h), own
     seed and theta each, 32 steps, forward + adjoint.  The batched context runs every
@@ -377,6 +437,8 @@ def run_batched(args):
         ctx = pm.PMContext(box, nm, npc, n, theta.tolist(), om_t, batch=B, stream=stream)
         tgt = torch.empty(B * M, device="cuda")
         ctx.forward(dens=tgt)
+        # launch shapes from the autotuner, timed on the final (clustered) state
+        out["tuning"], out["tuned_ms"] = ctx.autotune()
         ctx.set_inputs(omega=om)
         loss = torch.zeros(B, dtype=torch.float64, device="cuda")
         gw = torch.empty(B * N, device="cuda")
@@ -547,7 +609,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--batched", action="store_true", help="16-instance batched graph vs sequential runs")
+    ap.add_argument("--fft-compare", action="store_true", help="hand-written 3-D FFT beside cuFFT (torch.fft)")
     ap.add_argument("--compare-ckpt", action="store_true", help="reverse time vs checkpoints: memory/time")
     ap.add_argument("--precision-study", action="store_true", help="FP32 vs FP64 GPU run, errors per output")
     ap.add_argument("--op-case", action="store_true",
@@ -556,7 +620,9 @@ def main():
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
-    if args.batched:
+    if args.fft_compare:
+        run_fft_compare(args)
+    elif args.batched:
         run_batched(args)
     elif args.compare_ckpt:
         run_ckpt_compare(args)

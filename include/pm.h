@@ -190,6 +190,47 @@ const char* pm_last_cuda_error(void);
 /* Bytes of device scratch the context holds. */
 long long pm_scratch_bytes(const pm_ctx* ctx);
 
+/*
+ * Launch shapes of the tunable passes (not in the paper; they change speed, never
+ * results: the CIC sums are exact integers for any tile shape, and the staged and
+ * unstaged column passes run the same radix stages).
+ *   tile_log2_density[3] : log2 of the deposit tile extent along axes (z, y, x), the
+ *                          density-only deposit of the forward steps; 9..11 in total
+ *   tile_log2_adjoint[3] : the same for the density + pi deposit of the adjoint steps
+ *   threads_density,
+ *   threads_adjoint      : threads per tile, 256 or 512
+ *   tma_columns          : 1 = TMA-staged persistent y/z column passes (meshes 128..1024),
+ *                          0 = unstaged column passes
+ */
+typedef struct pm_tuning {
+  int tile_log2_density[3];
+  int tile_log2_adjoint[3];
+  int threads_density;
+  int threads_adjoint;
+  int tma_columns;
+} pm_tuning;
+
+/* Current launch shapes.  Errors: PM_ERR_ARG (null pointers). */
+int pm_get_tuning(pm_ctx* ctx, pm_tuning* out);
+
+/* Set launch shapes (validated on the host: PM_ERR_ARG if out of range, or tma_columns = 1
+ * for a mesh size without the staged passes). */
+int pm_set_tuning(pm_ctx* ctx, const pm_tuning* t);
+
+/*
+ * Autotuner: times every candidate deposit tile shape x threads per tile (for the forward
+ * and the adjoint deposit separately) and both column-pass forms on the context's current
+ * particle state (the final state of the last pm_forward, else the Zel'dovich state), each
+ * `reps` times with CUDA events on the context's stream (median; reps = 0 means 3), and
+ * keeps the fastest.  Uses the context's scratch meshes and its adjoint buffers as scratch
+ * (a following pm_adjoint re-initialises them); the forward state is kept.  Synchronises.
+ *   chosen  : optional, receives the chosen shapes
+ *   ms_best : optional, [3] doubles: best forward deposit, adjoint deposit and y column
+ *             pass time (ms)
+ * Errors: PM_ERR_ARG (reps outside 0..100), PM_ERR_CUDA.
+ */
+int pm_autotune(pm_ctx* ctx, int reps, pm_tuning* chosen, double* ms_best);
+
 /* ------------------------------------------------------------------------------------
  * Operator entry points: single rows of the hot path on the context's buffers, for
  * parity tests and benchmarks.  All arrays are device pointers in the context precision.

@@ -295,12 +295,6 @@ k_fft_x_c2r4(RowJob<T> job, int nrows, int dq, V4<T>* __restrict__ out4, const c
       const C* in = base + (grow % rows_per_inst) * L;
       xk[it] = in[k];
       xm[it] = k == 0 ? base[spec_main_len(N) + (grow % rows_per_inst)] : in[L - k];
-      if (q == dq) {
-        // component dq is the x derivative -i k_x of its spectrum (Nyquist kx = L: 0)
-        const T sk = (T)k, sl = k == 0 ? (T)0 : (T)(L - k);
-        xk[it] = cmake<C>(xk[it].y * sk, -xk[it].x * sk);
-        xm[it] = cmake<C>(xm[it].y * sl, -xm[it].x * sl);
-      }
     }
   }
 #pragma unroll
@@ -308,6 +302,12 @@ k_fft_x_c2r4(RowJob<T> job, int nrows, int dq, V4<T>* __restrict__ out4, const c
     const int idx = threadIdx.x + it * TL::NT;
     if (idx >= PAIRS) continue;
     const int c = idx / (L / 2 + 1), k = idx % (L / 2 + 1);
+    if (c / RT == dq) {
+      // component dq is the x derivative -i k_x of its spectrum (Nyquist kx = L: 0)
+      const T sk = (T)k, sl = k == 0 ? (T)0 : (T)(L - k);
+      xk[it] = cmake<C>(xk[it].y * sk, -xk[it].x * sk);
+      xm[it] = cmake<C>(xm[it].y * sl, -xm[it].x * sl);
+    }
     C zk, zm = cmake<C>(0, 0);
     if (k == 0) {
       const T x0 = xk[it].x, xl = xm[it].x;

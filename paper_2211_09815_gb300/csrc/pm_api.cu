@@ -155,6 +155,21 @@ const char* pm_last_cuda_error(void) { return g_cuda_err.c_str(); }
 
 long long pm_scratch_bytes(const pm_ctx* ctx) { return ctx ? ctx->eng->scratch_bytes() : 0; }
 
+int pm_get_tuning(pm_ctx* ctx, pm_tuning* out) {
+  if (!ctx || !out) return PM_ERR_ARG;
+  return ctx->eng->get_tuning(out);
+}
+
+int pm_set_tuning(pm_ctx* ctx, const pm_tuning* t) {
+  if (!ctx || !t) return PM_ERR_ARG;
+  return ctx->eng->set_tuning(t);
+}
+
+int pm_autotune(pm_ctx* ctx, int reps, pm_tuning* chosen, double* ms_best) {
+  if (!ctx || reps < 0 || reps > 100) return PM_ERR_ARG;
+  return ctx->eng->autotune(reps, chosen, ms_best);
+}
+
 int pm_op_density(pm_ctx* ctx, const void* disp, void* dens_out) {
   if (!ctx || !disp || !dens_out) return PM_ERR_ARG;
   return ctx->eng->op_density(disp, dens_out);

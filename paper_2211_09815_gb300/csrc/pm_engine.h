@@ -22,6 +22,9 @@ struct EngineBase {
   virtual int gradient_graph(const void* target, double* loss, void* gw, double* gt) = 0;
   virtual int power_spectrum(const void* dens, double* pk, double* kmean, double* nmodes) = 0;
   virtual int gradient(const void* omega, const void* target, double* loss, void* grad_omega, double* grad_theta) = 0;
+  virtual int get_tuning(pm_tuning* t) = 0;
+  virtual int set_tuning(const pm_tuning* t) = 0;
+  virtual int autotune(int reps, pm_tuning* chosen, double* ms_best) = 0;
 };
 
 // Creates the engine for cfg->precision; returns a status and sets *out on success.

@@ -2,6 +2,7 @@
 // discrete adjoint with reverse time integration (Sec. 3.5-3.6), templated on the real
 // type.  Included once per precision.
 #pragma once
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -164,11 +165,15 @@ class Engine : public EngineBase {
     int dev = 0;
     PMGB_CK(cudaGetDevice(&dev));
     PMGB_CK(cudaDeviceGetAttribute(&nsm_, cudaDevAttrMultiProcessorCount, dev));
+    // TMA-staged column passes for the mesh sizes that have them (PMGB_TMA=0 starts with
+    // the unstaged form; pm_set_tuning and pm_autotune switch between the two)
     const char* env = getenv("PMGB_TMA");
-    use_tma_ = tma_supported(nm_) && !(env && env[0] == '0');
+    tune_.tma_columns = (env && env[0] == '0') ? 0 : 1;
+    apply_tuning();
+    tune_.tma_columns = use_tma_ ? 1 : 0;
     PMGB_RET(alloc(&dev_err_, 1));
     PMGB_CK(cudaMemsetAsync(dev_err_, 0, sizeof(int), st_));
-    if (use_tma_)
+    if (tma_supported(nm_))
       for (int q = 0; q < 7; ++q) PMGB_RET(make_spec_tensor_maps<T>(nm_, B_, spec_[q], &tmy_[q], &tmz_[q]));
     PMGB_CK(cudaMemcpyAsync(omega_, omega, sizeof(T) * B_ * N_, cudaMemcpyDeviceToDevice, st_));
     PMGB_RET(tables(theta));
@@ -635,38 +640,145 @@ class Engine : public EngineBase {
     return PM_OK;
   }
 
-  // Tile shape of the assignment: 16 x 16 x 8 cells (x, y, z), or PMGB_TILE="lx,ly,lz"
-  // (log2 extents, at most 2^11 cells per tile); threads per tile 256 for the density alone
-  // and 512 with the pi sums, or PMGB_PULL_NT="n1,n4" (256 or 512 each).
+  // Bins of the tile-owner deposit, sized for the smallest tile the tuner may choose
+  // (2^9 cells); the tile shape and threads per tile of the density-only deposit (forward)
+  // and of the density + pi deposit (adjoint) are set separately (pm_tuning).
   int bin_setup() {
-    int lx = 4, ly = 4, lz = 3;
-    if (const char* env = getenv("PMGB_TILE")) {
-      int a, b, c;
-      if (sscanf(env, "%d,%d,%d", &a, &b, &c) == 3 && a >= 0 && b >= 0 && c >= 0 && a + b + c <= 11) {
-        lx = a;
-        ly = b;
-        lz = c;
-      }
-    }
-    bg_ = make_bin_geo(ilog2(nm_), lx, ly, lz);
-    nbin_ = (long long)B_ * bg_.nkeys + 1;
-    nscan_ = (int)((nbin_ + kScanBlock - 1) / kScanBlock);
+    tune_.tile_log2_density[0] = 3; tune_.tile_log2_density[1] = 4; tune_.tile_log2_density[2] = 4;
+    tune_.tile_log2_adjoint[0] = 3; tune_.tile_log2_adjoint[1] = 4; tune_.tile_log2_adjoint[2] = 4;
+    tune_.threads_density = 256;
+    tune_.threads_adjoint = 512;
+    tune_.tma_columns = 1;
+    const BinGeo smallest = make_bin_geo(ilog2(nm_), 3, 3, 3);
+    const long long maxbin = (long long)B_ * smallest.nkeys + 1;
     PMGB_RET(alloc(&bkeys_, (long long)B_ * N_));
     PMGB_RET(alloc(&blist_, (long long)B_ * N_));
-    PMGB_RET(alloc(&bcount_, nbin_));
-    PMGB_RET(alloc(&bstart_, nbin_));
-    PMGB_RET(alloc(&bcursor_, nbin_));
-    PMGB_RET(alloc(&bsums_, (long long)nscan_));
-    PMGB_CK(cudaMemsetAsync(bcount_, 0, sizeof(unsigned) * nbin_, st_));
-    if (const char* env = getenv("PMGB_PULL_NT")) {
-      int a = 0, b = 0;
-      if (sscanf(env, "%d,%d", &a, &b) == 2) {
-        pull_nt1_ = a == 512 ? 512 : 256;
-        pull_nt4_ = b == 512 ? 512 : 256;
-      }
-    }
+    PMGB_RET(alloc(&bcount_, maxbin));
+    PMGB_RET(alloc(&bstart_, maxbin));
+    PMGB_RET(alloc(&bcursor_, maxbin));
+    PMGB_RET(alloc(&bsums_, (maxbin + kScanBlock - 1) / kScanBlock));
+    PMGB_CK(cudaMemsetAsync(bcount_, 0, sizeof(unsigned) * maxbin, st_));
     ensure_smem_attr((const void*)k_pull_scatter<T, 4, 256>, 4 * 8 * 2048);
     ensure_smem_attr((const void*)k_pull_scatter<T, 4, 512>, 4 * 8 * 2048);
+    apply_tuning();
+    return PM_OK;
+  }
+  void apply_tuning() {
+    const int lg = ilog2(nm_);
+    bg1_ = make_bin_geo(lg, tune_.tile_log2_density[2], tune_.tile_log2_density[1], tune_.tile_log2_density[0]);
+    bg4_ = make_bin_geo(lg, tune_.tile_log2_adjoint[2], tune_.tile_log2_adjoint[1], tune_.tile_log2_adjoint[0]);
+    use_tma_ = tune_.tma_columns != 0 && tma_supported(nm_);
+  }
+  static bool tile_ok(const int* l) {
+    return l[0] >= 0 && l[1] >= 0 && l[2] >= 0 && l[0] + l[1] + l[2] >= 9 && l[0] + l[1] + l[2] <= 11 && l[0] <= 10 &&
+           l[1] <= 10 && l[2] <= 10;
+  }
+  int get_tuning(pm_tuning* t) override {
+    *t = tune_;
+    return PM_OK;
+  }
+  int set_tuning(const pm_tuning* t) override {
+    if (!tile_ok(t->tile_log2_density) || !tile_ok(t->tile_log2_adjoint)) return PM_ERR_ARG;
+    if ((t->threads_density != 256 && t->threads_density != 512) ||
+        (t->threads_adjoint != 256 && t->threads_adjoint != 512))
+      return PM_ERR_ARG;
+    if (t->tma_columns != 0 && t->tma_columns != 1) return PM_ERR_ARG;
+    if (t->tma_columns && !tma_supported(nm_)) return PM_ERR_ARG;
+    tune_ = *t;
+    apply_tuning();
+    return PM_OK;
+  }
+
+  // Autotuner: times every candidate of the tunable launches on this context's current
+  // particle state (the final state of the last forward run, or the Zel'dovich state if
+  // none) and keeps the fastest.  Candidates: deposit tile shapes (2^9..2^11 cells) x 256
+  // or 512 threads, separately for the density-only and the density + pi deposit; the
+  // y column pass with or without TMA staging.  Each candidate is timed `reps` times with
+  // CUDA events on the context's stream (median).  Results of the path do not depend on
+  // the choice: the deposit sums are exact integers, and both column-pass forms run the
+  // same radix stages.
+  int autotune(int reps, pm_tuning* chosen, double* ms_best) override {
+    if (reps < 1) reps = 3;
+    const bool prof_on = prof_.on;
+    prof_.on = false;
+    if (!have_fwd_) {
+      PMGB_RET(initial_conditions());
+    }
+    // synthetic adjoint state for the pi deposit: every pi_c = 7.1e-4 (bit pattern
+    // 0x3A3A3A3A), fixed-point exponents set from that maximum on the host
+    PMGB_CK(cudaMemsetAsync(xi_, 0x3A, sizeof(T) * B_ * 3 * N_, st_));
+    {
+      float v;
+      const unsigned bits = 0x3A3A3A3Au;
+      std::memcpy(&v, &bits, 4);
+      const int E = std::ilogb(v) + 1;
+      std::vector<int> e(3 * B_, fixed_top<T>(lgN_) - E);
+      PMGB_CK(cudaMemcpyAsync(e_pi_, e.data(), sizeof(int) * e.size(), cudaMemcpyHostToDevice, st_));
+      PMGB_CK(cudaStreamSynchronize(st_));
+    }
+    cudaEvent_t e0, e1;
+    PMGB_CK(cudaEventCreate(&e0));
+    PMGB_CK(cudaEventCreate(&e1));
+    auto time_it = [&](auto&& fn, double* ms) -> int {
+      std::vector<float> t;
+      PMGB_RET(fn());   // warm-up
+      for (int r = 0; r < reps; ++r) {
+        PMGB_CK(cudaEventRecord(e0, st_));
+        PMGB_RET(fn());
+        PMGB_CK(cudaEventRecord(e1, st_));
+        PMGB_CK(cudaEventSynchronize(e1));
+        float x = 0.f;
+        PMGB_CK(cudaEventElapsedTime(&x, e0, e1));
+        t.push_back(x);
+      }
+      std::sort(t.begin(), t.end());
+      *ms = t[t.size() / 2];
+      return PM_OK;
+    };
+    static const int kTiles[][3] = {{3, 4, 4}, {3, 3, 5}, {3, 3, 4}, {2, 4, 5}, {2, 4, 4}, {3, 3, 3}, {2, 3, 5}};
+    const int lg = ilog2(nm_);
+    const long long sis = 2 * spec_len_cx(nm_);
+    pm_tuning best = tune_;
+    double best_ms[3] = {1e30, 1e30, 1e30};
+    for (int nq = 0; nq < 2; ++nq) {
+      for (const auto& tl : kTiles) {
+        const int l[3] = {tl[0], tl[1], tl[2]};
+        if (!tile_ok(l)) continue;
+        for (int nt : {256, 512}) {
+          const BinGeo bg = make_bin_geo(lg, l[2], l[1], l[0]);
+          double ms = 0;
+          PMGB_RET(time_it([&]() { return deposit(s_, nq ? xi_ : nullptr, rmesh(0), sis, bg, nt); }, &ms));
+          if (ms < best_ms[nq]) {
+            best_ms[nq] = ms;
+            int* dst = nq ? best.tile_log2_adjoint : best.tile_log2_density;
+            dst[0] = l[0];
+            dst[1] = l[1];
+            dst[2] = l[2];
+            (nq ? best.threads_adjoint : best.threads_density) = nt;
+          }
+        }
+      }
+    }
+    if (tma_supported(nm_)) {
+      C* b1[1] = {spec_[6]};
+      for (int tma = 1; tma >= 0; --tma) {
+        use_tma_ = tma != 0;
+        double ms = 0;
+        PMGB_RET(time_it([&]() { return cols(nm_, -1, false, b1, 1); }, &ms));
+        if (ms < best_ms[2]) {
+          best_ms[2] = ms;
+          best.tma_columns = tma;
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    tune_ = best;
+    apply_tuning();
+    prof_.on = prof_on;
+    if (chosen) *chosen = best;
+    if (ms_best)
+      for (int k = 0; k < 3; ++k) ms_best[k] = best_ms[k] < 1e29 ? best_ms[k] : 0.0;
     return PM_OK;
   }
 
@@ -683,32 +795,41 @@ class Engine : public EngineBase {
       PMGB_CK(cudaMemsetAsync(pimax_, 0, sizeof(unsigned) * 3 * B_, st_));
     }
     prof_.begin(st_, P_SCATTER, 6);
-    k_bin_count<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, bg_, s, bcount_, bkeys_);
-    k_scan_blocks<<<nscan_, 256, 0, st_>>>(bcount_, bstart_, bsums_, nbin_);
-    k_scan_sums<<<1, 256, 0, st_>>>(bsums_, nscan_);
-    k_scan_add<<<(int)std::min<long long>((nbin_ + 255) / 256, 4096), 256, 0, st_>>>(bstart_, bcursor_, bsums_, nbin_);
-    k_bin_fill<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, bg_, bkeys_, bcursor_, blist_);
-    const int cells = 1 << (bg_.lx + bg_.ly + bg_.lz);
+    PMGB_RET(pi ? deposit(s, pi, dout, dis, bg4_, tune_.threads_adjoint)
+                : deposit(s, nullptr, dout, dis, bg1_, tune_.threads_density));
+    prof_.end(st_, P_SCATTER);
+    return PM_OK;
+  }
+  // binning + tile-owner deposit with tile geometry bg and nt threads per tile (e_pi_
+  // must hold the pi exponents when pi is given)
+  int deposit(const T* s, const T* pi, T* dout, long long dis, const BinGeo& bg, int nt) {
+    const long long nbin = (long long)B_ * bg.nkeys + 1;
+    const int nscan = (int)((nbin + kScanBlock - 1) / kScanBlock);
+    k_bin_count<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, bg, s, bcount_, bkeys_);
+    k_scan_blocks<<<nscan, 256, 0, st_>>>(bcount_, bstart_, bsums_, nbin);
+    k_scan_sums<<<1, 256, 0, st_>>>(bsums_, nscan);
+    k_scan_add<<<(int)std::min<long long>((nbin + 255) / 256, 4096), 256, 0, st_>>>(bstart_, bcursor_, bsums_, nbin);
+    k_bin_fill<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, bg, bkeys_, bcursor_, blist_);
+    const int cells = 1 << (bg.lx + bg.ly + bg.lz);
     const long long pis = 2 * spec_len_cx(nm_);
-    const dim3 grid(bg_.ntiles, B_);
+    const dim3 grid(bg.ntiles, B_);
     if (pi) {
-      if (pull_nt4_ == 512)
+      if (nt == 512)
         k_pull_scatter<T, 4, 512><<<grid, 512, 4 * 8 * cells, st_>>>(
-            geo_, bg_, s, pi, bstart_, blist_, e_d_, e_pi_, mass_, dout, dis, rmesh(4), rmesh(5), rmesh(6), pis);
+            geo_, bg, s, pi, bstart_, blist_, e_d_, e_pi_, mass_, dout, dis, rmesh(4), rmesh(5), rmesh(6), pis);
       else
         k_pull_scatter<T, 4, 256><<<grid, 256, 4 * 8 * cells, st_>>>(
-            geo_, bg_, s, pi, bstart_, blist_, e_d_, e_pi_, mass_, dout, dis, rmesh(4), rmesh(5), rmesh(6), pis);
+            geo_, bg, s, pi, bstart_, blist_, e_d_, e_pi_, mass_, dout, dis, rmesh(4), rmesh(5), rmesh(6), pis);
     } else {
-      if (pull_nt1_ == 512)
-        k_pull_scatter<T, 1, 512><<<grid, 512, 8 * cells, st_>>>(geo_, bg_, s, nullptr, bstart_, blist_, e_d_,
+      if (nt == 512)
+        k_pull_scatter<T, 1, 512><<<grid, 512, 8 * cells, st_>>>(geo_, bg, s, nullptr, bstart_, blist_, e_d_,
                                                                   nullptr, mass_, dout, dis, nullptr, nullptr,
                                                                   nullptr, 0);
       else
-        k_pull_scatter<T, 1, 256><<<grid, 256, 8 * cells, st_>>>(geo_, bg_, s, nullptr, bstart_, blist_, e_d_,
+        k_pull_scatter<T, 1, 256><<<grid, 256, 8 * cells, st_>>>(geo_, bg, s, nullptr, bstart_, blist_, e_d_,
                                                                   nullptr, mass_, dout, dis, nullptr, nullptr,
                                                                   nullptr, 0);
     }
-    prof_.end(st_, P_SCATTER);
     PMGB_CK(cudaGetLastError());
     return PM_OK;
   }
@@ -911,9 +1032,8 @@ class Engine : public EngineBase {
   cudaGraphExec_t graph_exec_ = nullptr;
   const void* graph_args_[4] = {nullptr, nullptr, nullptr, nullptr};
   T *s_ = nullptr, *p_ = nullptr, *a_ = nullptr, *xi_ = nullptr, *pi_ = nullptr, *s1_ = nullptr, *omega_ = nullptr;
-  BinGeo bg_{};
-  long long nbin_ = 0;
-  int nscan_ = 1, pull_nt1_ = 256, pull_nt4_ = 512;
+  BinGeo bg1_{}, bg4_{};
+  pm_tuning tune_{};
   unsigned *bkeys_ = nullptr, *blist_ = nullptr, *bcount_ = nullptr, *bstart_ = nullptr, *bcursor_ = nullptr,
            *bsums_ = nullptr;
   C* spec_[7] = {};

@@ -17,7 +17,8 @@ STATUS = {0: "PM_OK", 1: "PM_ERR_ARG", 2: "PM_ERR_OOM", 3: "PM_ERR_CUDA", 4: "PM
 SYMBOLS = ("pm_init", "pm_forward", "pm_loss_mse", "pm_adjoint", "pm_destroy", "pm_status_string",
            "pm_last_cuda_error", "pm_scratch_bytes", "pm_op_density", "pm_op_force", "pm_op_force_vjp",
            "pm_op_fft", "pm_op_za", "pm_set_inputs", "pm_gradient", "pm_profile", "pm_profile_read",
-           "pm_density_noalloc", "pm_power_spectrum", "pm_gradient_graph")
+           "pm_density_noalloc", "pm_power_spectrum", "pm_gradient_graph", "pm_get_tuning", "pm_set_tuning",
+           "pm_autotune")
 NOALLOC_MAX_CELLS = 128 ** 3
 PROF_NAMES = ("scatter", "fft_x_r2c", "fft_cols", "fused_z_force", "fused_z_adjoint", "fft_x_c2r",
               "gather_fwd", "gather_adj", "other")
@@ -25,6 +26,17 @@ PROF_NAMES = ("scatter", "fft_x_r2c", "fft_cols", "fused_z_force", "fused_z_adjo
 
 class PMLibraryError(RuntimeError):
     pass
+
+
+class PMTuning(ctypes.Structure):
+    """Launch shapes of the tunable passes (include/pm.h pm_tuning)."""
+    _fields_ = [("tile_log2_density", ctypes.c_int * 3), ("tile_log2_adjoint", ctypes.c_int * 3),
+                ("threads_density", ctypes.c_int), ("threads_adjoint", ctypes.c_int), ("tma_columns", ctypes.c_int)]
+
+    def as_dict(self):
+        return {"tile_log2_density": list(self.tile_log2_density), "tile_log2_adjoint": list(self.tile_log2_adjoint),
+                "threads_density": self.threads_density, "threads_adjoint": self.threads_adjoint,
+                "tma_columns": self.tma_columns}
 
 
 class PMError(RuntimeError):
@@ -74,6 +86,9 @@ def load_library(path=LIB_PATH):
     lib.pm_density_noalloc.argtypes = [ctypes.c_double, i, i, vp, vp, vp]
     lib.pm_power_spectrum.argtypes = [vp, vp, vp, vp, vp]
     lib.pm_gradient_graph.argtypes = [vp, vp, vp, vp, vp]
+    lib.pm_get_tuning.argtypes = [vp, ctypes.POINTER(PMTuning)]
+    lib.pm_set_tuning.argtypes = [vp, ctypes.POINTER(PMTuning)]
+    lib.pm_autotune.argtypes = [vp, i, ctypes.POINTER(PMTuning), vp]
     for name in SYMBOLS:
         getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
     _lib = lib
@@ -245,6 +260,30 @@ class PMContext:
         n = (ctypes.c_longlong * len(PROF_NAMES))()
         _check(load_library().pm_profile_read(self._h, ms, n), "pm_profile_read")
         return {name: (ms[i], n[i]) for i, name in enumerate(PROF_NAMES)}
+
+    def get_tuning(self):
+        t = PMTuning()
+        _check(load_library().pm_get_tuning(self._h, ctypes.byref(t)), "pm_get_tuning")
+        return t.as_dict()
+
+    def set_tuning(self, tuning):
+        """tuning: dict with the fields of PMTuning (missing fields keep their value)."""
+        t = PMTuning()
+        _check(load_library().pm_get_tuning(self._h, ctypes.byref(t)), "pm_get_tuning")
+        for k, v in tuning.items():
+            if k.startswith("tile_log2"):
+                getattr(t, k)[:] = list(v)
+            else:
+                setattr(t, k, int(v))
+        _check(load_library().pm_set_tuning(self._h, ctypes.byref(t)), "pm_set_tuning")
+
+    def autotune(self, reps=3):
+        """Time the candidate launch shapes on the current state and keep the fastest;
+        returns (chosen tuning dict, [best forward deposit, adjoint deposit, y pass] ms)."""
+        t = PMTuning()
+        ms = (ctypes.c_double * 3)()
+        _check(load_library().pm_autotune(self._h, int(reps), ctypes.byref(t), ms), "pm_autotune")
+        return t.as_dict(), list(ms)
 
     @property
     def scratch_bytes(self):
