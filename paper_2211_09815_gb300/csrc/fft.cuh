@@ -100,7 +100,18 @@ struct SmemTile {
   C* p;
   __device__ __forceinline__ C ld(int row, int c) const { return p[srow(row) * LD + c]; }
   __device__ __forceinline__ void st(int row, int c, C v) const { p[srow(row) * LD + c] = v; }
+  // Linear access for the radix stages: the rows base + d that a butterfly touches never
+  // carry out of the low four bits of base (see stage()), so the skewed row of base + d is
+  // srow(base) + delta(d) with a compile-time delta.
+  static constexpr bool kLinear = true;
+  static constexpr int kLD = LD;
+  __device__ __forceinline__ C* ptr(int row, int c) const { return p + srow(row) * LD + c; }
+  __host__ __device__ static constexpr int delta(int d) { return d + (d >> 4); }
 };
+
+// accessors without a linear form (global sequences, multipliers) take the generic path
+template <class X, class = void> struct IsLinear { static constexpr bool value = false; };
+template <class X> struct IsLinear<X, decltype(void(X::kLinear))> { static constexpr bool value = X::kLinear; };
 
 // one sequence per thread in global memory: element `row` at p[row * es]
 template <typename C>
@@ -131,8 +142,16 @@ __device__ __forceinline__ void stage(const Src& src, const Dst& dst, const TW& 
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
     const int j = (threadIdx.x + i * NT) / TC;
+    // rows j + r L/R: j < L/R, and L/R is a power of two, so the low four bits of j plus
+    // those of r L/R never carry (a linear tile reads them at compile-time offsets)
+    if constexpr (IsLinear<Src>::value) {
+      const C* p = src.ptr(j, c);
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[i][r] = src.ld(j + r * (L / R), c);
+      for (int r = 0; r < R; ++r) v[i][r] = p[Src::delta(r * (L / R)) * Src::kLD];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[i][r] = src.ld(j + r * (L / R), c);
+    }
     if constexpr (NS > 1) {
       const int jm = j % NS;
 #pragma unroll
@@ -145,8 +164,16 @@ __device__ __forceinline__ void stage(const Src& src, const Dst& dst, const TW& 
   for (int i = 0; i < PER; ++i) {
     const int j = (threadIdx.x + i * NT) / TC;
     const int jd = (j / NS) * NS * R + (j % NS);
+    // rows jd + r NS: jd = (multiple of NS R) + (j mod NS); for NS >= 16 the step is a
+    // multiple of 16, for NS < 16 (a power of two) the offsets stay inside the 16-row block
+    if constexpr (IsLinear<Dst>::value) {
+      C* p = dst.ptr(jd, c);
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst.st(jd + r * NS, c, v[i][r]);
+      for (int r = 0; r < R; ++r) p[Dst::delta(r * NS) * Dst::kLD] = v[i][r];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst.st(jd + r * NS, c, v[i][r]);
+    }
   }
 }
 

@@ -76,6 +76,10 @@ struct DenseTile {
   C* p;
   __device__ __forceinline__ C ld(int row, int c) const { return p[row * LD + c]; }
   __device__ __forceinline__ void st(int row, int c, C v) const { p[row * LD + c] = v; }
+  static constexpr bool kLinear = true;
+  static constexpr int kLD = LD;
+  __device__ __forceinline__ C* ptr(int row, int c) const { return p + row * LD + c; }
+  __host__ __device__ static constexpr int delta(int d) { return d; }
 };
 
 template <typename T, int L> struct TmaTile {
