@@ -222,7 +222,9 @@ template <typename T, int L> struct RowTile {
   // a tile never spans two instances: TR divides the n^2 = 4 L^2 rows of one mesh
   static constexpr int TR3 = TR2 < 4 * L * L ? TR2 : 4 * L * L;
   static constexpr int TR = TR3 < 1 ? 1 : TR3;
-  static constexpr int NT = TR * L / RMAX;
+  // at most 256 threads (measured faster than one radix item per thread at L = 512)
+  static constexpr int NT0 = TR * L / RMAX;
+  static constexpr int NT = NT0 > 256 ? 256 : NT0;
   static_assert(NT >= 1 && TR * L % RMAX == 0, "row tile needs whole work items");
   static constexpr int LD = TR + 1;
   static constexpr int SMEM = skew_rows(L) * LD * (int)sizeof(cx_t<T>);

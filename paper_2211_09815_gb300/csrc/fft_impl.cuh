@@ -262,7 +262,9 @@ k_fft_x_c2r(RowJob<T> job, int nrows, const cx_t<T>* __restrict__ twL, const cx_
 template <typename T, int L, int Q> struct C2R4Tile {
   static constexpr int RT = RowTile<T, L>::TR / 4;       // rows per block
   static constexpr int TR = Q * RT;                      // sequences per block
-  static constexpr int NT = TR * L / Plan<L>::RMAX;
+  // above 256 threads, two radix items per thread (measured faster at L = 512)
+  static constexpr int NT0 = TR * L / Plan<L>::RMAX;
+  static constexpr int NT = (NT0 > 256 && (NT0 / 2) % 32 == 0) ? NT0 / 2 : NT0;
   static constexpr int LD = TR + 1;
   static constexpr int SMEM = skew_rows(L) * LD * (int)sizeof(cx_t<T>);
 };
