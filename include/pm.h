@@ -195,7 +195,8 @@ long long pm_scratch_bytes(const pm_ctx* ctx);
  * results: the CIC sums are exact integers for any tile shape, and the staged and
  * unstaged column passes run the same radix stages).
  *   tile_log2_density[3] : log2 of the deposit tile extent along axes (z, y, x), the
- *                          density-only deposit of the forward steps; 9..11 in total
+ *                          density-only deposit of the forward steps; 9..11 in total,
+ *                          x at least 2
  *   tile_log2_adjoint[3] : the same for the density + pi deposit of the adjoint steps
  *   threads_density,
  *   threads_adjoint      : threads per tile, 256 or 512
@@ -237,7 +238,8 @@ int pm_autotune(pm_ctx* ctx, int reps, pm_tuning* chosen, double* ms_best);
  * ----------------------------------------------------------------------------------*/
 
 /* Overdensity delta (Sec. 2.2, Eq. 10; deterministic int64 fixed point) of particles at
- * x = q + disp.  disp [batch][3][n_ptcl^3] -> dens_out [batch][n_mesh^3]. */
+ * x = q + disp.  disp [batch][3][n_ptcl^3] -> dens_out [batch][n_mesh^3], dens_out aligned
+ * to 4 elements (16 bytes FP32, 32 bytes FP64; PM_ERR_ARG otherwise). */
 int pm_op_density(pm_ctx* ctx, const void* disp, void* dens_out);
 
 /* PM accelerations a = -grad varphi(q + disp) (Sec. 2.2): scatter, R2C, Green's function

@@ -12,7 +12,9 @@
 // meshes (delta and pi_c) once, in the working precision.
 //
 // Binning: a count (warp-aggregated integer atomics on an L2-resident array), an
-// exclusive scan, and a fill.
+// exclusive scan, and a fill that writes each particle's record (cell fractions, cell
+// within its tile, and in the adjoint the scaled pi) in bin order, so that a tile's CTA
+// reads its particles as contiguous runs.
 #pragma once
 #include "pm_kernels.cuh"
 
@@ -77,13 +79,33 @@ k_bin_count(Geo<T> g, BinGeo bg, const T* __restrict__ s, unsigned* __restrict__
   }
 }
 
-template <typename T>
+// local cell coordinates of a particle inside its own tile, 10 bits per axis
+__device__ __forceinline__ unsigned pack_local(const BinGeo& bg, const int c[3]) {
+  return ((unsigned)c[0] & ((1u << bg.lz) - 1)) << 20 | ((unsigned)c[1] & ((1u << bg.ly) - 1)) << 10 |
+         ((unsigned)c[2] & ((1u << bg.lx) - 1));
+}
+template <typename T> __device__ __forceinline__ T bits_to_real(unsigned u);
+template <> __device__ __forceinline__ float bits_to_real<float>(unsigned u) { return __uint_as_float(u); }
+template <> __device__ __forceinline__ double bits_to_real<double>(unsigned u) { return __longlong_as_double((long long)u); }
+template <typename T> __device__ __forceinline__ unsigned real_to_bits(T v);
+template <> __device__ __forceinline__ unsigned real_to_bits<float>(float v) { return __float_as_uint(v); }
+template <> __device__ __forceinline__ unsigned real_to_bits<double>(double v) { return (unsigned)__double_as_longlong(v); }
+
+// rec0[pos] = (t_0, t_1, t_2, local cell bits); with pi, rec1[pos] = (pi_c 2^e_c, 0)
+template <typename T, int NQ>
 __global__ void __launch_bounds__(kPtclThreads)
-k_bin_fill(Geo<T> g, BinGeo bg, const unsigned* __restrict__ keys, unsigned* __restrict__ cursor,
-           unsigned* __restrict__ list) {
+k_bin_fill(Geo<T> g, BinGeo bg, const T* __restrict__ s, const T* __restrict__ pi, const int* __restrict__ e_pi,
+           const unsigned* __restrict__ keys, unsigned* __restrict__ cursor, V4<T>* __restrict__ rec0,
+           V4<T>* __restrict__ rec1) {
   const int b = blockIdx.y;
   const int lane = threadIdx.x & 31;
   unsigned* cb = cursor + (long long)b * bg.nkeys;
+  const T* sb = s + (long long)b * 3 * g.N;
+  T sp[3] = {0, 0, 0};
+  if constexpr (NQ == 4) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) sp[c] = pow2i<T>(e_pi[c * gridDim.y + b]);
+  }
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long w0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); w0 < g.N; w0 += stride) {
     const long long w = w0 + lane;
@@ -99,7 +121,18 @@ k_bin_fill(Geo<T> g, BinGeo bg, const unsigned* __restrict__ keys, unsigned* __r
     unsigned pos = 0;
     if (valid && lane == leader) pos = atomicAdd(cb + key, (unsigned)__popc(peers));
     pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
-    if (valid) list[pos + __popc(peers & ((1u << lane) - 1u))] = (unsigned)i;
+    if (valid) {
+      pos += __popc(peers & ((1u << lane) - 1u));
+      const T sv[3] = {sb[i], sb[g.N + i], sb[2 * g.N + i]};
+      int cell[3];
+      T t[3];
+      cic_cell(g, i, sv, cell, t);
+      rec0[pos] = V4<T>{t[0], t[1], t[2], bits_to_real<T>(pack_local(bg, cell))};
+      if constexpr (NQ == 4) {
+        const T* pb = pi + (long long)b * 3 * g.N;
+        rec1[pos] = V4<T>{pb[i] * sp[0], pb[g.N + i] * sp[1], pb[2 * g.N + i] * sp[2], (T)0};
+      }
+    }
   }
 }
 
@@ -221,16 +254,17 @@ template <> __device__ __forceinline__ double words_to_real<double>(unsigned lo,
   return (double)(long long)(((unsigned long long)hi << 32) | lo);
 }
 
-// One CTA per tile (grid: tiles x instances).  NQ = 1: delta; NQ = 4: delta and the three
+// One CTA per tile (grid: tiles x instances; tile x extent >= 4, outputs 16-byte aligned).
+// NQ = 1: delta; NQ = 4: delta and the three
 // pi sums.  Outputs: delta = m acc 2^-e_d - 1 into dout (instance stride dis), pi_c =
 // acc 2^-e_c into p0..p2 (instance stride pis).  Dynamic shared memory: NQ * cells * 8 B
 // (low words [NQ][cells], then high words [NQ][cells]).
 template <typename T, int NQ, int NT>
 __global__ void __launch_bounds__(NT, NT >= 512 ? 3 : 1)
-k_pull_scatter(Geo<T> g, BinGeo bg, const T* __restrict__ s, const T* __restrict__ pi,
-               const unsigned* __restrict__ start, const unsigned* __restrict__ list, int e_d,
-               const int* __restrict__ e_pi, T mass, T* __restrict__ dout, long long dis, T* __restrict__ p0,
-               T* __restrict__ p1, T* __restrict__ p2, long long pis) {
+k_pull_scatter(Geo<T> g, BinGeo bg, const V4<T>* __restrict__ rec0, const V4<T>* __restrict__ rec1,
+               const unsigned* __restrict__ start, int e_d, const int* __restrict__ e_pi, T mass,
+               T* __restrict__ dout, long long dis, T* __restrict__ p0, T* __restrict__ p1, T* __restrict__ p2,
+               long long pis) {
   extern __shared__ __align__(16) unsigned acc[];   // [2][NQ][cells]
   __shared__ unsigned rbeg[20], rpre[21];
   const int b = blockIdx.y;
@@ -261,34 +295,27 @@ k_pull_scatter(Geo<T> g, BinGeo bg, const T* __restrict__ s, const T* __restrict
     if (r < 21) rpre[r] = x - len;   // exclusive prefix; rpre[20] = total
   }
   __syncthreads();
-  const T* sb = s + (long long)b * 3 * g.N;
-  const T* pb = nullptr;
   const T sd = pow2i<T>(e_d);
-  T sp[3] = {0, 0, 0};
-  if constexpr (NQ == 4) {
-    pb = pi + (long long)b * 3 * g.N;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) sp[c] = pow2i<T>(e_pi[c * gridDim.y + b]);
-  }
   const unsigned total = rpre[20];
   const unsigned mx = (1u << bg.lx) - 1, my = (1u << bg.ly) - 1, mz = (1u << bg.lz) - 1;
   for (unsigned f = threadIdx.x; f < total; f += blockDim.x) {
     int r = 0;
     while (f >= rpre[r + 1]) ++r;
     const unsigned d = (unsigned)((kRangeD >> (3 * r)) & 7u);
-    const long long i = list[rbeg[r] + (f - rpre[r])];
-    const T sv[3] = {sb[i], sb[g.N + i], sb[2 * g.N + i]};
-    int cell[3];
-    T t[3];
-    cic_cell(g, i, sv, cell, t);
-    const unsigned cls = bin_class(bg, cell);
+    const unsigned pos = rbeg[r] + (f - rpre[r]);
+    const V4<T> r0 = rec0[pos];
+    const T t[3] = {r0.x, r0.y, r0.z};
+    const unsigned packed = real_to_bits<T>(r0.w);
+    const int l0 = (int)(packed >> 20), l1 = (int)((packed >> 10) & 1023u), l2 = (int)(packed & 1023u);
+    const unsigned cls = (unsigned)((unsigned)l2 == mx) | ((unsigned)((unsigned)l1 == my) << 1) |
+                         ((unsigned)((unsigned)l0 == mz) << 2);
     T pv[3] = {0, 0, 0};
     if constexpr (NQ == 4) {
-      pv[0] = pb[i] * sp[0];
-      pv[1] = pb[g.N + i] * sp[1];
-      pv[2] = pb[2 * g.N + i] * sp[2];
+      const V4<T> r1 = rec1[pos];
+      pv[0] = r1.x;
+      pv[1] = r1.y;
+      pv[2] = r1.z;
     }
-    const int l0 = (int)((unsigned)cell[0] & mz), l1 = (int)((unsigned)cell[1] & my), l2 = (int)((unsigned)cell[2] & mx);
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       // corner e (bit 2: axis 0, bit 1: axis 1, bit 0: axis 2) crosses into the next tile
@@ -320,15 +347,22 @@ k_pull_scatter(Geo<T> g, BinGeo bg, const T* __restrict__ s, const T* __restrict
 #pragma unroll
     for (int c = 0; c < 3; ++c) mp[c] = pow2i<T>(-e_pi[c * gridDim.y + b]);
   }
-  for (int k = threadIdx.x; k < cells; k += blockDim.x) {
+  // four neighbouring x cells per thread (tile x extent >= 4): 16-byte shared loads of
+  // both words, one vector store per quantity
+  const long long tile_base = ((long long)(T0 << bg.lz) * g.nm + (T1 << bg.ly)) * g.nm + (T2 << bg.lx);
+  for (int k = threadIdx.x * 4; k < cells; k += blockDim.x * 4) {
     const int a2 = k & (int)mx, a1 = (k >> bg.lx) & (int)my, a0 = k >> (bg.lx + bg.ly);
-    const long long cell =
-        ((long long)((T0 << bg.lz) + a0) * g.nm + ((T1 << bg.ly) + a1)) * g.nm + ((T2 << bg.lx) + a2);
-    dout[b * dis + cell] = words_to_real<T>(acc[k], hacc[k]) * md - (T)1;
-    if constexpr (NQ == 4) {
-      p0[b * pis + cell] = words_to_real<T>(acc[cells + k], hacc[cells + k]) * mp[0];
-      p1[b * pis + cell] = words_to_real<T>(acc[2 * cells + k], hacc[2 * cells + k]) * mp[1];
-      p2[b * pis + cell] = words_to_real<T>(acc[3 * cells + k], hacc[3 * cells + k]) * mp[2];
+    const long long cell = tile_base + ((long long)a0 * g.nm + a1) * g.nm + a2;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const uint4 lo = *reinterpret_cast<const uint4*>(acc + q * cells + k);
+      const uint4 hi = *reinterpret_cast<const uint4*>(hacc + q * cells + k);
+      const T m = q == 0 ? md : mp[q - 1];
+      const T a = q == 0 ? (T)-1 : (T)0;
+      const V4<T> v{words_to_real<T>(lo.x, hi.x) * m + a, words_to_real<T>(lo.y, hi.y) * m + a,
+                    words_to_real<T>(lo.z, hi.z) * m + a, words_to_real<T>(lo.w, hi.w) * m + a};
+      T* o = q == 0 ? dout + b * dis : (q == 1 ? p0 : (q == 2 ? p1 : p2)) + b * pis;
+      *reinterpret_cast<V4<T>*>(o + cell) = v;
     }
   }
 }

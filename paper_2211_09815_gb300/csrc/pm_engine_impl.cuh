@@ -297,6 +297,7 @@ class Engine : public EngineBase {
 
   // ------------------------------------------------------------------ operators
   int op_density(const void* disp, void* dens) override {
+    if (reinterpret_cast<uintptr_t>(dens) % (4 * sizeof(T))) return PM_ERR_ARG;   // vector stores
     have_fwd_ = false;
     PMGB_CK(cudaMemcpyAsync(s_, disp, sizeof(T) * B_ * 3 * N_, cudaMemcpyDeviceToDevice, st_));
     PMGB_RET(scatter(s_, nullptr, (T*)dens, M_));
@@ -652,7 +653,8 @@ class Engine : public EngineBase {
     const BinGeo smallest = make_bin_geo(ilog2(nm_), 3, 3, 3);
     const long long maxbin = (long long)B_ * smallest.nkeys + 1;
     PMGB_RET(alloc(&bkeys_, (long long)B_ * N_));
-    PMGB_RET(alloc(&blist_, (long long)B_ * N_));
+    PMGB_RET(alloc(&brec0_, (long long)B_ * N_));
+    PMGB_RET(alloc(&brec1_, (long long)B_ * N_));
     PMGB_RET(alloc(&bcount_, maxbin));
     PMGB_RET(alloc(&bstart_, maxbin));
     PMGB_RET(alloc(&bcursor_, maxbin));
@@ -670,7 +672,7 @@ class Engine : public EngineBase {
     use_tma_ = tune_.tma_columns != 0 && tma_supported(nm_);
   }
   static bool tile_ok(const int* l) {
-    return l[0] >= 0 && l[1] >= 0 && l[2] >= 0 && l[0] + l[1] + l[2] >= 9 && l[0] + l[1] + l[2] <= 11 && l[0] <= 10 &&
+    return l[0] >= 0 && l[1] >= 0 && l[2] >= 2 && l[0] + l[1] + l[2] >= 9 && l[0] + l[1] + l[2] <= 11 && l[0] <= 10 &&
            l[1] <= 10 && l[2] <= 10;
   }
   int get_tuning(pm_tuning* t) override {
@@ -809,24 +811,29 @@ class Engine : public EngineBase {
     k_scan_blocks<<<nscan, 256, 0, st_>>>(bcount_, bstart_, bsums_, nbin);
     k_scan_sums<<<1, 256, 0, st_>>>(bsums_, nscan);
     k_scan_add<<<(int)std::min<long long>((nbin + 255) / 256, 4096), 256, 0, st_>>>(bstart_, bcursor_, bsums_, nbin);
-    k_bin_fill<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, bg, bkeys_, bcursor_, blist_);
+    if (pi)
+      k_bin_fill<T, 4><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, bg, s, pi, e_pi_, bkeys_, bcursor_, brec0_,
+                                                               brec1_);
+    else
+      k_bin_fill<T, 1><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, bg, s, nullptr, nullptr, bkeys_, bcursor_,
+                                                               brec0_, nullptr);
     const int cells = 1 << (bg.lx + bg.ly + bg.lz);
     const long long pis = 2 * spec_len_cx(nm_);
     const dim3 grid(bg.ntiles, B_);
     if (pi) {
       if (nt == 512)
         k_pull_scatter<T, 4, 512><<<grid, 512, 4 * 8 * cells, st_>>>(
-            geo_, bg, s, pi, bstart_, blist_, e_d_, e_pi_, mass_, dout, dis, rmesh(4), rmesh(5), rmesh(6), pis);
+            geo_, bg, brec0_, brec1_, bstart_, e_d_, e_pi_, mass_, dout, dis, rmesh(4), rmesh(5), rmesh(6), pis);
       else
         k_pull_scatter<T, 4, 256><<<grid, 256, 4 * 8 * cells, st_>>>(
-            geo_, bg, s, pi, bstart_, blist_, e_d_, e_pi_, mass_, dout, dis, rmesh(4), rmesh(5), rmesh(6), pis);
+            geo_, bg, brec0_, brec1_, bstart_, e_d_, e_pi_, mass_, dout, dis, rmesh(4), rmesh(5), rmesh(6), pis);
     } else {
       if (nt == 512)
-        k_pull_scatter<T, 1, 512><<<grid, 512, 8 * cells, st_>>>(geo_, bg, s, nullptr, bstart_, blist_, e_d_,
+        k_pull_scatter<T, 1, 512><<<grid, 512, 8 * cells, st_>>>(geo_, bg, brec0_, nullptr, bstart_, e_d_,
                                                                   nullptr, mass_, dout, dis, nullptr, nullptr,
                                                                   nullptr, 0);
       else
-        k_pull_scatter<T, 1, 256><<<grid, 256, 8 * cells, st_>>>(geo_, bg, s, nullptr, bstart_, blist_, e_d_,
+        k_pull_scatter<T, 1, 256><<<grid, 256, 8 * cells, st_>>>(geo_, bg, brec0_, nullptr, bstart_, e_d_,
                                                                   nullptr, mass_, dout, dis, nullptr, nullptr,
                                                                   nullptr, 0);
     }
@@ -1034,8 +1041,8 @@ class Engine : public EngineBase {
   T *s_ = nullptr, *p_ = nullptr, *a_ = nullptr, *xi_ = nullptr, *pi_ = nullptr, *s1_ = nullptr, *omega_ = nullptr;
   BinGeo bg1_{}, bg4_{};
   pm_tuning tune_{};
-  unsigned *bkeys_ = nullptr, *blist_ = nullptr, *bcount_ = nullptr, *bstart_ = nullptr, *bcursor_ = nullptr,
-           *bsums_ = nullptr;
+  unsigned *bkeys_ = nullptr, *bcount_ = nullptr, *bstart_ = nullptr, *bcursor_ = nullptr, *bsums_ = nullptr;
+  V4<T> *brec0_ = nullptr, *brec1_ = nullptr;
   C* spec_[7] = {};
   T* dens_ = nullptr;
   V4<T>* fvec_ = nullptr;

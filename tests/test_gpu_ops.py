@@ -98,3 +98,26 @@ def test_force_and_vjp_match_oracle(precision, nm, npc):
     assert rel_l2(acc2.cpu().numpy().reshape(3, -1), a_ref) < tol
     assert rel_l2(alpha.cpu().numpy().reshape(3, -1), al_ref) < tol
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_density_of_collapsed_particles_matches_oracle(precision):
+    """All 64^3 particles collapsed into a few cells: one mesh tile receives more than 2^16
+    particle visits, which takes the exact 64-bit accumulation path of the deposit."""
+    torch = torch_cuda()
+    box, nm, npc = 64.0, 64, 64
+    ctx, *_ = make_ctx(box, nm, npc, 1, precision=precision)
+    cfg = oracle_cfg(box, nm, npc, 1)
+    q = opm.lattice(cfg)
+    rng = np.random.default_rng(8)
+    target = np.array([[20.3], [33.7], [41.1]])
+    disp = target - q + rng.normal(scale=0.6, size=q.shape)
+    d = torch.from_numpy(disp).to("cuda", ctx.dtype).contiguous()
+    out = torch.empty(nm ** 3, device="cuda", dtype=ctx.dtype)
+    ctx.op_density(d, out)
+    ref = opm.density(q + d.cpu().numpy().astype(np.float64), cfg).ravel()
+    got = out.cpu().numpy().astype(np.float64)
+    tol = 1e-11 if precision else 1e-6
+    assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref))
+    assert abs((got + 1).sum() - nm ** 3) <= (1e-9 if precision else 1e-5) * nm ** 3
+    ctx.close()
