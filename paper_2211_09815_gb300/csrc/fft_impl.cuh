@@ -576,10 +576,12 @@ static void launch_fused_L(const ZJob<T>& job, bool adjoint, const cx_t<T>* tw, 
 template <typename T, int L> static int tiles_of() { return L * ((L / 2) / TmaTile<T, L>::TC); }
 
 template <typename T, int L, int DIR, int KIND>
-static void launch_tma_L(const CUtensorMap* maps, const TmaJob<T>& job, int tiles, const cx_t<T>* tw, int nsm,
-                         cudaStream_t st) {
+static void launch_tma_L(const CUtensorMap* maps, const CUtensorMap* omaps, const TmaJob<T>& job, int tiles,
+                         const cx_t<T>* tw, int nsm, cudaStream_t st) {
   using TT = TmaTile<T, L>;
-  TmaMaps m{};
+  TmaMaps m{}, om{};
+  if (omaps)
+    for (int i = 0; i < 2; ++i) om.m[i] = omaps[i];
   const int nmaps = KIND == 0 ? job.nbuf : ((KIND == 2 || KIND == 4) ? 2 : 1);
   for (int i = 0; i < nmaps; ++i) m.m[i] = maps[i];
   const size_t sm = KIND == 0 ? 2 * (size_t)TT::BYTES + 1024 : 3 * (size_t)TT::BYTES + (size_t)L * sizeof(cx_t<T>) + 1024;
@@ -587,7 +589,7 @@ static void launch_tma_L(const CUtensorMap* maps, const TmaJob<T>& job, int tile
   ensure_smem_attr((const void*)fn, (int)sm);
   const int items = KIND == 0 ? job.nbuf * tiles : tiles;
   const int grid = items < nsm ? items : nsm;
-  fn<<<grid, TT::NT, sm, st>>>(m, job, tiles, tw + L);
+  fn<<<grid, TT::NT, sm, st>>>(m, om, job, tiles, tw + L);
 }
 
 #define PMGB_DISPATCH_TMA(L_, CALL)                                                 \
@@ -609,9 +611,9 @@ int fft_cols_tma(int n, int batch, int dir, int zaxis, const CUtensorMap* maps, 
   job.zaxis = zaxis;
   job.err = err;
   if (dir < 0) {
-    PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, -1, 0>(maps, job, batch * tiles_of<T, LL>(), tw, nsm, st)));
+    PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, -1, 0>(maps, nullptr, job, batch * tiles_of<T, LL>(), tw, nsm, st)));
   } else {
-    PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, +1, 0>(maps, job, batch * tiles_of<T, LL>(), tw, nsm, st)));
+    PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, +1, 0>(maps, nullptr, job, batch * tiles_of<T, LL>(), tw, nsm, st)));
   }
   return PM_OK;
 }
@@ -626,7 +628,7 @@ int fft_ysplit_tma(int n, int batch, const CUtensorMap* umap, cx_t<T>* u, cx_t<T
   job.zaxis = 0;
   job.batch = batch;
   job.err = err;
-  PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, +1, 3>(umap, job, batch * tiles_of<T, LL>(), tw, nsm, st)));
+  PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, +1, 3>(umap, nullptr, job, batch * tiles_of<T, LL>(), tw, nsm, st)));
   return PM_OK;
 }
 
@@ -639,13 +641,13 @@ int fft_ymerge_tma(int n, int batch, const CUtensorMap* pmaps, cx_t<T>* p1, cons
   job.zaxis = 0;
   job.batch = batch;
   job.err = err;
-  PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, -1, 4>(pmaps, job, batch * tiles_of<T, LL>(), tw, nsm, st)));
+  PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, -1, 4>(pmaps, nullptr, job, batch * tiles_of<T, LL>(), tw, nsm, st)));
   return PM_OK;
 }
 
 template <typename T>
-int fft_fused_tma(int n, bool adjoint, const CUtensorMap* maps, const ZJob<T>& zj, const cx_t<T>* tw, int* err,
-                  int nsm, cudaStream_t st) {
+int fft_fused_tma(int n, bool adjoint, const CUtensorMap* maps, const CUtensorMap* omaps, const ZJob<T>& zj,
+                  const cx_t<T>* tw, int* err, int nsm, cudaStream_t st) {
   TmaJob<T> job{};
   for (int i = 0; i < 3; ++i) job.out[i] = zj.out[i];
   job.nbuf = 1;
@@ -655,9 +657,9 @@ int fft_fused_tma(int n, bool adjoint, const CUtensorMap* maps, const ZJob<T>& z
   job.dtab = zj.dtab;
   job.err = err;
   if (adjoint) {
-    PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, +1, 2>(maps, job, zj.batch * tiles_of<T, LL>(), tw, nsm, st)));
+    PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, +1, 2>(maps, nullptr, job, zj.batch * tiles_of<T, LL>(), tw, nsm, st)));
   } else {
-    PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, +1, 1>(maps, job, zj.batch * tiles_of<T, LL>(), tw, nsm, st)));
+    PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, +1, 1>(maps, omaps, job, zj.batch * tiles_of<T, LL>(), tw, nsm, st)));
   }
   return PM_OK;
 }

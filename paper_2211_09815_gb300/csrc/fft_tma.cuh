@@ -70,6 +70,20 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// TMA store of a shared-memory box into the tensor (bulk async-group of the issuing
+// thread); the writers of the box execute fence_proxy_async and a barrier first
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void* src, int c0, int c1, int c2, int c3) {
+  asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];"
+               ::"l"(reinterpret_cast<unsigned long long>(map)), "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2),
+                 "r"(c3)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the shared-memory sources of this thread's committed stores have been read
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// this thread's committed stores are complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // dense [L][TC] tile (TMA writes rows back to back)
 template <typename C, int LD>
 struct DenseTile {
@@ -186,8 +200,8 @@ struct YMergeDst {
 
 template <typename T, int L, int DIR, int KIND>
 __global__ void __launch_bounds__(TmaTile<T, L>::NT, 1)
-k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaJob<T> job, int tiles_per_buf,
-           const cx_t<T>* __restrict__ tw) {
+k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps omaps,
+           const __grid_constant__ TmaJob<T> job, int tiles_per_buf, const cx_t<T>* __restrict__ tw) {
   using C = cx_t<T>;
   using TT = TmaTile<T, L>;
   constexpr int N = L;
@@ -238,13 +252,28 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaJob<
         tma_load_4d(dst + r * TT::RB * TT::LD, &maps.m[buf], bar, kxg * TT::TC * TT::W, r * TT::RB, o, b);
     }
   };
+  // KIND 1 writes its two outputs with TMA stores from shared memory (the work tile, then
+  // the input's own ring slot); its next load is issued after the forward transform, when
+  // the stores of the previous tile have long been read out of that slot.
+  constexpr bool kStore = KIND == 1;
+  auto store = [&](const CUtensorMap* map, const C* src, int kxg, int o, int b) {
+#pragma unroll
+    for (int r = 0; r < L / TT::RB; ++r) tma_store_4d(map, src + r * TT::RB * TT::LD, kxg * TT::TC * TT::W, o, r * TT::RB, b);
+    bulk_commit();
+  };
   if (threadIdx.x == 0 && nq > 0) issue(0);
   const int c = threadIdx.x % TT::TC;
   for (int q = 0; q < nq; ++q) {
-    if (threadIdx.x == 0 && q + 1 < nq) issue(q + 1);
+    if (!kStore && threadIdx.x == 0 && q + 1 < nq) issue(q + 1);
     if (!mbar_wait(&bars[q & 1], (q >> 1) & 1, job.err)) {
-      // give the copies in flight a bounded chance to land before the CTA exits
-      if (threadIdx.x == 0 && q + 1 < nq) mbar_wait(&bars[(q + 1) & 1], ((q + 1) >> 1) & 1, nullptr);
+      // give the copies in flight a bounded chance to finish before the CTA exits
+      if (threadIdx.x == 0) {
+        if (kStore)
+          mbar_wait(&bars[q & 1], (q >> 1) & 1, nullptr);
+        else if (q + 1 < nq)
+          mbar_wait(&bars[(q + 1) & 1], ((q + 1) >> 1) & 1, nullptr);
+        if (kStore) bulk_wait_all();
+      }
       return;
     }
     int item, comp;
@@ -271,12 +300,25 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaJob<
       if constexpr (KIND == 1) {
         fft_tile<T, L, TT::TC, TT::NT, -1>(t, t, t, stw);
         __syncthreads();
-#pragma unroll 1
-        for (int cc = 0; cc < 2; ++cc) {
-          DenseMulSrc<T, N, TT::LD> src{cur, zc, cc};
-          GlobalSeq<C> g{job.out[cc] + base, es, true};
-          fft_tile<T, L, TT::TC, TT::NT, +1>(src, wt, g, stw);
+        if (threadIdx.x == 0) {
+          // the other ring slot and the work tile are no longer read by the previous
+          // tile's stores: refill the slot (the work tile is first written after the
+          // barrier inside the next radix stage)
+          bulk_wait_read_all();
+          if (q + 1 < nq) issue(q + 1);
         }
+        // z force: -i k_0 G T -> work -> out[0]
+        DenseMulSrc<T, N, TT::LD> src0{cur, zc, 0};
+        fft_tile<T, L, TT::TC, TT::NT, +1>(src0, wt, wt, stw);
+        fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) store(&omaps.m[0], work, kxg, o, b);
+        // U: G T -> in place in the ring slot -> out[1]
+        DenseMulSrc<T, N, TT::LD> src1{cur, zc, 1};
+        fft_tile<T, L, TT::TC, TT::NT, +1>(src1, t, t, stw);
+        fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) store(&omaps.m[1], cur, kxg, o, b);
       } else {
         DenseAccDst<T, N, TT::LD> acc{work, zc, comp};
         fft_tile<T, L, TT::TC, TT::NT, -1>(t, t, acc, stw);
@@ -308,6 +350,7 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaJob<
     }
     __syncthreads();
   }
+  if (kStore && threadIdx.x == 0) bulk_wait_all();
 }
 
 }  // namespace pmgb

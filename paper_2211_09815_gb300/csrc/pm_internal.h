@@ -71,8 +71,8 @@ template <typename T>
 int fft_cols_tma(int n, int batch, int dir, int zaxis, const CUtensorMap* maps, cx_t<T>* const* bufs, int nb,
                  const cx_t<T>* tw, int* err, int nsm, cudaStream_t st);
 template <typename T>
-int fft_fused_tma(int n, bool adjoint, const CUtensorMap* maps, const ZJob<T>& job, const cx_t<T>* tw, int* err,
-                  int nsm, cudaStream_t st);
+int fft_fused_tma(int n, bool adjoint, const CUtensorMap* maps, const CUtensorMap* omaps, const ZJob<T>& job,
+                  const cx_t<T>* tw, int* err, int nsm, cudaStream_t st);
 // the same split and merge over the main spectrum with TMA-staged tiles
 template <typename T>
 int fft_ysplit_tma(int n, int batch, const CUtensorMap* umap, cx_t<T>* u, cx_t<T>* out1, const cx_t<T>* tw,
