@@ -584,7 +584,7 @@ static void launch_tma_L(const CUtensorMap* maps, const CUtensorMap* omaps, cons
     for (int i = 0; i < 2; ++i) om.m[i] = omaps[i];
   const int nmaps = KIND == 0 ? job.nbuf : ((KIND == 2 || KIND == 4) ? 2 : 1);
   for (int i = 0; i < nmaps; ++i) m.m[i] = maps[i];
-  const size_t sm = KIND == 0 ? 2 * (size_t)TT::BYTES + 1024 : 3 * (size_t)TT::BYTES + (size_t)L * sizeof(cx_t<T>) + 1024;
+  const size_t sm = KIND == 0 ? 3 * (size_t)TT::BYTES + 1024 : 3 * (size_t)TT::BYTES + (size_t)L * sizeof(cx_t<T>) + 1024;
   auto fn = k_cols_tma<T, L, DIR, KIND>;
   ensure_smem_attr((const void*)fn, (int)sm);
   const int items = KIND == 0 ? job.nbuf * tiles : tiles;
@@ -619,7 +619,7 @@ int fft_cols_tma(int n, int batch, int dir, int zaxis, const CUtensorMap* maps, 
 }
 
 template <typename T>
-int fft_ysplit_tma(int n, int batch, const CUtensorMap* umap, cx_t<T>* u, cx_t<T>* out1, const cx_t<T>* tw,
+int fft_ysplit_tma(int n, int batch, const CUtensorMap* umaps, cx_t<T>* u, cx_t<T>* out1, const cx_t<T>* tw,
                    int* err, int nsm, cudaStream_t st) {
   TmaJob<T> job{};
   job.out[0] = u;
@@ -628,7 +628,7 @@ int fft_ysplit_tma(int n, int batch, const CUtensorMap* umap, cx_t<T>* u, cx_t<T
   job.zaxis = 0;
   job.batch = batch;
   job.err = err;
-  PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, +1, 3>(umap, nullptr, job, batch * tiles_of<T, LL>(), tw, nsm, st)));
+  PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, +1, 3>(umaps, umaps, job, batch * tiles_of<T, LL>(), tw, nsm, st)));
   return PM_OK;
 }
 

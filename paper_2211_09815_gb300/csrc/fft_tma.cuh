@@ -81,6 +81,8 @@ __device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void*
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // the shared-memory sources of this thread's committed stores have been read
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// ... all but the most recently committed one
+__device__ __forceinline__ void bulk_wait_read_but1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 // this thread's committed stores are complete
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
@@ -210,7 +212,10 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // TMA destinations must be 128-byte aligned: round the dynamic base up (1 KiB slack)
   C* ring0 = reinterpret_cast<C*>((reinterpret_cast<unsigned long long>(smem_raw) + 1023ull) & ~1023ull);
-  C* ring1 = ring0 + TT::TILE;
+  // ring slots of the prefetched tiles: three for the plain passes (no work tile), two
+  // and a work tile for the others
+  constexpr int NSLOT = KIND == 0 ? 3 : 2;
+  auto slot = [&](int q) { return ring0 + (q % NSLOT) * TT::TILE; };
   C* work = ring0 + 2 * TT::TILE;
   // twiddle table of the length-L transform: the fused passes copy it into shared memory
   // once per CTA (measured faster there; the plain column passes read it through L1)
@@ -218,13 +223,12 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
   if constexpr (KIND != 0)
     for (int m = threadIdx.x; m < L; m += blockDim.x) tws[m] = __ldg(tw + m);
   const SmemTw<C> stw{tws};
-  __shared__ unsigned long long bars[2];
+  __shared__ unsigned long long bars[NSLOT];
   const int items = KIND == 0 ? job.nbuf * tiles_per_buf : tiles_per_buf;
   const int my_items = blockIdx.x < (unsigned)items ? (items - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int nq = my_items * NL;
   if (threadIdx.x == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    for (int k = 0; k < NSLOT; ++k) mbar_init(&bars[k], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -240,8 +244,8 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
     const int buf = KIND == 0 ? item / tiles_per_buf : comp;
     const int u = KIND == 0 ? item % tiles_per_buf : item;
     const int kxg = u % NCG, o = (u / NCG) % N, b = u / (NCG * N);
-    C* dst = (q & 1) ? ring1 : ring0;
-    unsigned long long* bar = &bars[q & 1];
+    C* dst = slot(q);
+    unsigned long long* bar = &bars[q % NSLOT];
     fence_proxy_async();
     mbar_expect_tx(bar, TT::BYTES);
 #pragma unroll
@@ -252,26 +256,42 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
         tma_load_4d(dst + r * TT::RB * TT::LD, &maps.m[buf], bar, kxg * TT::TC * TT::W, r * TT::RB, o, b);
     }
   };
-  // KIND 1 writes its two outputs with TMA stores from shared memory (the work tile, then
-  // the input's own ring slot); its next load is issued after the forward transform, when
-  // the stores of the previous tile have long been read out of that slot.
-  constexpr bool kStore = KIND == 1;
+  // Results leave by TMA stores from shared memory for KIND 0, 1 and 3.  KIND 0: three
+  // slots, so the slot refilled at the top of an iteration was stored two iterations
+  // earlier.  KIND 1 and 3 (two outputs: the work tile, then the input's own slot): the
+  // next load is issued after the first output, when the previous tile's stores out of
+  // that slot have long been read.
+  constexpr bool kStore = KIND == 0 || KIND == 1 || KIND == 3;
   auto store = [&](const CUtensorMap* map, const C* src, int kxg, int o, int b) {
 #pragma unroll
-    for (int r = 0; r < L / TT::RB; ++r) tma_store_4d(map, src + r * TT::RB * TT::LD, kxg * TT::TC * TT::W, o, r * TT::RB, b);
+    for (int r = 0; r < L / TT::RB; ++r) {
+      if (job.zaxis)
+        tma_store_4d(map, src + r * TT::RB * TT::LD, kxg * TT::TC * TT::W, o, r * TT::RB, b);
+      else
+        tma_store_4d(map, src + r * TT::RB * TT::LD, kxg * TT::TC * TT::W, r * TT::RB, o, b);
+    }
     bulk_commit();
   };
   if (threadIdx.x == 0 && nq > 0) issue(0);
   const int c = threadIdx.x % TT::TC;
   for (int q = 0; q < nq; ++q) {
-    if (!kStore && threadIdx.x == 0 && q + 1 < nq) issue(q + 1);
-    if (!mbar_wait(&bars[q & 1], (q >> 1) & 1, job.err)) {
+    if (threadIdx.x == 0) {
+      if (KIND == 0) {
+        bulk_wait_read_but1();
+        if (q + 1 < nq) issue(q + 1);
+      } else if (KIND == 3) {
+        bulk_wait_read_but1();   // the work tile: its store is older than the newest
+      } else if (!kStore && q + 1 < nq) {
+        issue(q + 1);
+      }
+    }
+    if (!mbar_wait(&bars[q % NSLOT], (q / NSLOT) & 1, job.err)) {
       // give the copies in flight a bounded chance to finish before the CTA exits
       if (threadIdx.x == 0) {
-        if (kStore)
-          mbar_wait(&bars[q & 1], (q >> 1) & 1, nullptr);
+        if (KIND == 1 || KIND == 3)
+          mbar_wait(&bars[q % NSLOT], (q / NSLOT) & 1, nullptr);
         else if (q + 1 < nq)
-          mbar_wait(&bars[(q + 1) & 1], ((q + 1) >> 1) & 1, nullptr);
+          mbar_wait(&bars[(q + 1) % NSLOT], ((q + 1) / NSLOT) & 1, nullptr);
         if (kStore) bulk_wait_all();
       }
       return;
@@ -283,11 +303,13 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
     const long long es = job.zaxis ? (long long)N * (N / 2) : (N / 2);
     const long long base = (long long)b * spec_len_cx(N) + (job.zaxis ? (long long)o * (N / 2) : (long long)o * N * (N / 2)) +
                            kxg * TT::TC + c;
-    C* cur = (q & 1) ? ring1 : ring0;
+    C* cur = slot(q);
     DenseTile<C, TT::LD> t{cur};
     if constexpr (KIND == 0) {
-      GlobalSeq<C> g{job.out[item / tiles_per_buf] + base, es, true};
-      fft_tile<T, L, TT::TC, TT::NT, DIR>(t, t, g, tw);
+      fft_tile<T, L, TT::TC, TT::NT, DIR>(t, t, t, tw);
+      fence_proxy_async();
+      __syncthreads();
+      if (threadIdx.x == 0) store(&maps.m[item / tiles_per_buf], cur, kxg, o, b);
     } else if constexpr (KIND == 1 || KIND == 2) {
       ZCol<T, N> zc;
       zc.f1 = freq_of(o, N);
@@ -332,12 +354,19 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
       // inverse y of the shared x/y force transform U: IFFT(U) -> out[1] (the x component
       // before its -i k_2), IFFT(-i k_1 U) -> out[0] (the y component, in place)
       DenseTile<C, TT::LD> wt{work};
-      GlobalSeq<C> g1{job.out[1] + base, es, true};
-      fft_tile<T, L, TT::TC, TT::NT, +1>(t, wt, g1, stw);
+      fft_tile<T, L, TT::TC, TT::NT, +1>(t, wt, wt, stw);
+      fence_proxy_async();
       __syncthreads();
+      if (threadIdx.x == 0) {
+        store(&omaps.m[1], work, kxg, o, b);
+        bulk_wait_read_but1();   // the other slot's store (previous tile) has been read
+        if (q + 1 < nq) issue(q + 1);
+      }
       YMulSrc<T, N, TT::LD> src{cur};
-      GlobalSeq<C> g0{job.out[0] + base, es, true};
-      fft_tile<T, L, TT::TC, TT::NT, +1>(src, t, g0, stw);
+      fft_tile<T, L, TT::TC, TT::NT, +1>(src, t, t, stw);
+      fence_proxy_async();
+      __syncthreads();
+      if (threadIdx.x == 0) store(&omaps.m[0], cur, kxg, o, b);
     } else {
       // forward y of the adjoint's x and y sums: out[0] = i (k_1 Y(P_1) + k_2 Y(P_2))
       if (comp == 0) {

@@ -935,7 +935,8 @@ class Engine : public EngineBase {
       const int iu = spec_index(u), ib = spec_index(b);
       if (iu < 0 || ib < 0) return PM_ERR_STATE;
       if (split) {
-        PMGB_RET(fft_ysplit_tma<T>(n, B_, &tmy_[iu], u, b, tw_, dev_err_, nsm_, st_));
+        const CUtensorMap um[2] = {tmy_[iu], tmy_[ib]};
+        PMGB_RET(fft_ysplit_tma<T>(n, B_, um, u, b, tw_, dev_err_, nsm_, st_));
       } else {
         const CUtensorMap pm2[2] = {tmy_[iu], tmy_[ib]};
         PMGB_RET(fft_ymerge_tma<T>(n, B_, pm2, u, tw_, dev_err_, nsm_, st_));

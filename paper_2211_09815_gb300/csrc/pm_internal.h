@@ -75,7 +75,8 @@ int fft_fused_tma(int n, bool adjoint, const CUtensorMap* maps, const CUtensorMa
                   const cx_t<T>* tw, int* err, int nsm, cudaStream_t st);
 // the same split and merge over the main spectrum with TMA-staged tiles
 template <typename T>
-int fft_ysplit_tma(int n, int batch, const CUtensorMap* umap, cx_t<T>* u, cx_t<T>* out1, const cx_t<T>* tw,
+// umaps: y maps of u and out1
+int fft_ysplit_tma(int n, int batch, const CUtensorMap* umaps, cx_t<T>* u, cx_t<T>* out1, const cx_t<T>* tw,
                    int* err, int nsm, cudaStream_t st);
 template <typename T>
 int fft_ymerge_tma(int n, int batch, const CUtensorMap* pmaps, cx_t<T>* p1, const cx_t<T>* tw, int* err, int nsm,
