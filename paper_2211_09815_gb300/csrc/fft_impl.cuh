@@ -580,8 +580,8 @@ static void launch_tma_L(const CUtensorMap* maps, const CUtensorMap* omaps, cons
                          const cx_t<T>* tw, int nsm, cudaStream_t st) {
   using TT = TmaTile<T, L>;
   TmaMaps m{}, om{};
-  if (omaps)
-    for (int i = 0; i < 2; ++i) om.m[i] = omaps[i];
+  const int nomaps = (KIND == 1 || KIND == 3) ? 2 : ((KIND == 2 || KIND == 4) ? 1 : 0);
+  for (int i = 0; i < nomaps; ++i) om.m[i] = omaps[i];
   const int nmaps = KIND == 0 ? job.nbuf : ((KIND == 2 || KIND == 4) ? 2 : 1);
   for (int i = 0; i < nmaps; ++i) m.m[i] = maps[i];
   const size_t sm = KIND == 0 ? 3 * (size_t)TT::BYTES + 1024 : 3 * (size_t)TT::BYTES + (size_t)L * sizeof(cx_t<T>) + 1024;
@@ -641,7 +641,7 @@ int fft_ymerge_tma(int n, int batch, const CUtensorMap* pmaps, cx_t<T>* p1, cons
   job.zaxis = 0;
   job.batch = batch;
   job.err = err;
-  PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, -1, 4>(pmaps, nullptr, job, batch * tiles_of<T, LL>(), tw, nsm, st)));
+  PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, -1, 4>(pmaps, &pmaps[0], job, batch * tiles_of<T, LL>(), tw, nsm, st)));
   return PM_OK;
 }
 
@@ -657,7 +657,7 @@ int fft_fused_tma(int n, bool adjoint, const CUtensorMap* maps, const CUtensorMa
   job.dtab = zj.dtab;
   job.err = err;
   if (adjoint) {
-    PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, +1, 2>(maps, nullptr, job, zj.batch * tiles_of<T, LL>(), tw, nsm, st)));
+    PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, +1, 2>(maps, omaps, job, zj.batch * tiles_of<T, LL>(), tw, nsm, st)));
   } else {
     PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, +1, 1>(maps, omaps, job, zj.batch * tiles_of<T, LL>(), tw, nsm, st)));
   }

@@ -189,14 +189,13 @@ struct YAccDst {
   }
 };
 template <typename T, int LD>
-struct YMergeDst {
-  const cx_t<T>* acc;
-  cx_t<T>* out;     // this thread's column in HBM
-  long long es;
+struct YMergeDst {  // in place in the accumulator tile
+  cx_t<T>* acc;
   T k2;             // x frequency of the column
   __device__ __forceinline__ void st(int row, int c, cx_t<T> v) const {
-    const cx_t<T> a = acc[row * LD + c];
-    out[(long long)row * es] = cmake<cx_t<T>>(a.x - v.y * k2, a.y + v.x * k2);
+    cx_t<T>* q = acc + row * LD + c;
+    const cx_t<T> a = *q;
+    *q = cmake<cx_t<T>>(a.x - v.y * k2, a.y + v.x * k2);
   }
 };
 
@@ -256,12 +255,12 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
         tma_load_4d(dst + r * TT::RB * TT::LD, &maps.m[buf], bar, kxg * TT::TC * TT::W, r * TT::RB, o, b);
     }
   };
-  // Results leave by TMA stores from shared memory for KIND 0, 1 and 3.  KIND 0: three
-  // slots, so the slot refilled at the top of an iteration was stored two iterations
-  // earlier.  KIND 1 and 3 (two outputs: the work tile, then the input's own slot): the
-  // next load is issued after the first output, when the previous tile's stores out of
-  // that slot have long been read.
-  constexpr bool kStore = KIND == 0 || KIND == 1 || KIND == 3;
+  // Results leave by TMA stores from shared memory.  KIND 0: three slots, so the slot
+  // refilled at the top of an iteration was stored two iterations earlier.  KIND 1 and 3
+  // (two outputs: the work tile, then the input's own slot): the next load is issued after
+  // the first output, when the previous tile's stores out of that slot have long been
+  // read.  KIND 2 and 4 store only the work tile.
+  constexpr bool kStore = true;
   auto store = [&](const CUtensorMap* map, const C* src, int kxg, int o, int b) {
 #pragma unroll
     for (int r = 0; r < L / TT::RB; ++r) {
@@ -281,8 +280,8 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
         if (q + 1 < nq) issue(q + 1);
       } else if (KIND == 3) {
         bulk_wait_read_but1();   // the work tile: its store is older than the newest
-      } else if (!kStore && q + 1 < nq) {
-        issue(q + 1);
+      } else if ((KIND == 2 || KIND == 4) && q + 1 < nq) {
+        issue(q + 1);   // the ring slots are never store sources here
       }
     }
     if (!mbar_wait(&bars[q % NSLOT], (q / NSLOT) & 1, job.err)) {
@@ -342,12 +341,17 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
         __syncthreads();
         if (threadIdx.x == 0) store(&omaps.m[1], cur, kxg, o, b);
       } else {
+        // the accumulator (work tile) is first written by the last radix stage, after the
+        // barriers of the earlier ones: the previous item's store must have read it
+        if (comp == 0 && threadIdx.x == 0) bulk_wait_read_all();
         DenseAccDst<T, N, TT::LD> acc{work, zc, comp};
         fft_tile<T, L, TT::TC, TT::NT, -1>(t, t, acc, stw);
         if (comp == 1) {
           __syncthreads();
-          GlobalSeq<C> g{job.out[0] + base, es, true};
-          fft_tile<T, L, TT::TC, TT::NT, +1>(wt, wt, g, stw);
+          fft_tile<T, L, TT::TC, TT::NT, +1>(wt, wt, wt, stw);
+          fence_proxy_async();
+          __syncthreads();
+          if (threadIdx.x == 0) store(&omaps.m[0], work, kxg, o, b);
         }
       }
     } else if constexpr (KIND == 3) {
@@ -370,11 +374,15 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
     } else {
       // forward y of the adjoint's x and y sums: out[0] = i (k_1 Y(P_1) + k_2 Y(P_2))
       if (comp == 0) {
+        if (threadIdx.x == 0) bulk_wait_read_all();   // the previous item's store of the work tile
         YAccDst<T, N, TT::LD> acc{work};
         fft_tile<T, L, TT::TC, TT::NT, -1>(t, t, acc, stw);
       } else {
-        YMergeDst<T, TT::LD> dst{work, job.out[0] + base, es, (T)(kxg * TT::TC + c)};
+        YMergeDst<T, TT::LD> dst{work, (T)(kxg * TT::TC + c)};
         fft_tile<T, L, TT::TC, TT::NT, -1>(t, t, dst, stw);
+        fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) store(&omaps.m[0], work, kxg, o, b);
       }
     }
     __syncthreads();

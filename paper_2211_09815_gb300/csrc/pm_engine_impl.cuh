@@ -898,7 +898,7 @@ class Engine : public EngineBase {
       prof_.begin(st_, P_Z_ADJ, use_tma_ ? 2 : 1);
       if (use_tma_) {
         const CUtensorMap pm2[2] = {tmz_[4], tmz_[5]};
-        PMGB_RET(fft_fused_tma<T>(nm_, true, pm2, nullptr, za, tw_, dev_err_, nsm_, st_));
+        PMGB_RET(fft_fused_tma<T>(nm_, true, pm2, &tmz_[0], za, tw_, dev_err_, nsm_, st_));   // psi -> spec_[0]
         PMGB_RET(fft_fused_side<T>(nm_, za, true, tw_, st_));
       } else {
         PMGB_RET(fft_fused_z<T>(nm_, za, true, tw_, st_));
