@@ -165,6 +165,34 @@ def density(x, cfg):
     return cic_scatter(x, np.full(x.shape[1], cfg.mass), cfg) - 1.0
 
 
+def density_at(x, cfg, cells):
+    """The same overdensity at the flat mesh indices ``cells`` only, by direct summation
+    of m W over the particles whose CIC corners include them (for meshes too large to
+    deposit whole)."""
+    cells = np.asarray(cells, dtype=np.int64)
+    order = np.argsort(cells)
+    srt = cells[order]
+    mark = np.zeros(cfg.n_mesh ** 3, dtype=bool)
+    mark[srt] = True
+    n, l = cfg.n_mesh, cfg.cell
+    u = x / l
+    i = np.floor(u)
+    t = u - i
+    i = i.astype(np.int64)
+    acc = np.zeros(len(cells))
+    for d in itertools.product((0, 1), repeat=3):      # the 8 corners of Eq. 10
+        idx = (((i[0] + d[0]) % n) * n + (i[1] + d[1]) % n) * n + (i[2] + d[2]) % n
+        hit = mark[idx]
+        w = 1.0
+        for c in range(3):
+            tc = t[c][hit]
+            w = w * (tc if d[c] else 1.0 - tc)
+        np.add.at(acc, np.searchsorted(srt, idx[hit]), cfg.mass * w)
+    out = np.empty(len(cells))
+    out[order] = acc - 1.0
+    return out
+
+
 # ----------------------------------------------------------------------------- force
 
 def _green(cfg, Om):

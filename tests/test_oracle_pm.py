@@ -320,3 +320,13 @@ def test_power_spectrum_of_a_plane_wave():
     nn = np.sqrt(n0 ** 2 + n1 ** 2 + n2 ** 2)
     full = np.sum(np.floor(np.sqrt(np.add.outer(np.add.outer(np.fft.fftfreq(n, 1 / n) ** 2, np.fft.fftfreq(n, 1 / n) ** 2), np.fft.fftfreq(n, 1 / n) ** 2))) == 3)
     assert cnt[3] == full
+
+
+def test_density_at_sampled_cells_equals_full_deposit():
+    """The sampled-cell form used at full mesh sizes against the whole-mesh deposit."""
+    cfg = pm.PMConfig(box=32.0, n_mesh=16, n_ptcl=8, n_steps=1)
+    rng = np.random.default_rng(21)
+    x = pm.lattice(cfg) + rng.normal(scale=3.0, size=(3, 8 ** 3))
+    full = pm.density(x, cfg).ravel()
+    cells = rng.choice(16 ** 3, size=200, replace=False)
+    np.testing.assert_allclose(pm.density_at(x, cfg, cells), full[cells], rtol=0, atol=1e-12)
