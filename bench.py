@@ -526,7 +526,8 @@ def run_ckpt_compare(args):
 def run_precision_study(args):
     """FP32 against an FP64 GPU run of the same workload, per output: final displacement
     RMS (in cells), momentum relative L2, per-shell P(k) relative error, dJ/domega cosine
-    and relative L2, dJ/dtheta relative error."""
+    and relative L2, dJ/dtheta relative error; the FP32 gradient with reverse time
+    integration and with checkpoints every 8 steps."""
     import torch
     from paper_2211_09815_gb300 import build, inputs, pm
     build.build()
@@ -534,7 +535,7 @@ def run_precision_study(args):
     N, M = npc ** 3, nm ** 3
     out = {}
     tgt_np = None
-    for prec in (0, 1):
+    for prec, ck in ((0, 0), (0, 8), (1, 0)):
         dt = torch.float32 if prec == 0 else torch.float64
         if tgt_np is None:
             om2 = torch.from_numpy(inputs.white_noise(npc, 2)).cuda()
@@ -545,7 +546,7 @@ def run_precision_study(args):
             c0.close()
             del om2, t
         om = torch.from_numpy(inputs.white_noise(npc, 1)).to("cuda", dt)
-        ctx = pm.PMContext(box, nm, npc, n, [THETA], om, precision=prec)
+        ctx = pm.PMContext(box, nm, npc, n, [THETA], om, precision=prec, ckpt_every=ck)
         disp = torch.empty(3 * N, device="cuda", dtype=dt)
         mom = torch.empty_like(disp)
         ctx.forward(disp=disp, mom=mom)
@@ -559,13 +560,13 @@ def run_precision_study(args):
         t0 = time.perf_counter()
         ctx.adjoint(djdd=djdd, grad_omega=gw, grad_theta=gt)
         torch.cuda.synchronize()
-        out[prec] = dict(s=disp.cpu().numpy().astype(np.float64), p=mom.cpu().numpy().astype(np.float64),
+        out[(prec, ck)] = dict(s=disp.cpu().numpy().astype(np.float64), p=mom.cpu().numpy().astype(np.float64),
                          pk=pk[0], nmodes=nmodes, gw=gw.cpu().numpy().astype(np.float64), gt=gt.cpu().numpy(),
                          adj_s=time.perf_counter() - t0)
         ctx.close()
         del om, disp, mom, tgt, djdd, gw, gt
         torch.cuda.empty_cache()
-    a, b = out[0], out[1]
+    a, b, a8 = out[(0, 0)], out[(1, 0)], out[(0, 8)]
     cell = box / nm
     ok = b["nmodes"] > 0
     ok[0] = False
@@ -578,7 +579,10 @@ def run_precision_study(args):
         "grad_omega_rel_l2": float(np.linalg.norm(a["gw"] - b["gw"]) / np.linalg.norm(b["gw"])),
         "grad_theta_rel": (np.abs(a["gt"] / b["gt"] - 1)).tolist(),
         "grad_theta_fp64": b["gt"].tolist(),
-        "adjoint_seconds": {"f32": a["adj_s"], "f64": b["adj_s"]},
+        "ckpt8_f32": {"grad_omega_cosine": float(a8["gw"] @ b["gw"] / (np.linalg.norm(a8["gw"]) * np.linalg.norm(b["gw"]))),
+                      "grad_omega_rel_l2": float(np.linalg.norm(a8["gw"] - b["gw"]) / np.linalg.norm(b["gw"])),
+                      "grad_theta_rel": (np.abs(a8["gt"] / b["gt"] - 1)).tolist()},
+        "adjoint_seconds": {"f32": a["adj_s"], "f32_ckpt8": a8["adj_s"], "f64": b["adj_s"]},
     }
     print(json.dumps(res))
 

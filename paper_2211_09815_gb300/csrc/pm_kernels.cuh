@@ -28,6 +28,17 @@ template <typename T> struct Geo {
   long long M;    // mesh cells per instance
 };
 
+// correctly rounded products and fused multiply-adds, never re-associated or contracted
+// differently by the compiler: the forward and reverse passes gather the same force on a
+// particle bit for bit
+template <typename T> __device__ __forceinline__ T mul_rn(T a, T b);
+template <> __device__ __forceinline__ float mul_rn<float>(float a, float b) { return __fmul_rn(a, b); }
+template <> __device__ __forceinline__ double mul_rn<double>(double a, double b) { return __dmul_rn(a, b); }
+template <typename T> __device__ __forceinline__ T fma_rn(T a, T b, T c);
+template <> __device__ __forceinline__ float fma_rn<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <> __device__ __forceinline__ double fma_rn<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+
 // Cell index and fraction along each axis for particle i at displacement s (floor
 // convention: u = q/l + s/l with q/l = j*ratio + 1/2; the integer part of q/l is added
 // separately so that the fraction keeps the precision of s, not of x).
@@ -36,7 +47,7 @@ __device__ __forceinline__ void cic_cell(const Geo<T>& g, long long i, const T s
   const int j[3] = {(int)(i >> (2 * g.lg_np)), (int)((i >> g.lg_np) & (g.np - 1)), (int)(i & (g.np - 1))};
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const T v = (T)0.5 + s[c] * g.inv_l;
+    const T v = fma_rn<T>(s[c], g.inv_l, (T)0.5);
     const T f = floor(v);
     t[c] = v - f;
     cell[c] = (j[c] * g.ratio + (int)f) & (g.nm - 1);
@@ -251,10 +262,13 @@ k_gather_fwd(Geo<T> g, T* __restrict__ s, T* __restrict__ p, T* __restrict__ a_o
     T a[3] = {0, 0, 0};
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
-      const T w = ((d & 4) ? t[0] : (T)1 - t[0]) * ((d & 2) ? t[1] : (T)1 - t[1]) * ((d & 1) ? t[2] : (T)1 - t[2]);
-      a[0] += w * fv[d].x;
-      a[1] += w * fv[d].y;
-      a[2] += w * fv[d].z;
+      const T w0 = (d & 4) ? t[0] : (T)1 - t[0];
+      const T w1 = (d & 2) ? t[1] : (T)1 - t[1];
+      const T w2 = (d & 1) ? t[2] : (T)1 - t[2];
+      const T w = mul_rn<T>(mul_rn<T>(w0, w1), w2);
+      a[0] = fma_rn<T>(w, fv[d].x, a[0]);
+      a[1] = fma_rn<T>(w, fv[d].y, a[1]);
+      a[2] = fma_rn<T>(w, fv[d].z, a[2]);
     }
     T pv[3] = {pb[i], pb[g.N + i], pb[2 * g.N + i]};
 #pragma unroll
@@ -315,10 +329,10 @@ k_gather_adj(Geo<T> g, T mass, T* __restrict__ s, T* __restrict__ p, T* __restri
       const T w2 = (d & 1) ? t[2] : (T)1 - t[2];
       const T g0 = (d & 4) ? il : -il, g1 = (d & 2) ? il : -il, g2 = (d & 1) ? il : -il;
       const T h = qv[0] * fv[d].x + qv[1] * fv[d].y + qv[2] * fv[d].z + mass * fv[d].w;
-      const T w = w0 * w1 * w2;
-      a[0] += w * fv[d].x;
-      a[1] += w * fv[d].y;
-      a[2] += w * fv[d].z;
+      const T w = mul_rn<T>(mul_rn<T>(w0, w1), w2);
+      a[0] = fma_rn<T>(w, fv[d].x, a[0]);
+      a[1] = fma_rn<T>(w, fv[d].y, a[1]);
+      a[2] = fma_rn<T>(w, fv[d].z, a[2]);
       al[0] += g0 * w1 * w2 * h;
       al[1] += w0 * g1 * w2 * h;
       al[2] += w0 * w1 * g2 * h;
