@@ -111,10 +111,20 @@ k_bin_fill(Geo<T> g, BinGeo bg, const T* __restrict__ s, const T* __restrict__ p
     const long long w = w0 + lane;
     const bool valid = w < g.N;
     unsigned key = 0xFFFFFFFFu;
-    long long i = 0;
+    // every load of the particle first (key, position, pi), then the cursor atomic
+    V4<T> r0{0, 0, 0, 0}, r1{0, 0, 0, 0};
     if (valid) {
-      i = particle_of(g, w);
+      const long long i = particle_of(g, w);
       key = keys[(long long)b * g.N + i];
+      const T sv[3] = {sb[i], sb[g.N + i], sb[2 * g.N + i]};
+      if constexpr (NQ == 4) {
+        const T* pb = pi + (long long)b * 3 * g.N;
+        r1 = V4<T>{pb[i] * sp[0], pb[g.N + i] * sp[1], pb[2 * g.N + i] * sp[2], (T)0};
+      }
+      int cell[3];
+      T t[3];
+      cic_cell(g, i, sv, cell, t);
+      r0 = V4<T>{t[0], t[1], t[2], bits_to_real<T>(pack_local(bg, cell))};
     }
     const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
     const int leader = __ffs(peers) - 1;
@@ -123,15 +133,8 @@ k_bin_fill(Geo<T> g, BinGeo bg, const T* __restrict__ s, const T* __restrict__ p
     pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
     if (valid) {
       pos += __popc(peers & ((1u << lane) - 1u));
-      const T sv[3] = {sb[i], sb[g.N + i], sb[2 * g.N + i]};
-      int cell[3];
-      T t[3];
-      cic_cell(g, i, sv, cell, t);
-      rec0[pos] = V4<T>{t[0], t[1], t[2], bits_to_real<T>(pack_local(bg, cell))};
-      if constexpr (NQ == 4) {
-        const T* pb = pi + (long long)b * 3 * g.N;
-        rec1[pos] = V4<T>{pb[i] * sp[0], pb[g.N + i] * sp[1], pb[2 * g.N + i] * sp[2], (T)0};
-      }
+      rec0[pos] = r0;
+      if constexpr (NQ == 4) rec1[pos] = r1;
     }
   }
 }

@@ -253,6 +253,7 @@ k_gather_fwd(Geo<T> g, T* __restrict__ s, T* __restrict__ p, T* __restrict__ a_o
        w += (long long)gridDim.x * blockDim.x) {
     const long long i = particle_of(g, w);
     T sv[3] = {sb[i], sb[g.N + i], sb[2 * g.N + i]};
+    T pv[3] = {pb[i], pb[g.N + i], pb[2 * g.N + i]};   // in flight with the corner loads
     int cell[3];
     T t[3];
     cic_cell(g, i, sv, cell, t);
@@ -270,7 +271,6 @@ k_gather_fwd(Geo<T> g, T* __restrict__ s, T* __restrict__ p, T* __restrict__ a_o
       a[1] = fma_rn<T>(w, fv[d].y, a[1]);
       a[2] = fma_rn<T>(w, fv[d].z, a[2]);
     }
-    T pv[3] = {pb[i], pb[g.N + i], pb[2 * g.N + i]};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       pv[c] += a[c] * kA;
