@@ -20,37 +20,6 @@
 
 namespace pmgb {
 
-struct BinGeo {
-  int lx, ly, lz;       // log2 of the tile extent along axes 2, 1, 0
-  int ntx, nty, ntz;    // tiles per axis
-  int ntiles;           // per instance
-  long long nkeys;      // bins per instance = 8 ntiles
-};
-
-inline BinGeo make_bin_geo(int lg_nm, int lx, int ly, int lz) {
-  BinGeo b;
-  b.lx = lx < lg_nm ? lx : lg_nm;
-  b.ly = ly < lg_nm ? ly : lg_nm;
-  b.lz = lz < lg_nm ? lz : lg_nm;
-  b.ntx = 1 << (lg_nm - b.lx);
-  b.nty = 1 << (lg_nm - b.ly);
-  b.ntz = 1 << (lg_nm - b.lz);
-  b.ntiles = b.ntx * b.nty * b.ntz;
-  b.nkeys = 8LL * b.ntiles;
-  return b;
-}
-
-// class bits of a cell: on the last layer of its tile along x (bit 0), y (bit 1), z (bit 2)
-__device__ __forceinline__ unsigned bin_class(const BinGeo& bg, const int c[3]) {
-  const unsigned mx = (1u << bg.lx) - 1, my = (1u << bg.ly) - 1, mz = (1u << bg.lz) - 1;
-  return (unsigned)(((unsigned)c[2] & mx) == mx) | ((unsigned)(((unsigned)c[1] & my) == my) << 1) |
-         ((unsigned)(((unsigned)c[0] & mz) == mz) << 2);
-}
-__device__ __forceinline__ unsigned bin_key(const BinGeo& bg, const int c[3]) {
-  const unsigned tile = (((unsigned)c[0] >> bg.lz) * bg.nty + ((unsigned)c[1] >> bg.ly)) * bg.ntx + ((unsigned)c[2] >> bg.lx);
-  return tile * 8u + bin_class(bg, c);
-}
-
 // Warp-uniform loop over the work indices of this block's warps: every lane of a warp
 // takes the same number of iterations, so that the warp-wide match below sees all lanes.
 template <typename T>

@@ -182,6 +182,7 @@ class Engine : public EngineBase {
 
   // ------------------------------------------------------------------ forward
   int forward(void* disp, void* mom, void* dens) override {
+    counted_ = false;
     prof_.begin(st_, P_OTHER, 12);
     PMGB_RET(initial_conditions());
     prof_.end(st_, P_OTHER);
@@ -196,8 +197,11 @@ class Engine : public EngineBase {
       const long long fis = 2 * spec_len_cx(nm_);
       StepCoef<T> sc{fkA_, fkB_, fdr_};
       prof_.begin(st_, P_GATHER_FWD, 1);
+      // the bins of the next step's deposit are counted at the new positions
       k_gather_fwd<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, s_, p_, j == n_ ? a_ : nullptr, fvec_, sc, j,
-                                                              n_ + 1, cks, ckp);
+                                                              n_ + 1, cks, ckp, bg1_, j < n_ ? bcount_ : nullptr,
+                                                              bkeys_);
+      counted_ = j < n_;
       prof_.end(st_, P_GATHER_FWD);
       PMGB_CK(cudaGetLastError());
     }
@@ -239,6 +243,7 @@ class Engine : public EngineBase {
 
   // ------------------------------------------------------------------ adjoint
   int adjoint(const void* djdd, const void* djdx, const void* djdp, void* djdw, double* djdth) override {
+    counted_ = false;
     if (!have_fwd_) return PM_ERR_STATE;
     PMGB_CK(cudaMemsetAsync(pimax_, 0, sizeof(unsigned) * 3 * B_, st_));
     prof_.begin(st_, P_OTHER, 1);
@@ -261,7 +266,9 @@ class Engine : public EngineBase {
       double* pxp = part_ + (long long)(2 * j + 1) * B_ * G_;
       prof_.begin(st_, P_GATHER_ADJ, 1);
       k_gather_adj<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, mass_, s_, p_, xi_, pi_, nullptr, nullptr, fvec_,
-                                                              sc, j, n_ + 1, ckp, cks, ppa, pxp, pimax_);
+                                                              sc, j, n_ + 1, ckp, cks, ppa, pxp, pimax_, bg4_,
+                                                              j > 0 ? bcount_ : nullptr, bkeys_);
+      counted_ = j > 0;
       prof_.end(st_, P_GATHER_ADJ);
       PMGB_CK(cudaGetLastError());
     }
@@ -297,6 +304,7 @@ class Engine : public EngineBase {
 
   // ------------------------------------------------------------------ operators
   int op_density(const void* disp, void* dens) override {
+    counted_ = false;
     if (reinterpret_cast<uintptr_t>(dens) % (4 * sizeof(T))) return PM_ERR_ARG;   // vector stores
     have_fwd_ = false;
     PMGB_CK(cudaMemcpyAsync(s_, disp, sizeof(T) * B_ * 3 * N_, cudaMemcpyDeviceToDevice, st_));
@@ -305,6 +313,7 @@ class Engine : public EngineBase {
   }
 
   int op_force(const void* disp, const void* pi, void* acc, void* alpha) override {
+    counted_ = false;
     have_fwd_ = false;
     PMGB_CK(cudaMemcpyAsync(s_, disp, sizeof(T) * B_ * 3 * N_, cudaMemcpyDeviceToDevice, st_));
     const long long fis = 2 * spec_len_cx(nm_);
@@ -312,7 +321,7 @@ class Engine : public EngineBase {
     if (!pi) {
       PMGB_RET(force_chain(s_, nullptr, false));
       k_gather_fwd<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, s_, p_, (T*)acc, fvec_, sc, 0, 1, nullptr,
-                                                              nullptr);
+                                                              nullptr, bg1_, nullptr, nullptr);
     } else {
       PMGB_CK(cudaMemcpyAsync(pi_, pi, sizeof(T) * B_ * 3 * N_, cudaMemcpyDeviceToDevice, st_));
       PMGB_CK(cudaMemsetAsync(pimax_, 0, sizeof(unsigned) * 3 * B_, st_));
@@ -323,7 +332,7 @@ class Engine : public EngineBase {
       PMGB_RET(force_chain(s_, pi_, false));
       k_gather_adj<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, mass_, s_, p_, xi_, pi_, (T*)acc, (T*)alpha,
                                                               fvec_, sc, 0, 1, nullptr, nullptr, nullptr, nullptr,
-                                                              nullptr);
+                                                              nullptr, bg4_, nullptr, nullptr);
     }
     PMGB_CK(cudaGetLastError());
     return PM_OK;
@@ -700,6 +709,7 @@ class Engine : public EngineBase {
   // the choice: the deposit sums are exact integers, and both column-pass forms run the
   // same radix stages.
   int autotune(int reps, pm_tuning* chosen, double* ms_best) override {
+    counted_ = false;
     if (reps < 1) reps = 3;
     const bool prof_on = prof_.on;
     prof_.on = false;
@@ -796,18 +806,21 @@ class Engine : public EngineBase {
       PMGB_CK(cudaGetLastError());
       PMGB_CK(cudaMemsetAsync(pimax_, 0, sizeof(unsigned) * 3 * B_, st_));
     }
-    prof_.begin(st_, P_SCATTER, 6);
-    PMGB_RET(pi ? deposit(s, pi, dout, dis, bg4_, tune_.threads_adjoint)
-                : deposit(s, nullptr, dout, dis, bg1_, tune_.threads_density));
+    const bool pre = counted_;
+    counted_ = false;
+    prof_.begin(st_, P_SCATTER, pre ? 5 : 6);
+    PMGB_RET(pi ? deposit(s, pi, dout, dis, bg4_, tune_.threads_adjoint, pre)
+                : deposit(s, nullptr, dout, dis, bg1_, tune_.threads_density, pre));
     prof_.end(st_, P_SCATTER);
     return PM_OK;
   }
   // binning + tile-owner deposit with tile geometry bg and nt threads per tile (e_pi_
   // must hold the pi exponents when pi is given)
-  int deposit(const T* s, const T* pi, T* dout, long long dis, const BinGeo& bg, int nt) {
+  // (precounted: the previous gather already counted the bins of s with geometry bg)
+  int deposit(const T* s, const T* pi, T* dout, long long dis, const BinGeo& bg, int nt, bool precounted = false) {
     const long long nbin = (long long)B_ * bg.nkeys + 1;
     const int nscan = (int)((nbin + kScanBlock - 1) / kScanBlock);
-    k_bin_count<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, bg, s, bcount_, bkeys_);
+    if (!precounted) k_bin_count<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, bg, s, bcount_, bkeys_);
     k_scan_blocks<<<nscan, 256, 0, st_>>>(bcount_, bstart_, bsums_, nbin);
     k_scan_sums<<<1, 256, 0, st_>>>(bsums_, nscan);
     k_scan_add<<<(int)std::min<long long>((nbin + 255) / 256, 4096), 256, 0, st_>>>(bstart_, bcursor_, bsums_, nbin);
@@ -1042,6 +1055,7 @@ class Engine : public EngineBase {
   const void* graph_args_[4] = {nullptr, nullptr, nullptr, nullptr};
   T *s_ = nullptr, *p_ = nullptr, *a_ = nullptr, *xi_ = nullptr, *pi_ = nullptr, *s1_ = nullptr, *omega_ = nullptr;
   BinGeo bg1_{}, bg4_{};
+  bool counted_ = false;   // the last gather counted the bins of the next deposit
   pm_tuning tune_{};
   unsigned *bkeys_ = nullptr, *bcount_ = nullptr, *bstart_ = nullptr, *bcursor_ = nullptr, *bsums_ = nullptr;
   V4<T> *brec0_ = nullptr, *brec1_ = nullptr;

@@ -230,6 +230,55 @@ template <> __device__ __forceinline__ void fixed_words<double>(double v, unsign
   hi = (unsigned)(r >> 32);
 }
 
+// ------------------------------------------------------------------ deposit bins
+// Bins of the tile-owner deposit (bin_kernels.cuh): mesh tiles of 2^lx x 2^ly x 2^lz cells
+// (x = array axis 2), and per tile a class of three bits, set when the particle's cell is on
+// the tile's last layer along x, y or z (its CIC cloud reaches into the next tile there).
+struct BinGeo {
+  int lx, ly, lz;       // log2 of the tile extent along axes 2, 1, 0
+  int ntx, nty, ntz;    // tiles per axis
+  int ntiles;           // per instance
+  long long nkeys;      // bins per instance = 8 ntiles
+};
+
+inline BinGeo make_bin_geo(int lg_nm, int lx, int ly, int lz) {
+  BinGeo b;
+  b.lx = lx < lg_nm ? lx : lg_nm;
+  b.ly = ly < lg_nm ? ly : lg_nm;
+  b.lz = lz < lg_nm ? lz : lg_nm;
+  b.ntx = 1 << (lg_nm - b.lx);
+  b.nty = 1 << (lg_nm - b.ly);
+  b.ntz = 1 << (lg_nm - b.lz);
+  b.ntiles = b.ntx * b.nty * b.ntz;
+  b.nkeys = 8LL * b.ntiles;
+  return b;
+}
+
+// class bits of a cell: on the last layer of its tile along x (bit 0), y (bit 1), z (bit 2)
+__device__ __forceinline__ unsigned bin_class(const BinGeo& bg, const int c[3]) {
+  const unsigned mx = (1u << bg.lx) - 1, my = (1u << bg.ly) - 1, mz = (1u << bg.lz) - 1;
+  return (unsigned)(((unsigned)c[2] & mx) == mx) | ((unsigned)(((unsigned)c[1] & my) == my) << 1) |
+         ((unsigned)(((unsigned)c[0] & mz) == mz) << 2);
+}
+__device__ __forceinline__ unsigned bin_key(const BinGeo& bg, const int c[3]) {
+  const unsigned tile = (((unsigned)c[0] >> bg.lz) * bg.nty + ((unsigned)c[1] >> bg.ly)) * bg.ntx + ((unsigned)c[2] >> bg.lx);
+  return tile * 8u + bin_class(bg, c);
+}
+
+// Count a particle's bin for the next deposit (its key, and a warp-aggregated increment of
+// the bin count).  Every lane of the warp calls this together.
+template <typename T>
+__device__ __forceinline__ void count_bin(const Geo<T>& g, const BinGeo& bg, long long i, const T sv[3], int b,
+                                          unsigned* __restrict__ count, unsigned* __restrict__ keys) {
+  int cell[3];
+  T t[3];
+  cic_cell(g, i, sv, cell, t);
+  const unsigned key = bin_key(bg, cell);
+  keys[(long long)b * g.N + i] = key;
+  const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+  if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(count + (long long)b * bg.nkeys + key, (unsigned)__popc(peers));
+}
+
 // ---------------------------------------------------------------------- gathers
 template <typename T>
 struct StepCoef {  // per-instance coefficient tables [batch][n+1], indexed at step j
@@ -243,7 +292,7 @@ template <typename T>
 __global__ void __launch_bounds__(kPtclThreads)
 k_gather_fwd(Geo<T> g, T* __restrict__ s, T* __restrict__ p, T* __restrict__ a_out,
              const V4<T>* __restrict__ fvec, StepCoef<T> sc, int j, int nstep1, T* __restrict__ ck_s,
-             T* __restrict__ ck_p) {
+             T* __restrict__ ck_p, BinGeo bg, unsigned* __restrict__ bcount, unsigned* __restrict__ bkeys) {
   const int b = blockIdx.y;
   const T kA = sc.kA[b * nstep1 + j], kB = sc.kB[b * nstep1 + j], dr = sc.dr[b * nstep1 + j];
   T* sb = s + (long long)b * 3 * g.N;
@@ -282,6 +331,9 @@ k_gather_fwd(Geo<T> g, T* __restrict__ s, T* __restrict__ p, T* __restrict__ a_o
       sb[c * g.N + i] = sv[c];
       if (a_out) a_out[(long long)b * 3 * g.N + c * g.N + i] = a[c];
     }
+    // bin of the new position for the next step's deposit (the loop is warp-uniform: N is
+    // a multiple of 32 and so is the grid stride)
+    if (bcount) count_bin(g, bg, i, sv, b, bcount, bkeys);
   }
 }
 
@@ -294,7 +346,8 @@ k_gather_adj(Geo<T> g, T mass, T* __restrict__ s, T* __restrict__ p, T* __restri
              T* __restrict__ a_out, T* __restrict__ alpha_out, const V4<T>* __restrict__ fvec,
              StepCoef<T> sc, int j, int nstep1,
              const T* __restrict__ ck_p, const T* __restrict__ ck_s, double* __restrict__ part_pa,
-             double* __restrict__ part_xp, unsigned* __restrict__ pimax) {
+             double* __restrict__ part_xp, unsigned* __restrict__ pimax, BinGeo bg, unsigned* __restrict__ bcount,
+             unsigned* __restrict__ bkeys) {
   __shared__ double shd[kPtclThreads / 32];
   __shared__ float shf[kPtclThreads / 32];
   const int b = blockIdx.y;
@@ -360,6 +413,7 @@ k_gather_adj(Geo<T> g, T mass, T* __restrict__ s, T* __restrict__ p, T* __restri
       if (a_out) a_out[po + c * g.N + i] = a[c];
       if (alpha_out) alpha_out[po + c * g.N + i] = al[c];
     }
+    if (bcount) count_bin(g, bg, i, sv, b, bcount, bkeys);   // bin for the previous step's deposit
   }
   const double spa = block_sum(acc_pa.value(), shd);
   const double sxp = block_sum(acc_xp.value(), shd);
