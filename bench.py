@@ -459,6 +459,7 @@ def run_batched(args):
         max_diff = 0.0
         for b in range(B):
             c1 = pm.PMContext(box, nm, npc, n, [theta[b].tolist()], om[b].contiguous(), stream=stream)
+            c1.set_tuning(out["tuning"])   # the same launch shapes: results comparable bit for bit
             djdd = torch.empty(M, device="cuda")
             g1 = torch.empty(N, device="cuda")
             t1 = tgt[b * M:(b + 1) * M]
