@@ -11,10 +11,11 @@
 // exact and independent of the order of the particles.  The CTA then writes the real
 // meshes (delta and pi_c) once, in the working precision.
 //
-// Binning: a count (warp-aggregated integer atomics on an L2-resident array), an
-// exclusive scan, and a fill that writes each particle's record (cell fractions, cell
-// within its tile, and in the adjoint the scaled pi) in bin order, so that a tile's CTA
-// reads its particles as contiguous runs.
+// Binning: a count (warp-aggregated integer atomics on an L2-resident array; inside a
+// simulation step the gather kernels count the bins of the positions they have just
+// written, count_bin in pm_kernels.cuh), an exclusive scan, and a fill that writes each
+// particle's record (cell fractions, cell within its tile, and in the adjoint the scaled
+// pi) in bin order, so that a tile's CTA reads its particles as contiguous runs.
 #pragma once
 #include "pm_kernels.cuh"
 

@@ -6,9 +6,10 @@
 // inputs of its butterfly, applies the stage twiddles, does an R-point DFT in registers
 // and stores the R outputs at their Stockham positions.  A tile in shared memory is
 // laid out [L][LD] with the sequence index innermost, so that for column passes a warp's
-// loads and stores touch consecutive addresses.  The first stage of a column pass reads
-// straight from global memory and the last one writes straight back; the x passes load
-// rows into shared memory with coalesced reads first.
+// loads and stores touch consecutive addresses.  The unstaged column passes read the
+// first stage straight from global memory and write the last one straight back; the
+// TMA-staged ones (fft_tma.cuh) work on tiles in shared memory; the x passes load rows
+// into shared memory with coalesced reads first.
 #pragma once
 #include "common.cuh"
 

@@ -2,10 +2,11 @@
 // the main half spectrum), templated on the real type.
 //
 // One CTA per SM loops over column tiles (TC sequences x L elements).  A single thread
-// issues the tensor-memory-accelerator loads of the next tile into the other half of a
-// two-slot shared-memory ring (cp.async.bulk.tensor, completion on an mbarrier) before the
-// CTA works on the current tile, so HBM reads of tile t+1 overlap the radix stages of
-// tile t.  Results leave through the last radix stage's direct global stores.
+// issues the tensor-memory-accelerator loads of the next tile into a free slot of a
+// shared-memory ring (cp.async.bulk.tensor, completion on an mbarrier) while the CTA works
+// on the current tile, so HBM reads of tile t+1 overlap the radix stages of tile t.  The
+// last radix stage writes its tile into shared memory and the same thread stores it with
+// TMA (cp.async.bulk.tensor from shared memory, bulk async-groups).
 //   KIND 0: in-place column FFT of up to four buffers (direction DIR)
 //   KIND 1: z FFT of delta^, 2 inverse z FFTs: of -i k_0 G delta^ (z force) and of
 //           G delta^ (shared by the y and x force components; -i k_1 and -i k_2 are

@@ -31,8 +31,9 @@ template <typename T> struct RowBuf {
 };
 template <typename T> struct RowJob { RowBuf<T> b[4]; };
 
-// Fused z pass: spectra in -> spectra out with the Green's function multiplier
-// H_c = f_c * coef[b] / n^2 * (deconvolution) * (-i) per mode.
+// Fused z pass with the Green's function G = coef[b] / n^2 * (deconvolution) per mode.
+// Force: in[0] = delta^ -> out[0] = z force (-i k_0 G), out[1] = U (G, shared by the y and
+// x forces).  Adjoint: in[0] = P_0, in[1] = V -> out[0] = psi.
 template <typename T> struct ZJob {
   cx_t<T>* in[3];
   cx_t<T>* out[3];

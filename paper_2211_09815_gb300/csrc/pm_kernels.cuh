@@ -4,9 +4,10 @@
 //  k_scatter        CIC mass (and adjoint pi) assignment, Sec. 2.2 Eq. 10, int64 fixed point
 //                   with global atomics (the allocation-free density entry point; the
 //                   engine assigns by mesh tiles, bin_kernels.cuh)
-//  k_gather_fwd     CIC force gather + kick / kick / drift of Eq. 16 (one launch per step)
+//  k_gather_fwd     CIC force gather + kick / kick / drift of Eq. 16 (one launch per step);
+//                   counts the deposit bins of the new positions for the next step
 //  k_gather_adj     CIC gather of a and alpha (Eq. 49 F line) + reverse kicks and drift of
-//                   Eq. 49, FP64 partials of the theta terms of Eq. 51
+//                   Eq. 49, FP64 partials of the theta terms of Eq. 51; bin counts as above
 //  k_adjoint_init   xi_n = dJ/dx_n (density cotangent through the CIC weight gradient), pi_n
 //  k_density_out, k_mse, k_za_mul, k_za_adj_mul, k_ic_state, k_ic_adj_prep, k_final_theta
 #pragma once
