@@ -184,6 +184,23 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------------ ours
+def replica_seed(rank):
+    """White-noise stream of a replica: every rank simulates its own universe."""
+    return 1 + 10 * rank
+
+
+def replica_throughput(ms_local, steps, n_steps, world, dist=None, device="cpu"):
+    """Whole-job throughput of `world` independent replicas (no collective on the data
+    path): each rank ran `steps` gradient evaluations of `n_steps` PM steps in ms_local;
+    the job takes the slowest rank's time.  Returns (max ms over ranks, PM steps/s)."""
+    import torch
+    t = torch.tensor([ms_local], device=device, dtype=torch.float64)
+    if dist is not None and world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * n_steps * steps / (ms_max / 1e3)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2211_09815_gb300 import build, inputs, pm
@@ -201,7 +218,7 @@ def run_ours(args, rank, world, local_rank):
         if dist is not None:
             dist.barrier()
 
-    seed = 1 + 10 * rank
+    seed = replica_seed(rank)
     om_host = torch.from_numpy(inputs.white_noise(npc, seed)).pin_memory()
     om = om_host.to("cuda")
     # target density from a second seed, made by the same forward model
@@ -250,12 +267,8 @@ def run_ours(args, rank, world, local_rank):
     prof = ctx.profile_read()
     ctx.profile(False)
     loss_val = float(loss.item())
-    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max, value = replica_throughput(ms, args.steps, n, world, dist, "cuda")
     ms_per_eval = ms_max / args.steps
-    value = world * n * args.steps / (ms_max / 1e3)
 
     # end to end through the C ABI with host buffers: omega and target in, loss and
     # gradients out, copies inside the timed region
@@ -276,10 +289,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     e2e_ms = max(e0.elapsed_time(e1), wall * 1e3)
-    t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * n * args.steps / (float(t.item()) / 1e3)
+    _, e2e_value = replica_throughput(e2e_ms, args.steps, n, world, dist, "cuda")
     ctx.close()
 
     if rank != 0:
