@@ -195,9 +195,10 @@ long long pm_scratch_bytes(const pm_ctx* ctx);
  * results: the CIC sums are exact integers for any tile shape, and the staged and
  * unstaged column passes run the same radix stages).
  *   tile_log2_density[3] : log2 of the deposit tile extent along axes (z, y, x), the
- *                          density-only deposit of the forward steps; 9..11 in total,
+ *                          density-only deposit of the forward steps; 9..12 in total,
  *                          x at least 2
  *   tile_log2_adjoint[3] : the same for the density + pi deposit of the adjoint steps
+ *                          (9..11 in total)
  *   threads_density,
  *   threads_adjoint      : threads per tile, 256 or 512
  *   tma_columns          : 1 = TMA-staged persistent y/z column passes (meshes 128..1024),

@@ -680,16 +680,18 @@ class Engine : public EngineBase {
     bg4_ = make_bin_geo(lg, tune_.tile_log2_adjoint[2], tune_.tile_log2_adjoint[1], tune_.tile_log2_adjoint[0]);
     use_tma_ = tune_.tma_columns != 0 && tma_supported(nm_);
   }
-  static bool tile_ok(const int* l) {
-    return l[0] >= 0 && l[1] >= 0 && l[2] >= 2 && l[0] + l[1] + l[2] >= 9 && l[0] + l[1] + l[2] <= 11 && l[0] <= 10 &&
-           l[1] <= 10 && l[2] <= 10;
+  // tile extents: x at least 4 cells (vector write-out), 2^9..2^maxl cells (shared memory:
+  // 2^12 cells x 8 B for the density alone, 2^11 x 32 B with the pi sums)
+  static bool tile_ok(const int* l, int maxl) {
+    return l[0] >= 0 && l[1] >= 0 && l[2] >= 2 && l[0] + l[1] + l[2] >= 9 && l[0] + l[1] + l[2] <= maxl &&
+           l[0] <= 10 && l[1] <= 10 && l[2] <= 10;
   }
   int get_tuning(pm_tuning* t) override {
     *t = tune_;
     return PM_OK;
   }
   int set_tuning(const pm_tuning* t) override {
-    if (!tile_ok(t->tile_log2_density) || !tile_ok(t->tile_log2_adjoint)) return PM_ERR_ARG;
+    if (!tile_ok(t->tile_log2_density, 12) || !tile_ok(t->tile_log2_adjoint, 11)) return PM_ERR_ARG;
     if ((t->threads_density != 256 && t->threads_density != 512) ||
         (t->threads_adjoint != 256 && t->threads_adjoint != 512))
       return PM_ERR_ARG;
@@ -747,7 +749,8 @@ class Engine : public EngineBase {
       *ms = t[t.size() / 2];
       return PM_OK;
     };
-    static const int kTiles[][3] = {{3, 4, 4}, {3, 3, 5}, {3, 3, 4}, {2, 4, 5}, {2, 4, 4}, {3, 3, 3}, {2, 3, 5}};
+    static const int kTiles[][3] = {{3, 4, 4}, {3, 3, 5}, {3, 3, 4}, {2, 4, 5}, {2, 4, 4}, {3, 3, 3},
+                                    {2, 3, 5}, {4, 4, 4}, {3, 4, 5}, {3, 5, 4}};
     const int lg = ilog2(nm_);
     const long long sis = 2 * spec_len_cx(nm_);
     pm_tuning best = tune_;
@@ -755,7 +758,7 @@ class Engine : public EngineBase {
     for (int nq = 0; nq < 2; ++nq) {
       for (const auto& tl : kTiles) {
         const int l[3] = {tl[0], tl[1], tl[2]};
-        if (!tile_ok(l)) continue;
+        if (!tile_ok(l, nq ? 11 : 12)) continue;
         for (int nt : {256, 512}) {
           const BinGeo bg = make_bin_geo(lg, l[2], l[1], l[0]);
           double ms = 0;

@@ -22,7 +22,8 @@ def test_set_tuning_rejects_invalid_shapes():
     ctx, *_ = make_ctx(50.0, 32, 16, 2)
     t = ctx.get_tuning()
     assert t["threads_density"] in (256, 512) and t["threads_adjoint"] in (256, 512)
-    for bad in ({"tile_log2_density": [4, 4, 4]},       # 2^12 cells
+    for bad in ({"tile_log2_density": [4, 4, 5]},       # 2^13 cells
+                {"tile_log2_adjoint": [4, 4, 4]},       # 2^12 cells with the pi sums
                 {"tile_log2_adjoint": [2, 2, 2]},       # 2^6 cells
                 {"threads_density": 128},
                 {"tma_columns": 1}):                    # no staged passes below 128^3
@@ -43,7 +44,7 @@ def test_density_bitwise_equal_across_tile_shapes(precision):
     disp[:, ::2] *= 0.05
     d = torch.from_numpy(disp).to("cuda", ctx.dtype).contiguous()
     outs = []
-    for tile, nt in (([3, 4, 4], 256), ([3, 3, 5], 512), ([3, 3, 3], 256), ([2, 4, 5], 512)):
+    for tile, nt in (([3, 4, 4], 256), ([3, 3, 5], 512), ([3, 3, 3], 256), ([2, 4, 5], 512), ([4, 4, 4], 256)):
         ctx.set_tuning({"tile_log2_density": tile, "threads_density": nt})
         out = torch.empty(nm ** 3, device="cuda", dtype=ctx.dtype)
         ctx.op_density(d, out)
