@@ -92,6 +92,69 @@ def growth_factors(a, Om):
     return d1, dd1, gd, gk
 
 
+def _growth2_rhs(lna, y, Om):
+    """Both suppression-factor ODEs of App. A (Eq. 56) as one first-order system.
+
+    y = (G1, G1', G2, G2'), ' = d/d ln a, H'/H = -3/2 Omega_m(a) (flat LCDM):
+      G1'' = -(4 + H'/H) G1' - (3 + H'/H - 3/2 Omega_m(a)) G1
+      G2'' = -(6 + H'/H) G2' - (8 + 2 H'/H - 3/2 Omega_m(a)) G2 + 3/2 Omega_m(a) G1^2
+    """
+    a = np.exp(lna)
+    om = omega_m_of_a(a, Om)
+    dlnh = -1.5 * om
+    g1, dg1, g2, dg2 = y
+    ddg1 = -(4.0 + dlnh) * dg1 - (3.0 + dlnh - 1.5 * om) * g1
+    ddg2 = -(6.0 + dlnh) * dg2 - (8.0 + 2.0 * dlnh - 1.5 * om) * g2 + 1.5 * om * g1 * g1
+    return np.array([dg1, ddg1, dg2, ddg2])
+
+
+def growth_g2(a_targets, Om):
+    """G2 = D2/a^2 and G2' at each a in ``a_targets`` (App. A, Eqs. 55-57, second order).
+
+    The same RK4 scheme as ``growth_g1`` on the joint system (G1, G1', G2, G2') from
+    a_ic = 1e-4 with G1 = 1, G1' = 0, G2 = 3/7, G2' = 0 (Eq. 57).  Pinned: Omega_m = 1
+    gives G2 = 3/7 exactly; for LCDM D2 matches an independent adaptive integration of
+    the D-form ODE (Eq. 52) and the Bouchet et al. (1995) fit D2 ~ 3/7 D1^2
+    Omega_m(a)^(-1/143) (tests/test_oracle_cosmo.py).
+    """
+    a_targets = np.asarray(a_targets, dtype=np.float64)
+    order = np.argsort(a_targets)
+    out_g = np.zeros(a_targets.shape, dtype=np.result_type(Om, np.float64))
+    out_dg = np.zeros_like(out_g)
+    y = np.array([1.0 + 0.0 * Om, 0.0 * Om, 3.0 / 7.0 + 0.0 * Om, 0.0 * Om])
+    lna = np.log(A_IC)
+    for idx in order:
+        target = np.log(a_targets[idx])
+        span = target - lna
+        nsub = int(np.ceil(span / LNA_STEP)) if span > 0 else 0
+        if nsub > 0:
+            h = span / nsub
+            for _ in range(nsub):
+                k1 = _growth2_rhs(lna, y, Om)
+                k2 = _growth2_rhs(lna + 0.5 * h, y + 0.5 * h * k1, Om)
+                k3 = _growth2_rhs(lna + 0.5 * h, y + 0.5 * h * k2, Om)
+                k4 = _growth2_rhs(lna + h, y + h * k3, Om)
+                y = y + (h / 6.0) * (k1 + 2 * k2 + 2 * k3 + k4)
+                lna = lna + h
+            lna = target
+        out_g[idx] = y[2]
+        out_dg[idx] = y[3]
+    return out_g, out_dg
+
+
+def growth_factors2(a, Om):
+    """D2, D2' and G_D2 = a^2 H D2' at scale factors ``a`` (second-order LPT growth).
+
+    D2 = a^2 G2 and D2' = a^2 (2 G2 + G2') (App. A, Eq. 59 for m = 2, read with G_m' in
+    place of the printed G_1'); G_D2 is the factor of s2 in the 2LPT momentum,
+    p = a^2 H (D1' s1 + D2' s2) (Sec. 2.1, Eq. 2)."""
+    a = np.asarray(a, dtype=np.float64)
+    g, dg = growth_g2(a, Om)
+    d2 = a * a * g
+    dd2 = a * a * (2.0 * g + dg)
+    return d2, dd2, a ** 2 * hubble(a, Om) * dd2
+
+
 def time_grid(a0, a1, n_steps):
     """Scale factors a_0..a_n linear in a (Sec. 4, 'time steps linearly spaced in a')."""
     return a0 + (a1 - a0) * np.arange(n_steps + 1, dtype=np.float64) / n_steps

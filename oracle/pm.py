@@ -31,6 +31,7 @@ class PMConfig:
     a1: float = 1.0
     n_steps: int = 10
     deconv: bool = False
+    lpt_order: int = 1  # 1: Zel'dovich initial conditions, 2: 2LPT (Sec. 2.1, Eq. 2)
 
     @property
     def cell(self):
@@ -111,6 +112,115 @@ def za_initial_state(omega, theta, cfg):
     s1 = za_unit_displacement(omega, theta, cfg)
     d1, _, gd, _ = cosmo.growth_factors(np.array([cfg.a0]), theta[2])
     return d1[0] * s1, gd[0] * s1, s1
+
+
+# ------------------------------------------------------- second-order LPT (Sec. 2.1)
+
+_PAIRS = ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))
+
+
+def linear_delta_k(omega, theta, cfg, dlnp=None):
+    """delta1(k) = sqrt(P_lin(k) / l_p^3) DFT[omega](k) on the rfftn layout of the lattice
+    (Eq. 6 with the lattice normalisation of ``za_unit_displacement``), 0 at k = 0.  With
+    ``dlnp`` (a callable k -> d ln P / d theta_j) returns d delta1 / d theta_j =
+    1/2 dlnp delta1 instead."""
+    n, box = cfg.n_ptcl, cfg.box
+    lp = box / n
+    _, k2 = _derivative_multipliers(n, box)
+    k_safe = np.where(k2 > 0, np.sqrt(k2), 1.0)
+    amp = np.sqrt(cosmo.plin(k_safe, theta) / lp ** 3)
+    if dlnp is not None:
+        amp = amp * 0.5 * dlnp(k_safe)
+    amp = np.where(k2 > 0, amp, 0.0)
+    return amp * np.fft.rfftn(np.asarray(omega, dtype=np.float64).reshape(n, n, n))
+
+
+def lpt2_hessian(delta_k, cfg):
+    """The six second derivatives phi_ij = d_i d_j phi^(1) of the first-order potential,
+    laplacian phi^(1) = delta1 (Eq. 4): phi_ij = IDFT[(i k_i)(i k_j)(-1/k^2) delta1(k)] with
+    each i k_c zeroed on the Nyquist plane of axis c.  Returns {(i, j): real field}."""
+    n = cfg.n_ptcl
+    ks, k2 = _derivative_multipliers(n, cfg.box)
+    inv = np.where(k2 > 0, 1.0 / np.where(k2 > 0, k2, 1.0), 0.0)
+    return {(i, j): np.fft.irfftn(ks[i] * ks[j] * inv * delta_k, s=(n, n, n), axes=(0, 1, 2))
+            for i, j in _PAIRS}
+
+
+def lpt2_source(hess, hess_b=None):
+    """The 2LPT source S = sum_{i<j} (phi_ii phi_jj - phi_ij phi_ji) (Eq. 4, second line).
+    With ``hess_b`` returns the symmetric bilinear form whose diagonal is S:
+    1/2 sum_{i<j} (phi_ii phi'_jj + phi'_ii phi_jj - 2 phi_ij phi'_ij)."""
+    hb = hess if hess_b is None else hess_b
+    out = 0.0
+    for i, j in ((0, 1), (0, 2), (1, 2)):
+        out = out + 0.5 * (hess[i, i] * hb[j, j] + hb[i, i] * hess[j, j]) - hess[i, j] * hb[i, j]
+    return out
+
+
+def lpt2_displacement_from_source(src, cfg):
+    """s2 = -grad phi^(2) with laplacian phi^(2) = S (Eqs. 3-4):
+    s2_c = IDFT[i k_c / k^2 DFT[S]], (3, N)."""
+    n = cfg.n_ptcl
+    ks, k2 = _derivative_multipliers(n, cfg.box)
+    sk = np.fft.rfftn(src)
+    inv = np.where(k2 > 0, 1.0 / np.where(k2 > 0, k2, 1.0), 0.0)
+    return np.stack([np.fft.irfftn(1j * ks[c] * inv * sk, s=(n, n, n), axes=(0, 1, 2)).ravel()
+                     for c in range(3)])
+
+
+def lpt2_unit_displacement(omega, theta, cfg, dlnp=None):
+    """Second-order displacement s2 on the lattice for unit growth (Sec. 2.1, Eqs. 2-4).
+    With ``dlnp`` returns d s2 / d theta_j through P_lin: s2 is quadratic in delta1, so
+    the derivative is twice the bilinear source of (delta1, d delta1 / d theta_j)."""
+    dk = linear_delta_k(omega, theta, cfg)
+    hess = lpt2_hessian(dk, cfg)
+    if dlnp is None:
+        src = lpt2_source(hess)
+    else:
+        src = 2.0 * lpt2_source(hess, lpt2_hessian(linear_delta_k(omega, theta, cfg, dlnp=dlnp), cfg))
+    return lpt2_displacement_from_source(src, cfg)
+
+
+def lpt2_transpose(sbar2, omega, theta, cfg):
+    """Vector-Jacobian product of omega -> s2 at ``omega`` with sbar2 (3, N):
+
+      S_bar      = sum_c IDFT[conj(i k_c / k^2) DFT[sbar2_c]]   (transpose of the s2 map)
+      phi_bar_ii = S_bar sum_{j != i} phi_jj,  phi_bar_ij = -2 phi_ij S_bar (i < j)
+      omega_bar  = sum_ij IDFT[amp k_i k_j / k^2 DFT[phi_bar_ij]]  (real even multipliers)
+    with amp = sqrt(P/l_p^3).  Pinned by central differences, exact for the quadratic map."""
+    n, box = cfg.n_ptcl, cfg.box
+    lp = box / n
+    ks, k2 = _derivative_multipliers(n, box)
+    inv = np.where(k2 > 0, 1.0 / np.where(k2 > 0, k2, 1.0), 0.0)
+    hess = lpt2_hessian(linear_delta_k(omega, theta, cfg), cfg)
+    sk = 0.0
+    for c in range(3):
+        sk = sk + np.conj(1j * ks[c] * inv) * np.fft.rfftn(sbar2[c].reshape(n, n, n))
+    sbar = np.fft.irfftn(sk, s=(n, n, n), axes=(0, 1, 2))
+    bars = {}
+    for i in range(3):
+        bars[i, i] = sbar * sum(hess[j, j] for j in range(3) if j != i)
+    for i, j in ((0, 1), (0, 2), (1, 2)):
+        bars[i, j] = -2.0 * hess[i, j] * sbar
+    k_safe = np.where(k2 > 0, np.sqrt(k2), 1.0)
+    amp = np.where(k2 > 0, np.sqrt(cosmo.plin(k_safe, theta) / lp ** 3), 0.0)
+    acc = 0.0
+    for i, j in _PAIRS:
+        acc = acc + amp * ks[i] * ks[j] * inv * np.fft.rfftn(bars[i, j])
+    return np.fft.irfftn(acc, s=(n, n, n), axes=(0, 1, 2)).ravel()
+
+
+def lpt_initial_state(omega, theta, cfg):
+    """Initial state at a0 of order ``cfg.lpt_order`` (Sec. 2.1, Eq. 2):
+    s0 = D1 s1 + D2 s2, p0 = a^2 H (D1' s1 + D2' s2) = G_D s1 + G_D2 s2; the s2 terms are
+    absent at first order (Zel'dovich)."""
+    s0, p0, _ = za_initial_state(omega, theta, cfg)
+    if cfg.lpt_order == 2:
+        s2 = lpt2_unit_displacement(omega, theta, cfg)
+        d2, _, gd2 = cosmo.growth_factors2(np.array([cfg.a0]), theta[2])
+        s0 = s0 + d2[0] * s2
+        p0 = p0 + gd2[0] * s2
+    return s0, p0
 
 
 # ------------------------------------------------------------------------------- CIC
@@ -262,7 +372,7 @@ def forward(omega, theta, cfg, store_every=0, force_fn=None):
     if force_fn is None:
         def force_fn(x, _s):
             return pm_force(x, Om, cfg)[0]
-    s, p, _ = za_initial_state(omega, theta, cfg)
+    s, p = lpt_initial_state(omega, theta, cfg)
     k1, dd, k2 = cosmo.kdk_factors(cosmo.time_grid(cfg.a0, cfg.a1, cfg.n_steps), Om)
     store = {}
     if store_every:
@@ -304,7 +414,7 @@ def adjoint(omega, theta, cfg, fwd, dj_ddelta=None, dj_ds=None, dj_dp=None, ckpt
       K_{i-1/2}^{i-1}: p -= a K1_i;  xi += alpha K1_i;  g += (pi.a) dK1_i + zeta K1_i
     (D(t_c,t_b,t_a) = -D(t_c,t_a,t_b) turns the printed signs into these.)  Finally
     (Eq. 51) dJ/domega = (D1 xi_0 + G_D pi_0) . ds1/domega and the theta terms of the
-    initial conditions.  ``ckpt`` maps step j to a stored (s_j, p_j) that replaces the
+    initial conditions; with 2LPT also (D2 xi_0 + G_D2 pi_0) . ds2/domega and the s2 terms.  ``ckpt`` maps step j to a stored (s_j, p_j) that replaces the
     reverse-integrated state when step j is reached (piecewise resumption, Sec. 3.5).
     Returns dict(grad_omega (n_ptcl^3,), grad_theta (5,), s0, p0 (reverse-integrated)).
     """
@@ -358,6 +468,17 @@ def adjoint(omega, theta, cfg, fwd, dj_ddelta=None, dj_ds=None, dj_dp=None, ckpt
         grad_theta[j] = float(np.sum(sbar * za_unit_displacement(omega, theta, cfg, dlnp=dlnp)))
     grad_theta[2] += g_om + float(np.sum(xi * s1)) * dd1 + float(np.sum(pi * s1)) * dgd
     grad_omega = za_transpose(sbar, theta, cfg)
+    if cfg.lpt_order == 2:
+        # 2LPT: x0 += D2(a0) s2, p0 += G_D2(a0) s2 with s2 quadratic in delta1
+        d2, _, gd2 = cosmo.growth_factors2(np.array([cfg.a0]), Om)
+        dd2, dgd2 = (cosmo.complex_step(lambda th: cosmo.growth_factors2(np.array([cfg.a0]), th[2])[q], theta, 2)[0]
+                     for q in (0, 2))
+        s2 = lpt2_unit_displacement(omega, theta, cfg)
+        sbar2 = d2[0] * xi + gd2[0] * pi
+        for j, dlnp in enumerate(_dlnp_funcs(theta)):
+            grad_theta[j] += float(np.sum(sbar2 * lpt2_unit_displacement(omega, theta, cfg, dlnp=dlnp)))
+        grad_theta[2] += float(np.sum(xi * s2)) * dd2 + float(np.sum(pi * s2)) * dgd2
+        grad_omega = grad_omega + lpt2_transpose(sbar2, omega, theta, cfg)
     return dict(grad_omega=grad_omega, grad_theta=grad_theta, s0=s, p0=p, xi0=xi, pi0=pi)
 
 

@@ -102,3 +102,51 @@ def test_plin_parameter_dependence():
     assert np.allclose(cosmo.plin(k, th) / p0, (k / kp) ** 0.1, rtol=1e-12)
     d = cosmo.complex_step(lambda t: np.log(cosmo.plin(k, t)), THETA, 0)
     assert np.allclose(d, 1 / THETA[0], rtol=1e-12)
+
+
+# ------------------------------------------------------------ second-order growth (2LPT)
+
+def test_second_order_growth_matter_dominated_is_exact():
+    """App. A: with Omega_m = 1 the second-order growing mode is D2 = 3/7 a^2 exactly
+    (G2 = 3/7 solves Eq. 56 with G1 = 1); D2' = 2 D2 then."""
+    a = np.array([1e-3, 1 / 64, 0.3, 1.0])
+    g, dg = cosmo.growth_g2(a, 1.0)
+    assert np.allclose(g, 3.0 / 7.0, rtol=0, atol=1e-13)
+    assert np.allclose(dg, 0.0, rtol=0, atol=1e-13)
+    d2, dd2, gd2 = cosmo.growth_factors2(a, 1.0)
+    assert np.allclose(dd2, 2.0 * d2, rtol=1e-13)
+    assert np.allclose(gd2, a ** 2 * a ** -1.5 * dd2, rtol=1e-13)
+
+
+@pytest.mark.parametrize("Om", [0.25, 0.31, 0.35])
+def test_second_order_growth_matches_d_form_ode(Om):
+    """The G-form integration (Eq. 56) against an independent adaptive integration of the
+    D-form ODEs (Eq. 52): D'' + (2 + H'/H) D' - 3/2 Om(a) D = {0, 3/2 Om(a) D1^2}, from the
+    growing-mode values of Eq. 54 at a_ic."""
+    def rhs(lna, y):
+        a = np.exp(lna)
+        om = cosmo.omega_m_of_a(a, Om)
+        dlnh = -1.5 * om
+        d1, dd1, d2, dd2 = y
+        return [dd1, -(2 + dlnh) * dd1 + 1.5 * om * d1,
+                dd2, -(2 + dlnh) * dd2 + 1.5 * om * d2 + 1.5 * om * d1 * d1]
+    a = np.array([1 / 64, 0.1, 0.5, 1.0])
+    ai = cosmo.A_IC
+    sol = integrate.solve_ivp(rhs, (np.log(ai), 0.0), [ai, ai, 3 / 7 * ai ** 2, 6 / 7 * ai ** 2],
+                              method="DOP853", t_eval=np.log(a), rtol=1e-12, atol=1e-30)
+    d2, dd2, _ = cosmo.growth_factors2(a, Om)
+    assert np.allclose(d2, sol.y[2], rtol=1e-8, atol=0)
+    assert np.allclose(dd2, sol.y[3], rtol=1e-8, atol=0)
+    d1 = cosmo.growth_factors(a, Om)[0]
+    assert np.allclose(d1, sol.y[0], rtol=1e-8, atol=0)
+
+
+def test_second_order_growth_matches_bouchet_fit():
+    """Flat LCDM: D2 = 3/7 D1^2 Omega_m(a)^(-1/143) to better than 1e-3 (Bouchet et al.
+    1995 fit), so the sign and normalisation of D2 in Eq. 2 are the standard 2LPT ones."""
+    a = np.array([1 / 64, 0.2, 0.5, 1.0])
+    for Om in (0.25, 0.31):
+        d1 = cosmo.growth_factors(a, Om)[0]
+        d2 = cosmo.growth_factors2(a, Om)[0]
+        fit = 3.0 / 7.0 * d1 ** 2 * cosmo.omega_m_of_a(a, Om) ** (-1.0 / 143.0)
+        assert np.all(np.abs(d2 / fit - 1) < 1e-3)

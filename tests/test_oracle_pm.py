@@ -283,6 +283,139 @@ def test_reverse_time_adjoint_equals_stored_trajectory(fd_case):
     assert np.allclose(adj["grad_theta"], adj_st["grad_theta"], rtol=1e-9)
 
 
+# ------------------------------------------------------------------- 2LPT (Sec. 2.1)
+
+def _lpt2_of_field(delta1, cfg):
+    return pm.lpt2_displacement_from_source(pm.lpt2_source(pm.lpt2_hessian(np.fft.rfftn(delta1), cfg)), cfg)
+
+
+def test_lpt2_two_perpendicular_waves_closed_form():
+    """delta1 = A cos(k q0) + B cos(k q1): phi_00 = A cos(k q0), phi_11 = B cos(k q1), so
+    S = AB cos(k q0) cos(k q1) (Eq. 4), phi2 = -S / (2 k^2) and s2 = -grad phi2 gives
+    s2_0 = -AB sin(k q0) cos(k q1) / (2k), s2_1 = -AB cos(k q0) sin(k q1) / (2k), s2_2 = 0."""
+    n, box = 16, 64.0
+    cfg = pm.PMConfig(box=box, n_mesh=32, n_ptcl=n)
+    q = np.indices((n, n, n)).astype(np.float64) * (box / n)
+    k, A, B = 2 * np.pi / box * 2, 0.7, -1.3
+    s2 = _lpt2_of_field(A * np.cos(k * q[0]) + B * np.cos(k * q[1]), cfg)
+    want = np.stack([-A * B * np.sin(k * q[0]) * np.cos(k * q[1]) / (2 * k),
+                     -A * B * np.cos(k * q[0]) * np.sin(k * q[1]) / (2 * k), 0 * q[2]]).reshape(3, -1)
+    assert np.max(np.abs(s2 - want)) < 1e-13 * np.max(np.abs(want))
+
+
+def test_lpt2_diagonal_wave_uses_the_mixed_derivatives():
+    """delta1 = A cos(k (q0 + q1)) + B cos(k q2): phi_00 = phi_11 = phi_01 = A/2 cos u, so
+    the mixed term cancels the phi_00 phi_11 product and S = AB cos u cos v (u = k(q0+q1),
+    v = k q2); with |k|^2 = 3k^2, s2 = grad S / (3k^2).  A dropped or mis-signed phi_01^2
+    term fails here."""
+    n, box = 16, 64.0
+    cfg = pm.PMConfig(box=box, n_mesh=32, n_ptcl=n)
+    q = np.indices((n, n, n)).astype(np.float64) * (box / n)
+    k, A, B = 2 * np.pi / box, 0.9, 0.4
+    u, v = k * (q[0] + q[1]), k * q[2]
+    s2 = _lpt2_of_field(A * np.cos(u) + B * np.cos(v), cfg)
+    sx = -A * B * np.sin(u) * np.cos(v) / (3 * k)
+    want = np.stack([sx, sx, -A * B * np.cos(u) * np.sin(v) / (3 * k)]).reshape(3, -1)
+    assert np.max(np.abs(s2 - want)) < 1e-13 * np.max(np.abs(want))
+
+
+def test_lpt2_vanishes_for_one_dimensional_fields():
+    """A field that varies along one axis only has phi_ij = 0 unless i = j = that axis, so
+    S = 0 and 2LPT adds nothing (Zel'dovich is exact in one dimension)."""
+    n = 16
+    cfg = pm.PMConfig(box=50.0, n_mesh=32, n_ptcl=n)
+    line = np.random.default_rng(4).normal(size=n)
+    s2 = _lpt2_of_field(np.broadcast_to(line[None, :, None], (n, n, n)).copy(), cfg)
+    assert np.max(np.abs(s2)) < 1e-15 * n ** 3
+
+
+def test_lpt2_transpose_equals_exact_central_difference():
+    """s2 is quadratic in omega, so the central difference along v is exact up to
+    rounding: <sbar, (s2(w + h v) - s2(w - h v)) / 2h> = <lpt2_transpose(sbar), v>."""
+    cfg = pm.PMConfig(box=64.0, n_mesh=32, n_ptcl=16)
+    rng = np.random.default_rng(3)
+    w = inputs.white_noise(16, 1).astype(np.float64)
+    v = rng.normal(size=w.shape)
+    sb = rng.normal(size=(3, 16 ** 3))
+    h = 1e-3
+    fd = np.sum(sb * (pm.lpt2_unit_displacement(w + h * v, THETA, cfg)
+                      - pm.lpt2_unit_displacement(w - h * v, THETA, cfg))) / (2 * h)
+    ad = np.sum(pm.lpt2_transpose(sb, w, THETA, cfg) * v.ravel())
+    assert abs(fd - ad) < 1e-11 * abs(fd)
+
+
+@pytest.mark.parametrize("j", range(5))
+def test_lpt2_theta_derivative_vs_central_fd(j):
+    """d s2 / d theta_j through P_lin (twice the bilinear source) against central FD."""
+    cfg = pm.PMConfig(box=64.0, n_mesh=32, n_ptcl=16)
+    w = inputs.white_noise(16, 5).astype(np.float64)
+    an = pm.lpt2_unit_displacement(w, THETA, cfg, dlnp=pm._dlnp_funcs(THETA)[j])
+    h = 1e-6 * abs(THETA[j])
+    tp, tm = list(THETA), list(THETA)
+    tp[j] += h
+    tm[j] -= h
+    fd = (pm.lpt2_unit_displacement(w, tp, cfg) - pm.lpt2_unit_displacement(w, tm, cfg)) / (2 * h)
+    assert np.linalg.norm(an - fd) < 1e-8 * np.linalg.norm(fd)
+
+
+FD_CFG2 = pm.PMConfig(box=24.0, n_mesh=16, n_ptcl=8, n_steps=4, lpt_order=2)
+
+
+def _loss2(om, th, target):
+    return pm.mse_loss(pm.forward(om, th, FD_CFG2)["delta"], target)[0]
+
+
+@pytest.fixture(scope="module")
+def fd_case2():
+    om = inputs.white_noise(8, 1).astype(np.float64)
+    target = pm.forward(inputs.white_noise(8, 2).astype(np.float64), THETA, FD_CFG2)["delta"]
+    loss, adj, _ = pm.loss_and_gradient(om, THETA, target, FD_CFG2)
+    return om, target, loss, adj
+
+
+def test_lpt2_changes_the_initial_state_by_the_second_order_term():
+    om = inputs.white_noise(8, 1).astype(np.float64)
+    s1, p1 = pm.lpt_initial_state(om, THETA, pm.PMConfig(box=24.0, n_mesh=16, n_ptcl=8))
+    s2, p2 = pm.lpt_initial_state(om, THETA, FD_CFG2)
+    d2, _, gd2 = cosmo.growth_factors2(np.array([FD_CFG2.a0]), THETA[2])
+    u = pm.lpt2_unit_displacement(om, THETA, FD_CFG2)
+    assert np.allclose(s2 - s1, d2[0] * u, rtol=0, atol=1e-14 * np.abs(s1).max())
+    assert np.allclose(p2 - p1, gd2[0] * u, rtol=0, atol=1e-14 * np.abs(p1).max())
+
+
+def test_lpt2_adjoint_gradient_omega_vs_central_fd(fd_case2):
+    """dJ/domega with 2LPT initial conditions (the s2 VJP added to Eq. 51) against FD."""
+    om, target, _, adj = fd_case2
+    rng = np.random.default_rng(9)
+    v = rng.normal(size=om.shape)
+    h = 1e-6
+    fd = (_loss2(om + h * v, THETA, target) - _loss2(om - h * v, THETA, target)) / (2 * h)
+    assert abs(fd - np.sum(adj["grad_omega"] * v.ravel())) <= 1e-6 * abs(fd)
+
+
+@pytest.mark.parametrize("j", range(5))
+def test_lpt2_adjoint_gradient_theta_vs_central_fd(fd_case2, j):
+    """dJ/dtheta_j with 2LPT initial conditions (P_lin through s2, D2 and G_D2 through
+    Omega_m) against central FD."""
+    om, target, _, adj = fd_case2
+    h = 1e-6 * abs(THETA[j])
+    tp, tm = list(THETA), list(THETA)
+    tp[j] += h
+    tm[j] -= h
+    fd = (_loss2(om, tp, target) - _loss2(om, tm, target)) / (2 * h)
+    assert abs(fd - adj["grad_theta"][j]) <= 1e-6 * abs(fd) + 1e-12
+
+
+def test_lpt2_reversibility_fp64():
+    """Reverse integration recovers the 2LPT initial state to 1e-10 relative."""
+    cfg = pm.PMConfig(box=64.0, n_mesh=16, n_ptcl=8, n_steps=10, lpt_order=2)
+    om = inputs.white_noise(8, 13).astype(np.float64)
+    adj = pm.adjoint(om, THETA, cfg, pm.forward(om, THETA, cfg))
+    s0, p0 = pm.lpt_initial_state(om, THETA, cfg)
+    assert np.sqrt(np.mean((adj["s0"] - s0) ** 2)) < 1e-10 * np.std(s0)
+    assert np.sqrt(np.mean((adj["p0"] - p0) ** 2)) < 1e-10 * np.std(p0)
+
+
 def test_white_noise_power_recovers_plin():
     """Eq. 5-6: <|delta1(k)|^2> l_p^6 / V = P_lin(k), averaged over seeds and shells."""
     cfg = pm.PMConfig(box=200.0, n_mesh=32, n_ptcl=16)
