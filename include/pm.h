@@ -3,8 +3,8 @@
  * hand-written CUDA for sm_103a (GB300).  C ABI.
  *
  * Method: Li et al., "Differentiable Cosmological Simulation with the Adjoint Method"
- * (arXiv:2211.09815).  Forward model: Zel'dovich initial conditions from white noise
- * (Sec. 2.1, Eqs. 2-7), PM gravity by CIC scatter, FFT Poisson solve with the -ik
+ * (arXiv:2211.09815).  Forward model: Zel'dovich or 2LPT initial conditions from white
+ * noise (Sec. 2.1, Eqs. 2-7; App. A), PM gravity by CIC scatter, FFT Poisson solve with the -ik
  * gradient and CIC gather (Sec. 2.2, Eqs. 10-11), FastPM kick-drift-kick leapfrog
  * (Sec. 2.3, Eqs. 13-16).  Gradient: the discrete adjoint integrated backward in time
  * jointly with the reverse leapfrog (Sec. 3.6, Eqs. 49-51), with optional piecewise
@@ -61,6 +61,10 @@ typedef struct {
                        states (s_j, p_j) stored every k steps (Sec. 3.5) */
   int deconv;       /* 1: divide the Green's function by the CIC window prod sinc^4 */
   int batch;        /* independent instances B >= 1 (own theta and omega each) */
+  int lpt_order;    /* initial conditions (Sec. 2.1, Eq. 2): 0 or 1 = Zel'dovich (first
+                       order), 2 = 2LPT, s = D1 s1 + D2 s2 with the second-order growth of
+                       App. A (Eqs. 52-57); the adjoint then also back-propagates through
+                       s2 (10 more lattice FFTs forward, 16 in the adjoint, 3 N more values) */
 } pm_config;
 
 /*
@@ -78,7 +82,8 @@ typedef struct {
 int pm_init(pm_ctx** out, const pm_config* cfg, const double* theta, const void* omega, void* stream);
 
 /*
- * Forward model (Sec. 2.1-2.3): Zel'dovich ICs at a0, F_0, then n KDK steps (Eq. 16).
+ * Forward model (Sec. 2.1-2.3): Zel'dovich or 2LPT ICs at a0 (lpt_order), F_0, then n KDK
+ * steps (Eq. 16).
  *   disp_out : optional, [batch][3][n_ptcl^3], final displacement s_n
  *   mom_out  : optional, [batch][3][n_ptcl^3], final momentum p_n
  *   dens_out : optional, [batch][n_mesh^3], final overdensity delta_n (CIC, Eq. 10)
@@ -259,6 +264,11 @@ int pm_op_fft(pm_ctx* ctx, int dir, const void* in, void* out);
 /* Zel'dovich displacement for unit growth s1 (Sec. 2.1, Eqs. 3-6) of the context's omega.
  * s1_out: [batch][3][n_ptcl^3]. */
 int pm_op_za(pm_ctx* ctx, void* s1_out);
+
+/* Initial state at a0 of the context's lpt_order (Sec. 2.1, Eq. 2): s0 = D1 s1 (+ D2 s2),
+ * p0 = a^2 H (D1' s1 (+ D2' s2)).  s0_out, p0_out: optional (null: not written),
+ * [batch][3][n_ptcl^3].  Clears the forward state like the other operators. */
+int pm_op_ic(pm_ctx* ctx, void* s0_out, void* p0_out);
 
 /* ------------------------------------------------------------------------------------
  * Allocation-free entry point.  The paper has no counterpart: this is a service for

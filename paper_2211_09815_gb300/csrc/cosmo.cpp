@@ -84,6 +84,45 @@ static void factors(const std::vector<double>& a, R om, std::vector<R>& d1, std:
   }
 }
 
+// y = (G1, G1', G2, G2'): both suppression-factor ODEs of App. A (Eq. 56) with
+// G2'' = -(6 + H'/H) G2' - (8 + 2 H'/H - 3/2 Om(a)) G2 + 3/2 Om(a) G1^2.
+template <class R> static void rhs2(double lna, const R y[4], R om, R out[4]) {
+  rhs(lna, y, om, out);
+  const double a = std::exp(lna);
+  const R h2 = om / (a * a * a) + (1.0 - om);
+  const R oma = om / (a * a * a) / h2;
+  const R dlnh = -1.5 * oma;
+  out[2] = y[3];
+  out[3] = -(6.0 + dlnh) * y[3] - (8.0 + 2.0 * dlnh - 1.5 * oma) * y[2] + 1.5 * oma * y[0] * y[0];
+}
+
+// Second-order growth at one scale factor a: D2 = a^2 G2 and G_D2 = a^2 H D2' with
+// D2' = a^2 (2 G2 + G2') (App. A, Eq. 59 for m = 2), by RK4 in ln a from a_ic with
+// G1 = 1, G1' = 0, G2 = 3/7, G2' = 0 (Eq. 57).
+template <class R> static void factors2(double a, R om, R& d2, R& gd2) {
+  R y[4] = {R(1.0), R(0.0), R(3.0 / 7.0), R(0.0)};
+  double lna = std::log(kAic);
+  const double span = std::log(a) - lna;
+  if (span > 0) {
+    const int nsub = (int)std::ceil(span / kLnaStep);
+    const double h = span / nsub;
+    for (int s = 0; s < nsub; ++s) {
+      R k1[4], k2[4], k3[4], k4[4], t[4];
+      rhs2(lna, y, om, k1);
+      for (int c = 0; c < 4; ++c) t[c] = y[c] + 0.5 * h * k1[c];
+      rhs2(lna + 0.5 * h, t, om, k2);
+      for (int c = 0; c < 4; ++c) t[c] = y[c] + 0.5 * h * k2[c];
+      rhs2(lna + 0.5 * h, t, om, k3);
+      for (int c = 0; c < 4; ++c) t[c] = y[c] + h * k3[c];
+      rhs2(lna + h, t, om, k4);
+      for (int c = 0; c < 4; ++c) y[c] += (h / 6.0) * (k1[c] + 2.0 * k2[c] + 2.0 * k3[c] + k4[c]);
+      lna += h;
+    }
+  }
+  d2 = a * a * y[2];
+  gd2 = a * a * hubble(a, om) * (a * a * (2.0 * y[2] + y[3]));
+}
+
 // Eisenstein & Hu 1998 no-wiggle T(k), k in h/Mpc: their Eqs. 26 (sound horizon),
 // 28 (q), 29 (T0), 30 (Gamma_eff), 31 (alpha_Gamma).
 template <class R> static R transfer(double k, R om, R ob, R h) {
@@ -158,6 +197,11 @@ void time_coefficients(double a0, double a1, int n, double om, TimeCoef& out) {
   out.gd_a0 = gd[0];
   out.dd1_a0 = std::imag(cd1[0]) / kEps;
   out.dgd_a0 = std::imag(cgd[0]) / kEps;
+  cd cd2, cgd2;
+  factors2(a0, om, out.d2_a0, out.gd2_a0);
+  factors2(a0, cd(om, kEps), cd2, cgd2);
+  out.dd2_a0 = std::imag(cd2) / kEps;
+  out.dgd2_a0 = std::imag(cgd2) / kEps;
 }
 
 }  // namespace cosmo

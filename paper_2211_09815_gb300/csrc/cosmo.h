@@ -9,6 +9,7 @@ struct TimeCoef {
   // per step i = 1..n (index i-1): FastPM factors of Sec. 2.3, Eq. 15 and d/dOmega_m
   std::vector<double> k1, dd, k2, dk1, ddd, dk2;
   double d1_a0, gd_a0, dd1_a0, dgd_a0;  // D1, G_D at a0 and d/dOmega_m
+  double d2_a0, gd2_a0, dd2_a0, dgd2_a0; // D2, G_D2 = a^2 H D2' at a0 and d/dOmega_m (2LPT)
 };
 
 // K1_i, D_i, K2_i for a linear-in-a grid a0..a1 with n steps.

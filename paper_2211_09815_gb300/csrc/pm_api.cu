@@ -37,6 +37,7 @@ static int validate(const pm_config* c, const double* theta) {
   if (!pow2(c->n_mesh) || !pow2(c->n_ptcl) || c->n_ptcl < 4 || c->n_mesh < 8 || c->n_mesh > 1024) return PM_ERR_ARG;
   if (c->n_mesh % c->n_ptcl != 0) return PM_ERR_ARG;
   if (c->n_steps < 1 || c->batch < 1 || c->ckpt_every < 0) return PM_ERR_ARG;
+  if (c->lpt_order < 0 || c->lpt_order > 2) return PM_ERR_ARG;
   if (!(c->a0 > 0) || !(c->a1 > c->a0) || !std::isfinite(c->a1)) return PM_ERR_ARG;
   if (c->precision != PM_F32 && c->precision != PM_F64) return PM_ERR_ARG;
   if ((long long)c->batch * c->n_mesh * c->n_mesh * (c->n_mesh / 2) >= (1LL << 31)) return PM_ERR_ARG;
@@ -193,6 +194,11 @@ int pm_op_fft(pm_ctx* ctx, int dir, const void* in, void* out) {
 int pm_op_za(pm_ctx* ctx, void* s1_out) {
   if (!ctx || !s1_out) return PM_ERR_ARG;
   return ctx->eng->op_za(s1_out);
+}
+
+int pm_op_ic(pm_ctx* ctx, void* s0_out, void* p0_out) {
+  if (!ctx) return PM_ERR_ARG;
+  return ctx->eng->op_ic(s0_out, p0_out);
 }
 
 }  // extern "C"

@@ -15,6 +15,7 @@ struct EngineBase {
   virtual int op_force(const void* disp, const void* pi, void* acc, void* alpha) = 0;
   virtual int op_fft(int dir, const void* in, void* out) = 0;
   virtual int op_za(void* s1) = 0;
+  virtual int op_ic(void* s0, void* p0) = 0;
   virtual long long scratch_bytes() const = 0;
   virtual int profile(int enable) = 0;
   virtual int profile_read(double* ms, long long* launches) = 0;

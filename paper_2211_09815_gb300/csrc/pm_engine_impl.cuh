@@ -150,6 +150,8 @@ class Engine : public EngineBase {
     PMGB_RET(alloc(&xi_, pv));
     PMGB_RET(alloc(&pi_, pv));
     PMGB_RET(alloc(&s1_, pv));
+    lpt2_ = cfg->lpt_order == 2;
+    if (lpt2_) PMGB_RET(alloc(&s2_, pv));
     PMGB_RET(alloc(&omega_, (long long)B_ * N_));
     // particle bins of the mesh-tile assignment (bin_kernels.cuh)
     PMGB_RET(bin_setup());
@@ -183,7 +185,7 @@ class Engine : public EngineBase {
   // ------------------------------------------------------------------ forward
   int forward(void* disp, void* mom, void* dens) override {
     counted_ = false;
-    prof_.begin(st_, P_OTHER, 12);
+    prof_.begin(st_, P_OTHER, lpt2_ ? 12 + 26 : 12);
     PMGB_RET(initial_conditions());
     prof_.end(st_, P_OTHER);
     for (int j = 0; j <= n_; ++j) {
@@ -273,7 +275,7 @@ class Engine : public EngineBase {
       PMGB_CK(cudaGetLastError());
     }
     // per-step sums: part_[(2j+q)][b][G] -> steps_[(2j+q)][b]
-    prof_.begin(st_, P_OTHER, 15);
+    prof_.begin(st_, P_OTHER, lpt2_ ? 16 + 39 : 16);
     k_sum_partials<<<2 * (n_ + 1) * B_, 256, 0, st_>>>(part_, G_, steps_, 1.0);
     PMGB_CK(cudaGetLastError());
     PMGB_RET(ic_adjoint(djdw));
@@ -288,6 +290,10 @@ class Engine : public EngineBase {
     in.dlp = scal_ + 4 * B_;
     in.dd1 = dd1_;
     in.dgd = dgd_;
+    in.xs2 = lpt2_ ? scal_ + 9 * B_ : nullptr;
+    in.ps2 = lpt2_ ? scal_ + 10 * B_ : nullptr;
+    in.dd2 = dd2_;
+    in.dgd2 = dgd2_;
     in.nstep1 = n_ + 1;
     in.batch = B_;
     in.step_stride = 2 * B_;
@@ -458,6 +464,14 @@ class Engine : public EngineBase {
     return PM_OK;
   }
 
+  int op_ic(void* s0, void* p0) override {
+    have_fwd_ = false;
+    PMGB_RET(initial_conditions());
+    if (s0) PMGB_CK(cudaMemcpyAsync(s0, s_, sizeof(T) * B_ * 3 * N_, cudaMemcpyDeviceToDevice, st_));
+    if (p0) PMGB_CK(cudaMemcpyAsync(p0, p_, sizeof(T) * B_ * 3 * N_, cudaMemcpyDeviceToDevice, st_));
+    return PM_OK;
+  }
+
  private:
   template <typename U> int alloc(U** p, long long count) {
     void* q = nullptr;
@@ -481,8 +495,8 @@ class Engine : public EngineBase {
   int tables(const double* theta) {
     const int n1 = n_ + 1;
     std::vector<T> fkA(B_ * n1), fkB(B_ * n1), fdr(B_ * n1), rkA(B_ * n1), rkB(B_ * n1), rdr(B_ * n1);
-    std::vector<double> wpa(n1 * B_), wxp(n1 * B_), dd1(B_), dgd(B_);
-    std::vector<T> d1(B_), gd(B_), gcoef(B_);
+    std::vector<double> wpa(n1 * B_), wxp(n1 * B_), dd1(B_), dgd(B_), dd2(B_), dgd2(B_);
+    std::vector<T> d1(B_), gd(B_), d2(B_), gd2(B_), gcoef(B_);
     const int maxn2 = 3 * (np_ / 2) * (np_ / 2);
     const double kfp = 2.0 * M_PI / cfg_.box;
     const double lp = cfg_.box / np_;
@@ -509,6 +523,10 @@ class Engine : public EngineBase {
       }
       d1[b] = (T)tc.d1_a0;
       gd[b] = (T)tc.gd_a0;
+      d2[b] = (T)tc.d2_a0;
+      gd2[b] = (T)tc.gd2_a0;
+      dd2[b] = tc.dd2_a0;
+      dgd2[b] = tc.dgd2_a0;
       dd1[b] = tc.dd1_a0;
       dgd[b] = tc.dgd_a0;
       // H_c = -i k_c G / M with G = -3/2 Om / k^2: per mode f_c * coef / n^2 * (-i)
@@ -537,6 +555,11 @@ class Engine : public EngineBase {
     PMGB_RET(upload(&dgd_, dgd));
     PMGB_RET(upload(&d1_, d1));
     PMGB_RET(upload(&gd_, gd));
+    PMGB_RET(upload(&d2_, d2));
+    PMGB_RET(upload(&gd2_, gd2));
+    PMGB_RET(upload(&dd2_, dd2));
+    PMGB_RET(upload(&dgd2_, dgd2));
+    unit_ = (T)(1.0 / (double)N_);
     PMGB_RET(upload(&gcoef_, gcoef));
     PMGB_RET(upload(&amp_, amp));
     PMGB_RET(upload(&hdl_, hdl));
@@ -981,12 +1004,86 @@ class Engine : public EngineBase {
     // the lattice transforms use spec_[0..3] with the lattice instance stride
     PMGB_RET(lattice_r2c(omega_, N_, spec_[0]));
     k_za_mul<T><<<dim3(256, B_), 256, 0, st_>>>(spec_[0], spec_[1], spec_[2], spec_[3], np_, amp_, maxn2_,
-                                                inv_kfp_, lis);
+                                                inv_kfp_, lis, (T)0);
     PMGB_CK(cudaGetLastError());
     C* bufs[3] = {spec_[1], spec_[2], spec_[3]};
     PMGB_RET(lattice_c2r(bufs, 3));
     k_ic_state<T><<<dim3(256, B_), 256, 0, st_>>>(rmesh(1), rmesh(2), rmesh(3), 2 * lis, N_, d1_, gd_, s1_, s_, p_);
     PMGB_CK(cudaGetLastError());
+    if (lpt2_) PMGB_RET(lpt2_state());
+    return PM_OK;
+  }
+
+  // 2LPT (Sec. 2.1, Eqs. 2-4) from Omega^ in spec_[0]: the Hessian of the first-order
+  // potential in two groups of three (diagonal, mixed) through spec_[1..3], the source S
+  // accumulated in the real view of spec_[4], s2_c = IDFT[i k_c / k^2 S^] / n^3 through
+  // spec_[1..3], then s += D2 s2, p += G_D2 s2.  26 launches.
+  int lpt2_state() {
+    const long long lis = spec_len_cx(np_);
+    C* h[3] = {spec_[1], spec_[2], spec_[3]};
+    for (int g = 0; g < 2; ++g) {
+      k_lpt_hess<T><<<dim3(256, B_), 256, 0, st_>>>(spec_[0], h[0], h[1], h[2], np_, amp_, maxn2_, lis, g);
+      PMGB_CK(cudaGetLastError());
+      PMGB_RET(lattice_c2r(h, 3));
+      k_lpt_source<T><<<dim3(256, B_), 256, 0, st_>>>(rmesh(1), rmesh(2), rmesh(3), 2 * lis, N_, rmesh(4), 2 * lis,
+                                                      g);
+      PMGB_CK(cudaGetLastError());
+    }
+    PMGB_RET(lattice_r2c(rmesh(4), 2 * lis, spec_[4]));
+    k_za_mul<T><<<dim3(256, B_), 256, 0, st_>>>(spec_[4], h[0], h[1], h[2], np_, nullptr, maxn2_, inv_kfp_, lis,
+                                                unit_);
+    PMGB_CK(cudaGetLastError());
+    PMGB_RET(lattice_c2r(h, 3));
+    k_ic_state2<T><<<dim3(256, B_), 256, 0, st_>>>(rmesh(1), rmesh(2), rmesh(3), 2 * lis, N_, d2_, gd2_, s2_, s_,
+                                                   p_);
+    PMGB_CK(cudaGetLastError());
+    return PM_OK;
+  }
+
+  // Back-propagation through s2 (the transpose of lpt2_state): sbar2 = D2 xi_0 + G_D2 pi_0
+  // and the partials xi_0.s2, pi_0.s2; S_bar = sum_c IDFT[conj(i k_c / k^2) DFT sbar2_c] / n^3
+  // (real view of spec_[4]); per Hessian group phi_bar = dS/dphi S_bar, and
+  // sum_ij k_i k_j / k^2 amp DFT phi_bar_ij accumulated in spec_[5], where the Zel'dovich
+  // transpose adds its part.  Leaves Omega^ in spec_[0].  39 launches.
+  int lpt2_adjoint() {
+    const long long lis = spec_len_cx(np_);
+    k_ic_adj_prep<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(xi_, pi_, s2_, N_, d2_, gd2_, rmesh(1), rmesh(2),
+                                                             rmesh(3), 2 * lis, part_, part_ + (long long)B_ * G_);
+    PMGB_CK(cudaGetLastError());
+    k_sum_partials<<<2 * B_, 256, 0, st_>>>(part_, G_, scal_ + 9 * B_, 1.0);
+    PMGB_CK(cudaGetLastError());
+    RowJob<T> job{};
+    for (int c = 0; c < 3; ++c) job.b[c] = RowBuf<T>{rmesh(1 + c), 2 * lis, spec_[1 + c]};
+    job.b[3] = RowBuf<T>{omega_, N_, spec_[0]};
+    PMGB_RET(fft_x_r2c<T>(np_, job, 4, B_ * np_ * np_, tw_, st_));
+    PMGB_CK(cudaGetLastError());
+    C* bufs[4] = {spec_[1], spec_[2], spec_[3], spec_[0]};
+    PMGB_RET(cols(np_, -1, false, bufs, 4));
+    PMGB_RET(cols(np_, -1, true, bufs, 4));
+    k_za_adj_mul<T><<<dim3(Gz_, B_), kPtclThreads, 0, st_>>>(spec_[1], spec_[2], spec_[3], nullptr, nullptr, spec_[4],
+                                                             np_, nullptr, unit_, nullptr, maxn2_, inv_kfp_, lis,
+                                                             nullptr);
+    PMGB_CK(cudaGetLastError());
+    C* sb[1] = {spec_[4]};
+    PMGB_RET(lattice_c2r(sb, 1));
+    C* h[3] = {spec_[1], spec_[2], spec_[3]};
+    for (int g = 0; g < 2; ++g) {
+      k_lpt_hess<T><<<dim3(256, B_), 256, 0, st_>>>(spec_[0], h[0], h[1], h[2], np_, amp_, maxn2_, lis, g);
+      PMGB_CK(cudaGetLastError());
+      PMGB_RET(lattice_c2r(h, 3));
+      k_lpt_source_adj<T><<<dim3(256, B_), 256, 0, st_>>>(rmesh(1), rmesh(2), rmesh(3), 2 * lis, N_, rmesh(4),
+                                                          2 * lis, g);
+      PMGB_CK(cudaGetLastError());
+      RowJob<T> jh{};
+      for (int c = 0; c < 3; ++c) jh.b[c] = RowBuf<T>{rmesh(1 + c), 2 * lis, spec_[1 + c]};
+      PMGB_RET(fft_x_r2c<T>(np_, jh, 3, B_ * np_ * np_, tw_, st_));
+      PMGB_CK(cudaGetLastError());
+      PMGB_RET(cols(np_, -1, false, h, 3));
+      PMGB_RET(cols(np_, -1, true, h, 3));
+      k_lpt_hess_adj<T><<<dim3(256, B_), 256, 0, st_>>>(spec_[1], spec_[2], spec_[3], spec_[5], np_, amp_, maxn2_,
+                                                        lis, g);
+      PMGB_CK(cudaGetLastError());
+    }
     return PM_OK;
   }
   int lattice_r2c(const T* in, long long in_is, C* out) {
@@ -1012,6 +1109,7 @@ class Engine : public EngineBase {
   // sum_c B_c^T sbar_c, and the theta terms of P_lin, D1(a0), G_D(a0).
   int ic_adjoint(void* djdw) {
     const long long lis = spec_len_cx(np_);
+    if (lpt2_) PMGB_RET(lpt2_adjoint());
     k_ic_adj_prep<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(xi_, pi_, s1_, N_, d1_, gd_, rmesh(1), rmesh(2),
                                                              rmesh(3), 2 * lis, part_, part_ + (long long)B_ * G_);
     PMGB_CK(cudaGetLastError());
@@ -1026,8 +1124,9 @@ class Engine : public EngineBase {
     C* bufs[4] = {spec_[1], spec_[2], spec_[3], spec_[0]};
     PMGB_RET(cols(np_, -1, false, bufs, 4));
     PMGB_RET(cols(np_, -1, true, bufs, 4));
-    k_za_adj_mul<T><<<dim3(Gz_, B_), kPtclThreads, 0, st_>>>(spec_[1], spec_[2], spec_[3], spec_[0], spec_[5], np_,
-                                                             amp_, hdl_, maxn2_, inv_kfp_, lis, part_);
+    k_za_adj_mul<T><<<dim3(Gz_, B_), kPtclThreads, 0, st_>>>(spec_[1], spec_[2], spec_[3], spec_[0],
+                                                             lpt2_ ? spec_[5] : nullptr, spec_[5], np_, amp_, (T)0,
+                                                             hdl_, maxn2_, inv_kfp_, lis, part_);
     PMGB_CK(cudaGetLastError());
     k_sum_partials<<<5 * B_, 256, 0, st_>>>(part_, Gz_, scal_ + 4 * B_, 1.0);
     PMGB_CK(cudaGetLastError());
@@ -1067,7 +1166,9 @@ class Engine : public EngineBase {
   V4<T>* fvec_ = nullptr;
   T *ck_s_ = nullptr, *ck_p_ = nullptr;
   T *fkA_ = nullptr, *fkB_ = nullptr, *fdr_ = nullptr, *rkA_ = nullptr, *rkB_ = nullptr, *rdr_ = nullptr;
-  double *wpa_ = nullptr, *wxp_ = nullptr, *dd1_ = nullptr, *dgd_ = nullptr;
+  double *wpa_ = nullptr, *wxp_ = nullptr, *dd1_ = nullptr, *dgd_ = nullptr, *dd2_ = nullptr, *dgd2_ = nullptr;
+  T *s2_ = nullptr, *d2_ = nullptr, *gd2_ = nullptr, unit_ = 0;
+  bool lpt2_ = false;
   T *d1_ = nullptr, *gd_ = nullptr, *gcoef_ = nullptr, *amp_ = nullptr, *dtab_ = nullptr, *zero_ = nullptr;
   double* hdl_ = nullptr;
   C* tw_ = nullptr;

@@ -9,7 +9,8 @@
 //  k_gather_adj     CIC gather of a and alpha (Eq. 49 F line) + reverse kicks and drift of
 //                   Eq. 49, FP64 partials of the theta terms of Eq. 51; bin counts as above
 //  k_adjoint_init   xi_n = dJ/dx_n (density cotangent through the CIC weight gradient), pi_n
-//  k_density_out, k_mse, k_za_mul, k_za_adj_mul, k_ic_state, k_ic_adj_prep, k_final_theta
+//  k_density_out, k_mse, k_za_mul, k_za_adj_mul, k_ic_state, k_ic_adj_prep, k_final_theta,
+//  k_lpt_hess, k_lpt_source, k_lpt_source_adj, k_lpt_hess_adj, k_ic_state2
 #pragma once
 #include "common.cuh"
 #include "pm_internal.h"
@@ -528,10 +529,11 @@ __device__ __forceinline__ Mode mode_of(long long u, int n) {
 }
 __device__ __forceinline__ int nyq_zero(int f, int n, bool last) { return last ? (f == n / 2 ? 0 : f) : (f == -n / 2 ? 0 : f); }
 
-// s1^_c = B_c Omega, B_c = i k_c / k^2 sqrt(P / l_p^3) / n^3 (Sec. 2.1, Eqs. 3-6)
+// s1^_c = B_c Omega, B_c = i k_c / k^2 sqrt(P / l_p^3) / n^3 (Sec. 2.1, Eqs. 3-6).  With
+// amp = null the amplitude is the constant `unit` (the 2LPT s2 from the source spectrum).
 template <typename T>
 __global__ void k_za_mul(const cx_t<T>* __restrict__ om, cx_t<T>* o0, cx_t<T>* o1, cx_t<T>* o2, int n,
-                         const T* __restrict__ amp, int maxn2, T inv_kf, long long is) {
+                         const T* __restrict__ amp, int maxn2, T inv_kf, long long is, T unit) {
   using C = cx_t<T>;
   const int b = blockIdx.y;
   const long long tot = spec_len_cx(n);
@@ -539,7 +541,7 @@ __global__ void k_za_mul(const cx_t<T>* __restrict__ om, cx_t<T>* o0, cx_t<T>* o
     const Mode m = mode_of(u, n);
     const int n2 = m.f0 * m.f0 + m.f1 * m.f1 + m.f2 * m.f2;
     const C v = om[b * is + u];
-    const T base = n2 ? amp[(long long)b * (maxn2 + 1) + n2] * inv_kf / (T)n2 : (T)0;
+    const T base = n2 ? (amp ? amp[(long long)b * (maxn2 + 1) + n2] : unit) * inv_kf / (T)n2 : (T)0;
     const int fc[3] = {nyq_zero(m.f0, n, false), nyq_zero(m.f1, n, false), nyq_zero(m.f2, n, true)};
     C* outs[3] = {o0, o1, o2};
 #pragma unroll
@@ -550,12 +552,16 @@ __global__ void k_za_mul(const cx_t<T>* __restrict__ om, cx_t<T>* o0, cx_t<T>* o
   }
 }
 
-// Omega_bar = sum_c conj(B_c) S_c;  theta partials sum_k w Re[conj(Omega_bar) Omega] dlnP_j / 2
+// Omega_bar = sum_c conj(B_c) S_c (+ acc, the 2LPT part, when given);  theta partials
+// sum_k w Re[conj(Omega_bar) Omega] dlnP_j / 2.  With amp = null the amplitude is the
+// constant `unit` and no partials are taken (hdlnp = null): the transpose of the 2LPT
+// source -> s2 map.
 template <typename T>
 __global__ void __launch_bounds__(kPtclThreads)
 k_za_adj_mul(const cx_t<T>* s0, const cx_t<T>* s1, const cx_t<T>* s2, const cx_t<T>* __restrict__ om,
-             cx_t<T>* out, int n, const T* __restrict__ amp, const double* __restrict__ hdlnp, int maxn2,
-             T inv_kf, long long is, double* part /* [5][batch][grid] */) {
+             const cx_t<T>* acc_in, cx_t<T>* out, int n, const T* __restrict__ amp, T unit,
+             const double* __restrict__ hdlnp, int maxn2, T inv_kf, long long is,
+             double* part /* [5][batch][grid] */) {
   using C = cx_t<T>;
   __shared__ double shd[kPtclThreads / 32];
   const int b = blockIdx.y;
@@ -565,9 +571,9 @@ k_za_adj_mul(const cx_t<T>* s0, const cx_t<T>* s1, const cx_t<T>* s2, const cx_t
   for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < tot; u += (long long)gridDim.x * blockDim.x) {
     const Mode m = mode_of(u, n);
     const int n2 = m.f0 * m.f0 + m.f1 * m.f1 + m.f2 * m.f2;
-    const T base = n2 ? amp[(long long)b * (maxn2 + 1) + n2] * inv_kf / (T)n2 : (T)0;
+    const T base = n2 ? (amp ? amp[(long long)b * (maxn2 + 1) + n2] : unit) * inv_kf / (T)n2 : (T)0;
     const int fc[3] = {nyq_zero(m.f0, n, false), nyq_zero(m.f1, n, false), nyq_zero(m.f2, n, true)};
-    C r = cmake<C>(0, 0);
+    C r = acc_in ? acc_in[b * is + u] : cmake<C>(0, 0);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const C v = ins[c][b * is + u];
@@ -575,16 +581,139 @@ k_za_adj_mul(const cx_t<T>* s0, const cx_t<T>* s1, const cx_t<T>* s2, const cx_t
       r = cadd(r, cmake<C>(v.y * sc, -v.x * sc));  // -i v sc
     }
     out[b * is + u] = r;
+    if (!hdlnp) continue;
     const C w = om[b * is + u];
     const double re = (double)r.x * w.x + (double)r.y * w.y;
     const double wt = (m.f2 == 0 || m.f2 == n / 2) ? 1.0 : 2.0;
 #pragma unroll
     for (int j = 0; j < 5; ++j) acc[j] += wt * re * hdlnp[((long long)b * 5 + j) * (maxn2 + 1) + n2];
   }
+  if (!hdlnp) return;
 #pragma unroll
   for (int j = 0; j < 5; ++j) {
     const double r = block_sum(acc[j], shd);
     if (threadIdx.x == 0) part[((long long)j * gridDim.y + b) * gridDim.x + blockIdx.x] = r;
+  }
+}
+
+// ------------------------------------------------------------ 2LPT (Sec. 2.1, Eqs. 2-4)
+// The Hessian pairs (i, j) of the first-order potential: group 0 the diagonal ones
+// (00, 11, 22), group 1 the mixed ones (01, 02, 12).
+__device__ __forceinline__ void lpt_pair(int group, int q, int& i, int& j) {
+  i = group ? (q == 2 ? 1 : 0) : q;
+  j = group ? (q == 0 ? 1 : 2) : q;
+}
+
+// Hessian spectra phi_ij^ = (i k_i)(i k_j)(-1/k^2) delta1^ = k_i k_j / k^2 amp Omega
+// (laplacian phi = delta1, Eq. 4), each i k_c zeroed on the Nyquist plane of axis c, for
+// the three pairs of `group`; amp = sqrt(P / l_p^3) / n^3 per |n|^2.
+template <typename T>
+__global__ void k_lpt_hess(const cx_t<T>* __restrict__ om, cx_t<T>* o0, cx_t<T>* o1, cx_t<T>* o2, int n,
+                           const T* __restrict__ amp, int maxn2, long long is, int group) {
+  using C = cx_t<T>;
+  const int b = blockIdx.y;
+  const long long tot = spec_len_cx(n);
+  C* outs[3] = {o0, o1, o2};
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < tot; u += (long long)gridDim.x * blockDim.x) {
+    const Mode m = mode_of(u, n);
+    const int n2 = m.f0 * m.f0 + m.f1 * m.f1 + m.f2 * m.f2;
+    const C v = om[b * is + u];
+    const T base = n2 ? amp[(long long)b * (maxn2 + 1) + n2] / (T)n2 : (T)0;
+    const int fc[3] = {nyq_zero(m.f0, n, false), nyq_zero(m.f1, n, false), nyq_zero(m.f2, n, true)};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      int i, j;
+      lpt_pair(group, q, i, j);
+      const T sc = (T)(fc[i] * fc[j]) * base;
+      outs[q][b * is + u] = cmake<C>(v.x * sc, v.y * sc);
+    }
+  }
+}
+
+// The 2LPT source S = sum_{i<j} (phi_ii phi_jj - phi_ij^2) (Eq. 4) from the real Hessian
+// components r0..r2 of `group`: group 0 writes phi_00 phi_11 + phi_00 phi_22 +
+// phi_11 phi_22, group 1 subtracts phi_01^2 + phi_02^2 + phi_12^2.
+template <typename T>
+__global__ void k_lpt_source(const T* __restrict__ r0, const T* __restrict__ r1, const T* __restrict__ r2,
+                             long long ris, long long N, T* src, long long sis, int group) {
+  const int b = blockIdx.y;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const T h0 = r0[b * ris + i], h1 = r1[b * ris + i], h2 = r2[b * ris + i];
+    T* o = src + b * sis + i;
+    if (group == 0)
+      *o = h0 * h1 + h0 * h2 + h1 * h2;
+    else
+      *o = *o - (h0 * h0 + h1 * h1 + h2 * h2);
+  }
+}
+
+// Transpose of the source at each point, in place over the Hessian components of
+// `group`: phi_bar = dS/dphi S_bar, i.e. phi_bar_ii = S_bar sum_{j != i} phi_jj (group 0)
+// and phi_bar_ij = -2 phi_ij S_bar (group 1).
+template <typename T>
+__global__ void k_lpt_source_adj(T* r0, T* r1, T* r2, long long ris, long long N, const T* __restrict__ sbar,
+                                 long long sis, int group) {
+  const int b = blockIdx.y;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const T h0 = r0[b * ris + i], h1 = r1[b * ris + i], h2 = r2[b * ris + i];
+    const T sb = sbar[b * sis + i];
+    if (group == 0) {
+      r0[b * ris + i] = (h1 + h2) * sb;
+      r1[b * ris + i] = (h0 + h2) * sb;
+      r2[b * ris + i] = (h0 + h1) * sb;
+    } else {
+      r0[b * ris + i] = (T)-2 * h0 * sb;
+      r1[b * ris + i] = (T)-2 * h1 * sb;
+      r2[b * ris + i] = (T)-2 * h2 * sb;
+    }
+  }
+}
+
+// Transpose of Omega -> phi_ij (real even multipliers k_i k_j / k^2 amp): the spectra
+// i0..i2 of the Hessian adjoints of `group` summed into acc (group 0 overwrites acc).
+template <typename T>
+__global__ void k_lpt_hess_adj(const cx_t<T>* __restrict__ i0, const cx_t<T>* __restrict__ i1,
+                               const cx_t<T>* __restrict__ i2, cx_t<T>* acc, int n, const T* __restrict__ amp,
+                               int maxn2, long long is, int group) {
+  using C = cx_t<T>;
+  const int b = blockIdx.y;
+  const long long tot = spec_len_cx(n);
+  const C* ins[3] = {i0, i1, i2};
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < tot; u += (long long)gridDim.x * blockDim.x) {
+    const Mode m = mode_of(u, n);
+    const int n2 = m.f0 * m.f0 + m.f1 * m.f1 + m.f2 * m.f2;
+    const T base = n2 ? amp[(long long)b * (maxn2 + 1) + n2] / (T)n2 : (T)0;
+    const int fc[3] = {nyq_zero(m.f0, n, false), nyq_zero(m.f1, n, false), nyq_zero(m.f2, n, true)};
+    C r = group ? acc[b * is + u] : cmake<C>(0, 0);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      int i, j;
+      lpt_pair(group, q, i, j);
+      const T sc = (T)(fc[i] * fc[j]) * base;
+      const C v = ins[q][b * is + u];
+      r = cadd(r, cmake<C>(v.x * sc, v.y * sc));
+    }
+    acc[b * is + u] = r;
+  }
+}
+
+// Second-order terms of the initial state: s += D2 s2, p += G_D2 s2, s2 kept for the
+// adjoint's Omega_m terms (Sec. 2.1, Eq. 2).
+template <typename T>
+__global__ void k_ic_state2(const T* __restrict__ r0, const T* __restrict__ r1, const T* __restrict__ r2,
+                            long long ris, long long N, const T* __restrict__ d2, const T* __restrict__ gd2, T* s2,
+                            T* s, T* p) {
+  const int b = blockIdx.y;
+  const T* rs[3] = {r0 + b * ris, r1 + b * ris, r2 + b * ris};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T v = rs[c][i];
+      const long long o = (long long)b * 3 * N + c * N + i;
+      s2[o] = v;
+      s[o] = s[o] + d2[b] * v;
+      p[o] = p[o] + gd2[b] * v;
+    }
   }
 }
 
@@ -656,6 +785,10 @@ struct ThetaIn {
   const double* dlp;       // [5][batch]
   const double* dd1;       // [batch]   dD1(a0)/dOm
   const double* dgd;       // [batch]   dG_D(a0)/dOm
+  const double* xs2;       // [batch]   xi_0 . s2   (2LPT; null at first order)
+  const double* ps2;       // [batch]   pi_0 . s2
+  const double* dd2;       // [batch]   dD2(a0)/dOm
+  const double* dgd2;      // [batch]   dG_D2(a0)/dOm
   int nstep1, batch, step_stride;
 };
 static __global__ void k_final_theta(ThetaIn in, double* out) {
@@ -668,6 +801,7 @@ static __global__ void k_final_theta(ThetaIn in, double* out) {
     g += in.step_pa[o] * in.w_pa[w] + in.step_xp[o] * in.w_xp[w];
   }
   g += in.xs[b] * in.dd1[b] + in.ps[b] * in.dgd[b];
+  if (in.xs2) g += in.xs2[b] * in.dd2[b] + in.ps2[b] * in.dgd2[b];
   for (int j = 0; j < 5; ++j) out[5 * b + j] = in.dlp[j * in.batch + b] + (j == 2 ? g : 0.0);
 }
 

@@ -18,7 +18,7 @@ SYMBOLS = ("pm_init", "pm_forward", "pm_loss_mse", "pm_adjoint", "pm_destroy", "
            "pm_last_cuda_error", "pm_scratch_bytes", "pm_op_density", "pm_op_force", "pm_op_force_vjp",
            "pm_op_fft", "pm_op_za", "pm_set_inputs", "pm_gradient", "pm_profile", "pm_profile_read",
            "pm_density_noalloc", "pm_power_spectrum", "pm_gradient_graph", "pm_get_tuning", "pm_set_tuning",
-           "pm_autotune")
+           "pm_autotune", "pm_op_ic")
 NOALLOC_MAX_CELLS = 128 ** 3
 PROF_NAMES = ("scatter", "fft_x_r2c", "fft_cols", "fused_z_force", "fused_z_adjoint", "fft_x_c2r",
               "gather_fwd", "gather_adj", "other")
@@ -49,7 +49,7 @@ class PMConfig(ctypes.Structure):
     _fields_ = [("box", ctypes.c_double), ("n_mesh", ctypes.c_int), ("n_ptcl", ctypes.c_int),
                 ("n_steps", ctypes.c_int), ("a0", ctypes.c_double), ("a1", ctypes.c_double),
                 ("precision", ctypes.c_int), ("ckpt_every", ctypes.c_int), ("deconv", ctypes.c_int),
-                ("batch", ctypes.c_int)]
+                ("batch", ctypes.c_int), ("lpt_order", ctypes.c_int)]
 
 
 _lib = None
@@ -79,6 +79,7 @@ def load_library(path=LIB_PATH):
     lib.pm_op_force_vjp.argtypes = [vp, vp, vp, vp, vp]
     lib.pm_op_fft.argtypes = [vp, i, vp, vp]
     lib.pm_op_za.argtypes = [vp, vp]
+    lib.pm_op_ic.argtypes = [vp, vp, vp]
     lib.pm_set_inputs.argtypes = [vp, dp, vp]
     lib.pm_gradient.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.pm_profile.argtypes = [vp, i]
@@ -135,14 +136,16 @@ class PMContext:
     """One simulation context (owns the library's device scratch).
 
     omega: CUDA tensor [batch, n_ptcl, n_ptcl, n_ptcl] (float32 or float64 per precision);
-    theta: host sequence of shape [batch, 5] (A_s, n_s, Omega_m, Omega_b, h).
+    theta: host sequence of shape [batch, 5] (A_s, n_s, Omega_m, Omega_b, h);
+    lpt_order: 1 for Zel'dovich initial conditions, 2 for 2LPT.
     """
 
     def __init__(self, box, n_mesh, n_ptcl, n_steps, theta, omega, a0=1.0 / 64, a1=1.0,
-                 precision=PM_F32, ckpt_every=0, deconv=False, batch=1, stream=None):
+                 precision=PM_F32, ckpt_every=0, deconv=False, batch=1, stream=None, lpt_order=1):
         import torch
         lib = load_library()
-        self.cfg = PMConfig(box, n_mesh, n_ptcl, n_steps, a0, a1, precision, ckpt_every, int(deconv), batch)
+        self.cfg = PMConfig(box, n_mesh, n_ptcl, n_steps, a0, a1, precision, ckpt_every, int(deconv), batch,
+                            int(lpt_order))
         self.dtype = torch.float32 if precision == PM_F32 else torch.float64
         self.batch, self.n_mesh, self.n_ptcl = batch, n_mesh, n_ptcl
         self.N, self.M = n_ptcl ** 3, n_mesh ** 3
@@ -213,6 +216,12 @@ class PMContext:
 
     def op_za(self, s1):
         _check(load_library().pm_op_za(self._h, _ptr(s1, self.dtype, 3 * self.batch * self.N)), "pm_op_za")
+
+    def op_ic(self, s0=None, p0=None):
+        """Initial state (s0, p0) at a0 of the context's LPT order."""
+        v = 3 * self.batch * self.N
+        _check(load_library().pm_op_ic(self._h, _ptr(s0, self.dtype, v, "s0"), _ptr(p0, self.dtype, v, "p0")),
+               "pm_op_ic")
 
     def set_inputs(self, theta=None, omega=None):
         """theta: host [batch][5] or None; omega: host (pinned) or CUDA tensor or None."""

@@ -18,7 +18,7 @@ def ensure_built():
 
 
 def make_ctx(box, n_mesh, n_ptcl, n_steps, theta=inputs.THETA_FIDUCIAL, seed=1, precision=0, batch=1,
-             ckpt_every=0, deconv=False, a0=1 / 64, a1=1.0, omega=None):
+             ckpt_every=0, deconv=False, a0=1 / 64, a1=1.0, omega=None, lpt_order=1):
     torch = torch_cuda()
     ensure_built()
     from paper_2211_09815_gb300 import pm
@@ -30,12 +30,13 @@ def make_ctx(box, n_mesh, n_ptcl, n_steps, theta=inputs.THETA_FIDUCIAL, seed=1, 
     if th.shape[0] == 1 and batch > 1:
         th = np.repeat(th, batch, axis=0)
     ctx = pm.PMContext(box, n_mesh, n_ptcl, n_steps, th.tolist(), om, a0=a0, a1=a1, precision=precision,
-                       ckpt_every=ckpt_every, deconv=deconv, batch=batch)
+                       ckpt_every=ckpt_every, deconv=deconv, batch=batch, lpt_order=lpt_order)
     return ctx, om, omega, th
 
 
-def oracle_cfg(box, n_mesh, n_ptcl, n_steps, deconv=False, a0=1 / 64, a1=1.0):
-    return opm.PMConfig(box=box, n_mesh=n_mesh, n_ptcl=n_ptcl, n_steps=n_steps, deconv=deconv, a0=a0, a1=a1)
+def oracle_cfg(box, n_mesh, n_ptcl, n_steps, deconv=False, a0=1 / 64, a1=1.0, lpt_order=1):
+    return opm.PMConfig(box=box, n_mesh=n_mesh, n_ptcl=n_ptcl, n_steps=n_steps, deconv=deconv, a0=a0, a1=a1,
+                        lpt_order=lpt_order)
 
 
 def rel_l2(a, b):
