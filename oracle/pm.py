@@ -530,3 +530,29 @@ def power_spectrum(delta, box):
         pk = box ** 3 / m ** 2 * pw / cnt
         kmean = 2 * np.pi / box * ks / cnt
     return kmean, pk, cnt
+
+
+def power_loss(delta, box, target_pk, weights):
+    """Objective on the shell-averaged power spectrum (a summary-statistic objective,
+    Sec. 2.4): J = sum_b w_b (P_b - T_b)^2 with P_b from ``power_spectrum`` (bins
+    b < n/2), and dJ/d delta.
+
+    With F = DFT delta and C_b the number of full-k-space modes in shell b,
+    P_b = V / (M^2 C_b) sum_{k in b} |F(k)|^2, so d P_b / d delta(x) =
+    2 V / (M^2 C_b) sum_{k in b} F(k) e^{i k.x}: the unnormalised inverse DFT of F
+    restricted to the shell.  Hence dJ/d delta = IDFT_unnorm[g_b(k) F(k)] with
+    g_b = 2 w_b (P_b - T_b) 2 V / (M^2 C_b), and modes with |n| >= n/2 do not enter.
+    Returns (J, dJ/d delta as an (n, n, n) array).  Pinned by central differences."""
+    n = delta.shape[0]
+    _, pk, cnt = power_spectrum(delta, box)
+    diff = pk - np.asarray(target_pk, dtype=np.float64)
+    w = np.asarray(weights, dtype=np.float64)
+    loss = float(np.sum(w * diff * diff))
+    m = float(n) ** 3
+    with np.errstate(invalid="ignore", divide="ignore"):
+        g = np.where(cnt > 0, 2.0 * w * diff * 2.0 * box ** 3 / (m * m * cnt), 0.0)
+    _, (n0, n1, n2) = _kgrid(n, box)
+    b = np.floor(np.sqrt(n0 ** 2 + n1 ** 2 + n2 ** 2)).astype(np.int64)
+    coef = np.where(b < n // 2, g[np.minimum(b, n // 2 - 1)], 0.0)
+    grad = np.fft.irfftn(coef * np.fft.rfftn(delta), s=(n, n, n), axes=(0, 1, 2)) * m
+    return loss, grad
