@@ -358,7 +358,7 @@ def force_vjp(x, pi, f, Om, cfg):
 
 # ------------------------------------------------------------------------- integrate
 
-def forward(omega, theta, cfg, store_every=0, force_fn=None):
+def forward(omega, theta, cfg, store_every=0, force_fn=None, snapshots=()):
     """Zel'dovich ICs then the FastPM kick-drift-kick leapfrog (Sec. 2.3, Eq. 16).
 
     a_0 = F_0 first; then for i = 1..n: p += a K1_i; s += p D_i; a = F_i; p += a K2_i.
@@ -366,6 +366,9 @@ def forward(omega, theta, cfg, store_every=0, force_fn=None):
     density delta_n at a_n, and (store_every > 0) the states (s_j, p_j) at steps
     j = 0, k, 2k, ... for the checkpointed adjoint.  ``force_fn(x, s)`` replaces the PM
     force (used by the Zel'dovich-exactness pin with the linear-theory force).
+    ``snapshots``: steps j whose displacement s_j and density delta_j are returned in
+    "snap" as {j: (s_j, delta_j)} -- observations of intermediate states (Sec. 2.4: the
+    objective may depend on every z_0..z_n).
     """
     q = lattice(cfg)
     Om = theta[2]
@@ -375,8 +378,11 @@ def forward(omega, theta, cfg, store_every=0, force_fn=None):
     s, p = lpt_initial_state(omega, theta, cfg)
     k1, dd, k2 = cosmo.kdk_factors(cosmo.time_grid(cfg.a0, cfg.a1, cfg.n_steps), Om)
     store = {}
+    snap = {}
     if store_every:
         store[0] = (s.copy(), p.copy())
+    if 0 in snapshots:
+        snap[0] = (s.copy(), density(q + s, cfg))
     a = force_fn(q + s, s)
     for i in range(1, cfg.n_steps + 1):
         p = p + a * k1[i - 1]
@@ -385,7 +391,9 @@ def forward(omega, theta, cfg, store_every=0, force_fn=None):
         p = p + a * k2[i - 1]
         if store_every and i % store_every == 0:
             store[i] = (s.copy(), p.copy())
-    return dict(s=s, p=p, a=a, delta=density(q + s, cfg), store=store)
+        if i in snapshots:
+            snap[i] = (s.copy(), density(q + s, cfg))
+    return dict(s=s, p=p, a=a, delta=density(q + s, cfg), store=store, snap=snap)
 
 
 def mse_loss(delta, target):
@@ -402,7 +410,18 @@ def _dlnp_funcs(theta):
     return [make(j) for j in range(5)]
 
 
-def adjoint(omega, theta, cfg, fwd, dj_ddelta=None, dj_ds=None, dj_dp=None, ckpt=None):
+def _observation_cotangent(x, dj_ddelta, dj_ds, cfg):
+    """dJ/dx of an observation of the positions x: the density cotangent through the CIC
+    weight gradient, m sum_g grad W dJ/d delta(g), plus the direct displacement term."""
+    out = np.zeros_like(x)
+    if dj_ddelta is not None:
+        out += cfg.mass * cic_gather_grad(np.asarray(dj_ddelta).reshape((cfg.n_mesh,) * 3), x, cfg)
+    if dj_ds is not None:
+        out += dj_ds
+    return out
+
+
+def adjoint(omega, theta, cfg, fwd, dj_ddelta=None, dj_ds=None, dj_dp=None, ckpt=None, obs=None):
     """Discrete adjoint with reverse time integration (Sec. 3.6, Eqs. 49-51).
 
     Starts from the final state in ``fwd`` and integrates the leapfrog backward jointly
@@ -414,7 +433,10 @@ def adjoint(omega, theta, cfg, fwd, dj_ddelta=None, dj_ds=None, dj_dp=None, ckpt
       K_{i-1/2}^{i-1}: p -= a K1_i;  xi += alpha K1_i;  g += (pi.a) dK1_i + zeta K1_i
     (D(t_c,t_b,t_a) = -D(t_c,t_a,t_b) turns the printed signs into these.)  Finally
     (Eq. 51) dJ/domega = (D1 xi_0 + G_D pi_0) . ds1/domega and the theta terms of the
-    initial conditions; with 2LPT also (D2 xi_0 + G_D2 pi_0) . ds2/domega and the s2 terms.  ``ckpt`` maps step j to a stored (s_j, p_j) that replaces the
+    initial conditions; with 2LPT also (D2 xi_0 + G_D2 pi_0) . ds2/domega and the s2 terms.
+    ``obs`` maps steps j to cotangents (dJ/d delta_j or None, dJ/ds_j or None) of
+    observed intermediate states; each is added to xi when the reverse pass holds x_j
+    (after the last reverse kick that ends at step j, before the reverse drift of step j).  ``ckpt`` maps step j to a stored (s_j, p_j) that replaces the
     reverse-integrated state when step j is reached (piecewise resumption, Sec. 3.5).
     Returns dict(grad_omega (n_ptcl^3,), grad_theta (5,), s0, p0 (reverse-integrated)).
     """
@@ -430,11 +452,10 @@ def adjoint(omega, theta, cfg, fwd, dj_ddelta=None, dj_ds=None, dj_dp=None, ckpt
     p = fwd["p"].copy()
     g_om = 0.0
     x = q + s
-    xi = np.zeros_like(s)
-    if dj_ddelta is not None:
-        xi += cfg.mass * cic_gather_grad(np.asarray(dj_ddelta).reshape((cfg.n_mesh,) * 3), x, cfg)
-    if dj_ds is not None:
-        xi += dj_ds
+    obs = obs or {}
+    xi = _observation_cotangent(x, dj_ddelta, dj_ds, cfg)
+    if n in obs:
+        xi += _observation_cotangent(x, *obs[n], cfg)
     pi = np.zeros_like(s) if dj_dp is None else np.array(dj_dp, dtype=np.float64)
     a, f = pm_force(x, Om, cfg)
     alpha = force_vjp(x, pi, f, Om, cfg)
@@ -457,6 +478,8 @@ def adjoint(omega, theta, cfg, fwd, dj_ddelta=None, dj_ds=None, dj_dp=None, ckpt
         g_om += pa * dk1[i - 1] + (pa / Om) * k1[i - 1]
         if (i - 1) in ckpt:
             p = ckpt[i - 1][1].copy()
+        if (i - 1) in obs:
+            xi = xi + _observation_cotangent(x, *obs[i - 1], cfg)
     # initial conditions (Eq. 51): x0 = q + D1(a0) s1, p0 = G_D(a0) s1
     d1, _, gd, _ = cosmo.growth_factors(np.array([cfg.a0]), Om)
     dd1 = cosmo.complex_step(lambda th: cosmo.growth_factors(np.array([cfg.a0]), th[2])[0], theta, 2)[0]

@@ -1,0 +1,107 @@
+"""Objectives other than the field MSE (Sec. 2.4: observables compared at the level of
+the fields or of summary statistics), through the C ABI against the FP64 oracle:
+
+* the shell power spectrum objective J = sum_b w_b (P_b - T_b)^2 (pm_loss_power) as an
+  operator on a given density and through the whole adjoint;
+* objectives on the final particle state: cotangents dJ/dx_n, dJ/dp_n passed to pm_adjoint.
+"""
+import numpy as np
+import pytest
+
+from oracle import pm as opm
+from paper_2211_09815_gb300 import inputs
+
+from gpu_util import cosine, make_ctx, oracle_cfg, rel_l2, torch_cuda
+
+pytestmark = pytest.mark.gpu
+THETA = inputs.THETA_FIDUCIAL
+
+
+def _za_density(box, nm, npc, growth):
+    cfg = oracle_cfg(box, nm, npc, 1)
+    s1 = opm.za_unit_displacement(inputs.white_noise(npc, 3).astype(np.float64), THETA, cfg)
+    return opm.density(opm.lattice(cfg) + growth * s1, cfg)
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_power_loss_operator_matches_oracle(precision):
+    torch = torch_cuda()
+    box, nm, npc = 100.0, 64, 32
+    delta = _za_density(box, nm, npc, 0.5)
+    _, pk, _ = opm.power_spectrum(delta, box)
+    rng = np.random.default_rng(31)
+    target = pk * rng.uniform(0.7, 1.3, size=pk.shape)
+    w = 1.0 / target ** 2
+    loss_o, grad_o = opm.power_loss(delta, box, target, w)
+    ctx, *_ = make_ctx(box, nm, npc, 1, precision=precision)
+    d = torch.from_numpy(delta.ravel()).to("cuda", ctx.dtype)
+    djdd = torch.empty_like(d)
+    loss = ctx.loss_power(target[None], w[None], djdd, dens=d)
+    ctx.close()
+    tol = 1e-11 if precision else 2e-5
+    assert abs(loss[0] / loss_o - 1) < tol
+    assert rel_l2(djdd.cpu().numpy(), grad_o.ravel()) < tol
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_power_objective_gradient_matches_oracle(precision):
+    """J on P(k) of the final density, back-propagated through the reverse-time adjoint."""
+    torch = torch_cuda()
+    c = dict(box=32.0, n_mesh=32, n_ptcl=16, n_steps=6)
+    cfg = oracle_cfg(**c)
+    om = inputs.white_noise(c["n_ptcl"], 1).astype(np.float64)
+    tgt_delta = opm.forward(inputs.white_noise(c["n_ptcl"], 2).astype(np.float64), THETA, cfg)["delta"]
+    _, target, _ = opm.power_spectrum(tgt_delta, c["box"])
+    w = 1.0 / target ** 2
+    fwd = opm.forward(om, THETA, cfg)
+    loss_o, djdd_o = opm.power_loss(fwd["delta"], c["box"], target, w)
+    adj = opm.adjoint(om, THETA, cfg, fwd, dj_ddelta=djdd_o.ravel())
+
+    ctx, *_ = make_ctx(c["box"], c["n_mesh"], c["n_ptcl"], c["n_steps"], precision=precision)
+    M, N = c["n_mesh"] ** 3, c["n_ptcl"] ** 3
+    ctx.forward(dens=torch.empty(M, device="cuda", dtype=ctx.dtype))
+    djdd = torch.empty(M, device="cuda", dtype=ctx.dtype)
+    loss = ctx.loss_power(target[None], w[None], djdd)
+    gw = torch.empty(N, device="cuda", dtype=ctx.dtype)
+    gt = torch.zeros(5, dtype=torch.float64)
+    ctx.adjoint(djdd=djdd, grad_omega=gw, grad_theta=gt)
+    ctx.close()
+    g = gw.cpu().numpy()
+    if precision:
+        assert abs(loss[0] / loss_o - 1) < 1e-9
+        assert rel_l2(g, adj["grad_omega"]) < 1e-8
+        assert np.allclose(gt.numpy(), adj["grad_theta"], rtol=1e-8, atol=0)
+    else:
+        assert abs(loss[0] / loss_o - 1) < 1e-3
+        assert cosine(g, adj["grad_omega"]) >= 0.999
+        assert np.all(np.abs(gt.numpy() / adj["grad_theta"] - 1) < 1e-2)
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_particle_state_objective_gradient_matches_oracle(precision):
+    """J = <u, x_n> + <v, p_n> with seeded u, v: the cotangents dJ/dx_n = u and dJ/dp_n = v
+    enter the adjoint initial conditions (Eq. 50) directly."""
+    torch = torch_cuda()
+    c = dict(box=32.0, n_mesh=32, n_ptcl=16, n_steps=6)
+    cfg = oracle_cfg(**c)
+    N = c["n_ptcl"] ** 3
+    rng = np.random.default_rng(41)
+    u = rng.normal(size=(3, N))
+    v = rng.normal(size=(3, N))
+    om = inputs.white_noise(c["n_ptcl"], 1).astype(np.float64)
+    adj = opm.adjoint(om, THETA, cfg, opm.forward(om, THETA, cfg), dj_ds=u, dj_dp=v)
+
+    ctx, *_ = make_ctx(c["box"], c["n_mesh"], c["n_ptcl"], c["n_steps"], precision=precision)
+    ctx.forward()
+    gw = torch.empty(N, device="cuda", dtype=ctx.dtype)
+    gt = torch.zeros(5, dtype=torch.float64)
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a.ravel())).to("cuda", ctx.dtype)
+    ctx.adjoint(djdx=to(u), djdp=to(v), grad_omega=gw, grad_theta=gt)
+    ctx.close()
+    g = gw.cpu().numpy()
+    if precision:
+        assert rel_l2(g, adj["grad_omega"]) < 1e-8
+        assert np.allclose(gt.numpy(), adj["grad_theta"], rtol=1e-8, atol=0)
+    else:
+        assert cosine(g, adj["grad_omega"]) >= 0.999
+        assert rel_l2(g, adj["grad_omega"]) <= 1e-2

@@ -496,3 +496,60 @@ def test_power_loss_single_bin_value():
     assert loss == pytest.approx(pk[3] ** 2, rel=1e-14)
     loss0, grad0 = pm.power_loss(delta, box, pk, np.ones_like(pk))
     assert loss0 == 0.0 and np.max(np.abs(grad0)) == 0.0
+
+
+SNAP_CFG = pm.PMConfig(box=24.0, n_mesh=16, n_ptcl=8, n_steps=4)
+
+
+def _snapshot_loss(om, th, targets, u):
+    """J = sum_j MSE(delta_j, target_j) over observed steps + <u, s_3> (intermediate
+    observations of Sec. 2.4)."""
+    fwd = pm.forward(om, th, SNAP_CFG, snapshots=(0, 2, 3))
+    j = sum(pm.mse_loss(fwd["snap"][k][1], targets[k])[0] for k in (0, 2))
+    return j + float(np.sum(u * fwd["snap"][3][0]))
+
+
+@pytest.fixture(scope="module")
+def snapshot_case():
+    om = inputs.white_noise(8, 1).astype(np.float64)
+    other = pm.forward(inputs.white_noise(8, 2).astype(np.float64), THETA, SNAP_CFG, snapshots=(0, 2))
+    targets = {k: other["snap"][k][1] for k in (0, 2)}
+    u = np.random.default_rng(23).normal(size=(3, 8 ** 3))
+    fwd = pm.forward(om, THETA, SNAP_CFG, snapshots=(0, 2, 3))
+    obs = {k: (pm.mse_loss(fwd["snap"][k][1], targets[k])[1], None) for k in (0, 2)}
+    obs[3] = (None, u)
+    adj = pm.adjoint(om, THETA, SNAP_CFG, fwd, obs=obs)
+    return om, targets, u, adj
+
+
+def test_snapshot_states_equal_shorter_runs():
+    """The state observed at step j is the final state of a j-step run over the same
+    time grid (a1 = a_j)."""
+    om = inputs.white_noise(8, 1).astype(np.float64)
+    fwd = pm.forward(om, THETA, SNAP_CFG, snapshots=(2,))
+    agrid = cosmo.time_grid(SNAP_CFG.a0, SNAP_CFG.a1, SNAP_CFG.n_steps)
+    short = pm.PMConfig(box=24.0, n_mesh=16, n_ptcl=8, n_steps=2, a1=float(agrid[2]))
+    ref = pm.forward(om, THETA, short)
+    assert np.allclose(fwd["snap"][2][0], ref["s"], rtol=0, atol=1e-12 * np.abs(ref["s"]).max())
+    assert np.allclose(fwd["snap"][2][1], ref["delta"], rtol=0, atol=1e-12)
+
+
+def test_snapshot_objective_gradient_omega_vs_central_fd(snapshot_case):
+    """Cotangents of observed intermediate densities and displacements, injected when the
+    reverse pass reaches their step, give dJ/domega of the whole objective (central FD)."""
+    om, targets, u, adj = snapshot_case
+    v = np.random.default_rng(24).normal(size=om.shape)
+    h = 1e-6
+    fd = (_snapshot_loss(om + h * v, THETA, targets, u) - _snapshot_loss(om - h * v, THETA, targets, u)) / (2 * h)
+    assert abs(fd - np.sum(adj["grad_omega"] * v.ravel())) <= 1e-6 * abs(fd)
+
+
+@pytest.mark.parametrize("j", [0, 2])
+def test_snapshot_objective_gradient_theta_vs_central_fd(snapshot_case, j):
+    om, targets, u, adj = snapshot_case
+    h = 1e-6 * abs(THETA[j])
+    tp, tm = list(THETA), list(THETA)
+    tp[j] += h
+    tm[j] -= h
+    fd = (_snapshot_loss(om, tp, targets, u) - _snapshot_loss(om, tm, targets, u)) / (2 * h)
+    assert abs(fd - adj["grad_theta"][j]) <= 1e-6 * abs(fd) + 1e-12
