@@ -162,6 +162,23 @@ int pm_gradient_graph(pm_ctx* ctx, const void* target, double* loss, void* grad_
  */
 int pm_power_spectrum(pm_ctx* ctx, const void* dens, double* pk, double* kmean, double* nmodes);
 
+/*
+ * Objective on the shell-averaged power spectrum (a summary-statistic objective, Sec. 2.4):
+ * J = sum_b w_b (P_b - T_b)^2 per instance, P_b as in pm_power_spectrum, and its cotangent
+ * for pm_adjoint, dJ/d delta(x) = sum_b 2 w_b (P_b - T_b) 2V / (M^2 C_b)
+ * sum_{k in shell b} DFT[delta](k) e^{i k.x}  (C_b modes in shell b, V = box^3,
+ * M = n_mesh^3; modes with |n| >= n_mesh/2 do not enter).
+ *   dens         : device [batch][n_mesh^3], or null for the context's last forward density
+ *   pk_target    : [batch][n_mesh/2] doubles T_b, host or device
+ *   weights      : [batch][n_mesh/2] doubles w_b, host or device
+ *   loss_out     : optional [batch] doubles, host or device (host: synchronises)
+ *   dJ_ddens_out : device [batch][n_mesh^3]
+ * Deterministic (the bin sums of pm_power_spectrum).  Errors: PM_ERR_ARG for null
+ * target, weights or output; PM_ERR_STATE when dens is null before any forward.
+ */
+int pm_loss_power(pm_ctx* ctx, const void* dens, const double* pk_target, const double* weights, double* loss_out,
+                  void* dJ_ddens_out);
+
 /* Per-category timing of the context's kernel launches with CUDA events on its stream. */
 enum {
   PM_PROF_SCATTER = 0,   /* CIC scatter (density, and pi in the adjoint)        */
@@ -264,6 +281,30 @@ int pm_op_fft(pm_ctx* ctx, int dir, const void* in, void* out);
 /* Zel'dovich displacement for unit growth s1 (Sec. 2.1, Eqs. 3-6) of the context's omega.
  * s1_out: [batch][3][n_ptcl^3]. */
 int pm_op_za(pm_ctx* ctx, void* s1_out);
+
+/* Most snapshots pm_set_snapshots accepts. */
+#define PM_MAX_SNAPSHOTS 64
+
+/*
+ * Observed intermediate states (Sec. 2.4: the observation and the objective may depend on
+ * every state z_0..z_n, e.g. snapshots at the end of time steps).
+ *   nsnap    : 0..PM_MAX_SNAPSHOTS; 0 clears the snapshots
+ *   steps    : host [nsnap] ints, strictly ascending in 0..n_steps; step j is the state
+ *              after j leapfrog steps (0: the initial state, n_steps: the final one)
+ *   disp_out : optional device [nsnap][batch][3][n_ptcl^3]: every following pm_forward
+ *              writes s_j of snapshot q into disp_out[q]
+ *   dens_out : optional device [nsnap][batch][n_mesh^3]: delta_j likewise
+ *   dJ_ddisp : optional device [nsnap][batch][3][n_ptcl^3], dJ/dx_j
+ *   dJ_ddens : optional device [nsnap][batch][n_mesh^3], dJ/d delta_j
+ * Every following pm_adjoint adds the cotangents of snapshot q, read when the reverse pass
+ * reaches step j (so they may be written between pm_forward and pm_adjoint), to those of
+ * the final state.  The buffers stay owned by the caller and must outlive their use.
+ * Momenta are observed at the final step only (pm_adjoint's dJ_dmom): inside the leapfrog
+ * the momentum is held at half steps.  Drops a captured pm_gradient_graph.
+ * Errors: PM_ERR_ARG for a bad count or step list.
+ */
+int pm_set_snapshots(pm_ctx* ctx, int nsnap, const int* steps, void* disp_out, void* dens_out, const void* dJ_ddisp,
+                     const void* dJ_ddens);
 
 /* Initial state at a0 of the context's lpt_order (Sec. 2.1, Eq. 2): s0 = D1 s1 (+ D2 s2),
  * p0 = a^2 H (D1' s1 (+ D2' s2)).  s0_out, p0_out: optional (null: not written),

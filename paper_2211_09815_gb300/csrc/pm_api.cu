@@ -121,6 +121,12 @@ int pm_power_spectrum(pm_ctx* ctx, const void* dens, double* pk, double* kmean, 
   return ctx->eng->power_spectrum(dens, pk, kmean, nmodes);
 }
 
+int pm_loss_power(pm_ctx* ctx, const void* dens, const double* pk_target, const double* weights, double* loss_out,
+                  void* dJ_ddens_out) {
+  if (!ctx || !pk_target || !weights || !dJ_ddens_out) return PM_ERR_ARG;
+  return ctx->eng->loss_power(dens, pk_target, weights, loss_out, dJ_ddens_out);
+}
+
 int pm_profile(pm_ctx* ctx, int enable) {
   if (!ctx) return PM_ERR_ARG;
   return ctx->eng->profile(enable);
@@ -194,6 +200,12 @@ int pm_op_fft(pm_ctx* ctx, int dir, const void* in, void* out) {
 int pm_op_za(pm_ctx* ctx, void* s1_out) {
   if (!ctx || !s1_out) return PM_ERR_ARG;
   return ctx->eng->op_za(s1_out);
+}
+
+int pm_set_snapshots(pm_ctx* ctx, int nsnap, const int* steps, void* disp_out, void* dens_out,
+                     const void* dJ_ddisp, const void* dJ_ddens) {
+  if (!ctx) return PM_ERR_ARG;
+  return ctx->eng->set_snapshots(nsnap, steps, disp_out, dens_out, dJ_ddisp, dJ_ddens);
 }
 
 int pm_op_ic(pm_ctx* ctx, void* s0_out, void* p0_out) {

@@ -16,12 +16,15 @@ struct EngineBase {
   virtual int op_fft(int dir, const void* in, void* out) = 0;
   virtual int op_za(void* s1) = 0;
   virtual int op_ic(void* s0, void* p0) = 0;
+  virtual int set_snapshots(int ns, const int* steps, void* disp, void* dens, const void* gdisp,
+                            const void* gdens) = 0;
   virtual long long scratch_bytes() const = 0;
   virtual int profile(int enable) = 0;
   virtual int profile_read(double* ms, long long* launches) = 0;
   virtual int set_inputs(const double* theta, const void* omega) = 0;
   virtual int gradient_graph(const void* target, double* loss, void* gw, double* gt) = 0;
   virtual int power_spectrum(const void* dens, double* pk, double* kmean, double* nmodes) = 0;
+  virtual int loss_power(const void* dens, const double* tgt, const double* w, double* loss, void* djdd) = 0;
   virtual int gradient(const void* omega, const void* target, double* loss, void* grad_omega, double* grad_theta) = 0;
   virtual int get_tuning(pm_tuning* t) = 0;
   virtual int set_tuning(const pm_tuning* t) = 0;

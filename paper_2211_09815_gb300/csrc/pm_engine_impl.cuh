@@ -189,7 +189,14 @@ class Engine : public EngineBase {
     PMGB_RET(initial_conditions());
     prof_.end(st_, P_OTHER);
     for (int j = 0; j <= n_; ++j) {
-      PMGB_RET(force_chain(s_, nullptr, j == n_));
+      const int q = snap_of(j);
+      PMGB_RET(force_chain(s_, nullptr, j == n_ || (q >= 0 && snap_dens_)));
+      if (q >= 0 && snap_disp_)
+        PMGB_CK(cudaMemcpyAsync(snap_disp_ + (long long)q * B_ * 3 * N_, s_, sizeof(T) * B_ * 3 * N_,
+                                cudaMemcpyDeviceToDevice, st_));
+      if (q >= 0 && snap_dens_)
+        PMGB_CK(cudaMemcpyAsync(snap_dens_ + (long long)q * B_ * M_, dens_, sizeof(T) * B_ * M_,
+                                cudaMemcpyDeviceToDevice, st_));
       T* cks = nullptr;
       T* ckp = nullptr;
       if (nck_ && j < n_ && j % cfg_.ckpt_every == 0) {
@@ -255,6 +262,16 @@ class Engine : public EngineBase {
     PMGB_CK(cudaGetLastError());
     const long long fis = 2 * spec_len_cx(nm_);
     for (int j = n_; j >= 0; --j) {
+      // cotangents of an observed state j enter xi while the positions are x_j
+      const int q = snap_of(j);
+      if (q >= 0 && (snap_gdisp_ || snap_gdens_)) {
+        prof_.begin(st_, P_OTHER, 1);
+        k_obs_cotangent<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(
+            geo_, mass_, s_, snap_gdens_ ? snap_gdens_ + (long long)q * B_ * M_ : nullptr,
+            snap_gdisp_ ? snap_gdisp_ + (long long)q * B_ * 3 * N_ : nullptr, xi_);
+        prof_.end(st_, P_OTHER);
+        PMGB_CK(cudaGetLastError());
+      }
       PMGB_RET(force_chain(s_, pi_, false));
       const T* ckp = nullptr;
       const T* cks = nullptr;
@@ -394,14 +411,52 @@ class Engine : public EngineBase {
   // Shell-averaged P(k) of dens ([B][M]; null: the last forward density), n_mesh/2 bins
   int power_spectrum(const void* dens, double* pk, double* kmean, double* nmodes) override {
     const int nb = nm_ / 2;
+    if (!dens && !have_dens_) return PM_ERR_STATE;
+    PMGB_RET(power_dev(dens ? (const T*)dens : dens_));
+    if (pk) PMGB_CK(cudaMemcpyAsync(pk, pw_out_, sizeof(double) * B_ * nb, cudaMemcpyDefault, st_));
+    if (kmean) PMGB_CK(cudaMemcpyAsync(kmean, pw_out_ + B_ * nb, sizeof(double) * nb, cudaMemcpyDefault, st_));
+    if (nmodes) PMGB_CK(cudaMemcpyAsync(nmodes, pw_out_ + (B_ + 1) * nb, sizeof(double) * nb, cudaMemcpyDefault, st_));
+    PMGB_CK(cudaStreamSynchronize(st_));
+    return PM_OK;
+  }
+
+  // Objective on the shell power of delta (the last forward density when dens is null):
+  // J_b = sum w (P - T)^2 and dJ/d delta = IDFT_unnorm[g(|n|) delta^] (k_power_loss,
+  // k_power_grad, one inverse transform).
+  int loss_power(const void* dens, const double* tgt, const double* w, double* loss, void* djdd) override {
+    if (!dens && !have_dens_) return PM_ERR_STATE;
+    const int nb = nm_ / 2;
+    PMGB_RET(power_dev(dens ? (const T*)dens : dens_));
+    if (!pl_buf_) PMGB_RET(alloc(&pl_buf_, (long long)B_ * (3 * nb + 1)));
+    double* dt = pl_buf_;
+    double* dw = pl_buf_ + (long long)B_ * nb;
+    double* dg = pl_buf_ + 2LL * B_ * nb;
+    double* dl = pl_buf_ + 3LL * B_ * nb;
+    PMGB_CK(cudaMemcpyAsync(dt, tgt, sizeof(double) * B_ * nb, cudaMemcpyDefault, st_));
+    PMGB_CK(cudaMemcpyAsync(dw, w, sizeof(double) * B_ * nb, cudaMemcpyDefault, st_));
+    const double vol = cfg_.box * cfg_.box * cfg_.box;
+    k_power_loss<<<(B_ + 31) / 32, 32, 0, st_>>>(pw_out_, pw_out_ + (B_ + 1) * nb, dt, dw, nb, B_,
+                                                 2.0 * vol / ((double)M_ * (double)M_), dl, dg);
+    k_power_grad<T><<<dim3(512, B_), 256, 0, st_>>>(spec_[6], nm_, spec_len_cx(nm_), nb, dg);
+    PMGB_CK(cudaGetLastError());
+    PMGB_RET(c2r_real(nm_, spec_[6], (T*)djdd, M_));
+    if (loss) {
+      PMGB_CK(cudaMemcpyAsync(loss, dl, sizeof(double) * B_, cudaMemcpyDefault, st_));
+      if (is_host(loss)) PMGB_CK(cudaStreamSynchronize(st_));
+    }
+    return PM_OK;
+  }
+
+  // Shell power of d into pw_out_ (pk [B][nb], kmean [nb], nmodes [nb]); leaves delta^ in
+  // spec_[6].  Deterministic: per-bin int64 fixed point scaled from a first max pass.
+  int power_dev(const T* d) {
+    const int nb = nm_ / 2;
     if (!pw_acc_) {
       PMGB_RET(alloc(&pw_acc_, (long long)(B_ + 2) * nb));
       PMGB_RET(alloc(&pw_max_, (long long)B_ * nb));
       PMGB_RET(alloc(&pw_e_, (long long)B_ * nb));
       PMGB_RET(alloc(&pw_out_, (long long)(B_ + 2) * nb));
     }
-    if (!dens && !have_dens_) return PM_ERR_STATE;
-    const T* d = dens ? (const T*)dens : dens_;
     PMGB_RET(r2c_real(nm_, d, M_, spec_[6]));
     PMGB_CK(cudaMemsetAsync(pw_acc_, 0, sizeof(unsigned long long) * (B_ + 2) * nb, st_));
     PMGB_CK(cudaMemsetAsync(pw_max_, 0, sizeof(unsigned) * B_ * nb, st_));
@@ -416,10 +471,6 @@ class Engine : public EngineBase {
                                                         2.0 * M_PI / cfg_.box, pw_out_, pw_out_ + B_ * nb,
                                                         pw_out_ + (B_ + 1) * nb);
     PMGB_CK(cudaGetLastError());
-    if (pk) PMGB_CK(cudaMemcpyAsync(pk, pw_out_, sizeof(double) * B_ * nb, cudaMemcpyDefault, st_));
-    if (kmean) PMGB_CK(cudaMemcpyAsync(kmean, pw_out_ + B_ * nb, sizeof(double) * nb, cudaMemcpyDefault, st_));
-    if (nmodes) PMGB_CK(cudaMemcpyAsync(nmodes, pw_out_ + (B_ + 1) * nb, sizeof(double) * nb, cudaMemcpyDefault, st_));
-    PMGB_CK(cudaStreamSynchronize(st_));
     return PM_OK;
   }
 
@@ -463,6 +514,30 @@ class Engine : public EngineBase {
     PMGB_CK(cudaMemcpyAsync(s1, s1_, sizeof(T) * B_ * 3 * N_, cudaMemcpyDeviceToDevice, st_));
     return PM_OK;
   }
+
+  // Observed intermediate states: step -> snapshot index; the forward copies s_j and
+  // delta_j out, the adjoint adds their cotangents at step j.  A captured gradient graph
+  // is dropped (it holds the old settings).
+  int set_snapshots(int ns, const int* steps, void* disp, void* dens, const void* gdisp, const void* gdens) override {
+    if (ns < 0 || ns > PM_MAX_SNAPSHOTS || (ns > 0 && !steps)) return PM_ERR_ARG;
+    std::vector<int> map(n_ + 1, -1);
+    for (int q = 0; q < ns; ++q) {
+      if (steps[q] < 0 || steps[q] > n_ || (q > 0 && steps[q] <= steps[q - 1])) return PM_ERR_ARG;
+      map[steps[q]] = q;
+    }
+    if (ns == 0) map.clear();
+    snap_of_ = map;
+    snap_disp_ = ns ? (T*)disp : nullptr;
+    snap_dens_ = ns ? (T*)dens : nullptr;
+    snap_gdisp_ = ns ? (const T*)gdisp : nullptr;
+    snap_gdens_ = ns ? (const T*)gdens : nullptr;
+    if (graph_exec_) {
+      cudaGraphExecDestroy(graph_exec_);
+      graph_exec_ = nullptr;
+    }
+    return PM_OK;
+  }
+  int snap_of(int j) const { return snap_of_.empty() ? -1 : snap_of_[j]; }
 
   int op_ic(void* s0, void* p0) override {
     have_fwd_ = false;
@@ -1152,6 +1227,10 @@ class Engine : public EngineBase {
   unsigned* pw_max_ = nullptr;
   int* pw_e_ = nullptr;
   double* pw_out_ = nullptr;
+  double* pl_buf_ = nullptr;   // power objective: target, weights, g, loss
+  std::vector<int> snap_of_;   // observed states: step -> snapshot index (-1: none)
+  T *snap_disp_ = nullptr, *snap_dens_ = nullptr;
+  const T *snap_gdisp_ = nullptr, *snap_gdens_ = nullptr;
   bool have_dens_ = false;
   cudaGraphExec_t graph_exec_ = nullptr;
   const void* graph_args_[4] = {nullptr, nullptr, nullptr, nullptr};

@@ -9,6 +9,7 @@
 //  k_gather_adj     CIC gather of a and alpha (Eq. 49 F line) + reverse kicks and drift of
 //                   Eq. 49, FP64 partials of the theta terms of Eq. 51; bin counts as above
 //  k_adjoint_init   xi_n = dJ/dx_n (density cotangent through the CIC weight gradient), pi_n
+//  k_obs_cotangent  the same cotangent of an observed intermediate state, added to xi_j
 //  k_density_out, k_mse, k_za_mul, k_za_adj_mul, k_ic_state, k_ic_adj_prep, k_final_theta,
 //  k_lpt_hess, k_lpt_source, k_lpt_source_adj, k_lpt_hess_adj, k_ic_state2
 #pragma once
@@ -432,6 +433,29 @@ k_gather_adj(Geo<T> g, T mass, T* __restrict__ s, T* __restrict__ p, T* __restri
   }
 }
 
+// xv += m sum_g grad_x W(g - x_i) D(g) over the 8 CIC corners of particle i at
+// displacement sv: a density cotangent D carried to the particle position through the
+// weight gradient (floor convention, -1/l and +1/l per axis).
+template <typename T>
+__device__ __forceinline__ void cic_grad_gather(const Geo<T>& g, long long i, const T sv[3], const T* D, T mass,
+                                                T xv[3]) {
+  const T il = g.inv_l;
+  int cell[3];
+  T t[3];
+  cic_cell(g, i, sv, cell, t);
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+    const T w0 = (d & 4) ? t[0] : (T)1 - t[0];
+    const T w1 = (d & 2) ? t[1] : (T)1 - t[1];
+    const T w2 = (d & 1) ? t[2] : (T)1 - t[2];
+    const T g0 = (d & 4) ? il : -il, g1 = (d & 2) ? il : -il, g2 = (d & 1) ? il : -il;
+    const T h = mass * __ldg(D + corner_index(g, cell, d));
+    xv[0] += g0 * w1 * w2 * h;
+    xv[1] += w0 * g1 * w2 * h;
+    xv[2] += w0 * w1 * g2 * h;
+  }
+}
+
 // xi = m sum_g grad W(g - x) dJ/ddelta(g) (+ dJ/dx);  pi = dJ/dp (or 0)
 template <typename T>
 __global__ void __launch_bounds__(kPtclThreads)
@@ -440,28 +464,13 @@ k_adjoint_init(Geo<T> g, T mass, const T* __restrict__ s, const T* __restrict__ 
   __shared__ float shf[kPtclThreads / 32];
   const int b = blockIdx.y;
   const long long po = (long long)b * 3 * g.N;
-  const T il = g.inv_l;
   float mx[3] = {0.f, 0.f, 0.f};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
        i += (long long)gridDim.x * blockDim.x) {
     T xv[3] = {0, 0, 0};
     if (djdd) {
       const T sv[3] = {s[po + i], s[po + g.N + i], s[po + 2 * g.N + i]};
-      int cell[3];
-      T t[3];
-      cic_cell(g, i, sv, cell, t);
-      const T* D = djdd + (long long)b * g.M;
-#pragma unroll
-      for (int d = 0; d < 8; ++d) {
-        const T w0 = (d & 4) ? t[0] : (T)1 - t[0];
-        const T w1 = (d & 2) ? t[1] : (T)1 - t[1];
-        const T w2 = (d & 1) ? t[2] : (T)1 - t[2];
-        const T g0 = (d & 4) ? il : -il, g1 = (d & 2) ? il : -il, g2 = (d & 1) ? il : -il;
-        const T h = mass * __ldg(D + corner_index(g, cell, d));
-        xv[0] += g0 * w1 * w2 * h;
-        xv[1] += w0 * g1 * w2 * h;
-        xv[2] += w0 * w1 * g2 * h;
-      }
+      cic_grad_gather(g, i, sv, djdd + (long long)b * g.M, mass, xv);
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -476,6 +485,31 @@ k_adjoint_init(Geo<T> g, T mass, const T* __restrict__ s, const T* __restrict__ 
   for (int c = 0; c < 3; ++c) {
     const float m = block_max(mx[c], shf);
     if (threadIdx.x == 0) atomicMax(pimax + c * gridDim.y + b, __float_as_uint(m));
+  }
+}
+
+// Cotangent of an observed intermediate state (Sec. 2.4, objectives on z_0..z_n), added
+// when the reverse pass holds its positions x_j:  xi += m sum_g grad W dJ/d delta_j(g)
+// + dJ/dx_j.  xi enters nothing before the reverse drift of step j, so the sum is exact
+// whatever the kicks between add.
+template <typename T>
+__global__ void __launch_bounds__(kPtclThreads)
+k_obs_cotangent(Geo<T> g, T mass, const T* __restrict__ s, const T* __restrict__ djdd, const T* __restrict__ djdx,
+                T* __restrict__ xi) {
+  const int b = blockIdx.y;
+  const long long po = (long long)b * 3 * g.N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
+       i += (long long)gridDim.x * blockDim.x) {
+    T xv[3] = {0, 0, 0};
+    if (djdd) {
+      const T sv[3] = {s[po + i], s[po + g.N + i], s[po + 2 * g.N + i]};
+      cic_grad_gather(g, i, sv, djdd + (long long)b * g.M, mass, xv);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (djdx) xv[c] += djdx[po + c * g.N + i];
+      xi[po + c * g.N + i] += xv[c];
+    }
   }
 }
 
@@ -872,6 +906,43 @@ static __global__ void k_power_final(const unsigned long long* acc, const unsign
   if (i < nb) {
     if (kmean) kmean[bin] = c > 0 ? kf * ldexp((double)(long long)ksum[bin], -20) / c : 0.0;
     if (nmodes) nmodes[bin] = c;
+  }
+}
+
+// Objective on the shell power (summary statistic of Sec. 2.4), one thread per instance:
+// J = sum_b w_b (P_b - T_b)^2 in fixed bin order, and the per-bin factor of its density
+// cotangent g_b = 2 w_b (P_b - T_b) 2 V / (M^2 C_b) (0 for empty bins).
+static __global__ void k_power_loss(const double* __restrict__ pk, const double* __restrict__ nmodes,
+                                    const double* __restrict__ tgt, const double* __restrict__ w, int nb, int batch,
+                                    double two_v_m2, double* loss, double* g) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  double j = 0.0;
+  for (int i = 0; i < nb; ++i) {
+    const long long o = (long long)b * nb + i;
+    const double d = pk[o] - tgt[o];
+    j += w[o] * d * d;
+    const double c = nmodes[i];
+    g[o] = c > 0 ? 2.0 * w[o] * d * two_v_m2 / c : 0.0;
+  }
+  loss[b] = j;
+}
+
+// Cotangent spectrum g_b(|n|) delta^ in place over the half spectrum (bins b < nb, 0 beyond);
+// its unnormalised inverse transform is dJ/d delta (d P_b / d delta(x) is 2V / (M^2 C_b)
+// times the inverse transform of delta^ restricted to shell b).
+template <typename T>
+__global__ void k_power_grad(cx_t<T>* spec, int n, long long is, int nb, const double* __restrict__ g) {
+  const int b = blockIdx.y;
+  const long long tot = spec_len_cx(n);
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < tot; u += (long long)gridDim.x * blockDim.x) {
+    const Mode m = mode_of(u, n);
+    const int bin = isqrt_floor(m.f0 * m.f0 + m.f1 * m.f1 + m.f2 * m.f2);
+    const T f = bin < nb ? (T)g[(long long)b * nb + bin] : (T)0;
+    cx_t<T> v = spec[b * is + u];
+    v.x *= f;
+    v.y *= f;
+    spec[b * is + u] = v;
   }
 }
 

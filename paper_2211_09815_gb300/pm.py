@@ -18,7 +18,7 @@ SYMBOLS = ("pm_init", "pm_forward", "pm_loss_mse", "pm_adjoint", "pm_destroy", "
            "pm_last_cuda_error", "pm_scratch_bytes", "pm_op_density", "pm_op_force", "pm_op_force_vjp",
            "pm_op_fft", "pm_op_za", "pm_set_inputs", "pm_gradient", "pm_profile", "pm_profile_read",
            "pm_density_noalloc", "pm_power_spectrum", "pm_gradient_graph", "pm_get_tuning", "pm_set_tuning",
-           "pm_autotune", "pm_op_ic")
+           "pm_autotune", "pm_op_ic", "pm_loss_power", "pm_set_snapshots")
 NOALLOC_MAX_CELLS = 128 ** 3
 PROF_NAMES = ("scatter", "fft_x_r2c", "fft_cols", "fused_z_force", "fused_z_adjoint", "fft_x_c2r",
               "gather_fwd", "gather_adj", "other")
@@ -80,6 +80,8 @@ def load_library(path=LIB_PATH):
     lib.pm_op_fft.argtypes = [vp, i, vp, vp]
     lib.pm_op_za.argtypes = [vp, vp]
     lib.pm_op_ic.argtypes = [vp, vp, vp]
+    lib.pm_loss_power.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.pm_set_snapshots.argtypes = [vp, i, ctypes.POINTER(ctypes.c_int), vp, vp, vp, vp]
     lib.pm_set_inputs.argtypes = [vp, dp, vp]
     lib.pm_gradient.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.pm_profile.argtypes = [vp, i]
@@ -217,6 +219,20 @@ class PMContext:
     def op_za(self, s1):
         _check(load_library().pm_op_za(self._h, _ptr(s1, self.dtype, 3 * self.batch * self.N)), "pm_op_za")
 
+    def set_snapshots(self, steps, disp=None, dens=None, ddisp=None, ddens=None):
+        """Observe the states after the given steps (ascending, 0..n_steps): each forward
+        writes s_j into disp[q] and delta_j into dens[q]; each adjoint adds the cotangents
+        ddisp[q] (dJ/dx_j) and ddens[q] (dJ/d delta_j).  Buffers: CUDA tensors of
+        len(steps) x batch x (3 N or M) elements, kept referenced here while in use."""
+        steps = [int(j) for j in steps]
+        ns = len(steps)
+        v, m = ns * 3 * self.batch * self.N, ns * self.batch * self.M
+        arr = (ctypes.c_int * max(ns, 1))(*steps)
+        _check(load_library().pm_set_snapshots(self._h, ns, arr, _ptr(disp, self.dtype, v, "disp"),
+                                               _ptr(dens, self.dtype, m, "dens"), _ptr(ddisp, self.dtype, v, "ddisp"),
+                                               _ptr(ddens, self.dtype, m, "ddens")), "pm_set_snapshots")
+        self._snapshot_buffers = (disp, dens, ddisp, ddens) if ns else None
+
     def op_ic(self, s0=None, p0=None):
         """Initial state (s0, p0) at a0 of the context's LPT order."""
         v = 3 * self.batch * self.N
@@ -259,6 +275,21 @@ class PMContext:
                                                 pk.ctypes.data_as(f), km.ctypes.data_as(f), nm.ctypes.data_as(f)),
                "pm_power_spectrum")
         return km, pk, nm
+
+    def loss_power(self, pk_target, weights, djdd, dens=None):
+        """Objective sum_b w_b (P_b - T_b)^2 on the shell power of ``dens`` (the last forward
+        density when None) and its cotangent into ``djdd``; pk_target, weights: host
+        arrays [batch, n_mesh/2].  Returns the per-instance loss (float64 numpy)."""
+        import numpy as np
+        nb = self.n_mesh // 2
+        t = np.ascontiguousarray(np.broadcast_to(np.asarray(pk_target, dtype=np.float64), (self.batch, nb)))
+        w = np.ascontiguousarray(np.broadcast_to(np.asarray(weights, dtype=np.float64), (self.batch, nb)))
+        loss = np.zeros(self.batch)
+        f = ctypes.POINTER(ctypes.c_double)
+        _check(load_library().pm_loss_power(self._h, _ptr(dens, self.dtype, self.batch * self.M, "dens"),
+                                            t.ctypes.data_as(f), w.ctypes.data_as(f), loss.ctypes.data_as(f),
+                                            _ptr(djdd, self.dtype, self.batch * self.M, "djdd")), "pm_loss_power")
+        return loss
 
     def profile(self, enable=True):
         _check(load_library().pm_profile(self._h, int(enable)), "pm_profile")

@@ -105,3 +105,73 @@ def test_particle_state_objective_gradient_matches_oracle(precision):
     else:
         assert cosine(g, adj["grad_omega"]) >= 0.999
         assert rel_l2(g, adj["grad_omega"]) <= 1e-2
+
+
+SNAP = dict(box=32.0, n_mesh=32, n_ptcl=16, n_steps=6)
+SNAP_STEPS = (0, 2, 5, 6)
+
+
+def _snapshot_cotangents():
+    """Seeded cotangents of the observed densities and displacements (the same on both
+    sides; none derived from either path's outputs)."""
+    rng = np.random.default_rng(51)
+    N, M = SNAP["n_ptcl"] ** 3, SNAP["n_mesh"] ** 3
+    ddens = rng.normal(size=(len(SNAP_STEPS), M)) / M
+    ddisp = rng.normal(size=(len(SNAP_STEPS), 3, N)) * 1e-3
+    return ddens, ddisp
+
+
+@pytest.mark.parametrize("precision,ckpt", [(1, 0), (1, 2), (0, 0)])
+def test_snapshot_observations_match_oracle(precision, ckpt):
+    """pm_set_snapshots: the forward writes s_j and delta_j at the observed steps, and the
+    adjoint adds their cotangents when the reverse pass reaches each step (reverse time
+    integration, or resumption from checkpoints every 2 steps)."""
+    torch = torch_cuda()
+    cfg = oracle_cfg(**SNAP)
+    om = inputs.white_noise(SNAP["n_ptcl"], 1).astype(np.float64)
+    fwd = opm.forward(om, THETA, cfg, store_every=ckpt, snapshots=SNAP_STEPS)
+    ddens, ddisp = _snapshot_cotangents()
+    obs = {j: (ddens[q], ddisp[q]) for q, j in enumerate(SNAP_STEPS)}
+    adj = opm.adjoint(om, THETA, cfg, fwd, obs=obs, ckpt=fwd["store"] if ckpt else None)
+
+    ctx, *_ = make_ctx(SNAP["box"], SNAP["n_mesh"], SNAP["n_ptcl"], SNAP["n_steps"], precision=precision,
+                       ckpt_every=ckpt)
+    N, M, ns = SNAP["n_ptcl"] ** 3, SNAP["n_mesh"] ** 3, len(SNAP_STEPS)
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a.ravel())).to("cuda", ctx.dtype)
+    disp = torch.empty(ns * 3 * N, device="cuda", dtype=ctx.dtype)
+    dens = torch.empty(ns * M, device="cuda", dtype=ctx.dtype)
+    gd, gx = to(ddens), to(ddisp)
+    ctx.set_snapshots(SNAP_STEPS, disp=disp, dens=dens, ddisp=gx, ddens=gd)
+    ctx.forward()
+    gw = torch.empty(N, device="cuda", dtype=ctx.dtype)
+    gt = torch.zeros(5, dtype=torch.float64)
+    ctx.adjoint(grad_omega=gw, grad_theta=gt)
+    ctx.set_snapshots([])
+    ctx.close()
+    disp = disp.cpu().numpy().reshape(ns, 3, N)
+    dens = dens.cpu().numpy().reshape(ns, M)
+    g = gw.cpu().numpy()
+    if precision:
+        for q, j in enumerate(SNAP_STEPS):
+            assert rel_l2(disp[q], fwd["snap"][j][0]) < 1e-9
+            assert np.max(np.abs(dens[q] - fwd["snap"][j][1].ravel())) < 1e-8
+        assert rel_l2(g, adj["grad_omega"]) < 1e-8
+        assert np.allclose(gt.numpy(), adj["grad_theta"], rtol=1e-8, atol=0)
+    else:
+        cell = SNAP["box"] / SNAP["n_mesh"]
+        for q, j in enumerate(SNAP_STEPS):
+            assert np.sqrt(np.mean((disp[q] - fwd["snap"][j][0]) ** 2)) < 1e-3 * cell
+        assert cosine(g, adj["grad_omega"]) >= 0.999
+        assert rel_l2(g, adj["grad_omega"]) <= 1e-2
+
+
+def test_set_snapshots_rejects_bad_step_lists():
+    torch_cuda()
+    from paper_2211_09815_gb300 import pm
+    ctx, *_ = make_ctx(50.0, 32, 16, 4)
+    for bad in ([3, 2], [1, 1], [-1], [5], list(range(65))):
+        with pytest.raises(pm.PMError):
+            ctx.set_snapshots(bad)
+    ctx.set_snapshots([0, 4])
+    ctx.set_snapshots([])
+    ctx.close()
