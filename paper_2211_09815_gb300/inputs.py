@@ -60,3 +60,14 @@ def ensemble_theta(batch, seed=1000):
         u = uniform01(seed + b, 3)
         th[b] = (1.8e-9 + 0.6e-9 * u[0], 0.94 + 0.05 * u[1], 0.25 + 0.10 * u[2], 0.049, 0.68)
     return th
+
+
+def cross_target(n_mesh, half_width=1.5, amplitude=2.0):
+    """Synthetic target pattern for the white-noise optimisation (the paper's target image
+    is not available): overdensity ``amplitude`` in three orthogonal bars of half-width
+    ``half_width`` cells through the box centre, mean subtracted; float64 (n, n, n)."""
+    c = np.arange(n_mesh) - n_mesh / 2 + 0.5
+    x, y, z = np.meshgrid(c, c, c, indexing="ij")
+    near = lambda u: np.abs(u) < half_width
+    inside = (near(y) & near(z)) | (near(x) & near(z)) | (near(x) & near(y))
+    return amplitude * (inside - inside.mean())
