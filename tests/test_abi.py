@@ -52,3 +52,14 @@ def test_invalid_configs_are_rejected_on_the_host():
     ok = pm.PMConfig(100.0, 32, 16, 10, 1 / 64, 1.0, 0, 0, 0, 1)
     assert lib.pm_init(ctypes.byref(h), ctypes.byref(ok), nan, dummy, None) == 4
     assert lib.pm_forward(None, None, None, None) == 1
+
+
+def test_new_entry_points_reject_null_arguments_on_the_host():
+    """pm_op_ic, pm_loss_power and pm_set_snapshots check their pointers before any CUDA
+    call."""
+    import ctypes
+    lib = pm.load_library()
+    d = (ctypes.c_double * 4)()
+    assert lib.pm_op_ic(None, None, None) == 1
+    assert lib.pm_loss_power(None, None, d, d, None, ctypes.c_void_p(16)) == 1
+    assert lib.pm_set_snapshots(None, 0, None, None, None, None, None) == 1
