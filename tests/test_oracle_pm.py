@@ -358,6 +358,31 @@ def test_lpt2_theta_derivative_vs_central_fd(j):
     assert np.linalg.norm(an - fd) < 1e-8 * np.linalg.norm(fd)
 
 
+def test_lpt2_density_matches_second_order_perturbation_theory():
+    """Physics pin of the whole 2LPT chain (Eqs. 2-4 with the App. A growth at Omega_m = 1,
+    D1 = a, D2 = 3/7 a^2): for delta1 = eps (cos k q0 + cos k q1) the particle density's
+    Fourier coefficient at k1 + k2 is 2 F2(k1, k2) (eps/2)^2 + O(eps^4), with the
+    Eulerian perturbation-theory kernel F2 = 5/7 for perpendicular equal modes, i.e.
+    (5/14) eps^2; the Zel'dovich displacement alone gives the kernel 1/2, i.e. eps^2 / 4.
+    A wrong sign of the source or of D2 gives 1/7."""
+    n, box = 32, 100.0
+    cfg = pm.PMConfig(box=box, n_mesh=n, n_ptcl=n)
+    q = np.indices((n, n, n)).reshape(3, -1).astype(np.float64) * (box / n)
+    k, eps = 2 * np.pi / box, 1e-3
+    d1 = eps * (np.cos(k * q[0]) + np.cos(k * q[1])).reshape(n, n, n)
+    s1 = pm.lpt2_displacement_from_source(d1, cfg)        # the same ik/k^2 map as s1 from delta1
+    s2 = _lpt2_of_field(d1, cfg)
+    a = np.array([1.0])
+    dd1 = cosmo.growth_factors(a, 1.0)[0][0]
+    dd2 = cosmo.growth_factors2(a, 1.0)[0][0]
+
+    def coefficient(x):
+        return np.mean(np.exp(-1j * (k * x[0] + k * x[1]))) / eps ** 2
+
+    assert abs(coefficient(q + dd1 * s1) - 0.25) < 1e-5
+    assert abs(coefficient(q + dd1 * s1 + dd2 * s2) - 5.0 / 14.0) < 1e-5
+
+
 FD_CFG2 = pm.PMConfig(box=24.0, n_mesh=16, n_ptcl=8, n_steps=4, lpt_order=2)
 
 
