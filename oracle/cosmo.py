@@ -180,6 +180,18 @@ def kdk_factors(a_grid, Om):
     return k1, dd, k2
 
 
+def partial_drift_factor(a, a_grid, j, Om):
+    """Drift factor from a_j to a in (a_j, a_{j+1}] with the half-step momentum p_{j+1/2}:
+    the FastPM drift D of Sec. 2.3 (Eq. 15) evaluated up to a instead of a_{j+1},
+    [D1(a) - D1(a_j)] / G_D(a_{j+1/2}) -- the reading used for positions interpolated
+    between two steps (Sec. 2.4 names such snapshots without a formula).  Equals D_{j+1}
+    of ``kdk_factors`` at a = a_{j+1}."""
+    a_grid = np.asarray(a_grid, dtype=np.float64)
+    d1 = growth_factors(np.array([a_grid[j], a]), Om)[0]
+    gdh = growth_factors(np.array([0.5 * (a_grid[j] + a_grid[j + 1])]), Om)[2]
+    return (d1[1] - d1[0]) / gdh[0]
+
+
 def transfer_eh_nowiggle(k, Om, Ob, h, tcmb=T_CMB):
     """Eisenstein & Hu (1998) no-wiggle transfer function, k in h/Mpc (Sec. 2.1).
 

@@ -358,7 +358,7 @@ def force_vjp(x, pi, f, Om, cfg):
 
 # ------------------------------------------------------------------------- integrate
 
-def forward(omega, theta, cfg, store_every=0, force_fn=None, snapshots=()):
+def forward(omega, theta, cfg, store_every=0, force_fn=None, snapshots=(), snapshot_a=()):
     """Zel'dovich ICs then the FastPM kick-drift-kick leapfrog (Sec. 2.3, Eq. 16).
 
     a_0 = F_0 first; then for i = 1..n: p += a K1_i; s += p D_i; a = F_i; p += a K2_i.
@@ -366,9 +366,12 @@ def forward(omega, theta, cfg, store_every=0, force_fn=None, snapshots=()):
     density delta_n at a_n, and (store_every > 0) the states (s_j, p_j) at steps
     j = 0, k, 2k, ... for the checkpointed adjoint.  ``force_fn(x, s)`` replaces the PM
     force (used by the Zel'dovich-exactness pin with the linear-theory force).
-    ``snapshots``: steps j whose displacement s_j and density delta_j are returned in
-    "snap" as {j: (s_j, delta_j)} -- observations of intermediate states (Sec. 2.4: the
-    objective may depend on every z_0..z_n).
+    ``snapshots``: steps j whose displacement s_j, density delta_j and momentum p_j are
+    returned in "snap" as {j: (s_j, delta_j, p_j)} -- observations of intermediate states
+    (Sec. 2.4: the objective may depend on every z_0..z_n).  ``snapshot_a``: scale factors
+    a in (a_0, a_n] whose positions are interpolated between the two enclosing steps,
+    s(a) = s_j + p_{j+1/2} Dp_j(a) with the partial drift factor of
+    ``cosmo.partial_drift_factor``; returned in "snap_a" as {a: (s(a), delta(a))}.
     """
     q = lattice(cfg)
     Om = theta[2]
@@ -381,19 +384,25 @@ def forward(omega, theta, cfg, store_every=0, force_fn=None, snapshots=()):
     snap = {}
     if store_every:
         store[0] = (s.copy(), p.copy())
+    snap_a = {}
+    agrid = cosmo.time_grid(cfg.a0, cfg.a1, cfg.n_steps)
     if 0 in snapshots:
-        snap[0] = (s.copy(), density(q + s, cfg))
+        snap[0] = (s.copy(), density(q + s, cfg), p.copy())
     a = force_fn(q + s, s)
     for i in range(1, cfg.n_steps + 1):
         p = p + a * k1[i - 1]
+        for a_s in snapshot_a:
+            if agrid[i - 1] < a_s <= agrid[i]:
+                s_a = s + p * cosmo.partial_drift_factor(a_s, agrid, i - 1, Om)
+                snap_a[a_s] = (s_a, density(q + s_a, cfg))
         s = s + p * dd[i - 1]
         a = force_fn(q + s, s)
         p = p + a * k2[i - 1]
         if store_every and i % store_every == 0:
             store[i] = (s.copy(), p.copy())
         if i in snapshots:
-            snap[i] = (s.copy(), density(q + s, cfg))
-    return dict(s=s, p=p, a=a, delta=density(q + s, cfg), store=store, snap=snap)
+            snap[i] = (s.copy(), density(q + s, cfg), p.copy())
+    return dict(s=s, p=p, a=a, delta=density(q + s, cfg), store=store, snap=snap, snap_a=snap_a)
 
 
 def mse_loss(delta, target):
@@ -421,7 +430,7 @@ def _observation_cotangent(x, dj_ddelta, dj_ds, cfg):
     return out
 
 
-def adjoint(omega, theta, cfg, fwd, dj_ddelta=None, dj_ds=None, dj_dp=None, ckpt=None, obs=None):
+def adjoint(omega, theta, cfg, fwd, dj_ddelta=None, dj_ds=None, dj_dp=None, ckpt=None, obs=None, obs_a=None):
     """Discrete adjoint with reverse time integration (Sec. 3.6, Eqs. 49-51).
 
     Starts from the final state in ``fwd`` and integrates the leapfrog backward jointly
@@ -434,9 +443,15 @@ def adjoint(omega, theta, cfg, fwd, dj_ddelta=None, dj_ds=None, dj_dp=None, ckpt
     (D(t_c,t_b,t_a) = -D(t_c,t_a,t_b) turns the printed signs into these.)  Finally
     (Eq. 51) dJ/domega = (D1 xi_0 + G_D pi_0) . ds1/domega and the theta terms of the
     initial conditions; with 2LPT also (D2 xi_0 + G_D2 pi_0) . ds2/domega and the s2 terms.
-    ``obs`` maps steps j to cotangents (dJ/d delta_j or None, dJ/ds_j or None) of
-    observed intermediate states; each is added to xi when the reverse pass holds x_j
-    (after the last reverse kick that ends at step j, before the reverse drift of step j).  ``ckpt`` maps step j to a stored (s_j, p_j) that replaces the
+    ``obs`` maps steps j to cotangents (dJ/d delta_j or None, dJ/ds_j or None[, dJ/dp_j])
+    of observed intermediate states; the position terms are added to xi when the reverse
+    pass holds x_j (after the last reverse kick that ends at step j, before the reverse
+    drift of step j); dJ/dp_j is added to pi there, and the force VJP that the next reverse
+    kick (K2_j, the one that made p_j) uses is extended by its share, alpha(pi + v) =
+    alpha(pi) + alpha(v).  ``obs_a`` maps interpolated scale factors a (see ``forward``) to
+    (dJ/d delta(a) or None, dJ/ds(a) or None): with u their position cotangent at x(a),
+    xi_j += u and pi_{j+1/2} += Dp_j(a) u right after the reverse drift of step j + 1 (before
+    the force VJP at x_j), and the theta term (u . p_{j+1/2}) dDp_j/dOmega_m.  ``ckpt`` maps step j to a stored (s_j, p_j) that replaces the
     reverse-integrated state when step j is reached (piecewise resumption, Sec. 3.5).
     Returns dict(grad_omega (n_ptcl^3,), grad_theta (5,), s0, p0 (reverse-integrated)).
     """
@@ -453,10 +468,13 @@ def adjoint(omega, theta, cfg, fwd, dj_ddelta=None, dj_ds=None, dj_dp=None, ckpt
     g_om = 0.0
     x = q + s
     obs = obs or {}
+    obs_a = obs_a or {}
     xi = _observation_cotangent(x, dj_ddelta, dj_ds, cfg)
-    if n in obs:
-        xi += _observation_cotangent(x, *obs[n], cfg)
     pi = np.zeros_like(s) if dj_dp is None else np.array(dj_dp, dtype=np.float64)
+    if n in obs:
+        xi += _observation_cotangent(x, *obs[n][:2], cfg)
+        if len(obs[n]) > 2 and obs[n][2] is not None:
+            pi = pi + obs[n][2]
     a, f = pm_force(x, Om, cfg)
     alpha = force_vjp(x, pi, f, Om, cfg)
     for i in range(n, 0, -1):
@@ -469,6 +487,14 @@ def adjoint(omega, theta, cfg, fwd, dj_ddelta=None, dj_ds=None, dj_dp=None, ckpt
         pi = pi + xi * dd[i - 1]
         if (i - 1) in ckpt:
             s = ckpt[i - 1][0].copy()
+        for a_s, (djd, djs) in obs_a.items():
+            if agrid[i - 1] < a_s <= agrid[i]:
+                fac = cosmo.partial_drift_factor(a_s, agrid, i - 1, Om)
+                dfac = cosmo.complex_step(lambda th: cosmo.partial_drift_factor(a_s, agrid, i - 1, th[2]), theta, 2)
+                u = _observation_cotangent(q + s + p * fac, djd, djs, cfg)
+                xi = xi + u
+                pi = pi + fac * u
+                g_om += float(np.sum(u * p)) * dfac
         x = q + s
         a, f = pm_force(x, Om, cfg)
         alpha = force_vjp(x, pi, f, Om, cfg)
@@ -479,7 +505,10 @@ def adjoint(omega, theta, cfg, fwd, dj_ddelta=None, dj_ds=None, dj_dp=None, ckpt
         if (i - 1) in ckpt:
             p = ckpt[i - 1][1].copy()
         if (i - 1) in obs:
-            xi = xi + _observation_cotangent(x, *obs[i - 1], cfg)
+            xi = xi + _observation_cotangent(x, *obs[i - 1][:2], cfg)
+            if len(obs[i - 1]) > 2 and obs[i - 1][2] is not None:
+                pi = pi + obs[i - 1][2]
+                alpha = alpha + force_vjp(x, obs[i - 1][2], f, Om, cfg)
     # initial conditions (Eq. 51): x0 = q + D1(a0) s1, p0 = G_D(a0) s1
     d1, _, gd, _ = cosmo.growth_factors(np.array([cfg.a0]), Om)
     dd1 = cosmo.complex_step(lambda th: cosmo.growth_factors(np.array([cfg.a0]), th[2])[0], theta, 2)[0]

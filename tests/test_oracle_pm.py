@@ -619,3 +619,57 @@ def test_snapshot_objective_gradient_theta_vs_central_fd(snapshot_case, j):
     tm[j] -= h
     fd = (_snapshot_loss(om, tp, targets, u) - _snapshot_loss(om, tm, targets, u)) / (2 * h)
     assert abs(fd - adj["grad_theta"][j]) <= 1e-6 * abs(fd) + 1e-12
+
+
+A_OBS = (0.33, 0.8)     # between steps of SNAP_CFG's grid (1/64, 0.26, 0.51, 0.75, 1)
+
+
+def _interp_loss(om, th, target, u, v):
+    """J = MSE(delta(0.33), target) + <u, s(0.8)> + <v, p_2>: positions interpolated between
+    steps and a momentum observed at an intermediate step."""
+    fwd = pm.forward(om, th, SNAP_CFG, snapshots=(2,), snapshot_a=A_OBS)
+    j = pm.mse_loss(fwd["snap_a"][A_OBS[0]][1], target)[0]
+    return j + float(np.sum(u * fwd["snap_a"][A_OBS[1]][0])) + float(np.sum(v * fwd["snap"][2][2]))
+
+
+@pytest.fixture(scope="module")
+def interp_case():
+    om = inputs.white_noise(8, 1).astype(np.float64)
+    target = pm.forward(inputs.white_noise(8, 2).astype(np.float64), THETA, SNAP_CFG,
+                        snapshot_a=A_OBS)["snap_a"][A_OBS[0]][1]
+    rng = np.random.default_rng(25)
+    u = rng.normal(size=(3, 8 ** 3))
+    v = rng.normal(size=(3, 8 ** 3)) * 10.0
+    fwd = pm.forward(om, THETA, SNAP_CFG, snapshots=(2,), snapshot_a=A_OBS)
+    obs_a = {A_OBS[0]: (pm.mse_loss(fwd["snap_a"][A_OBS[0]][1], target)[1], None), A_OBS[1]: (None, u)}
+    adj = pm.adjoint(om, THETA, SNAP_CFG, fwd, obs={2: (None, None, v)}, obs_a=obs_a)
+    return om, target, u, v, adj
+
+
+def test_interpolated_snapshot_at_a_step_is_that_step():
+    """The interpolated position at a = a_j is the state after step j (the partial drift
+    factor equals the full one there)."""
+    om = inputs.white_noise(8, 1).astype(np.float64)
+    agrid = cosmo.time_grid(SNAP_CFG.a0, SNAP_CFG.a1, SNAP_CFG.n_steps)
+    fwd = pm.forward(om, THETA, SNAP_CFG, snapshots=(3,), snapshot_a=(float(agrid[3]),))
+    assert np.allclose(fwd["snap_a"][float(agrid[3])][0], fwd["snap"][3][0], rtol=0, atol=1e-12)
+
+
+def test_interpolated_and_momentum_observations_gradient_vs_central_fd(interp_case):
+    om, target, u, v, adj = interp_case
+    w = np.random.default_rng(26).normal(size=om.shape)
+    h = 1e-6
+    fd = (_interp_loss(om + h * w, THETA, target, u, v) - _interp_loss(om - h * w, THETA, target, u, v)) / (2 * h)
+    assert abs(fd - np.sum(adj["grad_omega"] * w.ravel())) <= 1e-6 * abs(fd)
+
+
+@pytest.mark.parametrize("j", [0, 2])
+def test_interpolated_and_momentum_observations_theta_vs_central_fd(interp_case, j):
+    """Omega_m enters the partial drift factors as well as the dynamics."""
+    om, target, u, v, adj = interp_case
+    h = 1e-6 * abs(THETA[j])
+    tp, tm = list(THETA), list(THETA)
+    tp[j] += h
+    tm[j] -= h
+    fd = (_interp_loss(om, tp, target, u, v) - _interp_loss(om, tm, target, u, v)) / (2 * h)
+    assert abs(fd - adj["grad_theta"][j]) <= 1e-6 * abs(fd) + 1e-12
