@@ -70,6 +70,26 @@ def test_gather_gradient_matches_finite_difference():
         assert np.allclose(fd, g[c], rtol=1e-6, atol=1e-7)
 
 
+def test_gather_gradient_at_a_cell_face_is_the_right_derivative():
+    """At a cell face (u = x/l an integer) the CIC weight of Eq. 10 has a kink; the floor
+    convention takes the right derivative, and the one-sided differences from the left
+    and the right differ by the jump of the weight gradient (the discontinuity behind
+    the FP32/FP64 gradient differences of trajectories that cross a face)."""
+    cfg = pm.PMConfig(box=10.0, n_mesh=8, n_ptcl=4)
+    rng = np.random.default_rng(3)
+    mesh = rng.normal(size=(8, 8, 8))
+    x = np.array([[3.0 * cfg.cell], [2.4 * cfg.cell], [5.7 * cfg.cell]])
+    g = pm.cic_gather_grad(mesh, x, cfg)[0, 0]
+    h = 1e-7
+    xr, xl = x.copy(), x.copy()
+    xr[0] += h
+    xl[0] -= h
+    right = (pm.cic_gather(mesh, xr, cfg)[0] - pm.cic_gather(mesh, x, cfg)[0]) / h
+    left = (pm.cic_gather(mesh, x, cfg)[0] - pm.cic_gather(mesh, xl, cfg)[0]) / h
+    assert abs(g - right) < 1e-6 * max(1.0, abs(g))
+    assert abs(right - left) > 1e-2 * max(abs(right), abs(left))
+
+
 # -------------------------------------------------------------------------- Fourier
 
 def _naive_force(delta, Om, box):
