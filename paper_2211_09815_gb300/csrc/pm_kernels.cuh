@@ -973,13 +973,4 @@ __global__ void k_std_to_spec(const cx_t<T>* __restrict__ in, cx_t<T>* __restric
   }
 }
 
-// strided copy of real meshes between layouts with different instance strides
-template <typename T>
-__global__ void k_copy_strided(const T* __restrict__ in, long long in_is, T* __restrict__ out, long long out_is,
-                               long long count) {
-  const int b = blockIdx.y;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
-    out[b * out_is + i] = in[b * in_is + i];
-}
-
 }  // namespace pmgb
