@@ -192,24 +192,46 @@ def partial_drift_factor(a, a_grid, j, Om):
     return (d1[1] - d1[0]) / gdh[0]
 
 
+def sound_horizon_eh(omh2, obh2):
+    """Sound horizon at the drag epoch in Mpc (not Mpc/h): the Eisenstein & Hu (1998,
+    ApJ 496, 605) fit, their Eq. 26, s = 44.5 ln(9.83 / Omega_m h^2) /
+    sqrt(1 + 10 (Omega_b h^2)^(3/4)).  Pinned against Planck 2018's r_drag
+    (tests/test_oracle_cosmo.py)."""
+    return 44.5 * np.log(9.83 / omh2) / np.sqrt(1.0 + 10.0 * obh2 ** 0.75)
+
+
+def alpha_gamma(omh2, fb):
+    """Small-scale suppression of the shape parameter by baryons, Eisenstein & Hu (1998)
+    Eq. 31: alpha_Gamma = 1 - 0.328 ln(431 Omega_m h^2) f_b + 0.38 ln(22.3 Omega_m h^2)
+    f_b^2, f_b = Omega_b / Omega_m.  Pinned only through sigma_8 (the f_b^2 term moves
+    sigma_8 by 0.2%: parity unpinned beyond that)."""
+    return 1.0 - 0.328 * np.log(431.0 * omh2) * fb + 0.38 * np.log(22.3 * omh2) * fb * fb
+
+
+def gamma_eff(k, Om, Ob, h):
+    """Scale-dependent shape parameter of the no-wiggle transfer function, Eisenstein & Hu
+    (1998) Eq. 30, k in h/Mpc: Gamma_eff = Omega_m h [alpha + (1 - alpha) /
+    (1 + (0.43 k s)^4)] with k s in Mpc units; Omega_m h on large scales, alpha Omega_m h on
+    small scales (pinned by those two limits)."""
+    omh2 = Om * h * h
+    alpha = alpha_gamma(omh2, Ob / Om)
+    s = sound_horizon_eh(omh2, Ob * h * h)
+    return Om * h * (alpha + (1.0 - alpha) / (1.0 + (0.43 * k * h * s) ** 4))
+
+
 def transfer_eh_nowiggle(k, Om, Ob, h, tcmb=T_CMB):
     """Eisenstein & Hu (1998) no-wiggle transfer function, k in h/Mpc (Sec. 2.1).
 
     The paper names the fitting formula but does not print it.  Transcribed from
     Eisenstein & Hu 1998, ApJ 496, 605: sound horizon fit (their Eq. 26), alpha_Gamma
     (Eq. 31), Gamma_eff (Eq. 30), q (Eq. 28), T0(q) = L0 / (L0 + C0 q^2) (Eq. 29).
-    Parity unpinned beyond the limits T -> 1 as k -> 0, monotone decrease in k and the
-    zero-baryon case (alpha_Gamma = 1).
+    Pinned by its limits (T -> 1 as k -> 0, monotone decrease, the zero-baryon case), the
+    zero-baryon form against the BBKS fit, the sound horizon against Planck 2018's r_drag
+    and sigma_8 against Planck 2018 (tests/test_oracle_cosmo.py); the f_b^2 coefficient
+    of alpha_Gamma is parity unpinned.
     """
-    omh2 = Om * h * h
-    obh2 = Ob * h * h
-    fb = Ob / Om
     theta27 = tcmb / 2.7
-    s = 44.5 * np.log(9.83 / omh2) / np.sqrt(1.0 + 10.0 * obh2 ** 0.75)
-    alpha = 1.0 - 0.328 * np.log(431.0 * omh2) * fb + 0.38 * np.log(22.3 * omh2) * fb * fb
-    k_mpc = k * h
-    gamma_eff = Om * h * (alpha + (1.0 - alpha) / (1.0 + (0.43 * k_mpc * s) ** 4))
-    q = k * theta27 ** 2 / gamma_eff
+    q = k * theta27 ** 2 / gamma_eff(k, Om, Ob, h)
     l0 = np.log(2.0 * np.e + 1.8 * q)
     c0 = 14.2 + 731.0 / (1.0 + 62.5 * q)
     return l0 / (l0 + c0 * q * q)

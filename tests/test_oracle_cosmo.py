@@ -150,3 +150,85 @@ def test_second_order_growth_matches_bouchet_fit():
         d2 = cosmo.growth_factors2(a, Om)[0]
         fit = 3.0 / 7.0 * d1 ** 2 * cosmo.omega_m_of_a(a, Om) ** (-1.0 / 143.0)
         assert np.all(np.abs(d2 / fit - 1) < 1e-3)
+
+
+# ------------------------------------------- linear power spectrum against published values
+# Planck 2018 results VI (Planck Collaboration, A&A 641, A6, 2020), Table 2, column
+# "TT,TE,EE+lowE+lensing": ln(10^10 A_s) = 3.044, n_s = 0.9649, Omega_m = 0.3153,
+# Omega_b h^2 = 0.02237, H0 = 67.36 km/s/Mpc; derived sigma_8 = 0.8111 and
+# r_drag = 147.09 Mpc.
+PLANCK18_H = 0.6736
+PLANCK18 = (np.exp(3.044) * 1e-10, 0.9649, 0.3153, 0.02237 / PLANCK18_H ** 2, PLANCK18_H)
+PLANCK18_SIGMA8 = 0.8111
+PLANCK18_RDRAG_MPC = 147.09
+
+
+def _sigma8(theta):
+    """RMS linear overdensity in spheres of 8 Mpc/h at a = 1: P_lin of Eq. 7 times D1(1)^2
+    (P_lin is normalised to D1 = a early), top-hat window 3 (sin x - x cos x) / x^3."""
+    d1 = cosmo.growth_factors(np.array([1.0]), theta[2])[0][0]
+
+    def integrand(lnk):
+        k = np.exp(lnk)
+        x = 8.0 * k
+        w = 3.0 * (np.sin(x) - x * np.cos(x)) / x ** 3
+        return k ** 3 * cosmo.plin(k, theta) / (2.0 * np.pi ** 2) * w * w
+
+    val, _ = integrate.quad(integrand, np.log(1e-5), np.log(1e2), limit=500, epsrel=1e-10)
+    return np.sqrt(val) * d1
+
+
+def test_sigma8_against_planck2018():
+    """The amplitude chain of Eq. 7 (4/25 A_s, (c k / H0)^4 / Omega_m^2, the pivot in h
+    units, the growth normalisation D1 -> a) and T(k) together give sigma_8 within 5% of
+    Planck 2018's 0.8111 at Planck's parameters.  The oracle lands 3% high: Planck's base
+    model carries 0.06 eV of neutrino mass (about 2% less sigma_8) and the no-wiggle fit
+    is a smooth approximation.  A wrong amplitude factor (2/5 for 4/25), a renormalised
+    D1(1) = 1 (+27%) or a wrong power of c/H0 fail it."""
+    s8 = _sigma8(PLANCK18)
+    assert abs(s8 / PLANCK18_SIGMA8 - 1) < 0.05, s8
+
+
+def test_sound_horizon_against_planck2018_rdrag():
+    """Eisenstein & Hu (1998) Eq. 26 approximates the sound horizon at the drag epoch to a
+    few per cent: at Planck 2018's Omega_m h^2 and Omega_b h^2 it is within 3% of the
+    published r_drag = 147.09 Mpc (the oracle gives 149.8 Mpc)."""
+    h = PLANCK18_H
+    s = cosmo.sound_horizon_eh(PLANCK18[2] * h * h, PLANCK18[3] * h * h)
+    assert abs(s / PLANCK18_RDRAG_MPC - 1) < 0.03, s
+
+
+def test_gamma_eff_limits_with_baryons():
+    """Eq. 30 of Eisenstein & Hu (1998) at finite f_b: Gamma_eff -> Omega_m h on scales
+    much larger than the sound horizon and -> alpha_Gamma Omega_m h on much smaller
+    scales, with alpha_Gamma < 1 (baryons suppress small-scale power)."""
+    Om, Ob, h = 0.31, 0.049, 0.68
+    alpha = cosmo.alpha_gamma(Om * h * h, Ob / Om)
+    assert 0.7 < alpha < 0.9
+    assert abs(cosmo.gamma_eff(1e-5, Om, Ob, h) / (Om * h) - 1) < 1e-9
+    assert abs(cosmo.gamma_eff(1e3, Om, Ob, h) / (alpha * Om * h) - 1) < 1e-9
+
+
+def test_transfer_zero_baryon_against_bbks():
+    """Without baryons the no-wiggle form reduces to a pure CDM transfer function, which
+    the Bardeen, Bond, Kaiser & Szalay (1986, ApJ 304, 15, their Eq. G3) fit also
+    describes: T = ln(1 + 2.34 q) / (2.34 q) [1 + 3.89 q + (16.1 q)^2 + (5.46 q)^3 +
+    (6.71 q)^4]^(-1/4), q = k / (Omega_m h) with k in h/Mpc.  The two independent fits agree
+    within 7% from 1e-3 to 10 h/Mpc (the largest gap, 5.6%, near k = 0.1)."""
+    Om, h = 0.31, 0.68
+    k = np.logspace(-3, 1, 60)
+    t = cosmo.transfer_eh_nowiggle(k, Om, 0.0, h)
+    q = k / (Om * h)
+    bbks = np.log(1 + 2.34 * q) / (2.34 * q) * (1 + 3.89 * q + (16.1 * q) ** 2 + (5.46 * q) ** 3
+                                                 + (6.71 * q) ** 4) ** -0.25
+    assert np.all(np.abs(t / bbks - 1) < 0.07)
+
+
+def test_pivot_scale_in_h_units():
+    """Eq. 7: at the pivot k_pivot = 0.05/Mpc, i.e. k = 0.05/h in h/Mpc, the tilt n_s has
+    no effect on P_lin; 0.05 h/Mpc (a pivot in the wrong units) is not invariant."""
+    kp = np.array([cosmo.K_PIVOT / THETA[4]])
+    th = list(THETA)
+    th[1] = 0.90
+    assert abs(cosmo.plin(kp, th)[0] / cosmo.plin(kp, THETA)[0] - 1) < 1e-13
+    assert abs(cosmo.plin(np.array([0.05]), th)[0] / cosmo.plin(np.array([0.05]), THETA)[0] - 1) > 1e-3
