@@ -74,6 +74,17 @@ def algorithmic_bytes(n_steps, N, M, batch=1):
     return {k: v * batch for k, v in b.items()}
 
 
+def compulsory_bytes_per_pm_step(N, M):
+    """Compulsory FP32 traffic of one adjoint-gradient PM step: the forward step (CIC
+    deposit 4M + 12N, R2C 8M, 3 C2R 24M, gather 12M + 48N) and the adjoint step (the forward
+    force again, the pi deposit 12M + 12N, 3 R2C 24M, one C2R of the summed spectra 16M, the
+    psi gather 4M, the particle arrays 48N more): 152 M + 180 N bytes."""
+    return 152 * M + 180 * N
+
+
+NOMINAL_HBM_GBS = 7900.0   # GB300 data-sheet HBM3e bandwidth, for context beside the measured copy
+
+
 # ----------------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi samples during the timed region (read-only queries)."""
@@ -164,23 +175,122 @@ def oracle_sample_seconds(repeats=1):
     return times
 
 
+def _oracle_worker(repeats):
+    """One pool worker: the sample step's seconds (the oracle as it stands, one thread)."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    return oracle_sample_seconds(repeats)
+
+
+def oracle_pool_round(procs, repeats=1):
+    """``procs`` oracle sample steps side by side, one per host core, in spawned processes
+    (never forked: the caller may hold a CUDA context).  Returns (wall seconds of the round,
+    [per-sample seconds])."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        pool.map(_oracle_worker, [0] * procs)        # start-up and imports outside the clock
+        t0 = time.perf_counter()
+        per = pool.map(_oracle_worker, [repeats] * procs)
+        wall = time.perf_counter() - t0
+    return wall, [t for ts in per for t in ts]
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def bench_config(world, workload="large"):
+    """The ``config`` object of both arms' JSON lines (the workload, not the launch shapes)."""
+    box, nm, npc, n = WORKLOADS[workload]
+    return {"workload": f"{npc}^3 particles, {nm}^3 mesh, {box:g} Mpc/h, {n} KDK steps a=1/64->1, ZA ICs, "
+                        "density MSE, reverse-time adjoint; one bench step = one gradient evaluation",
+            "batch": 1, "ckpt_every": 0, "l2": "inputs larger than L2 (every mesh pass streams 4.3-8.6 GB)",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args, rank, world):
+    """The FP64 oracle on the host cores: each bench step is one round of one sample step
+    per core in parallel processes; the rate is the sampled PM gradient steps per second of
+    the round (each sample is 1/512 of a large-workload PM step).  ms_per_step is the wall
+    time of a round, as timed."""
     if rank != 0:
         return
-    for _ in range(args.warmup):
-        oracle_sample_seconds(1)
-    times = oracle_sample_seconds(args.steps)
-    scale = SAMPLE_SCALE
-    t_scaled = float(np.mean(times)) * scale
-    value = 1.0 / t_scaled
-    sample = SAMPLE_TEXT
+    procs = host_cores()
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    walls = []
+    with ctx.Pool(procs) as pool:
+        for _ in range(args.warmup):
+            pool.map(_oracle_worker, [1] * procs)
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            pool.map(_oracle_worker, [1] * procs)
+            walls.append(time.perf_counter() - t0)
+    t_round = float(np.mean(walls))
+    pm_steps_per_round = procs / SAMPLE_SCALE
+    value = pm_steps_per_round / t_round
+    sample = SAMPLE_TEXT.replace("1 thread", "1 thread per process") + \
+        f"; {procs} processes in parallel per bench step (one per host core)"
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_scaled * 1e3, "higher_is_better": True,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_round * 1e3,
+           "pm_steps_per_bench_step": pm_steps_per_round, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "512^3 particles, 1024^3 mesh, 1000 Mpc/h, 100 KDK steps (sampled)"},
-           "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "config": bench_config(world, args.workload),
+           "cpu_baseline": {"value": value, "unit": "steps/s", "cores": procs, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+def run_oracle_full(args):
+    """The oracle's whole gradient (ICs, forward, MSE loss, reverse-time adjoint, IC adjoint)
+    at the 32^3 / 64^3 / 100 Mpc/h / 10-step workload in full, and at the 128^3 / 256^3 /
+    200 Mpc/h workload for ``--oracle-steps`` steps (63 in full take close to an hour per
+    process), with one process and with one process per host core."""
+    import multiprocessing as mp
+    import platform
+    cases = [("32^3 particles, 64^3 mesh, 100 Mpc/h, 10 steps (in full)", (100.0, 64, 32, 10)),
+             (f"128^3 particles, 256^3 mesh, 200 Mpc/h, {args.oracle_steps} of 63 steps", (200.0, 256, 128,
+                                                                                            args.oracle_steps))]
+    procs = host_cores()
+    cpu = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    cpu = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    ctx = mp.get_context("spawn")
+    res = {"mode": "oracle_full", "host_cores": procs, "cpu": cpu, "machine": platform.machine(), "cases": []}
+    for name, c in cases:
+        one = _oracle_gradient_seconds(c)
+        with ctx.Pool(procs) as pool:
+            t0 = time.perf_counter()
+            per = pool.map(_oracle_gradient_seconds, [c] * procs)
+            wall = time.perf_counter() - t0
+        n = c[3]
+        res["cases"].append({"workload": name, "seconds_1_process": one, "pm_steps_per_s_1_process": n / one,
+                             "seconds_per_process_all_cores": float(np.mean(per)),
+                             "pm_steps_per_s_all_cores": procs * n / wall, "processes": procs})
+    print(json.dumps(res))
+
+
+def _oracle_gradient_seconds(case):
+    """Seconds of one oracle gradient evaluation (the target's forward run excluded)."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import pm as opm
+    from paper_2211_09815_gb300 import inputs
+    box, nm, npc, n = case
+    cfg = opm.PMConfig(box=box, n_mesh=nm, n_ptcl=npc, n_steps=n)
+    tgt = opm.forward(inputs.white_noise(npc, 2).astype(np.float64), THETA, cfg)["delta"]
+    om = inputs.white_noise(npc, 1).astype(np.float64)
+    t0 = time.perf_counter()
+    opm.loss_and_gradient(om, THETA, tgt, cfg)
+    return time.perf_counter() - t0
 
 
 # ------------------------------------------------------------------------ ours
@@ -229,7 +339,9 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     ctx_t.close()
     del om2
-    ctx = pm.PMContext(box, nm, npc, n, [THETA], om)
+    # no stream synchronisation after each call inside the timed region: the device error
+    # flag is checked once after it (ctx.check())
+    ctx = pm.PMContext(box, nm, npc, n, [THETA], om, check_errors=False)
     djdd = torch.empty(M, device="cuda")
     gw = torch.empty(N, device="cuda")
     gt = torch.zeros(5, dtype=torch.float64, device="cuda")
@@ -239,18 +351,28 @@ def run_ours(args, rank, world, local_rank):
         # launch shapes from the autotuner, timed on the final (clustered) forward state
         ctx.forward()
         tuning, _ = ctx.autotune()
+    stream = torch.cuda.current_stream()
+    marks = []
 
-    def evaluation():
+    def evaluation(timed=False):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)] if timed else None
         ctx.forward()
+        if timed:
+            ev[0].record(stream)
         ctx.loss_mse(target, djdd, loss)
+        if timed:
+            ev[1].record(stream)
         ctx.adjoint(djdd=djdd, grad_omega=gw, grad_theta=gt)
+        if timed:
+            ev[2].record(stream)
+            marks.append(ev)
 
     for _ in range(args.warmup):
         evaluation()
     torch.cuda.synchronize()
+    ctx.check()
     ctx.profile_read()
     ctx.profile(True)
-    stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local_rank)
     barrier()
@@ -258,12 +380,17 @@ def run_ours(args, rank, world, local_rank):
     clocks.start()
     ev0.record(stream)
     for _ in range(args.steps):
-        evaluation()
+        evaluation(timed=True)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
+    ctx.check()
     ms = ev0.elapsed_time(ev1)
+    # forward (ICs + n steps) and adjoint (n reverse steps + IC adjoint) separately
+    starts = [ev0] + [m[2] for m in marks[:-1]]
+    ms_fwd = sum(a.elapsed_time(m[0]) for a, m in zip(starts, marks)) / args.steps
+    ms_adj = sum(m[1].elapsed_time(m[2]) for m in marks) / args.steps
     prof = ctx.profile_read()
     ctx.profile(False)
     loss_val = float(loss.item())
@@ -274,8 +401,8 @@ def run_ours(args, rank, world, local_rank):
     # gradients out, copies inside the timed region
     tgt_host = target.cpu().pin_memory()
     gw_host = torch.empty(N, dtype=torch.float32).pin_memory()
-    gt_host = torch.zeros(5, dtype=torch.float64)
-    loss_host = torch.zeros(1, dtype=torch.float64)
+    gt_host = torch.zeros(5, dtype=torch.float64).pin_memory()
+    loss_host = torch.zeros(1, dtype=torch.float64).pin_memory()
     ctx.gradient(tgt_host, omega=om_host, loss=loss_host, grad_omega=gw_host, grad_theta=gt_host)
     barrier()
     torch.cuda.synchronize()
@@ -288,6 +415,7 @@ def run_ours(args, rank, world, local_rank):
     e1.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
+    ctx.check()
     e2e_ms = max(e0.elapsed_time(e1), wall * 1e3)
     _, e2e_value = replica_throughput(e2e_ms, args.steps, n, world, dist, "cuda")
     ctx.close()
@@ -297,41 +425,45 @@ def run_ours(args, rank, world, local_rank):
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel category
+    peak, peak_kind = _peaks()
     alg = algorithmic_bytes(n, N, M)
+    ms_pm_step = ms_per_eval / n
+    # headline: the whole adjoint-gradient PM step (one forward + one adjoint step) against
+    # its compulsory traffic (one read and one write per 3-D FFT, fused Fourier multipliers:
+    # forward 48M + 60N, adjoint 104M + 120N bytes)
+    comp_bytes = compulsory_bytes_per_pm_step(N, M)
+    pass_bytes = sum(alg.values()) / n
+    traffic = _ncu_traffic_step()
+    achieved = comp_bytes / (ms_pm_step / 1e3) / 1e9
+    # the dominant kernel category on its own per-pass bytes
     cats = {k: v for k, v in prof.items() if k in alg}
     dom = max(cats, key=lambda k: cats[k][0])
     dom_ms, dom_launches = cats[dom]
-    dom_bytes = alg[dom] * args.steps
-    peak, peak_kind = _peaks()
-    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
-    traffic = _ncu_traffic(dom)
+    dom_achieved = alg[dom] * args.steps / (dom_ms / 1e3) / 1e9
     launches_total = int(sum(v[1] for v in prof.values()))
-    step_bytes = sum(alg.values()) / n
-    # compulsory traffic of one forward + one adjoint step (one read and one write per 3-D
-    # FFT, fused Fourier multipliers): forward 48M + 60N, adjoint 104M + 120N bytes
-    comp_bytes = 152 * M + 180 * N
     out = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_eval, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{npc}^3 particles, {nm}^3 mesh, {box:g} Mpc/h, {n} KDK steps a=1/64->1, "
-                               "ZA ICs, density MSE, reverse-time adjoint; one bench step = one gradient "
-                               "evaluation", "batch": 1, "ckpt_every": 0,
-                   "l2": "inputs larger than L2 (every mesh pass streams 4.3-8.6 GB)",
-                   "parallelism": f"replicas x{world}", "ms_per_pm_step": ms_per_eval / n,
-                   "tuning": tuning if tuning is not None else "defaults"},
+        "config": bench_config(world, args.workload),
+        "pm_steps_per_bench_step": n, "ms_per_pm_step": ms_pm_step,
+        "forward_steps_per_s": n / (ms_fwd / 1e3), "adjoint_steps_per_s": n / (ms_adj / 1e3),
+        "ms_per_eval_forward": ms_fwd, "ms_per_eval_adjoint": ms_adj,
+        "tuning": tuning if tuning is not None else "defaults",
         "particle_updates_per_s": 2 * N * value,
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
-                     "traffic": traffic, "alg_bytes": alg[dom] / (n + 1),
-                     "per": "PM step (one forward + one adjoint force chain of the category)",
-                     "traffic_source": "ncu DRAM bytes at 256^3/512^3 scaled x8 (profiles)",
-                     "launches": dom_launches},
-        "step_roofline": {"compulsory_GB_per_pm_step": comp_bytes / 1e9,
-                          "compulsory_frac": comp_bytes / (ms_per_eval / n / 1e3) / 1e9 / peak,
-                          "pass_GB_per_pm_step": step_bytes / 1e9,
-                          "pass_frac": step_bytes / (ms_per_eval / n / 1e3) / 1e9 / peak},
+        "roofline": {"bound": "hbm", "kernel": "whole adjoint-gradient PM step (forward step + adjoint step, "
+                                                "every kernel)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": f"{peak_kind} copy bandwidth", "alg_bytes": comp_bytes,
+                     "alg_bytes_kind": "compulsory: one read + one write per 3-D FFT, multipliers fused",
+                     "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
+                     "traffic": traffic, "traffic_source": TRAFFIC_NOTE if traffic else None,
+                     "per": "PM step", "per_pass_bytes": pass_bytes,
+                     "per_pass_frac": pass_bytes / (ms_pm_step / 1e3) / 1e9 / peak},
+        "roofline_dominant_kernel": {"kernel": dom, "achieved": dom_achieved, "peak": peak, "unit": "GB/s",
+                                     "frac": dom_achieved / peak, "alg_bytes": alg[dom] / (n + 1),
+                                     "per": "force chain pair (one forward + one adjoint force evaluation)",
+                                     "launches": dom_launches},
         "kernels_ms_per_eval": {k: v[0] / args.steps for k, v in prof.items()},
         "gpu_launches": launches_total,
         "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": 4 * (N + M),
@@ -340,10 +472,13 @@ def run_ours(args, rank, world, local_rank):
         "loss": loss_val,
     }
     if not args.no_cpu_baseline:
-        times = oracle_sample_seconds(3)
-        t = float(np.mean(times))
-        out["cpu_baseline"] = {"value": 1.0 / (t * SAMPLE_SCALE), "unit": "steps/s", "cores": 1, "kind": "oracle",
-                               "sample": SAMPLE_TEXT + "; mean of 3 samples, %.2f s each" % t}
+        procs = host_cores()
+        wall, per = oracle_pool_round(procs)
+        out["cpu_baseline"] = {"value": procs / SAMPLE_SCALE / wall, "unit": "steps/s", "cores": procs,
+                               "kind": "oracle",
+                               "sample": SAMPLE_TEXT.replace("1 thread", "1 thread per process") +
+                               f"; {procs} processes in parallel, one per host core; round of "
+                               f"{wall:.2f} s wall, {np.mean(per):.2f} s per sample"}
     print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
@@ -598,22 +733,38 @@ def run_precision_study(args):
     print(json.dumps(res))
 
 
-TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "ncu_medium_force_vjp_chain.md")
+TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "ncu_traffic_medium_force_chains.md")
+TRAFFIC_NOTE = ("ncu DRAM read + write bytes of every kernel of one forward and one adjoint force chain at "
+                "256^3/512^3, scaled x8 to 512^3/1024^3 (profiles/ncu_traffic_medium_force_chains.md)")
 
 
-def _ncu_traffic(category):
-    """DRAM bytes per PM step (one forward + one adjoint force chain) of a kernel category
-    at the large workload, from the table of the committed ncu summary of the current kernel
-    build (measured at 256^3/512^3 and scaled by the 8x larger M and N), else None."""
+def _ncu_traffic_table():
+    """{category: DRAM bytes per PM step at the large workload} from the committed ncu
+    summary of the current kernel build (measured at 256^3/512^3 and scaled by the 8x
+    larger M and N), or {} when the summary is absent."""
+    out = {}
     try:
         with open(TRAFFIC_SUMMARY) as f:
             for line in f:
                 cells = [c.strip() for c in line.strip().strip("|").split("|")]
-                if len(cells) == 6 and cells[0] == category:
-                    return float(cells[5])
-    except (OSError, ValueError):
-        return None
-    return None
+                if len(cells) == 6 and cells[0] not in ("category", "---"):
+                    try:
+                        out[cells[0]] = float(cells[5])
+                    except ValueError:
+                        pass
+    except OSError:
+        return {}
+    return out
+
+
+def _ncu_traffic(category):
+    return _ncu_traffic_table().get(category)
+
+
+def _ncu_traffic_step():
+    """DRAM bytes of a whole PM step (every category), or None without a summary."""
+    t = _ncu_traffic_table()
+    return sum(t.values()) if t else None
 
 
 def main():
@@ -629,6 +780,9 @@ def main():
     ap.add_argument("--fft-compare", action="store_true", help="hand-written 3-D FFT beside cuFFT (torch.fft)")
     ap.add_argument("--compare-ckpt", action="store_true", help="reverse time vs checkpoints: memory/time")
     ap.add_argument("--precision-study", action="store_true", help="FP32 vs FP64 GPU run, errors per output")
+    ap.add_argument("--oracle-full", action="store_true",
+                    help="time the oracle's whole gradient on the host cores (1 process and one per core)")
+    ap.add_argument("--oracle-steps", type=int, default=2, help="steps of the 128^3 case of --oracle-full")
     ap.add_argument("--op-case", action="store_true",
                     help="run one force and one force-VJP operator call (no timing), for profilers")
     args = ap.parse_args()
@@ -645,6 +799,8 @@ def main():
         run_precision_study(args)
     elif args.op_case:
         run_op_case(args)
+    elif args.oracle_full:
+        run_oracle_full(args)
     elif args.impl == "reference":
         run_reference(args, rank, world)
     else:

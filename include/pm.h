@@ -26,7 +26,13 @@
  * output pointer forces a synchronisation (noted per call).
  *
  * Errors: every call returns a status (PM_OK = 0).  Arguments are validated on the host
- * before any launch; nothing is written on error.  No exception crosses the ABI.
+ * before any launch; nothing is written on error.  No exception crosses the ABI.  The
+ * device-side waits of the TMA-staged FFT passes are bounded; a wait that gives up sets a
+ * device flag and its kernel returns early (the results of that work are then invalid).
+ * The flag is read, reported as PM_ERR_TIMEOUT and cleared by pm_check and by every call
+ * that synchronises the stream for a host output; an asynchronous call (pm_forward,
+ * pm_adjoint with device outputs, pm_gradient_graph, the operators) reports it through the
+ * next such call or pm_check.
  */
 #ifndef PMGB_PM_H
 #define PMGB_PM_H
@@ -203,6 +209,13 @@ int pm_profile_read(pm_ctx* ctx, double* ms, long long* launches);
 /* Release the context and all its device memory (synchronises its stream). */
 int pm_destroy(pm_ctx* ctx);
 
+/*
+ * Synchronise the context's stream and report any bounded device wait that gave up in
+ * the work enqueued so far: PM_ERR_TIMEOUT (and the flag is cleared), else PM_OK, or
+ * PM_ERR_CUDA if the stream itself failed.
+ */
+int pm_check(pm_ctx* ctx);
+
 /* Static description of a status code. */
 const char* pm_status_string(int status);
 
@@ -310,6 +323,25 @@ int pm_set_snapshots(pm_ctx* ctx, int nsnap, const int* steps, void* disp_out, v
  * p0 = a^2 H (D1' s1 (+ D2' s2)).  s0_out, p0_out: optional (null: not written),
  * [batch][3][n_ptcl^3].  Clears the forward state like the other operators. */
 int pm_op_ic(pm_ctx* ctx, void* s0_out, void* p0_out);
+
+/* ------------------------------------------------------------------------------------
+ * Fault injection on the host, for tests of the error paths (no GPU fault is involved).
+ * ----------------------------------------------------------------------------------*/
+
+/* Make the device allocation after `after` more successful ones fail with PM_ERR_OOM as
+ * if cudaMalloc had failed (no CUDA call is made for it); after < 0 disarms.  Process-wide;
+ * the failing allocation disarms it. */
+int pm_debug_fail_alloc(long long after);
+
+/* Device bytes held by all live contexts of this process (the allocation-free entry point's
+ * fixed array is not counted). */
+long long pm_debug_live_bytes(void);
+
+/* Spin limit of the first mbarrier wait of every CTA of the context's TMA-staged FFT passes
+ * (spins < 0 restores the normal limit of 2^24 polls; 0 gives up at once, so that the
+ * kernels take their timeout path: each CTA sets the flag, waits, bounded, for the copies
+ * it has in flight and returns).  PM_ERR_ARG for a null context. */
+int pm_debug_first_wait(pm_ctx* ctx, int spins);
 
 /* ------------------------------------------------------------------------------------
  * Allocation-free entry point.  The paper has no counterpart: this is a service for

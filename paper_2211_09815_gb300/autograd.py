@@ -4,7 +4,9 @@
 inputs and returns (delta_n, s_n, p_n); calling ``.backward()`` on any function of them
 runs the library's reverse-time adjoint (Sec. 3.6 of the paper) once and returns
 dJ/domega and dJ/dtheta.  The adjoint consumes the context's final state, so each
-forward supports one backward.
+forward supports one backward, and only while that state is still the context's: a
+backward after another call has replaced it (a second ``simulate`` on the same context,
+an operator call) raises instead of returning the gradient of the other inputs.
 """
 import torch
 
@@ -23,6 +25,7 @@ class PMSimulation(torch.autograd.Function):
         mom = torch.empty(B, 3, N, device="cuda", dtype=pm_ctx.dtype)
         pm_ctx.forward(disp=disp, mom=mom, dens=dens)
         ctx.pm_ctx = pm_ctx
+        ctx.state_version = pm_ctx.state_version
         ctx.omega_shape = omega.shape
         ctx.theta_meta = (theta.shape, theta.dtype, theta.device)
         return dens, disp, mom
@@ -30,6 +33,10 @@ class PMSimulation(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g_dens, g_disp, g_mom):
         p = ctx.pm_ctx
+        if p.state_version != ctx.state_version:
+            raise RuntimeError("the PMContext's forward state was replaced after this simulate() call "
+                               "(another simulate, adjoint or operator call on the same context); run the "
+                               "backward before reusing the context, or use one context per graph")
 
         def prep(g):
             return None if g is None else g.detach().to(p.dtype).contiguous()

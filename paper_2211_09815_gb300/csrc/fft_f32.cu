@@ -8,8 +8,8 @@ template int fft_x_r2c<float>(int, const RowJob<float>&, int, int, const cx_t<fl
 template int fft_x_c2r<float>(int, const RowJob<float>&, int, int, const cx_t<float>*, cudaStream_t);
 template int fft_fused_z<float>(int, const ZJob<float>&, bool, const cx_t<float>*, cudaStream_t);
 template int fft_cols_tma<float>(int, int, int, int, const CUtensorMap*, cx_t<float>* const*, int, const cx_t<float>*,
-                                int*, int, cudaStream_t);
-template int fft_fused_tma<float>(int, bool, const CUtensorMap*, const CUtensorMap*, const ZJob<float>&, const cx_t<float>*, int*, int,
+                                const WaitCtl&, int, cudaStream_t);
+template int fft_fused_tma<float>(int, bool, const CUtensorMap*, const CUtensorMap*, const ZJob<float>&, const cx_t<float>*, const WaitCtl&, int,
                                  cudaStream_t);
 template int fft_fused_side<float>(int, const ZJob<float>&, bool, const cx_t<float>*, cudaStream_t);
 template int make_spec_tensor_maps<float>(int, int, cx_t<float>*, CUtensorMap*, CUtensorMap*);
@@ -18,7 +18,7 @@ template int fft_cols_split<float>(int, const SeqMap&, const SeqMap&, cx_t<float
                                    cudaStream_t);
 template int fft_cols_merge<float>(int, const SeqMap&, const SeqMap&, cx_t<float>*, cx_t<float>*, const cx_t<float>*,
                                    cudaStream_t);
-template int fft_ysplit_tma<float>(int, int, const CUtensorMap*, cx_t<float>*, cx_t<float>*, const cx_t<float>*, int*, int,
+template int fft_ysplit_tma<float>(int, int, const CUtensorMap*, cx_t<float>*, cx_t<float>*, const cx_t<float>*, const WaitCtl&, int,
                                    cudaStream_t);
-template int fft_ymerge_tma<float>(int, int, const CUtensorMap*, cx_t<float>*, const cx_t<float>*, int*, int, cudaStream_t);
+template int fft_ymerge_tma<float>(int, int, const CUtensorMap*, cx_t<float>*, const cx_t<float>*, const WaitCtl&, int, cudaStream_t);
 }  // namespace pmgb

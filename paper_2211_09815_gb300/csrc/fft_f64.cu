@@ -8,8 +8,8 @@ template int fft_x_r2c<double>(int, const RowJob<double>&, int, int, const cx_t<
 template int fft_x_c2r<double>(int, const RowJob<double>&, int, int, const cx_t<double>*, cudaStream_t);
 template int fft_fused_z<double>(int, const ZJob<double>&, bool, const cx_t<double>*, cudaStream_t);
 template int fft_cols_tma<double>(int, int, int, int, const CUtensorMap*, cx_t<double>* const*, int, const cx_t<double>*,
-                                int*, int, cudaStream_t);
-template int fft_fused_tma<double>(int, bool, const CUtensorMap*, const CUtensorMap*, const ZJob<double>&, const cx_t<double>*, int*, int,
+                                const WaitCtl&, int, cudaStream_t);
+template int fft_fused_tma<double>(int, bool, const CUtensorMap*, const CUtensorMap*, const ZJob<double>&, const cx_t<double>*, const WaitCtl&, int,
                                  cudaStream_t);
 template int fft_fused_side<double>(int, const ZJob<double>&, bool, const cx_t<double>*, cudaStream_t);
 template int make_spec_tensor_maps<double>(int, int, cx_t<double>*, CUtensorMap*, CUtensorMap*);
@@ -18,7 +18,7 @@ template int fft_cols_split<double>(int, const SeqMap&, const SeqMap&, cx_t<doub
                                    cudaStream_t);
 template int fft_cols_merge<double>(int, const SeqMap&, const SeqMap&, cx_t<double>*, cx_t<double>*, const cx_t<double>*,
                                    cudaStream_t);
-template int fft_ysplit_tma<double>(int, int, const CUtensorMap*, cx_t<double>*, cx_t<double>*, const cx_t<double>*, int*, int,
+template int fft_ysplit_tma<double>(int, int, const CUtensorMap*, cx_t<double>*, cx_t<double>*, const cx_t<double>*, const WaitCtl&, int,
                                    cudaStream_t);
-template int fft_ymerge_tma<double>(int, int, const CUtensorMap*, cx_t<double>*, const cx_t<double>*, int*, int, cudaStream_t);
+template int fft_ymerge_tma<double>(int, int, const CUtensorMap*, cx_t<double>*, const cx_t<double>*, const WaitCtl&, int, cudaStream_t);
 }  // namespace pmgb

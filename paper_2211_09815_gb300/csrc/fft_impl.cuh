@@ -603,13 +603,14 @@ static void launch_tma_L(const CUtensorMap* maps, const CUtensorMap* omaps, cons
 
 template <typename T>
 int fft_cols_tma(int n, int batch, int dir, int zaxis, const CUtensorMap* maps, cx_t<T>* const* bufs, int nb,
-                 const cx_t<T>* tw, int* err, int nsm, cudaStream_t st) {
+                 const cx_t<T>* tw, const WaitCtl& wc, int nsm, cudaStream_t st) {
   TmaJob<T> job{};
   job.batch = batch;
   for (int i = 0; i < nb; ++i) job.out[i] = bufs[i];
   job.nbuf = nb;
   job.zaxis = zaxis;
-  job.err = err;
+  job.err = wc.err;
+  job.first_wait = wc.first_wait;
   if (dir < 0) {
     PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, -1, 0>(maps, nullptr, job, batch * tiles_of<T, LL>(), tw, nsm, st)));
   } else {
@@ -620,34 +621,36 @@ int fft_cols_tma(int n, int batch, int dir, int zaxis, const CUtensorMap* maps, 
 
 template <typename T>
 int fft_ysplit_tma(int n, int batch, const CUtensorMap* umaps, cx_t<T>* u, cx_t<T>* out1, const cx_t<T>* tw,
-                   int* err, int nsm, cudaStream_t st) {
+                   const WaitCtl& wc, int nsm, cudaStream_t st) {
   TmaJob<T> job{};
   job.out[0] = u;
   job.out[1] = out1;
   job.nbuf = 1;
   job.zaxis = 0;
   job.batch = batch;
-  job.err = err;
+  job.err = wc.err;
+  job.first_wait = wc.first_wait;
   PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, +1, 3>(umaps, umaps, job, batch * tiles_of<T, LL>(), tw, nsm, st)));
   return PM_OK;
 }
 
 template <typename T>
-int fft_ymerge_tma(int n, int batch, const CUtensorMap* pmaps, cx_t<T>* p1, const cx_t<T>* tw, int* err, int nsm,
+int fft_ymerge_tma(int n, int batch, const CUtensorMap* pmaps, cx_t<T>* p1, const cx_t<T>* tw, const WaitCtl& wc, int nsm,
                    cudaStream_t st) {
   TmaJob<T> job{};
   job.out[0] = p1;
   job.nbuf = 1;
   job.zaxis = 0;
   job.batch = batch;
-  job.err = err;
+  job.err = wc.err;
+  job.first_wait = wc.first_wait;
   PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, -1, 4>(pmaps, &pmaps[0], job, batch * tiles_of<T, LL>(), tw, nsm, st)));
   return PM_OK;
 }
 
 template <typename T>
 int fft_fused_tma(int n, bool adjoint, const CUtensorMap* maps, const CUtensorMap* omaps, const ZJob<T>& zj,
-                  const cx_t<T>* tw, int* err, int nsm, cudaStream_t st) {
+                  const cx_t<T>* tw, const WaitCtl& wc, int nsm, cudaStream_t st) {
   TmaJob<T> job{};
   for (int i = 0; i < 3; ++i) job.out[i] = zj.out[i];
   job.nbuf = 1;
@@ -655,7 +658,8 @@ int fft_fused_tma(int n, bool adjoint, const CUtensorMap* maps, const CUtensorMa
   job.batch = zj.batch;
   job.coef = zj.coef;
   job.dtab = zj.dtab;
-  job.err = err;
+  job.err = wc.err;
+  job.first_wait = wc.first_wait;
   if (adjoint) {
     PMGB_DISPATCH_TMA(n, (launch_tma_L<T, LL, +1, 2>(maps, omaps, job, zj.batch * tiles_of<T, LL>(), tw, nsm, st)));
   } else {

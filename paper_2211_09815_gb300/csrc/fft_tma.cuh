@@ -35,6 +35,7 @@ template <typename T> struct TmaJob {
   const T* coef;       // Green's function coefficient per instance (KIND 1, 2)
   const T* dtab;       // deconvolution table or null
   int* err;            // device error flag (mbarrier timeout)
+  int first_wait;      // spin limit of each CTA's first wait (< 0: the normal limit)
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -54,11 +55,13 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
       : "memory");
   return ok != 0;
 }
-// bounded wait: false (and the error flag set) if the phase never completes
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int* err) {
-  for (long long i = 0; i < (1LL << 24); ++i)
+// bounded wait: false (and the error flag set) if the phase does not complete within
+// `spins` polls (negative: 2^24 polls, far beyond any tile load)
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int* err, int spins = -1) {
+  const long long lim = spins < 0 ? (1LL << 24) : (long long)spins;
+  for (long long i = 0; i < lim; ++i)
     if (mbar_try_wait(bar, parity)) return true;
-  if (err) atomicExch(err, 1);
+  if (err) *(volatile int*)err = 1;
   return false;
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -285,12 +288,13 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
         issue(q + 1);   // the ring slots are never store sources here
       }
     }
-    if (!mbar_wait(&bars[q % NSLOT], (q / NSLOT) & 1, job.err)) {
-      // give the copies in flight a bounded chance to finish before the CTA exits
+    if (!mbar_wait(&bars[q % NSLOT], (q / NSLOT) & 1, job.err, q == 0 ? job.first_wait : -1)) {
+      // drain this CTA's loads in flight (bounded) before it exits: the load of slot q,
+      // and the next one where it was issued before this wait (KIND 0, 2, 4); then the
+      // committed stores
       if (threadIdx.x == 0) {
-        if (KIND == 1 || KIND == 3)
-          mbar_wait(&bars[q % NSLOT], (q / NSLOT) & 1, nullptr);
-        else if (q + 1 < nq)
+        mbar_wait(&bars[q % NSLOT], (q / NSLOT) & 1, nullptr);
+        if ((KIND == 0 || KIND == 2 || KIND == 4) && q + 1 < nq)
           mbar_wait(&bars[(q + 1) % NSLOT], ((q + 1) / NSLOT) & 1, nullptr);
         if (kStore) bulk_wait_all();
       }

@@ -11,11 +11,14 @@
 // fixed size (PM_NOALLOC_MAX_CELLS cells, 16 MiB), which every GPU that loads this
 // library holds until the process exits.  Host code cannot use the array's name as a
 // device address (on the host it names a host-side shadow), so the device address is
-// looked up once per device with cudaGetSymbolAddress while that device is current.
-// The first call on a device does this look-up; make that first call before any stream
-// capture.  All calls share the one array and it keeps the previous call's contents, so
-// each call clears the cells it uses before scattering; calls that overlap on the GPU
-// (different streams, or different host threads, on the same device) race on it.
+// looked up with cudaGetSymbolAddress while the device is current: once per device, and
+// again when the device's CUDA context has been replaced since (cudaDeviceReset), which
+// the context's unique id shows.  The first call on a device does this look-up; make that
+// first call before any stream capture.  All calls share the one array and it keeps the
+// previous call's contents, so each call clears the cells it uses before scattering;
+// calls that overlap on the GPU (different streams, or different host threads, on the
+// same device) race on it.
+#include <cmath>
 #include <mutex>
 
 #include "pm_engine.h"
@@ -28,8 +31,37 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned long long g_density_scratch[kMaxCells];
 
+struct DevEntry {
+  unsigned long long ctx_id;   // id of the context the address belongs to
+  unsigned long long* addr;
+};
 std::mutex g_mu;
-unsigned long long* g_addr[kMaxDevices] = {};
+DevEntry g_dev[kMaxDevices] = {};
+
+// id of the calling thread's current context (0: none current yet), through the driver
+// entry points of the runtime (no link against libcuda)
+unsigned long long current_context_id() {
+  using GetCur = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCur get_cur = nullptr;
+  static GetId get_id = nullptr;
+  if (!get_cur || !get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return 0;
+    get_cur = (GetCur)f1;
+    get_id = (GetId)f2;
+  }
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (get_cur(&c) != CUDA_SUCCESS || !c) return 0;
+  if (get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 int scratch_address(unsigned long long** out) {
   int dev = 0;
@@ -37,13 +69,16 @@ int scratch_address(unsigned long long** out) {
   if (e != cudaSuccess) { pmgb::set_cuda_error(e); return PM_ERR_CUDA; }
   if (dev < 0 || dev >= kMaxDevices) return PM_ERR_ARG;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
+  DevEntry& d = g_dev[dev];
+  const unsigned long long id = current_context_id();
+  if (!d.addr || id == 0 || id != d.ctx_id) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_density_scratch);
+    e = cudaGetSymbolAddress(&p, g_density_scratch);   // makes the device's context current
     if (e != cudaSuccess) { pmgb::set_cuda_error(e); return PM_ERR_CUDA; }
-    g_addr[dev] = static_cast<unsigned long long*>(p);
+    d.addr = static_cast<unsigned long long*>(p);
+    d.ctx_id = current_context_id();
   }
-  *out = g_addr[dev];
+  *out = d.addr;
   return PM_OK;
 }
 
@@ -55,7 +90,10 @@ extern "C" int pm_density_noalloc(double box, int n_mesh, int n_ptcl, const floa
                                   void* stream) {
   using namespace pmgb;
   if (!disp || !dens_out) return PM_ERR_ARG;
-  if (!(box > 0) || !pow2(n_mesh) || !pow2(n_ptcl) || n_ptcl < 4 || n_mesh % n_ptcl != 0) return PM_ERR_ARG;
+  // the checks of pm_init for these arguments (finite box, 8 <= n_mesh, power-of-two sizes)
+  if (!(box > 0) || !std::isfinite(box) || !pow2(n_mesh) || !pow2(n_ptcl) || n_ptcl < 4 || n_mesh < 8 ||
+      n_mesh % n_ptcl != 0)
+    return PM_ERR_ARG;
   const long long M = (long long)n_mesh * n_mesh * n_mesh;
   if (M > kMaxCells) return PM_ERR_ARG;  // larger meshes need pm_op_density with a context
   unsigned long long* acc = nullptr;
@@ -74,7 +112,7 @@ extern "C" int pm_density_noalloc(double box, int n_mesh, int n_ptcl, const floa
   g.M = M;
   int lgN = 0;
   while ((1LL << lgN) < N) ++lgN;
-  const int e_d = 61 - lgN;
+  const int e_d = fixed_top<float>(lgN);   // the quantum of pm_op_density: equal results bit for bit
   // the array keeps the previous call's sums: clear the cells this call uses
   cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * M, st);
   if (e != cudaSuccess) { set_cuda_error(e); return PM_ERR_CUDA; }

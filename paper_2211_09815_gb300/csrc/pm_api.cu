@@ -1,5 +1,6 @@
 // C ABI of libpmgb (declared in include/pm.h): host-side validation, context lifetime
 // and dispatch to the precision-specific engine.
+#include <atomic>
 #include <cmath>
 #include <mutex>
 #include <set>
@@ -28,6 +29,22 @@ void ensure_smem_attr(const void* fn, int bytes) {
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   done.insert({dev, fn});
 }
+
+static std::mutex g_hook_mu;
+static long long g_fail_after = -1;             // allocations still allowed (-1: no failure)
+static std::atomic<long long> g_live_bytes{0};
+
+bool alloc_gate() {
+  std::lock_guard<std::mutex> lk(g_hook_mu);
+  if (g_fail_after < 0) return true;
+  if (g_fail_after == 0) {
+    g_fail_after = -1;
+    return false;
+  }
+  --g_fail_after;
+  return true;
+}
+void live_bytes_add(long long delta) { g_live_bytes += delta; }
 
 static bool pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
 
@@ -211,6 +228,25 @@ int pm_set_snapshots(pm_ctx* ctx, int nsnap, const int* steps, void* disp_out, v
 int pm_op_ic(pm_ctx* ctx, void* s0_out, void* p0_out) {
   if (!ctx) return PM_ERR_ARG;
   return ctx->eng->op_ic(s0_out, p0_out);
+}
+
+int pm_check(pm_ctx* ctx) {
+  if (!ctx) return PM_ERR_ARG;
+  return ctx->eng->check();
+}
+
+int pm_debug_fail_alloc(long long after) {
+  std::lock_guard<std::mutex> lk(g_hook_mu);
+  g_fail_after = after < 0 ? -1 : after;
+  return PM_OK;
+}
+
+long long pm_debug_live_bytes(void) { return g_live_bytes.load(); }
+
+int pm_debug_first_wait(pm_ctx* ctx, int spins) {
+  if (!ctx) return PM_ERR_ARG;
+  ctx->eng->set_first_wait(spins);
+  return PM_OK;
 }
 
 }  // extern "C"

@@ -29,6 +29,11 @@ struct EngineBase {
   virtual int get_tuning(pm_tuning* t) = 0;
   virtual int set_tuning(const pm_tuning* t) = 0;
   virtual int autotune(int reps, pm_tuning* chosen, double* ms_best) = 0;
+  // synchronise the stream; PM_ERR_TIMEOUT if a bounded device wait gave up since the
+  // last check (the flag is cleared)
+  virtual int check() = 0;
+  // test hook: spin limit of the first mbarrier wait of every TMA-staged CTA (< 0: normal)
+  virtual void set_first_wait(int spins) = 0;
 };
 
 // Creates the engine for cfg->precision; returns a status and sets *out on success.
@@ -36,5 +41,10 @@ int make_engine(const pm_config* cfg, const double* theta, const void* omega, cu
 
 // Record the last CUDA error message for pm_last_cuda_error.
 void set_cuda_error(cudaError_t e);
+
+// Host-side fault injection for the allocation path (pm_debug_fail_alloc): false when the
+// next device allocation is to fail.  Bytes held by all engines (pm_debug_live_bytes).
+bool alloc_gate();
+void live_bytes_add(long long delta);
 
 }  // namespace pmgb

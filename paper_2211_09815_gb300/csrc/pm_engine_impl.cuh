@@ -95,7 +95,11 @@ class Engine : public EngineBase {
     if (st_) cudaStreamSynchronize(st_);
     if (graph_exec_) cudaGraphExecDestroy(graph_exec_);
     for (void* p : allocs_) cudaFree(p);
+    live_bytes_add(-bytes_);
   }
+
+  int check() override { return device_error(); }
+  void set_first_wait(int spins) override { first_wait_ = spins; }
 
   long long scratch_bytes() const override { return bytes_; }
 
@@ -245,7 +249,7 @@ class Engine : public EngineBase {
     PMGB_RET(loss_mse_dev(target, djdd));
     if (loss) {
       PMGB_CK(cudaMemcpyAsync(loss, scal_, sizeof(double) * B_, cudaMemcpyDefault, st_));
-      if (is_host(loss)) PMGB_CK(cudaStreamSynchronize(st_));
+      if (is_host(loss)) return device_error();
     }
     return PM_OK;
   }
@@ -317,11 +321,11 @@ class Engine : public EngineBase {
     k_final_theta<<<(B_ + 31) / 32, 32, 0, st_>>>(in, theta_out_);
     prof_.end(st_, P_OTHER);
     PMGB_CK(cudaGetLastError());
+    have_fwd_ = false;
     if (djdth) {
       PMGB_CK(cudaMemcpyAsync(djdth, theta_out_, sizeof(double) * 5 * B_, cudaMemcpyDefault, st_));
-      if (is_host(djdth)) PMGB_CK(cudaStreamSynchronize(st_));
+      if (is_host(djdth)) return device_error();
     }
-    have_fwd_ = false;
     return PM_OK;
   }
 
@@ -388,11 +392,10 @@ class Engine : public EngineBase {
   // One gradient evaluation with host or device buffers: omega in, target in, forward,
   // MSE loss, adjoint, loss / grad_omega / grad_theta out.  Host outputs synchronise.
   int gradient(const void* omega, const void* target, double* loss, void* grad_omega, double* grad_theta) override {
-    if (!tgt_) {
-      PMGB_RET(alloc(&tgt_, (long long)B_ * M_));
-      PMGB_RET(alloc(&djdd_, (long long)B_ * M_));
-      PMGB_RET(alloc(&gw_, (long long)B_ * N_));
-    }
+    // allocated on first use, each on its own (a failed allocation is retried next call)
+    if (!tgt_) PMGB_RET(alloc(&tgt_, (long long)B_ * M_));
+    if (!djdd_) PMGB_RET(alloc(&djdd_, (long long)B_ * M_));
+    if (!gw_) PMGB_RET(alloc(&gw_, (long long)B_ * N_));
     if (omega) PMGB_CK(cudaMemcpyAsync(omega_, omega, sizeof(T) * B_ * N_, cudaMemcpyDefault, st_));
     PMGB_CK(cudaMemcpyAsync(tgt_, target, sizeof(T) * B_ * M_, cudaMemcpyDefault, st_));
     PMGB_RET(forward(nullptr, nullptr, nullptr));
@@ -404,7 +407,7 @@ class Engine : public EngineBase {
     if (grad_omega) PMGB_CK(cudaMemcpyAsync(grad_omega, gw_, sizeof(T) * B_ * N_, cudaMemcpyDefault, st_));
     if (grad_theta) PMGB_CK(cudaMemcpyAsync(grad_theta, theta_out_, sizeof(double) * 5 * B_, cudaMemcpyDefault, st_));
     if ((loss && is_host(loss)) || (grad_omega && is_host(grad_omega)) || (grad_theta && is_host(grad_theta)))
-      PMGB_CK(cudaStreamSynchronize(st_));
+      return device_error();
     return PM_OK;
   }
 
@@ -416,8 +419,7 @@ class Engine : public EngineBase {
     if (pk) PMGB_CK(cudaMemcpyAsync(pk, pw_out_, sizeof(double) * B_ * nb, cudaMemcpyDefault, st_));
     if (kmean) PMGB_CK(cudaMemcpyAsync(kmean, pw_out_ + B_ * nb, sizeof(double) * nb, cudaMemcpyDefault, st_));
     if (nmodes) PMGB_CK(cudaMemcpyAsync(nmodes, pw_out_ + (B_ + 1) * nb, sizeof(double) * nb, cudaMemcpyDefault, st_));
-    PMGB_CK(cudaStreamSynchronize(st_));
-    return PM_OK;
+    return device_error();
   }
 
   // Objective on the shell power of delta (the last forward density when dens is null):
@@ -442,7 +444,7 @@ class Engine : public EngineBase {
     PMGB_RET(c2r_real(nm_, spec_[6], (T*)djdd, M_));
     if (loss) {
       PMGB_CK(cudaMemcpyAsync(loss, dl, sizeof(double) * B_, cudaMemcpyDefault, st_));
-      if (is_host(loss)) PMGB_CK(cudaStreamSynchronize(st_));
+      if (is_host(loss)) return device_error();
     }
     return PM_OK;
   }
@@ -451,12 +453,10 @@ class Engine : public EngineBase {
   // spec_[6].  Deterministic: per-bin int64 fixed point scaled from a first max pass.
   int power_dev(const T* d) {
     const int nb = nm_ / 2;
-    if (!pw_acc_) {
-      PMGB_RET(alloc(&pw_acc_, (long long)(B_ + 2) * nb));
-      PMGB_RET(alloc(&pw_max_, (long long)B_ * nb));
-      PMGB_RET(alloc(&pw_e_, (long long)B_ * nb));
-      PMGB_RET(alloc(&pw_out_, (long long)(B_ + 2) * nb));
-    }
+    if (!pw_acc_) PMGB_RET(alloc(&pw_acc_, (long long)(B_ + 2) * nb));
+    if (!pw_max_) PMGB_RET(alloc(&pw_max_, (long long)B_ * nb));
+    if (!pw_e_) PMGB_RET(alloc(&pw_e_, (long long)B_ * nb));
+    if (!pw_out_) PMGB_RET(alloc(&pw_out_, (long long)(B_ + 2) * nb));
     PMGB_RET(r2c_real(nm_, d, M_, spec_[6]));
     PMGB_CK(cudaMemsetAsync(pw_acc_, 0, sizeof(unsigned long long) * (B_ + 2) * nb, st_));
     PMGB_CK(cudaMemsetAsync(pw_max_, 0, sizeof(unsigned) * B_ * nb, st_));
@@ -551,10 +551,12 @@ class Engine : public EngineBase {
   template <typename U> int alloc(U** p, long long count) {
     void* q = nullptr;
     const size_t bytes = sizeof(U) * (size_t)(count > 0 ? count : 1);
+    if (!alloc_gate()) return PM_ERR_OOM;   // injected failure (test hook)
     cudaError_t e = cudaMalloc(&q, bytes);
     if (e != cudaSuccess) { set_cuda_error(e); cudaGetLastError(); return PM_ERR_OOM; }
     allocs_.push_back(q);
     bytes_ += (long long)bytes;
+    live_bytes_add((long long)bytes);
     *p = (U*)q;
     return PM_OK;
   }
@@ -703,7 +705,7 @@ class Engine : public EngineBase {
         if (i < 0) return PM_ERR_STATE;
         maps[q] = zaxis ? tmz_[i] : tmy_[i];
       }
-      PMGB_RET(fft_cols_tma<T>(n, B_, dir, zaxis ? 1 : 0, maps, bufs, nb, tw_, dev_err_, nsm_, st_));
+      PMGB_RET(fft_cols_tma<T>(n, B_, dir, zaxis ? 1 : 0, maps, bufs, nb, tw_, WaitCtl{dev_err_, first_wait_}, nsm_, st_));
       PMGB_CK(cudaGetLastError());
       ColBufs<T> sb{};
       for (int q = 0; q < nb; ++q) sb.p[q] = bufs[q] + spec_main_len(n);
@@ -995,7 +997,7 @@ class Engine : public EngineBase {
     prof_.begin(st_, P_Z_FORCE, use_tma_ ? 2 : 1);
     if (use_tma_) {
       const CUtensorMap fo[2] = {tmz_[1], tmz_[2]};   // z force, U
-      PMGB_RET(fft_fused_tma<T>(nm_, false, &tmz_[0], fo, zf, tw_, dev_err_, nsm_, st_));
+      PMGB_RET(fft_fused_tma<T>(nm_, false, &tmz_[0], fo, zf, tw_, WaitCtl{dev_err_, first_wait_}, nsm_, st_));
       PMGB_RET(fft_fused_side<T>(nm_, zf, false, tw_, st_));
     } else {
       PMGB_RET(fft_fused_z<T>(nm_, zf, false, tw_, st_));
@@ -1012,7 +1014,7 @@ class Engine : public EngineBase {
       prof_.begin(st_, P_Z_ADJ, use_tma_ ? 2 : 1);
       if (use_tma_) {
         const CUtensorMap pm2[2] = {tmz_[4], tmz_[5]};
-        PMGB_RET(fft_fused_tma<T>(nm_, true, pm2, &tmz_[0], za, tw_, dev_err_, nsm_, st_));   // psi -> spec_[0]
+        PMGB_RET(fft_fused_tma<T>(nm_, true, pm2, &tmz_[0], za, tw_, WaitCtl{dev_err_, first_wait_}, nsm_, st_));   // psi -> spec_[0]
         PMGB_RET(fft_fused_side<T>(nm_, za, true, tw_, st_));
       } else {
         PMGB_RET(fft_fused_z<T>(nm_, za, true, tw_, st_));
@@ -1050,10 +1052,10 @@ class Engine : public EngineBase {
       if (iu < 0 || ib < 0) return PM_ERR_STATE;
       if (split) {
         const CUtensorMap um[2] = {tmy_[iu], tmy_[ib]};
-        PMGB_RET(fft_ysplit_tma<T>(n, B_, um, u, b, tw_, dev_err_, nsm_, st_));
+        PMGB_RET(fft_ysplit_tma<T>(n, B_, um, u, b, tw_, WaitCtl{dev_err_, first_wait_}, nsm_, st_));
       } else {
         const CUtensorMap pm2[2] = {tmy_[iu], tmy_[ib]};
-        PMGB_RET(fft_ymerge_tma<T>(n, B_, pm2, u, tw_, dev_err_, nsm_, st_));
+        PMGB_RET(fft_ymerge_tma<T>(n, B_, pm2, u, tw_, WaitCtl{dev_err_, first_wait_}, nsm_, st_));
       }
     } else if (split) {
       PMGB_RET(fft_cols_split<T>(n, ymap(n), none, u, b, tw_, st_));
@@ -1259,6 +1261,7 @@ class Engine : public EngineBase {
   bool use_tma_ = false;
   int nsm_ = 1;
   int* dev_err_ = nullptr;
+  int first_wait_ = -1;   // spin limit of the TMA passes' first wait (test hook)
   CUtensorMap tmy_[7], tmz_[7];
 };
 

@@ -66,21 +66,29 @@ int fft_x_c2r4(int n, const RowJob<T>& job, int nrows, int dq, V4<T>* out4, cons
 template <typename T>
 int fft_fused_z(int n, const ZJob<T>& job, bool adjoint, const cx_t<T>* tw, cudaStream_t st);
 
+// Bounded mbarrier waits of the TMA-staged passes: the device flag a wait that gives up
+// sets, and the spin limit of each CTA's first wait (negative: the normal limit; a test
+// hook sets 0 so that the first wait gives up at once).
+struct WaitCtl {
+  int* err;
+  int first_wait;
+};
+
 // TMA-staged persistent column passes over the main half spectrum (mesh sizes 128..1024).
 bool tma_supported(int n);
 template <typename T>
 int fft_cols_tma(int n, int batch, int dir, int zaxis, const CUtensorMap* maps, cx_t<T>* const* bufs, int nb,
-                 const cx_t<T>* tw, int* err, int nsm, cudaStream_t st);
+                 const cx_t<T>* tw, const WaitCtl& wc, int nsm, cudaStream_t st);
 template <typename T>
 int fft_fused_tma(int n, bool adjoint, const CUtensorMap* maps, const CUtensorMap* omaps, const ZJob<T>& job,
-                  const cx_t<T>* tw, int* err, int nsm, cudaStream_t st);
+                  const cx_t<T>* tw, const WaitCtl& wc, int nsm, cudaStream_t st);
 // the same split and merge over the main spectrum with TMA-staged tiles
 template <typename T>
 // umaps: y maps of u and out1
 int fft_ysplit_tma(int n, int batch, const CUtensorMap* umaps, cx_t<T>* u, cx_t<T>* out1, const cx_t<T>* tw,
-                   int* err, int nsm, cudaStream_t st);
+                   const WaitCtl& wc, int nsm, cudaStream_t st);
 template <typename T>
-int fft_ymerge_tma(int n, int batch, const CUtensorMap* pmaps, cx_t<T>* p1, const cx_t<T>* tw, int* err, int nsm,
+int fft_ymerge_tma(int n, int batch, const CUtensorMap* pmaps, cx_t<T>* p1, const cx_t<T>* tw, const WaitCtl& wc, int nsm,
                    cudaStream_t st);
 // the side-plane (kx = n/2) tiles of the fused z passes only
 template <typename T>

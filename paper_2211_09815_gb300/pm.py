@@ -18,7 +18,8 @@ SYMBOLS = ("pm_init", "pm_forward", "pm_loss_mse", "pm_adjoint", "pm_destroy", "
            "pm_last_cuda_error", "pm_scratch_bytes", "pm_op_density", "pm_op_force", "pm_op_force_vjp",
            "pm_op_fft", "pm_op_za", "pm_set_inputs", "pm_gradient", "pm_profile", "pm_profile_read",
            "pm_density_noalloc", "pm_power_spectrum", "pm_gradient_graph", "pm_get_tuning", "pm_set_tuning",
-           "pm_autotune", "pm_op_ic", "pm_loss_power", "pm_set_snapshots")
+           "pm_autotune", "pm_op_ic", "pm_loss_power", "pm_set_snapshots", "pm_check", "pm_debug_fail_alloc",
+           "pm_debug_live_bytes", "pm_debug_first_wait")
 NOALLOC_MAX_CELLS = 128 ** 3
 PROF_NAMES = ("scatter", "fft_x_r2c", "fft_cols", "fused_z_force", "fused_z_adjoint", "fft_x_c2r",
               "gather_fwd", "gather_adj", "other")
@@ -92,6 +93,11 @@ def load_library(path=LIB_PATH):
     lib.pm_get_tuning.argtypes = [vp, ctypes.POINTER(PMTuning)]
     lib.pm_set_tuning.argtypes = [vp, ctypes.POINTER(PMTuning)]
     lib.pm_autotune.argtypes = [vp, i, ctypes.POINTER(PMTuning), vp]
+    lib.pm_check.argtypes = [vp]
+    lib.pm_debug_fail_alloc.argtypes = [ctypes.c_longlong]
+    lib.pm_debug_live_bytes.argtypes = []
+    lib.pm_debug_live_bytes.restype = ctypes.c_longlong
+    lib.pm_debug_first_wait.argtypes = [vp, i]
     for name in SYMBOLS:
         getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
     _lib = lib
@@ -104,12 +110,17 @@ def _check(status, where):
         raise PMError(status, where, lib.pm_last_cuda_error().decode() if status == 3 else "")
 
 
-def _ptr(t, dtype=None, numel=None, name="tensor"):
+def _ptr(t, dtype=None, numel=None, name="tensor", device=None):
+    """Device pointer of a contiguous CUDA tensor after checking dtype, size and device
+    (``device``: the CUDA device index the library launches on; default: the current one)."""
     if t is None:
         return None
     import torch
     if not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
+    dev = torch.cuda.current_device() if device is None else device
+    if t.device.index != dev:
+        raise ValueError(f"{name} is on cuda:{t.device.index}, the library launches on cuda:{dev}")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     if dtype is not None and t.dtype != dtype:
@@ -128,9 +139,12 @@ def density_noalloc(box, n_mesh, n_ptcl, disp, dens_out, stream=None):
     if n_mesh ** 3 > NOALLOC_MAX_CELLS:
         raise ValueError(f"n_mesh**3 = {n_mesh ** 3} exceeds the allocation-free limit {NOALLOC_MAX_CELLS}")
     st = stream if stream is not None else torch.cuda.current_stream()
+    dev = st.device.index
+    if dev != torch.cuda.current_device():
+        raise ValueError(f"the stream is on cuda:{dev}; make that device current first")
     _check(load_library().pm_density_noalloc(float(box), int(n_mesh), int(n_ptcl),
-                                             _ptr(disp, torch.float32, 3 * n_ptcl ** 3, "disp"),
-                                             _ptr(dens_out, torch.float32, n_mesh ** 3, "dens_out"),
+                                             _ptr(disp, torch.float32, 3 * n_ptcl ** 3, "disp", dev),
+                                             _ptr(dens_out, torch.float32, n_mesh ** 3, "dens_out", dev),
                                              ctypes.c_void_p(st.cuda_stream)), "pm_density_noalloc")
 
 
@@ -140,12 +154,19 @@ class PMContext:
     omega: CUDA tensor [batch, n_ptcl, n_ptcl, n_ptcl] (float32 or float64 per precision);
     theta: host sequence of shape [batch, 5] (A_s, n_s, Omega_m, Omega_b, h);
     lpt_order: 1 for Zel'dovich initial conditions, 2 for 2LPT.
+    check_errors: after every call that launches work, synchronise the stream and raise
+    PMError(PM_ERR_TIMEOUT) if a bounded device wait gave up (pm_check).
+    ``state_version`` counts the calls that replace the context's forward state.
     """
 
     def __init__(self, box, n_mesh, n_ptcl, n_steps, theta, omega, a0=1.0 / 64, a1=1.0,
-                 precision=PM_F32, ckpt_every=0, deconv=False, batch=1, stream=None, lpt_order=1):
+                 precision=PM_F32, ckpt_every=0, deconv=False, batch=1, stream=None, lpt_order=1,
+                 check_errors=True):
         import torch
         lib = load_library()
+        self.check_errors = check_errors
+        self.state_version = 0
+        self.device = torch.cuda.current_device()
         self.cfg = PMConfig(box, n_mesh, n_ptcl, n_steps, a0, a1, precision, ckpt_every, int(deconv), batch,
                             int(lpt_order))
         self.dtype = torch.float32 if precision == PM_F32 else torch.float64
@@ -156,9 +177,11 @@ class PMContext:
             raise ValueError("theta must have batch x 5 values")
         arr = (ctypes.c_double * len(th))(*th)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
+        if self.stream.device.index != self.device:
+            raise ValueError("the stream must belong to the current device")
         self._h = ctypes.c_void_p()
         _check(lib.pm_init(ctypes.byref(self._h), ctypes.byref(self.cfg), arr,
-                           _ptr(omega, self.dtype, batch * self.N, "omega"),
+                           self._p(omega, batch * self.N, "omega"),
                            ctypes.c_void_p(self.stream.cuda_stream)), "pm_init")
 
     def close(self):
@@ -172,52 +195,68 @@ class PMContext:
         except Exception:
             pass
 
+    def _p(self, t, numel=None, name="tensor", dtype="ctx"):
+        return _ptr(t, self.dtype if dtype == "ctx" else dtype, numel, name, self.device)
+
+    def _run(self, status, where, replaces_state=True):
+        """Raise on an error status; then, with check_errors, pm_check (synchronises)."""
+        if replaces_state:
+            self.state_version += 1
+        _check(status, where)
+        if self.check_errors:
+            _check(load_library().pm_check(self._h), where + " (pm_check)")
+
+    def check(self):
+        """pm_check: synchronise and raise PMError(PM_ERR_TIMEOUT) if a device wait gave up."""
+        _check(load_library().pm_check(self._h), "pm_check")
+
     def _new(self, *shape, dtype=None):
         import torch
         return torch.empty(*shape, device="cuda", dtype=dtype or self.dtype)
 
     def forward(self, disp=None, mom=None, dens=None):
         v = 3 * self.batch * self.N
-        _check(load_library().pm_forward(self._h, _ptr(disp, self.dtype, v, "disp"), _ptr(mom, self.dtype, v, "mom"),
-                                         _ptr(dens, self.dtype, self.batch * self.M, "dens")), "pm_forward")
+        self._run(load_library().pm_forward(self._h, self._p(disp, v, "disp"), self._p(mom, v, "mom"),
+                                            self._p(dens, self.batch * self.M, "dens")), "pm_forward")
 
     def loss_mse(self, target, djdd, loss=None):
         """loss: optional host float64 tensor [batch] or CUDA float64 tensor."""
         import torch
         out = loss if loss is not None else torch.zeros(self.batch, dtype=torch.float64)
-        _check(load_library().pm_loss_mse(self._h, _ptr(target, self.dtype, self.batch * self.M, "target"),
+        _check(load_library().pm_loss_mse(self._h, self._p(target, self.batch * self.M, "target"),
                                           ctypes.c_void_p(out.data_ptr()),
-                                          _ptr(djdd, self.dtype, self.batch * self.M, "djdd")), "pm_loss_mse")
+                                          self._p(djdd, self.batch * self.M, "djdd")), "pm_loss_mse")
         return out
 
     def adjoint(self, djdd=None, djdx=None, djdp=None, grad_omega=None, grad_theta=None):
         v = 3 * self.batch * self.N
         gt = ctypes.c_void_p(grad_theta.data_ptr()) if grad_theta is not None else None
-        _check(load_library().pm_adjoint(self._h, _ptr(djdd, self.dtype, self.batch * self.M, "djdd"),
-                                         _ptr(djdx, self.dtype, v, "djdx"), _ptr(djdp, self.dtype, v, "djdp"),
-                                         _ptr(grad_omega, self.dtype, self.batch * self.N, "grad_omega"), gt),
-               "pm_adjoint")
+        self._run(load_library().pm_adjoint(self._h, self._p(djdd, self.batch * self.M, "djdd"),
+                                            self._p(djdx, v, "djdx"), self._p(djdp, v, "djdp"),
+                                            self._p(grad_omega, self.batch * self.N, "grad_omega"), gt),
+                  "pm_adjoint")
 
     def op_density(self, disp, dens):
-        _check(load_library().pm_op_density(self._h, _ptr(disp, self.dtype, 3 * self.batch * self.N),
-                                            _ptr(dens, self.dtype, self.batch * self.M)), "pm_op_density")
+        self._run(load_library().pm_op_density(self._h, self._p(disp, 3 * self.batch * self.N, "disp"),
+                                               self._p(dens, self.batch * self.M, "dens")), "pm_op_density")
 
     def op_force(self, disp, acc):
         v = 3 * self.batch * self.N
-        _check(load_library().pm_op_force(self._h, _ptr(disp, self.dtype, v), _ptr(acc, self.dtype, v)),
-               "pm_op_force")
+        self._run(load_library().pm_op_force(self._h, self._p(disp, v, "disp"), self._p(acc, v, "acc")),
+                  "pm_op_force")
 
     def op_force_vjp(self, disp, pi, acc, alpha):
         v = 3 * self.batch * self.N
-        _check(load_library().pm_op_force_vjp(self._h, _ptr(disp, self.dtype, v), _ptr(pi, self.dtype, v),
-                                              _ptr(acc, self.dtype, v), _ptr(alpha, self.dtype, v)),
-               "pm_op_force_vjp")
+        self._run(load_library().pm_op_force_vjp(self._h, self._p(disp, v, "disp"), self._p(pi, v, "pi"),
+                                                 self._p(acc, v, "acc"), self._p(alpha, v, "alpha")),
+                  "pm_op_force_vjp")
 
     def op_fft(self, direction, inp, out):
-        _check(load_library().pm_op_fft(self._h, int(direction), _ptr(inp), _ptr(out)), "pm_op_fft")
+        self._run(load_library().pm_op_fft(self._h, int(direction), self._p(inp, name="inp", dtype=None),
+                                           self._p(out, name="out", dtype=None)), "pm_op_fft")
 
     def op_za(self, s1):
-        _check(load_library().pm_op_za(self._h, _ptr(s1, self.dtype, 3 * self.batch * self.N)), "pm_op_za")
+        self._run(load_library().pm_op_za(self._h, self._p(s1, 3 * self.batch * self.N, "s1")), "pm_op_za")
 
     def set_snapshots(self, steps, disp=None, dens=None, ddisp=None, ddens=None):
         """Observe the states after the given steps (ascending, 0..n_steps): each forward
@@ -228,16 +267,15 @@ class PMContext:
         ns = len(steps)
         v, m = ns * 3 * self.batch * self.N, ns * self.batch * self.M
         arr = (ctypes.c_int * max(ns, 1))(*steps)
-        _check(load_library().pm_set_snapshots(self._h, ns, arr, _ptr(disp, self.dtype, v, "disp"),
-                                               _ptr(dens, self.dtype, m, "dens"), _ptr(ddisp, self.dtype, v, "ddisp"),
-                                               _ptr(ddens, self.dtype, m, "ddens")), "pm_set_snapshots")
+        _check(load_library().pm_set_snapshots(self._h, ns, arr, self._p(disp, v, "disp"),
+                                               self._p(dens, m, "dens"), self._p(ddisp, v, "ddisp"),
+                                               self._p(ddens, m, "ddens")), "pm_set_snapshots")
         self._snapshot_buffers = (disp, dens, ddisp, ddens) if ns else None
 
     def op_ic(self, s0=None, p0=None):
         """Initial state (s0, p0) at a0 of the context's LPT order."""
         v = 3 * self.batch * self.N
-        _check(load_library().pm_op_ic(self._h, _ptr(s0, self.dtype, v, "s0"), _ptr(p0, self.dtype, v, "p0")),
-               "pm_op_ic")
+        self._run(load_library().pm_op_ic(self._h, self._p(s0, v, "s0"), self._p(p0, v, "p0")), "pm_op_ic")
 
     def set_inputs(self, theta=None, omega=None):
         """theta: host [batch][5] or None; omega: host (pinned) or CUDA tensor or None."""
@@ -246,22 +284,27 @@ class PMContext:
         if theta is not None:
             th = [float(v) for row in (theta if hasattr(theta[0], "__len__") else [theta]) for v in row]
             arr = (ctypes.c_double * len(th))(*th)
+        if omega is not None and omega.is_cuda and omega.device.index != self.device:
+            raise ValueError(f"omega is on cuda:{omega.device.index}, the context on cuda:{self.device}")
         om = ctypes.c_void_p(omega.data_ptr()) if omega is not None else None
-        _check(lib.pm_set_inputs(self._h, arr, om), "pm_set_inputs")
+        self._run(lib.pm_set_inputs(self._h, arr, om), "pm_set_inputs")
 
     def gradient(self, target, omega=None, loss=None, grad_omega=None, grad_theta=None):
         """All arguments are torch tensors on the host (pinned) or the device."""
         def p(t):
+            if t is not None and t.is_cuda and t.device.index != self.device:
+                raise ValueError(f"a tensor is on cuda:{t.device.index}, the context on cuda:{self.device}")
             return ctypes.c_void_p(t.data_ptr()) if t is not None else None
-        _check(load_library().pm_gradient(self._h, p(omega), p(target), p(loss), p(grad_omega), p(grad_theta)),
-               "pm_gradient")
+        self._run(load_library().pm_gradient(self._h, p(omega), p(target), p(loss), p(grad_omega), p(grad_theta)),
+                  "pm_gradient")
 
     def gradient_graph(self, target, loss=None, grad_omega=None, grad_theta=None):
         """pm_gradient_graph: device tensors only; needs a non-default stream."""
-        def p(t):
-            return ctypes.c_void_p(t.data_ptr()) if t is not None else None
-        _check(load_library().pm_gradient_graph(self._h, p(target), p(loss), p(grad_omega), p(grad_theta)),
-               "pm_gradient_graph")
+        def p(t, name):
+            return self._p(t, name=name, dtype=None)
+        self._run(load_library().pm_gradient_graph(self._h, p(target, "target"), p(loss, "loss"),
+                                                   p(grad_omega, "grad_omega"), p(grad_theta, "grad_theta")),
+                  "pm_gradient_graph")
 
     def power_spectrum(self, dens=None):
         """(kmean [n/2], P [batch, n/2], nmodes [n/2]) as float64 numpy arrays."""
@@ -271,7 +314,7 @@ class PMContext:
         km = np.zeros(nb)
         nm = np.zeros(nb)
         f = ctypes.POINTER(ctypes.c_double)
-        _check(load_library().pm_power_spectrum(self._h, _ptr(dens, self.dtype, self.batch * self.M, "dens"),
+        _check(load_library().pm_power_spectrum(self._h, self._p(dens, self.batch * self.M, "dens"),
                                                 pk.ctypes.data_as(f), km.ctypes.data_as(f), nm.ctypes.data_as(f)),
                "pm_power_spectrum")
         return km, pk, nm
@@ -286,9 +329,9 @@ class PMContext:
         w = np.ascontiguousarray(np.broadcast_to(np.asarray(weights, dtype=np.float64), (self.batch, nb)))
         loss = np.zeros(self.batch)
         f = ctypes.POINTER(ctypes.c_double)
-        _check(load_library().pm_loss_power(self._h, _ptr(dens, self.dtype, self.batch * self.M, "dens"),
+        _check(load_library().pm_loss_power(self._h, self._p(dens, self.batch * self.M, "dens"),
                                             t.ctypes.data_as(f), w.ctypes.data_as(f), loss.ctypes.data_as(f),
-                                            _ptr(djdd, self.dtype, self.batch * self.M, "djdd")), "pm_loss_power")
+                                            self._p(djdd, self.batch * self.M, "djdd")), "pm_loss_power")
         return loss
 
     def profile(self, enable=True):
@@ -322,7 +365,7 @@ class PMContext:
         returns (chosen tuning dict, [best forward deposit, adjoint deposit, y pass] ms)."""
         t = PMTuning()
         ms = (ctypes.c_double * 3)()
-        _check(load_library().pm_autotune(self._h, int(reps), ctypes.byref(t), ms), "pm_autotune")
+        self._run(load_library().pm_autotune(self._h, int(reps), ctypes.byref(t), ms), "pm_autotune", False)
         return t.as_dict(), list(ms)
 
     @property

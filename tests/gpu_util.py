@@ -46,3 +46,20 @@ def rel_l2(a, b):
 def cosine(a, b):
     a, b = np.ravel(a), np.ravel(b)
     return float(np.dot(a, b) / (np.linalg.norm(a) * np.linalg.norm(b)))
+
+
+def same_cells_fp32(disp32, cfg):
+    """Particles whose CIC cell the FP32 kernel arithmetic, floor(fma(s, n/L, 1/2)) added to
+    the lattice index, and the oracle's FP64 floor(x / l) agree on along every axis.  The
+    cell is an integer decided by floating point: a particle within FP32 rounding of a cell
+    face lands on either side, and there the weight gradient of Eq. 10 (floor convention)
+    jumps, so quantities built on it (alpha, dJ/dx) are compared on the other particles."""
+    n, npc = cfg.n_mesh, cfg.n_ptcl
+    j = np.indices((npc,) * 3).reshape(3, -1)
+    inv_l32 = np.float32(n / cfg.box)
+    # exact product of two FP32 values plus 1/2 in FP64, then one rounding to FP32: the fma
+    v32 = (np.asarray(disp32, dtype=np.float32).astype(np.float64) * np.float64(inv_l32) + 0.5).astype(np.float32)
+    c32 = (j * (n // npc) + np.floor(v32).astype(np.int64)) % n
+    x = opm.lattice(cfg) + np.asarray(disp32, dtype=np.float32).astype(np.float64)
+    c64 = np.floor(x / cfg.cell).astype(np.int64) % n
+    return np.all(c32 == c64, axis=0)

@@ -63,3 +63,38 @@ def test_new_entry_points_reject_null_arguments_on_the_host():
     assert lib.pm_op_ic(None, None, None) == 1
     assert lib.pm_loss_power(None, None, d, d, None, ctypes.c_void_p(16)) == 1
     assert lib.pm_set_snapshots(None, 0, None, None, None, None, None) == 1
+
+
+def test_noalloc_rejects_bad_arguments_on_the_host():
+    """pm_density_noalloc checks its arguments as pm_init does (finite box, power-of-two
+    sizes, 8 <= n_mesh, n_ptcl | n_mesh) before any CUDA call."""
+    import ctypes
+    lib = pm.load_library()
+    d = ctypes.c_void_p(256)
+    assert lib.pm_density_noalloc(float("nan"), 32, 16, d, d, None) == 1
+    assert lib.pm_density_noalloc(float("inf"), 32, 16, d, d, None) == 1
+    assert lib.pm_density_noalloc(-1.0, 32, 16, d, d, None) == 1
+    assert lib.pm_density_noalloc(100.0, 4, 4, d, d, None) == 1     # below 8 cells per side
+    assert lib.pm_density_noalloc(100.0, 48, 16, d, d, None) == 1    # not a power of two
+    assert lib.pm_density_noalloc(100.0, 32, 64, d, d, None) == 1    # n_ptcl does not divide n_mesh
+    assert lib.pm_density_noalloc(100.0, 32, 16, None, d, None) == 1
+
+
+def test_hooks_and_check_reject_null_contexts():
+    lib = pm.load_library()
+    assert lib.pm_check(None) == 1
+    assert lib.pm_debug_first_wait(None, 0) == 1
+    assert lib.pm_debug_fail_alloc(-1) == 0
+    assert lib.pm_debug_live_bytes() == 0
+
+
+def test_tensor_device_is_checked_before_the_call():
+    """A CUDA tensor on another device than the library launches on is refused on the host
+    (a stand-in tensor object: no GPU is needed)."""
+    import types
+    import pytest
+    fake = types.SimpleNamespace(is_cuda=True, device=types.SimpleNamespace(index=1),
+                                 is_contiguous=lambda: True, dtype=None, numel=lambda: 8, data_ptr=lambda: 256)
+    with pytest.raises(ValueError, match="cuda:1"):
+        pm._ptr(fake, device=0)
+    assert pm._ptr(fake, device=1).value == 256

@@ -17,10 +17,24 @@ def test_algorithmic_bytes_of_the_large_workload():
     assert bench.algorithmic_bytes(n, N, M, batch=16)["scatter"] == 16 * alg["scatter"]
 
 
-def test_ncu_traffic_table_is_read_for_the_dominant_category():
-    t = bench._ncu_traffic("fft_cols")
-    assert t is not None and 80e9 < t < 95e9
+def test_ncu_traffic_table_parser(tmp_path, monkeypatch):
+    """The bench reads per-category DRAM bytes per PM step from the committed ncu summary's
+    six-column table; the step's traffic is their sum, and a missing summary gives null."""
+    f = tmp_path / "t.md"
+    f.write_text("| category | a | b | c | d | bytes |\n|---|---|---|---|---|---|\n"
+                 "| fft_cols | 1 | 2 | 1.0 | 3 | 8.5e10 |\n| scatter | 1 | 2 | 1.0 | 3 | 4.0e10 |\n")
+    monkeypatch.setattr(bench, "TRAFFIC_SUMMARY", str(f))
+    assert bench._ncu_traffic("fft_cols") == 8.5e10
     assert bench._ncu_traffic("no_such_category") is None
+    assert bench._ncu_traffic_step() == 12.5e10
+    monkeypatch.setattr(bench, "TRAFFIC_SUMMARY", str(tmp_path / "absent.md"))
+    assert bench._ncu_traffic_step() is None
+
+
+def test_compulsory_bytes_of_the_large_workload():
+    """One forward + one adjoint PM step at 512^3 particles / 1024^3 mesh moves 187.4 GB of
+    compulsory traffic: the denominator of the headline roofline fraction."""
+    assert abs(bench.compulsory_bytes_per_pm_step(512 ** 3, 1024 ** 3) / 187.37e9 - 1) < 1e-3
 
 
 def test_clock_samples_median_and_throttle_reasons():

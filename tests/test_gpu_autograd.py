@@ -83,3 +83,21 @@ def test_autograd_fp32_matches_oracle_and_library_loss_path():
     ctx.adjoint(djdd=djdd, grad_omega=gw)
     assert rel_l2(gw.cpu().numpy(), g) < 1e-5
     ctx.close()
+
+
+def test_backward_after_the_context_state_was_replaced_raises():
+    """Two simulate() calls on one context, then backward through the first: the context
+    now holds the second call's final state, so the backward refuses instead of returning
+    the gradient at the second call's inputs; the second graph's backward still works."""
+    from paper_2211_09815_gb300.autograd import simulate
+    torch, ctx, om, tgt, _ = _setup(1)
+    om1 = om.clone().requires_grad_(True)
+    om2 = (om * 1.01).requires_grad_(True)
+    th = torch.tensor([THETA], dtype=torch.float64, requires_grad=True)
+    loss1 = _loss(torch, simulate, ctx, om1, th, tgt)
+    loss2 = _loss(torch, simulate, ctx, om2, th, tgt)
+    with pytest.raises(RuntimeError, match="forward state was replaced"):
+        loss1.backward()
+    loss2.backward()
+    assert om2.grad is not None and bool(torch.isfinite(om2.grad).all())
+    ctx.close()

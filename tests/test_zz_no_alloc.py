@@ -1,6 +1,7 @@
 """pm_density_noalloc -- the CIC density for callers that cannot call cudaMalloc (their
 device memory belongs to their own pool allocator, or they cannot afford the device
-synchronisation of an allocation) -- against the context-based pm_op_density.
+synchronisation of an allocation) -- against the context-based pm_op_density (the same
+fixed-point quantum, so bit for bit) and against the FP64 oracle's CIC density.
 
 Runs last (file name) so that a failure here cannot hide the other tests; it builds the
 library itself, so it also passes alone in a fresh process.
@@ -8,7 +9,9 @@ library itself, so it also passes alone in a fresh process.
 import numpy as np
 import pytest
 
-from gpu_util import ensure_built, torch_cuda
+from oracle import pm as opm
+
+from gpu_util import ensure_built, oracle_cfg, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -32,8 +35,13 @@ def test_noalloc_density_matches_context_density_on_two_calls(n_mesh, n_ptcl):
         torch.cuda.synchronize()
         r, g = ref.cpu().numpy(), got.cpu().numpy()
         assert np.all(np.isfinite(g))
-        # the same fixed-point deposit: equal up to float32 rounding (bitwise in practice)
-        assert np.max(np.abs(g - r)) <= 1e-6 * np.max(np.abs(r))
+        # the same fixed-point deposit with the same quantum: equal bit for bit
+        assert np.array_equal(g, r)
+        # and the CIC density of the oracle to FP32 rounding of the weights
+        cfg = oracle_cfg(box, n_mesh, n_ptcl, 1)
+        x = opm.lattice(cfg) + disp.cpu().numpy().astype(np.float64).reshape(3, -1)
+        o = opm.density(x, cfg).ravel()
+        assert np.max(np.abs(g - o)) <= 1e-5 * np.max(np.abs(o))
     ctx.close()
 
 
