@@ -238,6 +238,10 @@ long long pm_scratch_bytes(const pm_ctx* ctx);
  *   threads_adjoint      : threads per tile, 256 or 512
  *   tma_columns          : 1 = TMA-staged persistent y/z column passes (meshes 128..1024),
  *                          0 = unstaged column passes
+ *   fused_x              : 1 = the deposit writes the half spectra of its whole-row tiles
+ *                          (CIC deposit and x pass of the R2C in one kernel, meshes
+ *                          128..1024), 0 = the deposit writes real meshes and a separate x
+ *                          pass transforms them; the tile shapes above apply to the latter
  */
 typedef struct pm_tuning {
   int tile_log2_density[3];
@@ -245,6 +249,8 @@ typedef struct pm_tuning {
   int threads_density;
   int threads_adjoint;
   int tma_columns;
+  int fused_x;      /* 1 = deposit fused with the x pass of the R2C (tiles of whole x rows;
+                       meshes 128..1024), 0 = separate passes */
 } pm_tuning;
 
 /* Current launch shapes.  Errors: PM_ERR_ARG (null pointers). */

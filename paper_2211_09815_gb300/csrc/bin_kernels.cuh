@@ -227,21 +227,15 @@ template <> __device__ __forceinline__ double words_to_real<double>(unsigned lo,
   return (double)(long long)(((unsigned long long)hi << 32) | lo);
 }
 
-// One CTA per tile (grid: tiles x instances; tile x extent >= 4, outputs 16-byte aligned).
-// NQ = 1: delta; NQ = 4: delta and the three
-// pi sums.  Outputs: delta = m acc 2^-e_d - 1 into dout (instance stride dis), pi_c =
-// acc 2^-e_c into p0..p2 (instance stride pis).  Dynamic shared memory: NQ * cells * 8 B
-// (low words [NQ][cells], then high words [NQ][cells]).
-template <typename T, int NQ, int NT>
-__global__ void __launch_bounds__(NT, NT >= 512 ? 3 : 1)
-k_pull_scatter(Geo<T> g, BinGeo bg, const V4<T>* __restrict__ rec0, const V4<T>* __restrict__ rec1,
-               const unsigned* __restrict__ start, int e_d, const int* __restrict__ e_pi, T mass,
-               T* __restrict__ dout, long long dis, T* __restrict__ p0, T* __restrict__ p1, T* __restrict__ p2,
-               long long pis) {
-  extern __shared__ __align__(16) unsigned acc[];   // [2][NQ][cells]
-  __shared__ unsigned rbeg[20], rpre[21];
-  const int b = blockIdx.y;
-  const int tile = blockIdx.x;
+// Accumulation of one tile (shared by the unfused and the fused deposit): the ranges of
+// the tile's own bins and the reaching classes of its seven lower neighbours, each CIC
+// corner that lands in the tile rounded to fixed point and added exactly.  acc: low words
+// [NQ][cells], then high words [NQ][cells] (zeroed here).
+template <typename T, int NQ>
+__device__ __forceinline__ void pull_accumulate(const BinGeo& bg, const V4<T>* __restrict__ rec0,
+                                                const V4<T>* __restrict__ rec1, const unsigned* __restrict__ start,
+                                                int e_d, int b, int tile, unsigned* acc, unsigned* rbeg,
+                                                unsigned* rpre) {
   const int T2 = tile & (bg.ntx - 1), T1 = (tile / bg.ntx) & (bg.nty - 1), T0 = tile / (bg.ntx * bg.nty);
   const int cells = 1 << (bg.lx + bg.ly + bg.lz);
   for (int k = threadIdx.x; k < NQ * cells / 2; k += blockDim.x) reinterpret_cast<uint4*>(acc)[k] = make_uint4(0, 0, 0, 0);
@@ -314,6 +308,28 @@ k_pull_scatter(Geo<T> g, BinGeo bg, const V4<T>* __restrict__ rec0, const V4<T>*
     }
   }
   __syncthreads();
+}
+
+// One CTA per tile (grid: tiles x instances; tile x extent >= 4, outputs 16-byte aligned).
+// NQ = 1: delta; NQ = 4: delta and the three
+// pi sums.  Outputs: delta = m acc 2^-e_d - 1 into dout (instance stride dis), pi_c =
+// acc 2^-e_c into p0..p2 (instance stride pis).  Dynamic shared memory: NQ * cells * 8 B
+// (low words [NQ][cells], then high words [NQ][cells]).
+template <typename T, int NQ, int NT>
+__global__ void __launch_bounds__(NT, NT >= 512 ? 3 : 1)
+k_pull_scatter(Geo<T> g, BinGeo bg, const V4<T>* __restrict__ rec0, const V4<T>* __restrict__ rec1,
+               const unsigned* __restrict__ start, int e_d, const int* __restrict__ e_pi, T mass,
+               T* __restrict__ dout, long long dis, T* __restrict__ p0, T* __restrict__ p1, T* __restrict__ p2,
+               long long pis) {
+  extern __shared__ __align__(16) unsigned acc[];   // [2][NQ][cells]
+  __shared__ unsigned rbeg[20], rpre[21];
+  const int b = blockIdx.y;
+  const int tile = blockIdx.x;
+  const int T2 = tile & (bg.ntx - 1), T1 = (tile / bg.ntx) & (bg.nty - 1), T0 = tile / (bg.ntx * bg.nty);
+  const int cells = 1 << (bg.lx + bg.ly + bg.lz);
+  pull_accumulate<T, NQ>(bg, rec0, rec1, start, e_d, b, tile, acc, rbeg, rpre);
+  const unsigned* hacc = acc + NQ * cells;
+  const unsigned mx = (1u << bg.lx) - 1, my = (1u << bg.ly) - 1;
   const T md = mass * pow2i<T>(-e_d);
   T mp[3] = {0, 0, 0};
   if constexpr (NQ == 4) {

@@ -14,6 +14,7 @@
 #include "pm_engine.h"
 #include "pm_kernels.cuh"
 #include "bin_kernels.cuh"
+#include "deposit_r2c.cuh"
 
 namespace pmgb {
 
@@ -212,8 +213,8 @@ class Engine : public EngineBase {
       prof_.begin(st_, P_GATHER_FWD, 1);
       // the bins of the next step's deposit are counted at the new positions
       k_gather_fwd<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, s_, p_, j == n_ ? a_ : nullptr, fvec_, sc, j,
-                                                              n_ + 1, cks, ckp, bg1_, j < n_ ? bcount_ : nullptr,
-                                                              bkeys_);
+                                                              n_ + 1, cks, ckp, fused_ ? bgf1_ : bg1_,
+                                                              j < n_ ? bcount_ : nullptr, bkeys_);
       counted_ = j < n_;
       prof_.end(st_, P_GATHER_FWD);
       PMGB_CK(cudaGetLastError());
@@ -289,8 +290,9 @@ class Engine : public EngineBase {
       double* pxp = part_ + (long long)(2 * j + 1) * B_ * G_;
       prof_.begin(st_, P_GATHER_ADJ, 1);
       k_gather_adj<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, mass_, s_, p_, xi_, pi_, nullptr, nullptr, fvec_,
-                                                              sc, j, n_ + 1, ckp, cks, ppa, pxp, pimax_, bg4_,
-                                                              j > 0 ? bcount_ : nullptr, bkeys_);
+                                                              sc, j, n_ + 1, ckp, cks, ppa, pxp, pimax_,
+                                                              fused_ ? bgf4_ : bg4_, j > 0 ? bcount_ : nullptr,
+                                                              bkeys_);
       counted_ = j > 0;
       prof_.end(st_, P_GATHER_ADJ);
       PMGB_CK(cudaGetLastError());
@@ -759,6 +761,7 @@ class Engine : public EngineBase {
     tune_.threads_density = 256;
     tune_.threads_adjoint = 512;
     tune_.tma_columns = 1;
+    tune_.fused_x = fused_rows<T>(nm_, 1) > 0 ? 1 : 0;
     const BinGeo smallest = make_bin_geo(ilog2(nm_), 3, 3, 3);
     const long long maxbin = (long long)B_ * smallest.nkeys + 1;
     PMGB_RET(alloc(&bkeys_, (long long)B_ * N_));
@@ -779,6 +782,16 @@ class Engine : public EngineBase {
     bg1_ = make_bin_geo(lg, tune_.tile_log2_density[2], tune_.tile_log2_density[1], tune_.tile_log2_density[0]);
     bg4_ = make_bin_geo(lg, tune_.tile_log2_adjoint[2], tune_.tile_log2_adjoint[1], tune_.tile_log2_adjoint[0]);
     use_tma_ = tune_.tma_columns != 0 && tma_supported(nm_);
+    // deposit fused with the R2C x pass: tiles of whole x rows, R rows split over (y, z)
+    fused_ = tune_.fused_x != 0 && fused_rows<T>(nm_, 1) > 0;
+    if (fused_rows<T>(nm_, 1) > 0) {
+      auto geo = [&](int rows) {
+        const int lr = ilog2(rows);
+        return make_bin_geo(lg, lg, (lr + 1) / 2, lr / 2);
+      };
+      bgf1_ = geo(fused_rows<T>(nm_, 1));
+      bgf4_ = geo(fused_rows<T>(nm_, 4));
+    }
   }
   // tile extents: x at least 4 cells (vector write-out), 2^9..2^maxl cells (shared memory:
   // 2^12 cells x 8 B for the density alone, 2^11 x 32 B with the pi sums)
@@ -797,6 +810,7 @@ class Engine : public EngineBase {
       return PM_ERR_ARG;
     if (t->tma_columns != 0 && t->tma_columns != 1) return PM_ERR_ARG;
     if (t->tma_columns && !tma_supported(nm_)) return PM_ERR_ARG;
+    if ((t->fused_x != 0 && t->fused_x != 1) || (t->fused_x && fused_rows<T>(nm_, 1) == 0)) return PM_ERR_ARG;
     tune_ = *t;
     apply_tuning();
     return PM_OK;
@@ -901,7 +915,7 @@ class Engine : public EngineBase {
   // adjoint sums pi_c W -- by binning the particles over mesh tiles and one CTA per tile
   // (bin_kernels.cuh).  delta goes to dout (instance stride dis); the pi sums go to the real
   // views of spec_[4..6].
-  int scatter(const T* s, const T* pi, T* dout, long long dis) {
+  int scatter(const T* s, const T* pi, T* dout, long long dis, const FusedOut<T>* fo = nullptr) {
     if (pi) {
       prof_.begin(st_, P_OTHER, 1);
       k_pi_exponents<<<1, 64, 0, st_>>>(pimax_, e_pi_, 3 * B_, fixed_top<T>(lgN_));
@@ -912,15 +926,21 @@ class Engine : public EngineBase {
     const bool pre = counted_;
     counted_ = false;
     prof_.begin(st_, P_SCATTER, pre ? 5 : 6);
-    PMGB_RET(pi ? deposit(s, pi, dout, dis, bg4_, tune_.threads_adjoint, pre)
-                : deposit(s, nullptr, dout, dis, bg1_, tune_.threads_density, pre));
+    if (fo)
+      PMGB_RET(deposit(s, pi, nullptr, 0, pi ? bgf4_ : bgf1_, 0, pre, fo));
+    else
+      PMGB_RET(pi ? deposit(s, pi, dout, dis, bg4_, tune_.threads_adjoint, pre)
+                  : deposit(s, nullptr, dout, dis, bg1_, tune_.threads_density, pre));
     prof_.end(st_, P_SCATTER);
     return PM_OK;
   }
   // binning + tile-owner deposit with tile geometry bg and nt threads per tile (e_pi_
   // must hold the pi exponents when pi is given)
   // (precounted: the previous gather already counted the bins of s with geometry bg)
-  int deposit(const T* s, const T* pi, T* dout, long long dis, const BinGeo& bg, int nt, bool precounted = false) {
+  // (fo: the deposit fused with the R2C x pass, into the half spectra of fo; bg is then
+  // the whole-row geometry of fused_rows)
+  int deposit(const T* s, const T* pi, T* dout, long long dis, const BinGeo& bg, int nt, bool precounted = false,
+              const FusedOut<T>* fo = nullptr) {
     const long long nbin = (long long)B_ * bg.nkeys + 1;
     const int nscan = (int)((nbin + kScanBlock - 1) / kScanBlock);
     if (!precounted) k_bin_count<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, bg, s, bcount_, bkeys_);
@@ -933,6 +953,14 @@ class Engine : public EngineBase {
     else
       k_bin_fill<T, 1><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, bg, s, nullptr, nullptr, bkeys_, bcursor_,
                                                                brec0_, nullptr);
+    if (fo) {
+      if (pi)
+        PMGB_RET((launch_pull_r2c<T, 4>(nm_, bg, B_, brec0_, brec1_, bstart_, e_d_, e_pi_, mass_, *fo, tw_, st_)));
+      else
+        PMGB_RET((launch_pull_r2c<T, 1>(nm_, bg, B_, brec0_, nullptr, bstart_, e_d_, nullptr, mass_, *fo, tw_, st_)));
+      PMGB_CK(cudaGetLastError());
+      return PM_OK;
+    }
     const int cells = 1 << (bg.lx + bg.ly + bg.lz);
     const long long pis = 2 * spec_len_cx(nm_);
     const dim3 grid(bg.ntiles, B_);
@@ -969,16 +997,25 @@ class Engine : public EngineBase {
     const long long sis = 2 * spec_len_cx(nm_);
     T* dmesh = keep_density ? dens_ : rmesh(0);
     const long long dis = keep_density ? M_ : sis;
-    PMGB_RET(scatter(s, pi, dmesh, dis));
-    const int nb = pi ? 4 : 1;
-    RowJob<T> job{};
-    job.b[0] = RowBuf<T>{dmesh, dis, spec_[0]};
-    if (pi)
-      for (int c = 0; c < 3; ++c) job.b[1 + c] = RowBuf<T>{rmesh(4 + c), sis, spec_[4 + c]};
-    prof_.begin(st_, P_X_R2C, 1);
-    PMGB_RET(fft_x_r2c<T>(nm_, job, nb, B_ * nm_ * nm_, tw_, st_));
-    prof_.end(st_, P_X_R2C);
-    PMGB_CK(cudaGetLastError());
+    if (fused_) {
+      // deposit and x pass in one kernel: delta (and pi_c) straight into the half spectra
+      FusedOut<T> fo{};
+      fo.spec[0] = spec_[0];
+      for (int c = 0; c < 3; ++c) fo.spec[1 + c] = pi ? spec_[4 + c] : nullptr;
+      fo.dens = keep_density ? dens_ : nullptr;
+      PMGB_RET(scatter(s, pi, nullptr, 0, &fo));
+    } else {
+      PMGB_RET(scatter(s, pi, dmesh, dis));
+      const int nb = pi ? 4 : 1;
+      RowJob<T> job{};
+      job.b[0] = RowBuf<T>{dmesh, dis, spec_[0]};
+      if (pi)
+        for (int c = 0; c < 3; ++c) job.b[1 + c] = RowBuf<T>{rmesh(4 + c), sis, spec_[4 + c]};
+      prof_.begin(st_, P_X_R2C, 1);
+      PMGB_RET(fft_x_r2c<T>(nm_, job, nb, B_ * nm_ * nm_, tw_, st_));
+      prof_.end(st_, P_X_R2C);
+      PMGB_CK(cudaGetLastError());
+    }
     // y forward: delta (and P_0) in place; the adjoint's P_1 and P_2 merge into
     // V = i (k_1 P_1 + k_2 P_2) in spec_[5]
     C* fwdb[2] = {spec_[0], spec_[4]};
@@ -1238,6 +1275,8 @@ class Engine : public EngineBase {
   const void* graph_args_[4] = {nullptr, nullptr, nullptr, nullptr};
   T *s_ = nullptr, *p_ = nullptr, *a_ = nullptr, *xi_ = nullptr, *pi_ = nullptr, *s1_ = nullptr, *omega_ = nullptr;
   BinGeo bg1_{}, bg4_{};
+  BinGeo bgf1_{}, bgf4_{};   // whole-row tiles of the deposit fused with the R2C x pass
+  bool fused_ = false;
   bool counted_ = false;   // the last gather counted the bins of the next deposit
   pm_tuning tune_{};
   unsigned *bkeys_ = nullptr, *bcount_ = nullptr, *bstart_ = nullptr, *bcursor_ = nullptr, *bsums_ = nullptr;

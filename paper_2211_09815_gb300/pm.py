@@ -32,12 +32,13 @@ class PMLibraryError(RuntimeError):
 class PMTuning(ctypes.Structure):
     """Launch shapes of the tunable passes (include/pm.h pm_tuning)."""
     _fields_ = [("tile_log2_density", ctypes.c_int * 3), ("tile_log2_adjoint", ctypes.c_int * 3),
-                ("threads_density", ctypes.c_int), ("threads_adjoint", ctypes.c_int), ("tma_columns", ctypes.c_int)]
+                ("threads_density", ctypes.c_int), ("threads_adjoint", ctypes.c_int), ("tma_columns", ctypes.c_int),
+                ("fused_x", ctypes.c_int)]
 
     def as_dict(self):
         return {"tile_log2_density": list(self.tile_log2_density), "tile_log2_adjoint": list(self.tile_log2_adjoint),
                 "threads_density": self.threads_density, "threads_adjoint": self.threads_adjoint,
-                "tma_columns": self.tma_columns}
+                "tma_columns": self.tma_columns, "fused_x": self.fused_x}
 
 
 class PMError(RuntimeError):

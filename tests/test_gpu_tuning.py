@@ -26,7 +26,8 @@ def test_set_tuning_rejects_invalid_shapes():
                 {"tile_log2_adjoint": [4, 4, 4]},       # 2^12 cells with the pi sums
                 {"tile_log2_adjoint": [2, 2, 2]},       # 2^6 cells
                 {"threads_density": 128},
-                {"tma_columns": 1}):                    # no staged passes below 128^3
+                {"tma_columns": 1},                     # no staged passes below 128^3
+                {"fused_x": 1}):                        # no fused deposit below 128^3
         with pytest.raises(pm.PMError):
             ctx.set_tuning(bad)
     assert ctx.get_tuning() == t
@@ -115,4 +116,43 @@ def test_autotune_keeps_forward_state_and_gradient():
         # the other column-pass form rounds differently in the last bit; the FP32 reverse
         # integration amplifies that to the FP32 accuracy class of the gradient
         assert cosine(g1, g0) > 0.9999 and rel_l2(g1, g0) < 1e-3
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision,nm,npc", [(0, 128, 64), (1, 128, 32), (0, 256, 64)])
+def test_fused_deposit_and_x_pass_match_separate_passes(precision, nm, npc):
+    """The deposit fused with the R2C x pass (whole-row tiles, spectra written from shared
+    memory) against the separate deposit and x pass: the same exact integer sums, the same
+    conversion and radix stages.  The final density of a forward run is bitwise equal; the
+    forces, the VJP and the forward state equal to the last-bit rounding of the transform
+    (relative 1e-6), and both match the oracle."""
+    torch = torch_cuda()
+    box = 60.0
+    ctx, *_ = make_ctx(box, nm, npc, 3, precision=precision)
+    rng = np.random.default_rng(6)
+    d = torch.from_numpy(rng.normal(scale=2.0 * box / nm, size=(3, npc ** 3))).to("cuda", ctx.dtype).contiguous()
+    p = torch.from_numpy(rng.normal(size=(3, npc ** 3))).to("cuda", ctx.dtype).contiguous()
+    res = []
+    for fused in (1, 0):
+        ctx.set_tuning({"fused_x": fused})
+        assert ctx.get_tuning()["fused_x"] == fused
+        acc = torch.empty(3 * npc ** 3, device="cuda", dtype=ctx.dtype)
+        acc2, alpha = torch.empty_like(acc), torch.empty_like(acc)
+        ctx.op_force(d, acc)
+        ctx.op_force_vjp(d, p, acc2, alpha)
+        dens = torch.empty(nm ** 3, device="cuda", dtype=ctx.dtype)
+        disp = torch.empty(3 * npc ** 3, device="cuda", dtype=ctx.dtype)
+        ctx.forward(disp=disp, dens=dens)
+        res.append([x.cpu().numpy() for x in (acc, acc2, alpha, dens, disp)])
+    tol = 1e-13 if precision else 1e-6
+    for a, b in zip(res[0][:3], res[1][:3]):
+        assert rel_l2(a, b) < tol
+    assert rel_l2(res[0][4], res[1][4]) < tol
+    # the final density is the deposit's real output at the last step's positions
+    if np.array_equal(res[0][4], res[1][4]):
+        assert np.array_equal(res[0][3], res[1][3])
+    cfg = oracle_cfg(box, nm, npc, 1)
+    x = opm.lattice(cfg) + d.cpu().numpy().astype(np.float64)
+    a_ref, _ = opm.pm_force(x, inputs.THETA_FIDUCIAL[2], cfg)
+    assert rel_l2(res[0][0].reshape(3, -1), a_ref) < (1e-10 if precision else 3e-5)
     ctx.close()
