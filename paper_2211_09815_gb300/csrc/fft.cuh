@@ -28,24 +28,32 @@ template <> struct Plan<256>  { static constexpr int S = 2, R0 = 16, R1 = 16, R2
 template <> struct Plan<512>  { static constexpr int S = 3, R0 = 8,  R1 = 8, R2 = 8, RMAX = 8; };
 template <> struct Plan<1024> { static constexpr int S = 3, R0 = 16, R1 = 8, R2 = 8, RMAX = 16; };
 
-// cos(2 pi m / 16), exact values of the 16th roots of unity.
-__host__ __device__ constexpr double cos16(int m) {
-  m &= 15;
-  return m == 0 ? 1.0 : m == 1 ? 0.92387953251128675613 : m == 2 ? 0.70710678118654752440
-       : m == 3 ? 0.38268343236508977173 : m == 4 ? 0.0 : m == 5 ? -0.38268343236508977173
-       : m == 6 ? -0.70710678118654752440 : m == 7 ? -0.92387953251128675613 : m == 8 ? -1.0
-       : m == 9 ? -0.92387953251128675613 : m == 10 ? -0.70710678118654752440
-       : m == 11 ? -0.38268343236508977173 : m == 12 ? 0.0 : m == 13 ? 0.38268343236508977173
-       : m == 14 ? 0.70710678118654752440 : 0.92387953251128675613;
-}
-__host__ __device__ constexpr double sin16(int m) { return cos16(m - 4); }
+// Two-stage plans (radix 32) for the long column transforms, where shared memory, not
+// HBM, limits the three-stage plans: each stage reads and writes the whole tile once.
+template <int L> struct Plan2 : Plan<L> {};
+template <> struct Plan2<512>  { static constexpr int S = 2, R0 = 32, R1 = 16, R2 = 1, RMAX = 32; };
+template <> struct Plan2<1024> { static constexpr int S = 2, R0 = 32, R1 = 32, R2 = 1, RMAX = 32; };
 
-// v <- v * exp(DIR * 2 pi i k / R)
+// cos(2 pi m / 32): exact values of the 32nd roots of unity (the 16th roots are the even m).
+__host__ __device__ constexpr double cos32(int m) {
+  m &= 31;
+  const int a = m > 16 ? 32 - m : m;   // cos(2 pi m / 32) = cos(2 pi (32 - m) / 32)
+  const int b = a > 8 ? 16 - a : a;    // cos(pi - x) = -cos(x)
+  const double v = b == 0 ? 1.0 : b == 1 ? 0.98078528040323044913 : b == 2 ? 0.92387953251128675613
+                 : b == 3 ? 0.83146961230254523708 : b == 4 ? 0.70710678118654752440
+                 : b == 5 ? 0.55557023301960222474 : b == 6 ? 0.38268343236508977173
+                 : b == 7 ? 0.19509032201612826785 : 0.0;
+  return a > 8 ? -v : v;
+}
+__host__ __device__ constexpr double sin32(int m) { return cos32(m - 8); }
+
+// v <- v * exp(DIR * 2 pi i k / R), R <= 32
 template <int R, int DIR, typename C>
 __device__ __forceinline__ C root_mul(C v, int k) {
   using T = decltype(v.x);
-  const int m = k * (16 / R);
-  const T c = (T)cos16(m), s = (T)(DIR * sin16(m));
+  static_assert(R <= 32, "roots of unity up to order 32");
+  const int m = k * (32 / R);
+  const T c = (T)cos32(m), s = (T)(DIR * sin32(m));
   return cmake<C>(v.x * c - v.y * s, v.x * s + v.y * c);
 }
 
@@ -178,10 +186,10 @@ __device__ __forceinline__ void stage(const Src& src, const Dst& dst, const TW& 
   }
 }
 
-// Full length-L DFT of a tile: src -> (mid) -> dst.  `mid` must be a shared tile.
-template <typename T, int L, int TC, int NT, int DIR, class Src, class Mid, class Dst, class TW>
+// Full length-L DFT of a tile: src -> (mid) -> dst.  `mid` must be a shared tile.  P: the
+// radix plan (Plan<L> or Plan2<L>).
+template <typename T, int L, int TC, int NT, int DIR, class P = Plan<L>, class Src, class Mid, class Dst, class TW>
 __device__ __forceinline__ void fft_tile(const Src& src, const Mid& mid, const Dst& dst, const TW& tw) {
-  using P = Plan<L>;
   if constexpr (P::S == 1) {
     stage<T, L, TC, NT, P::R0, 1, DIR>(src, dst, tw);
   } else if constexpr (P::S == 2) {

@@ -102,9 +102,16 @@ struct DenseTile {
   __host__ __device__ static constexpr int delta(int d) { return d; }
 };
 
+// Tiles of the staged passes: 64 KB of TC columns (at least 128-byte rows of a TMA box for
+// L >= 512), transformed with the two-stage radix-32 plans at L = 512 and 1024, where a
+// third stage would add a read and a write of the whole tile in shared memory.
 template <typename T, int L> struct TmaTile {
+  using P = Plan2<L>;
   using CT = ColTile<T, L>;
-  static constexpr int TC = CT::TC, NT = CT::NT, LD = TC;
+  static constexpr int TC = L >= 512 ? 65536 / (L * (int)sizeof(cx_t<T>)) : CT::TC;
+  static constexpr int NT = TC * L / P::RMAX;
+  static constexpr int LD = TC;
+  static_assert(NT <= 512 && (L / 2) % TC == 0, "TMA tile shape");
   static constexpr int RB = L < 256 ? L : 256;                  // rows per TMA box
   static constexpr int TILE = L * TC;                            // complex elements per tile
   static constexpr int BYTES = TILE * (int)sizeof(cx_t<T>);
@@ -139,8 +146,8 @@ struct DenseMulSrc {
   const cx_t<T>* p;
   ZCol<T, N> z;
   int mode;
-  __device__ __forceinline__ cx_t<T> ld(int row, int c) const {
-    const cx_t<T> v = p[row * LD + c];
+  __device__ __forceinline__ cx_t<T> ld(int row, int c) const { return apply(p[row * LD + c], row, z, mode); }
+  static __device__ __forceinline__ cx_t<T> apply(cx_t<T> v, int row, const ZCol<T, N>& z, int mode) {
     const int f0 = freq_of(row, N);
     const T g = z.g(f0);
     if (mode == 1) return cmake<cx_t<T>>(v.x * g, v.y * g);
@@ -310,7 +317,7 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
     C* cur = slot(q);
     DenseTile<C, TT::LD> t{cur};
     if constexpr (KIND == 0) {
-      fft_tile<T, L, TT::TC, TT::NT, DIR>(t, t, t, tw);
+      fft_tile<T, L, TT::TC, TT::NT, DIR, typename TT::P>(t, t, t, tw);
       fence_proxy_async();
       __syncthreads();
       if (threadIdx.x == 0) store(&maps.m[item / tiles_per_buf], cur, kxg, o, b);
@@ -323,8 +330,59 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
       zc.dtab = job.dtab;
       zc.d12 = job.dtab ? job.dtab[zc.f1 < 0 ? zc.f1 + N : zc.f1] * job.dtab[zc.f2] : (T)1;
       DenseTile<C, TT::LD> wt{work};
-      if constexpr (KIND == 1) {
-        fft_tile<T, L, TT::TC, TT::NT, -1>(t, t, t, stw);
+      if constexpr (KIND == 1 && TT::P::S == 2) {
+        // two-stage plan (RA, RB): the forward transform's last stage leaves the spectrum
+        // in registers, item j holding rows j + RA r (r < RB) -- exactly the inputs of the
+        // first stage of an inverse transform planned as (RB, RA) -- so both inverse
+        // transforms start from registers instead of a shared-memory round trip
+        constexpr int RA = TT::P::R0, RB = TT::P::R1, TC = TT::TC, NT = TT::NT;
+        constexpr int PER = TC * (L / RB) / NT;
+        stage<T, L, TC, NT, RA, 1, -1>(t, t, stw);
+        __syncthreads();
+        C x[PER][RB];
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+          const int j = (threadIdx.x + i * NT) / TC;      // j < L / RB = RA
+#pragma unroll
+          for (int r = 0; r < RB; ++r) x[i][r] = cur[(j + r * RA) * TT::LD + c];
+#pragma unroll
+          for (int r = 1; r < RB; ++r) x[i][r] = cmul(x[i][r], twiddle<-1>(stw, r * j));   // jm = j, L/(RA RB) = 1
+          dft<RB, -1>(x[i]);                                // x[i][r] = X[j + RA r]
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          // the other ring slot and the work tile are no longer read by the previous
+          // tile's stores: refill the slot
+          bulk_wait_read_all();
+          if (q + 1 < nq) issue(q + 1);
+        }
+        __syncthreads();   // the work tile is written below, after that wait
+#pragma unroll
+        for (int mode = 0; mode < 2; ++mode) {
+          // mode 0: -i k_0 G X (z force) -> work; mode 1: G X (U) -> the ring slot
+          C* dst = mode == 0 ? work : cur;
+#pragma unroll
+          for (int i = 0; i < PER; ++i) {
+            const int j = (threadIdx.x + i * NT) / TC;
+            C y[RB];
+#pragma unroll
+            for (int r = 0; r < RB; ++r) y[r] = DenseMulSrc<T, N, TT::LD>::apply(x[i][r], j + RA * r, zc, mode);
+            dft<RB, +1>(y);                                  // inverse stage 1 (NS = 1)
+#pragma unroll
+            for (int r = 0; r < RB; ++r) dst[(j * RB + r) * TT::LD + c] = y[r];
+          }
+        }
+        __syncthreads();
+        stage<T, L, TC, NT, RA, RB, +1>(wt, wt, stw);        // inverse stage 2 of the z force
+        fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) store(&omaps.m[0], work, kxg, o, b);
+        stage<T, L, TC, NT, RA, RB, +1>(t, t, stw);          // and of U
+        fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) store(&omaps.m[1], cur, kxg, o, b);
+      } else if constexpr (KIND == 1) {
+        fft_tile<T, L, TT::TC, TT::NT, -1, typename TT::P>(t, t, t, stw);
         __syncthreads();
         if (threadIdx.x == 0) {
           // the other ring slot and the work tile are no longer read by the previous
@@ -335,13 +393,13 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
         }
         // z force: -i k_0 G T -> work -> out[0]
         DenseMulSrc<T, N, TT::LD> src0{cur, zc, 0};
-        fft_tile<T, L, TT::TC, TT::NT, +1>(src0, wt, wt, stw);
+        fft_tile<T, L, TT::TC, TT::NT, +1, typename TT::P>(src0, wt, wt, stw);
         fence_proxy_async();
         __syncthreads();
         if (threadIdx.x == 0) store(&omaps.m[0], work, kxg, o, b);
         // U: G T -> in place in the ring slot -> out[1]
         DenseMulSrc<T, N, TT::LD> src1{cur, zc, 1};
-        fft_tile<T, L, TT::TC, TT::NT, +1>(src1, t, t, stw);
+        fft_tile<T, L, TT::TC, TT::NT, +1, typename TT::P>(src1, t, t, stw);
         fence_proxy_async();
         __syncthreads();
         if (threadIdx.x == 0) store(&omaps.m[1], cur, kxg, o, b);
@@ -350,10 +408,10 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
         // barriers of the earlier ones: the previous item's store must have read it
         if (comp == 0 && threadIdx.x == 0) bulk_wait_read_all();
         DenseAccDst<T, N, TT::LD> acc{work, zc, comp};
-        fft_tile<T, L, TT::TC, TT::NT, -1>(t, t, acc, stw);
+        fft_tile<T, L, TT::TC, TT::NT, -1, typename TT::P>(t, t, acc, stw);
         if (comp == 1) {
           __syncthreads();
-          fft_tile<T, L, TT::TC, TT::NT, +1>(wt, wt, wt, stw);
+          fft_tile<T, L, TT::TC, TT::NT, +1, typename TT::P>(wt, wt, wt, stw);
           fence_proxy_async();
           __syncthreads();
           if (threadIdx.x == 0) store(&omaps.m[0], work, kxg, o, b);
@@ -363,7 +421,7 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
       // inverse y of the shared x/y force transform U: IFFT(U) -> out[1] (the x component
       // before its -i k_2), IFFT(-i k_1 U) -> out[0] (the y component, in place)
       DenseTile<C, TT::LD> wt{work};
-      fft_tile<T, L, TT::TC, TT::NT, +1>(t, wt, wt, stw);
+      fft_tile<T, L, TT::TC, TT::NT, +1, typename TT::P>(t, wt, wt, stw);
       fence_proxy_async();
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -372,7 +430,7 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
         if (q + 1 < nq) issue(q + 1);
       }
       YMulSrc<T, N, TT::LD> src{cur};
-      fft_tile<T, L, TT::TC, TT::NT, +1>(src, t, t, stw);
+      fft_tile<T, L, TT::TC, TT::NT, +1, typename TT::P>(src, t, t, stw);
       fence_proxy_async();
       __syncthreads();
       if (threadIdx.x == 0) store(&omaps.m[0], cur, kxg, o, b);
@@ -381,10 +439,10 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
       if (comp == 0) {
         if (threadIdx.x == 0) bulk_wait_read_all();   // the previous item's store of the work tile
         YAccDst<T, N, TT::LD> acc{work};
-        fft_tile<T, L, TT::TC, TT::NT, -1>(t, t, acc, stw);
+        fft_tile<T, L, TT::TC, TT::NT, -1, typename TT::P>(t, t, acc, stw);
       } else {
         YMergeDst<T, TT::LD> dst{work, (T)(kxg * TT::TC + c)};
-        fft_tile<T, L, TT::TC, TT::NT, -1>(t, t, dst, stw);
+        fft_tile<T, L, TT::TC, TT::NT, -1, typename TT::P>(t, t, dst, stw);
         fence_proxy_async();
         __syncthreads();
         if (threadIdx.x == 0) store(&omaps.m[0], work, kxg, o, b);
