@@ -52,16 +52,16 @@ def _peaks():
 
 
 # ------------------------------------------------------------------ algorithmic bytes
-def algorithmic_bytes(n_steps, N, M, batch=1, fused_x=False):
+def algorithmic_bytes(n_steps, N, M, batch=1, fused_x=0):
     """Per-pass FP32 traffic per gradient evaluation and per kernel category: one read and
     one write of every mesh a pass touches, particle arrays read and written once.
     Forward: n+1 force evaluations; adjoint: n+1 forward + adjoint force evaluations.
-    With the deposit fused with the R2C x pass (fused_x) the deposit writes the half
-    spectra (the same bytes as the real meshes) and the x pass of the R2C disappears."""
+    A deposit fused with the R2C x pass (fused_x bit 0: forward, bit 1: adjoint) writes
+    the half spectra (the same bytes as the real meshes) and its x pass disappears."""
     f = n_steps + 1
     b = {
         "scatter": f * (4 * M + 12 * N) + f * (16 * M + 24 * N),
-        "fft_x_r2c": 0 if fused_x else f * 8 * M + f * 32 * M,
+        "fft_x_r2c": (0 if fused_x & 1 else f * 8 * M) + (0 if fused_x & 2 else f * 32 * M),
         # y passes: forward chain delta (8M) + z force (8M) + the x/y split (4M in, 8M out);
         # adjoint chain delta, P_0 (16M) + the x/y merge (8M in, 4M out) + z force, psi
         # (16M) + split (12M)
@@ -428,7 +428,7 @@ def run_ours(args, rank, world, local_rank):
         return
 
     peak, peak_kind = _peaks()
-    alg = algorithmic_bytes(n, N, M, fused_x=bool(tuning.get("fused_x")))
+    alg = algorithmic_bytes(n, N, M, fused_x=int(tuning.get("fused_x", 0)))
     ms_pm_step = ms_per_eval / n
     # headline: the whole adjoint-gradient PM step (one forward + one adjoint step) against
     # its compulsory traffic (one read and one write per 3-D FFT, fused Fourier multipliers:

@@ -238,10 +238,11 @@ long long pm_scratch_bytes(const pm_ctx* ctx);
  *   threads_adjoint      : threads per tile, 256 or 512
  *   tma_columns          : 1 = TMA-staged persistent y/z column passes (meshes 128..1024),
  *                          0 = unstaged column passes
- *   fused_x              : 1 = the deposit writes the half spectra of its whole-row tiles
- *                          (CIC deposit and x pass of the R2C in one kernel, meshes
- *                          128..1024), 0 = the deposit writes real meshes and a separate x
- *                          pass transforms them; the tile shapes above apply to the latter
+ *   fused_x              : bit 0 (forward deposit) and bit 1 (adjoint deposit) set = that
+ *                          deposit writes the half spectra of its whole-row tiles (CIC
+ *                          deposit and x pass of the R2C in one kernel, meshes 128..1024);
+ *                          clear = it writes real meshes and a separate x pass transforms
+ *                          them (the tile shapes above apply to that form)
  */
 typedef struct pm_tuning {
   int tile_log2_density[3];
@@ -249,8 +250,9 @@ typedef struct pm_tuning {
   int threads_density;
   int threads_adjoint;
   int tma_columns;
-  int fused_x;      /* 1 = deposit fused with the x pass of the R2C (tiles of whole x rows;
-                       meshes 128..1024), 0 = separate passes */
+  int fused_x;      /* deposits fused with the x pass of the R2C (tiles of whole x rows;
+                       meshes 128..1024): bit 0 the density deposit of the forward steps,
+                       bit 1 the density + pi deposit of the adjoint steps; 0 = separate */
 } pm_tuning;
 
 /* Current launch shapes.  Errors: PM_ERR_ARG (null pointers). */
@@ -262,7 +264,8 @@ int pm_set_tuning(pm_ctx* ctx, const pm_tuning* t);
 
 /*
  * Autotuner: times every candidate deposit tile shape x threads per tile (for the forward
- * and the adjoint deposit separately) and both column-pass forms on the context's current
+ * and the adjoint deposit separately), then each deposit fused with the x pass against the
+ * best separate deposit plus x pass, and both column-pass forms on the context's current
  * particle state (the final state of the last pm_forward, else the Zel'dovich state), each
  * `reps` times with CUDA events on the context's stream (median; reps = 0 means 3), and
  * keeps the fastest.  Uses the context's scratch meshes and its adjoint buffers as scratch
@@ -318,12 +321,44 @@ int pm_op_za(pm_ctx* ctx, void* s1_out);
  * Every following pm_adjoint adds the cotangents of snapshot q, read when the reverse pass
  * reaches step j (so they may be written between pm_forward and pm_adjoint), to those of
  * the final state.  The buffers stay owned by the caller and must outlive their use.
- * Momenta are observed at the final step only (pm_adjoint's dJ_dmom): inside the leapfrog
- * the momentum is held at half steps.  Drops a captured pm_gradient_graph.
- * Errors: PM_ERR_ARG for a bad count or step list.
+ * Momenta of the snapshots: pm_set_snapshot_momenta.  Drops a captured pm_gradient_graph
+ * and the snapshot momenta.  Errors: PM_ERR_ARG for a bad count or step list.
  */
 int pm_set_snapshots(pm_ctx* ctx, int nsnap, const int* steps, void* disp_out, void* dens_out, const void* dJ_ddisp,
                      const void* dJ_ddens);
+
+/*
+ * Momenta of the states observed by pm_set_snapshots (Sec. 2.4: an objective on z_j =
+ * (x_j, p_j)), the full-step momentum p_j after the kick K2_j (p_0 the initial momentum).
+ *   mom_out : optional device [nsnap][batch][3][n_ptcl^3]: every following pm_forward writes
+ *             p_j of snapshot q into mom_out[q]
+ *   dJ_dmom : optional device [nsnap][batch][3][n_ptcl^3]: dJ/dp_j, added by every following
+ *             pm_adjoint where the reverse pass holds p_j: the reverse kick K2_j, which made
+ *             p_j, sees pi + dJ/dp_j, the reverse kick K1_{j+1} pi alone (Eq. 49)
+ * Null pointers clear the respective part.  Errors: PM_ERR_STATE without snapshots.
+ */
+int pm_set_snapshot_momenta(pm_ctx* ctx, void* mom_out, const void* dJ_dmom);
+
+/*
+ * Positions observed between steps (Sec. 2.4: observations need not fall on the time
+ * steps).  For a scale factor a inside step j + 1 (a_j < a <= a_{j+1}) the displacement is
+ * that of the step's drift stopped at a,
+ *   s(a) = s_j + Dp_j(a) p_{j+1/2},   Dp_j(a) = [D1(a) - D1(a_j)] / G_D(a_{j+1/2})
+ * (the FastPM drift factor of Eq. 15 with a in place of a_{j+1}).
+ *   na       : 0..PM_MAX_SNAPSHOTS; 0 clears
+ *   a        : host [na] doubles, strictly ascending in (a0, a1]
+ *   disp_out : optional device [na][batch][3][n_ptcl^3]: every following pm_forward writes
+ *              s(a_q)
+ *   dens_out : optional device [na][batch][n_mesh^3]: delta at q + s(a_q) (the same
+ *              deterministic fixed-point CIC deposit as pm_op_density)
+ *   dJ_ddisp, dJ_ddens : optional device cotangents on s(a_q) and delta(a_q): every following
+ *              pm_adjoint adds u = dJ/dx(a) (the density part through the CIC weight
+ *              gradient at x(a)) to xi_j and Dp_j(a) u to pi_{j+1/2}, with the theta term
+ *              (u . p_{j+1/2}) dDp_j/dOmega_m
+ * Drops a captured pm_gradient_graph.  Errors: PM_ERR_ARG for a bad count or a list.
+ */
+int pm_set_interp_snapshots(pm_ctx* ctx, int na, const double* a, void* disp_out, void* dens_out,
+                            const void* dJ_ddisp, const void* dJ_ddens);
 
 /* Initial state at a0 of the context's lpt_order (Sec. 2.1, Eq. 2): s0 = D1 s1 (+ D2 s2),
  * p0 = a^2 H (D1' s1 (+ D2' s2)).  s0_out, p0_out: optional (null: not written),

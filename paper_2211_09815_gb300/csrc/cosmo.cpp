@@ -204,5 +204,23 @@ void time_coefficients(double a0, double a1, int n, double om, TimeCoef& out) {
   out.dgd2_a0 = std::imag(cgd2) / kEps;
 }
 
+void partial_drift(double a0, double a1, int n, double om, double a, PartialDrift& out) {
+  auto node = [&](int i) { return a0 + (a1 - a0) * (0.5 * (2 * i)) / n; };   // a_i as in time_coefficients
+  int j = (int)std::ceil((a - a0) / (a1 - a0) * n) - 1;
+  j = j < 0 ? 0 : (j > n - 1 ? n - 1 : j);
+  while (j > 0 && !(node(j) < a)) --j;
+  while (j < n - 1 && node(j + 1) < a) ++j;
+  const double aj = node(j), ah = a0 + (a1 - a0) * (0.5 * (2 * j + 1)) / n;
+  std::vector<double> d1, gd, gk, d1h, gdh, gkh;
+  std::vector<cd> cd1, cgd, cgk, cd1h, cgdh, cgkh;
+  factors(std::vector<double>{aj, a}, om, d1, gd, gk);
+  factors(std::vector<double>{ah}, om, d1h, gdh, gkh);
+  factors(std::vector<double>{aj, a}, cd(om, kEps), cd1, cgd, cgk);
+  factors(std::vector<double>{ah}, cd(om, kEps), cd1h, cgdh, cgkh);
+  out.j = j;
+  out.fac = (d1[1] - d1[0]) / gdh[0];
+  out.dfac = std::imag((cd1[1] - cd1[0]) / cgdh[0]) / kEps;
+}
+
 }  // namespace cosmo
 }  // namespace pmgb

@@ -19,6 +19,15 @@ void time_coefficients(double a0, double a1, int n, double omega_m, TimeCoef& ou
 void plin_tables(const double theta[5], double kf, int maxn2, std::vector<double>& p,
                  std::vector<double>& dlnp);
 
+// Drift factor of a position observed at scale factor a inside step j + 1, a_j < a <=
+// a_{j+1} of the linear-in-a grid: the FastPM drift of Sec. 2.3 (Eq. 15) stopped at a,
+// Dp_j(a) = [D1(a) - D1(a_j)] / G_D(a_{j+1/2}), and its d/dOmega_m.
+struct PartialDrift {
+  int j;
+  double fac, dfac;
+};
+void partial_drift(double a0, double a1, int n, double omega_m, double a, PartialDrift& out);
+
 double transfer_eh(double k, double om, double ob, double h);
 double plin_value(double k, const double theta[5]);
 

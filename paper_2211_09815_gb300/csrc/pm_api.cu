@@ -225,6 +225,17 @@ int pm_set_snapshots(pm_ctx* ctx, int nsnap, const int* steps, void* disp_out, v
   return ctx->eng->set_snapshots(nsnap, steps, disp_out, dens_out, dJ_ddisp, dJ_ddens);
 }
 
+int pm_set_snapshot_momenta(pm_ctx* ctx, void* mom_out, const void* dJ_dmom) {
+  if (!ctx) return PM_ERR_ARG;
+  return ctx->eng->set_snapshot_momenta(mom_out, dJ_dmom);
+}
+
+int pm_set_interp_snapshots(pm_ctx* ctx, int na, const double* a, void* disp_out, void* dens_out,
+                            const void* dJ_ddisp, const void* dJ_ddens) {
+  if (!ctx) return PM_ERR_ARG;
+  return ctx->eng->set_interp_snapshots(na, a, disp_out, dens_out, dJ_ddisp, dJ_ddens);
+}
+
 int pm_op_ic(pm_ctx* ctx, void* s0_out, void* p0_out) {
   if (!ctx) return PM_ERR_ARG;
   return ctx->eng->op_ic(s0_out, p0_out);

@@ -210,14 +210,18 @@ class Engine : public EngineBase {
       }
       const long long fis = 2 * spec_len_cx(nm_);
       StepCoef<T> sc{fkA_, fkB_, fdr_};
+      T* snap_p = (q >= 0 && snap_mom_) ? snap_mom_ + (long long)q * B_ * 3 * N_ : nullptr;
       prof_.begin(st_, P_GATHER_FWD, 1);
       // the bins of the next step's deposit are counted at the new positions
       k_gather_fwd<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, s_, p_, j == n_ ? a_ : nullptr, fvec_, sc, j,
-                                                              n_ + 1, cks, ckp, fused_ ? bgf1_ : bg1_,
-                                                              j < n_ ? bcount_ : nullptr, bkeys_);
+                                                              n_ + 1, cks, ckp, fused1_ ? bgf1_ : bg1_,
+                                                              j < n_ ? bcount_ : nullptr, bkeys_, snap_p);
       counted_ = j < n_;
       prof_.end(st_, P_GATHER_FWD);
       PMGB_CK(cudaGetLastError());
+      // states observed between steps j and j + 1, from (s_{j+1}, p_{j+1/2})
+      for (size_t k = 0; k < interp_.size(); ++k)
+        if (interp_[k].j == j) PMGB_RET(interp_forward((int)k));
     }
     if (disp) PMGB_CK(cudaMemcpyAsync(disp, s_, sizeof(T) * B_ * 3 * N_, cudaMemcpyDeviceToDevice, st_));
     if (mom) PMGB_CK(cudaMemcpyAsync(mom, p_, sizeof(T) * B_ * 3 * N_, cudaMemcpyDeviceToDevice, st_));
@@ -260,6 +264,9 @@ class Engine : public EngineBase {
     counted_ = false;
     if (!have_fwd_) return PM_ERR_STATE;
     PMGB_CK(cudaMemsetAsync(pimax_, 0, sizeof(unsigned) * 3 * B_, st_));
+    const int nobs = n_ + 1 + (int)interp_.size();   // theta-term slots of the observations
+    const bool obs_theta = snap_gmom_ || (!interp_.empty() && (interp_gdisp_ || interp_gdens_));
+    if (obs_theta) PMGB_CK(cudaMemsetAsync(obs_part_, 0, sizeof(double) * nobs * B_ * G_, st_));
     prof_.begin(st_, P_OTHER, 1);
     k_adjoint_init<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, mass_, s_, (const T*)djdd, (const T*)djdx,
                                                               (const T*)djdp, xi_, pi_, pimax_);
@@ -277,6 +284,28 @@ class Engine : public EngineBase {
         prof_.end(st_, P_OTHER);
         PMGB_CK(cudaGetLastError());
       }
+      // positions observed between steps j and j + 1: (s_j, p_{j+1/2}) are held now
+      for (size_t k = 0; k < interp_.size(); ++k)
+        if (interp_[k].j == j && (interp_gdisp_ || interp_gdens_)) {
+          prof_.begin(st_, P_OTHER, 1);
+          k_obs_interp<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(
+              geo_, mass_, s_, p_, obs_fac_ + (long long)k * B_,
+              interp_gdens_ ? interp_gdens_ + (long long)k * B_ * M_ : nullptr,
+              interp_gdisp_ ? interp_gdisp_ + (long long)k * B_ * 3 * N_ : nullptr, xi_, pi_,
+              obs_part_ + (long long)(n_ + 1 + k) * B_ * G_, pimax_);
+          prof_.end(st_, P_OTHER);
+          PMGB_CK(cudaGetLastError());
+        }
+      // a momentum observed at step j: its share c of the cotangent enters pi before the
+      // force VJP, the rest after the reverse step
+      const T* vmom = (q >= 0 && snap_gmom_) ? snap_gmom_ + (long long)q * B_ * 3 * N_ : nullptr;
+      if (vmom) {
+        prof_.begin(st_, P_OTHER, 1);
+        k_obs_momentum<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, pi_, vmom, obs_c_, j, n_ + 1, 0, nullptr,
+                                                                  nullptr, pimax_);
+        prof_.end(st_, P_OTHER);
+        PMGB_CK(cudaGetLastError());
+      }
       PMGB_RET(force_chain(s_, pi_, false));
       const T* ckp = nullptr;
       const T* cks = nullptr;
@@ -289,13 +318,20 @@ class Engine : public EngineBase {
       double* ppa = part_ + (long long)(2 * j) * B_ * G_;
       double* pxp = part_ + (long long)(2 * j + 1) * B_ * G_;
       prof_.begin(st_, P_GATHER_ADJ, 1);
-      k_gather_adj<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, mass_, s_, p_, xi_, pi_, nullptr, nullptr, fvec_,
-                                                              sc, j, n_ + 1, ckp, cks, ppa, pxp, pimax_,
-                                                              fused_ ? bgf4_ : bg4_, j > 0 ? bcount_ : nullptr,
-                                                              bkeys_);
+      k_gather_adj<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, mass_, s_, p_, xi_, pi_, vmom ? a_ : nullptr,
+                                                              nullptr, fvec_, sc, j, n_ + 1, ckp, cks, ppa, pxp,
+                                                              pimax_, fused4_ ? bgf4_ : bg4_,
+                                                              j > 0 ? bcount_ : nullptr, bkeys_);
       counted_ = j > 0;
       prof_.end(st_, P_GATHER_ADJ);
       PMGB_CK(cudaGetLastError());
+      if (vmom) {
+        prof_.begin(st_, P_OTHER, 1);
+        k_obs_momentum<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, pi_, vmom, obs_c_, j, n_ + 1, 1, a_,
+                                                                  obs_part_ + (long long)j * B_ * G_, pimax_);
+        prof_.end(st_, P_OTHER);
+        PMGB_CK(cudaGetLastError());
+      }
     }
     // per-step sums: part_[(2j+q)][b][G] -> steps_[(2j+q)][b]
     prof_.begin(st_, P_OTHER, lpt2_ ? 16 + 39 : 16);
@@ -321,6 +357,10 @@ class Engine : public EngineBase {
     in.batch = B_;
     in.step_stride = 2 * B_;
     k_final_theta<<<(B_ + 31) / 32, 32, 0, st_>>>(in, theta_out_);
+    if (obs_theta) {
+      k_sum_partials<<<nobs * B_, 256, 0, st_>>>(obs_part_, G_, obs_sums_, 1.0);
+      k_obs_theta<<<(B_ + 31) / 32, 32, 0, st_>>>(obs_sums_, obs_w_, nobs, B_, theta_out_);
+    }
     prof_.end(st_, P_OTHER);
     PMGB_CK(cudaGetLastError());
     have_fwd_ = false;
@@ -529,6 +569,8 @@ class Engine : public EngineBase {
     }
     if (ns == 0) map.clear();
     snap_of_ = map;
+    snap_mom_ = nullptr;
+    snap_gmom_ = nullptr;
     snap_disp_ = ns ? (T*)disp : nullptr;
     snap_dens_ = ns ? (T*)dens : nullptr;
     snap_gdisp_ = ns ? (const T*)gdisp : nullptr;
@@ -540,6 +582,58 @@ class Engine : public EngineBase {
     return PM_OK;
   }
   int snap_of(int j) const { return snap_of_.empty() ? -1 : snap_of_[j]; }
+
+  int set_snapshot_momenta(void* mom, const void* gmom) override {
+    if (snap_of_.empty()) return PM_ERR_STATE;
+    snap_mom_ = (T*)mom;
+    snap_gmom_ = (const T*)gmom;
+    if (graph_exec_) {
+      cudaGraphExecDestroy(graph_exec_);
+      graph_exec_ = nullptr;
+    }
+    return PM_OK;
+  }
+
+  // Observed positions at scale factors between steps: each a_q in (a0, a1] (ascending)
+  // lies in step j + 1 = (a_j, a_{j+1}]; the partial drift factor and its d/dOmega_m per
+  // instance come from the host tables.
+  int set_interp_snapshots(int na, const double* a, void* disp, void* dens, const void* gdisp,
+                           const void* gdens) override {
+    if (na < 0 || na > PM_MAX_SNAPSHOTS || (na > 0 && !a)) return PM_ERR_ARG;
+    for (int k = 0; k < na; ++k)
+      if (!(a[k] > cfg_.a0) || !(a[k] <= cfg_.a1) || (k > 0 && !(a[k] > a[k - 1]))) return PM_ERR_ARG;
+    interp_a_.assign(a, a + na);
+    interp_disp_ = na ? (T*)disp : nullptr;
+    interp_dens_ = na ? (T*)dens : nullptr;
+    interp_gdisp_ = na ? (const T*)gdisp : nullptr;
+    interp_gdens_ = na ? (const T*)gdens : nullptr;
+    PMGB_RET(tables(theta_host_.data()));
+    if (graph_exec_) {
+      cudaGraphExecDestroy(graph_exec_);
+      graph_exec_ = nullptr;
+    }
+    return PM_OK;
+  }
+
+  // s(a_k) = s_{j+1} + (Dp_j(a_k) - D_{j+1}) p_{j+1/2} and, if asked, delta(a_k) by the
+  // global-atomic fixed-point deposit into the force mesh, free until the next force chain
+  // (the bins of the tile deposit are counted for the next step already).
+  int interp_forward(int k) {
+    T* out = interp_disp_ ? interp_disp_ + (long long)k * B_ * 3 * N_ : xi_;
+    prof_.begin(st_, P_OTHER, interp_dens_ ? 3 : 1);
+    k_interp_state<T><<<dim3(256, B_), 256, 0, st_>>>(s_, p_, obs_cf_ + (long long)k * B_, out, 3 * N_);
+    PMGB_CK(cudaGetLastError());
+    if (interp_dens_) {
+      unsigned long long* acc = reinterpret_cast<unsigned long long*>(fvec_);
+      PMGB_CK(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * B_ * M_, st_));
+      k_scatter<T, 1><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, out, nullptr, acc, e_d_, nullptr);
+      k_density_out<T><<<1024, 256, 0, st_>>>((const long long*)acc, interp_dens_ + (long long)k * B_ * M_,
+                                              (long long)B_ * M_, (T)(mass_ * std::ldexp(1.0, -e_d_)));
+      PMGB_CK(cudaGetLastError());
+    }
+    prof_.end(st_, P_OTHER);
+    return PM_OK;
+  }
 
   int op_ic(void* s0, void* p0) override {
     have_fwd_ = false;
@@ -573,6 +667,15 @@ class Engine : public EngineBase {
   // ---------------------------------------------------------------- host tables
   int tables(const double* theta) {
     const int n1 = n_ + 1;
+    if (theta != theta_host_.data()) theta_host_.assign(theta, theta + 5 * B_);
+    const int nq = (int)interp_a_.size();
+    // observations: share c_j of a momentum cotangent at step j that enters pi before the
+    // force VJP, the theta weights of the momentum (slot j) and interpolated-position
+    // (slot n + 1 + q) terms, and per interpolated position its step, drift factor and the
+    // forward coefficient Dp_j(a) - D_{j+1}
+    std::vector<T> oc((size_t)B_ * n1), ofac((size_t)std::max(1, nq) * B_), ocf((size_t)std::max(1, nq) * B_);
+    std::vector<double> ow((size_t)(n1 + nq) * B_, 0.0);
+    interp_.assign(nq, InterpObs{});
     std::vector<T> fkA(B_ * n1), fkB(B_ * n1), fdr(B_ * n1), rkA(B_ * n1), rkB(B_ * n1), rdr(B_ * n1);
     std::vector<double> wpa(n1 * B_), wxp(n1 * B_), dd1(B_), dgd(B_), dd2(B_), dgd2(B_);
     std::vector<T> d1(B_), gd(B_), d2(B_), gd2(B_), gcoef(B_);
@@ -599,6 +702,18 @@ class Engine : public EngineBase {
         if (j >= 1) w += tc.dk2[j - 1] + tc.k2[j - 1] / om;
         wpa[j * B_ + b] = w;
         wxp[j * B_ + b] = j >= 1 ? tc.ddd[j - 1] : 0.0;
+        const double k1n = j < n_ ? tc.k1[j] : 0.0, k2j = j >= 1 ? tc.k2[j - 1] : 0.0;
+        const double c = (k1n + k2j) != 0.0 ? k2j / (k1n + k2j) : 0.0;
+        oc[(size_t)b * n1 + j] = (T)c;
+        ow[(size_t)j * B_ + b] = (j >= 1 ? tc.dk2[j - 1] + k2j / om : 0.0) - c * w;
+      }
+      for (int k = 0; k < nq; ++k) {
+        cosmo::PartialDrift pd;
+        cosmo::partial_drift(cfg_.a0, cfg_.a1, n_, om, interp_a_[k], pd);
+        interp_[k].j = pd.j;
+        ofac[(size_t)k * B_ + b] = (T)pd.fac;
+        ocf[(size_t)k * B_ + b] = (T)(pd.fac - tc.dd[pd.j]);
+        ow[(size_t)(n1 + k) * B_ + b] = pd.dfac;
       }
       d1[b] = (T)tc.d1_a0;
       gd[b] = (T)tc.gd_a0;
@@ -628,6 +743,15 @@ class Engine : public EngineBase {
     PMGB_RET(upload(&rkA_, rkA));
     PMGB_RET(upload(&rkB_, rkB));
     PMGB_RET(upload(&rdr_, rdr));
+    PMGB_RET(upload(&obs_c_, oc));
+    PMGB_RET(upload_grow(&obs_fac_, ofac, obs_fac_n_));
+    PMGB_RET(upload_grow(&obs_cf_, ocf, obs_cf_n_));
+    PMGB_RET(upload_grow(&obs_w_, ow, obs_w_n_));
+    if (obs_sums_n_ < (long long)(n1 + nq) * B_) {
+      PMGB_RET(alloc(&obs_sums_, (long long)(n1 + nq) * B_));
+      PMGB_RET(alloc(&obs_part_, (long long)(n1 + nq) * B_ * G_));
+      obs_sums_n_ = (long long)(n1 + nq) * B_;
+    }
     PMGB_RET(upload(&wpa_, wpa));
     PMGB_RET(upload(&wxp_, wxp));
     PMGB_RET(upload(&dd1_, dd1));
@@ -670,6 +794,16 @@ class Engine : public EngineBase {
     PMGB_RET(alloc(&steps_, (long long)2 * (n_ + 1) * B_));
     PMGB_RET(alloc(&scal_, (long long)16 * B_));
     PMGB_RET(alloc(&theta_out_, (long long)5 * B_));
+    return PM_OK;
+  }
+  // upload into a buffer that is reallocated when the table outgrows it (cap: elements held)
+  template <typename U> int upload_grow(U** d, const std::vector<U>& h, long long& cap) {
+    if ((long long)h.size() > cap) {
+      PMGB_RET(alloc(d, (long long)h.size()));   // the old buffer stays owned until pm_destroy
+      cap = (long long)h.size();
+    }
+    PMGB_CK(cudaMemcpyAsync(*d, h.data(), sizeof(U) * h.size(), cudaMemcpyHostToDevice, st_));
+    PMGB_CK(cudaStreamSynchronize(st_));
     return PM_OK;
   }
   template <typename U> int upload(U** d, const std::vector<U>& h) {
@@ -761,7 +895,7 @@ class Engine : public EngineBase {
     tune_.threads_density = 256;
     tune_.threads_adjoint = 512;
     tune_.tma_columns = 1;
-    tune_.fused_x = fused_rows<T>(nm_, 1) > 0 ? 1 : 0;
+    tune_.fused_x = fused_rows<T>(nm_, 1) > 0 ? 3 : 0;
     const BinGeo smallest = make_bin_geo(ilog2(nm_), 3, 3, 3);
     const long long maxbin = (long long)B_ * smallest.nkeys + 1;
     PMGB_RET(alloc(&bkeys_, (long long)B_ * N_));
@@ -783,7 +917,8 @@ class Engine : public EngineBase {
     bg4_ = make_bin_geo(lg, tune_.tile_log2_adjoint[2], tune_.tile_log2_adjoint[1], tune_.tile_log2_adjoint[0]);
     use_tma_ = tune_.tma_columns != 0 && tma_supported(nm_);
     // deposit fused with the R2C x pass: tiles of whole x rows, R rows split over (y, z)
-    fused_ = tune_.fused_x != 0 && fused_rows<T>(nm_, 1) > 0;
+    fused1_ = (tune_.fused_x & 1) != 0 && fused_rows<T>(nm_, 1) > 0;
+    fused4_ = (tune_.fused_x & 2) != 0 && fused_rows<T>(nm_, 1) > 0;
     if (fused_rows<T>(nm_, 1) > 0) {
       auto geo = [&](int rows) {
         const int lr = ilog2(rows);
@@ -810,7 +945,7 @@ class Engine : public EngineBase {
       return PM_ERR_ARG;
     if (t->tma_columns != 0 && t->tma_columns != 1) return PM_ERR_ARG;
     if (t->tma_columns && !tma_supported(nm_)) return PM_ERR_ARG;
-    if ((t->fused_x != 0 && t->fused_x != 1) || (t->fused_x && fused_rows<T>(nm_, 1) == 0)) return PM_ERR_ARG;
+    if (t->fused_x < 0 || t->fused_x > 3 || (t->fused_x && fused_rows<T>(nm_, 1) == 0)) return PM_ERR_ARG;
     tune_ = *t;
     apply_tuning();
     return PM_OK;
@@ -886,6 +1021,33 @@ class Engine : public EngineBase {
             (nq ? best.threads_adjoint : best.threads_density) = nt;
           }
         }
+      }
+    }
+    // deposit fused with the R2C x pass against the chosen separate deposit + x pass, for
+    // the density deposit (bit 0) and the density + pi deposit (bit 1) separately
+    if (fused_rows<T>(nm_, 1) > 0) {
+      best.fused_x = 0;
+      for (int nq = 0; nq < 2; ++nq) {
+        const int* l = nq ? best.tile_log2_adjoint : best.tile_log2_density;
+        const BinGeo bg = make_bin_geo(lg, l[2], l[1], l[0]);
+        const int nt = nq ? best.threads_adjoint : best.threads_density;
+        double ms_sep = 0, ms_fused = 0;
+        PMGB_RET(time_it([&]() {
+          PMGB_RET(deposit(s_, nq ? xi_ : nullptr, rmesh(0), sis, bg, nt));
+          RowJob<T> job{};
+          job.b[0] = RowBuf<T>{rmesh(0), sis, spec_[0]};
+          if (nq)
+            for (int c = 0; c < 3; ++c) job.b[1 + c] = RowBuf<T>{rmesh(4 + c), sis, spec_[4 + c]};
+          return fft_x_r2c<T>(nm_, job, nq ? 4 : 1, B_ * nm_ * nm_, tw_, st_);
+        }, &ms_sep));
+        FusedOut<T> fo{};
+        fo.spec[0] = spec_[0];
+        for (int c = 0; c < 3; ++c) fo.spec[1 + c] = nq ? spec_[4 + c] : nullptr;
+        PMGB_RET(time_it([&]() { return deposit(s_, nq ? xi_ : nullptr, nullptr, 0, nq ? bgf4_ : bgf1_, 0, false, &fo); },
+                         &ms_fused));
+        if (ms_fused < ms_sep) best.fused_x |= 1 << nq;
+        fused_ms_[2 * nq] = ms_sep;
+        fused_ms_[2 * nq + 1] = ms_fused;
       }
     }
     if (tma_supported(nm_)) {
@@ -997,7 +1159,7 @@ class Engine : public EngineBase {
     const long long sis = 2 * spec_len_cx(nm_);
     T* dmesh = keep_density ? dens_ : rmesh(0);
     const long long dis = keep_density ? M_ : sis;
-    if (fused_) {
+    if (pi ? fused4_ : fused1_) {
       // deposit and x pass in one kernel: delta (and pi_c) straight into the half spectra
       FusedOut<T> fo{};
       fo.spec[0] = spec_[0];
@@ -1268,6 +1430,16 @@ class Engine : public EngineBase {
   double* pw_out_ = nullptr;
   double* pl_buf_ = nullptr;   // power objective: target, weights, g, loss
   std::vector<int> snap_of_;   // observed states: step -> snapshot index (-1: none)
+  T* snap_mom_ = nullptr;      // momenta of the observed states (forward output)
+  const T* snap_gmom_ = nullptr;   // their cotangents (adjoint input)
+  struct InterpObs { int j; };  // an observed scale factor in step j + 1 = (a_j, a_{j+1}]
+  std::vector<InterpObs> interp_;
+  std::vector<double> interp_a_, theta_host_;
+  T *interp_disp_ = nullptr, *interp_dens_ = nullptr;
+  const T *interp_gdisp_ = nullptr, *interp_gdens_ = nullptr;
+  T *obs_c_ = nullptr, *obs_fac_ = nullptr, *obs_cf_ = nullptr;
+  double *obs_w_ = nullptr, *obs_sums_ = nullptr, *obs_part_ = nullptr;
+  long long obs_fac_n_ = 0, obs_cf_n_ = 0, obs_w_n_ = 0, obs_sums_n_ = 0;
   T *snap_disp_ = nullptr, *snap_dens_ = nullptr;
   const T *snap_gdisp_ = nullptr, *snap_gdens_ = nullptr;
   bool have_dens_ = false;
@@ -1276,7 +1448,8 @@ class Engine : public EngineBase {
   T *s_ = nullptr, *p_ = nullptr, *a_ = nullptr, *xi_ = nullptr, *pi_ = nullptr, *s1_ = nullptr, *omega_ = nullptr;
   BinGeo bg1_{}, bg4_{};
   BinGeo bgf1_{}, bgf4_{};   // whole-row tiles of the deposit fused with the R2C x pass
-  bool fused_ = false;
+  bool fused1_ = false, fused4_ = false;
+  double fused_ms_[4] = {};   // autotuner: separate and fused deposit times (density, density + pi)   // forward (density) / adjoint (density + pi) deposit fused
   bool counted_ = false;   // the last gather counted the bins of the next deposit
   pm_tuning tune_{};
   unsigned *bkeys_ = nullptr, *bcount_ = nullptr, *bstart_ = nullptr, *bcursor_ = nullptr, *bsums_ = nullptr;

@@ -295,7 +295,8 @@ template <typename T>
 __global__ void __launch_bounds__(kPtclThreads)
 k_gather_fwd(Geo<T> g, T* __restrict__ s, T* __restrict__ p, T* __restrict__ a_out,
              const V4<T>* __restrict__ fvec, StepCoef<T> sc, int j, int nstep1, T* __restrict__ ck_s,
-             T* __restrict__ ck_p, BinGeo bg, unsigned* __restrict__ bcount, unsigned* __restrict__ bkeys) {
+             T* __restrict__ ck_p, BinGeo bg, unsigned* __restrict__ bcount, unsigned* __restrict__ bkeys,
+             T* __restrict__ snap_p = nullptr) {
   const int b = blockIdx.y;
   const T kA = sc.kA[b * nstep1 + j], kB = sc.kB[b * nstep1 + j], dr = sc.dr[b * nstep1 + j];
   T* sb = s + (long long)b * 3 * g.N;
@@ -327,6 +328,7 @@ k_gather_fwd(Geo<T> g, T* __restrict__ s, T* __restrict__ p, T* __restrict__ a_o
     for (int c = 0; c < 3; ++c) {
       pv[c] += a[c] * kA;
       if (ck_p) ck_p[(long long)b * 3 * g.N + c * g.N + i] = pv[c];
+      if (snap_p) snap_p[(long long)b * 3 * g.N + c * g.N + i] = pv[c];   // p_j of an observed state
       pv[c] += a[c] * kB;
       if (ck_s) ck_s[(long long)b * 3 * g.N + c * g.N + i] = sv[c];
       sv[c] += pv[c] * dr;
@@ -511,6 +513,118 @@ k_obs_cotangent(Geo<T> g, T mass, const T* __restrict__ s, const T* __restrict__
       xi[po + c * g.N + i] += xv[c];
     }
   }
+}
+
+// Cotangent v = dJ/dp_j of an observed momentum (Sec. 2.4), added to pi in two parts
+// around the reverse step at force step j: the reverse kick K1_{j+1} uses pi, the
+// reverse kick K2_j (the one that made p_j) pi + v.  The force VJP is linear in pi, so one
+// VJP of pi + c v with c = K2_j / (K1_{j+1} + K2_j) gives both kicks' alpha terms:
+//   mode 0 (before the force chain): pi += c v
+//   mode 1 (after the reverse step):  pi += (1 - c) v, and the FP64 block sums of v . a_j
+//   (the theta term of the K2_j kick that pi + c v does not carry).
+// The fixed-point exponent of the next pi deposit is kept valid: max |pi| is folded into
+// pimax.
+template <typename T>
+__global__ void __launch_bounds__(kPtclThreads)
+k_obs_momentum(Geo<T> g, T* __restrict__ pi, const T* __restrict__ v, const T* __restrict__ ctab, int j, int nstep1,
+               int mode, const T* __restrict__ a, double* __restrict__ part, unsigned* __restrict__ pimax) {
+  __shared__ double shd[kPtclThreads / 32];
+  __shared__ float shf[kPtclThreads / 32];
+  const int b = blockIdx.y;
+  const long long po = (long long)b * 3 * g.N;
+  const T c = ctab[b * nstep1 + j];
+  const T w = mode == 0 ? c : (T)1 - c;
+  double acc = 0.0;
+  float mx[3] = {0.f, 0.f, 0.f};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N; i += (long long)gridDim.x * blockDim.x) {
+    T va = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const long long o = po + k * g.N + i;
+      const T q = pi[o] + w * v[o];
+      pi[o] = q;
+      mx[k] = fmaxf(mx[k], abs_up<T>(q));
+      if (mode == 1) va += v[o] * a[o];
+    }
+    acc += (double)va;
+  }
+  if (mode == 1) {
+    const double r = block_sum(acc, shd);
+    if (threadIdx.x == 0) part[(long long)b * gridDim.x + blockIdx.x] = r;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float m = block_max(mx[k], shf);
+    if (threadIdx.x == 0) atomicMax(pimax + k * gridDim.y + b, __float_as_uint(m));
+  }
+}
+
+// Cotangent of positions observed at a scale factor a between steps j and j + 1 (Sec. 2.4):
+// x(a) = q + s_j + Dp_j(a) p_{j+1/2} with the partial drift factor fac = Dp_j(a), taken
+// while the reverse pass holds (s_j, p_{j+1/2}) before the force VJP at x_j:
+//   u = m sum_g grad W(g - x(a)) dJ/d delta(a)(g) + dJ/dx(a);  xi += u;  pi += fac u;
+// and the FP64 block sums of u . p_{j+1/2} (the theta term of Dp_j).
+template <typename T>
+__global__ void __launch_bounds__(kPtclThreads)
+k_obs_interp(Geo<T> g, T mass, const T* __restrict__ s, const T* __restrict__ p, const T* __restrict__ fac_tab,
+             const T* __restrict__ djdd, const T* __restrict__ djdx, T* __restrict__ xi, T* __restrict__ pi,
+             double* __restrict__ part, unsigned* __restrict__ pimax) {
+  __shared__ double shd[kPtclThreads / 32];
+  __shared__ float shf[kPtclThreads / 32];
+  const int b = blockIdx.y;
+  const long long po = (long long)b * 3 * g.N;
+  const T fac = fac_tab[b];
+  double acc = 0.0;
+  float mx[3] = {0.f, 0.f, 0.f};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N; i += (long long)gridDim.x * blockDim.x) {
+    T u[3] = {0, 0, 0};
+    const T pv[3] = {p[po + i], p[po + g.N + i], p[po + 2 * g.N + i]};
+    if (djdd) {
+      const T sa[3] = {s[po + i] + fac * pv[0], s[po + g.N + i] + fac * pv[1], s[po + 2 * g.N + i] + fac * pv[2]};
+      cic_grad_gather(g, i, sa, djdd + (long long)b * g.M, mass, u);
+    }
+    T up = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const long long o = po + k * g.N + i;
+      if (djdx) u[k] += djdx[o];
+      xi[o] += u[k];
+      const T q = pi[o] + fac * u[k];
+      pi[o] = q;
+      mx[k] = fmaxf(mx[k], abs_up<T>(q));
+      up += u[k] * pv[k];
+    }
+    acc += (double)up;
+  }
+  const double r = block_sum(acc, shd);
+  if (threadIdx.x == 0) part[(long long)b * gridDim.x + blockIdx.x] = r;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float m = block_max(mx[k], shf);
+    if (threadIdx.x == 0) atomicMax(pimax + k * gridDim.y + b, __float_as_uint(m));
+  }
+}
+
+// Forward: the displacement at an observed scale factor a between steps j and j + 1 from
+// the state right after the step's gather, s(a) = s_{j+1} + (Dp_j(a) - D_{j+1}) p_{j+1/2}.
+template <typename T>
+__global__ void k_interp_state(const T* __restrict__ s, const T* __restrict__ p, const T* __restrict__ cf_tab,
+                               T* __restrict__ out, long long n3) {
+  const int b = blockIdx.y;
+  const T cf = cf_tab[b];
+  const long long o = (long long)b * n3;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3; i += (long long)gridDim.x * blockDim.x)
+    out[o + i] = s[o + i] + cf * p[o + i];
+}
+
+// theta[b][2] (Omega_m) += sum_k w[k][b] sums[k][b]: the theta terms of the observations
+static __global__ void k_obs_theta(const double* __restrict__ sums, const double* __restrict__ w, int nk, int batch,
+                                   double* __restrict__ theta) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  double acc = 0.0;
+  for (int k = 0; k < nk; ++k) acc += w[(long long)k * batch + b] * sums[(long long)k * batch + b];
+  theta[5 * b + 2] += acc;
 }
 
 // delta = m acc 2^-e - 1 (no zeroing)

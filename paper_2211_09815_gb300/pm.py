@@ -19,7 +19,7 @@ SYMBOLS = ("pm_init", "pm_forward", "pm_loss_mse", "pm_adjoint", "pm_destroy", "
            "pm_op_fft", "pm_op_za", "pm_set_inputs", "pm_gradient", "pm_profile", "pm_profile_read",
            "pm_density_noalloc", "pm_power_spectrum", "pm_gradient_graph", "pm_get_tuning", "pm_set_tuning",
            "pm_autotune", "pm_op_ic", "pm_loss_power", "pm_set_snapshots", "pm_check", "pm_debug_fail_alloc",
-           "pm_debug_live_bytes", "pm_debug_first_wait")
+           "pm_debug_live_bytes", "pm_debug_first_wait", "pm_set_snapshot_momenta", "pm_set_interp_snapshots")
 NOALLOC_MAX_CELLS = 128 ** 3
 PROF_NAMES = ("scatter", "fft_x_r2c", "fft_cols", "fused_z_force", "fused_z_adjoint", "fft_x_c2r",
               "gather_fwd", "gather_adj", "other")
@@ -95,6 +95,8 @@ def load_library(path=LIB_PATH):
     lib.pm_set_tuning.argtypes = [vp, ctypes.POINTER(PMTuning)]
     lib.pm_autotune.argtypes = [vp, i, ctypes.POINTER(PMTuning), vp]
     lib.pm_check.argtypes = [vp]
+    lib.pm_set_snapshot_momenta.argtypes = [vp, vp, vp]
+    lib.pm_set_interp_snapshots.argtypes = [vp, i, dp, vp, vp, vp, vp]
     lib.pm_debug_fail_alloc.argtypes = [ctypes.c_longlong]
     lib.pm_debug_live_bytes.argtypes = []
     lib.pm_debug_live_bytes.restype = ctypes.c_longlong
@@ -272,6 +274,32 @@ class PMContext:
                                                self._p(dens, m, "dens"), self._p(ddisp, v, "ddisp"),
                                                self._p(ddens, m, "ddens")), "pm_set_snapshots")
         self._snapshot_buffers = (disp, dens, ddisp, ddens) if ns else None
+        self._snapshot_steps = steps
+        self._snapshot_momenta = None
+
+    def set_snapshot_momenta(self, mom=None, dmom=None):
+        """Momenta p_j of the snapshot steps: each forward writes them into mom[q], each
+        adjoint adds the cotangents dmom[q] (CUDA tensors of len(steps) x batch x 3 N)."""
+        ns = len(self._snapshot_steps)
+        v = ns * 3 * self.batch * self.N
+        _check(load_library().pm_set_snapshot_momenta(self._h, self._p(mom, v, "mom"), self._p(dmom, v, "dmom")),
+               "pm_set_snapshot_momenta")
+        self._snapshot_momenta = (mom, dmom)
+
+    def set_interp_snapshots(self, a_values, disp=None, dens=None, ddisp=None, ddens=None):
+        """Positions at scale factors between steps (ascending, in (a0, a1]): each forward
+        writes s(a_q) into disp[q] and delta(a_q) into dens[q]; each adjoint adds the
+        cotangents ddisp[q], ddens[q].  Buffers: CUDA tensors of len(a_values) x batch x
+        (3 N or M) elements, kept referenced here while in use."""
+        import numpy as np
+        a = np.ascontiguousarray(np.asarray(a_values, dtype=np.float64).ravel())
+        na = a.size
+        v, m = na * 3 * self.batch * self.N, na * self.batch * self.M
+        _check(load_library().pm_set_interp_snapshots(
+            self._h, na, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self._p(disp, v, "disp"),
+            self._p(dens, m, "dens"), self._p(ddisp, v, "ddisp"), self._p(ddens, m, "ddens")),
+            "pm_set_interp_snapshots")
+        self._interp_buffers = (disp, dens, ddisp, ddens) if na else None
 
     def op_ic(self, s0=None, p0=None):
         """Initial state (s0, p0) at a0 of the context's LPT order."""

@@ -177,3 +177,75 @@ def test_set_snapshots_rejects_bad_step_lists():
     ctx.set_snapshots([0, 4])
     ctx.set_snapshots([])
     ctx.close()
+
+
+@pytest.mark.parametrize("precision,ckpt", [(1, 0), (1, 2), (0, 0)])
+def test_momentum_and_interpolated_observations_match_oracle(precision, ckpt):
+    """Momenta observed at intermediate steps (pm_set_snapshot_momenta: the force VJP of
+    step j split between its two reverse kicks) and positions observed between steps
+    (pm_set_interp_snapshots: the drift of the step stopped at a), together with the step
+    snapshots: the forward outputs p_j, s(a), delta(a) and the whole gradient against the
+    oracle's FD-pinned adjoint (obs with dJ/dp_j, obs_a)."""
+    torch = torch_cuda()
+    cfg = oracle_cfg(**SNAP)
+    om = inputs.white_noise(SNAP["n_ptcl"], 1).astype(np.float64)
+    agrid = np.linspace(cfg.a0, cfg.a1, SNAP["n_steps"] + 1)
+    a_obs = [0.5 * (agrid[1] + agrid[2]), agrid[3] + 0.2 * (agrid[4] - agrid[3]), agrid[5]]
+    fwd = opm.forward(om, THETA, cfg, store_every=ckpt, snapshots=SNAP_STEPS, snapshot_a=a_obs)
+    N, M, ns, na = SNAP["n_ptcl"] ** 3, SNAP["n_mesh"] ** 3, len(SNAP_STEPS), len(a_obs)
+    rng = np.random.default_rng(41)
+    ddens, ddisp = _snapshot_cotangents()
+    dmom = rng.normal(size=(ns, 3, N)) * 1e-3
+    adens = rng.normal(size=(na, M)) / M
+    adisp = rng.normal(size=(na, 3, N)) * 1e-3
+    obs = {j: (ddens[q], ddisp[q], dmom[q]) for q, j in enumerate(SNAP_STEPS)}
+    obs_a = {a: (adens[k], adisp[k]) for k, a in enumerate(a_obs)}
+    adj = opm.adjoint(om, THETA, cfg, fwd, obs=obs, obs_a=obs_a, ckpt=fwd["store"] if ckpt else None)
+
+    ctx, *_ = make_ctx(SNAP["box"], SNAP["n_mesh"], SNAP["n_ptcl"], SNAP["n_steps"], precision=precision,
+                       ckpt_every=ckpt)
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a.ravel())).to("cuda", ctx.dtype)
+    mom = torch.empty(ns * 3 * N, device="cuda", dtype=ctx.dtype)
+    sa = torch.empty(na * 3 * N, device="cuda", dtype=ctx.dtype)
+    da = torch.empty(na * M, device="cuda", dtype=ctx.dtype)
+    ctx.set_snapshots(SNAP_STEPS, ddisp=to(ddisp), ddens=to(ddens))
+    gm = to(dmom)
+    ctx.set_snapshot_momenta(mom=mom, dmom=gm)
+    ctx.set_interp_snapshots(a_obs, disp=sa, dens=da, ddisp=to(adisp), ddens=to(adens))
+    ctx.forward()
+    gw = torch.empty(N, device="cuda", dtype=ctx.dtype)
+    gt = torch.zeros(5, dtype=torch.float64)
+    ctx.adjoint(grad_omega=gw, grad_theta=gt)
+    ctx.close()
+    mom = mom.cpu().numpy().reshape(ns, 3, N)
+    sa = sa.cpu().numpy().reshape(na, 3, N)
+    da = da.cpu().numpy().reshape(na, M)
+    g = gw.cpu().numpy()
+    if precision:
+        for q, j in enumerate(SNAP_STEPS):
+            assert rel_l2(mom[q], fwd["snap"][j][2]) < 1e-9
+        for k, a in enumerate(a_obs):
+            assert rel_l2(sa[k], fwd["snap_a"][a][0]) < 1e-9
+            assert np.max(np.abs(da[k] - fwd["snap_a"][a][1].ravel())) < 1e-8
+        assert rel_l2(g, adj["grad_omega"]) < 1e-8
+        assert np.allclose(gt.numpy(), adj["grad_theta"], rtol=1e-8, atol=0)
+    else:
+        cell = SNAP["box"] / SNAP["n_mesh"]
+        for k, a in enumerate(a_obs):
+            assert np.sqrt(np.mean((sa[k] - fwd["snap_a"][a][0]) ** 2)) < 1e-3 * cell
+        assert cosine(g, adj["grad_omega"]) >= 0.999
+        assert rel_l2(g, adj["grad_omega"]) <= 1e-2
+
+
+def test_observation_setters_reject_bad_arguments():
+    torch_cuda()
+    from paper_2211_09815_gb300 import pm
+    ctx, *_ = make_ctx(50.0, 32, 16, 4)
+    with pytest.raises(pm.PMError):      # no snapshots set
+        pm._check(pm.load_library().pm_set_snapshot_momenta(ctx._h, None, None), "x")
+    for bad in ([1 / 64], [0.5, 0.4], [0.3, 0.3], [1.5]):
+        with pytest.raises(pm.PMError):
+            ctx.set_interp_snapshots(bad)
+    ctx.set_interp_snapshots([0.5, 1.0])
+    ctx.set_interp_snapshots([])
+    ctx.close()
