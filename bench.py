@@ -473,6 +473,14 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "loss": loss_val,
     }
+    if world == 1 and not args.no_extras:
+        # the other configurations of the workload set, measured in the same run: the
+        # batched ensemble against 16 sequential runs, and the memory and time of
+        # checkpoints against reverse time integration
+        torch.cuda.empty_cache()
+        out["batched_ensemble"] = batched_ensemble(1, 2)
+        torch.cuda.empty_cache()
+        out["checkpoint_memory"] = ckpt_compare()
     if not args.no_cpu_baseline:
         procs = host_cores()
         wall, per = oracle_pool_round(procs)
@@ -566,6 +574,10 @@ def run_fft_compare(args):
 
 
 def run_batched(args):
+    print(json.dumps(batched_ensemble(args.warmup, args.steps)))
+
+
+def batched_ensemble(warmup, steps):
     """Batched ensemble: 16 instances of 128^3 particles on 256^3 meshes (200 Mpc/h), own
     seed and theta each, 32 steps, forward + adjoint.  The batched context runs every
     kernel once for all instances and replays a captured CUDA graph; it is compared with 16
@@ -581,7 +593,7 @@ def run_batched(args):
     with torch.cuda.stream(stream):
         om = torch.from_numpy(np.stack([inputs.white_noise(npc, 1 + b) for b in range(B)])).cuda()
         om_t = torch.from_numpy(np.stack([inputs.white_noise(npc, 101 + b) for b in range(B)])).cuda()
-        ctx = pm.PMContext(box, nm, npc, n, theta.tolist(), om_t, batch=B, stream=stream)
+        ctx = pm.PMContext(box, nm, npc, n, theta.tolist(), om_t, batch=B, stream=stream, check_errors=False)
         tgt = torch.empty(B * M, device="cuda")
         ctx.forward(dens=tgt)
         # launch shapes from the autotuner, timed on the final (clustered) state
@@ -590,22 +602,24 @@ def run_batched(args):
         loss = torch.zeros(B, dtype=torch.float64, device="cuda")
         gw = torch.empty(B * N, device="cuda")
         gt = torch.zeros(5 * B, dtype=torch.float64, device="cuda")
-        for _ in range(args.warmup):
+        for _ in range(max(warmup, 1)):
             ctx.gradient_graph(tgt, loss=loss, grad_omega=gw, grad_theta=gt)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             ctx.gradient_graph(tgt, loss=loss, grad_omega=gw, grad_theta=gt)
         e1.record(stream)
         stream.synchronize()
-        t_batched = e0.elapsed_time(e1) / args.steps
+        ctx.check()
+        t_batched = e0.elapsed_time(e1) / steps
         gw_b = gw.cpu().numpy().reshape(B, N)
         ctx.close()
         # 16 sequential single-instance contexts, eager launches
         t_single = 0.0
         max_diff = 0.0
         for b in range(B):
-            c1 = pm.PMContext(box, nm, npc, n, [theta[b].tolist()], om[b].contiguous(), stream=stream)
+            c1 = pm.PMContext(box, nm, npc, n, [theta[b].tolist()], om[b].contiguous(), stream=stream,
+                              check_errors=False)
             c1.set_tuning(out["tuning"])   # the same launch shapes: results comparable bit for bit
             djdd = torch.empty(M, device="cuda")
             g1 = torch.empty(N, device="cuda")
@@ -616,6 +630,7 @@ def run_batched(args):
             c1.forward(); c1.loss_mse(t1, djdd); c1.adjoint(djdd=djdd, grad_omega=g1)
             f1.record(stream)
             stream.synchronize()
+            c1.check()
             t_single += f0.elapsed_time(f1)
             max_diff = max(max_diff, float(np.max(np.abs(g1.cpu().numpy() - gw_b[b]))))
             c1.close()
@@ -624,10 +639,14 @@ def run_batched(args):
                 "batched_instance_steps_per_s": B * n / (t_batched / 1e3),
                 "sequential_instance_steps_per_s": B * n / (t_single / 1e3),
                 "max_abs_grad_diff_batched_vs_single": max_diff})
-    print(json.dumps(out))
+    return out
 
 
 def run_ckpt_compare(args):
+    print(json.dumps(ckpt_compare()))
+
+
+def ckpt_compare():
     """Reverse-time recomputation vs checkpoints every 8 steps vs every step (the stored
     trajectory) at 256^3 particles / 512^3 mesh / 400 Mpc/h / 63 steps: device memory,
     time per gradient evaluation and the gradient differences."""
@@ -645,7 +664,7 @@ def run_ckpt_compare(args):
     res, grads = {}, {}
     for k in (0, 8, 1):
         torch.cuda.synchronize()
-        ctx = pm.PMContext(box, nm, npc, n, [THETA], om, ckpt_every=k)
+        ctx = pm.PMContext(box, nm, npc, n, [THETA], om, ckpt_every=k, check_errors=False)
         djdd = torch.empty(M, device="cuda")
         gw = torch.empty(N, device="cuda")
         gt = torch.zeros(5, dtype=torch.float64, device="cuda")
@@ -656,6 +675,7 @@ def run_ckpt_compare(args):
         ctx.forward(); ctx.loss_mse(tgt, djdd); ctx.adjoint(djdd=djdd, grad_omega=gw, grad_theta=gt)
         e1.record()
         torch.cuda.synchronize()
+        ctx.check()
         res[f"ckpt_every_{k}"] = {"ms_per_eval": e0.elapsed_time(e1), "scratch_GB": ctx.scratch_bytes / 1e9}
         grads[k] = (gw.cpu().numpy().astype(np.float64), gt.cpu().numpy())
         ctx.close()
@@ -667,15 +687,17 @@ def run_ckpt_compare(args):
     res["grad_omega_reverse_vs_stored"] = {"rel_l2": rel(g0, g1), "cosine": cos(g0, g1)}
     res["grad_omega_ckpt8_vs_stored"] = {"rel_l2": rel(g8, g1), "cosine": cos(g8, g1)}
     res["grad_theta"] = {str(k): grads[k][1].tolist() for k in grads}
-    print(json.dumps({"mode": "ckpt_compare", "workload": "256^3 particles, 512^3 mesh, 400 Mpc/h, 63 steps",
-                      **res}))
+    return {"mode": "ckpt_compare", "workload": "256^3 particles, 512^3 mesh, 400 Mpc/h, 63 steps", **res}
 
 
 def run_precision_study(args):
     """FP32 against an FP64 GPU run of the same workload, per output: final displacement
     RMS (in cells), momentum relative L2, per-shell P(k) relative error, dJ/domega cosine
     and relative L2, dJ/dtheta relative error; the FP32 gradient with reverse time
-    integration and with checkpoints every 8 steps."""
+    integration and with checkpoints every 8 steps.  Control: the FP64 run again with every
+    omega value moved by one FP32 ulp (seeded signs), whose gradient difference from the
+    FP64 run measures how much of the FP32 gradient error is the problem's own
+    sensitivity (particles crossing cell faces, where the CIC weight gradient jumps)."""
     import torch
     from paper_2211_09815_gb300 import build, inputs, pm
     build.build()
@@ -683,7 +705,7 @@ def run_precision_study(args):
     N, M = npc ** 3, nm ** 3
     out = {}
     tgt_np = None
-    for prec, ck in ((0, 0), (0, 8), (1, 0)):
+    for prec, ck, pert in ((0, 0, False), (0, 8, False), (1, 0, False), (1, 0, True)):
         dt = torch.float32 if prec == 0 else torch.float64
         if tgt_np is None:
             om2 = torch.from_numpy(inputs.white_noise(npc, 2)).cuda()
@@ -693,7 +715,11 @@ def run_precision_study(args):
             tgt_np = t.cpu().numpy()
             c0.close()
             del om2, t
-        om = torch.from_numpy(inputs.white_noise(npc, 1)).to("cuda", dt)
+        om_np = inputs.white_noise(npc, 1)
+        if pert:
+            sign = np.where(inputs.uniform01(77, om_np.size).reshape(om_np.shape) < 0.5, -1.0, 1.0)
+            om_np = om_np.astype(np.float64) + sign * np.spacing(np.abs(om_np)).astype(np.float64)
+        om = torch.from_numpy(np.ascontiguousarray(om_np)).to("cuda", dt)
         ctx = pm.PMContext(box, nm, npc, n, [THETA], om, precision=prec, ckpt_every=ck)
         disp = torch.empty(3 * N, device="cuda", dtype=dt)
         mom = torch.empty_like(disp)
@@ -708,13 +734,13 @@ def run_precision_study(args):
         t0 = time.perf_counter()
         ctx.adjoint(djdd=djdd, grad_omega=gw, grad_theta=gt)
         torch.cuda.synchronize()
-        out[(prec, ck)] = dict(s=disp.cpu().numpy().astype(np.float64), p=mom.cpu().numpy().astype(np.float64),
+        out[(prec, ck, pert)] = dict(s=disp.cpu().numpy().astype(np.float64), p=mom.cpu().numpy().astype(np.float64),
                          pk=pk[0], nmodes=nmodes, gw=gw.cpu().numpy().astype(np.float64), gt=gt.cpu().numpy(),
                          adj_s=time.perf_counter() - t0)
         ctx.close()
         del om, disp, mom, tgt, djdd, gw, gt
         torch.cuda.empty_cache()
-    a, b, a8 = out[(0, 0)], out[(1, 0)], out[(0, 8)]
+    a, b, a8, bp = out[(0, 0, False)], out[(1, 0, False)], out[(0, 8, False)], out[(1, 0, True)]
     cell = box / nm
     ok = b["nmodes"] > 0
     ok[0] = False
@@ -731,6 +757,11 @@ def run_precision_study(args):
                       "grad_omega_rel_l2": float(np.linalg.norm(a8["gw"] - b["gw"]) / np.linalg.norm(b["gw"])),
                       "grad_theta_rel": (np.abs(a8["gt"] / b["gt"] - 1)).tolist()},
         "adjoint_seconds": {"f32": a["adj_s"], "f32_ckpt8": a8["adj_s"], "f64": b["adj_s"]},
+        "control_f64_omega_moved_1_f32_ulp": {
+            "disp_rms_cells": float(np.sqrt(np.mean((bp["s"] - b["s"]) ** 2)) / cell),
+            "grad_omega_cosine": float(bp["gw"] @ b["gw"] / (np.linalg.norm(bp["gw"]) * np.linalg.norm(b["gw"]))),
+            "grad_omega_rel_l2": float(np.linalg.norm(bp["gw"] - b["gw"]) / np.linalg.norm(b["gw"])),
+            "grad_theta_rel": (np.abs(bp["gt"] / b["gt"] - 1)).tolist()},
     }
     print(json.dumps(res))
 
@@ -778,6 +809,8 @@ def main():
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-ensemble and checkpoint-memory measurements of the main line")
     ap.add_argument("--batched", action="store_true", help="16-instance batched graph vs sequential runs")
     ap.add_argument("--fft-compare", action="store_true", help="hand-written 3-D FFT beside cuFFT (torch.fft)")
     ap.add_argument("--compare-ckpt", action="store_true", help="reverse time vs checkpoints: memory/time")

@@ -80,6 +80,17 @@ template <typename T> struct alignas(4 * sizeof(T)) V4 { T x, y, z, w; };
 __host__ __device__ inline long long spec_main_len(int n) { return (long long)n * n * (n / 2); }
 __host__ __device__ inline long long spec_len_cx(int n) { return spec_main_len(n) + (long long)n * n; }
 
+// z blocking of the main part of the mesh spectra: row (z, y) of the main array is stored
+// at ((z / zb) n + y) zb + z mod zb.  With zb = 1 this is the plain [z][y] order; for
+// 1024^3 meshes (zb = 8) a column tile of the y pass spans 32 MB instead of 4 MB and one
+// of the z pass 128 address blocks of 32 KB instead of 1024 rows 4 MB apart, which keeps
+// the pages a tile touches (and its address translations) few.  Lattice spectra and the
+// side planes always use the plain order.
+__host__ __device__ constexpr int spec_zb(int n) { return n >= 1024 ? 8 : 1; }
+__host__ __device__ inline long long spec_row(int n, int zb, int z, int y) {
+  return zb <= 1 ? (long long)z * n + y : ((long long)(z / zb) * n + y) * zb + (z % zb);
+}
+
 // Element q of a small array held in kernel parameters, chosen with selects: a dynamic
 // index into the parameter block would copy it to local memory in every thread.
 template <typename X, int K>

@@ -23,7 +23,8 @@ namespace pmgb {
 // Shape of the fused deposit for rows of n = 2L cells: R rows per tile, TC = NQ R row
 // transforms, NT threads.  R is chosen so that a tile holds 2^13 (one quantity) or 2^12
 // (four quantities) cells in FP32, half of that in FP64; NT gives the radix stages whole
-// work items.
+// work items (up to 1024 threads: the shared memory of a four-quantity tile admits one
+// CTA per SM, and the accumulation needs the warps).
 template <typename T, int NQ, int L> struct FusedDeposit {
   static constexpr int N = 2 * L;
   static constexpr int CELLS0 = (NQ == 1 ? 8192 : 4096) / (int)(sizeof(T) / 4);
@@ -32,7 +33,7 @@ template <typename T, int NQ, int L> struct FusedDeposit {
   static constexpr int CELLS = N * R;
   static constexpr int TC = NQ * R;                           // row transforms per tile
   static constexpr int NT0 = TC * L / Plan<L>::RMAX;
-  static constexpr int NT = NT0 > 512 ? 512 : NT0;
+  static constexpr int NT = NT0 > 1024 ? 1024 : NT0;   // one radix item per thread where possible
   static constexpr int LD = TC + 1;
   static constexpr int ACC_BYTES = NQ * CELLS * 8;
   static constexpr int FFT_BYTES = skew_rows(L) * LD * (int)sizeof(cx_t<T>);
@@ -112,7 +113,7 @@ k_pull_r2c(BinGeo bg, const V4<T>* __restrict__ rec0, const V4<T>* __restrict__ 
     const int q = c / R, r = c % R;
     const long long grow = (long long)((T0 << bg.lz) + (r >> bg.ly)) * N + ((T1 << bg.ly) + (r & ((1 << bg.ly) - 1)));
     C* spec = pick(out.spec, q) + (long long)b * spec_len_cx(N);
-    C* o = spec + grow * L;
+    C* o = spec + spec_row(N, spec_zb(N), (int)(grow / N), (int)(grow % N)) * L;
     const C zk = sm[srow(k) * FD::LD + c];
     if (k == 0) {
       o[0] = cmake<C>(zk.x + zk.y, (T)0);

@@ -169,8 +169,9 @@ k_fft_x_r2c(RowJob<T> job, int nrows, int nbuf, const cx_t<T>* __restrict__ twL,
     const int grow = r0 + row;
     if (grow >= nrows) continue;
     C* spec = rb0.spec;
-    C* out = spec + inst0 * spec_len_cx(N) + (grow % rows_per_inst) * L;
-    C* side = spec + inst0 * spec_len_cx(N) + spec_main_len(N) + (grow % rows_per_inst);
+    const long long rr = grow % rows_per_inst;
+    C* out = spec + inst0 * spec_len_cx(N) + spec_row(N, job.zb, (int)(rr / N), (int)(rr % N)) * L;
+    C* side = spec + inst0 * spec_len_cx(N) + spec_main_len(N) + rr;
     const C zk = sm[srow(k) * TL::LD + c];
     if (k == 0) {
       out[0] = cmake<C>(zk.x + zk.y, (T)0);
@@ -217,9 +218,10 @@ k_fft_x_c2r(RowJob<T> job, int nrows, const cx_t<T>* __restrict__ twL, const cx_
     if (idx < PAIRS && grow < nrows) {
       const int inst = (int)(grow / rows_per_inst);
       const C* base = rb.spec + inst * spec_len_cx(N);
-      const C* in = base + (grow % rows_per_inst) * L;
+      const long long rr = grow % rows_per_inst;
+      const C* in = base + spec_row(N, job.zb, (int)(rr / N), (int)(rr % N)) * L;
       xk[it] = in[k];
-      xm[it] = k == 0 ? base[spec_main_len(N) + (grow % rows_per_inst)] : in[L - k];
+      xm[it] = k == 0 ? base[spec_main_len(N) + rr] : in[L - k];
     }
   }
 #pragma unroll
@@ -294,9 +296,10 @@ k_fft_x_c2r4(RowJob<T> job, int nrows, int dq, V4<T>* __restrict__ out4, const c
     xm[it] = cmake<C>(0, 0);
     if (idx < PAIRS && grow < nrows) {
       const C* base = pick(job.b, q).spec + (grow / rows_per_inst) * spec_len_cx(N);
-      const C* in = base + (grow % rows_per_inst) * L;
+      const long long rr = grow % rows_per_inst;
+      const C* in = base + spec_row(N, job.zb, (int)(rr / N), (int)(rr % N)) * L;
       xk[it] = in[k];
-      xm[it] = k == 0 ? base[spec_main_len(N) + (grow % rows_per_inst)] : in[L - k];
+      xm[it] = k == 0 ? base[spec_main_len(N) + rr] : in[L - k];
     }
   }
 #pragma unroll
@@ -686,16 +689,20 @@ static int make_maps_L(int batch, cx_t<T>* buf, CUtensorMap* ymap, CUtensorMap* 
   }
   using TT = TmaTile<T, L>;
   constexpr int eb = (int)sizeof(cx_t<T>);
-  const cuuint64_t dims[4] = {(cuuint64_t)(L / 2) * TT::W, (cuuint64_t)L, (cuuint64_t)L, (cuuint64_t)batch};
-  const cuuint64_t strides[3] = {(cuuint64_t)(L / 2) * eb, (cuuint64_t)L * (L / 2) * eb,
-                                 (cuuint64_t)spec_len_cx(L) * eb};
-  const cuuint32_t ybox[4] = {(cuuint32_t)(TT::TC * TT::W), (cuuint32_t)TT::RB, 1, 1};
-  const cuuint32_t zbox[4] = {(cuuint32_t)(TT::TC * TT::W), 1, (cuuint32_t)TT::RB, 1};
-  const cuuint32_t es[4] = {1, 1, 1, 1};
-  const CUresult r1 = encode(ymap, CU_TENSOR_MAP_DATA_TYPE_INT64, 4, (void*)buf, dims, strides, ybox, es,
+  constexpr int ZB = TT::ZB;
+  // main array as (kx words, z mod ZB, y, z / ZB, instance): row (z, y) at
+  // ((z / ZB) L + y) ZB + z mod ZB (spec_row)
+  const cuuint64_t dims[5] = {(cuuint64_t)(L / 2) * TT::W, (cuuint64_t)ZB, (cuuint64_t)L, (cuuint64_t)(L / ZB),
+                              (cuuint64_t)batch};
+  const cuuint64_t strides[4] = {(cuuint64_t)(L / 2) * eb, (cuuint64_t)ZB * (L / 2) * eb,
+                                 (cuuint64_t)L * ZB * (L / 2) * eb, (cuuint64_t)spec_len_cx(L) * eb};
+  const cuuint32_t ybox[5] = {(cuuint32_t)(TT::TC * TT::W), 1, (cuuint32_t)TT::RB, 1, 1};
+  const cuuint32_t zbox[5] = {(cuuint32_t)(TT::TC * TT::W), (cuuint32_t)ZB, 1, (cuuint32_t)(TT::RB / ZB), 1};
+  const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  const CUresult r1 = encode(ymap, CU_TENSOR_MAP_DATA_TYPE_INT64, 5, (void*)buf, dims, strides, ybox, es,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  const CUresult r2 = encode(zmap, CU_TENSOR_MAP_DATA_TYPE_INT64, 4, (void*)buf, dims, strides, zbox, es,
+  const CUresult r2 = encode(zmap, CU_TENSOR_MAP_DATA_TYPE_INT64, 5, (void*)buf, dims, strides, zbox, es,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return (r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS) ? PM_OK : PM_ERR_CUDA;

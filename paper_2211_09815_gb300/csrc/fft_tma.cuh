@@ -74,12 +74,29 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, unsigned long long* bar, int c0, int c1,
+                                            int c2, int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], "
+      "[%7];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+        "r"(c4), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // TMA store of a shared-memory box into the tensor (bulk async-group of the issuing
 // thread); the writers of the box execute fence_proxy_async and a barrier first
 __device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void* src, int c0, int c1, int c2, int c3) {
   asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];"
                ::"l"(reinterpret_cast<unsigned long long>(map)), "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2),
                  "r"(c3)
+               : "memory");
+}
+__device__ __forceinline__ void tma_store_5d(const CUtensorMap* map, const void* src, int c0, int c1, int c2, int c3,
+                                             int c4) {
+  asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5, %6}], [%1];"
+               ::"l"(reinterpret_cast<unsigned long long>(map)), "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2),
+                 "r"(c3), "r"(c4)
                : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
@@ -116,6 +133,7 @@ template <typename T, int L> struct TmaTile {
   static constexpr int TILE = L * TC;                            // complex elements per tile
   static constexpr int BYTES = TILE * (int)sizeof(cx_t<T>);
   static constexpr int W = (int)sizeof(cx_t<T>) / 8;              // int64 words per complex
+  static constexpr int ZB = spec_zb(L);                          // z blocking of the main rows
 };
 
 // Green's function data for a z-pass column (kx, y), as in the unstaged fused kernels.
@@ -258,12 +276,15 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
     unsigned long long* bar = &bars[q % NSLOT];
     fence_proxy_async();
     mbar_expect_tx(bar, TT::BYTES);
+    // 5-D view of the main array: (kx words, z mod ZB, y, z / ZB, instance)
 #pragma unroll
     for (int r = 0; r < L / TT::RB; ++r) {
       if (job.zaxis)
-        tma_load_4d(dst + r * TT::RB * TT::LD, &maps.m[buf], bar, kxg * TT::TC * TT::W, o, r * TT::RB, b);
+        tma_load_5d(dst + r * TT::RB * TT::LD, &maps.m[buf], bar, kxg * TT::TC * TT::W, 0, o, r * (TT::RB / TT::ZB),
+                    b);
       else
-        tma_load_4d(dst + r * TT::RB * TT::LD, &maps.m[buf], bar, kxg * TT::TC * TT::W, r * TT::RB, o, b);
+        tma_load_5d(dst + r * TT::RB * TT::LD, &maps.m[buf], bar, kxg * TT::TC * TT::W, o % TT::ZB, r * TT::RB,
+                    o / TT::ZB, b);
     }
   };
   // Results leave by TMA stores from shared memory.  KIND 0: three slots, so the slot
@@ -276,9 +297,9 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
 #pragma unroll
     for (int r = 0; r < L / TT::RB; ++r) {
       if (job.zaxis)
-        tma_store_4d(map, src + r * TT::RB * TT::LD, kxg * TT::TC * TT::W, o, r * TT::RB, b);
+        tma_store_5d(map, src + r * TT::RB * TT::LD, kxg * TT::TC * TT::W, 0, o, r * (TT::RB / TT::ZB), b);
       else
-        tma_store_4d(map, src + r * TT::RB * TT::LD, kxg * TT::TC * TT::W, r * TT::RB, o, b);
+        tma_store_5d(map, src + r * TT::RB * TT::LD, kxg * TT::TC * TT::W, o % TT::ZB, r * TT::RB, o / TT::ZB, b);
     }
     bulk_commit();
   };
@@ -311,9 +332,6 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
     decode(q, item, comp);
     const int u = KIND == 0 ? item % tiles_per_buf : item;
     const int kxg = u % NCG, o = (u / NCG) % N, b = u / (NCG * N);
-    const long long es = job.zaxis ? (long long)N * (N / 2) : (N / 2);
-    const long long base = (long long)b * spec_len_cx(N) + (job.zaxis ? (long long)o * (N / 2) : (long long)o * N * (N / 2)) +
-                           kxg * TT::TC + c;
     C* cur = slot(q);
     DenseTile<C, TT::LD> t{cur};
     if constexpr (KIND == 0) {

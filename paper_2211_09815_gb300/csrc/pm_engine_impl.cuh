@@ -175,7 +175,7 @@ class Engine : public EngineBase {
     // TMA-staged column passes for the mesh sizes that have them (PMGB_TMA=0 starts with
     // the unstaged form; pm_set_tuning and pm_autotune switch between the two)
     const char* env = getenv("PMGB_TMA");
-    tune_.tma_columns = (env && env[0] == '0') ? 0 : 1;
+    tune_.tma_columns = (env && env[0] == '0' && spec_zb(nm_) <= 1) ? 0 : 1;
     apply_tuning();
     tune_.tma_columns = use_tma_ ? 1 : 0;
     PMGB_RET(alloc(&dev_err_, 1));
@@ -833,8 +833,10 @@ class Engine : public EngineBase {
       if (spec_[q] == p) return q;
     return -1;
   }
-  int cols(int n, int dir, bool zaxis, C* const* bufs, int nb) {
-    if (use_tma_ && n == nm_) {
+  // column pass over up to 4 spectra: mesh spectra (z-blocked main rows at 1024^3, see
+  // spec_row) take the TMA-staged passes, lattice spectra (plain order) the unstaged ones
+  int cols(int n, int dir, bool zaxis, C* const* bufs, int nb, bool mesh = true) {
+    if (use_tma_ && mesh && n == nm_) {
       CUtensorMap maps[4];
       for (int q = 0; q < nb; ++q) {
         const int i = spec_index(bufs[q]);
@@ -869,6 +871,7 @@ class Engine : public EngineBase {
   int r2c_real(int n, const T* in, long long in_is, C* out) {
     RowJob<T> job{};
     job.b[0] = RowBuf<T>{(void*)in, in_is, out};
+    job.zb = spec_zb(n);
     PMGB_RET(fft_x_r2c<T>(n, job, 1, B_ * n * n, tw_, st_));
     C* bufs[1] = {out};
     PMGB_RET(cols(n, -1, false, bufs, 1));
@@ -881,6 +884,7 @@ class Engine : public EngineBase {
     PMGB_RET(cols(n, +1, false, bufs, 1));
     RowJob<T> job{};
     job.b[0] = RowBuf<T>{(void*)out, out_is, in};
+    job.zb = spec_zb(n);
     PMGB_RET(fft_x_c2r<T>(n, job, 1, B_ * n * n, tw_, st_));
     PMGB_CK(cudaGetLastError());
     return PM_OK;
@@ -945,6 +949,7 @@ class Engine : public EngineBase {
       return PM_ERR_ARG;
     if (t->tma_columns != 0 && t->tma_columns != 1) return PM_ERR_ARG;
     if (t->tma_columns && !tma_supported(nm_)) return PM_ERR_ARG;
+    if (!t->tma_columns && spec_zb(nm_) > 1) return PM_ERR_ARG;   // z-blocked rows: staged passes only
     if (t->fused_x < 0 || t->fused_x > 3 || (t->fused_x && fused_rows<T>(nm_, 1) == 0)) return PM_ERR_ARG;
     tune_ = *t;
     apply_tuning();
@@ -1032,12 +1037,14 @@ class Engine : public EngineBase {
         const BinGeo bg = make_bin_geo(lg, l[2], l[1], l[0]);
         const int nt = nq ? best.threads_adjoint : best.threads_density;
         double ms_sep = 0, ms_fused = 0;
+        const SepTargets tg = sep_targets(false);
         PMGB_RET(time_it([&]() {
-          PMGB_RET(deposit(s_, nq ? xi_ : nullptr, rmesh(0), sis, bg, nt));
+          PMGB_RET(deposit(s_, nq ? xi_ : nullptr, tg.d, tg.dis, bg, nt, false, nullptr, &tg));
           RowJob<T> job{};
-          job.b[0] = RowBuf<T>{rmesh(0), sis, spec_[0]};
+          job.b[0] = RowBuf<T>{tg.d, tg.dis, spec_[0]};
           if (nq)
-            for (int c = 0; c < 3; ++c) job.b[1 + c] = RowBuf<T>{rmesh(4 + c), sis, spec_[4 + c]};
+            for (int c = 0; c < 3; ++c) job.b[1 + c] = RowBuf<T>{tg.p[c], tg.pis, spec_[4 + c]};
+          job.zb = spec_zb(nm_);
           return fft_x_r2c<T>(nm_, job, nq ? 4 : 1, B_ * nm_ * nm_, tw_, st_);
         }, &ms_sep));
         FusedOut<T> fo{};
@@ -1052,7 +1059,7 @@ class Engine : public EngineBase {
     }
     if (tma_supported(nm_)) {
       C* b1[1] = {spec_[6]};
-      for (int tma = 1; tma >= 0; --tma) {
+      for (int tma = 1; tma >= (spec_zb(nm_) > 1 ? 1 : 0); --tma) {   // blocked rows: staged passes only
         use_tma_ = tma != 0;
         double ms = 0;
         PMGB_RET(time_it([&]() { return cols(nm_, -1, false, b1, 1); }, &ms));
@@ -1077,7 +1084,35 @@ class Engine : public EngineBase {
   // adjoint sums pi_c W -- by binning the particles over mesh tiles and one CTA per tile
   // (bin_kernels.cuh).  delta goes to dout (instance stride dis); the pi sums go to the real
   // views of spec_[4..6].
-  int scatter(const T* s, const T* pi, T* dout, long long dis, const FusedOut<T>* fo = nullptr) {
+  // Real meshes of the separate deposit, transformed by the x pass of the R2C next: in place
+  // in the spectrum buffers (delta in spec_[0] or dens_, pi_c in spec_[4 + c]) when the
+  // main rows are in plain order; with z-blocked rows the x pass cannot run in place, and
+  // the meshes go to the force mesh buffer (free until the chain's last pass) instead.
+  struct SepTargets {
+    T* d;
+    long long dis;
+    T* p[3];
+    long long pis;
+  };
+  SepTargets sep_targets(bool keep_density) {
+    SepTargets tg;
+    const long long sis = 2 * spec_len_cx(nm_);
+    if (spec_zb(nm_) <= 1) {
+      tg.d = keep_density ? dens_ : rmesh(0);
+      tg.dis = keep_density ? M_ : sis;
+      for (int c = 0; c < 3; ++c) tg.p[c] = rmesh(4 + c);
+      tg.pis = sis;
+    } else {
+      T* f = reinterpret_cast<T*>(fvec_);
+      tg.d = keep_density ? dens_ : f;
+      tg.dis = M_;
+      for (int c = 0; c < 3; ++c) tg.p[c] = f + (long long)(1 + c) * B_ * M_;
+      tg.pis = M_;
+    }
+    return tg;
+  }
+  int scatter(const T* s, const T* pi, T* dout, long long dis, const FusedOut<T>* fo = nullptr,
+              const SepTargets* tg = nullptr) {
     if (pi) {
       prof_.begin(st_, P_OTHER, 1);
       k_pi_exponents<<<1, 64, 0, st_>>>(pimax_, e_pi_, 3 * B_, fixed_top<T>(lgN_));
@@ -1091,7 +1126,7 @@ class Engine : public EngineBase {
     if (fo)
       PMGB_RET(deposit(s, pi, nullptr, 0, pi ? bgf4_ : bgf1_, 0, pre, fo));
     else
-      PMGB_RET(pi ? deposit(s, pi, dout, dis, bg4_, tune_.threads_adjoint, pre)
+      PMGB_RET(pi ? deposit(s, pi, dout, dis, bg4_, tune_.threads_adjoint, pre, nullptr, tg)
                   : deposit(s, nullptr, dout, dis, bg1_, tune_.threads_density, pre));
     prof_.end(st_, P_SCATTER);
     return PM_OK;
@@ -1102,7 +1137,7 @@ class Engine : public EngineBase {
   // (fo: the deposit fused with the R2C x pass, into the half spectra of fo; bg is then
   // the whole-row geometry of fused_rows)
   int deposit(const T* s, const T* pi, T* dout, long long dis, const BinGeo& bg, int nt, bool precounted = false,
-              const FusedOut<T>* fo = nullptr) {
+              const FusedOut<T>* fo = nullptr, const SepTargets* tg = nullptr) {
     const long long nbin = (long long)B_ * bg.nkeys + 1;
     const int nscan = (int)((nbin + kScanBlock - 1) / kScanBlock);
     if (!precounted) k_bin_count<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, bg, s, bcount_, bkeys_);
@@ -1124,15 +1159,16 @@ class Engine : public EngineBase {
       return PM_OK;
     }
     const int cells = 1 << (bg.lx + bg.ly + bg.lz);
-    const long long pis = 2 * spec_len_cx(nm_);
+    const SepTargets dt = tg ? *tg : sep_targets(false);
+    const long long pis = dt.pis;
     const dim3 grid(bg.ntiles, B_);
     if (pi) {
       if (nt == 512)
         k_pull_scatter<T, 4, 512><<<grid, 512, 4 * 8 * cells, st_>>>(
-            geo_, bg, brec0_, brec1_, bstart_, e_d_, e_pi_, mass_, dout, dis, rmesh(4), rmesh(5), rmesh(6), pis);
+            geo_, bg, brec0_, brec1_, bstart_, e_d_, e_pi_, mass_, dout, dis, dt.p[0], dt.p[1], dt.p[2], pis);
       else
         k_pull_scatter<T, 4, 256><<<grid, 256, 4 * 8 * cells, st_>>>(
-            geo_, bg, brec0_, brec1_, bstart_, e_d_, e_pi_, mass_, dout, dis, rmesh(4), rmesh(5), rmesh(6), pis);
+            geo_, bg, brec0_, brec1_, bstart_, e_d_, e_pi_, mass_, dout, dis, dt.p[0], dt.p[1], dt.p[2], pis);
     } else {
       if (nt == 512)
         k_pull_scatter<T, 1, 512><<<grid, 512, 8 * cells, st_>>>(geo_, bg, brec0_, nullptr, bstart_, e_d_,
@@ -1156,9 +1192,6 @@ class Engine : public EngineBase {
   int force_chain(const T* s, const T* pi, bool keep_density) {
     // delta goes to the real view of spec_[0] (transformed in place) or, when the final
     // density is kept for the objective, to dens_
-    const long long sis = 2 * spec_len_cx(nm_);
-    T* dmesh = keep_density ? dens_ : rmesh(0);
-    const long long dis = keep_density ? M_ : sis;
     if (pi ? fused4_ : fused1_) {
       // deposit and x pass in one kernel: delta (and pi_c) straight into the half spectra
       FusedOut<T> fo{};
@@ -1167,12 +1200,14 @@ class Engine : public EngineBase {
       fo.dens = keep_density ? dens_ : nullptr;
       PMGB_RET(scatter(s, pi, nullptr, 0, &fo));
     } else {
-      PMGB_RET(scatter(s, pi, dmesh, dis));
+      SepTargets tg = sep_targets(keep_density);
+      PMGB_RET(scatter(s, pi, tg.d, tg.dis, nullptr, &tg));
       const int nb = pi ? 4 : 1;
       RowJob<T> job{};
-      job.b[0] = RowBuf<T>{dmesh, dis, spec_[0]};
+      job.b[0] = RowBuf<T>{tg.d, tg.dis, spec_[0]};
       if (pi)
-        for (int c = 0; c < 3; ++c) job.b[1 + c] = RowBuf<T>{rmesh(4 + c), sis, spec_[4 + c]};
+        for (int c = 0; c < 3; ++c) job.b[1 + c] = RowBuf<T>{tg.p[c], tg.pis, spec_[4 + c]};
+      job.zb = spec_zb(nm_);
       prof_.begin(st_, P_X_R2C, 1);
       PMGB_RET(fft_x_r2c<T>(nm_, job, nb, B_ * nm_ * nm_, tw_, st_));
       prof_.end(st_, P_X_R2C);
@@ -1233,6 +1268,7 @@ class Engine : public EngineBase {
     C* c2rb[4] = {spec_[1], spec_[2], spec_[3], spec_[0]};
     RowJob<T> jc{};
     for (int q = 0; q < 4; ++q) jc.b[q] = RowBuf<T>{nullptr, 0, (q < 3 || pi) ? c2rb[q] : nullptr};
+    jc.zb = spec_zb(nm_);
     prof_.begin(st_, P_X_C2R, 1);
     PMGB_RET(fft_x_c2r4<T>(nm_, jc, B_ * nm_ * nm_, 2, reinterpret_cast<V4<T>*>(fvec_), tw_, st_));
     prof_.end(st_, P_X_C2R);
@@ -1334,8 +1370,8 @@ class Engine : public EngineBase {
     PMGB_RET(fft_x_r2c<T>(np_, job, 4, B_ * np_ * np_, tw_, st_));
     PMGB_CK(cudaGetLastError());
     C* bufs[4] = {spec_[1], spec_[2], spec_[3], spec_[0]};
-    PMGB_RET(cols(np_, -1, false, bufs, 4));
-    PMGB_RET(cols(np_, -1, true, bufs, 4));
+    PMGB_RET(cols(np_, -1, false, bufs, 4, false));
+    PMGB_RET(cols(np_, -1, true, bufs, 4, false));
     k_za_adj_mul<T><<<dim3(Gz_, B_), kPtclThreads, 0, st_>>>(spec_[1], spec_[2], spec_[3], nullptr, nullptr, spec_[4],
                                                              np_, nullptr, unit_, nullptr, maxn2_, inv_kfp_, lis,
                                                              nullptr);
@@ -1354,8 +1390,8 @@ class Engine : public EngineBase {
       for (int c = 0; c < 3; ++c) jh.b[c] = RowBuf<T>{rmesh(1 + c), 2 * lis, spec_[1 + c]};
       PMGB_RET(fft_x_r2c<T>(np_, jh, 3, B_ * np_ * np_, tw_, st_));
       PMGB_CK(cudaGetLastError());
-      PMGB_RET(cols(np_, -1, false, h, 3));
-      PMGB_RET(cols(np_, -1, true, h, 3));
+      PMGB_RET(cols(np_, -1, false, h, 3, false));
+      PMGB_RET(cols(np_, -1, true, h, 3, false));
       k_lpt_hess_adj<T><<<dim3(256, B_), 256, 0, st_>>>(spec_[1], spec_[2], spec_[3], spec_[5], np_, amp_, maxn2_,
                                                         lis, g);
       PMGB_CK(cudaGetLastError());
@@ -1367,13 +1403,13 @@ class Engine : public EngineBase {
     job.b[0] = RowBuf<T>{(void*)in, in_is, out};
     PMGB_RET(fft_x_r2c<T>(np_, job, 1, B_ * np_ * np_, tw_, st_));
     C* bufs[1] = {out};
-    PMGB_RET(cols(np_, -1, false, bufs, 1));
-    PMGB_RET(cols(np_, -1, true, bufs, 1));
+    PMGB_RET(cols(np_, -1, false, bufs, 1, false));
+    PMGB_RET(cols(np_, -1, true, bufs, 1, false));
     return PM_OK;
   }
   int lattice_c2r(C* const* bufs, int nb) {
-    PMGB_RET(cols(np_, +1, true, bufs, nb));
-    PMGB_RET(cols(np_, +1, false, bufs, nb));
+    PMGB_RET(cols(np_, +1, true, bufs, nb, false));
+    PMGB_RET(cols(np_, +1, false, bufs, nb, false));
     RowJob<T> jc{};
     for (int q = 0; q < nb; ++q) jc.b[q] = RowBuf<T>{bufs[q], 2 * spec_len_cx(np_), bufs[q]};
     PMGB_RET(fft_x_c2r<T>(np_, jc, nb, B_ * np_ * np_, tw_, st_));
@@ -1398,8 +1434,8 @@ class Engine : public EngineBase {
     PMGB_RET(fft_x_r2c<T>(np_, job, 4, B_ * np_ * np_, tw_, st_));
     PMGB_CK(cudaGetLastError());
     C* bufs[4] = {spec_[1], spec_[2], spec_[3], spec_[0]};
-    PMGB_RET(cols(np_, -1, false, bufs, 4));
-    PMGB_RET(cols(np_, -1, true, bufs, 4));
+    PMGB_RET(cols(np_, -1, false, bufs, 4, false));
+    PMGB_RET(cols(np_, -1, true, bufs, 4, false));
     k_za_adj_mul<T><<<dim3(Gz_, B_), kPtclThreads, 0, st_>>>(spec_[1], spec_[2], spec_[3], spec_[0],
                                                              lpt2_ ? spec_[5] : nullptr, spec_[5], np_, amp_, (T)0,
                                                              hdl_, maxn2_, inv_kfp_, lis, part_);
@@ -1407,8 +1443,8 @@ class Engine : public EngineBase {
     k_sum_partials<<<5 * B_, 256, 0, st_>>>(part_, Gz_, scal_ + 4 * B_, 1.0);
     PMGB_CK(cudaGetLastError());
     C* ob[1] = {spec_[5]};
-    PMGB_RET(cols(np_, +1, true, ob, 1));
-    PMGB_RET(cols(np_, +1, false, ob, 1));
+    PMGB_RET(cols(np_, +1, true, ob, 1, false));
+    PMGB_RET(cols(np_, +1, false, ob, 1, false));
     RowJob<T> jc{};
     jc.b[0] = RowBuf<T>{djdw ? djdw : (void*)rmesh(5), djdw ? N_ : 2 * lis, spec_[5]};
     PMGB_RET(fft_x_c2r<T>(np_, jc, 1, B_ * np_ * np_, tw_, st_));

@@ -29,7 +29,10 @@ template <typename T> struct RowBuf {
   long long real_is;    // instance stride of `real` in elements
   cx_t<T>* spec;        // spectrum buffer (main + side)
 };
-template <typename T> struct RowJob { RowBuf<T> b[4]; };
+template <typename T> struct RowJob {
+  RowBuf<T> b[4];
+  int zb;               // z blocking of the spectra's main rows (spec_row); 0 or 1: plain order
+};
 
 // Fused z pass with the Green's function G = coef[b] / n^2 * (deconvolution) per mode.
 // Force: in[0] = delta^ -> out[0] = z force (-i k_0 G), out[1] = U (G, shared by the y and

@@ -655,16 +655,24 @@ k_mse(const T* __restrict__ dens, const T* __restrict__ tgt, T* __restrict__ gra
 }
 
 // ------------------------------------------------------------------ lattice spectra
-// Mode (i0, i1, kx) of an n^3 half spectrum from a flat index over main + side.
+// Mode (i0, i1, kx) of an n^3 half spectrum from a flat index over main + side (main rows
+// z-blocked by zb, spec_row).
 struct Mode { int f0, f1, f2; long long off; };
-__device__ __forceinline__ Mode mode_of(long long u, int n) {
+__device__ __forceinline__ Mode mode_of(long long u, int n, int zb = 1) {
   Mode m;
   const long long main = (long long)n * n * (n / 2);
   if (u < main) {
     const int kx = (int)(u % (n / 2));
     const long long t = u / (n / 2);
-    m.f1 = freq_of((int)(t % n), n);
-    m.f0 = freq_of((int)(t / n), n);
+    if (zb <= 1) {
+      m.f1 = freq_of((int)(t % n), n);
+      m.f0 = freq_of((int)(t / n), n);
+    } else {
+      const int zlo = (int)(t % zb);
+      const long long t2 = t / zb;
+      m.f1 = freq_of((int)(t2 % n), n);
+      m.f0 = freq_of((int)(t2 / n) * zb + zlo, n);
+    }
     m.f2 = kx;
   } else {
     const long long v = u - main;
@@ -970,7 +978,7 @@ __global__ void k_power_max(const cx_t<T>* __restrict__ spec, int n, long long i
   const int b = blockIdx.y;
   const long long tot = spec_len_cx(n);
   for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < tot; u += (long long)gridDim.x * blockDim.x) {
-    const Mode m = mode_of(u, n);
+    const Mode m = mode_of(u, n, spec_zb(n));
     const int bin = isqrt_floor(m.f0 * m.f0 + m.f1 * m.f1 + m.f2 * m.f2);
     if (bin >= nb) continue;
     const cx_t<T> v = spec[b * is + u];
@@ -986,7 +994,7 @@ __global__ void k_power_acc(const cx_t<T>* __restrict__ spec, int n, long long i
   const int b = blockIdx.y;
   const long long tot = spec_len_cx(n);
   for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < tot; u += (long long)gridDim.x * blockDim.x) {
-    const Mode m = mode_of(u, n);
+    const Mode m = mode_of(u, n, spec_zb(n));
     const int n2 = m.f0 * m.f0 + m.f1 * m.f1 + m.f2 * m.f2;
     const int bin = isqrt_floor(n2);
     if (bin >= nb) continue;
@@ -1050,7 +1058,7 @@ __global__ void k_power_grad(cx_t<T>* spec, int n, long long is, int nb, const d
   const int b = blockIdx.y;
   const long long tot = spec_len_cx(n);
   for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < tot; u += (long long)gridDim.x * blockDim.x) {
-    const Mode m = mode_of(u, n);
+    const Mode m = mode_of(u, n, spec_zb(n));
     const int bin = isqrt_floor(m.f0 * m.f0 + m.f1 * m.f1 + m.f2 * m.f2);
     const T f = bin < nb ? (T)g[(long long)b * nb + bin] : (T)0;
     cx_t<T> v = spec[b * is + u];
@@ -1070,7 +1078,8 @@ __global__ void k_spec_to_std(const cx_t<T>* __restrict__ spec, cx_t<T>* __restr
     const int k = (int)(r % h);
     const long long row = r / h;
     const cx_t<T>* base = spec + b * spec_len_cx(n);
-    out[u] = k < n / 2 ? base[row * (n / 2) + k] : base[spec_main_len(n) + row];
+    const long long mrow = spec_row(n, spec_zb(n), (int)(row / n), (int)(row % n));
+    out[u] = k < n / 2 ? base[mrow * (n / 2) + k] : base[spec_main_len(n) + row];
   }
 }
 template <typename T>
@@ -1082,7 +1091,8 @@ __global__ void k_std_to_spec(const cx_t<T>* __restrict__ in, cx_t<T>* __restric
     const int k = (int)(r % h);
     const long long row = r / h;
     cx_t<T>* base = spec + b * spec_len_cx(n);
-    if (k < n / 2) base[row * (n / 2) + k] = in[u];
+    const long long mrow = spec_row(n, spec_zb(n), (int)(row / n), (int)(row % n));
+    if (k < n / 2) base[mrow * (n / 2) + k] = in[u];
     else base[spec_main_len(n) + row] = in[u];
   }
 }
