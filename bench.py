@@ -694,7 +694,8 @@ def run_precision_study(args):
     """FP32 against an FP64 GPU run of the same workload, per output: final displacement
     RMS (in cells), momentum relative L2, per-shell P(k) relative error, dJ/domega cosine
     and relative L2, dJ/dtheta relative error; the FP32 gradient with reverse time
-    integration and with checkpoints every 8 steps.  Control: the FP64 run again with every
+    integration, with checkpoints every 8 steps and with the exactly reversible fixed-point
+    state (fixed_state).  Control: the FP64 run again with every
     omega value moved by one FP32 ulp (seeded signs), whose gradient difference from the
     FP64 run measures how much of the FP32 gradient error is the problem's own
     sensitivity (particles crossing cell faces, where the CIC weight gradient jumps)."""
@@ -705,7 +706,8 @@ def run_precision_study(args):
     N, M = npc ** 3, nm ** 3
     out = {}
     tgt_np = None
-    for prec, ck, pert in ((0, 0, False), (0, 8, False), (1, 0, False), (1, 0, True)):
+    for prec, ck, pert, fix in ((0, 0, False, False), (0, 8, False, False), (0, 0, False, True), (1, 0, False, False),
+                                (1, 0, True, False)):
         dt = torch.float32 if prec == 0 else torch.float64
         if tgt_np is None:
             om2 = torch.from_numpy(inputs.white_noise(npc, 2)).cuda()
@@ -720,7 +722,7 @@ def run_precision_study(args):
             sign = np.where(inputs.uniform01(77, om_np.size).reshape(om_np.shape) < 0.5, -1.0, 1.0)
             om_np = om_np.astype(np.float64) + sign * np.spacing(np.abs(om_np)).astype(np.float64)
         om = torch.from_numpy(np.ascontiguousarray(om_np)).to("cuda", dt)
-        ctx = pm.PMContext(box, nm, npc, n, [THETA], om, precision=prec, ckpt_every=ck)
+        ctx = pm.PMContext(box, nm, npc, n, [THETA], om, precision=prec, ckpt_every=ck, fixed_state=fix)
         disp = torch.empty(3 * N, device="cuda", dtype=dt)
         mom = torch.empty_like(disp)
         ctx.forward(disp=disp, mom=mom)
@@ -734,13 +736,14 @@ def run_precision_study(args):
         t0 = time.perf_counter()
         ctx.adjoint(djdd=djdd, grad_omega=gw, grad_theta=gt)
         torch.cuda.synchronize()
-        out[(prec, ck, pert)] = dict(s=disp.cpu().numpy().astype(np.float64), p=mom.cpu().numpy().astype(np.float64),
+        out[(prec, ck, pert, fix)] = dict(s=disp.cpu().numpy().astype(np.float64), p=mom.cpu().numpy().astype(np.float64),
                          pk=pk[0], nmodes=nmodes, gw=gw.cpu().numpy().astype(np.float64), gt=gt.cpu().numpy(),
                          adj_s=time.perf_counter() - t0)
         ctx.close()
         del om, disp, mom, tgt, djdd, gw, gt
         torch.cuda.empty_cache()
-    a, b, a8, bp = out[(0, 0, False)], out[(1, 0, False)], out[(0, 8, False)], out[(1, 0, True)]
+    a, b, a8 = out[(0, 0, False, False)], out[(1, 0, False, False)], out[(0, 8, False, False)]
+    bp, af = out[(1, 0, True, False)], out[(0, 0, False, True)]
     cell = box / nm
     ok = b["nmodes"] > 0
     ok[0] = False
@@ -757,6 +760,11 @@ def run_precision_study(args):
                       "grad_omega_rel_l2": float(np.linalg.norm(a8["gw"] - b["gw"]) / np.linalg.norm(b["gw"])),
                       "grad_theta_rel": (np.abs(a8["gt"] / b["gt"] - 1)).tolist()},
         "adjoint_seconds": {"f32": a["adj_s"], "f32_ckpt8": a8["adj_s"], "f64": b["adj_s"]},
+        "f32_fixed_state": {
+            "disp_rms_cells": float(np.sqrt(np.mean((af["s"] - b["s"]) ** 2)) / cell),
+            "grad_omega_cosine": float(af["gw"] @ b["gw"] / (np.linalg.norm(af["gw"]) * np.linalg.norm(b["gw"]))),
+            "grad_omega_rel_l2": float(np.linalg.norm(af["gw"] - b["gw"]) / np.linalg.norm(b["gw"])),
+            "grad_theta_rel": (np.abs(af["gt"] / b["gt"] - 1)).tolist()},
         "control_f64_omega_moved_1_f32_ulp": {
             "disp_rms_cells": float(np.sqrt(np.mean((bp["s"] - b["s"]) ** 2)) / cell),
             "grad_omega_cosine": float(bp["gw"] @ b["gw"] / (np.linalg.norm(bp["gw"]) * np.linalg.norm(b["gw"]))),

@@ -71,6 +71,12 @@ typedef struct {
                        order), 2 = 2LPT, s = D1 s1 + D2 s2 with the second-order growth of
                        App. A (Eqs. 52-57); the adjoint then also back-propagates through
                        s2 (10 more lattice FFTs forward, 16 in the adjoint, 3 N more values) */
+  int fixed_state;  /* 1: displacements and momenta held as 64-bit integers (units of 2^-40
+                       cells and 2^-36 cells per unit of drift factor); kicks and drifts add
+                       rounded increments that the reverse pass subtracts again, so reverse
+                       time integration recovers every forward state exactly (the paper's
+                       FP32 reversion error, Sec. 3.5, disappears).  Kernels read working-
+                       precision copies.  Not combined with ckpt_every > 0 (PM_ERR_ARG). */
 } pm_config;
 
 /*
@@ -359,6 +365,15 @@ int pm_set_snapshot_momenta(pm_ctx* ctx, void* mom_out, const void* dJ_dmom);
  */
 int pm_set_interp_snapshots(pm_ctx* ctx, int na, const double* a, void* disp_out, void* dens_out,
                             const void* dJ_ddisp, const void* dJ_ddens);
+
+/*
+ * The 64-bit fixed-point state of a context created with fixed_state = 1: displacement
+ * U = s / l 2^40 and momentum W = p / l 2^36 (l the cell size), device [batch][3][n_ptcl^3]
+ * each (either may be null).  After pm_forward it is the final state; after pm_adjoint the
+ * initial state recovered by the reverse pass, equal bit for bit to the one pm_forward
+ * started from.  Errors: PM_ERR_STATE for a context without the fixed-point state.
+ */
+int pm_get_fixed_state(pm_ctx* ctx, long long* disp_fixed, long long* mom_fixed);
 
 /* Initial state at a0 of the context's lpt_order (Sec. 2.1, Eq. 2): s0 = D1 s1 (+ D2 s2),
  * p0 = a^2 H (D1' s1 (+ D2' s2)).  s0_out, p0_out: optional (null: not written),

@@ -87,8 +87,10 @@ __host__ __device__ inline long long spec_len_cx(int n) { return spec_main_len(n
 // the pages a tile touches (and its address translations) few.  Lattice spectra and the
 // side planes always use the plain order.
 __host__ __device__ constexpr int spec_zb(int n) { return n >= 1024 ? 8 : 1; }
-__host__ __device__ inline long long spec_row(int n, int zb, int z, int y) {
-  return zb <= 1 ? (long long)z * n + y : ((long long)(z / zb) * n + y) * zb + (z % zb);
+__host__ __device__ constexpr int spec_lzb(int n) { return n >= 1024 ? 3 : 0; }   // log2 spec_zb
+// row of (z, y) with blocks of 2^lzb z values (shifts: the x passes are integer bound)
+__host__ __device__ inline long long spec_row(int n, int lzb, int z, int y) {
+  return ((((long long)(z >> lzb) * n + y)) << lzb) | (z & ((1 << lzb) - 1));
 }
 
 // Element q of a small array held in kernel parameters, chosen with selects: a dynamic

@@ -113,7 +113,7 @@ k_pull_r2c(BinGeo bg, const V4<T>* __restrict__ rec0, const V4<T>* __restrict__ 
     const int q = c / R, r = c % R;
     const long long grow = (long long)((T0 << bg.lz) + (r >> bg.ly)) * N + ((T1 << bg.ly) + (r & ((1 << bg.ly) - 1)));
     C* spec = pick(out.spec, q) + (long long)b * spec_len_cx(N);
-    C* o = spec + spec_row(N, spec_zb(N), (int)(grow / N), (int)(grow % N)) * L;
+    C* o = spec + spec_row(N, spec_lzb(N), (int)(grow / N), (int)(grow % N)) * L;
     const C zk = sm[srow(k) * FD::LD + c];
     if (k == 0) {
       o[0] = cmake<C>(zk.x + zk.y, (T)0);

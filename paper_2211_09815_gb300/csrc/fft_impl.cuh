@@ -170,7 +170,7 @@ k_fft_x_r2c(RowJob<T> job, int nrows, int nbuf, const cx_t<T>* __restrict__ twL,
     if (grow >= nrows) continue;
     C* spec = rb0.spec;
     const long long rr = grow % rows_per_inst;
-    C* out = spec + inst0 * spec_len_cx(N) + spec_row(N, job.zb, (int)(rr / N), (int)(rr % N)) * L;
+    C* out = spec + inst0 * spec_len_cx(N) + spec_row(N, job.lzb, (int)(rr / N), (int)(rr % N)) * L;
     C* side = spec + inst0 * spec_len_cx(N) + spec_main_len(N) + rr;
     const C zk = sm[srow(k) * TL::LD + c];
     if (k == 0) {
@@ -219,7 +219,7 @@ k_fft_x_c2r(RowJob<T> job, int nrows, const cx_t<T>* __restrict__ twL, const cx_
       const int inst = (int)(grow / rows_per_inst);
       const C* base = rb.spec + inst * spec_len_cx(N);
       const long long rr = grow % rows_per_inst;
-      const C* in = base + spec_row(N, job.zb, (int)(rr / N), (int)(rr % N)) * L;
+      const C* in = base + spec_row(N, job.lzb, (int)(rr / N), (int)(rr % N)) * L;
       xk[it] = in[k];
       xm[it] = k == 0 ? base[spec_main_len(N) + rr] : in[L - k];
     }
@@ -297,7 +297,7 @@ k_fft_x_c2r4(RowJob<T> job, int nrows, int dq, V4<T>* __restrict__ out4, const c
     if (idx < PAIRS && grow < nrows) {
       const C* base = pick(job.b, q).spec + (grow / rows_per_inst) * spec_len_cx(N);
       const long long rr = grow % rows_per_inst;
-      const C* in = base + spec_row(N, job.zb, (int)(rr / N), (int)(rr % N)) * L;
+      const C* in = base + spec_row(N, job.lzb, (int)(rr / N), (int)(rr % N)) * L;
       xk[it] = in[k];
       xm[it] = k == 0 ? base[spec_main_len(N) + rr] : in[L - k];
     }

@@ -55,6 +55,7 @@ static int validate(const pm_config* c, const double* theta) {
   if (c->n_mesh % c->n_ptcl != 0) return PM_ERR_ARG;
   if (c->n_steps < 1 || c->batch < 1 || c->ckpt_every < 0) return PM_ERR_ARG;
   if (c->lpt_order < 0 || c->lpt_order > 2) return PM_ERR_ARG;
+  if (c->fixed_state < 0 || c->fixed_state > 1 || (c->fixed_state && c->ckpt_every > 0)) return PM_ERR_ARG;
   if (!(c->a0 > 0) || !(c->a1 > c->a0) || !std::isfinite(c->a1)) return PM_ERR_ARG;
   if (c->precision != PM_F32 && c->precision != PM_F64) return PM_ERR_ARG;
   if ((long long)c->batch * c->n_mesh * c->n_mesh * (c->n_mesh / 2) >= (1LL << 31)) return PM_ERR_ARG;
@@ -234,6 +235,11 @@ int pm_set_interp_snapshots(pm_ctx* ctx, int na, const double* a, void* disp_out
                             const void* dJ_ddisp, const void* dJ_ddens) {
   if (!ctx) return PM_ERR_ARG;
   return ctx->eng->set_interp_snapshots(na, a, disp_out, dens_out, dJ_ddisp, dJ_ddens);
+}
+
+int pm_get_fixed_state(pm_ctx* ctx, long long* disp_fixed, long long* mom_fixed) {
+  if (!ctx) return PM_ERR_ARG;
+  return ctx->eng->get_fixed_state(disp_fixed, mom_fixed);
 }
 
 int pm_op_ic(pm_ctx* ctx, void* s0_out, void* p0_out) {

@@ -21,6 +21,7 @@ struct EngineBase {
   virtual int set_snapshot_momenta(void* mom, const void* gmom) = 0;
   virtual int set_interp_snapshots(int na, const double* a, void* disp, void* dens, const void* gdisp,
                                    const void* gdens) = 0;
+  virtual int get_fixed_state(long long* u, long long* w) = 0;
   virtual long long scratch_bytes() const = 0;
   virtual int profile(int enable) = 0;
   virtual int profile_read(double* ms, long long* launches) = 0;

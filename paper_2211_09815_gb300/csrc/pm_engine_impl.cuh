@@ -163,6 +163,19 @@ class Engine : public EngineBase {
     for (int q = 0; q < 7; ++q) PMGB_RET(alloc(&spec_[q], sl));
     PMGB_RET(alloc(&dens_, (long long)B_ * M_));
     PMGB_RET(alloc(&fvec_, (long long)B_ * M_));
+    if (cfg->fixed_state) {
+      PMGB_RET(alloc(&fix_u_, pv));
+      PMGB_RET(alloc(&fix_w_, pv));
+      const double l = cfg->box / nm_;
+      fx_.u = fix_u_;
+      fx_.w = fix_w_;
+      fx_.to_w = (T)(std::ldexp(1.0, kFixEP) / l);
+      fx_.from_u = (T)(l * std::ldexp(1.0, -kFixES));
+      fx_.from_w = (T)(l * std::ldexp(1.0, -kFixEP));
+      fx_.w_cells = (T)std::ldexp(1.0, -kFixEP);
+      fx_.du = (T)std::ldexp(1.0, kFixES);
+      fix_to_u_ = (T)(std::ldexp(1.0, kFixES) / l);
+    }
     if (cfg->ckpt_every > 0) {
       nck_ = (n_ + cfg->ckpt_every - 1) / cfg->ckpt_every;
       PMGB_RET(alloc(&ck_s_, pv * nck_));
@@ -215,7 +228,7 @@ class Engine : public EngineBase {
       // the bins of the next step's deposit are counted at the new positions
       k_gather_fwd<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, s_, p_, j == n_ ? a_ : nullptr, fvec_, sc, j,
                                                               n_ + 1, cks, ckp, fused1_ ? bgf1_ : bg1_,
-                                                              j < n_ ? bcount_ : nullptr, bkeys_, snap_p);
+                                                              j < n_ ? bcount_ : nullptr, bkeys_, snap_p, fx_);
       counted_ = j < n_;
       prof_.end(st_, P_GATHER_FWD);
       PMGB_CK(cudaGetLastError());
@@ -321,7 +334,7 @@ class Engine : public EngineBase {
       k_gather_adj<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, mass_, s_, p_, xi_, pi_, vmom ? a_ : nullptr,
                                                               nullptr, fvec_, sc, j, n_ + 1, ckp, cks, ppa, pxp,
                                                               pimax_, fused4_ ? bgf4_ : bg4_,
-                                                              j > 0 ? bcount_ : nullptr, bkeys_);
+                                                              j > 0 ? bcount_ : nullptr, bkeys_, fx_);
       counted_ = j > 0;
       prof_.end(st_, P_GATHER_ADJ);
       PMGB_CK(cudaGetLastError());
@@ -635,6 +648,13 @@ class Engine : public EngineBase {
     return PM_OK;
   }
 
+  int get_fixed_state(long long* u, long long* w) override {
+    if (!fx_.u) return PM_ERR_STATE;
+    if (u) PMGB_CK(cudaMemcpyAsync(u, fix_u_, sizeof(long long) * B_ * 3 * N_, cudaMemcpyDeviceToDevice, st_));
+    if (w) PMGB_CK(cudaMemcpyAsync(w, fix_w_, sizeof(long long) * B_ * 3 * N_, cudaMemcpyDeviceToDevice, st_));
+    return PM_OK;
+  }
+
   int op_ic(void* s0, void* p0) override {
     have_fwd_ = false;
     PMGB_RET(initial_conditions());
@@ -871,7 +891,7 @@ class Engine : public EngineBase {
   int r2c_real(int n, const T* in, long long in_is, C* out) {
     RowJob<T> job{};
     job.b[0] = RowBuf<T>{(void*)in, in_is, out};
-    job.zb = spec_zb(n);
+    job.lzb = spec_lzb(n);
     PMGB_RET(fft_x_r2c<T>(n, job, 1, B_ * n * n, tw_, st_));
     C* bufs[1] = {out};
     PMGB_RET(cols(n, -1, false, bufs, 1));
@@ -884,7 +904,7 @@ class Engine : public EngineBase {
     PMGB_RET(cols(n, +1, false, bufs, 1));
     RowJob<T> job{};
     job.b[0] = RowBuf<T>{(void*)out, out_is, in};
-    job.zb = spec_zb(n);
+    job.lzb = spec_lzb(n);
     PMGB_RET(fft_x_c2r<T>(n, job, 1, B_ * n * n, tw_, st_));
     PMGB_CK(cudaGetLastError());
     return PM_OK;
@@ -1044,7 +1064,7 @@ class Engine : public EngineBase {
           job.b[0] = RowBuf<T>{tg.d, tg.dis, spec_[0]};
           if (nq)
             for (int c = 0; c < 3; ++c) job.b[1 + c] = RowBuf<T>{tg.p[c], tg.pis, spec_[4 + c]};
-          job.zb = spec_zb(nm_);
+          job.lzb = spec_lzb(nm_);
           return fft_x_r2c<T>(nm_, job, nq ? 4 : 1, B_ * nm_ * nm_, tw_, st_);
         }, &ms_sep));
         FusedOut<T> fo{};
@@ -1207,7 +1227,7 @@ class Engine : public EngineBase {
       job.b[0] = RowBuf<T>{tg.d, tg.dis, spec_[0]};
       if (pi)
         for (int c = 0; c < 3; ++c) job.b[1 + c] = RowBuf<T>{tg.p[c], tg.pis, spec_[4 + c]};
-      job.zb = spec_zb(nm_);
+      job.lzb = spec_lzb(nm_);
       prof_.begin(st_, P_X_R2C, 1);
       PMGB_RET(fft_x_r2c<T>(nm_, job, nb, B_ * nm_ * nm_, tw_, st_));
       prof_.end(st_, P_X_R2C);
@@ -1268,7 +1288,7 @@ class Engine : public EngineBase {
     C* c2rb[4] = {spec_[1], spec_[2], spec_[3], spec_[0]};
     RowJob<T> jc{};
     for (int q = 0; q < 4; ++q) jc.b[q] = RowBuf<T>{nullptr, 0, (q < 3 || pi) ? c2rb[q] : nullptr};
-    jc.zb = spec_zb(nm_);
+    jc.lzb = spec_lzb(nm_);
     prof_.begin(st_, P_X_C2R, 1);
     PMGB_RET(fft_x_c2r4<T>(nm_, jc, B_ * nm_ * nm_, 2, reinterpret_cast<V4<T>*>(fvec_), tw_, st_));
     prof_.end(st_, P_X_C2R);
@@ -1323,6 +1343,10 @@ class Engine : public EngineBase {
     k_ic_state<T><<<dim3(256, B_), 256, 0, st_>>>(rmesh(1), rmesh(2), rmesh(3), 2 * lis, N_, d1_, gd_, s1_, s_, p_);
     PMGB_CK(cudaGetLastError());
     if (lpt2_) PMGB_RET(lpt2_state());
+    if (fx_.u) {
+      k_fix_init<T><<<dim3(256, B_), 256, 0, st_>>>(s_, p_, fx_, fix_to_u_, 3 * N_);
+      PMGB_CK(cudaGetLastError());
+    }
     return PM_OK;
   }
 
@@ -1505,6 +1529,9 @@ class Engine : public EngineBase {
   int* e_pi_ = nullptr;
   double *part_ = nullptr, *steps_ = nullptr, *scal_ = nullptr, *theta_out_ = nullptr;
   bool have_fwd_ = false;
+  long long *fix_u_ = nullptr, *fix_w_ = nullptr;   // fixed-point state (cfg.fixed_state)
+  FixState<T> fx_{};
+  T fix_to_u_ = 0;
   Prof prof_;
   bool use_tma_ = false;
   int nsm_ = 1;

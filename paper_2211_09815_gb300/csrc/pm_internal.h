@@ -31,7 +31,7 @@ template <typename T> struct RowBuf {
 };
 template <typename T> struct RowJob {
   RowBuf<T> b[4];
-  int zb;               // z blocking of the spectra's main rows (spec_row); 0 or 1: plain order
+  int lzb;              // log2 of the z blocking of the spectra's main rows (spec_row); 0: plain
 };
 
 // Fused z pass with the Green's function G = coef[b] / n^2 * (deconvolution) per mode.

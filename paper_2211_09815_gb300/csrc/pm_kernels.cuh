@@ -95,6 +95,27 @@ template <typename T> __device__ __forceinline__ long long to_fixed(T v);
 template <> __device__ __forceinline__ long long to_fixed<float>(float v) { return f2ll_rn(v); }
 template <> __device__ __forceinline__ long long to_fixed<double>(double v) { return __double2ll_rn(v); }
 
+// Exactly reversible particle state (pm_config.fixed_state): displacement and momentum held
+// as 64-bit integers, U = s / l in units of 2^-kFixES cells and W = p / l in units of
+// 2^-kFixEP cells per unit of drift factor.  A kick adds round(a K / l 2^kFixEP), a drift
+// round(w D 2^kFixES) with w the working-precision value of W; the reverse pass subtracts
+// the same rounded increments (the same forces at the same positions), so it recovers the
+// forward states bit for bit.  The kernels that read positions and momenta see working-
+// precision shadows s = U l 2^-kFixES, p = W l 2^-kFixEP.
+constexpr int kFixES = 40, kFixEP = 36;
+template <typename T> struct FixState {
+  long long* u;   // [batch][3][N] or null: floating-point state
+  long long* w;
+  T to_w;         // 2^kFixEP / l: momentum increment -> W units
+  T from_u;       // l 2^-kFixES: U -> displacement
+  T from_w;       // l 2^-kFixEP: W -> momentum
+  T w_cells;      // 2^-kFixEP: W -> cells per unit of drift factor
+  T du;           // 2^kFixES: cells -> U units
+};
+template <typename T> __device__ __forceinline__ T fix_to_real(long long v);
+template <> __device__ __forceinline__ float fix_to_real<float>(long long v) { return ll2f_rn(v); }
+template <> __device__ __forceinline__ double fix_to_real<double>(long long v) { return (double)v; }
+
 // Deterministic block sum of one double per thread (fixed shuffle tree + fixed warp order).
 __device__ __forceinline__ double block_sum(double v, double* sh) {
 #pragma unroll
@@ -296,7 +317,7 @@ __global__ void __launch_bounds__(kPtclThreads)
 k_gather_fwd(Geo<T> g, T* __restrict__ s, T* __restrict__ p, T* __restrict__ a_out,
              const V4<T>* __restrict__ fvec, StepCoef<T> sc, int j, int nstep1, T* __restrict__ ck_s,
              T* __restrict__ ck_p, BinGeo bg, unsigned* __restrict__ bcount, unsigned* __restrict__ bkeys,
-             T* __restrict__ snap_p = nullptr) {
+             T* __restrict__ snap_p = nullptr, FixState<T> fx = FixState<T>{}) {
   const int b = blockIdx.y;
   const T kA = sc.kA[b * nstep1 + j], kB = sc.kB[b * nstep1 + j], dr = sc.dr[b * nstep1 + j];
   T* sb = s + (long long)b * 3 * g.N;
@@ -326,15 +347,32 @@ k_gather_fwd(Geo<T> g, T* __restrict__ s, T* __restrict__ p, T* __restrict__ a_o
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      pv[c] += a[c] * kA;
-      if (ck_p) ck_p[(long long)b * 3 * g.N + c * g.N + i] = pv[c];
-      if (snap_p) snap_p[(long long)b * 3 * g.N + c * g.N + i] = pv[c];   // p_j of an observed state
-      pv[c] += a[c] * kB;
-      if (ck_s) ck_s[(long long)b * 3 * g.N + c * g.N + i] = sv[c];
-      sv[c] += pv[c] * dr;
+      const long long o = (long long)b * 3 * g.N + c * g.N + i;
+      if (fx.u) {
+        // fixed-point state: exact integer kicks and drift, shadows for the other kernels
+        long long W = fx.w[o], U = fx.u[o];
+        W += to_fixed<T>(mul_rn<T>(mul_rn<T>(a[c], kA), fx.to_w));
+        if (ck_p || snap_p) pv[c] = mul_rn<T>(fix_to_real<T>(W), fx.from_w);
+        if (ck_p) ck_p[o] = pv[c];
+        if (snap_p) snap_p[o] = pv[c];
+        W += to_fixed<T>(mul_rn<T>(mul_rn<T>(a[c], kB), fx.to_w));
+        if (ck_s) ck_s[o] = sv[c];
+        U += to_fixed<T>(mul_rn<T>(mul_rn<T>(mul_rn<T>(fix_to_real<T>(W), fx.w_cells), dr), fx.du));
+        fx.w[o] = W;
+        fx.u[o] = U;
+        pv[c] = mul_rn<T>(fix_to_real<T>(W), fx.from_w);
+        sv[c] = mul_rn<T>(fix_to_real<T>(U), fx.from_u);
+      } else {
+        pv[c] += a[c] * kA;
+        if (ck_p) ck_p[o] = pv[c];
+        if (snap_p) snap_p[o] = pv[c];   // p_j of an observed state
+        pv[c] += a[c] * kB;
+        if (ck_s) ck_s[o] = sv[c];
+        sv[c] += pv[c] * dr;
+      }
       pb[c * g.N + i] = pv[c];
       sb[c * g.N + i] = sv[c];
-      if (a_out) a_out[(long long)b * 3 * g.N + c * g.N + i] = a[c];
+      if (a_out) a_out[o] = a[c];
     }
     // bin of the new position for the next step's deposit (the loop is warp-uniform: N is
     // a multiple of 32 and so is the grid stride)
@@ -352,7 +390,7 @@ k_gather_adj(Geo<T> g, T mass, T* __restrict__ s, T* __restrict__ p, T* __restri
              StepCoef<T> sc, int j, int nstep1,
              const T* __restrict__ ck_p, const T* __restrict__ ck_s, double* __restrict__ part_pa,
              double* __restrict__ part_xp, unsigned* __restrict__ pimax, BinGeo bg, unsigned* __restrict__ bcount,
-             unsigned* __restrict__ bkeys) {
+             unsigned* __restrict__ bkeys, FixState<T> fx = FixState<T>{}) {
   __shared__ double shd[kPtclThreads / 32];
   __shared__ float shf[kPtclThreads / 32];
   const int b = blockIdx.y;
@@ -396,18 +434,36 @@ k_gather_adj(Geo<T> g, T mass, T* __restrict__ s, T* __restrict__ p, T* __restri
       al[2] += w0 * w1 * g2 * h;
     }
     acc_pa.add(qv[0] * a[0] + qv[1] * a[1] + qv[2] * a[2]);
+    long long W[3] = {0, 0, 0};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      pv[c] -= a[c] * cA;
+      if (fx.u) {
+        // the forward's rounded increments, subtracted in reverse order (checkpoints are
+        // never combined with the fixed-point state)
+        W[c] = fx.w[po + c * g.N + i];
+        W[c] -= to_fixed<T>(mul_rn<T>(mul_rn<T>(a[c], cA), fx.to_w));
+        W[c] -= to_fixed<T>(mul_rn<T>(mul_rn<T>(a[c], cB), fx.to_w));
+        pv[c] = mul_rn<T>(fix_to_real<T>(W[c]), fx.from_w);
+      } else {
+        pv[c] -= a[c] * cA;
+        if (ck_p) pv[c] = ck_p[po + c * g.N + i];
+        pv[c] -= a[c] * cB;
+      }
       xv[c] += al[c] * cA;
-      if (ck_p) pv[c] = ck_p[po + c * g.N + i];
-      pv[c] -= a[c] * cB;
       xv[c] += al[c] * cB;
     }
     acc_xp.add(xv[0] * pv[0] + xv[1] * pv[1] + xv[2] * pv[2]);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      sv[c] -= pv[c] * dr;
+      if (fx.u) {
+        long long U = fx.u[po + c * g.N + i];
+        U -= to_fixed<T>(mul_rn<T>(mul_rn<T>(mul_rn<T>(fix_to_real<T>(W[c]), fx.w_cells), dr), fx.du));
+        fx.u[po + c * g.N + i] = U;
+        fx.w[po + c * g.N + i] = W[c];
+        sv[c] = mul_rn<T>(fix_to_real<T>(U), fx.from_u);
+      } else {
+        sv[c] -= pv[c] * dr;
+      }
       qv[c] += xv[c] * dr;
       if (ck_s) sv[c] = ck_s[po + c * g.N + i];
       s[po + c * g.N + i] = sv[c];
@@ -891,6 +947,23 @@ __global__ void k_ic_state(const T* __restrict__ r0, const T* __restrict__ r1, c
   }
 }
 
+// Fixed-point state from the initial state: U = round(s / l 2^kFixES), W = round(p / l
+// 2^kFixEP), and s, p replaced by their shadows
+template <typename T>
+__global__ void k_fix_init(T* __restrict__ s, T* __restrict__ p, FixState<T> fx, T to_u, long long n3) {
+  const int b = blockIdx.y;
+  const long long o0 = (long long)b * n3;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3; i += (long long)gridDim.x * blockDim.x) {
+    const long long o = o0 + i;
+    const long long U = to_fixed<T>(mul_rn<T>(s[o], to_u));
+    const long long W = to_fixed<T>(mul_rn<T>(p[o], fx.to_w));
+    fx.u[o] = U;
+    fx.w[o] = W;
+    s[o] = mul_rn<T>(fix_to_real<T>(U), fx.from_u);
+    p[o] = mul_rn<T>(fix_to_real<T>(W), fx.from_w);
+  }
+}
+
 // sbar = D1 xi + G_D pi into the lattice FFT inputs; partials of xi.s1 and pi.s1
 template <typename T>
 __global__ void __launch_bounds__(kPtclThreads)
@@ -1078,7 +1151,7 @@ __global__ void k_spec_to_std(const cx_t<T>* __restrict__ spec, cx_t<T>* __restr
     const int k = (int)(r % h);
     const long long row = r / h;
     const cx_t<T>* base = spec + b * spec_len_cx(n);
-    const long long mrow = spec_row(n, spec_zb(n), (int)(row / n), (int)(row % n));
+    const long long mrow = spec_row(n, spec_lzb(n), (int)(row / n), (int)(row % n));
     out[u] = k < n / 2 ? base[mrow * (n / 2) + k] : base[spec_main_len(n) + row];
   }
 }
@@ -1091,7 +1164,7 @@ __global__ void k_std_to_spec(const cx_t<T>* __restrict__ in, cx_t<T>* __restric
     const int k = (int)(r % h);
     const long long row = r / h;
     cx_t<T>* base = spec + b * spec_len_cx(n);
-    const long long mrow = spec_row(n, spec_zb(n), (int)(row / n), (int)(row % n));
+    const long long mrow = spec_row(n, spec_lzb(n), (int)(row / n), (int)(row % n));
     if (k < n / 2) base[mrow * (n / 2) + k] = in[u];
     else base[spec_main_len(n) + row] = in[u];
   }

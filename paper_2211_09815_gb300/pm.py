@@ -19,7 +19,8 @@ SYMBOLS = ("pm_init", "pm_forward", "pm_loss_mse", "pm_adjoint", "pm_destroy", "
            "pm_op_fft", "pm_op_za", "pm_set_inputs", "pm_gradient", "pm_profile", "pm_profile_read",
            "pm_density_noalloc", "pm_power_spectrum", "pm_gradient_graph", "pm_get_tuning", "pm_set_tuning",
            "pm_autotune", "pm_op_ic", "pm_loss_power", "pm_set_snapshots", "pm_check", "pm_debug_fail_alloc",
-           "pm_debug_live_bytes", "pm_debug_first_wait", "pm_set_snapshot_momenta", "pm_set_interp_snapshots")
+           "pm_debug_live_bytes", "pm_debug_first_wait", "pm_set_snapshot_momenta", "pm_set_interp_snapshots",
+           "pm_get_fixed_state")
 NOALLOC_MAX_CELLS = 128 ** 3
 PROF_NAMES = ("scatter", "fft_x_r2c", "fft_cols", "fused_z_force", "fused_z_adjoint", "fft_x_c2r",
               "gather_fwd", "gather_adj", "other")
@@ -51,7 +52,7 @@ class PMConfig(ctypes.Structure):
     _fields_ = [("box", ctypes.c_double), ("n_mesh", ctypes.c_int), ("n_ptcl", ctypes.c_int),
                 ("n_steps", ctypes.c_int), ("a0", ctypes.c_double), ("a1", ctypes.c_double),
                 ("precision", ctypes.c_int), ("ckpt_every", ctypes.c_int), ("deconv", ctypes.c_int),
-                ("batch", ctypes.c_int), ("lpt_order", ctypes.c_int)]
+                ("batch", ctypes.c_int), ("lpt_order", ctypes.c_int), ("fixed_state", ctypes.c_int)]
 
 
 _lib = None
@@ -96,6 +97,7 @@ def load_library(path=LIB_PATH):
     lib.pm_autotune.argtypes = [vp, i, ctypes.POINTER(PMTuning), vp]
     lib.pm_check.argtypes = [vp]
     lib.pm_set_snapshot_momenta.argtypes = [vp, vp, vp]
+    lib.pm_get_fixed_state.argtypes = [vp, vp, vp]
     lib.pm_set_interp_snapshots.argtypes = [vp, i, dp, vp, vp, vp, vp]
     lib.pm_debug_fail_alloc.argtypes = [ctypes.c_longlong]
     lib.pm_debug_live_bytes.argtypes = []
@@ -164,14 +166,14 @@ class PMContext:
 
     def __init__(self, box, n_mesh, n_ptcl, n_steps, theta, omega, a0=1.0 / 64, a1=1.0,
                  precision=PM_F32, ckpt_every=0, deconv=False, batch=1, stream=None, lpt_order=1,
-                 check_errors=True):
+                 check_errors=True, fixed_state=False):
         import torch
         lib = load_library()
         self.check_errors = check_errors
         self.state_version = 0
         self.device = torch.cuda.current_device()
         self.cfg = PMConfig(box, n_mesh, n_ptcl, n_steps, a0, a1, precision, ckpt_every, int(deconv), batch,
-                            int(lpt_order))
+                            int(lpt_order), int(fixed_state))
         self.dtype = torch.float32 if precision == PM_F32 else torch.float64
         self.batch, self.n_mesh, self.n_ptcl = batch, n_mesh, n_ptcl
         self.N, self.M = n_ptcl ** 3, n_mesh ** 3
@@ -300,6 +302,15 @@ class PMContext:
             self._p(dens, m, "dens"), self._p(ddisp, v, "ddisp"), self._p(ddens, m, "ddens")),
             "pm_set_interp_snapshots")
         self._interp_buffers = (disp, dens, ddisp, ddens) if na else None
+
+    def get_fixed_state(self, disp_fixed=None, mom_fixed=None):
+        """The 64-bit fixed-point state (contexts with fixed_state=True) into int64 CUDA
+        tensors of batch x 3 N elements."""
+        import torch
+        v = 3 * self.batch * self.N
+        self._run(load_library().pm_get_fixed_state(self._h, self._p(disp_fixed, v, "disp_fixed", torch.int64),
+                                                    self._p(mom_fixed, v, "mom_fixed", torch.int64)),
+                  "pm_get_fixed_state", False)
 
     def op_ic(self, s0=None, p0=None):
         """Initial state (s0, p0) at a0 of the context's LPT order."""
