@@ -221,10 +221,13 @@ template <typename T, int L, int BYTES = 65536> struct ColTile {
 // Fused z passes keep two tiles of the column-pass shape.
 template <typename T, int L> using FusedTile = ColTile<T, L, 65536>;
 // Row passes (x axis): TR rows of L = n/2 complex values, tile padded to LD = TR + 1 so
-// that the transposing row loads do not collide in shared-memory banks.
+// that the transposing row loads do not collide in shared-memory banks.  Rows of 512
+// points run the two-stage radix-32 plan on 64 KB tiles (one shared-memory round trip less
+// than three radix-8 stages); shorter rows the three-stage plans on 32 KB tiles.
 template <typename T, int L> struct RowTile {
-  static constexpr int RMAX = Plan<L>::RMAX;
-  static constexpr int TR0 = 32768 / (L * (int)sizeof(cx_t<T>));
+  using P = Plan2<L>;
+  static constexpr int RMAX = P::RMAX;
+  static constexpr int TR0 = (RMAX == 32 ? 65536 : 32768) / (L * (int)sizeof(cx_t<T>));
   static constexpr int TR1 = TR0 > 128 ? 128 : TR0;
   static constexpr int TRMAXNT = 512 * RMAX / L;
   static constexpr int TR2 = TR1 < TRMAXNT ? TR1 : TRMAXNT;

@@ -160,7 +160,7 @@ k_fft_x_r2c(RowJob<T> job, int nrows, int nbuf, const cx_t<T>* __restrict__ twL,
   }
   __syncthreads();
   SmemTile<C, TL::LD> t{sm};
-  fft_tile<T, L, TL::TR, TL::NT, -1>(t, t, t, twL);
+  fft_tile<T, L, TL::TR, TL::NT, -1, typename TL::P>(t, t, t, twL);
   __syncthreads();
   // even/odd split: X[k] = E[k] + W^k O[k], E = (Z[k] + conj Z[L-k]) / 2, O = -i (Z[k] - conj Z[L-k]) / 2
   for (int idx = threadIdx.x; idx < TL::TR * (L / 2 + 1); idx += TL::NT) {
@@ -245,7 +245,7 @@ k_fft_x_c2r(RowJob<T> job, int nrows, const cx_t<T>* __restrict__ twL, const cx_
   }
   __syncthreads();
   SmemTile<C, TL::LD> t{sm};
-  fft_tile<T, L, TL::TR, TL::NT, +1>(t, t, t, twL);
+  fft_tile<T, L, TL::TR, TL::NT, +1, typename TL::P>(t, t, t, twL);
   __syncthreads();
   for (int idx = threadIdx.x; idx < TL::TR * L; idx += TL::NT) {
     const int row = idx / L, j = idx % L;
@@ -262,10 +262,11 @@ k_fft_x_c2r(RowJob<T> job, int nrows, const cx_t<T>* __restrict__ twL, const cx_
 // load.  The block holds TR/4 rows of each component; a null spectrum pointer reads as 0.
 // Component dq (or none if dq < 0) is multiplied by -i k_x on the way in.
 template <typename T, int L, int Q> struct C2R4Tile {
+  using P = typename RowTile<T, L>::P;
   static constexpr int RT = RowTile<T, L>::TR / 4;       // rows per block
   static constexpr int TR = Q * RT;                      // sequences per block
   // above 256 threads, two radix items per thread (measured faster at L = 512)
-  static constexpr int NT0 = TR * L / Plan<L>::RMAX;
+  static constexpr int NT0 = TR * L / P::RMAX;
   static constexpr int NT = (NT0 > 256 && (NT0 / 2) % 32 == 0) ? NT0 / 2 : NT0;
   static constexpr int LD = TR + 1;
   static constexpr int SMEM = skew_rows(L) * LD * (int)sizeof(cx_t<T>);
@@ -329,7 +330,7 @@ k_fft_x_c2r4(RowJob<T> job, int nrows, int dq, V4<T>* __restrict__ out4, const c
   }
   __syncthreads();
   SmemTile<C, TL::LD> t{sm};
-  fft_tile<T, L, TL::TR, TL::NT, +1>(t, t, t, twL);
+  fft_tile<T, L, TL::TR, TL::NT, +1, typename TL::P>(t, t, t, twL);
   __syncthreads();
   for (int idx = threadIdx.x; idx < RT * L; idx += TL::NT) {
     const int row = idx / L, j = idx % L;
@@ -772,7 +773,7 @@ template <typename T, int L, int Q>
 static void launch_c2r4_LQ(const RowJob<T>& job, int nrows, int dq, V4<T>* out4, const cx_t<T>* tw,
                            cudaStream_t st) {
   using TL = C2R4Tile<T, L, Q>;
-  if constexpr (RowTile<T, L>::TR % 4 == 0 && (TL::TR * L) % Plan<L>::RMAX == 0) {
+  if constexpr (RowTile<T, L>::TR % 4 == 0 && (TL::TR * L) % TL::P::RMAX == 0) {
     const size_t sm = TL::SMEM;
     auto fn = k_fft_x_c2r4<T, L, Q>;
     set_smem<T, L>((const void*)fn, sm);

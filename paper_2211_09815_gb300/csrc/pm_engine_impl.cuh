@@ -919,7 +919,7 @@ class Engine : public EngineBase {
     tune_.threads_density = 256;
     tune_.threads_adjoint = 512;
     tune_.tma_columns = 1;
-    tune_.fused_x = fused_rows<T>(nm_, 1) > 0 ? 3 : 0;
+    tune_.fused_x = fused_rows<T>(nm_, 1) > 0 && !cfg_.fixed_state ? 3 : 0;
     const BinGeo smallest = make_bin_geo(ilog2(nm_), 3, 3, 3);
     const long long maxbin = (long long)B_ * smallest.nkeys + 1;
     PMGB_RET(alloc(&bkeys_, (long long)B_ * N_));
@@ -941,8 +941,10 @@ class Engine : public EngineBase {
     bg4_ = make_bin_geo(lg, tune_.tile_log2_adjoint[2], tune_.tile_log2_adjoint[1], tune_.tile_log2_adjoint[0]);
     use_tma_ = tune_.tma_columns != 0 && tma_supported(nm_);
     // deposit fused with the R2C x pass: tiles of whole x rows, R rows split over (y, z)
-    fused1_ = (tune_.fused_x & 1) != 0 && fused_rows<T>(nm_, 1) > 0;
-    fused4_ = (tune_.fused_x & 2) != 0 && fused_rows<T>(nm_, 1) > 0;
+    // (with the fixed-point state the forward and the reverse deposit take the same x pass,
+    // so that both see bitwise the same forces)
+    fused1_ = (tune_.fused_x & 1) != 0 && fused_rows<T>(nm_, 1) > 0 && !cfg_.fixed_state;
+    fused4_ = (tune_.fused_x & 2) != 0 && fused_rows<T>(nm_, 1) > 0 && !cfg_.fixed_state;
     if (fused_rows<T>(nm_, 1) > 0) {
       auto geo = [&](int rows) {
         const int lr = ilog2(rows);
@@ -970,7 +972,8 @@ class Engine : public EngineBase {
     if (t->tma_columns != 0 && t->tma_columns != 1) return PM_ERR_ARG;
     if (t->tma_columns && !tma_supported(nm_)) return PM_ERR_ARG;
     if (!t->tma_columns && spec_zb(nm_) > 1) return PM_ERR_ARG;   // z-blocked rows: staged passes only
-    if (t->fused_x < 0 || t->fused_x > 3 || (t->fused_x && fused_rows<T>(nm_, 1) == 0)) return PM_ERR_ARG;
+    if (t->fused_x < 0 || t->fused_x > 3 || (t->fused_x && (fused_rows<T>(nm_, 1) == 0 || cfg_.fixed_state)))
+      return PM_ERR_ARG;
     tune_ = *t;
     apply_tuning();
     return PM_OK;
@@ -1050,7 +1053,7 @@ class Engine : public EngineBase {
     }
     // deposit fused with the R2C x pass against the chosen separate deposit + x pass, for
     // the density deposit (bit 0) and the density + pi deposit (bit 1) separately
-    if (fused_rows<T>(nm_, 1) > 0) {
+    if (fused_rows<T>(nm_, 1) > 0 && !cfg_.fixed_state) {
       best.fused_x = 0;
       for (int nq = 0; nq < 2; ++nq) {
         const int* l = nq ? best.tile_log2_adjoint : best.tile_log2_density;
