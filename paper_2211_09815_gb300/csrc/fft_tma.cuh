@@ -358,6 +358,7 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
         stage<T, L, TC, NT, RA, 1, -1>(t, t, stw);
         __syncthreads();
         C x[PER][RB];
+        T gz[PER][RB];
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
           const int j = (threadIdx.x + i * NT) / TC;      // j < L / RB = RA
@@ -375,6 +376,18 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
           if (q + 1 < nq) issue(q + 1);
         }
         __syncthreads();   // the work tile is written below, after that wait
+        // the Green's function of each row, shared by both outputs (one division per element)
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+          const int j = (threadIdx.x + i * NT) / TC;
+#pragma unroll
+          for (int r = 0; r < RB; ++r) {
+            const int f0 = freq_of(j + RA * r, N);
+            const T gv = zc.g(f0);
+            x[i][r] = cmake<C>(x[i][r].x * gv, x[i][r].y * gv);      // G X
+            gz[i][r] = (T)zc.fc(0, f0);                               // k_0 (Nyquist row 0)
+          }
+        }
 #pragma unroll
         for (int mode = 0; mode < 2; ++mode) {
           // mode 0: -i k_0 G X (z force) -> work; mode 1: G X (U) -> the ring slot
@@ -384,7 +397,8 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
             const int j = (threadIdx.x + i * NT) / TC;
             C y[RB];
 #pragma unroll
-            for (int r = 0; r < RB; ++r) y[r] = DenseMulSrc<T, N, TT::LD>::apply(x[i][r], j + RA * r, zc, mode);
+            for (int r = 0; r < RB; ++r)
+              y[r] = mode == 1 ? x[i][r] : cmake<C>(x[i][r].y * gz[i][r], -x[i][r].x * gz[i][r]);
             dft<RB, +1>(y);                                  // inverse stage 1 (NS = 1)
 #pragma unroll
             for (int r = 0; r < RB; ++r) dst[(j * RB + r) * TT::LD + c] = y[r];
