@@ -384,7 +384,7 @@ k_gather_fwd(Geo<T> g, T* __restrict__ s, T* __restrict__ p, T* __restrict__ a_o
 // p -= a K1_{j+1}; xi += alpha K1_{j+1}; (p := stored p_j); p -= a K2_j; xi += alpha K2_j;
 // s -= p D_j; pi += xi D_j; (s := stored s_{j-1}).  FP64 partials of pi.a and xi.p.
 template <typename T>
-__global__ void __launch_bounds__(kPtclThreads, 3)   // three CTAs per SM: the random corner loads want warps
+__global__ void __launch_bounds__(kPtclThreads)
 k_gather_adj(Geo<T> g, T mass, T* __restrict__ s, T* __restrict__ p, T* __restrict__ xi, T* __restrict__ pi,
              T* __restrict__ a_out, T* __restrict__ alpha_out, const V4<T>* __restrict__ fvec,
              StepCoef<T> sc, int j, int nstep1,
