@@ -232,7 +232,7 @@ template <> __device__ __forceinline__ double words_to_real<double>(unsigned lo,
 // corner that lands in the tile rounded to fixed point and added exactly.  acc: low words
 // [NQ][cells], then high words [NQ][cells] (zeroed here).
 template <typename T, int NQ>
-__device__ __forceinline__ bool pull_accumulate(const BinGeo& bg, const V4<T>* __restrict__ rec0,
+__device__ __forceinline__ void pull_accumulate(const BinGeo& bg, const V4<T>* __restrict__ rec0,
                                                 const V4<T>* __restrict__ rec1, const unsigned* __restrict__ start,
                                                 int e_d, int b, int tile, unsigned* acc, unsigned* rbeg,
                                                 unsigned* rpre) {
@@ -265,13 +265,6 @@ __device__ __forceinline__ bool pull_accumulate(const BinGeo& bg, const V4<T>* _
   const T sd = pow2i<T>(e_d);
   const unsigned total = rpre[20];
   const unsigned mx = (1u << bg.lx) - 1, my = (1u << bg.ly) - 1, mz = (1u << bg.lz) - 1;
-  // Split form: an FP32 contribution is an int32 v (|v| <= 2^30); with fewer than 2^11
-  // records in the tile no cell receives 2^11 contributions, so the sums of its low 21
-  // bits (unsigned) and of v >> 21 (signed) each fit one 32-bit word and need no carries:
-  // atomic additions whose results are not used (reductions), no dependency on a returned
-  // value.  The exact two-word form with carries otherwise.  Either way the cell sum is
-  // the exact integer (split_words_value / words_to_real).
-  const bool split = sizeof(T) == 4 && total < 2048u;
   for (unsigned f = threadIdx.x; f < total; f += blockDim.x) {
     int r = 0;
     while (f >= rpre[r + 1]) ++r;
@@ -304,38 +297,17 @@ __device__ __forceinline__ bool pull_accumulate(const BinGeo& bg, const V4<T>* _
       const T w = ((e & 4) ? t[0] : (T)1 - t[0]) * ((e & 2) ? t[1] : (T)1 - t[1]) * ((e & 1) ? t[2] : (T)1 - t[2]);
       unsigned vl, vh;
       fixed_words<T>(w * sd, vl, vh);
-      if (split) {
-        atomicAdd(acc + loc, vl & 0x1FFFFFu);
-        atomicAdd(hacc + loc, (unsigned)((int)vl >> 21));
-      } else {
-        smem_add64(acc + loc, hacc + loc, vl, vh);
-      }
+      smem_add64(acc + loc, hacc + loc, vl, vh);
       if constexpr (NQ == 4) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           fixed_words<T>(pv[c] * w, vl, vh);
-          if (split) {
-            atomicAdd(acc + (1 + c) * cells + loc, vl & 0x1FFFFFu);
-            atomicAdd(hacc + (1 + c) * cells + loc, (unsigned)((int)vl >> 21));
-          } else {
-            smem_add64(acc + (1 + c) * cells + loc, hacc + (1 + c) * cells + loc, vl, vh);
-          }
+          smem_add64(acc + (1 + c) * cells + loc, hacc + (1 + c) * cells + loc, vl, vh);
         }
       }
     }
   }
   __syncthreads();
-  return split;
-}
-
-// the exact cell sum of the split form: low-21-bit digits plus the signed high parts << 21
-template <typename T> __device__ __forceinline__ T split_words_to_real(unsigned s0, unsigned s1) {
-  const long long v = (long long)s0 + ((long long)(int)s1 << 21);
-  if constexpr (sizeof(T) == 4) return ll2f_rn(v);
-  else return (T)v;
-}
-template <typename T> __device__ __forceinline__ T acc_to_real(bool split, unsigned lo, unsigned hi) {
-  return split ? split_words_to_real<T>(lo, hi) : words_to_real<T>(lo, hi);
 }
 
 // One CTA per tile (grid: tiles x instances; tile x extent >= 4, outputs 16-byte aligned).
@@ -355,7 +327,7 @@ k_pull_scatter(Geo<T> g, BinGeo bg, const V4<T>* __restrict__ rec0, const V4<T>*
   const int tile = blockIdx.x;
   const int T2 = tile & (bg.ntx - 1), T1 = (tile / bg.ntx) & (bg.nty - 1), T0 = tile / (bg.ntx * bg.nty);
   const int cells = 1 << (bg.lx + bg.ly + bg.lz);
-  const bool split = pull_accumulate<T, NQ>(bg, rec0, rec1, start, e_d, b, tile, acc, rbeg, rpre);
+  pull_accumulate<T, NQ>(bg, rec0, rec1, start, e_d, b, tile, acc, rbeg, rpre);
   const unsigned* hacc = acc + NQ * cells;
   const unsigned mx = (1u << bg.lx) - 1, my = (1u << bg.ly) - 1;
   const T md = mass * pow2i<T>(-e_d);
@@ -376,8 +348,8 @@ k_pull_scatter(Geo<T> g, BinGeo bg, const V4<T>* __restrict__ rec0, const V4<T>*
       const uint4 hi = *reinterpret_cast<const uint4*>(hacc + q * cells + k);
       const T m = q == 0 ? md : mp[q - 1];
       const T a = q == 0 ? (T)-1 : (T)0;
-      const V4<T> v{acc_to_real<T>(split, lo.x, hi.x) * m + a, acc_to_real<T>(split, lo.y, hi.y) * m + a,
-                    acc_to_real<T>(split, lo.z, hi.z) * m + a, acc_to_real<T>(split, lo.w, hi.w) * m + a};
+      const V4<T> v{words_to_real<T>(lo.x, hi.x) * m + a, words_to_real<T>(lo.y, hi.y) * m + a,
+                    words_to_real<T>(lo.z, hi.z) * m + a, words_to_real<T>(lo.w, hi.w) * m + a};
       T* o = q == 0 ? dout + b * dis : (q == 1 ? p0 : (q == 2 ? p1 : p2)) + b * pis;
       *reinterpret_cast<V4<T>*>(o + cell) = v;
     }

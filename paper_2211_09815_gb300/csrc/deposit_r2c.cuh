@@ -62,7 +62,7 @@ k_pull_r2c(BinGeo bg, const V4<T>* __restrict__ rec0, const V4<T>* __restrict__ 
   __shared__ unsigned rbeg[20], rpre[21];
   const int b = blockIdx.y;
   const int tile = blockIdx.x;
-  const bool split = pull_accumulate<T, NQ>(bg, rec0, rec1, start, e_d, b, tile, acc, rbeg, rpre);
+  pull_accumulate<T, NQ>(bg, rec0, rec1, start, e_d, b, tile, acc, rbeg, rpre);
 
   // exact sums -> working precision: delta = m acc 2^-e_d - 1, pi_c = acc 2^-e_c; two
   // neighbouring x cells (one complex of the packed row) per item, all read before the
@@ -85,7 +85,7 @@ k_pull_r2c(BinGeo bg, const V4<T>* __restrict__ rec0, const V4<T>* __restrict__ 
     const uint2 hi = *reinterpret_cast<const uint2*>(hacc + u);
     const T m = q == 0 ? md : (q == 1 ? mp[0] : (q == 2 ? mp[1] : mp[2]));   // selects: no local array
     const T a = q == 0 ? (T)-1 : (T)0;
-    v[it] = cmake<C>(acc_to_real<T>(split, lo.x, hi.x) * m + a, acc_to_real<T>(split, lo.y, hi.y) * m + a);
+    v[it] = cmake<C>(words_to_real<T>(lo.x, hi.x) * m + a, words_to_real<T>(lo.y, hi.y) * m + a);
     if (q == 0 && out.dens) {
       const int r = k / N, x = k % N;
       const long long cell = ((long long)((T0 << bg.lz) + (r >> bg.ly)) * N + ((T1 << bg.ly) + (r & ((1 << bg.ly) - 1)))) * N + x;
