@@ -380,11 +380,15 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     torch.cuda.synchronize()
     clocks.start()
+    if args.profile_range:
+        torch.cuda.profiler.start()   # profilers started with capture off see the timed region only
     ev0.record(stream)
     for _ in range(args.steps):
         evaluation(timed=True)
     ev1.record(stream)
     torch.cuda.synchronize()
+    if args.profile_range:
+        torch.cuda.profiler.stop()
     barrier()
     clk = clocks.stop()
     ctx.check()
@@ -817,6 +821,8 @@ def main():
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket the timed evaluations with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-ensemble and checkpoint-memory measurements of the main line")
     ap.add_argument("--batched", action="store_true", help="16-instance batched graph vs sequential runs")
