@@ -509,6 +509,8 @@ def run_op_case(args):
     N = npc ** 3
     om = torch.from_numpy(inputs.white_noise(npc, 1)).to("cuda")
     ctx = pm.PMContext(box, nm, npc, n, [THETA], om)
+    # the deposit and x pass as separate kernels, the form the autotuner picks at 1024^3
+    ctx.set_tuning({"fused_x": args.fused_x})
     disp = torch.empty(3 * N, device="cuda")
     ctx.forward(disp=disp)
     pi = torch.ones(3 * N, device="cuda") * 1e-3
@@ -832,6 +834,7 @@ def main():
     ap.add_argument("--oracle-full", action="store_true",
                     help="time the oracle's whole gradient on the host cores (1 process and one per core)")
     ap.add_argument("--oracle-steps", type=int, default=2, help="steps of the 128^3 case of --oracle-full")
+    ap.add_argument("--fused-x", type=int, default=0, help="--op-case: pm_tuning.fused_x (0: separate passes)")
     ap.add_argument("--op-case", action="store_true",
                     help="run one force and one force-VJP operator call (no timing), for profilers")
     args = ap.parse_args()

@@ -47,12 +47,25 @@ __host__ __device__ constexpr double cos32(int m) {
 }
 __host__ __device__ constexpr double sin32(int m) { return cos32(m - 8); }
 
-// v <- v * exp(DIR * 2 pi i k / R), R <= 32
+// v <- v * exp(DIR * 2 pi i k / R), R <= 32.  k is a compile-time index of the unrolled
+// butterflies, so the multiples of pi/4 resolve to their exact forms at compile time: a
+// swap and negation for +-i and -1 (a product with a zero cosine would stay in the code:
+// x * 0 is not folded under IEEE rules), two products for the diagonals.
 template <int R, int DIR, typename C>
 __device__ __forceinline__ C root_mul(C v, int k) {
   using T = decltype(v.x);
   static_assert(R <= 32, "roots of unity up to order 32");
-  const int m = k * (32 / R);
+  const int m = (k * (32 / R)) & 31;
+  if (m == 0) return v;
+  if (m == 16) return cmake<C>(-v.x, -v.y);
+  if (m == 8) return DIR > 0 ? cmake<C>(-v.y, v.x) : cmake<C>(v.y, -v.x);       // DIR i
+  if (m == 24) return DIR > 0 ? cmake<C>(v.y, -v.x) : cmake<C>(-v.y, v.x);      // -DIR i
+  if ((m & 3) == 0) {   // m = 4, 12, 20, 28: (+-1 +- i) / sqrt(2)
+    const T h = (T)0.70710678118654752440;
+    const T c = m == 4 || m == 28 ? (T)1 : (T)-1;
+    const T s = (T)(DIR * (m < 16 ? 1 : -1));
+    return cmake<C>((c * v.x - s * v.y) * h, (s * v.x + c * v.y) * h);
+  }
   const T c = (T)cos32(m), s = (T)(DIR * sin32(m));
   return cmake<C>(v.x * c - v.y * s, v.x * s + v.y * c);
 }
