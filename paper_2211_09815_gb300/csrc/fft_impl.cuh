@@ -121,6 +121,11 @@ k_fft_cols_yx(const SeqMap mm, const SeqMap ms, int ntiles_main, ColBufs<T> bufs
 // rows of n = 2L reals -> L complex (main) + 1 (side).  The row pairs (2j, 2j+1) are read
 // as one complex number and transformed as L-point sequences; the even/odd split below
 // recovers the real transform.  The buffers of one row tile are neighbouring blocks.
+//
+// Work items of the split (and of the untangling before the C2R below) are the pairs
+// (k, L - k), k < L/2, of every row, indexed row-major so that a power of two divides them,
+// and then the middle k = L/2 of every row; the address of each row of the tile is worked
+// out once, into shared memory.
 template <typename T, int L>
 __global__ void __launch_bounds__(RowTile<T, L>::NT)
 k_fft_x_r2c(RowJob<T> job, int nrows, int nbuf, const cx_t<T>* __restrict__ twL,
@@ -129,28 +134,33 @@ k_fft_x_r2c(RowJob<T> job, int nrows, int nbuf, const cx_t<T>* __restrict__ twL,
   using TL = RowTile<T, L>;
   constexpr int N = 2 * L;
   constexpr int RT = TL::TR;   // rows per tile
+  constexpr int KH = L / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ C* s_out[RT];     // main spectrum row of each tile row (null past nrows)
   C* sm = reinterpret_cast<C*>(smem_raw);
   const int qb = blockIdx.x % nbuf;
   const int r0 = (blockIdx.x / nbuf) * RT;
   const long long rows_per_inst = (long long)N * N;
-  // all rows of a tile belong to one instance (RT divides N^2)
+  // all rows of a tile belong to one instance (RT divides N^2) and are consecutive there
   const int inst0 = (int)(min((long long)r0, (long long)nrows - 1) / rows_per_inst);
+  const long long rr0 = r0 % rows_per_inst;
   const RowBuf<T> rb0 = pick(job.b, qb);
+  C* const spec0 = rb0.spec + inst0 * spec_len_cx(N);
+  for (int c = threadIdx.x; c < RT; c += TL::NT) {
+    const long long rr = rr0 + c;
+    s_out[c] = r0 + c < nrows ? spec0 + spec_row(N, job.lzb, (int)(rr / N), (int)(rr % N)) * L : nullptr;
+  }
   // load, transposing into [L][LD]; every load of the thread is issued before the first
-  // shared-memory store so that ITER loads per thread are in flight at once
+  // shared-memory store so that ITER loads per thread are in flight at once.  The tile's
+  // rows are one contiguous run of RT n reals.
   constexpr int ITER = RT * L / TL::NT;
   static_assert(ITER * TL::NT == RT * L, "row loads must divide evenly");
+  const C* tile_in = reinterpret_cast<const C*>(reinterpret_cast<const T*>(rb0.real) + inst0 * rb0.real_is + rr0 * N);
   C raw[ITER];
-  bool ok[ITER];
 #pragma unroll
   for (int it = 0; it < ITER; ++it) {
     const int idx = threadIdx.x + it * TL::NT;
-    const int row = idx / L, j = idx % L;
-    const int grow = r0 + row;
-    ok[it] = grow < nrows;
-    const long long off = inst0 * rb0.real_is + (long long)(ok[it] ? grow % rows_per_inst : 0) * N + 2 * j;
-    raw[it] = ok[it] ? *reinterpret_cast<const C*>(reinterpret_cast<const T*>(rb0.real) + off) : cmake<C>(0, 0);
+    raw[it] = r0 + idx / L < nrows ? tile_in[idx] : cmake<C>(0, 0);
   }
 #pragma unroll
   for (int it = 0; it < ITER; ++it) {
@@ -163,19 +173,16 @@ k_fft_x_r2c(RowJob<T> job, int nrows, int nbuf, const cx_t<T>* __restrict__ twL,
   fft_tile<T, L, TL::TR, TL::NT, -1, typename TL::P>(t, t, t, twL);
   __syncthreads();
   // even/odd split: X[k] = E[k] + W^k O[k], E = (Z[k] + conj Z[L-k]) / 2, O = -i (Z[k] - conj Z[L-k]) / 2
-  for (int idx = threadIdx.x; idx < TL::TR * (L / 2 + 1); idx += TL::NT) {
-    const int c = idx / (L / 2 + 1), k = idx % (L / 2 + 1);
-    const int row = c;
-    const int grow = r0 + row;
-    if (grow >= nrows) continue;
-    C* spec = rb0.spec;
-    const long long rr = grow % rows_per_inst;
-    C* out = spec + inst0 * spec_len_cx(N) + spec_row(N, job.lzb, (int)(rr / N), (int)(rr % N)) * L;
-    C* side = spec + inst0 * spec_len_cx(N) + spec_main_len(N) + rr;
+  constexpr int PAIRS = RT * KH;
+  for (int u = threadIdx.x; u < PAIRS + RT; u += TL::NT) {
+    const int c = u < PAIRS ? u / KH : u - PAIRS;
+    const int k = u < PAIRS ? u % KH : KH;
+    C* out = s_out[c];
+    if (!out) continue;
     const C zk = sm[srow(k) * TL::LD + c];
     if (k == 0) {
       out[0] = cmake<C>(zk.x + zk.y, (T)0);
-      *side = cmake<C>(zk.x - zk.y, (T)0);
+      spec0[spec_main_len(N) + rr0 + c] = cmake<C>(zk.x - zk.y, (T)0);
       continue;
     }
     const C zm = sm[srow(L - k) * TL::LD + c];
@@ -192,43 +199,61 @@ k_fft_x_r2c(RowJob<T> job, int nrows, int nbuf, const cx_t<T>* __restrict__ twL,
 
 // ---------------------------------------------------------------- x pass, C2R
 // L complex (main) + side -> n = 2L reals (unnormalised).  The output may alias the input.
+// Z[k] = E'[k] + i O'[k], E' = X[k] + conj X[L-k], O' = (X[k] - conj X[L-k]) conj(W^k), for
+// the pairs (k, L - k) of every row (work items as in the R2C split).
+template <typename T, int L, int TR, int NT>
+struct C2RUntangle {
+  static constexpr int KH = L / 2;
+  static constexpr int PAIRS = TR * KH;
+  static constexpr int ITEMS = PAIRS + TR;                    // + the middle k = L/2 of every row
+  static constexpr int ITER = (ITEMS + NT - 1) / NT;
+  __device__ __forceinline__ static int seq(int u) { return u < PAIRS ? u / KH : u - PAIRS; }
+  __device__ __forceinline__ static int freq(int u) { return u < PAIRS ? u % KH : KH; }
+};
+
 template <typename T, int L>
 __global__ void __launch_bounds__(RowTile<T, L>::NT)
 k_fft_x_c2r(RowJob<T> job, int nrows, const cx_t<T>* __restrict__ twL, const cx_t<T>* __restrict__ twN) {
   using C = cx_t<T>;
   using TL = RowTile<T, L>;
+  using U = C2RUntangle<T, L, TL::TR, TL::NT>;
   constexpr int N = 2 * L;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ const C* s_in[TL::TR];     // main spectrum row of each tile row (null past nrows)
   C* sm = reinterpret_cast<C*>(smem_raw);
   const RowBuf<T> rb = pick(job.b, blockIdx.y);
   const int r0 = blockIdx.x * TL::TR;
   const long long rows_per_inst = (long long)N * N;
-  // Z[k] = E'[k] + i O'[k], E' = X[k] + conj X[L-k], O' = (X[k] - conj X[L-k]) conj(W^k);
+  // all rows of a tile belong to one instance (TR divides N^2) and are consecutive there
+  const int inst0 = (int)(min((long long)r0, (long long)nrows - 1) / rows_per_inst);
+  const long long rr0 = r0 % rows_per_inst;
+  const C* const base = rb.spec + inst0 * spec_len_cx(N);
+  for (int c = threadIdx.x; c < TL::TR; c += TL::NT) {
+    const long long rr = rr0 + c;
+    s_in[c] = r0 + c < nrows ? base + spec_row(N, job.lzb, (int)(rr / N), (int)(rr % N)) * L : nullptr;
+  }
+  __syncthreads();
   // all loads of the thread are issued before the first use
-  constexpr int PAIRS = TL::TR * (L / 2 + 1);
-  constexpr int ITER = (PAIRS + TL::NT - 1) / TL::NT;
-  C xk[ITER], xm[ITER];
+  C xk[U::ITER], xm[U::ITER];
 #pragma unroll
-  for (int it = 0; it < ITER; ++it) {
-    const int idx = threadIdx.x + it * TL::NT;
-    const int row = idx / (L / 2 + 1), k = idx % (L / 2 + 1);
-    const int grow = r0 + row;
+  for (int it = 0; it < U::ITER; ++it) {
+    const int u = threadIdx.x + it * TL::NT;
     xk[it] = cmake<C>(0, 0);
     xm[it] = cmake<C>(0, 0);
-    if (idx < PAIRS && grow < nrows) {
-      const int inst = (int)(grow / rows_per_inst);
-      const C* base = rb.spec + inst * spec_len_cx(N);
-      const long long rr = grow % rows_per_inst;
-      const C* in = base + spec_row(N, job.lzb, (int)(rr / N), (int)(rr % N)) * L;
-      xk[it] = in[k];
-      xm[it] = k == 0 ? base[spec_main_len(N) + rr] : in[L - k];
+    if (u < U::ITEMS) {
+      const int c = U::seq(u), k = U::freq(u);
+      const C* in = s_in[c];
+      if (in) {
+        xk[it] = in[k];
+        xm[it] = k == 0 ? base[spec_main_len(N) + rr0 + c] : in[L - k];
+      }
     }
   }
 #pragma unroll
-  for (int it = 0; it < ITER; ++it) {
-    const int idx = threadIdx.x + it * TL::NT;
-    if (idx >= PAIRS) continue;
-    const int row = idx / (L / 2 + 1), k = idx % (L / 2 + 1);
+  for (int it = 0; it < U::ITER; ++it) {
+    const int u = threadIdx.x + it * TL::NT;
+    if (u >= U::ITEMS) continue;
+    const int row = U::seq(u), k = U::freq(u);
     C zk, zm = cmake<C>(0, 0);
     if (k == 0) {
       const T x0 = xk[it].x, xl = xm[it].x;
@@ -247,13 +272,12 @@ k_fft_x_c2r(RowJob<T> job, int nrows, const cx_t<T>* __restrict__ twL, const cx_
   SmemTile<C, TL::LD> t{sm};
   fft_tile<T, L, TL::TR, TL::NT, +1, typename TL::P>(t, t, t, twL);
   __syncthreads();
+  // the tile's rows are one contiguous run of TR n reals
+  C* tile_out = reinterpret_cast<C*>(reinterpret_cast<T*>(rb.real) + inst0 * rb.real_is + rr0 * N);
   for (int idx = threadIdx.x; idx < TL::TR * L; idx += TL::NT) {
     const int row = idx / L, j = idx % L;
-    const int grow = r0 + row;
-    if (grow >= nrows) continue;
-    const int inst = (int)(grow / rows_per_inst);
-    T* out = reinterpret_cast<T*>(rb.real) + inst * rb.real_is + (grow % rows_per_inst) * N + 2 * j;
-    *reinterpret_cast<C*>(out) = sm[srow(j) * TL::LD + row];
+    if (r0 + row >= nrows) continue;
+    tile_out[idx] = sm[srow(j) * TL::LD + row];
   }
 }
 
@@ -278,36 +302,49 @@ k_fft_x_c2r4(RowJob<T> job, int nrows, int dq, V4<T>* __restrict__ out4, const c
              const cx_t<T>* __restrict__ twN) {
   using C = cx_t<T>;
   using TL = C2R4Tile<T, L, Q>;
+  using U = C2RUntangle<T, L, TL::TR, TL::NT>;
   constexpr int N = 2 * L;
   constexpr int RT = TL::RT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ const C* s_in[TL::TR];     // main spectrum row of sequence c = (component, row)
+  __shared__ const C* s_side[TL::TR];   // its side-plane element (kx = L)
   C* sm = reinterpret_cast<C*>(smem_raw);
   const int r0 = blockIdx.x * RT;
   const long long rows_per_inst = (long long)N * N;
-  constexpr int PAIRS = TL::TR * (L / 2 + 1);
-  constexpr int ITER = (PAIRS + TL::NT - 1) / TL::NT;
-  C xk[ITER], xm[ITER];
-#pragma unroll
-  for (int it = 0; it < ITER; ++it) {
-    const int idx = threadIdx.x + it * TL::NT;
-    const int c = idx / (L / 2 + 1), k = idx % (L / 2 + 1);
-    const int q = c / RT, row = c % RT;
-    const int grow = r0 + row;
-    xk[it] = cmake<C>(0, 0);
-    xm[it] = cmake<C>(0, 0);
-    if (idx < PAIRS && grow < nrows) {
+  for (int c = threadIdx.x; c < TL::TR; c += TL::NT) {
+    const int q = c / RT, grow = r0 + c % RT;
+    const C* in = nullptr;
+    const C* side = nullptr;
+    if (grow < nrows) {
       const C* base = pick(job.b, q).spec + (grow / rows_per_inst) * spec_len_cx(N);
       const long long rr = grow % rows_per_inst;
-      const C* in = base + spec_row(N, job.lzb, (int)(rr / N), (int)(rr % N)) * L;
-      xk[it] = in[k];
-      xm[it] = k == 0 ? base[spec_main_len(N) + rr] : in[L - k];
+      in = base + spec_row(N, job.lzb, (int)(rr / N), (int)(rr % N)) * L;
+      side = base + spec_main_len(N) + rr;
+    }
+    s_in[c] = in;
+    s_side[c] = side;
+  }
+  __syncthreads();
+  C xk[U::ITER], xm[U::ITER];
+#pragma unroll
+  for (int it = 0; it < U::ITER; ++it) {
+    const int u = threadIdx.x + it * TL::NT;
+    xk[it] = cmake<C>(0, 0);
+    xm[it] = cmake<C>(0, 0);
+    if (u < U::ITEMS) {
+      const int c = U::seq(u), k = U::freq(u);
+      const C* in = s_in[c];
+      if (in) {
+        xk[it] = in[k];
+        xm[it] = k == 0 ? *s_side[c] : in[L - k];
+      }
     }
   }
 #pragma unroll
-  for (int it = 0; it < ITER; ++it) {
-    const int idx = threadIdx.x + it * TL::NT;
-    if (idx >= PAIRS) continue;
-    const int c = idx / (L / 2 + 1), k = idx % (L / 2 + 1);
+  for (int it = 0; it < U::ITER; ++it) {
+    const int u = threadIdx.x + it * TL::NT;
+    if (u >= U::ITEMS) continue;
+    const int c = U::seq(u), k = U::freq(u);
     if (c / RT == dq) {
       // component dq is the x derivative -i k_x of its spectrum (Nyquist kx = L: 0)
       const T sk = (T)k, sl = k == 0 ? (T)0 : (T)(L - k);
@@ -332,14 +369,14 @@ k_fft_x_c2r4(RowJob<T> job, int nrows, int dq, V4<T>* __restrict__ out4, const c
   SmemTile<C, TL::LD> t{sm};
   fft_tile<T, L, TL::TR, TL::NT, +1, typename TL::P>(t, t, t, twL);
   __syncthreads();
+  V4<T>* const tile_out = out4 + (long long)r0 * N;
   for (int idx = threadIdx.x; idx < RT * L; idx += TL::NT) {
     const int row = idx / L, j = idx % L;
-    const int grow = r0 + row;
-    if (grow >= nrows) continue;
+    if (r0 + row >= nrows) continue;
     const C v0 = sm[srow(j) * TL::LD + row], v1 = sm[srow(j) * TL::LD + RT + row];
     const C v2 = sm[srow(j) * TL::LD + 2 * RT + row];
     const C v3 = Q == 4 ? sm[srow(j) * TL::LD + (Q - 1) * RT + row] : cmake<C>(0, 0);
-    V4<T>* o = out4 + (long long)grow * N + 2 * j;
+    V4<T>* o = tile_out + 2 * idx;
     o[0] = V4<T>{v0.x, v1.x, v2.x, v3.x};
     o[1] = V4<T>{v0.y, v1.y, v2.y, v3.y};
   }

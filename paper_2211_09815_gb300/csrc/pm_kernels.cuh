@@ -234,19 +234,14 @@ template <> inline int fixed_top<float>(int lgN) { return 61 - lgN < 30 ? 61 - l
 template <> inline int fixed_top<double>(int lgN) { return 61 - lgN; }
 
 // A fixed-point contribution as the two 32-bit words of an int64, correctly rounded
-// (nearest-even).  FP32 (|v| <= 2^30): below 2^23 the rounding is that of one FP32
-// addition of 2^23 (whose result's ulp is 1), above it v is an integer and its significand
-// is shifted into place.
+// (nearest-even).  FP32 contributions are at most 2^30 in magnitude (fixed_top), so one
+// hardware conversion to int32 rounds them (ties to even, symmetric in the sign) and the
+// high word is the sign extension.
 template <typename T> __device__ __forceinline__ void fixed_words(T v, unsigned& lo, unsigned& hi);
 template <> __device__ __forceinline__ void fixed_words<float>(float v, unsigned& lo, unsigned& hi) {
-  const float a = fabsf(v);
-  const unsigned ua = __float_as_uint(a);
-  const unsigned small = __float_as_uint(__fadd_rn(a, 8388608.0f)) - 0x4B000000u;
-  const unsigned big = ((ua & 0x7FFFFFu) | 0x800000u) << (((ua >> 23) - 150u) & 31u);
-  const unsigned r = a < 8388608.0f ? small : big;
-  const bool neg = v < 0.0f;
-  lo = neg ? 0u - r : r;
-  hi = (neg && r != 0u) ? 0xFFFFFFFFu : 0u;
+  const int r = __float2int_rn(v);
+  lo = (unsigned)r;
+  hi = (unsigned)(r >> 31);
 }
 template <> __device__ __forceinline__ void fixed_words<double>(double v, unsigned& lo, unsigned& hi) {
   const unsigned long long r = (unsigned long long)__double2ll_rn(v);
