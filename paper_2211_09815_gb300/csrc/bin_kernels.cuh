@@ -238,28 +238,31 @@ __device__ __forceinline__ void pull_accumulate(const BinGeo& bg, const V4<T>* _
                                                 unsigned* rpre) {
   const int T2 = tile & (bg.ntx - 1), T1 = (tile / bg.ntx) & (bg.nty - 1), T0 = tile / (bg.ntx * bg.nty);
   const int cells = 1 << (bg.lx + bg.ly + bg.lz);
+  // the first warp reads the range bounds (one lane per range) before the accumulator is
+  // cleared, so that their latency overlaps the clearing
+  const int ri = threadIdx.x;
+  unsigned ra = 0, re = 0;
+  if (ri < 20) {
+    const int d = (int)((kRangeD >> (3 * ri)) & 7u), c0 = (int)((kRangeC >> (3 * ri)) & 7u);
+    const int S2 = (T2 - (d & 1)) & (bg.ntx - 1);
+    const int S1 = (T1 - ((d >> 1) & 1)) & (bg.nty - 1);
+    const int S0 = (T0 - ((d >> 2) & 1)) & (bg.ntz - 1);
+    const long long key0 = (long long)b * bg.nkeys + ((long long)(S0 * bg.nty + S1) * bg.ntx + S2) * 8 + c0;
+    ra = start[key0];
+    re = start[key0 + (d == 0 ? 8 : 1)];
+  }
   for (int k = threadIdx.x; k < NQ * cells / 2; k += blockDim.x) reinterpret_cast<uint4*>(acc)[k] = make_uint4(0, 0, 0, 0);
   unsigned* hacc = acc + NQ * cells;
   if (threadIdx.x < 32) {
-    const int r = threadIdx.x;   // one lane per range
-    unsigned len = 0;
-    if (r < 20) {
-      const int d = (int)((kRangeD >> (3 * r)) & 7u), c0 = (int)((kRangeC >> (3 * r)) & 7u);
-      const int S2 = (T2 - (d & 1)) & (bg.ntx - 1);
-      const int S1 = (T1 - ((d >> 1) & 1)) & (bg.nty - 1);
-      const int S0 = (T0 - ((d >> 2) & 1)) & (bg.ntz - 1);
-      const long long key0 = (long long)b * bg.nkeys + ((long long)(S0 * bg.nty + S1) * bg.ntx + S2) * 8 + c0;
-      const unsigned a = start[key0], e = start[key0 + (d == 0 ? 8 : 1)];
-      rbeg[r] = a;
-      len = e - a;
-    }
+    const unsigned len = re - ra;
+    if (ri < 20) rbeg[ri] = ra;
     unsigned x = len;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-      if (r >= o) x += y;
+      if (ri >= o) x += y;
     }
-    if (r < 21) rpre[r] = x - len;   // exclusive prefix; rpre[20] = total
+    if (ri < 21) rpre[ri] = x - len;   // exclusive prefix; rpre[20] = total
   }
   __syncthreads();
   const T sd = pow2i<T>(e_d);

@@ -144,7 +144,19 @@ class Engine : public EngineBase {
     geo_.M = M_;
     lgN_ = ilog2(N_);
     e_d_ = fixed_top<T>(lgN_);
-    G_ = (int)std::min<long long>((N_ + kPtclThreads - 1) / kPtclThreads, kMaxRedBlocks);
+    {
+      int dev = 0;
+      PMGB_CK(cudaGetDevice(&dev));
+      PMGB_CK(cudaDeviceGetAttribute(&nsm_, cudaDevAttrMultiProcessorCount, dev));
+    }
+    // particle loops: whole waves of resident blocks (grid-stride loops, every thread the
+    // same share), so that no partial last wave leaves SMs idle; G_ is also the number of
+    // per-block partial sums of the reductions
+    G_ = wave_grid((const void*)k_gather_adj<T>, N_);
+    Gf_ = wave_grid((const void*)k_gather_fwd<T>, N_);
+    Gc_ = wave_grid((const void*)k_bin_count<T>, N_);
+    Gb1_ = wave_grid((const void*)k_bin_fill<T, 1>, N_);
+    Gb4_ = wave_grid((const void*)k_bin_fill<T, 4>, N_);
     Gm_ = (int)std::min<long long>((M_ + kPtclThreads - 1) / kPtclThreads, kMaxRedBlocks);
     Gz_ = (int)std::min<long long>((spec_len_cx(np_) + kPtclThreads - 1) / kPtclThreads, kMaxRedBlocks);
     const long long pv = (long long)B_ * 3 * N_;
@@ -181,10 +193,7 @@ class Engine : public EngineBase {
       PMGB_RET(alloc(&ck_s_, pv * nck_));
       PMGB_RET(alloc(&ck_p_, pv * nck_));
     }
-    // TMA-staged column passes for the mesh-size spectra
-    int dev = 0;
-    PMGB_CK(cudaGetDevice(&dev));
-    PMGB_CK(cudaDeviceGetAttribute(&nsm_, cudaDevAttrMultiProcessorCount, dev));
+    // TMA-staged column passes for the mesh-size spectra (nsm_: set above)
     // TMA-staged column passes for the mesh sizes that have them (PMGB_TMA=0 starts with
     // the unstaged form; pm_set_tuning and pm_autotune switch between the two)
     const char* env = getenv("PMGB_TMA");
@@ -226,7 +235,7 @@ class Engine : public EngineBase {
       T* snap_p = (q >= 0 && snap_mom_) ? snap_mom_ + (long long)q * B_ * 3 * N_ : nullptr;
       prof_.begin(st_, P_GATHER_FWD, 1);
       // the bins of the next step's deposit are counted at the new positions
-      k_gather_fwd<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, s_, p_, j == n_ ? a_ : nullptr, fvec_, sc, j,
+      k_gather_fwd<T><<<dim3(Gf_, B_), kPtclThreads, 0, st_>>>(geo_, s_, p_, j == n_ ? a_ : nullptr, fvec_, sc, j,
                                                               n_ + 1, cks, ckp, fused1_ ? bgf1_ : bg1_,
                                                               j < n_ ? bcount_ : nullptr, bkeys_, snap_p, fx_);
       counted_ = j < n_;
@@ -402,7 +411,7 @@ class Engine : public EngineBase {
     StepCoef<T> sc{zero_, zero_, zero_};
     if (!pi) {
       PMGB_RET(force_chain(s_, nullptr, false));
-      k_gather_fwd<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, s_, p_, (T*)acc, fvec_, sc, 0, 1, nullptr,
+      k_gather_fwd<T><<<dim3(Gf_, B_), kPtclThreads, 0, st_>>>(geo_, s_, p_, (T*)acc, fvec_, sc, 0, 1, nullptr,
                                                               nullptr, bg1_, nullptr, nullptr);
     } else {
       PMGB_CK(cudaMemcpyAsync(pi_, pi, sizeof(T) * B_ * 3 * N_, cudaMemcpyDeviceToDevice, st_));
@@ -1163,15 +1172,15 @@ class Engine : public EngineBase {
               const FusedOut<T>* fo = nullptr, const SepTargets* tg = nullptr) {
     const long long nbin = (long long)B_ * bg.nkeys + 1;
     const int nscan = (int)((nbin + kScanBlock - 1) / kScanBlock);
-    if (!precounted) k_bin_count<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, bg, s, bcount_, bkeys_);
+    if (!precounted) k_bin_count<T><<<dim3(Gc_, B_), kPtclThreads, 0, st_>>>(geo_, bg, s, bcount_, bkeys_);
     k_scan_blocks<<<nscan, 256, 0, st_>>>(bcount_, bstart_, bsums_, nbin);
     k_scan_sums<<<1, 256, 0, st_>>>(bsums_, nscan);
     k_scan_add<<<(int)std::min<long long>((nbin + 255) / 256, 4096), 256, 0, st_>>>(bstart_, bcursor_, bsums_, nbin);
     if (pi)
-      k_bin_fill<T, 4><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, bg, s, pi, e_pi_, bkeys_, bcursor_, brec0_,
+      k_bin_fill<T, 4><<<dim3(Gb4_, B_), kPtclThreads, 0, st_>>>(geo_, bg, s, pi, e_pi_, bkeys_, bcursor_, brec0_,
                                                                brec1_);
     else
-      k_bin_fill<T, 1><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, bg, s, nullptr, nullptr, bkeys_, bcursor_,
+      k_bin_fill<T, 1><<<dim3(Gb1_, B_), kPtclThreads, 0, st_>>>(geo_, bg, s, nullptr, nullptr, bkeys_, bcursor_,
                                                                brec0_, nullptr);
     if (fo) {
       if (pi)
@@ -1482,6 +1491,21 @@ class Engine : public EngineBase {
   pm_config cfg_{};
   cudaStream_t st_ = 0;
   int B_ = 1, np_ = 0, nm_ = 0, n_ = 0, lgN_ = 0, e_d_ = 0, G_ = 1, Gm_ = 1, Gz_ = 1, nck_ = 0, maxn2_ = 0;
+  int Gf_ = 1, Gc_ = 1, Gb1_ = 1, Gb4_ = 1;   // grids of the particle loops
+
+  // Grid of a particle loop over `work` items: at most kMaxRedBlocks blocks, rounded down
+  // to whole waves of the blocks the kernel keeps resident on all SMs.
+  int wave_grid(const void* fn, long long work) const {
+    const long long need = (work + kPtclThreads - 1) / kPtclThreads;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kPtclThreads, 0) != cudaSuccess || occ < 1) {
+      (void)cudaGetLastError();
+      occ = 1;
+    }
+    const long long wave = (long long)occ * nsm_;
+    const long long cap = wave >= kMaxRedBlocks ? kMaxRedBlocks : (kMaxRedBlocks / wave) * wave;
+    return (int)std::max<long long>(1, std::min(need, cap));
+  }
   long long N_ = 0, M_ = 0, bytes_ = 0;
   T mass_ = 1, inv_kfp_ = 1;
   Geo<T> geo_{};
@@ -1537,7 +1561,7 @@ class Engine : public EngineBase {
   T fix_to_u_ = 0;
   Prof prof_;
   bool use_tma_ = false;
-  int nsm_ = 1;
+  int nsm_ = 1;   // SM count
   int* dev_err_ = nullptr;
   int first_wait_ = -1;   // spin limit of the TMA passes' first wait (test hook)
   CUtensorMap tmy_[7], tmz_[7];

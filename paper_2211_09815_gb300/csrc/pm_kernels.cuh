@@ -318,10 +318,19 @@ k_gather_fwd(Geo<T> g, T* __restrict__ s, T* __restrict__ p, T* __restrict__ a_o
   T* sb = s + (long long)b * 3 * g.N;
   T* pb = p + (long long)b * 3 * g.N;
   const V4<T>* F = fvec + (long long)b * g.M;
-  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < g.N;
-       w += (long long)gridDim.x * blockDim.x) {
+  // the displacement of the thread's next particle is read one iteration ahead, so that
+  // its latency overlaps this particle's corner loads (each particle has one thread: the
+  // value is not written before it is used)
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  T sn[3] = {0, 0, 0};
+  if (w < g.N) {
+    const long long i0 = particle_of(g, w);
+    sn[0] = sb[i0], sn[1] = sb[g.N + i0], sn[2] = sb[2 * g.N + i0];
+  }
+  for (; w < g.N; w += stride) {
     const long long i = particle_of(g, w);
-    T sv[3] = {sb[i], sb[g.N + i], sb[2 * g.N + i]};
+    T sv[3] = {sn[0], sn[1], sn[2]};
     T pv[3] = {pb[i], pb[g.N + i], pb[2 * g.N + i]};   // in flight with the corner loads
     int cell[3];
     T t[3];
@@ -329,6 +338,10 @@ k_gather_fwd(Geo<T> g, T* __restrict__ s, T* __restrict__ p, T* __restrict__ a_o
     V4<T> fv[8];
 #pragma unroll
     for (int d = 0; d < 8; ++d) fv[d] = F[corner_index(g, cell, d)];
+    if (w + stride < g.N) {
+      const long long in = particle_of(g, w + stride);
+      sn[0] = sb[in], sn[1] = sb[g.N + in], sn[2] = sb[2 * g.N + in];
+    }
     T a[3] = {0, 0, 0};
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
