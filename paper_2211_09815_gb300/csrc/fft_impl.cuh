@@ -619,7 +619,7 @@ template <typename T, int L> static int tiles_of() { return L * ((L / 2) / TmaTi
 template <typename T, int L, int DIR, int KIND>
 static void launch_tma_L(const CUtensorMap* maps, const CUtensorMap* omaps, const TmaJob<T>& job, int tiles,
                          const cx_t<T>* tw, int nsm, cudaStream_t st) {
-  using TT = TmaTile<T, L>;
+  using TT = TmaTile<T, L, typename TmaPlanOf<T, L, KIND>::type>;
   TmaMaps m{}, om{};
   const int nomaps = (KIND == 1 || KIND == 3) ? 2 : ((KIND == 2 || KIND == 4) ? 1 : 0);
   for (int i = 0; i < nomaps; ++i) om.m[i] = omaps[i];

@@ -18,6 +18,8 @@
 // Every mbarrier wait is bounded: on timeout the CTA records an error flag, waits (again
 // bounded) for its own copies in flight, and returns.
 #pragma once
+#include <type_traits>
+
 #include <cuda.h>
 
 #include "fft.cuh"
@@ -122,10 +124,23 @@ struct DenseTile {
 // Tiles of the staged passes: 64 KB of TC columns (at least 128-byte rows of a TMA box for
 // L >= 512), transformed with the two-stage radix-32 plans at L = 512 and 1024, where a
 // third stage would add a read and a write of the whole tile in shared memory.
-template <typename T, int L> struct TmaTile {
-  using P = Plan2<L>;
-  using CT = ColTile<T, L>;
-  static constexpr int TC = L >= 512 ? 65536 / (L * (int)sizeof(cx_t<T>)) : CT::TC;
+template <typename T, int L> constexpr int tma_tc() {
+  return L >= 512 ? 65536 / (L * (int)sizeof(cx_t<T>)) : ColTile<T, L>::TC;
+}
+// Radix plan of a TMA column pass: the two-stage radix-32 plans, except for the fused
+// adjoint z pass (KIND 2), which takes the three-stage radix-16 plan where its thread count
+// (one radix-16 butterfly per thread) fits in a block: twice the warps per SM for a pass
+// of three transforms per tile bound by instruction latency, not by HBM (measured 9%
+// faster at 1024^3).  The fused z force keeps radix 32: its register hand-off saves a
+// shared-memory round trip and a Green's function per element (radix 16 without it was
+// 21% slower), and the y split and merge (KIND 3, 4) were 5% slower with radix 16.
+template <typename T, int L, int KIND> struct TmaPlanOf {
+  static constexpr bool kR16 = KIND == 2 && tma_tc<T, L>() * L / Plan<L>::RMAX <= 512;
+  using type = std::conditional_t<kR16, Plan<L>, Plan2<L>>;
+};
+template <typename T, int L, class PL = Plan2<L>> struct TmaTile {
+  using P = PL;
+  static constexpr int TC = tma_tc<T, L>();
   static constexpr int NT = TC * L / P::RMAX;
   static constexpr int LD = TC;
   static_assert(NT <= 512 && (L / 2) % TC == 0, "TMA tile shape");
@@ -229,11 +244,11 @@ struct YMergeDst {  // in place in the accumulator tile
 };
 
 template <typename T, int L, int DIR, int KIND>
-__global__ void __launch_bounds__(TmaTile<T, L>::NT, 1)
+__global__ void __launch_bounds__(TmaTile<T, L, typename TmaPlanOf<T, L, KIND>::type>::NT, 1)
 k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps omaps,
            const __grid_constant__ TmaJob<T> job, int tiles_per_buf, const cx_t<T>* __restrict__ tw) {
   using C = cx_t<T>;
-  using TT = TmaTile<T, L>;
+  using TT = TmaTile<T, L, typename TmaPlanOf<T, L, KIND>::type>;
   constexpr int N = L;
   constexpr int NCG = (N / 2) / TT::TC;            // column groups per row of the main array
   constexpr int NL = (KIND == 2 || KIND == 4) ? 2 : 1;   // loads per work item
