@@ -94,6 +94,12 @@ class Engine : public EngineBase {
 
   ~Engine() override {
     if (st_) cudaStreamSynchronize(st_);
+    if (cp_st_) {
+      cudaStreamSynchronize(cp_st_);
+      cudaStreamDestroy(cp_st_);
+    }
+    if (cp_in_) cudaEventDestroy(cp_in_);
+    if (cp_done_) cudaEventDestroy(cp_done_);
     if (graph_exec_) cudaGraphExecDestroy(graph_exec_);
     for (void* p : allocs_) cudaFree(p);
     live_bytes_add(-bytes_);
@@ -460,9 +466,22 @@ class Engine : public EngineBase {
     if (!tgt_) PMGB_RET(alloc(&tgt_, (long long)B_ * M_));
     if (!djdd_) PMGB_RET(alloc(&djdd_, (long long)B_ * M_));
     if (!gw_) PMGB_RET(alloc(&gw_, (long long)B_ * N_));
+    // The target is first read by the loss, after the whole forward run: its upload goes
+    // on a copy stream of its own, ordered after the work already queued (the previous
+    // call's loss reads tgt_) and waited for before the loss, so that it overlaps the
+    // forward run.
+    if (!cp_st_) {
+      PMGB_CK(cudaStreamCreateWithFlags(&cp_st_, cudaStreamNonBlocking));
+      PMGB_CK(cudaEventCreateWithFlags(&cp_in_, cudaEventDisableTiming));
+      PMGB_CK(cudaEventCreateWithFlags(&cp_done_, cudaEventDisableTiming));
+    }
+    PMGB_CK(cudaEventRecord(cp_in_, st_));
+    PMGB_CK(cudaStreamWaitEvent(cp_st_, cp_in_, 0));
+    PMGB_CK(cudaMemcpyAsync(tgt_, target, sizeof(T) * B_ * M_, cudaMemcpyDefault, cp_st_));
+    PMGB_CK(cudaEventRecord(cp_done_, cp_st_));
     if (omega) PMGB_CK(cudaMemcpyAsync(omega_, omega, sizeof(T) * B_ * N_, cudaMemcpyDefault, st_));
-    PMGB_CK(cudaMemcpyAsync(tgt_, target, sizeof(T) * B_ * M_, cudaMemcpyDefault, st_));
     PMGB_RET(forward(nullptr, nullptr, nullptr));
+    PMGB_CK(cudaStreamWaitEvent(st_, cp_done_, 0));
     PMGB_RET(loss_mse_dev(tgt_, djdd_));
     PMGB_RET(adjoint(djdd_, nullptr, nullptr, gw_, nullptr));
     if (loss) {
@@ -1562,6 +1581,8 @@ class Engine : public EngineBase {
   Prof prof_;
   bool use_tma_ = false;
   int nsm_ = 1;   // SM count
+  cudaStream_t cp_st_ = nullptr;                       // copy stream of pm_gradient's target
+  cudaEvent_t cp_in_ = nullptr, cp_done_ = nullptr;     // its order after st_, its completion
   int* dev_err_ = nullptr;
   int first_wait_ = -1;   // spin limit of the TMA passes' first wait (test hook)
   CUtensorMap tmy_[7], tmz_[7];
