@@ -485,6 +485,8 @@ def run_ours(args, rank, world, local_rank):
         out["batched_ensemble"] = batched_ensemble(1, 2)
         torch.cuda.empty_cache()
         out["checkpoint_memory"] = ckpt_compare()
+        torch.cuda.empty_cache()
+        out["smaller_workloads"] = {w: workload_rate(w) for w in ("small", "medium")}
     if not args.no_cpu_baseline:
         procs = host_cores()
         wall, per = oracle_pool_round(procs)
@@ -577,6 +579,53 @@ def run_fft_compare(args):
                       "io_GB_per_transform": gb,
                       "ours_note": "x, y, z passes + layout conversion to [n][n][n/2+1]",
                       "max_rel_diff_vs_cufft": err}))
+
+
+def workload_rate(name, warmup=3, steps=3):
+    """Gradient steps/s of another single-instance configuration of the workload set, timed
+    like the main line: autotuned on the final forward state, CUDA events on the launching
+    stream around `steps` evaluations after `warmup`, the error flag checked after."""
+    import torch
+    from paper_2211_09815_gb300 import inputs, pm
+    box, nm, npc, n = WORKLOADS[name]
+    N, M = npc ** 3, nm ** 3
+    om2 = torch.from_numpy(inputs.white_noise(npc, 2)).to("cuda")
+    c = pm.PMContext(box, nm, npc, n, [THETA], om2)
+    target = torch.empty(M, device="cuda")
+    c.forward(dens=target)
+    c.close()
+    om = torch.from_numpy(inputs.white_noise(npc, 1)).to("cuda")
+    ctx = pm.PMContext(box, nm, npc, n, [THETA], om, check_errors=False)
+    ctx.forward()
+    ctx.autotune()
+    djdd = torch.empty(M, device="cuda")
+    gw = torch.empty(N, device="cuda")
+    gt = torch.zeros(5, dtype=torch.float64, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+    def evaluation():
+        ctx.forward()
+        ctx.loss_mse(target, djdd, loss)
+        ctx.adjoint(djdd=djdd, grad_omega=gw, grad_theta=gt)
+
+    for _ in range(warmup):
+        evaluation()
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        evaluation()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    ctx.close()
+    ms = e0.elapsed_time(e1) / steps
+    peak, kind = _peaks()
+    frac = compulsory_bytes_per_pm_step(N, M) * n / (ms * 1e-3) / 1e9 / peak
+    return {"workload": f"{npc}^3 particles, {nm}^3 mesh, {box:g} Mpc/h, {n} steps", "steps_per_s": n / (ms * 1e-3),
+            "ms_per_eval": ms, "timed_evals": steps, "warmup": warmup,
+            "roofline_frac_compulsory": frac, "peak_kind": kind}
 
 
 def run_batched(args):
@@ -826,7 +875,7 @@ def main():
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed evaluations with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the batched-ensemble and checkpoint-memory measurements of the main line")
+                    help="skip the batched-ensemble, checkpoint-memory and smaller-workload measurements of the main line")
     ap.add_argument("--batched", action="store_true", help="16-instance batched graph vs sequential runs")
     ap.add_argument("--fft-compare", action="store_true", help="hand-written 3-D FFT beside cuFFT (torch.fft)")
     ap.add_argument("--compare-ckpt", action="store_true", help="reverse time vs checkpoints: memory/time")
