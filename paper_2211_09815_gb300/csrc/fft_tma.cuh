@@ -132,8 +132,9 @@ template <typename T, int L> constexpr int tma_tc() {
 // (one radix-16 butterfly per thread) fits in a block: twice the warps per SM for a pass
 // of three transforms per tile bound by instruction latency, not by HBM (measured 9%
 // faster at 1024^3).  The fused z force keeps radix 32: its register hand-off saves a
-// shared-memory round trip and a Green's function per element (radix 16 without it was
-// 21% slower), and the y split and merge (KIND 3, 4) were 5% slower with radix 16.
+// shared-memory round trip and a Green's function per element (radix 16 was 21% slower
+// without the hand-off and 11% slower with it, forward 16-8-8 into inverse 8-8-16), and
+// the y split and merge (KIND 3, 4) were 5% slower with radix 16.
 template <typename T, int L, int KIND> struct TmaPlanOf {
   static constexpr bool kR16 = KIND == 2 && tma_tc<T, L>() * L / Plan<L>::RMAX <= 512;
   using type = std::conditional_t<kR16, Plan<L>, Plan2<L>>;
@@ -363,19 +364,14 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
       zc.dtab = job.dtab;
       zc.d12 = job.dtab ? job.dtab[zc.f1 < 0 ? zc.f1 + N : zc.f1] * job.dtab[zc.f2] : (T)1;
       DenseTile<C, TT::LD> wt{work};
-      if constexpr (KIND == 1 && (TT::P::S == 2 || TT::P::S == 3)) {
-        // the forward transform's last stage (radix RB) leaves the spectrum in registers,
-        // item j holding rows j + RA r (r < RB, RA = L / RB) -- exactly the inputs of the
-        // first stage of an inverse transform with the radices in reverse order -- so both
-        // inverse transforms start from registers instead of a shared-memory round trip
-        constexpr int S = TT::P::S, TC = TT::TC, NT = TT::NT;
-        constexpr int RB = S == 2 ? TT::P::R1 : TT::P::R2, RA = L / RB;
+      if constexpr (KIND == 1 && TT::P::S == 2) {
+        // two-stage plan (RA, RB): the forward transform's last stage leaves the spectrum
+        // in registers, item j holding rows j + RA r (r < RB) -- exactly the inputs of the
+        // first stage of an inverse transform planned as (RB, RA) -- so both inverse
+        // transforms start from registers instead of a shared-memory round trip
+        constexpr int RA = TT::P::R0, RB = TT::P::R1, TC = TT::TC, NT = TT::NT;
         constexpr int PER = TC * (L / RB) / NT;
-        stage<T, L, TC, NT, TT::P::R0, 1, -1>(t, t, stw);
-        if constexpr (S == 3) {
-          __syncthreads();
-          stage<T, L, TC, NT, TT::P::R1, TT::P::R0, -1>(t, t, stw);
-        }
+        stage<T, L, TC, NT, RA, 1, -1>(t, t, stw);
         __syncthreads();
         C x[PER][RB];
         T gz[PER][RB];
@@ -425,24 +421,11 @@ k_cols_tma(const __grid_constant__ TmaMaps maps, const __grid_constant__ TmaMaps
           }
         }
         __syncthreads();
-        // the remaining inverse stages (radices in reverse order) of the z force, then of U
-        if constexpr (S == 2) {
-          stage<T, L, TC, NT, RA, RB, +1>(wt, wt, stw);
-        } else {
-          stage<T, L, TC, NT, TT::P::R1, RB, +1>(wt, wt, stw);
-          __syncthreads();
-          stage<T, L, TC, NT, TT::P::R0, RB * TT::P::R1, +1>(wt, wt, stw);
-        }
+        stage<T, L, TC, NT, RA, RB, +1>(wt, wt, stw);        // inverse stage 2 of the z force
         fence_proxy_async();
         __syncthreads();
         if (threadIdx.x == 0) store(&omaps.m[0], work, kxg, o, b);
-        if constexpr (S == 2) {
-          stage<T, L, TC, NT, RA, RB, +1>(t, t, stw);
-        } else {
-          stage<T, L, TC, NT, TT::P::R1, RB, +1>(t, t, stw);
-          __syncthreads();
-          stage<T, L, TC, NT, TT::P::R0, RB * TT::P::R1, +1>(t, t, stw);
-        }
+        stage<T, L, TC, NT, RA, RB, +1>(t, t, stw);          // and of U
         fence_proxy_async();
         __syncthreads();
         if (threadIdx.x == 0) store(&omaps.m[1], cur, kxg, o, b);
