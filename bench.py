@@ -487,6 +487,12 @@ def run_ours(args, rank, world, local_rank):
         out["checkpoint_memory"] = ckpt_compare()
         torch.cuda.empty_cache()
         out["smaller_workloads"] = {w: workload_rate(w) for w in ("small", "medium")}
+        torch.cuda.empty_cache()
+        # the reduced-precision form on the main workload (accuracy: --precision-study)
+        rp = workload_rate(args.workload, 3, 2, half_force=True)
+        out["reduced_precision"] = {"form": "FP16 force meshes with a power-of-two scale per row and field "
+                                            "(pm_config.half_force); FFTs, deposit and particles FP32", **rp,
+                                    "speedup_vs_fp32": rp["steps_per_s"] / value}
     if not args.no_cpu_baseline:
         procs = host_cores()
         wall, per = oracle_pool_round(procs)
@@ -581,10 +587,11 @@ def run_fft_compare(args):
                       "max_rel_diff_vs_cufft": err}))
 
 
-def workload_rate(name, warmup=3, steps=3):
-    """Gradient steps/s of another single-instance configuration of the workload set, timed
-    like the main line: autotuned on the final forward state, CUDA events on the launching
-    stream around `steps` evaluations after `warmup`, the error flag checked after."""
+def workload_rate(name, warmup=3, steps=3, half_force=False):
+    """Gradient steps/s of a single-instance configuration of the workload set (with
+    `half_force`, the FP16 force-mesh form), timed like the main line: autotuned on the
+    final forward state, CUDA events on the launching stream around `steps` evaluations
+    after `warmup`, the error flag checked after."""
     import torch
     from paper_2211_09815_gb300 import inputs, pm
     box, nm, npc, n = WORKLOADS[name]
@@ -595,7 +602,7 @@ def workload_rate(name, warmup=3, steps=3):
     c.forward(dens=target)
     c.close()
     om = torch.from_numpy(inputs.white_noise(npc, 1)).to("cuda")
-    ctx = pm.PMContext(box, nm, npc, n, [THETA], om, check_errors=False)
+    ctx = pm.PMContext(box, nm, npc, n, [THETA], om, check_errors=False, half_force=half_force)
     ctx.forward()
     ctx.autotune()
     djdd = torch.empty(M, device="cuda")
@@ -761,8 +768,9 @@ def run_precision_study(args):
     N, M = npc ** 3, nm ** 3
     out = {}
     tgt_np = None
-    for prec, ck, pert, fix in ((0, 0, False, False), (0, 8, False, False), (0, 0, False, True), (1, 0, False, False),
-                                (1, 0, True, False)):
+    for prec, ck, pert, fix, hf in ((0, 0, False, False, False), (0, 8, False, False, False),
+                                    (0, 0, False, True, False), (0, 0, False, False, True),
+                                    (1, 0, False, False, False), (1, 0, True, False, False)):
         dt = torch.float32 if prec == 0 else torch.float64
         if tgt_np is None:
             om2 = torch.from_numpy(inputs.white_noise(npc, 2)).cuda()
@@ -777,7 +785,8 @@ def run_precision_study(args):
             sign = np.where(inputs.uniform01(77, om_np.size).reshape(om_np.shape) < 0.5, -1.0, 1.0)
             om_np = om_np.astype(np.float64) + sign * np.spacing(np.abs(om_np)).astype(np.float64)
         om = torch.from_numpy(np.ascontiguousarray(om_np)).to("cuda", dt)
-        ctx = pm.PMContext(box, nm, npc, n, [THETA], om, precision=prec, ckpt_every=ck, fixed_state=fix)
+        ctx = pm.PMContext(box, nm, npc, n, [THETA], om, precision=prec, ckpt_every=ck, fixed_state=fix,
+                           half_force=hf)
         disp = torch.empty(3 * N, device="cuda", dtype=dt)
         mom = torch.empty_like(disp)
         ctx.forward(disp=disp, mom=mom)
@@ -791,14 +800,15 @@ def run_precision_study(args):
         t0 = time.perf_counter()
         ctx.adjoint(djdd=djdd, grad_omega=gw, grad_theta=gt)
         torch.cuda.synchronize()
-        out[(prec, ck, pert, fix)] = dict(s=disp.cpu().numpy().astype(np.float64), p=mom.cpu().numpy().astype(np.float64),
+        out[(prec, ck, pert, fix, hf)] = dict(s=disp.cpu().numpy().astype(np.float64), p=mom.cpu().numpy().astype(np.float64),
                          pk=pk[0], nmodes=nmodes, gw=gw.cpu().numpy().astype(np.float64), gt=gt.cpu().numpy(),
                          adj_s=time.perf_counter() - t0)
         ctx.close()
         del om, disp, mom, tgt, djdd, gw, gt
         torch.cuda.empty_cache()
-    a, b, a8 = out[(0, 0, False, False)], out[(1, 0, False, False)], out[(0, 8, False, False)]
-    bp, af = out[(1, 0, True, False)], out[(0, 0, False, True)]
+    a, b, a8 = out[(0, 0, False, False, False)], out[(1, 0, False, False, False)], out[(0, 8, False, False, False)]
+    bp, af = out[(1, 0, True, False, False)], out[(0, 0, False, True, False)]
+    ah = out[(0, 0, False, False, True)]
     cell = box / nm
     ok = b["nmodes"] > 0
     ok[0] = False
@@ -815,6 +825,13 @@ def run_precision_study(args):
                       "grad_omega_rel_l2": float(np.linalg.norm(a8["gw"] - b["gw"]) / np.linalg.norm(b["gw"])),
                       "grad_theta_rel": (np.abs(a8["gt"] / b["gt"] - 1)).tolist()},
         "adjoint_seconds": {"f32": a["adj_s"], "f32_ckpt8": a8["adj_s"], "f64": b["adj_s"]},
+        "f32_half_force": {
+            "disp_rms_cells": float(np.sqrt(np.mean((ah["s"] - b["s"]) ** 2)) / cell),
+            "mom_rel_l2": float(np.linalg.norm(ah["p"] - b["p"]) / np.linalg.norm(b["p"])),
+            "pk_max_rel": float(np.max(np.abs(ah["pk"][ok] / b["pk"][ok] - 1))),
+            "grad_omega_cosine": float(ah["gw"] @ b["gw"] / (np.linalg.norm(ah["gw"]) * np.linalg.norm(b["gw"]))),
+            "grad_omega_rel_l2": float(np.linalg.norm(ah["gw"] - b["gw"]) / np.linalg.norm(b["gw"])),
+            "grad_theta_rel": (np.abs(ah["gt"] / b["gt"] - 1)).tolist()},
         "f32_fixed_state": {
             "disp_rms_cells": float(np.sqrt(np.mean((af["s"] - b["s"]) ** 2)) / cell),
             "grad_omega_cosine": float(af["gw"] @ b["gw"] / (np.linalg.norm(af["gw"]) * np.linalg.norm(b["gw"]))),

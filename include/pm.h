@@ -77,6 +77,13 @@ typedef struct {
                        time integration recovers every forward state exactly (the paper's
                        FP32 reversion error, Sec. 3.5, disappears).  Kernels read working-
                        precision copies.  Not combined with ckpt_every > 0 (PM_ERR_ARG). */
+  int half_force;   /* 1 (PM_F32 only, else PM_ERR_ARG): the force meshes that the gathers read
+                       are stored in FP16, four halves per cell, each field of a mesh row
+                       scaled by a power of two chosen from the row's largest magnitude (an
+                       int8 exponent per row and field); the row transforms compute in FP32
+                       and the gathers convert back.  Halves the bytes of the [cell][4] mesh
+                       written by the C2R x passes and read by the gathers, at FP16 rounding
+                       of the force (a reduced-precision form, not the paper's). */
 } pm_config;
 
 /*

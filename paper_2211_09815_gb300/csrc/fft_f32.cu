@@ -13,7 +13,7 @@ template int fft_fused_tma<float>(int, bool, const CUtensorMap*, const CUtensorM
                                  cudaStream_t);
 template int fft_fused_side<float>(int, const ZJob<float>&, bool, const cx_t<float>*, cudaStream_t);
 template int make_spec_tensor_maps<float>(int, int, cx_t<float>*, CUtensorMap*, CUtensorMap*);
-template int fft_x_c2r4<float>(int, const RowJob<float>&, int, int, V4<float>*, const cx_t<float>*, cudaStream_t);
+template int fft_x_c2r4<float>(int, const RowJob<float>&, int, int, void*, signed char*, const cx_t<float>*, cudaStream_t);
 template int fft_cols_split<float>(int, const SeqMap&, const SeqMap&, cx_t<float>*, cx_t<float>*, const cx_t<float>*,
                                    cudaStream_t);
 template int fft_cols_merge<float>(int, const SeqMap&, const SeqMap&, cx_t<float>*, cx_t<float>*, const cx_t<float>*,

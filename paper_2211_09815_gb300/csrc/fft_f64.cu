@@ -13,7 +13,7 @@ template int fft_fused_tma<double>(int, bool, const CUtensorMap*, const CUtensor
                                  cudaStream_t);
 template int fft_fused_side<double>(int, const ZJob<double>&, bool, const cx_t<double>*, cudaStream_t);
 template int make_spec_tensor_maps<double>(int, int, cx_t<double>*, CUtensorMap*, CUtensorMap*);
-template int fft_x_c2r4<double>(int, const RowJob<double>&, int, int, V4<double>*, const cx_t<double>*, cudaStream_t);
+template int fft_x_c2r4<double>(int, const RowJob<double>&, int, int, void*, signed char*, const cx_t<double>*, cudaStream_t);
 template int fft_cols_split<double>(int, const SeqMap&, const SeqMap&, cx_t<double>*, cx_t<double>*, const cx_t<double>*,
                                    cudaStream_t);
 template int fft_cols_merge<double>(int, const SeqMap&, const SeqMap&, cx_t<double>*, cx_t<double>*, const cx_t<double>*,

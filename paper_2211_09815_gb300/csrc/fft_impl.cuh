@@ -9,6 +9,8 @@
 #pragma once
 #include <type_traits>
 
+#include <cuda_fp16.h>
+
 #include "fft.cuh"
 #include "fft_tma.cuh"
 #include "pm_internal.h"
@@ -296,10 +298,14 @@ template <typename T, int L, int Q> struct C2R4Tile {
   static constexpr int SMEM = skew_rows(L) * LD * (int)sizeof(cx_t<T>);
 };
 
-template <typename T, int L, int Q>
+// H: the FP16 force mesh (pm_config.half_force, FP32 only): per cell four halves, each
+// field of a row scaled by 2^-e so that the row's largest magnitude lies in [2^14, 2^15),
+// e stored as one int8 per (row, field) in fexp ([rows][4]); FP16 keeps 11 significant
+// bits of every value in the row down to 2^-29 of its largest.
+template <typename T, int L, int Q, bool H = false>
 __global__ void __launch_bounds__(C2R4Tile<T, L, Q>::NT)
-k_fft_x_c2r4(RowJob<T> job, int nrows, int dq, V4<T>* __restrict__ out4, const cx_t<T>* __restrict__ twL,
-             const cx_t<T>* __restrict__ twN) {
+k_fft_x_c2r4(RowJob<T> job, int nrows, int dq, void* __restrict__ out, signed char* __restrict__ fexp,
+             const cx_t<T>* __restrict__ twL, const cx_t<T>* __restrict__ twN) {
   using C = cx_t<T>;
   using TL = C2R4Tile<T, L, Q>;
   using U = C2RUntangle<T, L, TL::TR, TL::NT>;
@@ -369,16 +375,55 @@ k_fft_x_c2r4(RowJob<T> job, int nrows, int dq, V4<T>* __restrict__ out4, const c
   SmemTile<C, TL::LD> t{sm};
   fft_tile<T, L, TL::TR, TL::NT, +1, typename TL::P>(t, t, t, twL);
   __syncthreads();
-  V4<T>* const tile_out = out4 + (long long)r0 * N;
-  for (int idx = threadIdx.x; idx < RT * L; idx += TL::NT) {
-    const int row = idx / L, j = idx % L;
-    if (r0 + row >= nrows) continue;
-    const C v0 = sm[srow(j) * TL::LD + row], v1 = sm[srow(j) * TL::LD + RT + row];
-    const C v2 = sm[srow(j) * TL::LD + 2 * RT + row];
-    const C v3 = Q == 4 ? sm[srow(j) * TL::LD + (Q - 1) * RT + row] : cmake<C>(0, 0);
-    V4<T>* o = tile_out + 2 * idx;
-    o[0] = V4<T>{v0.x, v1.x, v2.x, v3.x};
-    o[1] = V4<T>{v0.y, v1.y, v2.y, v3.y};
+  if constexpr (!H) {
+    V4<T>* const tile_out = reinterpret_cast<V4<T>*>(out) + (long long)r0 * N;
+    for (int idx = threadIdx.x; idx < RT * L; idx += TL::NT) {
+      const int row = idx / L, j = idx % L;
+      if (r0 + row >= nrows) continue;
+      const C v0 = sm[srow(j) * TL::LD + row], v1 = sm[srow(j) * TL::LD + RT + row];
+      const C v2 = sm[srow(j) * TL::LD + 2 * RT + row];
+      const C v3 = Q == 4 ? sm[srow(j) * TL::LD + (Q - 1) * RT + row] : cmake<C>(0, 0);
+      V4<T>* o = tile_out + 2 * idx;
+      o[0] = V4<T>{v0.x, v1.x, v2.x, v3.x};
+      o[1] = V4<T>{v0.y, v1.y, v2.y, v3.y};
+    }
+  } else {
+    static_assert(sizeof(T) == 4, "the FP16 force mesh is an FP32-path form");
+    // largest magnitude per (row, field): bit patterns of non-negative floats order like
+    // the values, so an unsigned max finds it
+    __shared__ unsigned smax[RT * 4];
+    __shared__ float sscale[RT * 4];
+    for (int k = threadIdx.x; k < RT * 4; k += TL::NT) smax[k] = 0u;
+    __syncthreads();
+    for (int k = threadIdx.x; k < Q * RT * L; k += TL::NT) {
+      const int c = k / L, j = k % L;   // sequence c = q RT + row
+      const C v = sm[srow(j) * TL::LD + c];
+      atomicMax(&smax[(c % RT) * 4 + c / RT], __float_as_uint(fmaxf(fabsf(v.x), fabsf(v.y))));
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < RT * 4; k += TL::NT) {
+      const float m = __uint_as_float(smax[k]);
+      int e = m > 0.f ? ilogbf(m) - 14 : 0;   // m 2^-e in [2^14, 2^15)
+      e = e < -120 ? -120 : (e > 120 ? 120 : e);
+      sscale[k] = __int_as_float((127 - e) << 23);   // 2^-e
+      const int row = k / 4;
+      if (r0 + row < nrows) fexp[(long long)(r0 + row) * 4 + k % 4] = (signed char)e;
+    }
+    __syncthreads();
+    uint4* const tile_out = reinterpret_cast<uint4*>(out) + (long long)r0 * (N / 2);
+    for (int idx = threadIdx.x; idx < RT * L; idx += TL::NT) {
+      const int row = idx / L, j = idx % L;
+      if (r0 + row >= nrows) continue;
+      const float* sc = sscale + row * 4;
+      const C v0 = sm[srow(j) * TL::LD + row], v1 = sm[srow(j) * TL::LD + RT + row];
+      const C v2 = sm[srow(j) * TL::LD + 2 * RT + row];
+      const C v3 = Q == 4 ? sm[srow(j) * TL::LD + (Q - 1) * RT + row] : cmake<C>(0, 0);
+      // cells 2j and 2j + 1 of the row: (f_0, f_1, f_2, f_3) as two half2 each
+      const __half2 a0 = __floats2half2_rn(v0.x * sc[0], v1.x * sc[1]), a1 = __floats2half2_rn(v2.x * sc[2], v3.x * sc[3]);
+      const __half2 b0 = __floats2half2_rn(v0.y * sc[0], v1.y * sc[1]), b1 = __floats2half2_rn(v2.y * sc[2], v3.y * sc[3]);
+      tile_out[idx] = make_uint4(*reinterpret_cast<const unsigned*>(&a0), *reinterpret_cast<const unsigned*>(&a1),
+                                 *reinterpret_cast<const unsigned*>(&b0), *reinterpret_cast<const unsigned*>(&b1));
+    }
   }
 }
 
@@ -807,27 +852,31 @@ int fft_x_r2c(int n, const RowJob<T>& job, int nbuf, int nrows, const cx_t<T>* t
 }
 
 template <typename T, int L, int Q>
-static void launch_c2r4_LQ(const RowJob<T>& job, int nrows, int dq, V4<T>* out4, const cx_t<T>* tw,
+static void launch_c2r4_LQ(const RowJob<T>& job, int nrows, int dq, void* out, signed char* fexp, const cx_t<T>* tw,
                            cudaStream_t st) {
   using TL = C2R4Tile<T, L, Q>;
   if constexpr (RowTile<T, L>::TR % 4 == 0 && (TL::TR * L) % TL::P::RMAX == 0) {
     const size_t sm = TL::SMEM;
-    auto fn = k_fft_x_c2r4<T, L, Q>;
+    auto fn = k_fft_x_c2r4<T, L, Q, false>;
+    if constexpr (sizeof(T) == 4)
+      if (fexp) fn = k_fft_x_c2r4<T, L, Q, true>;
     set_smem<T, L>((const void*)fn, sm);
-    fn<<<(nrows + TL::RT - 1) / TL::RT, TL::NT, sm, st>>>(job, nrows, dq, out4, tw + L, tw + 2 * L);
+    fn<<<(nrows + TL::RT - 1) / TL::RT, TL::NT, sm, st>>>(job, nrows, dq, out, fexp, tw + L, tw + 2 * L);
   }
 }
 template <typename T, int L>
-static void launch_c2r4_L(const RowJob<T>& job, int nrows, int dq, V4<T>* out4, const cx_t<T>* tw,
+static void launch_c2r4_L(const RowJob<T>& job, int nrows, int dq, void* out, signed char* fexp, const cx_t<T>* tw,
                           cudaStream_t st) {
-  if (job.b[3].spec) launch_c2r4_LQ<T, L, 4>(job, nrows, dq, out4, tw, st);
-  else launch_c2r4_LQ<T, L, 3>(job, nrows, dq, out4, tw, st);
+  if (job.b[3].spec) launch_c2r4_LQ<T, L, 4>(job, nrows, dq, out, fexp, tw, st);
+  else launch_c2r4_LQ<T, L, 3>(job, nrows, dq, out, fexp, tw, st);
 }
 
 template <typename T>
-int fft_x_c2r4(int n, const RowJob<T>& job, int nrows, int dq, V4<T>* out4, const cx_t<T>* tw, cudaStream_t st) {
+int fft_x_c2r4(int n, const RowJob<T>& job, int nrows, int dq, void* out, signed char* fexp, const cx_t<T>* tw,
+               cudaStream_t st) {
   if (n < 8 || n > 1024) return PM_ERR_ARG;
-  PMGB_DISPATCH_L(n / 2, (launch_c2r4_L<T, (LL < 512 ? LL : 512)>(job, nrows, dq, out4, tw, st)));
+  if (fexp && sizeof(T) != 4) return PM_ERR_ARG;
+  PMGB_DISPATCH_L(n / 2, (launch_c2r4_L<T, (LL < 512 ? LL : 512)>(job, nrows, dq, out, fexp, tw, st)));
   return PM_OK;
 }
 

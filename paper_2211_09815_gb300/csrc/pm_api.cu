@@ -56,6 +56,7 @@ static int validate(const pm_config* c, const double* theta) {
   if (c->n_steps < 1 || c->batch < 1 || c->ckpt_every < 0) return PM_ERR_ARG;
   if (c->lpt_order < 0 || c->lpt_order > 2) return PM_ERR_ARG;
   if (c->fixed_state < 0 || c->fixed_state > 1 || (c->fixed_state && c->ckpt_every > 0)) return PM_ERR_ARG;
+  if (c->half_force < 0 || c->half_force > 1 || (c->half_force && c->precision != PM_F32)) return PM_ERR_ARG;
   if (!(c->a0 > 0) || !(c->a1 > c->a0) || !std::isfinite(c->a1)) return PM_ERR_ARG;
   if (c->precision != PM_F32 && c->precision != PM_F64) return PM_ERR_ARG;
   if ((long long)c->batch * c->n_mesh * c->n_mesh * (c->n_mesh / 2) >= (1LL << 31)) return PM_ERR_ARG;

@@ -158,8 +158,9 @@ class Engine : public EngineBase {
     // particle loops: whole waves of resident blocks (grid-stride loops, every thread the
     // same share), so that no partial last wave leaves SMs idle; G_ is also the number of
     // per-block partial sums of the reductions
-    G_ = wave_grid((const void*)k_gather_adj<T>, N_);
-    Gf_ = wave_grid((const void*)k_gather_fwd<T>, N_);
+    hf_ = cfg->half_force != 0 && sizeof(T) == 4;
+    G_ = wave_grid((const void*)gather_adj_fn(), N_);
+    Gf_ = wave_grid((const void*)gather_fwd_fn(), N_);
     Gc_ = wave_grid((const void*)k_bin_count<T>, N_);
     Gb1_ = wave_grid((const void*)k_bin_fill<T, 1>, N_);
     Gb4_ = wave_grid((const void*)k_bin_fill<T, 4>, N_);
@@ -181,6 +182,7 @@ class Engine : public EngineBase {
     for (int q = 0; q < 7; ++q) PMGB_RET(alloc(&spec_[q], sl));
     PMGB_RET(alloc(&dens_, (long long)B_ * M_));
     PMGB_RET(alloc(&fvec_, (long long)B_ * M_));
+    if (hf_) PMGB_RET(alloc(&fexp_, (long long)B_ * nm_ * nm_));   // int8 exponent quadruple per row
     if (cfg->fixed_state) {
       PMGB_RET(alloc(&fix_u_, pv));
       PMGB_RET(alloc(&fix_w_, pv));
@@ -241,8 +243,8 @@ class Engine : public EngineBase {
       T* snap_p = (q >= 0 && snap_mom_) ? snap_mom_ + (long long)q * B_ * 3 * N_ : nullptr;
       prof_.begin(st_, P_GATHER_FWD, 1);
       // the bins of the next step's deposit are counted at the new positions
-      k_gather_fwd<T><<<dim3(Gf_, B_), kPtclThreads, 0, st_>>>(geo_, s_, p_, j == n_ ? a_ : nullptr, fvec_, sc, j,
-                                                              n_ + 1, cks, ckp, fused1_ ? bgf1_ : bg1_,
+      gather_fwd_fn()<<<dim3(Gf_, B_), kPtclThreads, 0, st_>>>(geo_, s_, p_, j == n_ ? a_ : nullptr, fvec_, fexp_, sc,
+                                                              j, n_ + 1, cks, ckp, fused1_ ? bgf1_ : bg1_,
                                                               j < n_ ? bcount_ : nullptr, bkeys_, snap_p, fx_);
       counted_ = j < n_;
       prof_.end(st_, P_GATHER_FWD);
@@ -346,8 +348,8 @@ class Engine : public EngineBase {
       double* ppa = part_ + (long long)(2 * j) * B_ * G_;
       double* pxp = part_ + (long long)(2 * j + 1) * B_ * G_;
       prof_.begin(st_, P_GATHER_ADJ, 1);
-      k_gather_adj<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, mass_, s_, p_, xi_, pi_, vmom ? a_ : nullptr,
-                                                              nullptr, fvec_, sc, j, n_ + 1, ckp, cks, ppa, pxp,
+      gather_adj_fn()<<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, mass_, s_, p_, xi_, pi_, vmom ? a_ : nullptr,
+                                                              nullptr, fvec_, fexp_, sc, j, n_ + 1, ckp, cks, ppa, pxp,
                                                               pimax_, fused4_ ? bgf4_ : bg4_,
                                                               j > 0 ? bcount_ : nullptr, bkeys_, fx_);
       counted_ = j > 0;
@@ -417,8 +419,8 @@ class Engine : public EngineBase {
     StepCoef<T> sc{zero_, zero_, zero_};
     if (!pi) {
       PMGB_RET(force_chain(s_, nullptr, false));
-      k_gather_fwd<T><<<dim3(Gf_, B_), kPtclThreads, 0, st_>>>(geo_, s_, p_, (T*)acc, fvec_, sc, 0, 1, nullptr,
-                                                              nullptr, bg1_, nullptr, nullptr);
+      gather_fwd_fn()<<<dim3(Gf_, B_), kPtclThreads, 0, st_>>>(geo_, s_, p_, (T*)acc, fvec_, fexp_, sc, 0, 1, nullptr,
+                                                              nullptr, bg1_, nullptr, nullptr, nullptr, FixState<T>{});
     } else {
       PMGB_CK(cudaMemcpyAsync(pi_, pi, sizeof(T) * B_ * 3 * N_, cudaMemcpyDeviceToDevice, st_));
       PMGB_CK(cudaMemsetAsync(pimax_, 0, sizeof(unsigned) * 3 * B_, st_));
@@ -427,9 +429,9 @@ class Engine : public EngineBase {
       k_adjoint_init<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, mass_, s_, nullptr, nullptr, (const T*)pi,
                                                                 xi_, pi_, pimax_);
       PMGB_RET(force_chain(s_, pi_, false));
-      k_gather_adj<T><<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, mass_, s_, p_, xi_, pi_, (T*)acc, (T*)alpha,
-                                                              fvec_, sc, 0, 1, nullptr, nullptr, nullptr, nullptr,
-                                                              nullptr, bg4_, nullptr, nullptr);
+      gather_adj_fn()<<<dim3(G_, B_), kPtclThreads, 0, st_>>>(geo_, mass_, s_, p_, xi_, pi_, (T*)acc, (T*)alpha,
+                                                              fvec_, fexp_, sc, 0, 1, nullptr, nullptr, nullptr, nullptr,
+                                                              nullptr, bg4_, nullptr, nullptr, FixState<T>{});
     }
     PMGB_CK(cudaGetLastError());
     return PM_OK;
@@ -1321,7 +1323,7 @@ class Engine : public EngineBase {
     for (int q = 0; q < 4; ++q) jc.b[q] = RowBuf<T>{nullptr, 0, (q < 3 || pi) ? c2rb[q] : nullptr};
     jc.lzb = spec_lzb(nm_);
     prof_.begin(st_, P_X_C2R, 1);
-    PMGB_RET(fft_x_c2r4<T>(nm_, jc, B_ * nm_ * nm_, 2, reinterpret_cast<V4<T>*>(fvec_), tw_, st_));
+    PMGB_RET(fft_x_c2r4<T>(nm_, jc, B_ * nm_ * nm_, 2, fvec_, reinterpret_cast<signed char*>(fexp_), tw_, st_));
     prof_.end(st_, P_X_C2R);
     PMGB_CK(cudaGetLastError());
     return PM_OK;
@@ -1581,6 +1583,19 @@ class Engine : public EngineBase {
   Prof prof_;
   bool use_tma_ = false;
   int nsm_ = 1;   // SM count
+  bool hf_ = false;        // pm_config.half_force: the FP16 [cell][4] force mesh (FP32 path)
+  int* fexp_ = nullptr;    // its int8 exponent quadruples, one int per mesh row [B][n][n]
+  // the gathers of the force mesh in its stored form
+  decltype(&k_gather_fwd<T, false>) gather_fwd_fn() const {
+    if constexpr (sizeof(T) == 4)
+      if (hf_) return &k_gather_fwd<T, true>;
+    return &k_gather_fwd<T, false>;
+  }
+  decltype(&k_gather_adj<T, false>) gather_adj_fn() const {
+    if constexpr (sizeof(T) == 4)
+      if (hf_) return &k_gather_adj<T, true>;
+    return &k_gather_adj<T, false>;
+  }
   cudaStream_t cp_st_ = nullptr;                       // copy stream of pm_gradient's target
   cudaEvent_t cp_in_ = nullptr, cp_done_ = nullptr;     // its order after st_, its completion
   int* dev_err_ = nullptr;

@@ -65,7 +65,8 @@ int fft_x_c2r(int n, const RowJob<T>& job, int nbuf, int nrows, const cx_t<T>* t
 // C2R of up to four components into one interleaved [cell][4] real mesh; component dq
 // (none if dq < 0) is multiplied by -i k_x first
 template <typename T>
-int fft_x_c2r4(int n, const RowJob<T>& job, int nrows, int dq, V4<T>* out4, const cx_t<T>* tw, cudaStream_t st);
+int fft_x_c2r4(int n, const RowJob<T>& job, int nrows, int dq, void* out, signed char* fexp, const cx_t<T>* tw,
+               cudaStream_t st);
 template <typename T>
 int fft_fused_z(int n, const ZJob<T>& job, bool adjoint, const cx_t<T>* tw, cudaStream_t st);
 

@@ -13,6 +13,7 @@
 //  k_density_out, k_mse, k_za_mul, k_za_adj_mul, k_ic_state, k_ic_adj_prep, k_final_theta,
 //  k_lpt_hess, k_lpt_source, k_lpt_source_adj, k_lpt_hess_adj, k_ic_state2
 #pragma once
+#include <cuda_fp16.h>
 #include "common.cuh"
 #include "pm_internal.h"
 
@@ -89,6 +90,38 @@ __device__ __forceinline__ long long corner_index(const Geo<T>& g, const int cel
   const int i1 = (cell[1] + ((d >> 1) & 1)) & m;
   const int i2 = (cell[2] + (d & 1)) & m;
   return ((long long)i0 * g.nm + i1) * g.nm + i2;
+}
+
+// The eight CIC corners of the [cell][4] force mesh: FP32 V4 per cell, or (H, FP32 path
+// only) the FP16 mesh of k_fft_x_c2r4<..., true>: four halves per cell, each field of a row
+// (fixed z, y) scaled by 2^-e with e an int8 of the row's packed quadruple in fexp.
+template <typename T, bool H>
+__device__ __forceinline__ void load_corners(const Geo<T>& g, const void* __restrict__ fvec,
+                                             const int* __restrict__ fexp, int b, const int cell[3], V4<T> fv[8]) {
+  if constexpr (!H) {
+    const V4<T>* F = reinterpret_cast<const V4<T>*>(fvec) + (long long)b * g.M;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) fv[d] = F[corner_index(g, cell, d)];
+  } else {
+    static_assert(sizeof(T) == 4, "the FP16 force mesh is an FP32-path form");
+    const uint2* F = reinterpret_cast<const uint2*>(fvec) + (long long)b * g.M;
+    const int* E = fexp + (long long)b * g.nm * g.nm;
+    const int m = g.nm - 1;
+    int ew[4];   // exponent quadruples of the rows (z0 + dz, y0 + dy), index 2 dz + dy
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ew[k] = __ldg(E + ((cell[0] + (k >> 1)) & m) * g.nm + ((cell[1] + (k & 1)) & m));
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      const uint2 u = __ldg(F + corner_index(g, cell, d));
+      const int w = ew[(d >> 1) & 3];
+      const float2 lo = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+      const float2 hi = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+      fv[d] = V4<T>{lo.x * __int_as_float(((int)(signed char)(w & 0xFF) + 127) << 23),
+                    lo.y * __int_as_float(((int)(signed char)((w >> 8) & 0xFF) + 127) << 23),
+                    hi.x * __int_as_float(((int)(signed char)((w >> 16) & 0xFF) + 127) << 23),
+                    hi.y * __int_as_float(((int)(signed char)((w >> 24) & 0xFF) + 127) << 23)};
+    }
+  }
 }
 
 template <typename T> __device__ __forceinline__ long long to_fixed(T v);
@@ -307,17 +340,17 @@ struct StepCoef {  // per-instance coefficient tables [batch][n+1], indexed at s
 };
 
 // a = sum_g W f(g);  p += a kA;  (store p_j);  p += a kB;  (store s_j);  s += p dr
-template <typename T>
+template <typename T, bool H = false>
 __global__ void __launch_bounds__(kPtclThreads)
 k_gather_fwd(Geo<T> g, T* __restrict__ s, T* __restrict__ p, T* __restrict__ a_out,
-             const V4<T>* __restrict__ fvec, StepCoef<T> sc, int j, int nstep1, T* __restrict__ ck_s,
+             const void* __restrict__ fvec, const int* __restrict__ fexp, StepCoef<T> sc, int j, int nstep1,
+             T* __restrict__ ck_s,
              T* __restrict__ ck_p, BinGeo bg, unsigned* __restrict__ bcount, unsigned* __restrict__ bkeys,
              T* __restrict__ snap_p = nullptr, FixState<T> fx = FixState<T>{}) {
   const int b = blockIdx.y;
   const T kA = sc.kA[b * nstep1 + j], kB = sc.kB[b * nstep1 + j], dr = sc.dr[b * nstep1 + j];
   T* sb = s + (long long)b * 3 * g.N;
   T* pb = p + (long long)b * 3 * g.N;
-  const V4<T>* F = fvec + (long long)b * g.M;
   // the displacement of the thread's next particle is read one iteration ahead, so that
   // its latency overlaps this particle's corner loads (each particle has one thread: the
   // value is not written before it is used)
@@ -336,8 +369,7 @@ k_gather_fwd(Geo<T> g, T* __restrict__ s, T* __restrict__ p, T* __restrict__ a_o
     T t[3];
     cic_cell(g, i, sv, cell, t);
     V4<T> fv[8];
-#pragma unroll
-    for (int d = 0; d < 8; ++d) fv[d] = F[corner_index(g, cell, d)];
+    load_corners<T, H>(g, fvec, fexp, b, cell, fv);
     if (w + stride < g.N) {
       const long long in = particle_of(g, w + stride);
       sn[0] = sb[in], sn[1] = sb[g.N + in], sn[2] = sb[2 * g.N + in];
@@ -391,11 +423,11 @@ k_gather_fwd(Geo<T> g, T* __restrict__ s, T* __restrict__ p, T* __restrict__ a_o
 // Reverse step at force step j (Eq. 49): a_j = sum W f, alpha_j = sum grad W [pi.f + m psi];
 // p -= a K1_{j+1}; xi += alpha K1_{j+1}; (p := stored p_j); p -= a K2_j; xi += alpha K2_j;
 // s -= p D_j; pi += xi D_j; (s := stored s_{j-1}).  FP64 partials of pi.a and xi.p.
-template <typename T>
+template <typename T, bool H = false>
 __global__ void __launch_bounds__(kPtclThreads)
 k_gather_adj(Geo<T> g, T mass, T* __restrict__ s, T* __restrict__ p, T* __restrict__ xi, T* __restrict__ pi,
-             T* __restrict__ a_out, T* __restrict__ alpha_out, const V4<T>* __restrict__ fvec,
-             StepCoef<T> sc, int j, int nstep1,
+             T* __restrict__ a_out, T* __restrict__ alpha_out, const void* __restrict__ fvec,
+             const int* __restrict__ fexp, StepCoef<T> sc, int j, int nstep1,
              const T* __restrict__ ck_p, const T* __restrict__ ck_s, double* __restrict__ part_pa,
              double* __restrict__ part_xp, unsigned* __restrict__ pimax, BinGeo bg, unsigned* __restrict__ bcount,
              unsigned* __restrict__ bkeys, FixState<T> fx = FixState<T>{}) {
@@ -404,7 +436,6 @@ k_gather_adj(Geo<T> g, T mass, T* __restrict__ s, T* __restrict__ p, T* __restri
   const int b = blockIdx.y;
   const T cA = sc.kA[b * nstep1 + j], cB = sc.kB[b * nstep1 + j], dr = sc.dr[b * nstep1 + j];
   const long long po = (long long)b * 3 * g.N;
-  const V4<T>* F = fvec + (long long)b * g.M;
   const T il = g.inv_l;
   KahanAcc<T> acc_pa, acc_xp;
   float mx[3] = {0.f, 0.f, 0.f};
@@ -423,8 +454,7 @@ k_gather_adj(Geo<T> g, T mass, T* __restrict__ s, T* __restrict__ p, T* __restri
     T t[3];
     cic_cell(g, i, sv, cell, t);
     V4<T> fv[8];
-#pragma unroll
-    for (int d = 0; d < 8; ++d) fv[d] = F[corner_index(g, cell, d)];
+    load_corners<T, H>(g, fvec, fexp, b, cell, fv);
     T a[3] = {0, 0, 0}, al[3] = {0, 0, 0};
 #pragma unroll
     for (int d = 0; d < 8; ++d) {

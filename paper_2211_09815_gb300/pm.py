@@ -52,7 +52,8 @@ class PMConfig(ctypes.Structure):
     _fields_ = [("box", ctypes.c_double), ("n_mesh", ctypes.c_int), ("n_ptcl", ctypes.c_int),
                 ("n_steps", ctypes.c_int), ("a0", ctypes.c_double), ("a1", ctypes.c_double),
                 ("precision", ctypes.c_int), ("ckpt_every", ctypes.c_int), ("deconv", ctypes.c_int),
-                ("batch", ctypes.c_int), ("lpt_order", ctypes.c_int), ("fixed_state", ctypes.c_int)]
+                ("batch", ctypes.c_int), ("lpt_order", ctypes.c_int), ("fixed_state", ctypes.c_int),
+                ("half_force", ctypes.c_int)]
 
 
 _lib = None
@@ -159,6 +160,8 @@ class PMContext:
     omega: CUDA tensor [batch, n_ptcl, n_ptcl, n_ptcl] (float32 or float64 per precision);
     theta: host sequence of shape [batch, 5] (A_s, n_s, Omega_m, Omega_b, h);
     lpt_order: 1 for Zel'dovich initial conditions, 2 for 2LPT.
+    fixed_state: the exactly reversible 64-bit integer particle state.
+    half_force: FP16 force meshes between the C2R x passes and the gathers (FP32 only).
     check_errors: after every call that launches work, synchronise the stream and raise
     PMError(PM_ERR_TIMEOUT) if a bounded device wait gave up (pm_check).
     ``state_version`` counts the calls that replace the context's forward state.
@@ -166,14 +169,14 @@ class PMContext:
 
     def __init__(self, box, n_mesh, n_ptcl, n_steps, theta, omega, a0=1.0 / 64, a1=1.0,
                  precision=PM_F32, ckpt_every=0, deconv=False, batch=1, stream=None, lpt_order=1,
-                 check_errors=True, fixed_state=False):
+                 check_errors=True, fixed_state=False, half_force=False):
         import torch
         lib = load_library()
         self.check_errors = check_errors
         self.state_version = 0
         self.device = torch.cuda.current_device()
         self.cfg = PMConfig(box, n_mesh, n_ptcl, n_steps, a0, a1, precision, ckpt_every, int(deconv), batch,
-                            int(lpt_order), int(fixed_state))
+                            int(lpt_order), int(fixed_state), int(half_force))
         self.dtype = torch.float32 if precision == PM_F32 else torch.float64
         self.batch, self.n_mesh, self.n_ptcl = batch, n_mesh, n_ptcl
         self.N, self.M = n_ptcl ** 3, n_mesh ** 3

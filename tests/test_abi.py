@@ -47,6 +47,8 @@ def test_invalid_configs_are_rejected_on_the_host():
         pm.PMConfig(100.0, 32, 16, 10, 1 / 64, 1.0, 0, 0, 0, 1, 3), # LPT order
         pm.PMConfig(100.0, 32, 16, 10, 1 / 64, 1.0, 0, 0, 0, 1, 1, 2),   # fixed_state flag
         pm.PMConfig(100.0, 32, 16, 10, 1 / 64, 1.0, 0, 8, 0, 1, 1, 1),   # fixed state with checkpoints
+        pm.PMConfig(100.0, 32, 16, 10, 1 / 64, 1.0, 0, 0, 0, 1, 1, 0, 2),   # half_force flag
+        pm.PMConfig(100.0, 32, 16, 10, 1 / 64, 1.0, 1, 0, 0, 1, 1, 0, 1),   # FP16 force mesh with FP64
     ]
     for cfg in bad:
         assert lib.pm_init(ctypes.byref(h), ctypes.byref(cfg), th, dummy, None) == 1

@@ -23,9 +23,15 @@ pytestmark = pytest.mark.gpu
 BOX, NM, NP, NS = 200.0, 256, 128, 63
 
 
-def _run(precision, omega, target):
+def _run(precision, omega, target, half_force=False):
     torch = torch_cuda()
-    ctx, *_ = make_ctx(BOX, NM, NP, NS, precision=precision, omega=omega[None])
+    if half_force:
+        from paper_2211_09815_gb300 import pm
+        make_ctx(8.0, 8, 4, 1)[0].close()   # builds and loads the library
+        ctx = pm.PMContext(BOX, NM, NP, NS, [inputs.THETA_FIDUCIAL],
+                           torch.from_numpy(omega[None].astype(np.float32)).cuda(), half_force=True)
+    else:
+        ctx, *_ = make_ctx(BOX, NM, NP, NS, precision=precision, omega=omega[None])
     dt = ctx.dtype
     N, M = NP ** 3, NM ** 3
     disp = torch.empty(3 * N, device="cuda", dtype=dt)
@@ -76,3 +82,71 @@ def test_fp32_against_fp64_at_128_cubed():
     print(f"FP32 vs FP64: disp {d32 / cell:.2e} cell, dJ/domega rel-L2 {err:.2e}; FP64 moved by {k:.1f} FP32 ulps: "
           f"disp {dk / cell:.2e} cell, dJ/domega rel-L2 {floor:.2e}")
     assert err <= 3.0 * floor
+
+
+def test_fp16_force_mesh_against_fp64_at_128_cubed():
+    """The reduced-precision form (pm_config.half_force: FP16 force meshes with a power-of-two
+    scale per row and field) against FP64: the forward targets (displacement <= 1e-3 cell,
+    P(k) <= 1e-4) and dJ/domega cosine >= 0.999 still hold; its errors exceed the FP32 form's
+    (FP16 keeps 11 significant bits of a force value where FP32 keeps 24)."""
+    torch = torch_cuda()
+    om = inputs.white_noise(NP, 1).astype(np.float64)
+    ctx, *_ = make_ctx(BOX, NM, NP, NS, precision=1, omega=inputs.white_noise(NP, 2).astype(np.float64)[None])
+    t = torch.empty(NM ** 3, device="cuda", dtype=torch.float64)
+    ctx.forward(dens=t)
+    target = t.cpu().numpy()
+    ctx.close()
+    cell = BOX / NM
+    s64, pk64, nmodes, g64, gt64 = _run(1, om, target)
+    s32, pk32, _, g32, _ = _run(0, om, target)
+    s16, pk16, _, g16, gt16 = _run(0, om, target, half_force=True)
+    d16 = np.sqrt(np.mean((s16 - s64) ** 2))
+    d32 = np.sqrt(np.mean((s32 - s64) ** 2))
+    ok = nmodes > 0
+    ok[0] = False
+    print(f"FP16 force mesh: disp {d16 / cell:.2e} cell (FP32 {d32 / cell:.2e}), P(k) "
+          f"{np.max(np.abs(pk16[ok] / pk64[ok] - 1)):.2e}, dJ/domega cosine {cosine(g16, g64):.7f}, "
+          f"rel-L2 {rel_l2(g16, g64):.2e}")
+    assert d16 <= 1e-3 * cell
+    assert np.max(np.abs(pk16[ok] / pk64[ok] - 1)) <= 1e-4
+    assert cosine(g16, g64) >= 0.999
+    assert np.all(np.abs(gt16 / gt64 - 1) <= 3e-2)
+    assert d16 > d32   # the reduced form is really in use
+
+
+def test_fp16_force_mesh_operator_error_is_fp16_rounding():
+    """pm_op_force and pm_op_force_vjp with the FP16 mesh against the FP32 mesh on the same
+    clustered state.  A mesh value is rounded to within 2^-11 of its row's largest, and the
+    CIC weights sum to 1, so every acceleration moves by at most 2^-11 of the largest force
+    (asserted: 2^-10 of the largest acceleration).  alpha takes differences of corner values
+    (the CIC weight gradient), so its rounding does not shrink with it: relative L2 <= 1e-2.
+    Both forms are bitwise deterministic."""
+    torch = torch_cuda()
+    from paper_2211_09815_gb300 import pm
+    make_ctx(8.0, 8, 4, 1)[0].close()
+    box, nm, npc = 100.0, 128, 64
+    N = npc ** 3
+    om = torch.from_numpy(inputs.white_noise(npc, 1)[None]).cuda()
+    cell = box / nm
+    disp = torch.from_numpy((3.0 * cell * np.stack([inputs.white_noise(npc, 41 + c).ravel() for c in range(3)]))
+                            .astype(np.float32)).cuda().reshape(-1)
+    pi = torch.from_numpy(np.stack([inputs.white_noise(npc, 51 + c).ravel() for c in range(3)])
+                          .astype(np.float32)).cuda().reshape(-1)
+    out = {}
+    for hf in (False, True, True):
+        ctx = pm.PMContext(box, nm, npc, 1, [inputs.THETA_FIDUCIAL], om, half_force=hf)
+        acc = torch.empty(3 * N, device="cuda")
+        acc2, alpha = torch.empty_like(acc), torch.empty_like(acc)
+        ctx.op_force(disp, acc)
+        ctx.op_force_vjp(disp, pi, acc2, alpha)
+        ctx.close()
+        res = (acc.cpu().numpy(), alpha.cpu().numpy())
+        if hf in out:
+            assert all(np.array_equal(a, b) for a, b in zip(res, out[hf]))
+        out[hf] = res
+    (a32, al32), (a16, al16) = out[False], out[True]
+    print(f"FP16 mesh: acc max error {np.max(np.abs(a16 - a32)) / np.max(np.abs(a32)):.2e} of max, "
+          f"alpha rel-L2 {rel_l2(al16, al32):.2e}")
+    assert np.max(np.abs(a16 - a32)) <= 2.0 ** -10 * np.max(np.abs(a32))
+    assert rel_l2(al16, al32) <= 1e-2
+    assert np.max(np.abs(a16 - a32)) > 0.0 and np.max(np.abs(al16 - al32)) > 0.0
