@@ -395,10 +395,18 @@ k_fft_x_c2r4(RowJob<T> job, int nrows, int dq, void* __restrict__ out, signed ch
     __shared__ float sscale[RT * 4];
     for (int k = threadIdx.x; k < RT * 4; k += TL::NT) smax[k] = 0u;
     __syncthreads();
+    // with L and NT multiples of 32, a warp's 32 items lie in one sequence and every lane
+    // runs the same iterations: one reduction and one atomic per warp
     for (int k = threadIdx.x; k < Q * RT * L; k += TL::NT) {
       const int c = k / L, j = k % L;   // sequence c = q RT + row
       const C v = sm[srow(j) * TL::LD + c];
-      atomicMax(&smax[(c % RT) * 4 + c / RT], __float_as_uint(fmaxf(fabsf(v.x), fabsf(v.y))));
+      unsigned m = __float_as_uint(fmaxf(fabsf(v.x), fabsf(v.y)));
+      if constexpr (L % 32 == 0 && TL::NT % 32 == 0) {
+        m = __reduce_max_sync(0xFFFFFFFFu, m);
+        if ((threadIdx.x & 31) == 0) atomicMax(&smax[(c % RT) * 4 + c / RT], m);
+      } else {
+        atomicMax(&smax[(c % RT) * 4 + c / RT], m);
+      }
     }
     __syncthreads();
     for (int k = threadIdx.x; k < RT * 4; k += TL::NT) {
